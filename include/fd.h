@@ -1,0 +1,182 @@
+/*
+ * fd.h -- C ABI of the B300 finite-difference time-stepping library.
+ *
+ * One context (fd_ctx) holds one simulation on one GPU: a structured 2-D or
+ * 3-D grid, its time levels and model coefficients in HBM, optional point
+ * sources and receivers, and a CUDA stream.  The calls follow the problem
+ * statement of a Devito operator (thesis §2.1.1: Grid(shape, extent),
+ * TimeFunction(time_order, space_order), initial data written into u.data[0],
+ * sparse functions for sources and receivers, op(time=nt, dt=dt)) and the
+ * benchmark problem of §5.1.2.
+ *
+ * Equations (L = Σ_d (1/h_d²) Σ_{k=-r..r} w_|k| shift_d^k, r = space_order/2,
+ * w = central second-derivative weights of order space_order; outside the grid
+ * every field is zero):
+ *
+ *   FD_DIFFUSION  (§5.1.2, u_t = ν Σ_d u_dd, forward Euler, time order 1):
+ *       u^{n+1} = u^n + ν dt L u^n     on interior nodes (index 1..n_d-2 on
+ *       every axis, §2.1.1's grid.interior); boundary nodes keep the values
+ *       given to fd_set_field.
+ *   FD_ACOUSTIC   (the seismic operator of §6.2.1, m u_tt + damp u_t = L u + src,
+ *       second-order leapfrog on every node, σ = damp·dt/2):
+ *       u^{n+1} = [dt² L u^n + 2m u^n - (m-σ) u^{n-1}] / (m+σ)
+ *       then u^{n+1}(node) += wgt·dt²·s_j(t_n)/m(node) over the 2^D multilinear
+ *       corners of every source j, and rec_k(t_{n+1}) = Σ wgt·u^{n+1}(node).
+ *   Time levels rotate by pointer (§3.3.2: t0 = time mod 2, t1 = (time+1) mod 2).
+ *
+ * Arrays crossing this boundary are float32, dense, C order, interior only
+ * (no halo): 3-D [n0][n1][n2], 2-D [n0][n1], last axis contiguous.  Axis d has
+ * shape[d] nodes at coordinates i·spacing[d], i = 0..shape[d]-1.  Coordinates
+ * are float32 [npoints][ndim] in the same axis order.  Multilinear corners:
+ * x = c/h, i = floor(x), f = x - i, a point on the last node uses i = n-2,
+ * f = 1; x within 1e-9·(n-1) beyond an end is snapped onto it; further out is
+ * FD_EINVAL.
+ *
+ * Ownership: every pointer argument is borrowed for the duration of the call;
+ * its contents are copied.  By default pointers are host pointers (any host
+ * memory; pinned memory makes the copies asynchronous).  With
+ * fd_options.device_ptrs = 1 they are device pointers valid on the context's
+ * stream.  All library memory is allocated by fd_create/fd_set_* and freed by
+ * fd_destroy.
+ *
+ * Errors: every call returns an fd_status; fd_last_error() gives the text.  A
+ * CUDA error makes the context failed: every later call returns FD_ECUDA until
+ * fd_destroy.  Calls in the wrong order return FD_ESTATE.  Not thread-safe per
+ * context; separate contexts are independent.
+ */
+#ifndef FD_B300_FD_H
+#define FD_B300_FD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fd_ctx fd_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  FD_OK = 0,
+  FD_EINVAL = 1,       /* bad argument (shape, order, dt above the stability limit, ...) */
+  FD_ENOMEM = 2,       /* device or host allocation failed */
+  FD_ECUDA = 3,        /* CUDA error; the context is failed from now on */
+  FD_ESTATE = 4,       /* call out of order (e.g. fd_run before fd_set_model) */
+  FD_ETIMEOUT = 5,     /* a kernel's bounded wait expired (reported by fd_read) */
+  FD_EUNSUPPORTED = 6  /* valid request this build does not provide */
+} fd_status;
+
+typedef enum { FD_DIFFUSION = 0, FD_ACOUSTIC = 1 } fd_equation;
+
+typedef enum {
+  FD_KERNEL_AUTO = 0,  /* pipelined kernel where available, else plain */
+  FD_KERNEL_PLAIN = 1, /* one thread per point, neighbours through L1/L2 */
+  FD_KERNEL_TMA = 2    /* 3-D: TMA-fed shared-memory plane ring, z streamed in registers */
+} fd_kernel;
+
+typedef struct {
+  double nu;          /* diffusion coefficient ν (FD_DIFFUSION only); default 0.5,
+                         the benchmark value of §5.1.2 */
+  void *cuda_stream;  /* cudaStream_t for all work; NULL: the library creates one */
+  int device_ptrs;    /* 1: array arguments are device pointers (see Ownership) */
+  int use_graphs;     /* 1 (default): fd_run replays captured CUDA graphs of the step loop */
+  int profile;        /* 1: time every stencil launch with CUDA events (fd_profile);
+                         steps are launched one by one instead of by graph */
+  int kernel;         /* fd_kernel; default FD_KERNEL_AUTO */
+} fd_options;
+
+/* Fill *opt with the defaults above. */
+void fd_options_default(fd_options *opt);
+
+/*
+ * Create a context.  ndim ∈ {2,3}; shape[d] ≥ 1 (FD_ACOUSTIC: ≥ 2);
+ * spacing[d] > 0; space_order even in [2,16]; dt > 0.  FD_DIFFUSION checks
+ * stability here: ν dt Σ_d S/h_d² ≤ 2 with S = -(w_0 + 2 Σ_k (-1)^k w_k);
+ * FD_ACOUSTIC checks it in fd_set_model.  Fields start at zero.  opt may be
+ * NULL (defaults).  On failure *out is NULL.
+ */
+fd_status fd_create(fd_ctx **out, int ndim, const int64_t *shape,
+                    const double *spacing, int space_order, double dt,
+                    fd_equation eq, const fd_options *opt);
+
+/*
+ * FD_ACOUSTIC: squared slowness m (> 0 everywhere) and damping coefficient
+ * damp (≥ 0; NULL means 0).  Rejects dt above the leapfrog limit
+ * 2 / sqrt(max(1/m) · Σ_d S/h_d²) with FD_EINVAL.  May be called again.
+ */
+fd_status fd_set_model(fd_ctx *ctx, const float *m, const float *damp);
+
+/*
+ * Set the current time level(s).  FD_ACOUSTIC: u_cur = u^n, u_prev = u^{n-1}
+ * (NULL: equal to u_cur).  FD_DIFFUSION: u_cur only (u_prev ignored); the
+ * boundary values given here are held.  Does not change the step counter.
+ */
+fd_status fd_set_field(fd_ctx *ctx, const float *u_cur, const float *u_prev);
+
+/*
+ * FD_ACOUSTIC: nsrc point sources at coords [nsrc][ndim] with wavelets
+ * [nt][nsrc] (row n = s(t_n) for global step n).  Replaces earlier sources;
+ * nsrc = 0 removes them.  fd_run fails with FD_EINVAL if it would pass step nt.
+ */
+fd_status fd_set_sources(fd_ctx *ctx, int nsrc, const float *coords, int nt,
+                         const float *wavelets);
+
+/*
+ * FD_ACOUSTIC: nrec receivers at coords [nrec][ndim].  Traces are recorded
+ * for every step run afterwards: row 0 = interpolation of u at step 0, row
+ * n+1 after step n (the library grows the trace buffer as needed).
+ * Replaces earlier receivers and clears recorded traces.
+ */
+fd_status fd_set_receivers(fd_ctx *ctx, int nrec, const float *coords);
+
+/* Advance nt ≥ 0 steps (asynchronous on the context stream). */
+fd_status fd_run(fd_ctx *ctx, int nt);
+
+/*
+ * Copy results out and synchronise the stream.  u: current level u^n
+ * (dense, interior), NULL to skip.  rec: traces [n+1][nrec] for the steps
+ * run so far (n = fd_steps_done), NULL to skip.  Returns FD_ETIMEOUT if a
+ * kernel reported an expired wait.
+ */
+fd_status fd_read(fd_ctx *ctx, float *u, float *rec);
+
+/* Previous level u^{n-1} (FD_ACOUSTIC), for checkpoint/resume; syncs. */
+fd_status fd_read_prev(fd_ctx *ctx, float *u_prev);
+
+/* Set the global step counter (resume from a checkpoint at step n ≥ 0). */
+fd_status fd_set_step(fd_ctx *ctx, int64_t n);
+
+/* Steps advanced so far (the global step counter); -1 for NULL. */
+int64_t fd_steps_done(const fd_ctx *ctx);
+
+/*
+ * Profiling (fd_options.profile = 1): number of stencil launches and their
+ * summed CUDA-event time in ms since the last call; synchronises and resets.
+ */
+fd_status fd_profile(fd_ctx *ctx, int64_t *launches, double *stencil_ms);
+
+/* Name of the stencil kernel variant fd_run launches (static string). */
+const char *fd_kernel_name(const fd_ctx *ctx);
+
+/* Release everything.  NULL is a no-op. */
+void fd_destroy(fd_ctx *ctx);
+
+/* Text of the last error on ctx (or of the last failed fd_create when ctx is NULL). */
+const char *fd_last_error(const fd_ctx *ctx);
+
+/*
+ * Host-only helpers (no GPU needed).
+ * fd_weights: w_0..w_r (r = space_order/2) of the central second-derivative
+ *   stencil, as the library uses them; returns FD_EINVAL for a bad order.
+ * fd_stability_symbol: S = -(w_0 + 2 Σ_k (-1)^k w_k) for that order (NaN if bad).
+ */
+fd_status fd_weights(int space_order, double *w);
+double fd_stability_symbol(int space_order);
+
+/* Library version string. */
+const char *fd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FD_B300_FD_H */

@@ -1,0 +1,229 @@
+"""Thin ctypes binding of the C ABI in include/fd.h (argument marshalling only).
+
+Every function keeps the C name and meaning.  Arrays may be numpy arrays (host)
+or torch CUDA tensors (device; the context must then be created with
+``device_ptrs=1``); they must be float32 and C-contiguous, or they are
+converted.  Statuses other than FD_OK raise :class:`FdError` carrying the
+status and ``fd_last_error``.  There is no fallback: if the CUDA library is
+missing, loading fails loudly.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfd_b300.so")
+
+FD_OK, FD_EINVAL, FD_ENOMEM, FD_ECUDA, FD_ESTATE, FD_ETIMEOUT, FD_EUNSUPPORTED = range(7)
+STATUS_NAMES = ["FD_OK", "FD_EINVAL", "FD_ENOMEM", "FD_ECUDA", "FD_ESTATE", "FD_ETIMEOUT",
+                "FD_EUNSUPPORTED"]
+FD_DIFFUSION, FD_ACOUSTIC = 0, 1
+FD_KERNEL_AUTO, FD_KERNEL_PLAIN, FD_KERNEL_TMA = 0, 1, 2
+
+
+class FdError(RuntimeError):
+    def __init__(self, status, message):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {message}")
+
+
+class fd_options(ctypes.Structure):
+    _fields_ = [("nu", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
+                ("device_ptrs", ctypes.c_int), ("use_graphs", ctypes.c_int),
+                ("profile", ctypes.c_int), ("kernel", ctypes.c_int)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+
+# name -> (restype, argtypes); every entry point declared in include/fd.h
+SIGNATURES = {
+    "fd_options_default": (None, [ctypes.POINTER(fd_options)]),
+    "fd_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_i64),
+                                 ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_double,
+                                 ctypes.c_int, ctypes.POINTER(fd_options)]),
+    "fd_set_model": (ctypes.c_int, [_vp, _vp, _vp]),
+    "fd_set_field": (ctypes.c_int, [_vp, _vp, _vp]),
+    "fd_set_sources": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp]),
+    "fd_set_receivers": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+    "fd_run": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "fd_read": (ctypes.c_int, [_vp, _vp, _vp]),
+    "fd_read_prev": (ctypes.c_int, [_vp, _vp]),
+    "fd_set_step": (ctypes.c_int, [_vp, _i64]),
+    "fd_steps_done": (_i64, [_vp]),
+    "fd_profile": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double)]),
+    "fd_kernel_name": (ctypes.c_char_p, [_vp]),
+    "fd_destroy": (None, [_vp]),
+    "fd_last_error": (ctypes.c_char_p, [_vp]),
+    "fd_weights": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "fd_stability_symbol": (ctypes.c_double, [ctypes.c_int]),
+    "fd_version": (ctypes.c_char_p, []),
+}
+
+
+def load(path=None):
+    """Load libfd_b300.so (raises OSError if it is missing or unloadable)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OSError(f"CUDA library {p} is missing: build it with paper_1906_10811_b300.build.build()")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(ctx, st):
+    if st != FD_OK:
+        msg = load().fd_last_error(ctx)
+        raise FdError(st, msg.decode() if msg else "")
+
+
+def _ptr(x, keep):
+    """Address of a float32 C-contiguous array (numpy host array or torch tensor)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):                       # torch tensor
+        import torch
+        t = x.detach()
+        if t.dtype != torch.float32 or not t.is_contiguous():
+            t = t.to(torch.float32).contiguous()
+        keep.append(t)
+        return t.data_ptr()
+    a = np.ascontiguousarray(x, dtype=np.float32)
+    keep.append(a)
+    return a.ctypes.data
+
+
+def _out_ptr(x):
+    """Address of a preallocated float32 C-contiguous output (no conversion)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        import torch
+        assert x.dtype == torch.float32 and x.is_contiguous(), "outputs must be float32 contiguous"
+        return x.data_ptr()
+    assert x.dtype == np.float32 and x.flags.c_contiguous, "outputs must be float32 C-contiguous"
+    return x.ctypes.data
+
+
+def options(nu=0.5, cuda_stream=None, device_ptrs=False, use_graphs=True, profile=False,
+            kernel=FD_KERNEL_AUTO):
+    o = fd_options()
+    load().fd_options_default(ctypes.byref(o))
+    o.nu = nu
+    o.cuda_stream = cuda_stream
+    o.device_ptrs = int(bool(device_ptrs))
+    o.use_graphs = int(bool(use_graphs))
+    o.profile = int(bool(profile))
+    o.kernel = int(kernel)
+    return o
+
+
+def fd_options_default():
+    o = fd_options()
+    load().fd_options_default(ctypes.byref(o))
+    return o
+
+
+def fd_create(ndim, shape, spacing, space_order, dt, eq, opt=None):
+    lib = load()
+    shp = (_i64 * max(ndim, 1))(*[int(s) for s in shape][:max(ndim, 1)])
+    sp = (ctypes.c_double * max(ndim, 1))(*[float(h) for h in spacing][:max(ndim, 1)])
+    out = _vp()
+    st = lib.fd_create(ctypes.byref(out), ndim, shp, sp, int(space_order), float(dt), int(eq),
+                       ctypes.byref(opt) if opt is not None else None)
+    if st != FD_OK:
+        raise FdError(st, lib.fd_last_error(None).decode())
+    return out.value
+
+
+def fd_set_model(ctx, m, damp=None):
+    keep = []
+    _check(ctx, load().fd_set_model(ctx, _ptr(m, keep), _ptr(damp, keep)))
+
+
+def fd_set_field(ctx, u_cur, u_prev=None):
+    keep = []
+    _check(ctx, load().fd_set_field(ctx, _ptr(u_cur, keep), _ptr(u_prev, keep)))
+
+
+def fd_set_sources(ctx, nsrc, coords, nt, wavelets):
+    keep = []
+    _check(ctx, load().fd_set_sources(ctx, int(nsrc), _ptr(coords, keep), int(nt),
+                                      _ptr(wavelets, keep)))
+
+
+def fd_set_receivers(ctx, nrec, coords):
+    keep = []
+    _check(ctx, load().fd_set_receivers(ctx, int(nrec), _ptr(coords, keep)))
+
+
+def fd_run(ctx, nt):
+    _check(ctx, load().fd_run(ctx, int(nt)))
+
+
+def fd_read(ctx, u=None, rec=None):
+    """Fill the given preallocated outputs (numpy float32 or torch float32)."""
+    _check(ctx, load().fd_read(ctx, _out_ptr(u), _out_ptr(rec)))
+
+
+def fd_read_prev(ctx, u_prev):
+    _check(ctx, load().fd_read_prev(ctx, _out_ptr(u_prev)))
+
+
+def fd_set_step(ctx, n):
+    _check(ctx, load().fd_set_step(ctx, int(n)))
+
+
+def fd_steps_done(ctx):
+    return int(load().fd_steps_done(ctx))
+
+
+def fd_profile(ctx):
+    """(launches, stencil_ms) since the previous call."""
+    n = _i64()
+    ms = ctypes.c_double()
+    _check(ctx, load().fd_profile(ctx, ctypes.byref(n), ctypes.byref(ms)))
+    return int(n.value), float(ms.value)
+
+
+def fd_kernel_name(ctx):
+    return load().fd_kernel_name(ctx).decode()
+
+
+def fd_destroy(ctx):
+    if ctx:
+        load().fd_destroy(ctx)
+
+
+def fd_last_error(ctx=None):
+    return load().fd_last_error(ctx).decode()
+
+
+def fd_weights(space_order):
+    w = (ctypes.c_double * 9)()
+    st = load().fd_weights(int(space_order), w)
+    if st != FD_OK:
+        raise FdError(st, f"bad space order {space_order}")
+    return [w[k] for k in range(space_order // 2 + 1)]
+
+
+def fd_stability_symbol(space_order):
+    return float(load().fd_stability_symbol(int(space_order)))
+
+
+def fd_version():
+    return load().fd_version().decode()

@@ -1,0 +1,884 @@
+// fd_capi.cu -- runtime behind the C ABI of include/fd.h.
+//
+// A context owns: the padded time levels u[2] (rotated by pointer, thesis
+// §3.3.2), the acoustic coefficient fields A and C, a dense copy of m for the
+// source scaling, the sparse-operator tables, the trace buffer, a device step
+// counter, and the cached CUDA graphs of the step loop.  The host time loop of
+// an OPS program (one ops_par_loop per step, §3.3.3) becomes one graph replay
+// per chunk of steps; nothing crosses the host/device boundary inside a run.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/fd.h"
+#include "fd_common.cuh"
+#include "fd_kernels_plain.cuh"
+#include "fd_kernels_tma.cuh"
+
+using namespace fdk;
+
+namespace {
+
+constexpr int kGraphChunk = 64;  // steps per captured graph
+constexpr int kGraphCacheMax = 6;
+thread_local std::string g_create_error;  // fd_last_error(NULL)
+
+// ---------------------------------------------------------------------------
+// Weights: closed form of the central second-derivative stencil of order 2r,
+//   w_k = 2 (-1)^(k+1) / k² · Π_{i=0}^{k-1} (r-i) / Π_{i=1}^{k} (r+i),
+//   w_0 = -2 Σ_{k≥1} w_k,
+// evaluated in long double.
+// ---------------------------------------------------------------------------
+bool lib_weights(int so, double *w) {
+  if (so < 2 || so > 2 * kMaxR || (so & 1)) return false;
+  const int r = so / 2;
+  long double sum = 0.0L;
+  for (int k = 1; k <= r; ++k) {
+    long double ratio = 1.0L;
+    for (int i = 0; i < k; ++i) ratio *= (long double)(r - i) / (long double)(r + i + 1);
+    const long double wk = (k % 2 ? 2.0L : -2.0L) / ((long double)k * k) * ratio;
+    w[k] = (double)wk;
+    sum += wk;
+  }
+  w[0] = (double)(-2.0L * sum);
+  return true;
+}
+
+double lib_symbol(int so) {
+  double w[kMaxR + 1];
+  if (!lib_weights(so, w)) return NAN;
+  double s = w[0];
+  for (int k = 1; k <= so / 2; ++k) s += 2.0 * (k % 2 ? -w[k] : w[k]);
+  return -s;
+}
+
+struct GraphEntry {
+  int parity;
+  int len;
+  cudaGraphExec_t exec;
+};
+
+using StencilFn = void (*)(const float *, float *, const float *, const float *, Geom, Coef);
+
+}  // namespace
+
+struct fd_ctx {
+  // problem
+  int ndim = 0;
+  int64_t shape[3] = {1, 1, 1};
+  double h[3] = {1, 1, 1};
+  int so = 0;
+  double dt = 0;
+  fd_equation eq = FD_DIFFUSION;
+  fd_options opt{};
+  Geom g{};
+  Coef coef{};
+  int nc = 0;  // 2^ndim corners
+  // device
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  float *u[2] = {nullptr, nullptr};
+  int cur = 0;  // u[cur] = u^n, u[cur ^ 1] = u^{n-1}
+  float *A = nullptr, *C = nullptr, *m_dense = nullptr, *stage = nullptr;
+  int64_t *d_step = nullptr;
+  unsigned *d_stats = nullptr;
+  int *d_err = nullptr;
+  // kernel selection
+  StencilFn plain_fn = nullptr;
+  TmaPlan tma{};
+  bool use_tma = false;
+  const char *kernel_name = "none";
+  // sources
+  int nsrc = 0, nt_wav = 0;
+  float *wav = nullptr, *src_scale = nullptr;
+  int64_t *src_off = nullptr, *src_dense = nullptr;
+  double *src_w = nullptr;
+  bool src_dirty = false;
+  // receivers
+  int nrec = 0;
+  int64_t *rec_off = nullptr;
+  float *rec_w = nullptr, *rec = nullptr;
+  int64_t rec_cap = 0;   // rows
+  int64_t rec_rows = 0;  // rows recorded (valid)
+  // state
+  bool model_set = false;
+  int64_t step = 0;
+  bool failed = false;
+  std::string err;
+  std::vector<GraphEntry> graphs;
+  // profiling
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used = 0;
+};
+
+namespace {
+
+fd_status fail(fd_ctx *c, fd_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) {
+    c->err = buf;
+    if (st == FD_ECUDA) c->failed = true;
+  } else {
+    g_create_error = buf;
+  }
+  return st;
+}
+
+#define CU(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? FD_ENOMEM : FD_ECUDA,           \
+                  "%s failed: %s", #call, cudaGetErrorString(e_));                     \
+  } while (0)
+
+#define CHECK_LAUNCH() CU(cudaGetLastError())
+
+fd_status check_usable(fd_ctx *c) {
+  if (!c) return FD_EINVAL;
+  if (c->failed) return FD_ECUDA;
+  CU(cudaSetDevice(c->device));
+  return FD_OK;
+}
+
+template <typename T>
+fd_status dalloc(fd_ctx *c, T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(c, e == cudaErrorMemoryAllocation ? FD_ENOMEM : FD_ECUDA,
+                "cudaMalloc(%zu bytes): %s", count * sizeof(T), cudaGetErrorString(e));
+  }
+  return FD_OK;
+}
+
+template <typename T>
+void dfree(T *&p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void drop_graphs(fd_ctx *c) {
+  for (auto &gph : c->graphs) cudaGraphExecDestroy(gph.exec);
+  c->graphs.clear();
+}
+
+// Copy n elements of user data (host or device per options) to a device buffer.
+template <typename T>
+fd_status to_device(fd_ctx *c, T *dst, const T *src, size_t n) {
+  if (n == 0) return FD_OK;
+  CU(cudaMemcpyAsync(dst, src, n * sizeof(T),
+                     c->opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     c->stream));
+  return FD_OK;
+}
+
+// User coordinates (host or device) -> host vector.
+fd_status coords_to_host(fd_ctx *c, const float *src, size_t n, std::vector<float> &out) {
+  out.resize(n);
+  if (n == 0) return FD_OK;
+  if (c->opt.device_ptrs) {
+    CU(cudaMemcpyAsync(out.data(), src, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+  } else {
+    std::memcpy(out.data(), src, n * sizeof(float));
+  }
+  return FD_OK;
+}
+
+int blocks_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 148 * 32));
+}
+
+// Scatter a dense interior array (host or device) into a padded field.
+fd_status load_field(fd_ctx *c, float *padded, const float *user) {
+  const size_t n = (size_t)c->g.n0 * c->g.n1 * c->g.n2;
+  const float *src = user;
+  if (!c->opt.device_ptrs) {
+    CU(cudaMemcpyAsync(c->stage, user, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    src = c->stage;
+  }
+  k_scatter<<<blocks_for(n, 256), 256, 0, c->stream>>>(src, padded, c->g);
+  CHECK_LAUNCH();
+  return FD_OK;
+}
+
+fd_status store_field(fd_ctx *c, const float *padded, float *user) {
+  const size_t n = (size_t)c->g.n0 * c->g.n1 * c->g.n2;
+  float *dst = c->opt.device_ptrs ? user : c->stage;
+  k_gather<<<blocks_for(n, 256), 256, 0, c->stream>>>(padded, dst, c->g);
+  CHECK_LAUNCH();
+  if (!c->opt.device_ptrs)
+    CU(cudaMemcpyAsync(user, c->stage, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  return FD_OK;
+}
+
+// Multilinear corners of one point (the rule documented in fd.h).
+bool corners(const fd_ctx *c, const float *pt, int64_t *pad_off, int64_t *dense_idx, double *w) {
+  int64_t i[3] = {0, 0, 0};
+  double f[3] = {0, 0, 0};
+  for (int d = 0; d < c->ndim; ++d) {
+    const int64_t n = c->shape[d];
+    if (n < 2) return false;
+    double x = (double)pt[d] / c->h[d];
+    const double last = (double)(n - 1), tol = 1e-9 * last;
+    if (!(x >= -tol && x <= last + tol)) return false;
+    x = std::min(std::max(x, 0.0), last);
+    i[d] = (int64_t)std::floor(x);
+    f[d] = x - (double)i[d];
+    if (i[d] == n - 1) {
+      i[d] = n - 2;
+      f[d] = 1.0;
+    }
+  }
+  for (int b = 0; b < c->nc; ++b) {
+    int64_t node[3] = {0, 0, 0};
+    double wt = 1.0;
+    for (int d = 0; d < c->ndim; ++d) {
+      const int bit = (b >> (c->ndim - 1 - d)) & 1;
+      node[d] = i[d] + bit;
+      wt *= bit ? f[d] : 1.0 - f[d];
+    }
+    int z, y, x;
+    if (c->ndim == 3) {
+      z = (int)node[0]; y = (int)node[1]; x = (int)node[2];
+    } else {
+      z = 0; y = (int)node[0]; x = (int)node[1];
+    }
+    pad_off[b] = gidx(c->g, z, y, x);
+    dense_idx[b] = ((int64_t)z * c->g.n1 + y) * c->g.n2 + x;
+    w[b] = wt;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Launching one step.
+// ---------------------------------------------------------------------------
+fd_status launch_stencil(fd_ctx *c, const float *ucur, float *unext) {
+  if (c->use_tma) {
+    cudaError_t e = launch_tma_step(c->tma, ucur == c->u[0] ? 0 : 1, unext, c->A, c->C,
+                                    c->coef, c->d_err, c->stream);
+    if (e != cudaSuccess) return fail(c, FD_ECUDA, "TMA stencil launch: %s", cudaGetErrorString(e));
+    return FD_OK;
+  }
+  dim3 block(32, 8);
+  dim3 grid((c->g.n2 + 31) / 32, (c->g.n1 + 7) / 8, c->g.n0);
+  c->plain_fn<<<grid, block, 0, c->stream>>>(ucur, unext, c->A, c->C, c->g, c->coef);
+  CHECK_LAUNCH();
+  return FD_OK;
+}
+
+fd_status launch_sparse(fd_ctx *c, float *unext, int j) {
+  if (c->eq != FD_ACOUSTIC || (c->nsrc == 0 && c->nrec == 0)) return FD_OK;
+  const bool small = c->nsrc * c->nc <= 2048 && c->nrec * c->nc <= 2048;
+  if (small) {
+    if (c->nc == 8)
+      k_sparse_fused<8><<<1, 512, 0, c->stream>>>(unext, c->d_step, j, c->nsrc, c->src_off,
+                                                   c->src_scale, c->wav, c->nrec, c->rec_off,
+                                                   c->rec_w, c->rec);
+    else
+      k_sparse_fused<4><<<1, 512, 0, c->stream>>>(unext, c->d_step, j, c->nsrc, c->src_off,
+                                                   c->src_scale, c->wav, c->nrec, c->rec_off,
+                                                   c->rec_w, c->rec);
+    CHECK_LAUNCH();
+    return FD_OK;
+  }
+  if (c->nsrc) {
+    const int n = c->nsrc * c->nc;
+    if (c->nc == 8)
+      k_inject<8><<<(n + 255) / 256, 256, 0, c->stream>>>(unext, c->d_step, j, c->nsrc,
+                                                           c->src_off, c->src_scale, c->wav);
+    else
+      k_inject<4><<<(n + 255) / 256, 256, 0, c->stream>>>(unext, c->d_step, j, c->nsrc,
+                                                           c->src_off, c->src_scale, c->wav);
+    CHECK_LAUNCH();
+  }
+  if (c->nrec) {
+    const int n = c->nrec * c->nc;
+    if (c->nc == 8)
+      k_interp<8><<<(n + 255) / 256, 256, 0, c->stream>>>(unext, c->d_step, j, c->nrec,
+                                                           c->rec_off, c->rec_w, c->rec);
+    else
+      k_interp<4><<<(n + 255) / 256, 256, 0, c->stream>>>(unext, c->d_step, j, c->nrec,
+                                                           c->rec_off, c->rec_w, c->rec);
+    CHECK_LAUNCH();
+  }
+  return FD_OK;
+}
+
+// Record row 0 = interp(u^0) (needs *d_step = 0).
+fd_status launch_interp_row0(fd_ctx *c) {
+  const int n = c->nrec * c->nc;
+  if (c->nc == 8)
+    k_interp<8><<<(n + 255) / 256, 256, 0, c->stream>>>(c->u[c->cur], c->d_step, -1, c->nrec,
+                                                         c->rec_off, c->rec_w, c->rec);
+  else
+    k_interp<4><<<(n + 255) / 256, 256, 0, c->stream>>>(c->u[c->cur], c->d_step, -1, c->nrec,
+                                                         c->rec_off, c->rec_w, c->rec);
+  CHECK_LAUNCH();
+  return FD_OK;
+}
+
+// Steps j = 0..len-1 of a chunk starting with u^n in u[parity]; ends by
+// advancing the device step counter by len.
+fd_status enqueue_chunk(fd_ctx *c, int parity, int len, bool timed) {
+  for (int j = 0; j < len; ++j) {
+    const int b = parity ^ (j & 1);
+    float *ucur = c->u[b], *unext = c->u[b ^ 1];
+    if (timed) {
+      if (c->ev_used + 2 > c->ev.size()) {
+        for (int k = 0; k < 64; ++k) {
+          cudaEvent_t e;
+          CU(cudaEventCreate(&e));
+          c->ev.push_back(e);
+        }
+      }
+      CU(cudaEventRecord(c->ev[c->ev_used], c->stream));
+    }
+    fd_status st = launch_stencil(c, ucur, unext);
+    if (st) return st;
+    if (timed) {
+      CU(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
+      c->ev_used += 2;
+    }
+    st = launch_sparse(c, unext, j);
+    if (st) return st;
+  }
+  k_advance_step<<<1, 1, 0, c->stream>>>(c->d_step, len);
+  CHECK_LAUNCH();
+  return FD_OK;
+}
+
+fd_status get_graph(fd_ctx *c, int parity, int len, cudaGraphExec_t *out) {
+  for (auto &gph : c->graphs)
+    if (gph.parity == parity && gph.len == len) {
+      *out = gph.exec;
+      return FD_OK;
+    }
+  if ((int)c->graphs.size() >= kGraphCacheMax) {
+    cudaGraphExecDestroy(c->graphs.front().exec);
+    c->graphs.erase(c->graphs.begin());
+  }
+  cudaGraph_t graph;
+  CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  fd_status st = enqueue_chunk(c, parity, len, false);
+  cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  if (st) {
+    if (e == cudaSuccess) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(c, FD_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+  cudaGraphExec_t exec;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(c, FD_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  c->graphs.push_back({parity, len, exec});
+  *out = exec;
+  return FD_OK;
+}
+
+// Make the trace buffer hold at least `rows` rows (keeps recorded rows).
+fd_status ensure_rec_capacity(fd_ctx *c, int64_t rows) {
+  if (c->nrec == 0 || rows <= c->rec_cap) return FD_OK;
+  int64_t cap = std::max<int64_t>(rows, std::max<int64_t>(2 * c->rec_cap, 1024));
+  float *nb = nullptr;
+  fd_status st = dalloc(c, &nb, (size_t)cap * c->nrec);
+  if (st) return st;
+  cudaError_t e = cudaMemsetAsync(nb, 0, (size_t)cap * c->nrec * sizeof(float), c->stream);
+  if (e == cudaSuccess && c->rec && c->rec_rows > 0)
+    e = cudaMemcpyAsync(nb, c->rec, (size_t)c->rec_rows * c->nrec * sizeof(float),
+                        cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) {
+    cudaFree(nb);
+    return fail(c, FD_ECUDA, "trace buffer growth: %s", cudaGetErrorString(e));
+  }
+  CU(cudaStreamSynchronize(c->stream));
+  dfree(c->rec);
+  c->rec = nb;
+  c->rec_cap = cap;
+  drop_graphs(c);
+  return FD_OK;
+}
+
+fd_status prepare_sources(fd_ctx *c) {
+  if (!c->src_dirty || c->nsrc == 0) return FD_OK;
+  const int n = c->nsrc * c->nc;
+  k_source_scales<<<(n + 255) / 256, 256, 0, c->stream>>>(c->src_dense, c->src_w, c->m_dense,
+                                                           c->src_scale, n, c->dt);
+  CHECK_LAUNCH();
+  c->src_dirty = false;
+  return FD_OK;
+}
+
+void select_kernel(fd_ctx *c) {
+  const int R = c->so / 2;
+  const bool three = c->ndim == 3;
+  const bool ac = c->eq == FD_ACOUSTIC;
+#define PICK(RR)                                                                       \
+  case RR:                                                                             \
+    c->plain_fn = three ? (ac ? k_stencil_plain<RR, kAcoustic, true>                   \
+                              : k_stencil_plain<RR, kDiffusion, true>)                 \
+                        : (ac ? k_stencil_plain<RR, kAcoustic, false>                  \
+                              : k_stencil_plain<RR, kDiffusion, false>);               \
+    break;
+  switch (R) {
+    PICK(1) PICK(2) PICK(3) PICK(4) PICK(5) PICK(6) PICK(7) PICK(8)
+  }
+#undef PICK
+  c->kernel_name = three ? "stencil3d_plain" : "stencil2d_plain";
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void fd_options_default(fd_options *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->nu = 0.5;
+  o->use_graphs = 1;
+  o->kernel = FD_KERNEL_AUTO;
+}
+
+const char *fd_version(void) { return "fd_b300 0.1 (sm_103a)"; }
+
+fd_status fd_weights(int space_order, double *w) {
+  if (!w) return FD_EINVAL;
+  return lib_weights(space_order, w) ? FD_OK : FD_EINVAL;
+}
+
+double fd_stability_symbol(int space_order) { return lib_symbol(space_order); }
+
+fd_status fd_create(fd_ctx **out, int ndim, const int64_t *shape, const double *spacing,
+                    int space_order, double dt, fd_equation eq, const fd_options *opt) {
+  fd_ctx *c = nullptr;
+  if (!out) return fail(nullptr, FD_EINVAL, "out is NULL");
+  *out = nullptr;
+  g_create_error.clear();
+  if (ndim != 2 && ndim != 3) return fail(nullptr, FD_EINVAL, "ndim must be 2 or 3 (got %d)", ndim);
+  if (!shape || !spacing) return fail(nullptr, FD_EINVAL, "shape/spacing is NULL");
+  if (eq != FD_DIFFUSION && eq != FD_ACOUSTIC)
+    return fail(nullptr, FD_EINVAL, "unknown equation %d", (int)eq);
+  if (space_order < 2 || space_order > 2 * kMaxR || (space_order & 1))
+    return fail(nullptr, FD_EINVAL, "space_order must be even in [2,16] (got %d)", space_order);
+  const int64_t nmin = eq == FD_ACOUSTIC ? 2 : 1;
+  int64_t npts = 1;
+  for (int d = 0; d < ndim; ++d) {
+    if (shape[d] < nmin || shape[d] > (1 << 20))
+      return fail(nullptr, FD_EINVAL, "shape[%d] = %lld out of range", d, (long long)shape[d]);
+    if (!(spacing[d] > 0.0) || !std::isfinite(spacing[d]))
+      return fail(nullptr, FD_EINVAL, "spacing[%d] must be positive and finite", d);
+    npts *= shape[d];
+  }
+  if (npts > ((int64_t)1 << 34)) return fail(nullptr, FD_EINVAL, "grid too large");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(nullptr, FD_EINVAL, "dt must be positive and finite");
+  fd_options o;
+  fd_options_default(&o);
+  if (opt) o = *opt;
+  if (o.kernel < FD_KERNEL_AUTO || o.kernel > FD_KERNEL_TMA)
+    return fail(nullptr, FD_EINVAL, "unknown kernel selector %d", o.kernel);
+  const double S = lib_symbol(space_order);
+  if (eq == FD_DIFFUSION) {
+    if (!(o.nu > 0.0) || !std::isfinite(o.nu)) return fail(nullptr, FD_EINVAL, "nu must be positive");
+    double lam = 0.0;
+    for (int d = 0; d < ndim; ++d) lam += S / (spacing[d] * spacing[d]);
+    if (o.nu * dt * lam > 2.0 * (1.0 + 1e-12))
+      return fail(nullptr, FD_EINVAL,
+                  "dt = %g exceeds the forward-Euler limit %g (nu dt sum S/h^2 <= 2)", dt,
+                  2.0 / (o.nu * lam));
+  }
+
+  c = new (std::nothrow) fd_ctx();
+  if (!c) return fail(nullptr, FD_ENOMEM, "host allocation failed");
+  c->ndim = ndim;
+  for (int d = 0; d < ndim; ++d) {
+    c->shape[d] = shape[d];
+    c->h[d] = spacing[d];
+  }
+  c->so = space_order;
+  c->dt = dt;
+  c->eq = eq;
+  c->opt = o;
+  c->nc = 1 << ndim;
+  const int R = space_order / 2;
+  Geom &g = c->g;
+  if (ndim == 3) {
+    g.n0 = (int)shape[0]; g.n1 = (int)shape[1]; g.n2 = (int)shape[2];
+    g.R0 = R;
+  } else {
+    g.n0 = 1; g.n1 = (int)shape[0]; g.n2 = (int)shape[1];
+    g.R0 = 0;
+  }
+  g.R = R;
+  g.px = kHaloX + ((g.n2 + R + 31) / 32) * 32;
+  g.py = g.n1 + 2 * R;
+  g.plane = (int64_t)g.px * g.py;
+  g.total = g.plane * (g.n0 + 2 * g.R0);
+
+  // coefficients (axis mapping: user axis d -> internal axis d + 3 - ndim)
+  double w[kMaxR + 1];
+  lib_weights(space_order, w);
+  const double scale = eq == FD_DIFFUSION ? o.nu * dt : 1.0;
+  double wc = 0.0;
+  std::memset(&c->coef, 0, sizeof c->coef);
+  for (int d = 0; d < ndim; ++d) {
+    const int ax = d + 3 - ndim;
+    const double s = scale / (spacing[d] * spacing[d]);
+    for (int k = 1; k <= R; ++k) c->coef.w[ax][k] = (float)(w[k] * s);
+    wc += w[0] * s;
+  }
+  c->coef.wc = (float)wc;
+  select_kernel(c);
+
+  auto bail = [&](fd_status st) {
+    g_create_error = c->err;
+    fd_destroy(c);
+    return st;
+  };
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) {
+    fail(c, FD_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    return bail(FD_ECUDA);
+  }
+  if (o.cuda_stream) {
+    c->stream = (cudaStream_t)o.cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      fail(c, FD_ECUDA, "stream creation: %s", cudaGetErrorString(e));
+      return bail(FD_ECUDA);
+    }
+    c->own_stream = true;
+  }
+  fd_status st = FD_OK;
+  for (int b = 0; b < 2 && !st; ++b) st = dalloc(c, &c->u[b], (size_t)g.total);
+  if (!st && eq == FD_ACOUSTIC) st = dalloc(c, &c->A, (size_t)g.total);
+  if (!st && eq == FD_ACOUSTIC) st = dalloc(c, &c->C, (size_t)g.total);
+  if (!st && eq == FD_ACOUSTIC) st = dalloc(c, &c->m_dense, (size_t)npts);
+  if (!st && !o.device_ptrs) st = dalloc(c, &c->stage, (size_t)npts);
+  if (!st) st = dalloc(c, &c->d_step, 1);
+  if (!st) st = dalloc(c, &c->d_stats, 4);
+  if (!st) st = dalloc(c, &c->d_err, 4);
+  if (st) return bail(st);
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+    e = cudaMemsetAsync(c->u[b], 0, g.total * sizeof(float), c->stream);
+  if (eq == FD_ACOUSTIC) {
+    if (!e) e = cudaMemsetAsync(c->A, 0, g.total * sizeof(float), c->stream);
+    if (!e) e = cudaMemsetAsync(c->C, 0, g.total * sizeof(float), c->stream);
+  }
+  if (!e) e = cudaMemsetAsync(c->d_err, 0, 4 * sizeof(int), c->stream);
+  if (!e) e = cudaMemsetAsync(c->d_step, 0, sizeof(int64_t), c->stream);
+  if (e) {
+    fail(c, FD_ECUDA, "initialisation: %s", cudaGetErrorString(e));
+    return bail(FD_ECUDA);
+  }
+  // pipelined 3-D kernel where it applies
+  c->use_tma = false;
+  if (ndim == 3 && o.kernel != FD_KERNEL_PLAIN) {
+    const char *why = nullptr;
+    e = plan_tma(c->tma, c->g, eq == FD_ACOUSTIC ? kAcoustic : kDiffusion, c->u, c->A, c->C, &why);
+    if (e == cudaSuccess) {
+      c->use_tma = true;
+      c->kernel_name = c->tma.name;
+    } else {
+      cudaGetLastError();
+      if (o.kernel == FD_KERNEL_TMA) {
+        fail(c, FD_EUNSUPPORTED, "TMA kernel unavailable: %s", why ? why : cudaGetErrorString(e));
+        return bail(FD_EUNSUPPORTED);
+      }
+    }
+  } else if (o.kernel == FD_KERNEL_TMA) {
+    fail(c, FD_EUNSUPPORTED, "the TMA kernel is 3-D only");
+    return bail(FD_EUNSUPPORTED);
+  }
+  *out = c;
+  return FD_OK;
+}
+
+fd_status fd_set_model(fd_ctx *c, const float *m, const float *damp) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  if (c->eq != FD_ACOUSTIC) return fail(c, FD_EUNSUPPORTED, "fd_set_model is for FD_ACOUSTIC");
+  if (!m) return fail(c, FD_EINVAL, "m is NULL");
+  const size_t n = (size_t)c->g.n0 * c->g.n1 * c->g.n2;
+  float *damp_dev = nullptr;
+  st = to_device(c, c->m_dense, m, n);
+  if (st) return st;
+  if (damp) {
+    if (c->opt.device_ptrs) {
+      damp_dev = const_cast<float *>(damp);
+    } else {
+      CU(cudaMemcpyAsync(c->stage, damp, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+      damp_dev = c->stage;
+    }
+  }
+  unsigned init[2] = {0x7f800000u, 0u};
+  CU(cudaMemcpyAsync(c->d_stats, init, sizeof init, cudaMemcpyHostToDevice, c->stream));
+  k_coefficients<<<blocks_for(n, 256), 256, 0, c->stream>>>(c->m_dense, damp_dev, c->A, c->C,
+                                                            c->g, c->dt, c->d_stats);
+  CHECK_LAUNCH();
+  unsigned stats[2];
+  CU(cudaMemcpyAsync(stats, c->d_stats, sizeof stats, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  c->model_set = false;
+  if (stats[1]) return fail(c, FD_EINVAL, "m must be positive and finite, damp non-negative and finite");
+  float mmin;
+  std::memcpy(&mmin, &stats[0], sizeof mmin);
+  double lam = 0.0;
+  const double S = lib_symbol(c->so);
+  for (int d = 0; d < c->ndim; ++d) lam += S / (c->h[d] * c->h[d]);
+  const double dtmax = 2.0 * std::sqrt((double)mmin / lam);
+  if (c->dt > dtmax * (1.0 + 1e-12))
+    return fail(c, FD_EINVAL, "dt = %g exceeds the leapfrog limit %g for min(m) = %g", c->dt,
+                dtmax, (double)mmin);
+  c->model_set = true;
+  c->src_dirty = c->nsrc > 0;
+  return FD_OK;
+}
+
+fd_status fd_set_field(fd_ctx *c, const float *u_cur, const float *u_prev) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  if (!u_cur) return fail(c, FD_EINVAL, "u_cur is NULL");
+  if (c->eq == FD_DIFFUSION) {
+    st = load_field(c, c->u[c->cur], u_cur);
+    if (!st) st = load_field(c, c->u[c->cur ^ 1], u_cur);  // boundary values in both levels
+    return st;
+  }
+  st = load_field(c, c->u[c->cur], u_cur);
+  if (!st) st = load_field(c, c->u[c->cur ^ 1], u_prev ? u_prev : u_cur);
+  return st;
+}
+
+fd_status fd_set_sources(fd_ctx *c, int nsrc, const float *coords, int nt, const float *wavelets) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  if (c->eq != FD_ACOUSTIC) return fail(c, FD_EUNSUPPORTED, "sources need FD_ACOUSTIC");
+  if (nsrc < 0 || nsrc > (1 << 22)) return fail(c, FD_EINVAL, "nsrc out of range");
+  if (nsrc > 0 && (!coords || !wavelets || nt < 1)) return fail(c, FD_EINVAL, "coords/wavelets missing");
+  std::vector<float> pts;
+  st = coords_to_host(c, coords, (size_t)nsrc * c->ndim, pts);
+  if (st) return st;
+  const int n = nsrc * c->nc;
+  std::vector<int64_t> off(n), dense(n);
+  std::vector<double> w(n);
+  for (int j = 0; j < nsrc; ++j)
+    if (!corners(c, &pts[(size_t)j * c->ndim], &off[(size_t)j * c->nc], &dense[(size_t)j * c->nc],
+                 &w[(size_t)j * c->nc]))
+      return fail(c, FD_EINVAL, "source %d lies outside the grid", j);
+  CU(cudaStreamSynchronize(c->stream));
+  dfree(c->src_off); dfree(c->src_dense); dfree(c->src_w); dfree(c->src_scale); dfree(c->wav);
+  drop_graphs(c);
+  c->nsrc = 0;
+  c->nt_wav = 0;
+  if (nsrc == 0) return FD_OK;
+  if ((st = dalloc(c, &c->src_off, n)) || (st = dalloc(c, &c->src_dense, n)) ||
+      (st = dalloc(c, &c->src_w, n)) || (st = dalloc(c, &c->src_scale, n)) ||
+      (st = dalloc(c, &c->wav, (size_t)nt * nsrc)))
+    return st;
+  CU(cudaMemcpyAsync(c->src_off, off.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->src_dense, dense.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->src_w, w.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  st = to_device(c, c->wav, wavelets, (size_t)nt * nsrc);
+  if (st) return st;
+  CU(cudaStreamSynchronize(c->stream));  // the host vectors go out of scope
+  c->nsrc = nsrc;
+  c->nt_wav = nt;
+  c->src_dirty = true;
+  return FD_OK;
+}
+
+fd_status fd_set_receivers(fd_ctx *c, int nrec, const float *coords) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  if (c->eq != FD_ACOUSTIC) return fail(c, FD_EUNSUPPORTED, "receivers need FD_ACOUSTIC");
+  if (nrec < 0 || nrec > (1 << 22)) return fail(c, FD_EINVAL, "nrec out of range");
+  if (nrec > 0 && !coords) return fail(c, FD_EINVAL, "coords missing");
+  std::vector<float> pts;
+  st = coords_to_host(c, coords, (size_t)nrec * c->ndim, pts);
+  if (st) return st;
+  const int n = nrec * c->nc;
+  std::vector<int64_t> off(n), dense(n);
+  std::vector<double> w(n);
+  std::vector<float> wf(n);
+  for (int k = 0; k < nrec; ++k)
+    if (!corners(c, &pts[(size_t)k * c->ndim], &off[(size_t)k * c->nc], &dense[(size_t)k * c->nc],
+                 &w[(size_t)k * c->nc]))
+      return fail(c, FD_EINVAL, "receiver %d lies outside the grid", k);
+  for (int i = 0; i < n; ++i) wf[i] = (float)w[i];
+  CU(cudaStreamSynchronize(c->stream));
+  dfree(c->rec_off); dfree(c->rec_w); dfree(c->rec);
+  drop_graphs(c);
+  c->nrec = 0;
+  c->rec_cap = 0;
+  c->rec_rows = 0;
+  if (nrec == 0) return FD_OK;
+  if ((st = dalloc(c, &c->rec_off, n)) || (st = dalloc(c, &c->rec_w, n))) return st;
+  CU(cudaMemcpyAsync(c->rec_off, off.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->rec_w, wf.data(), n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  c->nrec = nrec;
+  if (c->step > 0) {  // rows before the current step stay zero
+    st = ensure_rec_capacity(c, c->step + 1);
+    if (st) return st;
+    c->rec_rows = c->step + 1;
+  }
+  return FD_OK;
+}
+
+fd_status fd_run(fd_ctx *c, int nt) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  if (nt < 0) return fail(c, FD_EINVAL, "nt must be >= 0");
+  if (c->eq == FD_ACOUSTIC && !c->model_set)
+    return fail(c, FD_ESTATE, "fd_set_model has not succeeded");
+  if (c->nsrc > 0 && c->step + nt > c->nt_wav)
+    return fail(c, FD_EINVAL, "step %lld exceeds the wavelet length %d",
+                (long long)(c->step + nt), c->nt_wav);
+  if (nt == 0) return FD_OK;
+  if (c->nrec > 0) {
+    st = ensure_rec_capacity(c, c->step + nt + 1);
+    if (st) return st;
+  }
+  st = prepare_sources(c);
+  if (st) return st;
+  k_set_step<<<1, 1, 0, c->stream>>>(c->d_step, c->step);
+  CHECK_LAUNCH();
+  if (c->nrec > 0 && c->rec_rows == 0 && c->step == 0) {
+    st = launch_interp_row0(c);
+    if (st) return st;
+  }
+  for (int done = 0; done < nt;) {
+    const int len = std::min(kGraphChunk, nt - done);
+    if (c->opt.use_graphs && !c->opt.profile) {
+      cudaGraphExec_t exec;
+      st = get_graph(c, c->cur, len, &exec);
+      if (st) return st;
+      CU(cudaGraphLaunch(exec, c->stream));
+    } else {
+      st = enqueue_chunk(c, c->cur, len, c->opt.profile != 0);
+      if (st) return st;
+    }
+    c->cur ^= (len & 1);
+    done += len;
+  }
+  c->step += nt;
+  if (c->nrec > 0) c->rec_rows = c->step + 1;
+  return FD_OK;
+}
+
+fd_status fd_read(fd_ctx *c, float *u, float *rec) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  if (u) {
+    st = store_field(c, c->u[c->cur], u);
+    if (st) return st;
+  }
+  if (rec && c->nrec > 0) {
+    const int64_t rows = c->step + 1;
+    if (c->rec_rows < rows) {
+      // no step has been run since the receivers were set: record row 0 now
+      st = ensure_rec_capacity(c, rows);
+      if (st) return st;
+      k_set_step<<<1, 1, 0, c->stream>>>(c->d_step, 0);
+      CHECK_LAUNCH();
+      st = launch_interp_row0(c);
+      if (st) return st;
+      c->rec_rows = 1;
+    }
+    CU(cudaMemcpyAsync(rec, c->rec, (size_t)rows * c->nrec * sizeof(float),
+                       c->opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       c->stream));
+  }
+  int errs[4];
+  CU(cudaMemcpyAsync(errs, c->d_err, sizeof errs, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (errs[0])
+    return fail(c, FD_ETIMEOUT, "a stencil kernel gave up waiting (code %d, block %d)", errs[0],
+                errs[1]);
+  return FD_OK;
+}
+
+fd_status fd_read_prev(fd_ctx *c, float *u_prev) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  if (!u_prev) return fail(c, FD_EINVAL, "u_prev is NULL");
+  st = store_field(c, c->u[c->cur ^ 1], u_prev);
+  if (st) return st;
+  CU(cudaStreamSynchronize(c->stream));
+  return FD_OK;
+}
+
+fd_status fd_set_step(fd_ctx *c, int64_t n) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  if (n < 0) return fail(c, FD_EINVAL, "step must be >= 0");
+  c->step = n;
+  if (c->nrec > 0) {
+    st = ensure_rec_capacity(c, n + 1);
+    if (st) return st;
+    c->rec_rows = n + 1;  // rows before n are left at zero
+  }
+  return FD_OK;
+}
+
+int64_t fd_steps_done(const fd_ctx *c) { return c ? c->step : -1; }
+
+fd_status fd_profile(fd_ctx *c, int64_t *launches, double *stencil_ms) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  CU(cudaStreamSynchronize(c->stream));
+  double total = 0.0;
+  for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]));
+    total += ms;
+  }
+  if (launches) *launches = (int64_t)(c->ev_used / 2);
+  if (stencil_ms) *stencil_ms = total;
+  c->ev_used = 0;
+  return FD_OK;
+}
+
+const char *fd_kernel_name(const fd_ctx *c) { return c ? c->kernel_name : "none"; }
+
+void fd_destroy(fd_ctx *c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
+  for (auto e : c->ev) cudaEventDestroy(e);
+  destroy_tma(c->tma);
+  dfree(c->u[0]); dfree(c->u[1]); dfree(c->A); dfree(c->C); dfree(c->m_dense); dfree(c->stage);
+  dfree(c->d_step); dfree(c->d_stats); dfree(c->d_err);
+  dfree(c->wav); dfree(c->src_scale); dfree(c->src_off); dfree(c->src_dense); dfree(c->src_w);
+  dfree(c->rec_off); dfree(c->rec_w); dfree(c->rec);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+const char *fd_last_error(const fd_ctx *c) {
+  if (!c) return g_create_error.c_str();
+  return c->err.c_str();
+}
+
+}  // extern "C"

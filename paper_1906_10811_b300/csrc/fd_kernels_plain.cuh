@@ -1,0 +1,179 @@
+// fd_kernels_plain.cuh -- plain stencil kernels, setup kernels, sparse kernels.
+//
+// The plain stencil kernel computes one grid point per thread and reads its
+// 2·D·R neighbours straight from global memory (L1/L2 serve the re-reads).
+// It is the simple design the pipelined kernel is measured against, and the
+// path for 2-D grids.
+#pragma once
+
+#include "fd_common.cuh"
+
+namespace fdk {
+
+// ---------------------------------------------------------------------------
+// One time step, plain.  Block (32, 8): x along lanes, y along warps; grid.z = z.
+//   diffusion: un = u + (ν dt L) u on interior nodes (coefficients carry ν dt)
+//   acoustic : un = A·(L u) + (1 + C)·u − C·un   (un holds u^{n-1} on entry)
+// with A = dt²/(m+σ), C = (m−σ)/(m+σ): the leapfrog update solved for u^{n+1}.
+// ---------------------------------------------------------------------------
+template <int R, int EQ, bool THREE_D>
+__global__ void __launch_bounds__(256)
+k_stencil_plain(const float *__restrict__ u, float *un, const float *__restrict__ A,
+                const float *__restrict__ C, Geom g, Coef c) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * 8 + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= g.n2 || y >= g.n1) return;
+  const int64_t p = gidx(g, z, y, x);
+  const float uc = u[p];
+  float lap = c.wc * uc;
+#pragma unroll
+  for (int k = 1; k <= R; ++k) {
+    lap = fmaf(c.w[2][k], u[p + k] + u[p - k], lap);
+    lap = fmaf(c.w[1][k], u[p + (int64_t)k * g.px] + u[p - (int64_t)k * g.px], lap);
+    if (THREE_D)
+      lap = fmaf(c.w[0][k], u[p + k * g.plane] + u[p - k * g.plane], lap);
+  }
+  if (EQ == kAcoustic) {
+    const float a = A[p], cc = C[p];
+    const float prev = un[p];
+    un[p] = fmaf(a, lap, fmaf(1.f + cc, uc, -cc * prev));
+  } else {
+    const bool interior = x > 0 && x < g.n2 - 1 && y > 0 && y < g.n1 - 1 &&
+                          (!THREE_D || (z > 0 && z < g.n0 - 1));
+    if (interior) un[p] = uc + lap;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Layout moves between dense interior arrays and the padded layout.
+// ---------------------------------------------------------------------------
+__global__ void k_scatter(const float *__restrict__ dense, float *__restrict__ padded, Geom g) {
+  const int64_t n = (int64_t)g.n0 * g.n1 * g.n2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.n2);
+    const int64_t r = i / g.n2;
+    const int y = (int)(r % g.n1);
+    const int z = (int)(r / g.n1);
+    padded[gidx(g, z, y, x)] = dense[i];
+  }
+}
+
+__global__ void k_gather(const float *__restrict__ padded, float *__restrict__ dense, Geom g) {
+  const int64_t n = (int64_t)g.n0 * g.n1 * g.n2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.n2);
+    const int64_t r = i / g.n2;
+    const int y = (int)(r % g.n1);
+    const int z = (int)(r / g.n1);
+    dense[i] = padded[gidx(g, z, y, x)];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Acoustic coefficients, once per model (double arithmetic, rounded once):
+//   σ = damp·dt/2,  A = dt²/(m+σ),  C = (m−σ)/(m+σ).
+// stats[0]: min over m of its bit pattern (m > 0 → ordered like the value),
+// stats[1]: set when some m ≤ 0 or non-finite, or some damp < 0 or non-finite.
+// ---------------------------------------------------------------------------
+__global__ void k_coefficients(const float *__restrict__ m, const float *__restrict__ damp,
+                               float *__restrict__ A, float *__restrict__ C, Geom g, double dt,
+                               unsigned *stats) {
+  const int64_t n = (int64_t)g.n0 * g.n1 * g.n2;
+  unsigned local_min = 0x7f800000u, bad = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float mf = m[i];
+    const float df = damp ? damp[i] : 0.f;
+    if (!(mf > 0.f) || !isfinite(mf) || !(df >= 0.f) || !isfinite(df)) bad = 1;
+    local_min = min(local_min, __float_as_uint(mf));
+    const double md = mf, sig = (double)df * dt * 0.5;
+    const int x = (int)(i % g.n2);
+    const int64_t r = i / g.n2;
+    const int y = (int)(r % g.n1);
+    const int z = (int)(r / g.n1);
+    const int64_t p = gidx(g, z, y, x);
+    A[p] = (float)(dt * dt / (md + sig));
+    C[p] = (float)((md - sig) / (md + sig));
+  }
+  // warp-reduce before the atomics
+  for (int o = 16; o > 0; o >>= 1) {
+    local_min = min(local_min, __shfl_xor_sync(0xffffffffu, local_min, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&stats[0], local_min);
+    if (bad) atomicOr(&stats[1], 1u);
+  }
+}
+
+// Source scales w·dt²/m(node) in double, rounded once.
+__global__ void k_source_scales(const int64_t *__restrict__ dense_node, const double *__restrict__ w,
+                                const float *__restrict__ m, float *__restrict__ scale, int n,
+                                double dt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) scale[i] = (float)(w[i] * dt * dt / (double)m[dense_node[i]]);
+}
+
+// ---------------------------------------------------------------------------
+// Step counter: kernels of step j in a chunk read n = *step + j.
+// ---------------------------------------------------------------------------
+__global__ void k_set_step(int64_t *step, int64_t n) { *step = n; }
+__global__ void k_advance_step(int64_t *step, int by) { *step += by; }
+
+// ---------------------------------------------------------------------------
+// Sparse operators.  NC = 2^D corners per point.
+// Injection: un[node] += scale · s_j(t_n) (atomics: sources may share nodes).
+// Interpolation: rec[n+1][k] = Σ_c w_kc · un[node_kc]; NC lanes per receiver,
+// reduced with warp shuffles.  Every lane of a warp must take part.
+// ---------------------------------------------------------------------------
+template <int NC>
+__device__ __forceinline__ void interp_group_store(const float *un, const int64_t *__restrict__ roff,
+                                                   const float *__restrict__ rw, float *rec,
+                                                   int64_t row, int nrec, int k, int c) {
+  float v = 0.f;
+  if (k < nrec) v = rw[k * NC + c] * un[roff[k * NC + c]];
+#pragma unroll
+  for (int o = NC / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (c == 0 && k < nrec) rec[row * nrec + k] = v;
+}
+
+// Single block: injection, block barrier, interpolation (small source/receiver sets).
+template <int NC>
+__global__ void __launch_bounds__(512)
+k_sparse_fused(float *un, const int64_t *__restrict__ step, int j, int nsrc,
+               const int64_t *__restrict__ soff, const float *__restrict__ sscale,
+               const float *__restrict__ wav, int nrec, const int64_t *__restrict__ roff,
+               const float *__restrict__ rw, float *rec) {
+  const int64_t n = *step + j;
+  for (int i = threadIdx.x; i < nsrc * NC; i += blockDim.x)
+    atomicAdd(un + soff[i], sscale[i] * wav[n * nsrc + i / NC]);
+  __syncthreads();
+  const int groups = blockDim.x / NC;
+  for (int base = 0; base < nrec; base += groups)
+    interp_group_store<NC>(un, roff, rw, rec, n + 1, nrec, base + threadIdx.x / NC,
+                           threadIdx.x % NC);
+}
+
+template <int NC>
+__global__ void k_inject(float *un, const int64_t *__restrict__ step, int j, int nsrc,
+                         const int64_t *__restrict__ soff, const float *__restrict__ sscale,
+                         const float *__restrict__ wav) {
+  const int64_t n = *step + j;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nsrc * NC) atomicAdd(un + soff[i], sscale[i] * wav[n * nsrc + i / NC]);
+}
+
+// rec row = *step + j + 1 (j = -1 with *step = 0 records row 0).
+template <int NC>
+__global__ void k_interp(const float *un, const int64_t *__restrict__ step, int j, int nrec,
+                         const int64_t *__restrict__ roff, const float *__restrict__ rw,
+                         float *rec) {
+  const int64_t n = *step + j;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  interp_group_store<NC>(un, roff, rw, rec, n + 1, nrec, t / NC, t % NC);
+}
+
+}  // namespace fdk

@@ -1,0 +1,108 @@
+"""``Solver``: a Python object over one fd_ctx (marshalling only; all work runs in
+the CUDA library).  Host mode takes and returns numpy arrays; device mode
+(``device=True``) takes and returns torch CUDA tensors on a torch stream."""
+
+import numpy as np
+
+from . import binding as B
+
+_EQ = {"diffusion": B.FD_DIFFUSION, "acoustic": B.FD_ACOUSTIC}
+_KERNEL = {"auto": B.FD_KERNEL_AUTO, "plain": B.FD_KERNEL_PLAIN, "tma": B.FD_KERNEL_TMA}
+
+
+class Solver:
+    """One simulation: ``Solver(shape, spacing, space_order, dt, equation)``.
+
+    Mirrors a Devito operator's problem statement (thesis §2.1.1: a Grid with
+    shape and spacing, a TimeFunction of a space order, initial data, sparse
+    sources/receivers, ``op(time=nt, dt=dt)``).
+    """
+
+    def __init__(self, shape, spacing, space_order, dt, equation="acoustic", nu=0.5,
+                 device=False, stream=None, graphs=True, profile=False, kernel="auto"):
+        self.ctx = None
+        self.shape = tuple(int(s) for s in shape)
+        self.ndim = len(self.shape)
+        self.device = bool(device)
+        cuda_stream = None
+        if self.device:
+            import torch
+            self._torch = torch
+            s = stream if stream is not None else torch.cuda.current_stream()
+            cuda_stream = s.cuda_stream
+            self.stream = s
+        opt = B.options(nu=nu, cuda_stream=cuda_stream, device_ptrs=self.device, use_graphs=graphs,
+                        profile=profile, kernel=_KERNEL[kernel])
+        self.ctx = B.fd_create(self.ndim, self.shape, spacing, space_order, dt, _EQ[equation], opt)
+        self.nrec = 0
+
+    # -- lifecycle ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "ctx", None):
+            B.fd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- inputs ------------------------------------------------------------
+    def set_model(self, m, damp=None):
+        B.fd_set_model(self.ctx, m, damp)
+
+    def set_field(self, u, u_prev=None):
+        B.fd_set_field(self.ctx, u, u_prev)
+
+    def set_sources(self, coords, wavelets):
+        n = 0 if coords is None else len(coords)
+        nt = 0 if wavelets is None else int(wavelets.shape[0])
+        B.fd_set_sources(self.ctx, n, coords, nt, wavelets)
+
+    def set_receivers(self, coords):
+        self.nrec = 0 if coords is None else len(coords)
+        B.fd_set_receivers(self.ctx, self.nrec, coords)
+
+    def set_step(self, n):
+        B.fd_set_step(self.ctx, n)
+
+    # -- run / outputs -----------------------------------------------------
+    def run(self, nt):
+        B.fd_run(self.ctx, nt)
+        return self
+
+    @property
+    def steps(self):
+        return B.fd_steps_done(self.ctx)
+
+    @property
+    def kernel_name(self):
+        return B.fd_kernel_name(self.ctx)
+
+    def _empty(self, shape):
+        if self.device:
+            return self._torch.empty(shape, dtype=self._torch.float32, device="cuda")
+        return np.empty(shape, dtype=np.float32)
+
+    def read(self, field=True, traces=True):
+        """(u^n, traces [n+1][nrec]); either is None when not requested or absent."""
+        u = self._empty(self.shape) if field else None
+        rec = self._empty((self.steps + 1, self.nrec)) if traces and self.nrec else None
+        B.fd_read(self.ctx, u, rec)
+        return u, rec
+
+    def read_prev(self):
+        u = self._empty(self.shape)
+        B.fd_read_prev(self.ctx, u)
+        return u
+
+    def profile(self):
+        """(stencil launches, summed stencil ms) since the previous call."""
+        return B.fd_profile(self.ctx)
