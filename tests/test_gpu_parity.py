@@ -1,0 +1,251 @@
+"""GPU parity through the C ABI against the FP64 oracle, on sizes the oracle
+finishes in seconds that still span several tiles and ragged edges.
+
+Tolerances (spec accuracy targets, FP32 GPU vs FP64 oracle, relative
+L2 over all values): diffusion 1e-5, acoustic wavefield and traces 1e-4.
+Where two GPU runs must agree exactly (graphs vs eager launches, chunked runs,
+host vs device pointers, resume from a checkpoint), the comparison is bitwise:
+with one source no two atomic additions meet, so the arithmetic is identical.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import fdsynth
+from helpers import gpu_acoustic, oracle_acoustic, rel_l2, small_problem
+from oracle import core as oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL_DIFF = 1e-5
+TOL_WAVE = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1906_10811_b300 import build
+    build.build()
+
+
+# ----------------------------------------------------------------------------
+# Diffusion (thesis §5.1.2)
+# ----------------------------------------------------------------------------
+def test_diffusion_benchmark_problem():
+    """128² nodes, ν = 0.5, so 2, ν dt/h² = 0.2, 100 steps."""
+    from paper_1906_10811_b300 import Solver
+    p = fdsynth.diffusion_problem(128)
+    with Solver((128, 128), p["spacing"], 2, p["dt"], "diffusion", nu=0.5) as s:
+        s.set_field(p["u0"])
+        s.run(100)
+        u, _ = s.read()
+    ref = oracle.diffusion(p["u0"], p["spacing"], 2, 0.5, p["dt"], 100)
+    assert rel_l2(u, ref) <= TOL_DIFF
+    h = p["spacing"][0]
+    g = 1 - 4 * 0.2 * 2 * math.sin(math.pi * h / 2) ** 2
+    assert rel_l2(u, g ** 100 * p["u0"].astype(np.float64)) <= TOL_DIFF
+    assert np.all(u[0] == 0) and np.all(u[:, -1] == 0)
+
+
+@pytest.mark.parametrize("so", (2, 4, 8, 12, 16))
+@pytest.mark.parametrize("shape", [(37, 45), (3, 70), (19, 23, 41), (3, 5, 4), (9, 34, 33)])
+def test_diffusion_parity(so, shape):
+    from paper_1906_10811_b300 import Solver, fd_stability_symbol
+    nd = len(shape)
+    rng = np.random.default_rng(so + 10 * nd)
+    u0 = fdsynth.random_field(shape, seed=so)
+    h = tuple(rng.uniform(0.5, 1.5, nd))
+    lam = sum(fd_stability_symbol(so) / hd ** 2 for hd in h)
+    nu = 0.7
+    dt = fdsynth.f32(0.9 * 2 / (nu * lam))
+    with Solver(shape, h, so, dt, "diffusion", nu=nu) as s:
+        s.set_field(u0)
+        s.run(25)
+        u, _ = s.read()
+    ref = oracle.diffusion(u0, h, so, nu, dt, 25)
+    assert rel_l2(u, ref) <= TOL_DIFF
+
+
+def test_diffusion_boundary_held_and_plain_vs_auto():
+    from paper_1906_10811_b300 import Solver
+    shape = (21, 18, 40)
+    u0 = fdsynth.random_field(shape, seed=3)
+    outs = []
+    for kernel in ("plain", "auto"):
+        with Solver(shape, (1.0,) * 3, 8, 0.05, "diffusion", nu=0.5, kernel=kernel) as s:
+            s.set_field(u0)
+            s.run(13)
+            outs.append(s.read()[0])
+    ref = oracle.diffusion(u0, (1.0,) * 3, 8, 0.5, 0.05, 13)
+    for u in outs:
+        assert rel_l2(u, ref) <= TOL_DIFF
+        for ax in range(3):
+            for i in (0, shape[ax] - 1):
+                assert np.array_equal(np.take(u, i, axis=ax), np.take(u0, i, axis=ax))
+
+
+# ----------------------------------------------------------------------------
+# Acoustic (the seismic operator of thesis §6.2.1)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("so", (2, 4, 6, 8, 10, 12, 14, 16))
+@pytest.mark.parametrize("shape", [(23, 29, 37), (40, 33, 70)])
+def test_acoustic_parity_3d(so, shape):
+    p = small_problem(shape, so, nt=90)
+    g = gpu_acoustic(p, 90)
+    o = oracle_acoustic(p, 90)
+    assert rel_l2(g["u"], o["u"]) <= TOL_WAVE
+    assert rel_l2(g["u_prev"], o["u_prev"]) <= TOL_WAVE
+    assert rel_l2(g["rec"], o["rec"]) <= TOL_WAVE
+    assert np.abs(o["rec"]).max() > 0
+
+
+@pytest.mark.parametrize("so", (2, 8, 16))
+@pytest.mark.parametrize("shape", [(61, 53), (17, 130)])
+def test_acoustic_parity_2d(so, shape):
+    p = small_problem(shape, so, nt=150)
+    g = gpu_acoustic(p, 150)
+    o = oracle_acoustic(p, 150)
+    assert rel_l2(g["u"], o["u"]) <= TOL_WAVE
+    assert rel_l2(g["rec"], o["rec"]) <= TOL_WAVE
+
+
+@pytest.mark.parametrize("kernel", ("plain", "auto"))
+def test_acoustic_kernels_many_sources_and_receivers(kernel):
+    """Random sources (two sharing a node) and receivers, including points on
+    the grid boundary; enough of them to take the multi-block sparse path."""
+    shape, so, nt = (26, 31, 35), 8, 60
+    p = small_problem(shape, so, nt)
+    pts = fdsynth.random_points(shape, p["spacing"], 300, seed=5)
+    pts[1] = pts[0]
+    ext = np.array([(n - 1) * h for n, h in zip(shape, p["spacing"])], dtype=np.float32)
+    pts[2] = ext
+    pts[3] = 0
+    p["src_coords"] = pts
+    p["wavelet"] = np.repeat(p["wavelet"], 300, axis=1) * np.linspace(0.5, 1.5, 300, dtype=np.float32)
+    p["rec_coords"] = np.vstack([fdsynth.random_points(shape, p["spacing"], 400, seed=6), ext[None], np.zeros((1, 3), np.float32)])
+    g = gpu_acoustic(p, nt, kernel=kernel)
+    o = oracle_acoustic(p, nt)
+    assert rel_l2(g["u"], o["u"]) <= TOL_WAVE
+    assert rel_l2(g["rec"], o["rec"]) <= TOL_WAVE
+
+
+def test_acoustic_without_damping_and_sources_matches_closed_form():
+    """Homogeneous m, so 2, sine mode with u^{-1} = cos θ u^0: u^n = cos(nθ) u^0."""
+    from paper_1906_10811_b300 import Solver
+    shape, h, m, dt, nt = (30, 34, 38), 10.0, 0.25, 2.0, 200
+    u0 = np.ones(())
+    lam = 0.0
+    for n, k in zip(shape, (1, 2, 3)):
+        i = np.arange(n)
+        u0 = np.multiply.outer(u0, np.sin(k * math.pi * (i + 1) / (n + 1)))
+        lam += -4.0 * math.sin(k * math.pi / (2 * (n + 1))) ** 2
+    cth = 1.0 + dt * dt * lam / (h * h) / (2 * m)
+    with Solver(shape, (h,) * 3, 2, dt, "acoustic") as s:
+        s.set_model(np.full(shape, m, np.float32))
+        s.set_field(u0.astype(np.float32), (cth * u0).astype(np.float32))
+        s.run(nt)
+        u, _ = s.read()
+    assert rel_l2(u, math.cos(nt * math.acos(cth)) * u0) <= TOL_WAVE
+
+
+def test_graphs_eager_profile_chunks_and_device_pointers_agree_bitwise():
+    p = small_problem((30, 27, 66), 8, nt=150)
+    ref = gpu_acoustic(p, 150)
+    variants = [
+        gpu_acoustic(p, 150, graphs=False),
+        gpu_acoustic(p, 150, profile=True),
+        gpu_acoustic(p, 150, chunks=[1, 63, 64, 7, 15]),
+        gpu_acoustic(p, 150, device=True),
+    ]
+    for v in variants:
+        assert np.array_equal(v["u"], ref["u"])
+        assert np.array_equal(v["rec"], ref["rec"])
+    launches, ms = variants[1]["profile"]
+    assert launches == 150 and ms > 0
+
+
+def test_checkpoint_resume_is_bitwise():
+    from paper_1906_10811_b300 import Solver
+    p = small_problem((25, 30, 41), 4, nt=100)
+    full = gpu_acoustic(p, 100)
+    first = gpu_acoustic(p, 40)
+    with Solver(p["shape"], p["spacing"], 4, p["dt"], "acoustic") as s:
+        s.set_model(p["m"], p["damp"])
+        s.set_field(first["u"], first["u_prev"])
+        s.set_step(40)
+        s.set_sources(p["src_coords"], p["wavelet"])
+        s.set_receivers(p["rec_coords"])
+        s.run(60)
+        u, rec = s.read()
+    assert np.array_equal(u, full["u"])
+    assert np.array_equal(rec[41:], full["rec"][41:])
+    assert np.all(rec[:40] == 0)
+
+
+def test_edge_cases():
+    from paper_1906_10811_b300 import Solver
+    # smallest acoustic grid, one source on a corner node, receivers on nodes
+    shape = (2, 2, 2)
+    m = np.full(shape, 0.2, np.float32)
+    wav = fdsynth.ricker(10, 1.0, 0.05).reshape(-1, 1)
+    src = np.array([[10.0, 0.0, 10.0]], np.float32)
+    rec = np.array([[0, 0, 0], [10, 10, 10], [5, 5, 5]], np.float32)
+    with Solver(shape, (10.0,) * 3, 16, 1.0, "acoustic") as s:
+        s.set_model(m)
+        s.set_sources(src, wav)
+        s.set_receivers(rec)
+        s.run(0)
+        u0, r0 = s.read()
+        assert np.all(u0 == 0) and r0.shape == (1, 3)
+        s.run(10)
+        u, r = s.read()
+    ou, _, orec = oracle.acoustic(m, 1.0, (10.0,) * 3, 16, 10, src_coords=src, wavelet=wav, rec_coords=rec)
+    assert rel_l2(u, ou) <= TOL_WAVE and rel_l2(r, orec) <= TOL_WAVE
+    # no receivers: read gives no traces; diffusion with one interior node
+    with Solver((3, 3), (1.0, 1.0), 2, 0.1, "diffusion") as s:
+        u0 = np.arange(9, dtype=np.float32).reshape(3, 3)
+        s.set_field(u0)
+        s.run(4)
+        u, r = s.read()
+        assert r is None
+    assert rel_l2(u, oracle.diffusion(u0, (1.0, 1.0), 2, 0.5, 0.1, 4)) <= TOL_DIFF
+
+
+def test_errors_are_reported():
+    from paper_1906_10811_b300 import FdError, Solver, binding
+    shape = (10, 11, 12)
+    m = np.full(shape, 0.1, np.float32)         # leapfrog limit for dt: 1.43
+    with Solver(shape, (10.0,) * 3, 8, 1.0, "acoustic") as s:
+        with pytest.raises(FdError) as e:
+            s.run(1)
+        assert e.value.status == binding.FD_ESTATE
+        with pytest.raises(FdError) as e:                # dt above the leapfrog limit
+            s.set_model(np.full(shape, 0.01, np.float32))
+        assert e.value.status == binding.FD_EINVAL
+        bad = m.copy()
+        bad[3, 4, 5] = 0
+        with pytest.raises(FdError) as e:
+            s.set_model(bad)
+        assert e.value.status == binding.FD_EINVAL
+        neg = np.zeros(shape, np.float32)
+        neg[0, 0, 0] = -1
+        with pytest.raises(FdError) as e:
+            s.set_model(m, neg)
+        assert e.value.status == binding.FD_EINVAL
+        s.set_model(m)
+        with pytest.raises(FdError) as e:                # outside the grid
+            s.set_sources(np.array([[0, 0, 111.0]], np.float32), np.zeros((5, 1), np.float32))
+        assert e.value.status == binding.FD_EINVAL
+        s.set_sources(np.array([[50, 50, 50.0]], np.float32), np.zeros((5, 1), np.float32))
+        with pytest.raises(FdError) as e:                # wavelet too short
+            s.run(6)
+        assert e.value.status == binding.FD_EINVAL
+        s.run(5)
+        assert s.steps == 5
+    with Solver((8, 8), (1.0, 1.0), 2, 0.1, "diffusion") as s:
+        with pytest.raises(FdError) as e:
+            s.set_sources(np.array([[1.0, 1.0]], np.float32), np.zeros((5, 1), np.float32))
+        assert e.value.status == binding.FD_EUNSUPPORTED
