@@ -1,0 +1,342 @@
+#!/usr/bin/env python
+"""Benchmark of the explicit FD sweep on B300 through the C ABI.
+
+Default workload (one GPU): a 3-D acoustic shot, 256³ FP32 grid (dx = 10 m,
+40-point damping layer inside it), space order 8, layered velocity 1.5-4.5 km/s
+with 5% smoothed noise, CFL dt, a 10 Hz Ricker source at the centre and a line
+of 256 receivers, 500 time steps.  One benchmark *step* is one whole shot:
+coefficient setup from m and damp, field reset, 500 time steps (stencil,
+injection, interpolation).  ``value`` is grid-point updates per second (GPts/s)
+with every input already resident in HBM; ``e2e`` is the same metric through
+the C ABI with pinned host buffers (host->device copies of the shot's inputs and
+the device->host read of its traces inside the timed region).
+
+``--workload roofline512 --so {4,8,12,16}`` runs the 512³ sweep (200 steps, one
+source, no receivers).  ``--impl reference`` times the FP64 CPU oracle on the
+same workload instead (a bounded sample of time steps per step).
+
+Multi-GPU (torchrun): shots are independent, so each rank runs its own shot on
+its own GPU with no collective in the data path (weak scaling); ranks meet only
+at the barriers around the timed region, and the slowest rank's time counts.
+"""
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import fdsynth  # noqa: E402
+
+BYTES_PER_POINT = {"acoustic": 20}   # read u^n, u^{n-1}, A, C; write u^{n+1} (FP32)
+FALLBACK_HBM_GBS = 6400.0
+
+WORKLOADS = {
+    "acoustic256": dict(n=256, so=8, nt=500, nrec=256, nbl=40),
+    "roofline512": dict(n=512, so=8, nt=200, nrec=0, nbl=40),
+}
+
+# DRAM bytes per stencil launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
+# keyed by (kernel name, workload, space order); see profiles/.  None until captured.
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="acoustic256", choices=sorted(WORKLOADS))
+    ap.add_argument("--so", type=int, default=None)
+    ap.add_argument("--nt", type=int, default=None)
+    ap.add_argument("--kernel", default="auto", choices=["auto", "plain", "tma"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def problem(args):
+    w = dict(WORKLOADS[args.workload])
+    if args.so:
+        w["so"] = args.so
+    if args.nt:
+        w["nt"] = args.nt
+    p = fdsynth.acoustic_problem(n=w["n"], ndim=3, so=w["so"], nbl=w["nbl"], nt=w["nt"],
+                                 nrec=w["nrec"], seed=0)
+    return w, p
+
+
+def config_of(args, w, kernel_name=None):
+    cfg = {"workload": f"acoustic3d_{w['n']}^3_so{w['so']}_nt{w['nt']}",
+           "grid": [w["n"]] * 3, "space_order": w["so"], "nt": w["nt"], "nrec": w["nrec"],
+           "nsrc": 1, "damping_layer": w["nbl"], "dx_m": 10.0,
+           "step": "one shot: coefficient setup + field reset + nt time steps",
+           "l2": "inputs larger than L2 (u^n, u^{n-1}, A, C = 4 x %.0f MB)" %
+                 ((w["n"] + 8) ** 2 * (w["n"] + 64) * 4 / 1e6)}
+    if kernel_name:
+        cfg["kernel"] = kernel_name
+    return cfg
+
+
+def load_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_threads():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def time_oracle(p, steps):
+    """Oracle GPts/s over `steps` time steps of the shot (source and receivers included)."""
+    from oracle import core as oracle
+    m = p["m"].astype(np.float64)
+    damp = p["damp"].astype(np.float64)
+    rec = p["rec_coords"] if len(p["rec_coords"]) else None
+    t0 = time.perf_counter()
+    oracle.acoustic(m, p["dt"], p["spacing"], p["so"], steps, damp=damp,
+                    src_coords=p["src_coords"], wavelet=p["wavelet"], rec_coords=rec)
+    dt = time.perf_counter() - t0
+    return m.size * steps / dt / 1e9, dt
+
+
+def cpu_baseline(p, budget_s):
+    _, t1 = time_oracle(p, 1)
+    k = int(max(1, min(p["nt"], round(budget_s / max(t1, 1e-3)))))
+    v, t = time_oracle(p, k)
+    return {"value": round(v, 4), "unit": "GPts/s", "cores": cpu_threads(), "kind": "oracle",
+            "sample": f"first {k} of {p['nt']} time steps of the same shot (FP64, "
+                      f"{t:.1f} s), OpenMP over grid rows"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    w, p = problem(args)
+    _, t1 = time_oracle(p, 1)
+    per_step = int(max(1, min(p["nt"], round(6.0 / max(t1, 1e-3)))))
+    for _ in range(args.warmup):
+        time_oracle(p, per_step)
+    vals, total = [], 0.0
+    for _ in range(args.steps):
+        v, t = time_oracle(p, per_step)
+        vals.append(v)
+        total += t
+    value = (p["m"].size * per_step * args.steps) / total / 1e9
+    line = {"impl": "reference", "metric": "GPts/s & % HBM roofline per stencil", "value": round(value, 4),
+            "unit": "GPts/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(args, w),
+            "cpu_baseline": {"value": round(value, 4), "unit": "GPts/s", "cores": cpu_threads(),
+                             "kind": "oracle",
+                             "sample": f"each step = first {per_step} of {p['nt']} time steps of the shot"},
+            "e2e": {"value": round(value, 4), "unit": "GPts/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1906_10811_b300 import Solver, build
+    build.build()
+
+    w, p = problem(args)
+    npts = int(np.prod(p["shape"]))
+    nt = p["nt"]
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    m_d, damp_d = dev(p["m"]), dev(p["damp"])
+    zeros_d = torch.zeros(p["shape"], dtype=torch.float32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---------------- device-resident timed region ----------------
+    s = Solver(p["shape"], p["spacing"], p["so"], p["dt"], "acoustic", device=True, profile=True,
+               kernel=args.kernel)
+    s.set_sources(dev(p["src_coords"]), dev(p["wavelet"]))
+    if w["nrec"]:
+        s.set_receivers(dev(p["rec_coords"]))
+
+    def shot():
+        s.set_model(m_d, damp_d)
+        s.set_field(zeros_d)
+        s.set_step(0)
+        s.run(nt)
+
+    for _ in range(args.warmup):
+        shot()
+    s.profile()                                            # reset the per-launch timers
+    launches0 = s.kernel_launches
+    gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    clocks = ClockSampler(gpu_id)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        shot()
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    launches = s.kernel_launches - launches0
+    n_st, st_ms = s.profile()
+    kernel_name = s.kernel_name
+    _, rec_dev = s.read(field=False)
+    s.close()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * npts * nt * args.steps / (ms / 1e3) / 1e9
+
+    peak, peak_kind = load_peak()
+    avg_launch_s = st_ms / max(n_st, 1) / 1e3
+    achieved = BYTES_PER_POINT["acoustic"] * npts / avg_launch_s / 1e9
+    traffic = NCU_TRAFFIC.get((kernel_name, args.workload, w["so"]))
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": kernel_name, "bytes_per_point": BYTES_PER_POINT["acoustic"],
+                "points_per_launch": npts, "avg_launch_us": round(avg_launch_s * 1e6, 2),
+                "launches_timed": n_st, "stencil_share_of_step": round(st_ms / ms, 4),
+                "peak_source": f"{peak_kind} HBM copy bandwidth (of {peak_kind})",
+                "gpts_per_s_kernel": round(npts / avg_launch_s / 1e9, 2)}
+
+    # ---------------- end to end through the C ABI with host buffers ----------------
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        m_h, damp_h, zero_h = pin(p["m"]), pin(p["damp"]), pin(np.zeros(p["shape"], np.float32))
+        src_h, wav_h, rc_h = pin(p["src_coords"]), pin(p["wavelet"]), pin(p["rec_coords"])
+        rec_out = torch.empty((nt + 1, max(w["nrec"], 1)), dtype=torch.float32).pin_memory().numpy()
+        h2d = m_h.nbytes + damp_h.nbytes + zero_h.nbytes + src_h.nbytes + wav_h.nbytes + rc_h.nbytes
+        d2h = (nt + 1) * w["nrec"] * 4
+        se = Solver(p["shape"], p["spacing"], p["so"], p["dt"], "acoustic", device=False,
+                    kernel=args.kernel)
+        from paper_1906_10811_b300 import binding as B
+
+        def shot_e2e():
+            se.set_model(m_h, damp_h)
+            se.set_sources(src_h, wav_h)
+            if w["nrec"]:
+                se.set_receivers(rc_h)
+            se.set_field(zero_h)
+            se.set_step(0)
+            se.run(nt)
+            B.fd_read(se.ctx, None, rec_out if w["nrec"] else None)
+
+        for _ in range(args.warmup):
+            shot_e2e()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            shot_e2e()
+        barrier()
+        te = time.perf_counter() - t0
+        se.close()
+        if world > 1:
+            t = torch.tensor([te], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": round(world * npts * nt * args.steps / te / 1e9, 3), "unit": "GPts/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(p, args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": "GPts/s & % HBM roofline per stencil", "value": round(value, 3),
+                "unit": "GPts/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_of(args, w, kernel_name), "roofline": roofline,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -142,7 +142,9 @@ fd_status fd_read(fd_ctx *ctx, float *u, float *rec);
 /* Previous level u^{n-1} (FD_ACOUSTIC), for checkpoint/resume; syncs. */
 fd_status fd_read_prev(fd_ctx *ctx, float *u_prev);
 
-/* Set the global step counter (resume from a checkpoint at step n ≥ 0). */
+/* Set the global step counter (resume from a checkpoint at step n ≥ 0).
+ * Trace rows 0..n keep their contents (zero in a context that has not run);
+ * n = 0 makes the next fd_run record row 0 afresh. */
 fd_status fd_set_step(fd_ctx *ctx, int64_t n);
 
 /* Steps advanced so far (the global step counter); -1 for NULL. */
@@ -156,6 +158,10 @@ fd_status fd_profile(fd_ctx *ctx, int64_t *launches, double *stencil_ms);
 
 /* Name of the stencil kernel variant fd_run launches (static string). */
 const char *fd_kernel_name(const fd_ctx *ctx);
+
+/* CUDA kernels this context has launched so far (kernel nodes of replayed
+ * graphs included); -1 for NULL. */
+int64_t fd_kernel_launches(const fd_ctx *ctx);
 
 /* Release everything.  NULL is a no-op. */
 void fd_destroy(fd_ctx *ctx);

@@ -57,6 +57,7 @@ SIGNATURES = {
     "fd_steps_done": (_i64, [_vp]),
     "fd_profile": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double)]),
     "fd_kernel_name": (ctypes.c_char_p, [_vp]),
+    "fd_kernel_launches": (_i64, [_vp]),
     "fd_destroy": (None, [_vp]),
     "fd_last_error": (ctypes.c_char_p, [_vp]),
     "fd_weights": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
@@ -202,6 +203,10 @@ def fd_profile(ctx):
 
 def fd_kernel_name(ctx):
     return load().fd_kernel_name(ctx).decode()
+
+
+def fd_kernel_launches(ctx):
+    return int(load().fd_kernel_launches(ctx))
 
 
 def fd_destroy(ctx):

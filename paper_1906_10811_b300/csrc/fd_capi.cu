@@ -62,6 +62,7 @@ double lib_symbol(int so) {
 struct GraphEntry {
   int parity;
   int len;
+  int64_t kernels;  // kernel nodes in the graph
   cudaGraphExec_t exec;
 };
 
@@ -117,6 +118,7 @@ struct fd_ctx {
   // profiling
   std::vector<cudaEvent_t> ev;
   size_t ev_used = 0;
+  int64_t launches = 0;  // kernels this context has launched (graph nodes included)
 };
 
 namespace {
@@ -144,7 +146,11 @@ fd_status fail(fd_ctx *c, fd_status st, const char *fmt, ...) {
                   "%s failed: %s", #call, cudaGetErrorString(e_));                     \
   } while (0)
 
-#define CHECK_LAUNCH() CU(cudaGetLastError())
+#define CHECK_LAUNCH()   \
+  do {                   \
+    CU(cudaGetLastError()); \
+    ++c->launches;       \
+  } while (0)
 
 fd_status check_usable(fd_ctx *c) {
   if (!c) return FD_EINVAL;
@@ -366,10 +372,11 @@ fd_status enqueue_chunk(fd_ctx *c, int parity, int len, bool timed) {
   return FD_OK;
 }
 
-fd_status get_graph(fd_ctx *c, int parity, int len, cudaGraphExec_t *out) {
+fd_status get_graph(fd_ctx *c, int parity, int len, cudaGraphExec_t *out, int64_t *kernels) {
   for (auto &gph : c->graphs)
     if (gph.parity == parity && gph.len == len) {
       *out = gph.exec;
+      *kernels = gph.kernels;
       return FD_OK;
     }
   if ((int)c->graphs.size() >= kGraphCacheMax) {
@@ -378,7 +385,10 @@ fd_status get_graph(fd_ctx *c, int parity, int len, cudaGraphExec_t *out) {
   }
   cudaGraph_t graph;
   CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  const int64_t before = c->launches;
   fd_status st = enqueue_chunk(c, parity, len, false);
+  const int64_t captured = c->launches - before;
+  c->launches = before;  // counted when the graph is replayed
   cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
   if (st) {
     if (e == cudaSuccess) cudaGraphDestroy(graph);
@@ -389,8 +399,9 @@ fd_status get_graph(fd_ctx *c, int parity, int len, cudaGraphExec_t *out) {
   e = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return fail(c, FD_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
-  c->graphs.push_back({parity, len, exec});
+  c->graphs.push_back({parity, len, captured, exec});
   *out = exec;
+  *kernels = captured;
   return FD_OK;
 }
 
@@ -772,9 +783,11 @@ fd_status fd_run(fd_ctx *c, int nt) {
     const int len = std::min(kGraphChunk, nt - done);
     if (c->opt.use_graphs && !c->opt.profile) {
       cudaGraphExec_t exec;
-      st = get_graph(c, c->cur, len, &exec);
+      int64_t kernels = 0;
+      st = get_graph(c, c->cur, len, &exec, &kernels);
       if (st) return st;
       CU(cudaGraphLaunch(exec, c->stream));
+      c->launches += kernels;
     } else {
       st = enqueue_chunk(c, c->cur, len, c->opt.profile != 0);
       if (st) return st;
@@ -837,7 +850,9 @@ fd_status fd_set_step(fd_ctx *c, int64_t n) {
   if (c->nrec > 0) {
     st = ensure_rec_capacity(c, n + 1);
     if (st) return st;
-    c->rec_rows = n + 1;  // rows before n are left at zero
+    // n = 0: row 0 is recorded by the next fd_run; n > 0: rows 0..n keep
+    // their contents (zero in a context that has not run)
+    c->rec_rows = n == 0 ? 0 : n + 1;
   }
   return FD_OK;
 }
@@ -861,6 +876,8 @@ fd_status fd_profile(fd_ctx *c, int64_t *launches, double *stencil_ms) {
 }
 
 const char *fd_kernel_name(const fd_ctx *c) { return c ? c->kernel_name : "none"; }
+
+int64_t fd_kernel_launches(const fd_ctx *c) { return c ? c->launches : -1; }
 
 void fd_destroy(fd_ctx *c) {
   if (!c) return;

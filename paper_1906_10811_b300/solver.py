@@ -86,6 +86,10 @@ class Solver:
     def kernel_name(self):
         return B.fd_kernel_name(self.ctx)
 
+    @property
+    def kernel_launches(self):
+        return B.fd_kernel_launches(self.ctx)
+
     def _empty(self, shape):
         if self.device:
             return self._torch.empty(shape, dtype=self._torch.float32, device="cuda")
