@@ -181,6 +181,50 @@ double fd_stability_symbol(int space_order);
 /* Library version string. */
 const char *fd_version(void);
 
+/*
+ * No-allocation acoustic run (the paper has no counterpart; this is a service
+ * entry point of the library).
+ *
+ * For callers that cannot allocate GPU memory: applications whose own memory
+ * pool already holds the device (cudaMalloc would fail or would break their
+ * accounting), and latency-critical loops where cudaMalloc/cudaFree would stall
+ * on device-wide synchronisation.  It advances nt ≥ 0 FD_ACOUSTIC steps (no
+ * sources or receivers) with the same arithmetic as fd_run, and allocates
+ * nothing: its working copies (two zero-halo time levels, the coefficient
+ * fields A and C, the set-up reduction words) live in one file-scope device
+ * array of FD_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds
+ * until the process exits.
+ *
+ * Arguments: ndim, shape, spacing, space_order, dt as for fd_create; m (> 0),
+ * damp (≥ 0, NULL = 0), u_cur = u^n, u_prev = u^{n-1} (NULL = u_cur) are DEVICE
+ * pointers to dense interior arrays; outputs u_out = u^{n+nt} and u_prev_out =
+ * u^{n+nt-1} (NULL to skip) are DEVICE pointers the caller owns.  cuda_stream is
+ * a cudaStream_t (NULL = legacy default stream); the work is ordered on it.
+ *
+ * Limits and behaviour:
+ *  - the four padded fields must fit: 4 × (n0+2r)(n1+2r)(32 + roundup32(n2+r))
+ *    × 4 B + 256 B ≤ FD_NOALLOC_SCRATCH_BYTES (3-D; 2-D has no halo along axis
+ *    0), e.g. up to 80³ at space order 8; larger grids return FD_EINVAL with the
+ *    byte counts in fd_last_error(NULL).
+ *  - the first call on a device looks up the array's device address for that
+ *    device (with the device current); make that first call before any stream
+ *    capture on that device.
+ *  - the call synchronises the stream once, after the coefficient set-up, to
+ *    validate m, damp and dt (FD_EINVAL as in fd_set_model); the steps and the
+ *    copies into u_out/u_prev_out are then queued on the stream and complete
+ *    in stream order.
+ *  - every call shares the one array and it keeps the last call's contents:
+ *    the call clears what must start at zero itself, but calls whose work
+ *    overlaps on the GPU (different streams or host threads without ordering)
+ *    race with each other and must not be issued.
+ *  - errors: FD_EINVAL / FD_ECUDA / FD_EUNSUPPORTED, text in fd_last_error(NULL).
+ */
+#define FD_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+fd_status fd_acoustic_run_noalloc(int ndim, const int64_t *shape, const double *spacing,
+                                  int space_order, double dt, const float *m,
+                                  const float *damp, const float *u_cur, const float *u_prev,
+                                  int nt, float *u_out, float *u_prev_out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

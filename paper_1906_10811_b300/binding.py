@@ -63,6 +63,10 @@ SIGNATURES = {
     "fd_weights": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "fd_stability_symbol": (ctypes.c_double, [ctypes.c_int]),
     "fd_version": (ctypes.c_char_p, []),
+    "fd_acoustic_run_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_i64),
+                                               ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                               ctypes.c_double, _vp, _vp, _vp, _vp, ctypes.c_int,
+                                               _vp, _vp, _vp]),
 }
 
 
@@ -232,3 +236,25 @@ def fd_stability_symbol(space_order):
 
 def fd_version():
     return load().fd_version().decode()
+
+
+def fd_acoustic_run_noalloc(shape, spacing, space_order, dt, m, damp, u_cur, u_prev, nt, u_out,
+                            u_prev_out=None, cuda_stream=None):
+    """No-allocation acoustic run on caller-owned device tensors (see include/fd.h).
+
+    For callers that cannot allocate GPU memory; all array arguments are torch
+    CUDA tensors (float32, contiguous) or raw device addresses.
+    """
+    for x in (m, damp, u_cur, u_prev, u_out, u_prev_out):
+        if x is not None and not (hasattr(x, "is_cuda") and x.is_cuda):
+            raise TypeError("fd_acoustic_run_noalloc takes torch CUDA tensors only")
+    lib = load()
+    nd = len(shape)
+    shp = (_i64 * nd)(*[int(x) for x in shape])
+    sp = (ctypes.c_double * nd)(*[float(h) for h in spacing])
+    keep = []
+    st = lib.fd_acoustic_run_noalloc(nd, shp, sp, int(space_order), float(dt), _ptr(m, keep),
+                                     _ptr(damp, keep), _ptr(u_cur, keep), _ptr(u_prev, keep),
+                                     int(nt), _out_ptr(u_out), _out_ptr(u_prev_out), cuda_stream)
+    if st != FD_OK:
+        raise FdError(st, lib.fd_last_error(None).decode())

@@ -899,3 +899,185 @@ const char *fd_last_error(const fd_ctx *c) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// No-allocation entry point: fd_acoustic_run_noalloc.
+//
+// Some callers cannot allocate GPU memory: a host application whose own pool
+// (for example a framework's caching allocator) already holds the device's
+// memory, or a latency-critical loop where cudaMalloc/cudaFree would stall on
+// device-wide synchronisation.  This entry point runs acoustic steps on buffers
+// the caller passes, keeping its working copies (the zero-halo time levels and
+// the coefficient fields A and C, plus the reduction words of the set-up
+// kernel) in one file-scope device array of fixed size instead of allocating.
+// ===========================================================================
+#include <mutex>
+
+namespace {
+
+constexpr size_t kNoAllocFloats = FD_NOALLOC_SCRATCH_BYTES / sizeof(float);
+constexpr size_t kNoAllocStatsFloats = 64;  // 256 B for the set-up kernel's reduction words
+constexpr int kNoAllocMaxDevices = 64;
+
+// Reserved on every GPU that loads the library, until the process exits.
+// Every call shares it and it keeps the last call's contents.
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocFloats];
+
+std::mutex g_noalloc_mutex;
+float *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+__global__ void k_noalloc_init_stats(unsigned *stats) {
+  stats[0] = 0x7f800000u;  // identity of the min over m's bit patterns
+  stats[1] = 0u;           // no invalid value seen
+}
+
+StencilFn plain_acoustic_fn(int R, bool three) {
+#define NA_PICK(RR) \
+  case RR:          \
+    return three ? k_stencil_plain<RR, kAcoustic, true> : k_stencil_plain<RR, kAcoustic, false>;
+  switch (R) {
+    NA_PICK(1) NA_PICK(2) NA_PICK(3) NA_PICK(4) NA_PICK(5) NA_PICK(6) NA_PICK(7) NA_PICK(8)
+  }
+#undef NA_PICK
+  return nullptr;
+}
+
+}  // namespace
+
+#define NA_CU(call)                                                                    \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(nullptr, FD_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));  \
+  } while (0)
+
+extern "C" fd_status fd_acoustic_run_noalloc(int ndim, const int64_t *shape, const double *spacing,
+                                             int space_order, double dt, const float *m,
+                                             const float *damp, const float *u_cur,
+                                             const float *u_prev, int nt, float *u_out,
+                                             float *u_prev_out, void *cuda_stream) {
+  g_create_error.clear();
+  if (ndim != 2 && ndim != 3) return fail(nullptr, FD_EINVAL, "ndim must be 2 or 3 (got %d)", ndim);
+  if (!shape || !spacing || !m || !u_cur || !u_out)
+    return fail(nullptr, FD_EINVAL, "shape, spacing, m, u_cur and u_out must not be NULL");
+  if (space_order < 2 || space_order > 2 * kMaxR || (space_order & 1))
+    return fail(nullptr, FD_EINVAL, "space_order must be even in [2,16] (got %d)", space_order);
+  if (nt < 0) return fail(nullptr, FD_EINVAL, "nt must be >= 0");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(nullptr, FD_EINVAL, "dt must be positive and finite");
+  for (int d = 0; d < ndim; ++d) {
+    if (shape[d] < 2 || shape[d] > (1 << 20))
+      return fail(nullptr, FD_EINVAL, "shape[%d] = %lld out of range", d, (long long)shape[d]);
+    if (!(spacing[d] > 0.0) || !std::isfinite(spacing[d]))
+      return fail(nullptr, FD_EINVAL, "spacing[%d] must be positive and finite", d);
+  }
+  // every array argument must be device memory (a host address would fault the kernels)
+  const void *ptrs[6] = {m, damp, u_cur, u_prev, u_out, u_prev_out};
+  for (const void *q : ptrs) {
+    if (!q) continue;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, q) != cudaSuccess ||
+        (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+      cudaGetLastError();
+      return fail(nullptr, FD_EINVAL, "array arguments must be device pointers");
+    }
+  }
+  const int R = space_order / 2;
+  Geom g{};
+  if (ndim == 3) {
+    g.n0 = (int)shape[0]; g.n1 = (int)shape[1]; g.n2 = (int)shape[2];
+    g.R0 = R;
+  } else {
+    g.n0 = 1; g.n1 = (int)shape[0]; g.n2 = (int)shape[1];
+    g.R0 = 0;
+  }
+  g.R = R;
+  g.px = kHaloX + ((g.n2 + R + 31) / 32) * 32;
+  g.py = g.n1 + 2 * R;
+  g.plane = (int64_t)g.px * g.py;
+  g.total = g.plane * (g.n0 + 2 * g.R0);
+  const size_t need = kNoAllocStatsFloats + 4 * (size_t)g.total;
+  if (need > kNoAllocFloats)
+    return fail(nullptr, FD_EINVAL,
+                "grid needs %zu bytes of working memory (four zero-halo fields); the "
+                "no-allocation entry point holds %zu bytes",
+                need * sizeof(float), (size_t)FD_NOALLOC_SCRATCH_BYTES);
+
+  // set-up, once per device: the device address of the file-scope array
+  int dev = 0;
+  NA_CU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(nullptr, FD_EUNSUPPORTED, "device %d", dev);
+  float *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+      void *p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess)
+        return fail(nullptr, FD_ECUDA, "cudaGetSymbolAddress(scratch) failed: %s",
+                    cudaGetErrorString(e));
+      g_noalloc_addr[dev] = (float *)p;
+    }
+    base = g_noalloc_addr[dev];
+  }
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  unsigned *stats = (unsigned *)base;
+  float *lev0 = base + kNoAllocStatsFloats;
+  float *lev1 = lev0 + g.total;
+  float *A = lev1 + g.total;
+  float *C = A + g.total;
+  const int64_t n = (int64_t)g.n0 * g.n1 * g.n2;
+
+  // the halos must start at zero; the reduction words at their identities
+  NA_CU(cudaMemsetAsync(lev0, 0, 2 * g.total * sizeof(float), stream));
+  k_noalloc_init_stats<<<1, 1, 0, stream>>>(stats);
+  NA_CU(cudaGetLastError());
+  k_scatter<<<blocks_for(n, 256), 256, 0, stream>>>(u_cur, lev0, g);
+  NA_CU(cudaGetLastError());
+  k_scatter<<<blocks_for(n, 256), 256, 0, stream>>>(u_prev ? u_prev : u_cur, lev1, g);
+  NA_CU(cudaGetLastError());
+  k_coefficients<<<blocks_for(n, 256), 256, 0, stream>>>(m, damp, A, C, g, dt, stats);
+  NA_CU(cudaGetLastError());
+  unsigned host_stats[2] = {0, 0};
+  NA_CU(cudaMemcpyAsync(host_stats, stats, sizeof host_stats, cudaMemcpyDeviceToHost, stream));
+  NA_CU(cudaStreamSynchronize(stream));
+  if (host_stats[1])
+    return fail(nullptr, FD_EINVAL, "m must be positive and finite, damp non-negative and finite");
+  float mmin;
+  std::memcpy(&mmin, &host_stats[0], sizeof mmin);
+  const double S = lib_symbol(space_order);
+  double lam = 0.0;
+  for (int d = 0; d < ndim; ++d) lam += S / (spacing[d] * spacing[d]);
+  const double dtmax = 2.0 * std::sqrt((double)mmin / lam);
+  if (dt > dtmax * (1.0 + 1e-12))
+    return fail(nullptr, FD_EINVAL, "dt = %g exceeds the leapfrog limit %g for min(m) = %g", dt,
+                dtmax, (double)mmin);
+
+  Coef coef;
+  std::memset(&coef, 0, sizeof coef);
+  double w[kMaxR + 1];
+  lib_weights(space_order, w);
+  double wc = 0.0;
+  for (int d = 0; d < ndim; ++d) {
+    const int ax = d + 3 - ndim;
+    const double s = 1.0 / (spacing[d] * spacing[d]);
+    for (int k = 1; k <= R; ++k) coef.w[ax][k] = (float)(w[k] * s);
+    wc += w[0] * s;
+  }
+  coef.wc = (float)wc;
+  StencilFn fn = plain_acoustic_fn(R, ndim == 3);
+  float *cur = lev0, *prev = lev1;
+  dim3 block(32, 8);
+  dim3 grid((g.n2 + 31) / 32, (g.n1 + 7) / 8, g.n0);
+  for (int s = 0; s < nt; ++s) {
+    fn<<<grid, block, 0, stream>>>(cur, prev, A, C, g, coef);  // u^{n+1} over u^{n-1}
+    NA_CU(cudaGetLastError());
+    std::swap(cur, prev);
+  }
+  k_gather<<<blocks_for(n, 256), 256, 0, stream>>>(cur, u_out, g);
+  NA_CU(cudaGetLastError());
+  if (u_prev_out) {
+    k_gather<<<blocks_for(n, 256), 256, 0, stream>>>(prev, u_prev_out, g);
+    NA_CU(cudaGetLastError());
+  }
+  return FD_OK;
+}
