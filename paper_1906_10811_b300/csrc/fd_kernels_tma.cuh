@@ -1,23 +1,445 @@
-// fd_kernels_tma.cuh -- pipelined 3-D stencil kernel (TMA plane ring).
+// fd_kernels_tma.cuh -- pipelined 3-D stencil kernel: TMA plane ring + register z-queue.
+//
+// Work: the grid's (x, y) extent is cut into TX × TY tiles; a "tile-plane" is one
+// tile at one z.  The W = tiles × n0 tile-planes are split into G contiguous
+// ranges (tile-major, z fastest), one per persistent CTA (G = SMs × resident
+// CTAs), so every CTA gets the same number of planes to within one.  A range is
+// a few z-segments of single tiles; a CTA streams each segment along z.
+//
+// Per CTA: warp NW (the last) is the producer; one lane issues
+//   - a TMA load of the u^n plane p (tile plus halo: (TX+2·HXB) × (TY+2R)) into
+//     ring U (DU slots), for every p in [za-R, zb+R) of a segment [za, zb);
+//   - TMA loads of the u^{n-1}, A, C tiles (TX × TY) of plane p-R into ring X
+//     (DX slots) when p-R is a plane the CTA updates (acoustic only).
+// The NW consumer warps own NY rows each (lane = x).  For every plane p they
+// push u^n(p) at their points into a register queue of 2R+1 planes, and once
+// the queue holds p-2R..p they update plane zc = p-R: z-neighbours from the
+// queue, x- and y-neighbours from the shared copy of plane zc (still in ring U),
+// then store u^{n+1} with coalesced 128-byte rows.
+//
+// Every mbarrier wait is bounded (clock64 budget).  On expiry the kernel writes
+// an error code and its block index into err[0..1], stops, waits (bounded) for
+// its own TMA copies in flight, and returns; fd_read reports FD_ETIMEOUT.
 #pragma once
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "fd_common.cuh"
 
 namespace fdk {
 
-struct TmaPlan {
-  const char *name = "none";
-};
+constexpr int kTmaTX = 32;        // tile width in x (one warp of lanes)
+constexpr int kTmaTY = 16;        // tile height in y
+constexpr int kTmaNY = 2;         // rows per consumer thread
+constexpr int kTmaNW = kTmaTY / kTmaNY;  // consumer warps
+constexpr int kTmaThreads = (kTmaNW + 1) * 32;
+constexpr int kTmaDX = 4;         // slots of the u^{n-1}/A/C ring
+constexpr long long kWaitBudget = 1ll << 31;  // clock cycles (~1 s at 2 GHz)
 
-inline cudaError_t plan_tma(TmaPlan &, const Geom &, int, float *const *, float *, float *,
-                            const char **why) {
-  *why = "not built";
-  return cudaErrorNotSupported;
+__host__ __device__ constexpr int tma_hxb(int R) { return (R + 3) / 4 * 4; }   // x halo, 16-B multiple
+__host__ __device__ constexpr int tma_du(int R) { return R + 4; }              // ring U slots
+__host__ __device__ constexpr int tma_bw(int R) { return kTmaTX + 2 * tma_hxb(R); }  // box width
+__host__ __device__ constexpr int tma_bh(int R) { return kTmaTY + 2 * R; }           // box height
+__host__ __device__ constexpr int tma_ubytes(int R) { return tma_bw(R) * tma_bh(R) * 4; }
+__host__ __device__ constexpr int tma_xbytes() { return kTmaTX * kTmaTY * 4; }
+__host__ __device__ constexpr int tma_align128(int b) { return (b + 127) / 128 * 128; }
+// shared memory: barriers (1 KB) | ring U | ring X (three tiles per slot)
+__host__ __device__ constexpr int tma_smem_bytes(int R, bool acoustic) {
+  return 1024 + tma_du(R) * tma_align128(tma_ubytes(R)) +
+         (acoustic ? kTmaDX * 3 * tma_xbytes() : 0);
 }
 
-inline cudaError_t launch_tma_step(const TmaPlan &, int, float *, const float *, const float *,
-                                   const Coef &, int *, cudaStream_t) {
-  return cudaErrorNotSupported;
+// ---------------------------------------------------------------------------
+// PTX helpers (mbarrier, TMA)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of the given parity; false if the budget ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > kWaitBudget) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap *map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
+}
+
+// Contiguous share [q0, q1) of the W tile-planes for CTA b of G.
+__device__ __forceinline__ void cta_range(int64_t W, int b, int G, int64_t &q0, int64_t &q1) {
+  q0 = W * b / G;
+  q1 = W * (b + 1) / G;
+}
+
+struct TmaArgs {
+  Geom g;
+  Coef c;
+  int tiles_x;       // tiles along x
+  int64_t W;         // tile-planes
+  float *out;        // u^{n+1} (padded layout; the buffer that held u^{n-1})
+  int *err;          // err[0] = code, err[1] = block
+};
+
+template <int R, int EQ>
+__global__ void __launch_bounds__(kTmaThreads, 2)
+k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
+                const __grid_constant__ CUtensorMap map_p,   // u^{n-1}, tile box
+                const __grid_constant__ CUtensorMap map_a,   // A, tile box
+                const __grid_constant__ CUtensorMap map_c,   // C, tile box
+                const TmaArgs args) {
+  constexpr int HXB = tma_hxb(R), BW = tma_bw(R), BH = tma_bh(R), DU = tma_du(R);
+  constexpr int USLOT = tma_align128(tma_ubytes(R)) / 4;  // floats per ring-U slot
+  constexpr int XT = kTmaTX * kTmaTY;                      // floats per tile
+  constexpr int Q = 2 * R + 1;                             // queue length
+  constexpr bool AC = EQ == kAcoustic;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t *full_u = reinterpret_cast<uint64_t *>(smem);
+  uint64_t *empty_u = full_u + DU;
+  uint64_t *full_x = empty_u + DU;
+  uint64_t *empty_x = full_x + kTmaDX;
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(empty_x + kTmaDX);
+  float *ring_u = reinterpret_cast<float *>(smem + 1024);
+  float *ring_x = ring_u + DU * USLOT;
+
+  const Geom &g = args.g;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < DU; ++i) {
+      mbar_init(&full_u[i], 1);
+      mbar_init(&empty_u[i], kTmaNW);
+    }
+    for (int i = 0; i < kTmaDX; ++i) {
+      mbar_init(&full_x[i], 1);
+      mbar_init(&empty_x[i], kTmaNW);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+
+  int64_t q0, q1;
+  cta_range(args.W, blockIdx.x, gridDim.x, q0, q1);
+  const int n0 = g.n0;
+
+  if (warp == kTmaNW) {
+    // ------------------------------- producer -------------------------------
+    if (lane == 0) {
+      tma_prefetch_desc(&map_u);
+      if (AC) {
+        tma_prefetch_desc(&map_p);
+        tma_prefetch_desc(&map_a);
+        tma_prefetch_desc(&map_c);
+      }
+      uint32_t su = 0, sx = 0;  // fills issued to rings U and X
+      bool ok = true;
+      for (int64_t q = q0; q < q1 && ok;) {
+        const int tile = (int)(q / n0);
+        const int za = (int)(q % n0);
+        const int zb = (int)min((int64_t)n0, za + (q1 - q));
+        q += zb - za;
+        const int x0 = (tile % args.tiles_x) * kTmaTX, y0 = (tile / args.tiles_x) * kTmaTY;
+        for (int p = za - R; p < zb + R; ++p) {
+          if (*abort_flag) { ok = false; break; }
+          const int zc = p - R;
+          if (AC && zc >= za) {
+            const uint32_t slot = sx % kTmaDX;
+            if (sx >= (uint32_t)kTmaDX && !mbar_wait(&empty_x[slot], ((sx / kTmaDX) - 1) & 1)) {
+              ok = false;
+              break;
+            }
+            float *dst = ring_x + slot * 3 * XT;
+            mbar_expect_tx(&full_x[slot], 3 * XT * 4);
+            tma_load_3d(dst, &map_p, x0 + kHaloX, y0 + R, zc + R, &full_x[slot]);
+            tma_load_3d(dst + XT, &map_a, x0 + kHaloX, y0 + R, zc + R, &full_x[slot]);
+            tma_load_3d(dst + 2 * XT, &map_c, x0 + kHaloX, y0 + R, zc + R, &full_x[slot]);
+            ++sx;
+          }
+          const uint32_t slot = su % DU;
+          if (su >= (uint32_t)DU && !mbar_wait(&empty_u[slot], ((su / DU) - 1) & 1)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full_u[slot], BW * BH * 4);
+          tma_load_3d(ring_u + slot * USLOT, &map_u, x0 + kHaloX - HXB, y0, p + R, &full_u[slot]);
+          ++su;
+        }
+      }
+      if (!ok && atomicCAS(args.err, 0, 2) == 0) args.err[1] = blockIdx.x;
+      if (!ok) *abort_flag = 1;
+      // drain: every fill issued must land before the block exits
+      __syncwarp(1u);
+      bool drained = true;
+      for (uint32_t i = 0; i < (uint32_t)DU && i < su; ++i) {
+        const uint32_t last = su - 1 - ((su - 1 - i) % DU);  // last fill of slot i
+        drained &= mbar_wait(&full_u[last % DU], (last / DU) & 1);
+      }
+      for (uint32_t i = 0; i < (uint32_t)kTmaDX && i < sx; ++i) {
+        const uint32_t last = sx - 1 - ((sx - 1 - i) % kTmaDX);
+        drained &= mbar_wait(&full_x[last % kTmaDX], (last / kTmaDX) & 1);
+      }
+      if (!drained && atomicCAS(args.err, 0, 3) == 0) args.err[1] = blockIdx.x;
+    }
+    return;
+  }
+
+  // --------------------------------- consumers --------------------------------
+  const float wc = args.c.wc;
+  float wz[R + 1], wy[R + 1], wx[R + 1];
+#pragma unroll
+  for (int k = 1; k <= R; ++k) {
+    wz[k] = args.c.w[0][k];
+    wy[k] = args.c.w[1][k];
+    wx[k] = args.c.w[2][k];
+  }
+  float qz[kTmaNY][Q];
+  uint32_t su = 0, sx = 0;
+  const int row0 = warp * kTmaNY;  // first tile row of this thread
+  for (int64_t q = q0; q < q1;) {
+    const int tile = (int)(q / n0);
+    const int za = (int)(q % n0);
+    const int zb = (int)min((int64_t)n0, za + (q1 - q));
+    q += zb - za;
+    const int x = (tile % args.tiles_x) * kTmaTX + lane;
+    const int ybase = (tile / args.tiles_x) * kTmaTY + row0;
+    int p = za - R;
+    const int pend = zb + R;
+    while (p < pend) {
+#pragma unroll
+      for (int ph = 0; ph < Q; ++ph) {
+        if (p < pend) {
+          const uint32_t slot = su % DU;
+          if (!mbar_wait(&full_u[slot], (su / DU) & 1)) goto timeout;
+          const float *pl = ring_u + slot * USLOT;
+#pragma unroll
+          for (int j = 0; j < kTmaNY; ++j) qz[j][ph] = pl[(R + row0 + j) * BW + HXB + lane];
+          const int zc = p - R;
+          if (zc >= za) {
+            // update plane zc: its shared copy is fill su - R of ring U
+            const uint32_t cs = (su - R) % DU;
+            const float *cp = ring_u + cs * USLOT;
+            const float *xs = nullptr;
+            uint32_t xslot = 0;
+            if (AC) {
+              xslot = sx % kTmaDX;
+              if (!mbar_wait(&full_x[xslot], (sx / kTmaDX) & 1)) goto timeout;
+              xs = ring_x + xslot * 3 * XT;
+            }
+            // y column of this thread: rows row0-R .. row0+NY-1+R of the tile
+            float ycol[kTmaNY + 2 * R];
+#pragma unroll
+            for (int i = 0; i < kTmaNY + 2 * R; ++i) ycol[i] = cp[(row0 + i) * BW + HXB + lane];
+#pragma unroll
+            for (int j = 0; j < kTmaNY; ++j) {
+              const float *rowp = cp + (R + row0 + j) * BW + HXB + lane;
+              const float uc = qz[j][(ph + 1 + R) % Q];
+              float lap = wc * uc;
+#pragma unroll
+              for (int k = 1; k <= R; ++k) {
+                lap = fmaf(wx[k], rowp[k] + rowp[-k], lap);
+                lap = fmaf(wy[k], ycol[R + j + k] + ycol[R + j - k], lap);
+                lap = fmaf(wz[k], qz[j][(ph + 1 + R + k) % Q] + qz[j][(ph + 1 + R - k + Q) % Q], lap);
+              }
+              const int y = ybase + j;
+              if (x < g.n2 && y < g.n1) {
+                const int64_t o = gidx(g, zc, y, x);
+                if (AC) {
+                  const int t = (row0 + j) * kTmaTX + lane;
+                  const float up = xs[t], a = xs[XT + t], cc = xs[2 * XT + t];
+                  args.out[o] = fmaf(a, lap, fmaf(1.f + cc, uc, -cc * up));
+                } else if (x > 0 && x < g.n2 - 1 && y > 0 && y < g.n1 - 1 && zc > 0 &&
+                           zc < n0 - 1) {
+                  args.out[o] = uc + lap;
+                }
+              }
+            }
+            __syncwarp();
+            if (lane == 0) {
+              if (AC) mbar_arrive(&empty_x[xslot]);
+              mbar_arrive(&empty_u[cs]);
+            }
+            if (AC) ++sx;
+          }
+          if (p < za || p >= zb) {  // plane used for the queue only
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty_u[slot]);
+          }
+          ++su;
+          ++p;
+        }
+      }
+    }
+  }
+  return;
+timeout:
+  if (lane == 0) {
+    if (atomicCAS(args.err, 0, 1) == 0) args.err[1] = blockIdx.x;
+    *abort_flag = 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct TmaPlan {
+  const char *name = "none";
+  CUtensorMap map_u[2];   // u levels, halo box
+  CUtensorMap map_t[2];   // u levels, tile box (u^{n-1} reads)
+  CUtensorMap map_a, map_c;
+  TmaArgs args{};
+  float *level[2] = {nullptr, nullptr};
+  void (*fn)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, TmaArgs) = nullptr;
+  int grid = 0;
+  int smem = 0;
+};
+
+using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
+
+inline EncodeFn tma_encoder() {
+  static EncodeFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeFn)p;
+  }
+  return fn;
+}
+
+inline bool encode_map(EncodeFn enc, CUtensorMap *m, float *base, const Geom &g, int bw, int bh) {
+  const cuuint64_t dims[3] = {(cuuint64_t)g.px, (cuuint64_t)g.py, (cuuint64_t)(g.n0 + 2 * g.R0)};
+  const cuuint64_t strides[2] = {(cuuint64_t)g.px * 4, (cuuint64_t)g.plane * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int R, int EQ>
+inline cudaError_t tma_configure(TmaPlan &pl) {
+  pl.fn = k_stencil3d_tma<R, EQ>;
+  pl.smem = tma_smem_bytes(R, EQ == kAcoustic);
+  cudaError_t e = cudaFuncSetAttribute(k_stencil3d_tma<R, EQ>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, pl.smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil3d_tma<R, EQ>, kTmaThreads,
+                                                    pl.smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  pl.grid = sms * per_sm;
+  return cudaSuccess;
+}
+
+// Build the plan: tensor maps for both levels and the coefficient fields.
+inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, float *const *level, float *A,
+                            float *C, const char **why) {
+  *why = nullptr;
+  if (g.R0 == 0 || g.R < 1 || g.R > kMaxR) {
+    *why = "3-D grids only";
+    return cudaErrorNotSupported;
+  }
+  // TMA rules: 16-B aligned bases and strides, inner box extent a 16-B multiple,
+  // x coordinates multiples of 4 floats (x0 + kHaloX - HXB with x0 % 32 == 0).
+  if ((g.px * 4) % 16 || tma_hxb(g.R) % 4 || (tma_bw(g.R) * 4) % 16 || kHaloX % 4 ||
+      tma_bw(g.R) > 256 || tma_bh(g.R) > 256 || (kTmaTX * 4) % 16) {
+    *why = "layout violates the TMA alignment rules";
+    return cudaErrorNotSupported;
+  }
+  EncodeFn enc = tma_encoder();
+  if (!enc) {
+    *why = "cuTensorMapEncodeTiled unavailable";
+    return cudaErrorNotSupported;
+  }
+  const int R = g.R;
+  for (int b = 0; b < 2; ++b) {
+    if (!encode_map(enc, &pl.map_u[b], level[b], g, tma_bw(R), tma_bh(R)) ||
+        !encode_map(enc, &pl.map_t[b], level[b], g, kTmaTX, kTmaTY)) {
+      *why = "tensor map encoding failed";
+      return cudaErrorInvalidValue;
+    }
+    pl.level[b] = level[b];
+  }
+  if (eq == kAcoustic) {
+    if (!encode_map(enc, &pl.map_a, A, g, kTmaTX, kTmaTY) ||
+        !encode_map(enc, &pl.map_c, C, g, kTmaTX, kTmaTY)) {
+      *why = "tensor map encoding failed";
+      return cudaErrorInvalidValue;
+    }
+  } else {
+    pl.map_a = pl.map_t[0];
+    pl.map_c = pl.map_t[0];
+  }
+  cudaError_t e = cudaErrorNotSupported;
+  const bool ac = eq == kAcoustic;
+#define TMA_CASE(RR)                                                                  \
+  case RR:                                                                            \
+    e = ac ? tma_configure<RR, kAcoustic>(pl) : tma_configure<RR, kDiffusion>(pl);    \
+    break;
+  switch (R) { TMA_CASE(1) TMA_CASE(2) TMA_CASE(3) TMA_CASE(4) TMA_CASE(5) TMA_CASE(6) TMA_CASE(7) TMA_CASE(8) }
+#undef TMA_CASE
+  if (e != cudaSuccess) {
+    *why = "kernel configuration failed";
+    return e;
+  }
+  pl.args.g = g;
+  pl.args.tiles_x = (g.n2 + kTmaTX - 1) / kTmaTX;
+  const int tiles_y = (g.n1 + kTmaTY - 1) / kTmaTY;
+  pl.args.W = (int64_t)pl.args.tiles_x * tiles_y * g.n0;
+  if (pl.grid > pl.args.W) pl.grid = (int)pl.args.W;
+  pl.name = ac ? "stencil3d_tma_acoustic" : "stencil3d_tma_diffusion";
+  return cudaSuccess;
+}
+
+// One step with u^n in level[cur]; writes u^{n+1} into out (= level[cur ^ 1]).
+inline cudaError_t launch_tma_step(const TmaPlan &pl, int cur, float *out, const float *,
+                                   const float *, const Coef &c, int *err, cudaStream_t s) {
+  TmaArgs a = pl.args;
+  a.c = c;
+  a.out = out;
+  a.err = err;
+  pl.fn<<<pl.grid, kTmaThreads, pl.smem, s>>>(pl.map_u[cur], pl.map_t[cur ^ 1], pl.map_a,
+                                              pl.map_c, a);
+  return cudaGetLastError();
 }
 
 inline void destroy_tma(TmaPlan &) {}
