@@ -1,10 +1,14 @@
 // fd_kernels_tma.cuh -- pipelined 3-D stencil kernel: TMA plane ring + register z-queue.
 //
 // Work: the grid's (x, y) extent is cut into TX × TY tiles; a "tile-plane" is one
-// tile at one z.  The W = tiles × n0 tile-planes are split into G contiguous
-// ranges (tile-major, z fastest), one per persistent CTA (G = SMs × resident
-// CTAs), so every CTA gets the same number of planes to within one.  A range is
-// a few z-segments of single tiles; a CTA streams each segment along z.
+// tile at one z.  The W = tiles × n0 tile-planes are ordered z-block-major (z
+// blocks of ZB planes; inside a block tile by tile, x fastest, then z) and split
+// into G contiguous ranges, one per persistent CTA (G = SMs × resident CTAs), so
+// every CTA gets the same number of planes to within one.  With ZB about W/G,
+// CTAs that hold neighbouring tiles start at the same z and stream in step, so
+// the halo rows one tile shares with the next are still in L2 when the other
+// reads them.  A range is a few z-segments of single tiles; a CTA streams each
+// segment along z.
 //
 // Per CTA: warp NW (the last) is the producer; one lane issues
 //   - a TMA load of the u^n plane p (tile plus halo: (TX+2·HXB) × (TY+2R)) into
@@ -23,6 +27,8 @@
 #pragma once
 
 #include <cuda.h>
+
+#include <algorithm>
 #include <cudaTypedefs.h>
 
 #include "fd_common.cuh"
@@ -104,10 +110,26 @@ __device__ __forceinline__ void cta_range(int64_t W, int b, int G, int64_t &q0, 
   q1 = W * (b + 1) / G;
 }
 
+// Position q (z-block-major order) -> segment: tile, first plane za, end zb
+// (the segment ends at the end of the z-block or of the range, whichever is first).
+__device__ __forceinline__ void segment_at(int64_t q, int64_t q1, int ntiles, int zblock, int n0,
+                                           int &tile, int &za, int &zb) {
+  const int64_t per_block = (int64_t)ntiles * zblock;
+  const int k = (int)(q / per_block);
+  const int64_t r = q - k * per_block;
+  const int z0 = k * zblock;
+  const int len = min(zblock, n0 - z0);
+  tile = (int)(r / len);
+  za = z0 + (int)(r % len);
+  zb = (int)min((int64_t)(z0 + len), za + (q1 - q));
+}
+
 struct TmaArgs {
   Geom g;
   Coef c;
   int tiles_x;       // tiles along x
+  int ntiles;        // tiles in a plane
+  int zblock;        // planes per z-block of the work order
   int64_t W;         // tile-planes
   float *out;        // u^{n+1} (padded layout; the buffer that held u^{n-1})
   int *err;          // err[0] = code, err[1] = block
@@ -167,9 +189,8 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
       uint32_t su = 0, sx = 0;  // fills issued to rings U and X
       bool ok = true;
       for (int64_t q = q0; q < q1 && ok;) {
-        const int tile = (int)(q / n0);
-        const int za = (int)(q % n0);
-        const int zb = (int)min((int64_t)n0, za + (q1 - q));
+        int tile, za, zb;
+        segment_at(q, q1, args.ntiles, args.zblock, n0, tile, za, zb);
         q += zb - za;
         const int x0 = (tile % args.tiles_x) * kTmaTX, y0 = (tile / args.tiles_x) * kTmaTY;
         for (int p = za - R; p < zb + R; ++p) {
@@ -229,12 +250,14 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
   uint32_t su = 0, sx = 0;
   const int row0 = warp * kTmaNY;  // first tile row of this thread
   for (int64_t q = q0; q < q1;) {
-    const int tile = (int)(q / n0);
-    const int za = (int)(q % n0);
-    const int zb = (int)min((int64_t)n0, za + (q1 - q));
+    int tile, za, zb;
+    segment_at(q, q1, args.ntiles, args.zblock, n0, tile, za, zb);
     q += zb - za;
     const int x = (tile % args.tiles_x) * kTmaTX + lane;
     const int ybase = (tile / args.tiles_x) * kTmaTY + row0;
+    // output row pointers advance one plane per updated plane
+    const bool xin = x < g.n2;
+    float *optr = args.out + gidx(g, za, ybase, x);
     int p = za - R;
     const int pend = zb + R;
     while (p < pend) {
@@ -274,18 +297,19 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
                 lap = fmaf(wz[k], qz[j][(ph + 1 + R + k) % Q] + qz[j][(ph + 1 + R - k + Q) % Q], lap);
               }
               const int y = ybase + j;
-              if (x < g.n2 && y < g.n1) {
-                const int64_t o = gidx(g, zc, y, x);
+              if (xin && y < g.n1) {
+                float *o = optr + j * g.px;
                 if (AC) {
                   const int t = (row0 + j) * kTmaTX + lane;
                   const float up = xs[t], a = xs[XT + t], cc = xs[2 * XT + t];
-                  args.out[o] = fmaf(a, lap, fmaf(1.f + cc, uc, -cc * up));
+                  *o = fmaf(a, lap, fmaf(1.f + cc, uc, -cc * up));
                 } else if (x > 0 && x < g.n2 - 1 && y > 0 && y < g.n1 - 1 && zc > 0 &&
                            zc < n0 - 1) {
-                  args.out[o] = uc + lap;
+                  *o = uc + lap;
                 }
               }
             }
+            optr += g.plane;
             __syncwarp();
             if (lane == 0) {
               if (AC) mbar_arrive(&empty_x[xslot]);
@@ -348,7 +372,7 @@ inline bool encode_map(EncodeFn enc, CUtensorMap *m, float *base, const Geom &g,
   const cuuint32_t estr[3] = {1, 1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+             CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <int R, int EQ>
@@ -424,8 +448,12 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, float *const *le
   pl.args.g = g;
   pl.args.tiles_x = (g.n2 + kTmaTX - 1) / kTmaTX;
   const int tiles_y = (g.n1 + kTmaTY - 1) / kTmaTY;
-  pl.args.W = (int64_t)pl.args.tiles_x * tiles_y * g.n0;
+  pl.args.ntiles = pl.args.tiles_x * tiles_y;
+  pl.args.W = (int64_t)pl.args.ntiles * g.n0;
   if (pl.grid > pl.args.W) pl.grid = (int)pl.args.W;
+  // z-block height: about one CTA's share, so neighbouring tiles stream in step
+  const int64_t share = (pl.args.W + pl.grid - 1) / pl.grid;
+  pl.args.zblock = (int)std::min<int64_t>(g.n0, std::max<int64_t>(1, share));
   pl.name = ac ? "stencil3d_tma_acoustic" : "stencil3d_tma_diffusion";
   return cudaSuccess;
 }
