@@ -15,7 +15,7 @@
 //     ring U (DU slots), for every p in [za-R, zb+R) of a segment [za, zb);
 //   - TMA loads of the u^{n-1}, A, C tiles (TX × TY) of plane p-R into ring X
 //     (DX slots) when p-R is a plane the CTA updates (acoustic only).
-// The NW consumer warps own NY rows each (lane = x).  For every plane p they
+// The NW consumer warps own NY rows each (lane = x; TY = NW·NY).  For every plane p they
 // push u^n(p) at their points into a register queue of 2R+1 planes, and once
 // the queue holds p-2R..p they update plane zc = p-R: z-neighbours from the
 // queue, x- and y-neighbours from the shared copy of plane zc (still in ring U),
@@ -36,24 +36,25 @@
 namespace fdk {
 
 constexpr int kTmaTX = 32;        // tile width in x (one warp of lanes)
-constexpr int kTmaTY = 16;        // tile height in y
-constexpr int kTmaNY = 2;         // rows per consumer thread
-constexpr int kTmaNW = kTmaTY / kTmaNY;  // consumer warps
+constexpr int kTmaNW = 8;         // consumer warps
 constexpr int kTmaThreads = (kTmaNW + 1) * 32;
 constexpr int kTmaDX = 4;         // slots of the u^{n-1}/A/C ring
 constexpr long long kWaitBudget = 1ll << 31;  // clock cycles (~1 s at 2 GHz)
 
+// rows per consumer thread: 4 up to radius 4, 2 above (register queue of 2R+1 planes per row)
+__host__ __device__ constexpr int tma_ny(int R) { return R <= 4 ? 4 : 2; }
+__host__ __device__ constexpr int tma_ty(int R) { return kTmaNW * tma_ny(R); }          // tile height
 __host__ __device__ constexpr int tma_hxb(int R) { return (R + 3) / 4 * 4; }   // x halo, 16-B multiple
 __host__ __device__ constexpr int tma_du(int R) { return R + 4; }              // ring U slots
 __host__ __device__ constexpr int tma_bw(int R) { return kTmaTX + 2 * tma_hxb(R); }  // box width
-__host__ __device__ constexpr int tma_bh(int R) { return kTmaTY + 2 * R; }           // box height
+__host__ __device__ constexpr int tma_bh(int R) { return tma_ty(R) + 2 * R; }        // box height
 __host__ __device__ constexpr int tma_ubytes(int R) { return tma_bw(R) * tma_bh(R) * 4; }
-__host__ __device__ constexpr int tma_xbytes() { return kTmaTX * kTmaTY * 4; }
+__host__ __device__ constexpr int tma_xbytes(int R) { return kTmaTX * tma_ty(R) * 4; }
 __host__ __device__ constexpr int tma_align128(int b) { return (b + 127) / 128 * 128; }
 // shared memory: barriers (1 KB) | ring U | ring X (three tiles per slot)
 __host__ __device__ constexpr int tma_smem_bytes(int R, bool acoustic) {
   return 1024 + tma_du(R) * tma_align128(tma_ubytes(R)) +
-         (acoustic ? kTmaDX * 3 * tma_xbytes() : 0);
+         (acoustic ? kTmaDX * 3 * tma_xbytes(R) : 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -142,9 +143,10 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
                 const __grid_constant__ CUtensorMap map_a,   // A, tile box
                 const __grid_constant__ CUtensorMap map_c,   // C, tile box
                 const TmaArgs args) {
-  constexpr int HXB = tma_hxb(R), BW = tma_bw(R), BH = tma_bh(R), DU = tma_du(R);
+  constexpr int NY = tma_ny(R), TY = tma_ty(R);
+  constexpr int HXB = tma_hxb(R), BW = tma_bw(R), DU = tma_du(R);
   constexpr int USLOT = tma_align128(tma_ubytes(R)) / 4;  // floats per ring-U slot
-  constexpr int XT = kTmaTX * kTmaTY;                      // floats per tile
+  constexpr int XT = kTmaTX * TY;                          // floats per tile
   constexpr int Q = 2 * R + 1;                             // queue length
   constexpr bool AC = EQ == kAcoustic;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -192,7 +194,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
         int tile, za, zb;
         segment_at(q, q1, args.ntiles, args.zblock, n0, tile, za, zb);
         q += zb - za;
-        const int x0 = (tile % args.tiles_x) * kTmaTX, y0 = (tile / args.tiles_x) * kTmaTY;
+        const int x0 = (tile % args.tiles_x) * kTmaTX, y0 = (tile / args.tiles_x) * TY;
         for (int p = za - R; p < zb + R; ++p) {
           if (*abort_flag) { ok = false; break; }
           const int zc = p - R;
@@ -214,7 +216,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
             ok = false;
             break;
           }
-          mbar_expect_tx(&full_u[slot], BW * BH * 4);
+          mbar_expect_tx(&full_u[slot], tma_ubytes(R));
           tma_load_3d(ring_u + slot * USLOT, &map_u, x0 + kHaloX - HXB, y0, p + R, &full_u[slot]);
           ++su;
         }
@@ -222,7 +224,6 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
       if (!ok && atomicCAS(args.err, 0, 2) == 0) args.err[1] = blockIdx.x;
       if (!ok) *abort_flag = 1;
       // drain: every fill issued must land before the block exits
-      __syncwarp(1u);
       bool drained = true;
       for (uint32_t i = 0; i < (uint32_t)DU && i < su; ++i) {
         const uint32_t last = su - 1 - ((su - 1 - i) % DU);  // last fill of slot i
@@ -238,75 +239,90 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
   }
 
   // --------------------------------- consumers --------------------------------
-  const float wc = args.c.wc;
-  float wz[R + 1], wy[R + 1], wx[R + 1];
-#pragma unroll
-  for (int k = 1; k <= R; ++k) {
-    wz[k] = args.c.w[0][k];
-    wy[k] = args.c.w[1][k];
-    wx[k] = args.c.w[2][k];
-  }
-  float qz[kTmaNY][Q];
+  // Fill s of ring U is plane za-R+(s-s0) of the current segment (s0 = its first
+  // fill); the queue slot of plane za-R+m is m mod Q.
+  float qz[NY][Q];
   uint32_t su = 0, sx = 0;
-  const int row0 = warp * kTmaNY;  // first tile row of this thread
+  const int row0 = warp * NY;  // first tile row of this thread
+  const float *const wk0 = args.c.w[0];
+  const float *const wk1 = args.c.w[1];
+  const float *const wk2 = args.c.w[2];
   for (int64_t q = q0; q < q1;) {
     int tile, za, zb;
     segment_at(q, q1, args.ntiles, args.zblock, n0, tile, za, zb);
     q += zb - za;
     const int x = (tile % args.tiles_x) * kTmaTX + lane;
-    const int ybase = (tile / args.tiles_x) * kTmaTY + row0;
-    // output row pointers advance one plane per updated plane
-    const bool xin = x < g.n2;
+    const int ybase = (tile / args.tiles_x) * TY + row0;
+    // which of this thread's rows it stores (diffusion: interior nodes only)
+    unsigned rows_ok = 0;
+#pragma unroll
+    for (int j = 0; j < NY; ++j) {
+      const int y = ybase + j;
+      const bool in = AC ? (x < g.n2 && y < g.n1)
+                         : (x > 0 && x < g.n2 - 1 && y > 0 && y < g.n1 - 1);
+      rows_ok |= (in ? 1u : 0u) << j;
+    }
     float *optr = args.out + gidx(g, za, ybase, x);
-    int p = za - R;
-    const int pend = zb + R;
-    while (p < pend) {
+
+    // warm-up: planes za-R .. za+R-1 fill queue slots 0 .. 2R-1
 #pragma unroll
-      for (int ph = 0; ph < Q; ++ph) {
-        if (p < pend) {
-          const uint32_t slot = su % DU;
-          if (!mbar_wait(&full_u[slot], (su / DU) & 1)) goto timeout;
-          const float *pl = ring_u + slot * USLOT;
+    for (int m = 0; m < 2 * R; ++m) {
+      const int p = za - R + m;
+      const uint32_t slot = su % DU;
+      if (!mbar_wait(&full_u[slot], (su / DU) & 1)) goto timeout;
+      const float *pl = ring_u + slot * USLOT + (R + row0) * BW + HXB + lane;
 #pragma unroll
-          for (int j = 0; j < kTmaNY; ++j) qz[j][ph] = pl[(R + row0 + j) * BW + HXB + lane];
-          const int zc = p - R;
-          if (zc >= za) {
-            // update plane zc: its shared copy is fill su - R of ring U
-            const uint32_t cs = (su - R) % DU;
-            const float *cp = ring_u + cs * USLOT;
+      for (int j = 0; j < NY; ++j) qz[j][m] = pl[j * BW];
+      if (p < za || p >= zb) {  // plane used for the queue only
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty_u[slot]);
+      }
+      ++su;
+    }
+    // steady state: update zc = za + i after pushing plane zc + R (slot (i+2R) mod Q)
+    {
+      const int nseg = zb - za;
+      int i = 0;
+      while (true) {
+#pragma unroll
+        for (int ph = 0; ph < Q; ++ph) {
+          if (i >= nseg) goto segment_done;
+          {
+            const int zc = za + i;
+            const uint32_t slot = su % DU;
+            if (!mbar_wait(&full_u[slot], (su / DU) & 1)) goto timeout;
+            const float *pl = ring_u + slot * USLOT + (R + row0) * BW + HXB + lane;
+#pragma unroll
+            for (int j = 0; j < NY; ++j) qz[j][(ph + 2 * R) % Q] = pl[j * BW];
+            const uint32_t cs = (su - R) % DU;  // ring-U slot holding plane zc
+            const float *cp = ring_u + cs * USLOT + row0 * BW + HXB + lane;
             const float *xs = nullptr;
             uint32_t xslot = 0;
             if (AC) {
               xslot = sx % kTmaDX;
               if (!mbar_wait(&full_x[xslot], (sx / kTmaDX) & 1)) goto timeout;
-              xs = ring_x + xslot * 3 * XT;
+              xs = ring_x + xslot * 3 * XT + row0 * kTmaTX + lane;
             }
-            // y column of this thread: rows row0-R .. row0+NY-1+R of the tile
-            float ycol[kTmaNY + 2 * R];
+            float ycol[NY + 2 * R];  // this thread's column, rows row0-R .. row0+NY-1+R
 #pragma unroll
-            for (int i = 0; i < kTmaNY + 2 * R; ++i) ycol[i] = cp[(row0 + i) * BW + HXB + lane];
+            for (int r = 0; r < NY + 2 * R; ++r) ycol[r] = cp[r * BW];
 #pragma unroll
-            for (int j = 0; j < kTmaNY; ++j) {
-              const float *rowp = cp + (R + row0 + j) * BW + HXB + lane;
-              const float uc = qz[j][(ph + 1 + R) % Q];
-              float lap = wc * uc;
+            for (int j = 0; j < NY; ++j) {
+              const float *rowp = cp + (R + j) * BW;
+              const float uc = qz[j][(ph + R) % Q];
+              float lap = args.c.wc * uc;
 #pragma unroll
               for (int k = 1; k <= R; ++k) {
-                lap = fmaf(wx[k], rowp[k] + rowp[-k], lap);
-                lap = fmaf(wy[k], ycol[R + j + k] + ycol[R + j - k], lap);
-                lap = fmaf(wz[k], qz[j][(ph + 1 + R + k) % Q] + qz[j][(ph + 1 + R - k + Q) % Q], lap);
+                lap = fmaf(wk2[k], rowp[k] + rowp[-k], lap);
+                lap = fmaf(wk1[k], ycol[R + j + k] + ycol[R + j - k], lap);
+                lap = fmaf(wk0[k], qz[j][(ph + R + k) % Q] + qz[j][(ph + R - k + Q) % Q], lap);
               }
-              const int y = ybase + j;
-              if (xin && y < g.n1) {
-                float *o = optr + j * g.px;
-                if (AC) {
-                  const int t = (row0 + j) * kTmaTX + lane;
-                  const float up = xs[t], a = xs[XT + t], cc = xs[2 * XT + t];
-                  *o = fmaf(a, lap, fmaf(1.f + cc, uc, -cc * up));
-                } else if (x > 0 && x < g.n2 - 1 && y > 0 && y < g.n1 - 1 && zc > 0 &&
-                           zc < n0 - 1) {
-                  *o = uc + lap;
-                }
+              if (AC) {
+                const float up = xs[j * kTmaTX], a = xs[XT + j * kTmaTX],
+                            cc = xs[2 * XT + j * kTmaTX];
+                if (rows_ok & (1u << j)) optr[j * g.px] = fmaf(a, lap, fmaf(1.f + cc, uc, -cc * up));
+              } else {
+                if ((rows_ok & (1u << j)) && zc > 0 && zc < n0 - 1) optr[j * g.px] = uc + lap;
               }
             }
             optr += g.plane;
@@ -314,18 +330,16 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
             if (lane == 0) {
               if (AC) mbar_arrive(&empty_x[xslot]);
               mbar_arrive(&empty_u[cs]);
+              if (zc + R >= zb) mbar_arrive(&empty_u[slot]);  // trailing plane: queue only
             }
             if (AC) ++sx;
+            ++su;
+            ++i;
           }
-          if (p < za || p >= zb) {  // plane used for the queue only
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty_u[slot]);
-          }
-          ++su;
-          ++p;
         }
       }
     }
+  segment_done:;
   }
   return;
 timeout:
@@ -405,7 +419,7 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, float *const *le
   // TMA rules: 16-B aligned bases and strides, inner box extent a 16-B multiple,
   // x coordinates multiples of 4 floats (x0 + kHaloX - HXB with x0 % 32 == 0).
   if ((g.px * 4) % 16 || tma_hxb(g.R) % 4 || (tma_bw(g.R) * 4) % 16 || kHaloX % 4 ||
-      tma_bw(g.R) > 256 || tma_bh(g.R) > 256 || (kTmaTX * 4) % 16) {
+      tma_bw(g.R) > 256 || tma_bh(g.R) > 256 || tma_ty(g.R) > 256 || (kTmaTX * 4) % 16) {
     *why = "layout violates the TMA alignment rules";
     return cudaErrorNotSupported;
   }
@@ -417,15 +431,15 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, float *const *le
   const int R = g.R;
   for (int b = 0; b < 2; ++b) {
     if (!encode_map(enc, &pl.map_u[b], level[b], g, tma_bw(R), tma_bh(R)) ||
-        !encode_map(enc, &pl.map_t[b], level[b], g, kTmaTX, kTmaTY)) {
+        !encode_map(enc, &pl.map_t[b], level[b], g, kTmaTX, tma_ty(R))) {
       *why = "tensor map encoding failed";
       return cudaErrorInvalidValue;
     }
     pl.level[b] = level[b];
   }
   if (eq == kAcoustic) {
-    if (!encode_map(enc, &pl.map_a, A, g, kTmaTX, kTmaTY) ||
-        !encode_map(enc, &pl.map_c, C, g, kTmaTX, kTmaTY)) {
+    if (!encode_map(enc, &pl.map_a, A, g, kTmaTX, tma_ty(R)) ||
+        !encode_map(enc, &pl.map_c, C, g, kTmaTX, tma_ty(R))) {
       *why = "tensor map encoding failed";
       return cudaErrorInvalidValue;
     }
@@ -447,7 +461,7 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, float *const *le
   }
   pl.args.g = g;
   pl.args.tiles_x = (g.n2 + kTmaTX - 1) / kTmaTX;
-  const int tiles_y = (g.n1 + kTmaTY - 1) / kTmaTY;
+  const int tiles_y = (g.n1 + tma_ty(R) - 1) / tma_ty(R);
   pl.args.ntiles = pl.args.tiles_x * tiles_y;
   pl.args.W = (int64_t)pl.args.ntiles * g.n0;
   if (pl.grid > pl.args.W) pl.grid = (int)pl.args.W;
