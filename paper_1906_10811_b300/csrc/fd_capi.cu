@@ -109,6 +109,15 @@ struct fd_ctx {
   float *rec_w = nullptr, *rec = nullptr;
   int64_t rec_cap = 0;   // rows
   int64_t rec_rows = 0;  // rows recorded (valid)
+  // pipelined path: injection fused into the stencil epilogue, receivers
+  // sampled by a side-stream kernel that overlaps the next step's stencil
+  std::vector<int64_t> h_src_dense;  // source corner nodes (dense index)
+  int4 *sp_entries = nullptr;
+  int *sp_first = nullptr;
+  bool sp_dirty = true;
+  bool fused = false;                // this run uses the fused/overlapped sparse path
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_step[2] = {nullptr, nullptr}, ev_rec[2] = {nullptr, nullptr};
   // state
   bool model_set = false;
   int64_t step = 0;
@@ -277,11 +286,23 @@ bool corners(const fd_ctx *c, const float *pt, int64_t *pad_off, int64_t *dense_
 // ---------------------------------------------------------------------------
 // Launching one step.
 // ---------------------------------------------------------------------------
-fd_status launch_stencil(fd_ctx *c, const float *ucur, float *unext) {
+fd_status launch_stencil(fd_ctx *c, const float *ucur, float *unext, int j) {
   if (c->use_tma) {
-    cudaError_t e = launch_tma_step(c->tma, ucur == c->u[0] ? 0 : 1, unext, c->A, c->C,
-                                    c->coef, c->d_err, c->stream);
+    SparseArgs sp{};
+    if (c->fused && c->nsrc > 0) {
+      sp.entries = c->sp_entries;
+      sp.first = c->sp_first;
+      sp.src_scale = c->src_scale;
+      sp.wav = c->wav;
+      sp.step = c->d_step;
+      sp.j = j;
+      sp.nsrc = c->nsrc;
+      sp.nc = c->nc;
+    }
+    cudaError_t e = launch_tma_step(c->tma, ucur == c->u[0] ? 0 : 1, unext, c->coef, c->d_err, sp,
+                                    c->stream);
     if (e != cudaSuccess) return fail(c, FD_ECUDA, "TMA stencil launch: %s", cudaGetErrorString(e));
+    ++c->launches;
     return FD_OK;
   }
   dim3 block(32, 8);
@@ -292,7 +313,7 @@ fd_status launch_stencil(fd_ctx *c, const float *ucur, float *unext) {
 }
 
 fd_status launch_sparse(fd_ctx *c, float *unext, int j) {
-  if (c->eq != FD_ACOUSTIC || (c->nsrc == 0 && c->nrec == 0)) return FD_OK;
+  if (c->eq != FD_ACOUSTIC || (c->nsrc == 0 && c->nrec == 0) || c->fused) return FD_OK;
   const bool small = c->nsrc * c->nc <= 2048 && c->nrec * c->nc <= 2048;
   if (small) {
     if (c->nc == 8)
@@ -344,10 +365,29 @@ fd_status launch_interp_row0(fd_ctx *c) {
 
 // Steps j = 0..len-1 of a chunk starting with u^n in u[parity]; ends by
 // advancing the device step counter by len.
+// Receiver samples of step j (row n+1) from unext on the side stream; the
+// stencil that next overwrites unext (step j+2) waits for it.
+fd_status launch_receivers_side(fd_ctx *c, float *unext, int j) {
+  CU(cudaEventRecord(c->ev_step[j & 1], c->stream));
+  CU(cudaStreamWaitEvent(c->side, c->ev_step[j & 1], 0));
+  const int n = c->nrec * c->nc;
+  if (c->nc == 8)
+    k_interp<8><<<(n + 255) / 256, 256, 0, c->side>>>(unext, c->d_step, j, c->nrec, c->rec_off,
+                                                       c->rec_w, c->rec);
+  else
+    k_interp<4><<<(n + 255) / 256, 256, 0, c->side>>>(unext, c->d_step, j, c->nrec, c->rec_off,
+                                                       c->rec_w, c->rec);
+  CHECK_LAUNCH();
+  CU(cudaEventRecord(c->ev_rec[j & 1], c->side));
+  return FD_OK;
+}
+
 fd_status enqueue_chunk(fd_ctx *c, int parity, int len, bool timed) {
+  const bool overlap = c->fused && c->nrec > 0;
   for (int j = 0; j < len; ++j) {
     const int b = parity ^ (j & 1);
     float *ucur = c->u[b], *unext = c->u[b ^ 1];
+    if (overlap && j >= 2) CU(cudaStreamWaitEvent(c->stream, c->ev_rec[j & 1], 0));
     if (timed) {
       if (c->ev_used + 2 > c->ev.size()) {
         for (int k = 0; k < 64; ++k) {
@@ -358,14 +398,18 @@ fd_status enqueue_chunk(fd_ctx *c, int parity, int len, bool timed) {
       }
       CU(cudaEventRecord(c->ev[c->ev_used], c->stream));
     }
-    fd_status st = launch_stencil(c, ucur, unext);
+    fd_status st = launch_stencil(c, ucur, unext, j);
     if (st) return st;
     if (timed) {
       CU(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
       c->ev_used += 2;
     }
-    st = launch_sparse(c, unext, j);
+    st = overlap ? launch_receivers_side(c, unext, j) : launch_sparse(c, unext, j);
     if (st) return st;
+  }
+  if (overlap) {  // join the side stream before the step counter moves
+    CU(cudaStreamWaitEvent(c->stream, c->ev_rec[(len - 1) & 1], 0));
+    if (len >= 2) CU(cudaStreamWaitEvent(c->stream, c->ev_rec[len & 1], 0));
   }
   k_advance_step<<<1, 1, 0, c->stream>>>(c->d_step, len);
   CHECK_LAUNCH();
@@ -435,6 +479,59 @@ fd_status prepare_sources(fd_ctx *c) {
                                                            c->src_scale, n, c->dt);
   CHECK_LAUNCH();
   c->src_dirty = false;
+  return FD_OK;
+}
+
+// Pipelined path: the source corners as entries keyed by (tile, plane) of the
+// pipelined kernel; receivers need only the side stream and its events.
+fd_status prepare_fused(fd_ctx *c) {
+  c->fused = false;
+  if (!c->use_tma || c->eq != FD_ACOUSTIC || (c->nsrc == 0 && c->nrec == 0)) return FD_OK;
+  if (!c->side) {
+    CU(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+      CU(cudaEventCreateWithFlags(&c->ev_step[i], cudaEventDisableTiming));
+      CU(cudaEventCreateWithFlags(&c->ev_rec[i], cudaEventDisableTiming));
+    }
+  }
+  if (c->sp_dirty) {
+    const int ty = tma_ty(c->g.R), tiles_x = c->tma.args.tiles_x;
+    struct E { int64_t key; int idx, x, y, z; };
+    std::vector<E> es;
+    for (size_t i = 0; i < c->h_src_dense.size(); ++i) {
+      const int64_t d = c->h_src_dense[i];
+      const int x = (int)(d % c->g.n2);
+      const int y = (int)((d / c->g.n2) % c->g.n1);
+      const int z = (int)(d / ((int64_t)c->g.n1 * c->g.n2));
+      const int tile = (y / ty) * tiles_x + x / kTmaTX;
+      es.push_back({(int64_t)tile * c->g.n0 + z, (int)i, x, y, z});
+    }
+    std::sort(es.begin(), es.end(), [](const E &a, const E &b) {
+      return a.key != b.key ? a.key < b.key : a.idx < b.idx;
+    });
+    const int64_t nkeys = (int64_t)c->g.n0 * c->tma.args.ntiles;
+    std::vector<int> first(nkeys + 1, 0);
+    for (const E &e : es) ++first[e.key + 1];
+    for (int64_t k = 0; k < nkeys; ++k) first[k + 1] += first[k];
+    std::vector<int4> ent(es.size());
+    for (size_t i = 0; i < es.size(); ++i) ent[i] = make_int4(es[i].x, es[i].y, es[i].z, es[i].idx);
+    CU(cudaStreamSynchronize(c->stream));
+    dfree(c->sp_entries);
+    dfree(c->sp_first);
+    drop_graphs(c);
+    if (!es.empty()) {
+      fd_status st = dalloc(c, &c->sp_entries, ent.size());
+      if (!st) st = dalloc(c, &c->sp_first, first.size());
+      if (st) return st;
+      CU(cudaMemcpyAsync(c->sp_entries, ent.data(), ent.size() * sizeof(int4),
+                         cudaMemcpyHostToDevice, c->stream));
+      CU(cudaMemcpyAsync(c->sp_first, first.data(), first.size() * sizeof(int),
+                         cudaMemcpyHostToDevice, c->stream));
+      CU(cudaStreamSynchronize(c->stream));
+    }
+    c->sp_dirty = false;
+  }
+  c->fused = true;
   return FD_OK;
 }
 
@@ -702,6 +799,8 @@ fd_status fd_set_sources(fd_ctx *c, int nsrc, const float *coords, int nt, const
   drop_graphs(c);
   c->nsrc = 0;
   c->nt_wav = 0;
+  c->h_src_dense.clear();
+  c->sp_dirty = true;
   if (nsrc == 0) return FD_OK;
   if ((st = dalloc(c, &c->src_off, n)) || (st = dalloc(c, &c->src_dense, n)) ||
       (st = dalloc(c, &c->src_w, n)) || (st = dalloc(c, &c->src_scale, n)) ||
@@ -716,6 +815,8 @@ fd_status fd_set_sources(fd_ctx *c, int nsrc, const float *coords, int nt, const
   c->nsrc = nsrc;
   c->nt_wav = nt;
   c->src_dirty = true;
+  c->h_src_dense = dense;
+  c->sp_dirty = true;
   return FD_OK;
 }
 
@@ -773,6 +874,10 @@ fd_status fd_run(fd_ctx *c, int nt) {
   }
   st = prepare_sources(c);
   if (st) return st;
+  const bool was_fused = c->fused;
+  st = prepare_fused(c);
+  if (st) return st;
+  if (was_fused != c->fused) drop_graphs(c);
   k_set_step<<<1, 1, 0, c->stream>>>(c->d_step, c->step);
   CHECK_LAUNCH();
   if (c->nrec > 0 && c->rec_rows == 0 && c->step == 0) {
@@ -889,6 +994,15 @@ void fd_destroy(fd_ctx *c) {
   dfree(c->d_step); dfree(c->d_stats); dfree(c->d_err);
   dfree(c->wav); dfree(c->src_scale); dfree(c->src_off); dfree(c->src_dense); dfree(c->src_w);
   dfree(c->rec_off); dfree(c->rec_w); dfree(c->rec);
+  dfree(c->sp_entries); dfree(c->sp_first);
+  for (int i = 0; i < 2; ++i) {
+    if (c->ev_step[i]) cudaEventDestroy(c->ev_step[i]);
+    if (c->ev_rec[i]) cudaEventDestroy(c->ev_rec[i]);
+  }
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    cudaStreamDestroy(c->side);
+  }
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }

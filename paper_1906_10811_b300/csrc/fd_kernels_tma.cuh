@@ -29,6 +29,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <climits>
 #include <cudaTypedefs.h>
 
 #include "fd_common.cuh"
@@ -125,6 +126,19 @@ __device__ __forceinline__ void segment_at(int64_t q, int64_t q1, int ntiles, in
   zb = (int)min((int64_t)(z0 + len), za + (q1 - q));
 }
 
+// Point-source injection inside the stencil epilogue.  Entries (source
+// corners) are sorted by (tile, plane, source); first[tile * n0 + z] is the
+// first entry of that tile at plane z or later.
+struct SparseArgs {
+  const int4 *entries;     // {x, y, z, corner index}
+  const int *first;        // ntiles * n0 + 1 offsets (nullptr: no sources)
+  const float *src_scale;  // [nsrc*NC] w·dt²/m(node)
+  const float *wav;        // [nt][nsrc]
+  const int64_t *step;     // device step counter; this launch is step *step + j
+  int j;
+  int nsrc, nc;
+};
+
 struct TmaArgs {
   Geom g;
   Coef c;
@@ -134,6 +148,7 @@ struct TmaArgs {
   int64_t W;         // tile-planes
   float *out;        // u^{n+1} (padded layout; the buffer that held u^{n-1})
   int *err;          // err[0] = code, err[1] = block
+  SparseArgs sp;
 };
 
 template <int R, int EQ>
@@ -244,6 +259,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
   float qz[NY][Q];
   uint32_t su = 0, sx = 0;
   const int row0 = warp * NY;  // first tile row of this thread
+  const int64_t nstep = (AC && args.sp.first) ? *args.sp.step + args.sp.j : 0;
   const float *const wk0 = args.c.w[0];
   const float *const wk1 = args.c.w[1];
   const float *const wk2 = args.c.w[2];
@@ -263,6 +279,13 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
       rows_ok |= (in ? 1u : 0u) << j;
     }
     float *optr = args.out + gidx(g, za, ybase, x);
+    // sparse entries of this segment: [ecur, eend), next one in a register
+    int ecur = 0, eend = 0, nxt_z = INT_MAX;
+    if (AC && args.sp.first) {
+      ecur = args.sp.first[tile * n0 + za];
+      eend = args.sp.first[tile * n0 + zb];
+      if (ecur < eend) nxt_z = args.sp.entries[ecur].z;
+    }
 
     // warm-up: planes za-R .. za+R-1 fill queue slots 0 .. 2R-1
 #pragma unroll
@@ -306,6 +329,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
             float ycol[NY + 2 * R];  // this thread's column, rows row0-R .. row0+NY-1+R
 #pragma unroll
             for (int r = 0; r < NY + 2 * R; ++r) ycol[r] = cp[r * BW];
+            float val[NY];
 #pragma unroll
             for (int j = 0; j < NY; ++j) {
               const float *rowp = cp + (R + j) * BW;
@@ -320,9 +344,49 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
               if (AC) {
                 const float up = xs[j * kTmaTX], a = xs[XT + j * kTmaTX],
                             cc = xs[2 * XT + j * kTmaTX];
-                if (rows_ok & (1u << j)) optr[j * g.px] = fmaf(a, lap, fmaf(1.f + cc, uc, -cc * up));
+                val[j] = fmaf(a, lap, fmaf(1.f + cc, uc, -cc * up));
               } else {
-                if ((rows_ok & (1u << j)) && zc > 0 && zc < n0 - 1) optr[j * g.px] = uc + lap;
+                val[j] = uc + lap;
+              }
+            }
+            if (AC && nxt_z == zc) {
+              // source corners at this tile-plane (most planes have none): 32 per
+              // batch, one per lane, coefficients fetched in parallel; the owner
+              // lane adds them in entry order
+              while (true) {
+                const int e = ecur + lane;
+                const int4 en = e < eend ? args.sp.entries[e] : make_int4(0, 0, INT_MAX, 0);
+                const int cnt = __popc(__ballot_sync(0xffffffffu, en.z == zc));  // a prefix
+                const int jr = en.y - ybase;
+                const bool here = en.z == zc && jr >= 0 && jr < NY;
+                float add = 0.f;
+                if (here)
+                  add = args.sp.src_scale[en.w] *
+                        args.sp.wav[nstep * args.sp.nsrc + en.w / args.sp.nc];
+                unsigned mine = __ballot_sync(0xffffffffu, here);
+                while (mine) {
+                  const int b = __ffs(mine) - 1;
+                  mine &= mine - 1;
+                  const int ex = __shfl_sync(0xffffffffu, en.x, b);
+                  const int ej = __shfl_sync(0xffffffffu, jr, b);
+                  const float ad = __shfl_sync(0xffffffffu, add, b);
+                  if (ex == x) {
+#pragma unroll
+                    for (int j = 0; j < NY; ++j)
+                      if (j == ej) val[j] += ad;
+                  }
+                }
+                ecur += cnt;
+                if (cnt < 32) break;
+              }
+              nxt_z = ecur < eend ? args.sp.entries[ecur].z : INT_MAX;
+            }
+#pragma unroll
+            for (int j = 0; j < NY; ++j) {
+              if (AC) {
+                if (rows_ok & (1u << j)) optr[j * g.px] = val[j];
+              } else {
+                if ((rows_ok & (1u << j)) && zc > 0 && zc < n0 - 1) optr[j * g.px] = val[j];
               }
             }
             optr += g.plane;
@@ -473,12 +537,13 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, float *const *le
 }
 
 // One step with u^n in level[cur]; writes u^{n+1} into out (= level[cur ^ 1]).
-inline cudaError_t launch_tma_step(const TmaPlan &pl, int cur, float *out, const float *,
-                                   const float *, const Coef &c, int *err, cudaStream_t s) {
+inline cudaError_t launch_tma_step(const TmaPlan &pl, int cur, float *out, const Coef &c, int *err,
+                                   const SparseArgs &sp, cudaStream_t s) {
   TmaArgs a = pl.args;
   a.c = c;
   a.out = out;
   a.err = err;
+  a.sp = sp;
   pl.fn<<<pl.grid, kTmaThreads, pl.smem, s>>>(pl.map_u[cur], pl.map_t[cur ^ 1], pl.map_a,
                                               pl.map_c, a);
   return cudaGetLastError();
