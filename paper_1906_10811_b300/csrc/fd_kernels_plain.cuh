@@ -73,7 +73,8 @@ __global__ void k_gather(const float *__restrict__ padded, float *__restrict__ d
 }
 
 // ---------------------------------------------------------------------------
-// Acoustic coefficients, once per model (double arithmetic, rounded once):
+// Acoustic coefficients, once per model, in FP32 with correctly rounded
+// divisions (about one ulp from the exact values; C is exactly 1 where damp = 0):
 //   σ = damp·dt/2,  A = dt²/(m+σ),  C = (m−σ)/(m+σ).
 // stats[0]: min over m of its bit pattern (m > 0 → ordered like the value),
 // stats[1]: set when some m ≤ 0 or non-finite, or some damp < 0 or non-finite.
@@ -82,6 +83,7 @@ __global__ void k_coefficients(const float *__restrict__ m, const float *__restr
                                float *__restrict__ A, float *__restrict__ C, Geom g, double dt,
                                unsigned *stats) {
   const int64_t n = (int64_t)g.n0 * g.n1 * g.n2;
+  const float dt2 = (float)(dt * dt), half_dt = (float)(0.5 * dt);
   unsigned local_min = 0x7f800000u, bad = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -89,14 +91,14 @@ __global__ void k_coefficients(const float *__restrict__ m, const float *__restr
     const float df = damp ? damp[i] : 0.f;
     if (!(mf > 0.f) || !isfinite(mf) || !(df >= 0.f) || !isfinite(df)) bad = 1;
     local_min = min(local_min, __float_as_uint(mf));
-    const double md = mf, sig = (double)df * dt * 0.5;
+    const float sig = df * half_dt;
     const int x = (int)(i % g.n2);
     const int64_t r = i / g.n2;
     const int y = (int)(r % g.n1);
     const int z = (int)(r / g.n1);
     const int64_t p = gidx(g, z, y, x);
-    A[p] = (float)(dt * dt / (md + sig));
-    C[p] = (float)((md - sig) / (md + sig));
+    A[p] = __fdiv_rn(dt2, mf + sig);
+    C[p] = __fdiv_rn(mf - sig, mf + sig);
   }
   // warp-reduce before the atomics
   for (int o = 16; o > 0; o >>= 1) {
