@@ -44,9 +44,13 @@ WORKLOADS = {
     "roofline512": dict(n=512, so=8, nt=200, nrec=0, nbl=40),
 }
 
-# DRAM bytes per stencil launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
-# keyed by (kernel name, workload, space order); see profiles/.  None until captured.
-NCU_TRAFFIC = {}
+# DRAM bytes per stencil launch from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by (kernel name, workload, space order); the
+# captures are summarised in profiles/.  Absent (null) when not captured for the
+# kernel as it is now.
+NCU_TRAFFIC = {
+    ("stencil3d_tma_acoustic", "acoustic256", 8): 370.2e6,
+}
 
 
 def parse():
