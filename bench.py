@@ -148,6 +148,25 @@ def dist_setup(args):
     return world, rank, local
 
 
+def reduce_max(x):
+    """Maximum of a float over all ranks (identity without torch.distributed).
+
+    Works with NCCL (CUDA tensor) and gloo (CPU tensor) process groups."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Aggregate throughput: every rank processed units_per_rank in the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def cpu_threads():
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
@@ -261,11 +280,8 @@ def run_ours(args):
     kernel_name = s.kernel_name
     _, rec_dev = s.read(field=False)
     s.close()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * npts * nt * args.steps / (ms / 1e3) / 1e9
+    ms = reduce_max(ms)
+    value = whole_job_rate(npts * nt * args.steps, world, ms / 1e3) / 1e9
 
     peak, peak_kind = load_peak()
     avg_launch_s = st_ms / max(n_st, 1) / 1e3
@@ -311,11 +327,8 @@ def run_ours(args):
         barrier()
         te = time.perf_counter() - t0
         se.close()
-        if world > 1:
-            t = torch.tensor([te], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": round(world * npts * nt * args.steps / te / 1e9, 3), "unit": "GPts/s",
+        te = reduce_max(te)
+        e2e = {"value": round(whole_job_rate(npts * nt * args.steps, world, te) / 1e9, 3), "unit": "GPts/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     cpu = None
