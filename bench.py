@@ -48,9 +48,7 @@ WORKLOADS = {
 # dram__bytes_write.sum), keyed by (kernel name, workload, space order); the
 # captures are summarised in profiles/.  Absent (null) when not captured for the
 # kernel as it is now.
-NCU_TRAFFIC = {
-    ("stencil3d_tma_acoustic", "acoustic256", 8): 370.2e6,
-}
+NCU_TRAFFIC = {}
 
 
 def parse():

@@ -704,7 +704,9 @@ fd_status fd_create(fd_ctx **out, int ndim, const int64_t *shape, const double *
   c->use_tma = false;
   if (ndim == 3 && o.kernel != FD_KERNEL_PLAIN) {
     const char *why = nullptr;
-    e = plan_tma(c->tma, c->g, eq == FD_ACOUSTIC ? kAcoustic : kDiffusion, c->u, c->A, c->C, &why);
+    const bool iso = spacing[0] == spacing[1] && spacing[1] == spacing[2];
+    e = plan_tma(c->tma, c->g, eq == FD_ACOUSTIC ? kAcoustic : kDiffusion, iso, c->u, c->A, c->C,
+                 &why);
     if (e == cudaSuccess) {
       c->use_tma = true;
       c->kernel_name = c->tma.name;

@@ -39,9 +39,12 @@ __host__ __device__ inline int64_t gidx(const Geom &g, int z, int y, int x) {
 // on the host in double, rounded once to float: no divisions are left in the
 // kernels (thesis §5.1.5: hoisting the divisions out of the generated kernel
 // gave the GPU its 3-4x).
+// The kernels evaluate L u = Σ_axes Σ_k w[axis][k] ((u_{+k} + u_{-k}) - 2u): the
+// centre weight w_0 = -2 Σ_k w_k is implied, so the FP32 operator sums to zero
+// exactly and leaves constants alone however the weights round.
 struct Coef {
   float w[3][kMaxR + 1];  // w[axis][k] for k = 1..R; axis 0 unused in 2-D
-  float wc;               // Σ_axes w_0 / h_axis² (centre coefficient)
+  float wc;               // Σ_axes w_0 / h_axis² (kept for reference; not used by the kernels)
 };
 
 }  // namespace fdk

@@ -12,6 +12,7 @@ namespace fdk {
 
 // ---------------------------------------------------------------------------
 // One time step, plain.  Block (32, 8): x along lanes, y along warps; grid.z = z.
+// L u = Σ_axes Σ_k w_k/h² ((u_{+k} + u_{-k}) - 2u)  (the centre weight is implied)
 //   diffusion: un = u + (ν dt L) u on interior nodes (coefficients carry ν dt)
 //   acoustic : un = A·(L u) + (1 + C)·u − C·un   (un holds u^{n-1} on entry)
 // with A = dt²/(m+σ), C = (m−σ)/(m+σ): the leapfrog update solved for u^{n+1}.
@@ -26,13 +27,16 @@ k_stencil_plain(const float *__restrict__ u, float *un, const float *__restrict_
   if (x >= g.n2 || y >= g.n1) return;
   const int64_t p = gidx(g, z, y, x);
   const float uc = u[p];
-  float lap = c.wc * uc;
+  const float uc2 = uc + uc;
+  // difference form: the weights of every pair sum to zero exactly, so the
+  // FP32 operator annihilates constants (no drift from rounded weights)
+  float lap = 0.f;
 #pragma unroll
   for (int k = 1; k <= R; ++k) {
-    lap = fmaf(c.w[2][k], u[p + k] + u[p - k], lap);
-    lap = fmaf(c.w[1][k], u[p + (int64_t)k * g.px] + u[p - (int64_t)k * g.px], lap);
+    lap = fmaf(c.w[2][k], (u[p + k] + u[p - k]) - uc2, lap);
+    lap = fmaf(c.w[1][k], (u[p + (int64_t)k * g.px] + u[p - (int64_t)k * g.px]) - uc2, lap);
     if (THREE_D)
-      lap = fmaf(c.w[0][k], u[p + k * g.plane] + u[p - k * g.plane], lap);
+      lap = fmaf(c.w[0][k], (u[p + k * g.plane] + u[p - k * g.plane]) - uc2, lap);
   }
   if (EQ == kAcoustic) {
     const float a = A[p], cc = C[p];

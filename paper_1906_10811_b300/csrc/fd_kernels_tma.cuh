@@ -151,7 +151,10 @@ struct TmaArgs {
   SparseArgs sp;
 };
 
-template <int R, int EQ>
+// ISO: equal spacing on all axes, so one weight per k multiplies the sum of the
+// six neighbours minus 6u (still exact for constants); otherwise one difference
+// per axis.
+template <int R, int EQ, bool ISO>
 __global__ void __launch_bounds__(kTmaThreads, 2)
 k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
                 const __grid_constant__ CUtensorMap map_p,   // u^{n-1}, tile box
@@ -334,12 +337,25 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
             for (int j = 0; j < NY; ++j) {
               const float *rowp = cp + (R + j) * BW;
               const float uc = qz[j][(ph + R) % Q];
-              float lap = args.c.wc * uc;
+              // difference form: the weights multiplying each k sum to zero exactly
+              float lap = 0.f;
+              if (ISO) {
+                const float uc6 = 6.f * uc;
 #pragma unroll
-              for (int k = 1; k <= R; ++k) {
-                lap = fmaf(wk2[k], rowp[k] + rowp[-k], lap);
-                lap = fmaf(wk1[k], ycol[R + j + k] + ycol[R + j - k], lap);
-                lap = fmaf(wk0[k], qz[j][(ph + R + k) % Q] + qz[j][(ph + R - k + Q) % Q], lap);
+                for (int k = 1; k <= R; ++k) {
+                  const float s6 = ((rowp[k] + rowp[-k]) + (ycol[R + j + k] + ycol[R + j - k])) +
+                                   (qz[j][(ph + R + k) % Q] + qz[j][(ph + R - k + Q) % Q]);
+                  lap = fmaf(wk2[k], s6 - uc6, lap);
+                }
+              } else {
+                const float uc2 = uc + uc;
+#pragma unroll
+                for (int k = 1; k <= R; ++k) {
+                  lap = fmaf(wk2[k], (rowp[k] + rowp[-k]) - uc2, lap);
+                  lap = fmaf(wk1[k], (ycol[R + j + k] + ycol[R + j - k]) - uc2, lap);
+                  lap = fmaf(wk0[k], (qz[j][(ph + R + k) % Q] + qz[j][(ph + R - k + Q) % Q]) - uc2,
+                             lap);
+                }
               }
               if (AC) {
                 const float up = xs[j * kTmaTX], a = xs[XT + j * kTmaTX],
@@ -453,16 +469,16 @@ inline bool encode_map(EncodeFn enc, CUtensorMap *m, float *base, const Geom &g,
              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int R, int EQ>
+template <int R, int EQ, bool ISO>
 inline cudaError_t tma_configure(TmaPlan &pl) {
-  pl.fn = k_stencil3d_tma<R, EQ>;
+  pl.fn = k_stencil3d_tma<R, EQ, ISO>;
   pl.smem = tma_smem_bytes(R, EQ == kAcoustic);
-  cudaError_t e = cudaFuncSetAttribute(k_stencil3d_tma<R, EQ>,
+  cudaError_t e = cudaFuncSetAttribute(k_stencil3d_tma<R, EQ, ISO>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, pl.smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil3d_tma<R, EQ>, kTmaThreads,
-                                                    pl.smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil3d_tma<R, EQ, ISO>,
+                                                    kTmaThreads, pl.smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   int dev = 0, sms = 0;
@@ -473,8 +489,8 @@ inline cudaError_t tma_configure(TmaPlan &pl) {
 }
 
 // Build the plan: tensor maps for both levels and the coefficient fields.
-inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, float *const *level, float *A,
-                            float *C, const char **why) {
+inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float *const *level,
+                            float *A, float *C, const char **why) {
   *why = nullptr;
   if (g.R0 == 0 || g.R < 1 || g.R > kMaxR) {
     *why = "3-D grids only";
@@ -513,9 +529,12 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, float *const *le
   }
   cudaError_t e = cudaErrorNotSupported;
   const bool ac = eq == kAcoustic;
-#define TMA_CASE(RR)                                                                  \
-  case RR:                                                                            \
-    e = ac ? tma_configure<RR, kAcoustic>(pl) : tma_configure<RR, kDiffusion>(pl);    \
+#define TMA_CASE(RR)                                                                   \
+  case RR:                                                                             \
+    e = ac ? (iso ? tma_configure<RR, kAcoustic, true>(pl)                             \
+                  : tma_configure<RR, kAcoustic, false>(pl))                           \
+           : (iso ? tma_configure<RR, kDiffusion, true>(pl)                            \
+                  : tma_configure<RR, kDiffusion, false>(pl));                         \
     break;
   switch (R) { TMA_CASE(1) TMA_CASE(2) TMA_CASE(3) TMA_CASE(4) TMA_CASE(5) TMA_CASE(6) TMA_CASE(7) TMA_CASE(8) }
 #undef TMA_CASE
