@@ -166,6 +166,46 @@ int64_t fd_kernel_launches(const fd_ctx *ctx);
 /* Release everything.  NULL is a no-op. */
 void fd_destroy(fd_ctx *ctx);
 
+/*
+ * Batches: many FD_ACOUSTIC shots of one space order stepped together, as a
+ * serving loop that admits and retires shots between runs needs (continuous
+ * batching; the spec serving pattern built on the §6.2.1 operator).
+ * A batch tick advances every member one step with one persistent pipelined
+ * kernel for all 3-D members (their tile-planes shared out over the CTAs), one
+ * kernel for all 2-D members, one source-injection kernel for the 2-D members
+ * (3-D injection is fused) and one receiver kernel for all.  Members stay
+ * ordinary contexts: after fd_batch_run, fd_read / fd_run work on them as
+ * usual, and a member's results are bitwise those of running it alone.
+ *
+ * fd_batch_create: cuda_stream = cudaStream_t for the batch's work (NULL: own
+ *   stream).  Members on other streams are ordered before and after each run
+ *   with events.
+ * fd_batch_add: ctx must be FD_ACOUSTIC, of the batch's space order, with a
+ *   model set, on the batch's device; 3-D members need the pipelined kernel
+ *   and must agree on whether their spacing is isotropic.  The batch borrows
+ *   the context: remove it before fd_destroy.
+ * fd_batch_run: nticks ≥ 0 steps of every member (FD_EINVAL if a member would
+ *   pass its wavelet); asynchronous on the batch stream.
+ * fd_batch_remove: synchronises the batch stream and drops the member.
+ */
+typedef struct fd_batch fd_batch;
+fd_status fd_batch_create(fd_batch **out, int space_order, void *cuda_stream);
+fd_status fd_batch_add(fd_batch *b, fd_ctx *ctx);
+fd_status fd_batch_remove(fd_batch *b, fd_ctx *ctx);
+fd_status fd_batch_run(fd_batch *b, int nticks);
+int fd_batch_size(const fd_batch *b);
+int64_t fd_batch_kernel_launches(const fd_batch *b);
+const char *fd_batch_last_error(const fd_batch *b);
+void fd_batch_destroy(fd_batch *b);
+
+/*
+ * Device bytes fd_create + fd_set_* + fd_run allocate for an FD_ACOUSTIC shot
+ * (fields with halo, coefficients, m, staging, traces for nt steps, sparse
+ * tables) -- the admission measure of a serving loop.  -1 for bad arguments.
+ */
+int64_t fd_footprint_bytes(int ndim, const int64_t *shape, int space_order, int nrec, int nt,
+                           int nsrc);
+
 /* Text of the last error on ctx (or of the last failed fd_create when ctx is NULL). */
 const char *fd_last_error(const fd_ctx *ctx);
 

@@ -63,6 +63,16 @@ SIGNATURES = {
     "fd_weights": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "fd_stability_symbol": (ctypes.c_double, [ctypes.c_int]),
     "fd_version": (ctypes.c_char_p, []),
+    "fd_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _vp]),
+    "fd_batch_add": (ctypes.c_int, [_vp, _vp]),
+    "fd_batch_remove": (ctypes.c_int, [_vp, _vp]),
+    "fd_batch_run": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "fd_batch_size": (ctypes.c_int, [_vp]),
+    "fd_batch_kernel_launches": (_i64, [_vp]),
+    "fd_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "fd_batch_destroy": (None, [_vp]),
+    "fd_footprint_bytes": (_i64, [ctypes.c_int, ctypes.POINTER(_i64), ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_int]),
     "fd_acoustic_run_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_i64),
                                                ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                                ctypes.c_double, _vp, _vp, _vp, _vp, ctypes.c_int,
@@ -211,6 +221,50 @@ def fd_kernel_name(ctx):
 
 def fd_kernel_launches(ctx):
     return int(load().fd_kernel_launches(ctx))
+
+
+def _bcheck(batch, st):
+    if st != FD_OK:
+        msg = load().fd_batch_last_error(batch) if batch else load().fd_last_error(None)
+        raise FdError(st, msg.decode() if msg else "")
+
+
+def fd_batch_create(space_order, cuda_stream=None):
+    out = _vp()
+    st = load().fd_batch_create(ctypes.byref(out), int(space_order), cuda_stream)
+    _bcheck(None, st)
+    return out.value
+
+
+def fd_batch_add(batch, ctx):
+    _bcheck(batch, load().fd_batch_add(batch, ctx))
+
+
+def fd_batch_remove(batch, ctx):
+    _bcheck(batch, load().fd_batch_remove(batch, ctx))
+
+
+def fd_batch_run(batch, nticks):
+    _bcheck(batch, load().fd_batch_run(batch, int(nticks)))
+
+
+def fd_batch_size(batch):
+    return int(load().fd_batch_size(batch))
+
+
+def fd_batch_kernel_launches(batch):
+    return int(load().fd_batch_kernel_launches(batch))
+
+
+def fd_batch_destroy(batch):
+    if batch:
+        load().fd_batch_destroy(batch)
+
+
+def fd_footprint_bytes(shape, space_order, nrec, nt, nsrc=1):
+    nd = len(shape)
+    shp = (_i64 * nd)(*[int(x) for x in shape])
+    return int(load().fd_footprint_bytes(nd, shp, int(space_order), int(nrec), int(nt), int(nsrc)))
 
 
 def fd_destroy(ctx):

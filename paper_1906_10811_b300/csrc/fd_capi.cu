@@ -67,6 +67,7 @@ struct GraphEntry {
 };
 
 using StencilFn = void (*)(const float *, float *, const float *, const float *, Geom, Coef);
+using StencilFn2D = void (*)(const MemberDesc *, int, const int64_t *);
 
 }  // namespace
 
@@ -1012,6 +1013,356 @@ void fd_destroy(fd_ctx *c) {
 const char *fd_last_error(const fd_ctx *c) {
   if (!c) return g_create_error.c_str();
   return c->err.c_str();
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Batches: many acoustic shots stepped together (continuous batching).
+//
+// Members stay ordinary contexts (their own fields, traces and step counters);
+// a batch tick launches one persistent pipelined kernel for all 3-D members
+// (k_stencil3d_tma<..., MULTI>: the CTAs share out the members' tile-planes),
+// one kernel for all 2-D members, one injection kernel for the 2-D members'
+// sources (3-D injection is fused), and one receiver kernel for everyone.
+// ===========================================================================
+struct fd_batch {
+  int so = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<fd_ctx *> members;
+  ShotDesc *d_shots = nullptr;   // 3-D members
+  int64_t *d_wpre = nullptr;
+  MemberDesc *d_mem = nullptr;   // every member (2-D stencil, injection, receivers)
+  int2 *d_src = nullptr, *d_rec = nullptr;
+  int64_t *d_tick = nullptr;
+  size_t cap_shots = 0, cap_mem = 0, cap_src = 0, cap_rec = 0;
+  ShotDesc *h_shots = nullptr;   // pinned staging
+  MemberDesc *h_mem = nullptr;
+  std::vector<int2> h_src, h_rec;
+  std::vector<int64_t> h_wpre;
+  cudaEvent_t ev = nullptr;
+  int64_t launches = 0;
+  bool failed = false;
+  std::string err;
+};
+
+namespace {
+
+fd_status bfail(fd_batch *b, fd_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  b->err = buf;
+  if (st == FD_ECUDA) b->failed = true;
+  return st;
+}
+
+#define BCU(call)                                                                      \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return bfail(b, e_ == cudaErrorMemoryAllocation ? FD_ENOMEM : FD_ECUDA,          \
+                   "%s failed: %s", #call, cudaGetErrorString(e_));                    \
+  } while (0)
+
+template <typename T>
+fd_status bgrow(fd_batch *b, T **dev, T **host, size_t *cap, size_t need) {
+  if (need <= *cap) return FD_OK;
+  const size_t n = std::max<size_t>(need, 2 * *cap + 8);
+  if (*dev) cudaFree(*dev);
+  *dev = nullptr;
+  BCU(cudaMalloc((void **)dev, n * sizeof(T)));
+  if (host) {
+    if (*host) cudaFreeHost(*host);
+    *host = nullptr;
+    BCU(cudaMallocHost((void **)host, n * sizeof(T)));
+  }
+  *cap = n;
+  return FD_OK;
+}
+
+StencilFn2D batch2d_fn(int R) {
+  switch (R) {
+    case 1: return k_stencil2d_batch<1>;
+    case 2: return k_stencil2d_batch<2>;
+    case 3: return k_stencil2d_batch<3>;
+    case 4: return k_stencil2d_batch<4>;
+    case 5: return k_stencil2d_batch<5>;
+    case 6: return k_stencil2d_batch<6>;
+    case 7: return k_stencil2d_batch<7>;
+    default: return k_stencil2d_batch<8>;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+fd_status fd_batch_create(fd_batch **out, int space_order, void *cuda_stream) {
+  if (!out) return FD_EINVAL;
+  *out = nullptr;
+  if (space_order < 2 || space_order > 2 * kMaxR || (space_order & 1))
+    return fail(nullptr, FD_EINVAL, "space_order must be even in [2,16] (got %d)", space_order);
+  fd_batch *b = new (std::nothrow) fd_batch();
+  if (!b) return fail(nullptr, FD_ENOMEM, "host allocation failed");
+  b->so = space_order;
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess) {
+    if (cuda_stream) {
+      b->stream = (cudaStream_t)cuda_stream;
+    } else {
+      e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+      b->own_stream = e == cudaSuccess;
+    }
+  }
+  if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_tick, sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    fail(nullptr, FD_ECUDA, "batch creation: %s", cudaGetErrorString(e));
+    fd_batch_destroy(b);
+    return FD_ECUDA;
+  }
+  *out = b;
+  return FD_OK;
+}
+
+fd_status fd_batch_add(fd_batch *b, fd_ctx *c) {
+  if (!b || !c) return FD_EINVAL;
+  if (b->failed) return FD_ECUDA;
+  if (c->failed) return bfail(b, FD_ECUDA, "member context has failed");
+  if (c->eq != FD_ACOUSTIC || c->so != b->so)
+    return bfail(b, FD_EINVAL, "members must be FD_ACOUSTIC contexts of space order %d", b->so);
+  if (!c->model_set) return bfail(b, FD_ESTATE, "member has no model (fd_set_model)");
+  if (c->ndim == 3 && !c->use_tma)
+    return bfail(b, FD_EUNSUPPORTED, "3-D members need the pipelined kernel (FD_KERNEL_AUTO/TMA)");
+  if (c->device != b->device) return bfail(b, FD_EINVAL, "member lives on another device");
+  if (std::find(b->members.begin(), b->members.end(), c) != b->members.end())
+    return bfail(b, FD_EINVAL, "already a member");
+  if (c->ndim == 3 && !b->members.empty()) {
+    for (fd_ctx *o : b->members)
+      if (o->ndim == 3 && o->tma.fn_multi != c->tma.fn_multi)
+        return bfail(b, FD_EUNSUPPORTED, "3-D members must share spacing isotropy");
+  }
+  b->members.push_back(c);
+  return FD_OK;
+}
+
+fd_status fd_batch_remove(fd_batch *b, fd_ctx *c) {
+  if (!b || !c) return FD_EINVAL;
+  auto it = std::find(b->members.begin(), b->members.end(), c);
+  if (it == b->members.end()) return bfail(b, FD_EINVAL, "not a member");
+  cudaStreamSynchronize(b->stream);
+  b->members.erase(it);
+  return FD_OK;
+}
+
+int fd_batch_size(const fd_batch *b) { return b ? (int)b->members.size() : -1; }
+
+int64_t fd_batch_kernel_launches(const fd_batch *b) { return b ? b->launches : -1; }
+
+const char *fd_batch_last_error(const fd_batch *b) { return b ? b->err.c_str() : ""; }
+
+fd_status fd_batch_run(fd_batch *b, int nticks) {
+  if (!b) return FD_EINVAL;
+  if (b->failed) return FD_ECUDA;
+  if (nticks < 0) return bfail(b, FD_EINVAL, "nticks must be >= 0");
+  if (nticks == 0 || b->members.empty()) return FD_OK;
+  BCU(cudaSetDevice(b->device));
+  const int R = b->so / 2;
+  // members: checks, per-member preparation, order after their own streams
+  for (fd_ctx *c : b->members) {
+    if (c->failed) return bfail(b, FD_ECUDA, "member context has failed");
+    if (c->nsrc > 0 && c->step + nticks > c->nt_wav)
+      return bfail(b, FD_EINVAL, "a member would pass its wavelet length");
+    fd_status st = FD_OK;
+    if (c->nrec > 0) st = ensure_rec_capacity(c, c->step + nticks + 1);
+    if (!st) st = prepare_sources(c);
+    if (!st && c->ndim == 3) st = prepare_fused(c);
+    if (st) return bfail(b, st, "member preparation: %s", c->err.c_str());
+    if (c->nrec > 0 && c->rec_rows == 0 && c->step == 0) {  // trace row 0
+      k_set_step<<<1, 1, 0, c->stream>>>(c->d_step, 0);
+      st = launch_interp_row0(c);
+      if (st) return bfail(b, st, "member trace row 0: %s", c->err.c_str());
+      c->rec_rows = 1;
+    }
+    if (c->stream != b->stream) {
+      BCU(cudaEventRecord(b->ev, c->stream));
+      BCU(cudaStreamWaitEvent(b->stream, b->ev, 0));
+    }
+  }
+  // descriptor tables (host staging is pinned; wait for the previous run's copies)
+  BCU(cudaStreamSynchronize(b->stream));
+  std::vector<fd_ctx *> m3;
+  for (fd_ctx *c : b->members)
+    if (c->ndim == 3) m3.push_back(c);
+  const size_t nm = b->members.size(), n3 = m3.size();
+  fd_status st = bgrow(b, &b->d_mem, &b->h_mem, &b->cap_mem, nm);
+  if (!st) st = bgrow(b, &b->d_shots, &b->h_shots, &b->cap_shots, std::max<size_t>(n3, 1));
+  if (st) return st;
+  if (b->d_wpre) cudaFree(b->d_wpre);
+  b->d_wpre = nullptr;
+  BCU(cudaMalloc((void **)&b->d_wpre, (n3 + 1) * sizeof(int64_t)));
+  b->h_src.clear();
+  b->h_rec.clear();
+  int64_t blk = 0;
+  for (size_t i = 0; i < nm; ++i) {
+    fd_ctx *c = b->members[i];
+    MemberDesc &d = b->h_mem[i];
+    std::memset(&d, 0, sizeof d);
+    d.level[0] = c->u[0];
+    d.level[1] = c->u[1];
+    d.A = c->A;
+    d.C = c->C;
+    d.g = c->g;
+    d.c = c->coef;
+    d.cur0 = c->cur;
+    d.step0 = c->step;
+    d.src_off = c->src_off;
+    d.src_scale = c->src_scale;
+    d.wav = c->wav;
+    d.nsrc = c->nsrc;
+    d.nc = c->nc;
+    d.rec_off = c->rec_off;
+    d.rec_w = c->rec_w;
+    d.rec = c->rec;
+    d.nrec = c->nrec;
+    d.blk0 = blk;  // non-decreasing over members; 3-D members own no 2-D blocks
+    if (c->ndim == 2) {
+      d.blocks_x = (c->g.n2 + 31) / 32;
+      blk += (int64_t)d.blocks_x * ((c->g.n1 + 7) / 8);
+      for (int k = 0; k < c->nsrc * c->nc; ++k) b->h_src.push_back(make_int2((int)i, k));
+    }
+    for (int k = 0; k < c->nrec; ++k) b->h_rec.push_back(make_int2((int)i, k));
+  }
+  b->h_wpre.assign(n3 + 1, 0);
+  int64_t wtot = 0;
+  for (size_t i = 0; i < n3; ++i) wtot += m3[i]->tma.args.W;
+  const TmaPlan &plan0 = n3 ? m3[0]->tma : TmaPlan();
+  const int grid3 = n3 ? (int)std::min<int64_t>(plan0.grid_multi, std::max<int64_t>(wtot, 1)) : 0;
+  const int64_t share = n3 ? (wtot + grid3 - 1) / grid3 : 1;
+  for (size_t i = 0; i < n3; ++i) {
+    fd_ctx *c = m3[i];
+    ShotDesc &d = b->h_shots[i];
+    std::memset(&d, 0, sizeof d);
+    d.map_u[0] = c->tma.map_u[0];
+    d.map_u[1] = c->tma.map_u[1];
+    d.map_t[0] = c->tma.map_t[0];
+    d.map_t[1] = c->tma.map_t[1];
+    d.map_a = c->tma.map_a;
+    d.map_c = c->tma.map_c;
+    d.g = c->g;
+    d.c = c->coef;
+    d.level[0] = c->u[0];
+    d.level[1] = c->u[1];
+    d.tiles_x = c->tma.args.tiles_x;
+    d.ntiles = c->tma.args.ntiles;
+    d.zblock = (int)std::min<int64_t>(c->g.n0, std::max<int64_t>(1, share));
+    d.cur0 = c->cur;
+    d.step0 = c->step;
+    if (c->nsrc > 0) {
+      d.entries = c->sp_entries;
+      d.first = c->sp_first;
+      d.src_scale = c->src_scale;
+      d.wav = c->wav;
+      d.nsrc = c->nsrc;
+      d.nc = c->nc;
+    }
+    b->h_wpre[i + 1] = b->h_wpre[i] + c->tma.args.W;
+  }
+  if (!b->h_src.empty()) st = bgrow<int2>(b, &b->d_src, nullptr, &b->cap_src, b->h_src.size());
+  if (!st && !b->h_rec.empty()) st = bgrow<int2>(b, &b->d_rec, nullptr, &b->cap_rec, b->h_rec.size());
+  if (st) return st;
+  BCU(cudaMemcpyAsync(b->d_mem, b->h_mem, nm * sizeof(MemberDesc), cudaMemcpyHostToDevice, b->stream));
+  if (n3) {
+    BCU(cudaMemcpyAsync(b->d_shots, b->h_shots, n3 * sizeof(ShotDesc), cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaMemcpyAsync(b->d_wpre, b->h_wpre.data(), (n3 + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, b->stream));
+  }
+  if (!b->h_src.empty())
+    BCU(cudaMemcpyAsync(b->d_src, b->h_src.data(), b->h_src.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+  if (!b->h_rec.empty())
+    BCU(cudaMemcpyAsync(b->d_rec, b->h_rec.data(), b->h_rec.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+  k_set_step<<<1, 1, 0, b->stream>>>(b->d_tick, 0);
+  BCU(cudaGetLastError());
+  ++b->launches;
+  // error word of the pipelined kernel: the first 3-D member's
+  BatchArgs ba{b->d_shots, b->d_wpre, (int)n3, b->d_tick, n3 ? m3[0]->d_err : nullptr};
+  const int nsrc_e = (int)b->h_src.size(), nrec_e = (int)b->h_rec.size();
+  const StencilFn2D f2 = batch2d_fn(R);
+  for (int t = 0; t < nticks; ++t) {
+    if (n3) {
+      plan0.fn_multi<<<grid3, kTmaThreads, plan0.smem, b->stream>>>(
+          plan0.map_u[0], plan0.map_t[0], plan0.map_a, plan0.map_c, TmaArgs{}, ba);
+      BCU(cudaGetLastError());
+      ++b->launches;
+    }
+    if (blk > 0) {
+      f2<<<(unsigned)blk, dim3(32, 8), 0, b->stream>>>(b->d_mem, (int)nm, b->d_tick);
+      BCU(cudaGetLastError());
+      ++b->launches;
+    }
+    if (nsrc_e) {
+      k_inject_batch<<<(nsrc_e + 255) / 256, 256, 0, b->stream>>>(b->d_src, nsrc_e, b->d_mem, b->d_tick);
+      BCU(cudaGetLastError());
+      ++b->launches;
+    }
+    if (nrec_e) {
+      k_interp_batch<<<(nrec_e * 8 + 255) / 256, 256, 0, b->stream>>>(b->d_rec, nrec_e, b->d_mem, b->d_tick);
+      BCU(cudaGetLastError());
+      ++b->launches;
+    }
+    k_advance_step<<<1, 1, 0, b->stream>>>(b->d_tick, 1);
+    BCU(cudaGetLastError());
+    ++b->launches;
+  }
+  BCU(cudaEventRecord(b->ev, b->stream));
+  for (fd_ctx *c : b->members) {
+    c->step += nticks;
+    c->cur ^= (nticks & 1);
+    if (c->nrec > 0) c->rec_rows = c->step + 1;
+    if (c->stream != b->stream) BCU(cudaStreamWaitEvent(c->stream, b->ev, 0));
+  }
+  return FD_OK;
+}
+
+void fd_batch_destroy(fd_batch *b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->d_shots) cudaFree(b->d_shots);
+  if (b->d_wpre) cudaFree(b->d_wpre);
+  if (b->d_mem) cudaFree(b->d_mem);
+  if (b->d_src) cudaFree(b->d_src);
+  if (b->d_rec) cudaFree(b->d_rec);
+  if (b->d_tick) cudaFree(b->d_tick);
+  if (b->h_shots) cudaFreeHost(b->h_shots);
+  if (b->h_mem) cudaFreeHost(b->h_mem);
+  if (b->ev) cudaEventDestroy(b->ev);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+int64_t fd_footprint_bytes(int ndim, const int64_t *shape, int space_order, int nrec, int nt,
+                           int nsrc) {
+  if ((ndim != 2 && ndim != 3) || !shape || space_order < 2 || space_order > 2 * kMaxR ||
+      (space_order & 1) || nrec < 0 || nt < 0 || nsrc < 0)
+    return -1;
+  const int R = space_order / 2;
+  int64_t n0 = 1, n1, n2, r0 = 0;
+  if (ndim == 3) {
+    n0 = shape[0]; n1 = shape[1]; n2 = shape[2]; r0 = R;
+  } else {
+    n1 = shape[0]; n2 = shape[1];
+  }
+  const int64_t px = kHaloX + (n2 + R + 31) / 32 * 32;
+  const int64_t field = px * (n1 + 2 * R) * (n0 + 2 * r0) * 4;
+  const int64_t npts = n0 * n1 * n2;
+  const int nc = 1 << ndim;
+  const int64_t rows = std::max<int64_t>(nt + 1, 1024);
+  return 4 * field + 2 * npts * 4 + rows * nrec * 4 + (int64_t)nrec * nc * 12 +
+         (int64_t)nsrc * nc * 24 + (int64_t)nt * nsrc * 4 + (1 << 16);
 }
 
 }  // extern "C"

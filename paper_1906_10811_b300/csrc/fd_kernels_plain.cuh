@@ -18,13 +18,10 @@ namespace fdk {
 // with A = dt²/(m+σ), C = (m−σ)/(m+σ): the leapfrog update solved for u^{n+1}.
 // ---------------------------------------------------------------------------
 template <int R, int EQ, bool THREE_D>
-__global__ void __launch_bounds__(256)
-k_stencil_plain(const float *__restrict__ u, float *un, const float *__restrict__ A,
-                const float *__restrict__ C, Geom g, Coef c) {
-  const int x = blockIdx.x * 32 + threadIdx.x;
-  const int y = blockIdx.y * 8 + threadIdx.y;
-  const int z = blockIdx.z;
-  if (x >= g.n2 || y >= g.n1) return;
+__device__ __forceinline__ void plain_point(const float *__restrict__ u, float *un,
+                                            const float *__restrict__ A,
+                                            const float *__restrict__ C, const Geom &g,
+                                            const Coef &c, int z, int y, int x) {
   const int64_t p = gidx(g, z, y, x);
   const float uc = u[p];
   const float uc2 = uc + uc;
@@ -47,6 +44,17 @@ k_stencil_plain(const float *__restrict__ u, float *un, const float *__restrict_
                           (!THREE_D || (z > 0 && z < g.n0 - 1));
     if (interior) un[p] = uc + lap;
   }
+}
+
+template <int R, int EQ, bool THREE_D>
+__global__ void __launch_bounds__(256)
+k_stencil_plain(const float *__restrict__ u, float *un, const float *__restrict__ A,
+                const float *__restrict__ C, Geom g, Coef c) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * 8 + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= g.n2 || y >= g.n1) return;
+  plain_point<R, EQ, THREE_D>(u, un, A, C, g, c, z, y, x);
 }
 
 // ---------------------------------------------------------------------------
@@ -180,6 +188,85 @@ __global__ void k_interp(const float *un, const int64_t *__restrict__ step, int 
   const int64_t n = *step + j;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   interp_group_store<NC>(un, roff, rw, rec, n + 1, nrec, t / NC, t % NC);
+}
+
+}  // namespace fdk
+
+namespace fdk {
+
+// ---------------------------------------------------------------------------
+// Batched shots.  At batch tick t a member is at global step step0 + t with
+// u^n in level[cur0 ^ (t & 1)]; it writes u^{n+1} into the other level.
+// ---------------------------------------------------------------------------
+struct MemberDesc {
+  float *level[2];
+  const float *A, *C;
+  Geom g;
+  Coef c;
+  int cur0;
+  int64_t step0;
+  int64_t blk0;      // first block of this member in the batched 2-D grid
+  int blocks_x;      // blocks along x (2-D members)
+  const int64_t *src_off;
+  const float *src_scale, *wav;
+  int nsrc, nc;
+  const int64_t *rec_off;
+  const float *rec_w;
+  float *rec;
+  int nrec;
+};
+
+// One step of every 2-D member: blocks of 32 × 8 points, block -> member by
+// binary search over blk0.
+template <int R>
+__global__ void __launch_bounds__(256)
+k_stencil2d_batch(const MemberDesc *__restrict__ d, int n, const int64_t *tick) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (d[mid].blk0 <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const MemberDesc &m = d[lo];
+  const int64_t b = blockIdx.x - m.blk0;
+  const int x = (int)(b % m.blocks_x) * 32 + threadIdx.x;
+  const int y = (int)(b / m.blocks_x) * 8 + threadIdx.y;
+  if (x >= m.g.n2 || y >= m.g.n1) return;
+  const int par = m.cur0 ^ (int)(*tick & 1);
+  plain_point<R, kAcoustic, false>(m.level[par], m.level[par ^ 1], m.A, m.C, m.g, m.c, 0, y, x);
+}
+
+// Source corners of the 2-D members: entry = (member, corner).
+__global__ void k_inject_batch(const int2 *__restrict__ e, int n, const MemberDesc *__restrict__ d,
+                               const int64_t *tick) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const MemberDesc &m = d[e[i].x];
+  const int k = e[i].y;
+  const int64_t t = *tick;
+  float *un = m.level[m.cur0 ^ (int)(t & 1) ^ 1];
+  atomicAdd(un + m.src_off[k], m.src_scale[k] * m.wav[(m.step0 + t) * m.nsrc + k / m.nc]);
+}
+
+// Receivers of every member: entry = (member, receiver); 8 lanes per receiver
+// (lanes beyond the member's 2^D corners add zero), shuffle reduction.
+__global__ void k_interp_batch(const int2 *__restrict__ e, int n, const MemberDesc *__restrict__ d,
+                               const int64_t *tick) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = t >> 3, c = t & 7;
+  float v = 0.f;
+  const MemberDesc *m = nullptr;
+  int k = 0;
+  if (r < n) {
+    m = &d[e[r].x];
+    k = e[r].y;
+    if (c < m->nc) {
+      const float *un = m->level[m->cur0 ^ (int)(*tick & 1) ^ 1];
+      v = m->rec_w[k * m->nc + c] * un[m->rec_off[k * m->nc + c]];
+    }
+  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (r < n && c == 0) m->rec[(m->step0 + *tick + 1) * m->nrec + k] = v;
 }
 
 }  // namespace fdk

@@ -151,16 +151,43 @@ struct TmaArgs {
   SparseArgs sp;
 };
 
+// One shot of a batch (device memory, one per member).  At batch tick t the
+// shot is at global step step0 + t with u^n in level[cur0 ^ (t & 1)].
+struct alignas(64) ShotDesc {
+  CUtensorMap map_u[2];   // levels, halo box
+  CUtensorMap map_t[2];   // levels, tile box (u^{n-1} reads)
+  CUtensorMap map_a, map_c;
+  Geom g;
+  Coef c;
+  float *level[2];
+  int tiles_x, ntiles, zblock, cur0;
+  int64_t step0;
+  const int4 *entries;     // source corners (see SparseArgs); nullptr: none
+  const int *first;
+  const float *src_scale;
+  const float *wav;
+  int nsrc, nc;
+};
+
+struct BatchArgs {
+  const ShotDesc *shots;
+  const int64_t *wpre;     // nshots + 1 prefix sums of the shots' tile-planes
+  int nshots;
+  const int64_t *tick;     // device tick counter of the batch
+  int *err;
+};
+
 // ISO: equal spacing on all axes, so one weight per k multiplies the sum of the
 // six neighbours minus 6u (still exact for constants); otherwise one difference
-// per axis.
-template <int R, int EQ, bool ISO>
+// per axis.  MULTI: the launch steps every shot of a batch (BatchArgs); the
+// work order concatenates the shots' tile-planes, shot by shot.
+template <int R, int EQ, bool ISO, bool MULTI>
 __global__ void __launch_bounds__(kTmaThreads, 2)
 k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
                 const __grid_constant__ CUtensorMap map_p,   // u^{n-1}, tile box
                 const __grid_constant__ CUtensorMap map_a,   // A, tile box
                 const __grid_constant__ CUtensorMap map_c,   // C, tile box
-                const TmaArgs args) {
+                const TmaArgs args, const BatchArgs bat) {
   constexpr int NY = tma_ny(R), TY = tma_ty(R);
   constexpr int HXB = tma_hxb(R), BW = tma_bw(R), DU = tma_du(R);
   constexpr int USLOT = tma_align128(tma_ubytes(R)) / 4;  // floats per ring-U slot
@@ -176,8 +203,8 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
   float *ring_u = reinterpret_cast<float *>(smem + 1024);
   float *ring_x = ring_u + DU * USLOT;
 
-  const Geom &g = args.g;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int *const err = MULTI ? bat.err : args.err;
   if (threadIdx.x == 0) {
     for (int i = 0; i < DU; ++i) {
       mbar_init(&full_u[i], 1);
@@ -194,25 +221,52 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
   __syncthreads();
 
   int64_t q0, q1;
-  cta_range(args.W, blockIdx.x, gridDim.x, q0, q1);
-  const int n0 = g.n0;
+  cta_range(MULTI ? bat.wpre[bat.nshots] : args.W, blockIdx.x, gridDim.x, q0, q1);
+  const int64_t tick = MULTI ? *bat.tick : 0;
+  // the shot owning position q (batches: shots are visited in increasing q)
+  int shot = 0;
+  auto locate = [&](int64_t q, int &tile, int &za, int &zb, int &tiles_x, int &n0s) {
+    if constexpr (MULTI) {
+      while (q >= bat.wpre[shot + 1]) ++shot;
+      const ShotDesc &d = bat.shots[shot];
+      segment_at(q - bat.wpre[shot], min(q1, bat.wpre[shot + 1]) - bat.wpre[shot], d.ntiles,
+                 d.zblock, d.g.n0, tile, za, zb);
+      tiles_x = d.tiles_x;
+      n0s = d.g.n0;
+    } else {
+      segment_at(q, q1, args.ntiles, args.zblock, args.g.n0, tile, za, zb);
+      tiles_x = args.tiles_x;
+      n0s = args.g.n0;
+    }
+  };
 
   if (warp == kTmaNW) {
     // ------------------------------- producer -------------------------------
     if (lane == 0) {
-      tma_prefetch_desc(&map_u);
-      if (AC) {
-        tma_prefetch_desc(&map_p);
-        tma_prefetch_desc(&map_a);
-        tma_prefetch_desc(&map_c);
+      if constexpr (!MULTI) {
+        tma_prefetch_desc(&map_u);
+        if (AC) {
+          tma_prefetch_desc(&map_p);
+          tma_prefetch_desc(&map_a);
+          tma_prefetch_desc(&map_c);
+        }
       }
       uint32_t su = 0, sx = 0;  // fills issued to rings U and X
       bool ok = true;
       for (int64_t q = q0; q < q1 && ok;) {
-        int tile, za, zb;
-        segment_at(q, q1, args.ntiles, args.zblock, n0, tile, za, zb);
+        int tile, za, zb, tiles_x, n0s;
+        locate(q, tile, za, zb, tiles_x, n0s);
         q += zb - za;
-        const int x0 = (tile % args.tiles_x) * kTmaTX, y0 = (tile / args.tiles_x) * TY;
+        const int x0 = (tile % tiles_x) * kTmaTX, y0 = (tile / tiles_x) * TY;
+        const CUtensorMap *mu = &map_u, *mp = &map_p, *ma = &map_a, *mc = &map_c;
+        if constexpr (MULTI) {
+          const ShotDesc &d = bat.shots[shot];
+          const int par = d.cur0 ^ (int)(tick & 1);
+          mu = &d.map_u[par];
+          mp = &d.map_t[par ^ 1];
+          ma = &d.map_a;
+          mc = &d.map_c;
+        }
         for (int p = za - R; p < zb + R; ++p) {
           if (*abort_flag) { ok = false; break; }
           const int zc = p - R;
@@ -224,9 +278,9 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
             }
             float *dst = ring_x + slot * 3 * XT;
             mbar_expect_tx(&full_x[slot], 3 * XT * 4);
-            tma_load_3d(dst, &map_p, x0 + kHaloX, y0 + R, zc + R, &full_x[slot]);
-            tma_load_3d(dst + XT, &map_a, x0 + kHaloX, y0 + R, zc + R, &full_x[slot]);
-            tma_load_3d(dst + 2 * XT, &map_c, x0 + kHaloX, y0 + R, zc + R, &full_x[slot]);
+            tma_load_3d(dst, mp, x0 + kHaloX, y0 + R, zc + R, &full_x[slot]);
+            tma_load_3d(dst + XT, ma, x0 + kHaloX, y0 + R, zc + R, &full_x[slot]);
+            tma_load_3d(dst + 2 * XT, mc, x0 + kHaloX, y0 + R, zc + R, &full_x[slot]);
             ++sx;
           }
           const uint32_t slot = su % DU;
@@ -235,11 +289,11 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
             break;
           }
           mbar_expect_tx(&full_u[slot], tma_ubytes(R));
-          tma_load_3d(ring_u + slot * USLOT, &map_u, x0 + kHaloX - HXB, y0, p + R, &full_u[slot]);
+          tma_load_3d(ring_u + slot * USLOT, mu, x0 + kHaloX - HXB, y0, p + R, &full_u[slot]);
           ++su;
         }
       }
-      if (!ok && atomicCAS(args.err, 0, 2) == 0) args.err[1] = blockIdx.x;
+      if (!ok && atomicCAS(err, 0, 2) == 0) err[1] = blockIdx.x;
       if (!ok) *abort_flag = 1;
       // drain: every fill issued must land before the block exits
       bool drained = true;
@@ -251,7 +305,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
         const uint32_t last = sx - 1 - ((sx - 1 - i) % kTmaDX);
         drained &= mbar_wait(&full_x[last % kTmaDX], (last / kTmaDX) & 1);
       }
-      if (!drained && atomicCAS(args.err, 0, 3) == 0) args.err[1] = blockIdx.x;
+      if (!drained && atomicCAS(err, 0, 3) == 0) err[1] = blockIdx.x;
     }
     return;
   }
@@ -262,16 +316,34 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
   float qz[NY][Q];
   uint32_t su = 0, sx = 0;
   const int row0 = warp * NY;  // first tile row of this thread
-  const int64_t nstep = (AC && args.sp.first) ? *args.sp.step + args.sp.j : 0;
-  const float *const wk0 = args.c.w[0];
-  const float *const wk1 = args.c.w[1];
-  const float *const wk2 = args.c.w[2];
+  int64_t nstep = 0;
+  if constexpr (!MULTI) nstep = (AC && args.sp.first) ? *args.sp.step + args.sp.j : 0;
+  // per-shot parameters (for one shot they stay the kernel's own arguments)
+  const float *wk0 = args.c.w[0], *wk1 = args.c.w[1], *wk2 = args.c.w[2];
+  SparseArgs sp = args.sp;
+  Geom g = args.g;
+  float *out = args.out;
   for (int64_t q = q0; q < q1;) {
-    int tile, za, zb;
-    segment_at(q, q1, args.ntiles, args.zblock, n0, tile, za, zb);
+    int tile, za, zb, tiles_x, n0;
+    locate(q, tile, za, zb, tiles_x, n0);
     q += zb - za;
-    const int x = (tile % args.tiles_x) * kTmaTX + lane;
-    const int ybase = (tile / args.tiles_x) * TY + row0;
+    if constexpr (MULTI) {
+      const ShotDesc &d = bat.shots[shot];
+      g = d.g;
+      wk0 = d.c.w[0];
+      wk1 = d.c.w[1];
+      wk2 = d.c.w[2];
+      out = d.level[d.cur0 ^ (int)(tick & 1) ^ 1];
+      sp.entries = d.entries;
+      sp.first = d.first;
+      sp.src_scale = d.src_scale;
+      sp.wav = d.wav;
+      sp.nsrc = d.nsrc;
+      sp.nc = d.nc;
+      nstep = d.step0 + tick;
+    }
+    const int x = (tile % tiles_x) * kTmaTX + lane;
+    const int ybase = (tile / tiles_x) * TY + row0;
     // which of this thread's rows it stores (diffusion: interior nodes only)
     unsigned rows_ok = 0;
 #pragma unroll
@@ -281,13 +353,13 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
                          : (x > 0 && x < g.n2 - 1 && y > 0 && y < g.n1 - 1);
       rows_ok |= (in ? 1u : 0u) << j;
     }
-    float *optr = args.out + gidx(g, za, ybase, x);
+    float *optr = out + gidx(g, za, ybase, x);
     // sparse entries of this segment: [ecur, eend), next one in a register
     int ecur = 0, eend = 0, nxt_z = INT_MAX;
-    if (AC && args.sp.first) {
-      ecur = args.sp.first[tile * n0 + za];
-      eend = args.sp.first[tile * n0 + zb];
-      if (ecur < eend) nxt_z = args.sp.entries[ecur].z;
+    if (AC && sp.first) {
+      ecur = sp.first[tile * n0 + za];
+      eend = sp.first[tile * n0 + zb];
+      if (ecur < eend) nxt_z = sp.entries[ecur].z;
     }
 
     // warm-up: planes za-R .. za+R-1 fill queue slots 0 .. 2R-1
@@ -371,14 +443,13 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
               // lane adds them in entry order
               while (true) {
                 const int e = ecur + lane;
-                const int4 en = e < eend ? args.sp.entries[e] : make_int4(0, 0, INT_MAX, 0);
+                const int4 en = e < eend ? sp.entries[e] : make_int4(0, 0, INT_MAX, 0);
                 const int cnt = __popc(__ballot_sync(0xffffffffu, en.z == zc));  // a prefix
                 const int jr = en.y - ybase;
                 const bool here = en.z == zc && jr >= 0 && jr < NY;
                 float add = 0.f;
                 if (here)
-                  add = args.sp.src_scale[en.w] *
-                        args.sp.wav[nstep * args.sp.nsrc + en.w / args.sp.nc];
+                  add = sp.src_scale[en.w] * sp.wav[nstep * sp.nsrc + en.w / sp.nc];
                 unsigned mine = __ballot_sync(0xffffffffu, here);
                 while (mine) {
                   const int b = __ffs(mine) - 1;
@@ -395,7 +466,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
                 ecur += cnt;
                 if (cnt < 32) break;
               }
-              nxt_z = ecur < eend ? args.sp.entries[ecur].z : INT_MAX;
+              nxt_z = ecur < eend ? sp.entries[ecur].z : INT_MAX;
             }
 #pragma unroll
             for (int j = 0; j < NY; ++j) {
@@ -424,7 +495,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
   return;
 timeout:
   if (lane == 0) {
-    if (atomicCAS(args.err, 0, 1) == 0) args.err[1] = blockIdx.x;
+    if (atomicCAS(err, 0, 1) == 0) err[1] = blockIdx.x;
     *abort_flag = 1;
   }
 }
@@ -439,7 +510,9 @@ struct TmaPlan {
   CUtensorMap map_a, map_c;
   TmaArgs args{};
   float *level[2] = {nullptr, nullptr};
-  void (*fn)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, TmaArgs) = nullptr;
+  void (*fn)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, TmaArgs, BatchArgs) = nullptr;
+  void (*fn_multi)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, TmaArgs, BatchArgs) = nullptr;
+  int grid_multi = 0;
   int grid = 0;
   int smem = 0;
 };
@@ -471,20 +544,31 @@ inline bool encode_map(EncodeFn enc, CUtensorMap *m, float *base, const Geom &g,
 
 template <int R, int EQ, bool ISO>
 inline cudaError_t tma_configure(TmaPlan &pl) {
-  pl.fn = k_stencil3d_tma<R, EQ, ISO>;
+  pl.fn = k_stencil3d_tma<R, EQ, ISO, false>;
+  pl.fn_multi = (EQ == kAcoustic) ? k_stencil3d_tma<R, EQ, ISO, true> : nullptr;
   pl.smem = tma_smem_bytes(R, EQ == kAcoustic);
-  cudaError_t e = cudaFuncSetAttribute(k_stencil3d_tma<R, EQ, ISO>,
+  cudaError_t e = cudaFuncSetAttribute(k_stencil3d_tma<R, EQ, ISO, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, pl.smem);
+  if (e == cudaSuccess && EQ == kAcoustic)
+    e = cudaFuncSetAttribute(k_stencil3d_tma<R, EQ, ISO, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, pl.smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil3d_tma<R, EQ, ISO>,
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil3d_tma<R, EQ, ISO, false>,
                                                     kTmaThreads, pl.smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int per_sm_multi = per_sm;
+  if (EQ == kAcoustic) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm_multi, k_stencil3d_tma<R, EQ, ISO, true>, kTmaThreads, pl.smem);
+    if (e != cudaSuccess) return e;
+  }
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   pl.grid = sms * per_sm;
+  pl.grid_multi = sms * std::max(per_sm_multi, 1);
   return cudaSuccess;
 }
 
@@ -564,7 +648,7 @@ inline cudaError_t launch_tma_step(const TmaPlan &pl, int cur, float *out, const
   a.err = err;
   a.sp = sp;
   pl.fn<<<pl.grid, kTmaThreads, pl.smem, s>>>(pl.map_u[cur], pl.map_t[cur ^ 1], pl.map_a,
-                                              pl.map_c, a);
+                                              pl.map_c, a, BatchArgs{});
   return cudaGetLastError();
 }
 

@@ -110,3 +110,55 @@ class Solver:
     def profile(self):
         """(stencil launches, summed stencil ms) since the previous call."""
         return B.fd_profile(self.ctx)
+
+
+class Batch:
+    """Shots of one space order stepped together (see fd_batch_* in include/fd.h).
+
+    ``add``/``remove`` take :class:`Solver` objects; ``run(n)`` advances every
+    member n steps with one set of batched launches per step.  A member keeps
+    its own state, so ``Solver.read`` works on it afterwards.
+    """
+
+    def __init__(self, space_order, stream=None):
+        self.handle = None
+        cs = None
+        if stream is not None:
+            cs = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        self.handle = B.fd_batch_create(space_order, cs)
+        self.members = []
+
+    def add(self, solver):
+        B.fd_batch_add(self.handle, solver.ctx)
+        self.members.append(solver)
+
+    def remove(self, solver):
+        B.fd_batch_remove(self.handle, solver.ctx)
+        self.members.remove(solver)
+
+    def run(self, nticks):
+        B.fd_batch_run(self.handle, nticks)
+
+    @property
+    def kernel_launches(self):
+        return B.fd_batch_kernel_launches(self.handle)
+
+    def __len__(self):
+        return B.fd_batch_size(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            B.fd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
