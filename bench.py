@@ -12,7 +12,11 @@ the C ABI with pinned host buffers (host->device copies of the shot's inputs and
 the device->host read of its traces inside the timed region).
 
 ``--workload roofline512 --so {4,8,12,16}`` runs the 512³ sweep (200 steps, one
-source, no receivers).  ``--impl reference`` times the FP64 CPU oracle on the
+source, no receivers).  ``--workload serving`` serves a seeded Poisson stream of
+64 shots (2-D 200²-1000² and 3-D 128³-320³ grids, so 8, 300-1000 steps, one
+source and 128-512 receivers each) with the continuous-batching server under an
+HBM budget, and the same stream one shot at a time; it reports shots/s and
+p50/p99 latency for both.  ``--impl reference`` times the FP64 CPU oracle on the
 same workload instead (a bounded sample of time steps per step).
 
 Multi-GPU (torchrun): shots are independent, so each rank runs its own shot on
@@ -57,7 +61,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="acoustic256", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="acoustic256", choices=sorted(WORKLOADS) + ["serving"])
+    ap.add_argument("--shots", type=int, default=64)
+    ap.add_argument("--mean-gap", type=float, default=0.015)
+    ap.add_argument("--hbm-budget-gb", type=float, default=8.0)
     ap.add_argument("--so", type=int, default=None)
     ap.add_argument("--nt", type=int, default=None)
     ap.add_argument("--kernel", default="auto", choices=["auto", "plain", "tma"])
@@ -346,10 +353,49 @@ def run_ours(args):
     return 0
 
 
+def run_serving(args):
+    import torch
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    from paper_1906_10811_b300 import build
+    from paper_1906_10811_b300.serve import (DeviceBackend, Server, ShotRequest, serve_sequential,
+                                             summarize)
+    build.build()
+    stream = fdsynth.serving_stream(nshots=args.shots, seed=2 + rank, mean_gap_s=args.mean_gap)
+    reqs = [ShotRequest(i, a, p) for i, a, p in stream]
+    pts = sum(int(np.prod(p["shape"])) * p["nt"] for _, _, p in stream)
+    # warm the library (module load, first graphs) on a small shot
+    warm = fdsynth.serving_stream(nshots=2, seed=99, sizes2d=(64, 64), sizes3d=(32, 32),
+                                  nt_range=(10, 10), nrec_range=(8, 8))
+    serve_sequential([ShotRequest(i, 0.0, p) for i, _, p in warm])
+    be = DeviceBackend(8)
+    srv = Server(be, hbm_budget=int(args.hbm_budget_gb * 2 ** 30), max_members=64, ticks_per_round=32)
+    batched = summarize(srv.serve(reqs))
+    be.close()
+    seq = summarize(serve_sequential(reqs))
+    line = {"metric": "served shots/s", "value": round(batched["shots_per_s"], 3), "unit": "shots/s",
+            "n_gpus": world, "steps": args.shots, "warmup": 1,
+            "ms_per_step": round(1e3 * batched["seconds"] / args.shots, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"poisson stream of {args.shots} acoustic shots, so 8",
+                       "grids": "2-D 200^2-1000^2, 3-D 128^3-320^3", "nt": "300-1000",
+                       "receivers": "128-512", "mean_gap_s": args.mean_gap,
+                       "hbm_budget_gb": args.hbm_budget_gb, "grid_point_updates": pts},
+            "serving": {k: round(v, 4) for k, v in batched.items()},
+            "sequential": {k: round(v, 4) for k, v in seq.items()},
+            "speedup_vs_sequential": round(batched["shots_per_s"] / seq["shots_per_s"], 3),
+            "gpts_per_s": round(pts / batched["seconds"] / 1e9, 2)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 

@@ -186,3 +186,31 @@ def acoustic_problem(n=256, ndim=3, so=8, nbl=40, h=10.0, nt=500, nrec=256,
     rec = receiver_line(shape, spacing, nrec, nbl) if nrec else np.zeros((0, ndim), np.float32)
     return dict(shape=shape, spacing=spacing, so=so, dt=dt, nt=nt, m=m, damp=damp,
                 vel=v, src_coords=src, wavelet=wav, rec_coords=rec)
+
+
+def serving_stream(nshots=64, seed=2, mean_gap_s=0.01, sizes2d=(200, 1000), sizes3d=(128, 320),
+                   nt_range=(300, 1000), nrec_range=(128, 512), so=8, frac3d=0.5, nbl=40):
+    """A seeded Poisson stream of acoustic shots for the serving workload.
+
+    Each shot: a 2-D grid of n² (n uniform in ``sizes2d``) or a 3-D grid of n³
+    (n uniform in ``sizes3d``), chosen with probability ``frac3d``; the layered
+    model recipe with its own seed; one Ricker source at the centre; a receiver
+    line of nrec (uniform in ``nrec_range``) receivers; nt uniform in
+    ``nt_range`` steps.  Arrival gaps are exponential with mean ``mean_gap_s``.
+    Returns a list of (id, arrival seconds, problem dict).
+    """
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(nshots):
+        t += float(rng.exponential(mean_gap_s))
+        three = bool(rng.random() < frac3d)
+        lo, hi = sizes3d if three else sizes2d
+        n = int(rng.integers(lo, hi + 1))
+        nt = int(rng.integers(nt_range[0], nt_range[1] + 1))
+        nrec = int(rng.integers(nrec_range[0], nrec_range[1] + 1))
+        layer = min(nbl, max(4, n // 8))
+        p = acoustic_problem(n=n, ndim=3 if three else 2, so=so, nbl=layer, nt=nt, nrec=nrec,
+                             seed=1000 + i)
+        out.append((i, t, p))
+    return out

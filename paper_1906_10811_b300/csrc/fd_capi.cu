@@ -169,11 +169,13 @@ fd_status check_usable(fd_ctx *c) {
   return FD_OK;
 }
 
+// Context memory comes from the device's stream-ordered pool on the context
+// stream: admitting or retiring a shot does not synchronise the device.
 template <typename T>
 fd_status dalloc(fd_ctx *c, T **p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+  cudaError_t e = cudaMallocAsync((void **)p, count * sizeof(T), c->stream);
   if (e != cudaSuccess) {
     *p = nullptr;
     cudaGetLastError();
@@ -184,8 +186,8 @@ fd_status dalloc(fd_ctx *c, T **p, size_t count) {
 }
 
 template <typename T>
-void dfree(T *&p) {
-  if (p) cudaFree(p);
+void dfree(fd_ctx *c, T *&p) {
+  if (p) cudaFreeAsync(p, c->stream);
   p = nullptr;
 }
 
@@ -462,11 +464,11 @@ fd_status ensure_rec_capacity(fd_ctx *c, int64_t rows) {
     e = cudaMemcpyAsync(nb, c->rec, (size_t)c->rec_rows * c->nrec * sizeof(float),
                         cudaMemcpyDeviceToDevice, c->stream);
   if (e != cudaSuccess) {
-    cudaFree(nb);
+    cudaFreeAsync(nb, c->stream);
     return fail(c, FD_ECUDA, "trace buffer growth: %s", cudaGetErrorString(e));
   }
   CU(cudaStreamSynchronize(c->stream));
-  dfree(c->rec);
+  dfree(c, c->rec);
   c->rec = nb;
   c->rec_cap = cap;
   drop_graphs(c);
@@ -517,8 +519,8 @@ fd_status prepare_fused(fd_ctx *c) {
     std::vector<int4> ent(es.size());
     for (size_t i = 0; i < es.size(); ++i) ent[i] = make_int4(es[i].x, es[i].y, es[i].z, es[i].idx);
     CU(cudaStreamSynchronize(c->stream));
-    dfree(c->sp_entries);
-    dfree(c->sp_first);
+    dfree(c, c->sp_entries);
+    dfree(c, c->sp_first);
     drop_graphs(c);
     if (!es.empty()) {
       fd_status st = dalloc(c, &c->sp_entries, ent.size());
@@ -798,7 +800,7 @@ fd_status fd_set_sources(fd_ctx *c, int nsrc, const float *coords, int nt, const
                  &w[(size_t)j * c->nc]))
       return fail(c, FD_EINVAL, "source %d lies outside the grid", j);
   CU(cudaStreamSynchronize(c->stream));
-  dfree(c->src_off); dfree(c->src_dense); dfree(c->src_w); dfree(c->src_scale); dfree(c->wav);
+  dfree(c, c->src_off); dfree(c, c->src_dense); dfree(c, c->src_w); dfree(c, c->src_scale); dfree(c, c->wav);
   drop_graphs(c);
   c->nsrc = 0;
   c->nt_wav = 0;
@@ -842,7 +844,7 @@ fd_status fd_set_receivers(fd_ctx *c, int nrec, const float *coords) {
       return fail(c, FD_EINVAL, "receiver %d lies outside the grid", k);
   for (int i = 0; i < n; ++i) wf[i] = (float)w[i];
   CU(cudaStreamSynchronize(c->stream));
-  dfree(c->rec_off); dfree(c->rec_w); dfree(c->rec);
+  dfree(c, c->rec_off); dfree(c, c->rec_w); dfree(c, c->rec);
   drop_graphs(c);
   c->nrec = 0;
   c->rec_cap = 0;
@@ -993,11 +995,11 @@ void fd_destroy(fd_ctx *c) {
   drop_graphs(c);
   for (auto e : c->ev) cudaEventDestroy(e);
   destroy_tma(c->tma);
-  dfree(c->u[0]); dfree(c->u[1]); dfree(c->A); dfree(c->C); dfree(c->m_dense); dfree(c->stage);
-  dfree(c->d_step); dfree(c->d_stats); dfree(c->d_err);
-  dfree(c->wav); dfree(c->src_scale); dfree(c->src_off); dfree(c->src_dense); dfree(c->src_w);
-  dfree(c->rec_off); dfree(c->rec_w); dfree(c->rec);
-  dfree(c->sp_entries); dfree(c->sp_first);
+  dfree(c, c->u[0]); dfree(c, c->u[1]); dfree(c, c->A); dfree(c, c->C); dfree(c, c->m_dense); dfree(c, c->stage);
+  dfree(c, c->d_step); dfree(c, c->d_stats); dfree(c, c->d_err);
+  dfree(c, c->wav); dfree(c, c->src_scale); dfree(c, c->src_off); dfree(c, c->src_dense); dfree(c, c->src_w);
+  dfree(c, c->rec_off); dfree(c, c->rec_w); dfree(c, c->rec);
+  dfree(c, c->sp_entries); dfree(c, c->sp_first);
   for (int i = 0; i < 2; ++i) {
     if (c->ev_step[i]) cudaEventDestroy(c->ev_step[i]);
     if (c->ev_rec[i]) cudaEventDestroy(c->ev_rec[i]);
@@ -1033,15 +1035,17 @@ struct fd_batch {
   bool own_stream = false;
   std::vector<fd_ctx *> members;
   ShotDesc *d_shots = nullptr;   // 3-D members
-  int64_t *d_wpre = nullptr;
+  int4 *d_items = nullptr;       // work items of the pipelined kernel
+  unsigned *d_ticket = nullptr;  // [2] item tickets
+  size_t cap_items = 0;
   MemberDesc *d_mem = nullptr;   // every member (2-D stencil, injection, receivers)
   int2 *d_src = nullptr, *d_rec = nullptr;
   int64_t *d_tick = nullptr;
   size_t cap_shots = 0, cap_mem = 0, cap_src = 0, cap_rec = 0;
-  ShotDesc *h_shots = nullptr;   // pinned staging
-  MemberDesc *h_mem = nullptr;
+  std::vector<ShotDesc> h_shots;  // staging (pageable: cudaMemcpyAsync copies it out before
+  std::vector<MemberDesc> h_mem;  // returning, so the next run may refill it at once)
   std::vector<int2> h_src, h_rec;
-  std::vector<int64_t> h_wpre;
+  std::vector<int4> h_items;
   cudaEvent_t ev = nullptr;
   int64_t launches = 0;
   bool failed = false;
@@ -1073,6 +1077,7 @@ template <typename T>
 fd_status bgrow(fd_batch *b, T **dev, T **host, size_t *cap, size_t need) {
   if (need <= *cap) return FD_OK;
   const size_t n = std::max<size_t>(need, 2 * *cap + 8);
+  if (*dev) BCU(cudaStreamSynchronize(b->stream));  // earlier runs may still read it
   if (*dev) cudaFree(*dev);
   *dev = nullptr;
   BCU(cudaMalloc((void **)dev, n * sizeof(T)));
@@ -1120,6 +1125,7 @@ fd_status fd_batch_create(fd_batch **out, int space_order, void *cuda_stream) {
     }
   }
   if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_tick, sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_ticket, 2 * sizeof(unsigned));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     fail(nullptr, FD_ECUDA, "batch creation: %s", cudaGetErrorString(e));
@@ -1194,18 +1200,16 @@ fd_status fd_batch_run(fd_batch *b, int nticks) {
       BCU(cudaStreamWaitEvent(b->stream, b->ev, 0));
     }
   }
-  // descriptor tables (host staging is pinned; wait for the previous run's copies)
-  BCU(cudaStreamSynchronize(b->stream));
+  // descriptor tables (device tables are rewritten in stream order)
   std::vector<fd_ctx *> m3;
   for (fd_ctx *c : b->members)
     if (c->ndim == 3) m3.push_back(c);
   const size_t nm = b->members.size(), n3 = m3.size();
-  fd_status st = bgrow(b, &b->d_mem, &b->h_mem, &b->cap_mem, nm);
-  if (!st) st = bgrow(b, &b->d_shots, &b->h_shots, &b->cap_shots, std::max<size_t>(n3, 1));
+  fd_status st = bgrow<MemberDesc>(b, &b->d_mem, nullptr, &b->cap_mem, nm);
+  if (!st) st = bgrow<ShotDesc>(b, &b->d_shots, nullptr, &b->cap_shots, std::max<size_t>(n3, 1));
   if (st) return st;
-  if (b->d_wpre) cudaFree(b->d_wpre);
-  b->d_wpre = nullptr;
-  BCU(cudaMalloc((void **)&b->d_wpre, (n3 + 1) * sizeof(int64_t)));
+  b->h_mem.resize(nm);
+  b->h_shots.resize(std::max<size_t>(n3, 1));
   b->h_src.clear();
   b->h_rec.clear();
   int64_t blk = 0;
@@ -1238,12 +1242,33 @@ fd_status fd_batch_run(fd_batch *b, int nticks) {
     }
     for (int k = 0; k < c->nrec; ++k) b->h_rec.push_back(make_int2((int)i, k));
   }
-  b->h_wpre.assign(n3 + 1, 0);
-  int64_t wtot = 0;
-  for (size_t i = 0; i < n3; ++i) wtot += m3[i]->tma.args.W;
+  // work items: z-layers over all 3-D members, thick while much work remains
+  // and thinner towards the end (guided), tile by tile within a shot
   const TmaPlan &plan0 = n3 ? m3[0]->tma : TmaPlan();
-  const int grid3 = n3 ? (int)std::min<int64_t>(plan0.grid_multi, std::max<int64_t>(wtot, 1)) : 0;
-  const int64_t share = n3 ? (wtot + grid3 - 1) / grid3 : 1;
+  b->h_items.clear();
+  int grid3 = 0;
+  if (n3) {
+    int zmax = 0;
+    for (fd_ctx *c : m3) zmax = std::max(zmax, c->g.n0);
+    for (int z = 0; z < zmax;) {
+      int64_t tiles_here = 0, rem = 0;
+      for (fd_ctx *c : m3)
+        if (c->g.n0 > z) {
+          tiles_here += c->tma.args.ntiles;
+          rem += (int64_t)c->tma.args.ntiles * (c->g.n0 - z);
+        }
+      const int64_t per_tile = rem / std::max<int64_t>(tiles_here, 1);
+      const int h = (int)std::min<int64_t>(128, std::max<int64_t>(16, per_tile / 2));
+      for (size_t i = 0; i < n3; ++i) {
+        fd_ctx *c = m3[i];
+        if (c->g.n0 <= z) continue;
+        const int zb = std::min(c->g.n0, z + h);
+        for (int t = 0; t < c->tma.args.ntiles; ++t) b->h_items.push_back(make_int4((int)i, t, z, zb));
+      }
+      z += h;
+    }
+    grid3 = (int)std::min<int64_t>(plan0.grid_multi, (int64_t)b->h_items.size());
+  }
   for (size_t i = 0; i < n3; ++i) {
     fd_ctx *c = m3[i];
     ShotDesc &d = b->h_shots[i];
@@ -1260,7 +1285,7 @@ fd_status fd_batch_run(fd_batch *b, int nticks) {
     d.level[1] = c->u[1];
     d.tiles_x = c->tma.args.tiles_x;
     d.ntiles = c->tma.args.ntiles;
-    d.zblock = (int)std::min<int64_t>(c->g.n0, std::max<int64_t>(1, share));
+    d.zblock = c->g.n0;
     d.cur0 = c->cur;
     d.step0 = c->step;
     if (c->nsrc > 0) {
@@ -1271,15 +1296,20 @@ fd_status fd_batch_run(fd_batch *b, int nticks) {
       d.nsrc = c->nsrc;
       d.nc = c->nc;
     }
-    b->h_wpre[i + 1] = b->h_wpre[i] + c->tma.args.W;
   }
-  if (!b->h_src.empty()) st = bgrow<int2>(b, &b->d_src, nullptr, &b->cap_src, b->h_src.size());
+  if (!b->h_items.empty())
+    st = bgrow<int4>(b, &b->d_items, nullptr, &b->cap_items, b->h_items.size());
+  if (!st && !b->h_src.empty()) st = bgrow<int2>(b, &b->d_src, nullptr, &b->cap_src, b->h_src.size());
   if (!st && !b->h_rec.empty()) st = bgrow<int2>(b, &b->d_rec, nullptr, &b->cap_rec, b->h_rec.size());
   if (st) return st;
-  BCU(cudaMemcpyAsync(b->d_mem, b->h_mem, nm * sizeof(MemberDesc), cudaMemcpyHostToDevice, b->stream));
+  BCU(cudaMemcpyAsync(b->d_mem, b->h_mem.data(), nm * sizeof(MemberDesc), cudaMemcpyHostToDevice,
+                      b->stream));
   if (n3) {
-    BCU(cudaMemcpyAsync(b->d_shots, b->h_shots, n3 * sizeof(ShotDesc), cudaMemcpyHostToDevice, b->stream));
-    BCU(cudaMemcpyAsync(b->d_wpre, b->h_wpre.data(), (n3 + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaMemcpyAsync(b->d_shots, b->h_shots.data(), n3 * sizeof(ShotDesc),
+                        cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaMemcpyAsync(b->d_items, b->h_items.data(), b->h_items.size() * sizeof(int4),
+                        cudaMemcpyHostToDevice, b->stream));
+    BCU(cudaMemsetAsync(b->d_ticket, 0, 2 * sizeof(unsigned), b->stream));
   }
   if (!b->h_src.empty())
     BCU(cudaMemcpyAsync(b->d_src, b->h_src.data(), b->h_src.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
@@ -1289,7 +1319,8 @@ fd_status fd_batch_run(fd_batch *b, int nticks) {
   BCU(cudaGetLastError());
   ++b->launches;
   // error word of the pipelined kernel: the first 3-D member's
-  BatchArgs ba{b->d_shots, b->d_wpre, (int)n3, b->d_tick, n3 ? m3[0]->d_err : nullptr};
+  BatchArgs ba{b->d_shots, b->d_items, (int)b->h_items.size(), b->d_ticket, b->d_tick,
+               n3 ? m3[0]->d_err : nullptr};
   const int nsrc_e = (int)b->h_src.size(), nrec_e = (int)b->h_rec.size();
   const StencilFn2D f2 = batch2d_fn(R);
   for (int t = 0; t < nticks; ++t) {
@@ -1332,13 +1363,12 @@ void fd_batch_destroy(fd_batch *b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->d_shots) cudaFree(b->d_shots);
-  if (b->d_wpre) cudaFree(b->d_wpre);
+  if (b->d_items) cudaFree(b->d_items);
+  if (b->d_ticket) cudaFree(b->d_ticket);
   if (b->d_mem) cudaFree(b->d_mem);
   if (b->d_src) cudaFree(b->d_src);
   if (b->d_rec) cudaFree(b->d_rec);
   if (b->d_tick) cudaFree(b->d_tick);
-  if (b->h_shots) cudaFreeHost(b->h_shots);
-  if (b->h_mem) cudaFreeHost(b->h_mem);
   if (b->ev) cudaEventDestroy(b->ev);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;

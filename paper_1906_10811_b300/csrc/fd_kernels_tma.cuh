@@ -169,18 +169,23 @@ struct alignas(64) ShotDesc {
   int nsrc, nc;
 };
 
+// Batch work: items {shot, tile, za, zb} ordered z-layer by z-layer (thick
+// layers first, thin last), shot by shot, tile by tile; CTAs take them in
+// order from a ticket counter, so neighbouring tiles stream in step and the
+// last items are short.
 struct BatchArgs {
   const ShotDesc *shots;
-  const int64_t *wpre;     // nshots + 1 prefix sums of the shots' tile-planes
-  int nshots;
+  const int4 *items;
+  int nitems;
+  unsigned *ticket;        // [2]: counter of this tick (tick & 1); the other is reset
   const int64_t *tick;     // device tick counter of the batch
   int *err;
 };
 
 // ISO: equal spacing on all axes, so one weight per k multiplies the sum of the
 // six neighbours minus 6u (still exact for constants); otherwise one difference
-// per axis.  MULTI: the launch steps every shot of a batch (BatchArgs); the
-// work order concatenates the shots' tile-planes, shot by shot.
+// per axis.  MULTI: the launch steps every shot of a batch (BatchArgs), taking
+// work items dynamically; one shot takes static contiguous ranges.
 template <int R, int EQ, bool ISO, bool MULTI>
 __global__ void __launch_bounds__(kTmaThreads, 2)
 k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
@@ -200,6 +205,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
   uint64_t *full_x = empty_u + DU;
   uint64_t *empty_x = full_x + kTmaDX;
   volatile int *abort_flag = reinterpret_cast<volatile int *>(empty_x + kTmaDX);
+  volatile int4 *item_ring = reinterpret_cast<volatile int4 *>(smem + 512);  // batches: 4 items
   float *ring_u = reinterpret_cast<float *>(smem + 1024);
   float *ring_x = ring_u + DU * USLOT;
 
@@ -220,25 +226,13 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
   }
   __syncthreads();
 
-  int64_t q0, q1;
-  cta_range(MULTI ? bat.wpre[bat.nshots] : args.W, blockIdx.x, gridDim.x, q0, q1);
+  int64_t q0 = 0, q1 = 0;
+  if constexpr (!MULTI) cta_range(args.W, blockIdx.x, gridDim.x, q0, q1);
   const int64_t tick = MULTI ? *bat.tick : 0;
-  // the shot owning position q (batches: shots are visited in increasing q)
+  if constexpr (MULTI) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) bat.ticket[(tick + 1) & 1] = 0u;  // next tick's
+  }
   int shot = 0;
-  auto locate = [&](int64_t q, int &tile, int &za, int &zb, int &tiles_x, int &n0s) {
-    if constexpr (MULTI) {
-      while (q >= bat.wpre[shot + 1]) ++shot;
-      const ShotDesc &d = bat.shots[shot];
-      segment_at(q - bat.wpre[shot], min(q1, bat.wpre[shot + 1]) - bat.wpre[shot], d.ntiles,
-                 d.zblock, d.g.n0, tile, za, zb);
-      tiles_x = d.tiles_x;
-      n0s = d.g.n0;
-    } else {
-      segment_at(q, q1, args.ntiles, args.zblock, args.g.n0, tile, za, zb);
-      tiles_x = args.tiles_x;
-      n0s = args.g.n0;
-    }
-  };
 
   if (warp == kTmaNW) {
     // ------------------------------- producer -------------------------------
@@ -253,10 +247,41 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
       }
       uint32_t su = 0, sx = 0;  // fills issued to rings U and X
       bool ok = true;
-      for (int64_t q = q0; q < q1 && ok;) {
-        int tile, za, zb, tiles_x, n0s;
-        locate(q, tile, za, zb, tiles_x, n0s);
-        q += zb - za;
+      int64_t q = q0;
+      unsigned nitem = 0;        // batches: items taken by this block
+      while (ok) {
+        int tile, za, zb, tiles_x;
+        if constexpr (MULTI) {
+          const unsigned it = atomicAdd(&bat.ticket[tick & 1], 1u);
+          const int4 item = it < (unsigned)bat.nitems ? bat.items[it] : make_int4(-1, 0, 0, 0);
+          item_ring[nitem & 3].x = item.x;
+          item_ring[nitem & 3].y = item.y;
+          item_ring[nitem & 3].z = item.z;
+          item_ring[nitem & 3].w = item.w;
+          ++nitem;
+          if (item.x < 0) {
+            // no work left: complete the next ring-U phase without data so the
+            // consumers read the end mark published above
+            const uint32_t slot = su % DU;
+            if (su >= (uint32_t)DU && !mbar_wait(&empty_u[slot], ((su / DU) - 1) & 1)) {
+              ok = false;
+              break;
+            }
+            mbar_arrive(&full_u[slot]);
+            ++su;
+            break;
+          }
+          shot = item.x;
+          tile = item.y;
+          za = item.z;
+          zb = item.w;
+          tiles_x = bat.shots[shot].tiles_x;
+        } else {
+          if (q >= q1) break;
+          segment_at(q, q1, args.ntiles, args.zblock, args.g.n0, tile, za, zb);
+          q += zb - za;
+          tiles_x = args.tiles_x;
+        }
         const int x0 = (tile % tiles_x) * kTmaTX, y0 = (tile / tiles_x) * TY;
         const CUtensorMap *mu = &map_u, *mp = &map_p, *ma = &map_a, *mc = &map_c;
         if constexpr (MULTI) {
@@ -323,10 +348,30 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
   SparseArgs sp = args.sp;
   Geom g = args.g;
   float *out = args.out;
-  for (int64_t q = q0; q < q1;) {
+  int64_t q = q0;
+  unsigned nitem = 0;
+  while (true) {
     int tile, za, zb, tiles_x, n0;
-    locate(q, tile, za, zb, tiles_x, n0);
-    q += zb - za;
+    if constexpr (MULTI) {
+      // the next item is published with the first fill of its planes
+      if (!mbar_wait(&full_u[su % DU], (su / DU) & 1)) goto timeout;
+      const int4 item = make_int4(item_ring[nitem & 3].x, item_ring[nitem & 3].y,
+                                  item_ring[nitem & 3].z, item_ring[nitem & 3].w);
+      ++nitem;
+      if (item.x < 0) break;
+      shot = item.x;
+      tile = item.y;
+      za = item.z;
+      zb = item.w;
+      tiles_x = bat.shots[shot].tiles_x;
+      n0 = bat.shots[shot].g.n0;
+    } else {
+      if (q >= q1) break;
+      segment_at(q, q1, args.ntiles, args.zblock, args.g.n0, tile, za, zb);
+      q += zb - za;
+      tiles_x = args.tiles_x;
+      n0 = args.g.n0;
+    }
     if constexpr (MULTI) {
       const ShotDesc &d = bat.shots[shot];
       g = d.g;

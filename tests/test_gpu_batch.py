@@ -112,9 +112,11 @@ def test_batch_rejects_wrong_members():
 
 
 def test_footprint_covers_allocations():
+    """The admission measure bounds what a shot takes from the device (the
+    stream-ordered pool reserves in chunks of tens of MB: one chunk of slack)."""
     import torch
     from paper_1906_10811_b300 import fd_footprint_bytes
-    p = small_problem((64, 64, 64), 8, 200, nrec=32)
+    p = small_problem((192, 160, 176), 8, 200, nrec=32)
     torch.cuda.synchronize()
     free0, _ = torch.cuda.mem_get_info()
     s = _solver(p)
@@ -125,4 +127,4 @@ def test_footprint_covers_allocations():
     fp = fd_footprint_bytes(p["shape"], 8, 32, 200)
     s.close()
     assert fp > 0
-    assert used <= fp * 1.25 + (8 << 20)
+    assert used <= fp * 1.1 + (64 << 20)

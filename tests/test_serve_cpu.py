@@ -1,0 +1,100 @@
+"""Scheduling policy of the continuous-batching server, with a simulated
+backend and clock (no GPU): first-come-first-served admission under the HBM
+budget and slot limit, admission while other shots run, exact step counts,
+retirement and latency accounting."""
+
+from paper_1906_10811_b300.serve import Server, ShotRequest, summarize
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def sleep(self, dt):
+        self.t += dt
+
+
+class FakeBackend:
+    """Shots cost `size` units of memory; a tick costs 1e-3 s per member."""
+
+    def __init__(self, clock):
+        self.clock = clock
+        self.members = {}
+        self.used = 0
+        self.peak_used = 0
+        self.peak_members = 0
+
+    def footprint(self, req):
+        return req.problem["size"]
+
+    def start(self, req):
+        return req
+
+    def add(self, h):
+        self.members[h.id] = [h, 0]
+        self.used += h.problem["size"]
+        self.peak_used = max(self.peak_used, self.used)
+        self.peak_members = max(self.peak_members, len(self.members))
+
+    def run(self, n):
+        for m in self.members.values():
+            m[1] += n
+            assert m[1] <= m[0].problem["nt"], "a shot ran past its end"
+        self.clock.t += 1e-3 * n * len(self.members)
+
+    def finish(self, h):
+        steps = self.members.pop(h.id)[1]
+        assert steps == h.problem["nt"]
+        self.used -= h.problem["size"]
+        return steps
+
+
+def _reqs(spec):
+    return [ShotRequest(i, a, {"size": s, "nt": nt}) for i, (a, s, nt) in enumerate(spec)]
+
+
+def test_budget_slots_and_fifo():
+    clk = FakeClock()
+    be = FakeBackend(clk)
+    reqs = _reqs([(0.0, 4, 50), (0.0, 4, 30), (0.0, 4, 20), (0.001, 2, 10), (0.5, 1, 5)])
+    srv = Server(be, hbm_budget=10, max_members=3, ticks_per_round=8, clock=clk, sleep=clk.sleep)
+    res = srv.serve(reqs)
+    assert [r.id for r in res] == [0, 1, 2, 3, 4]
+    assert all(r.traces == reqs[r.id].problem["nt"] for r in res)
+    assert be.peak_used <= 10 and be.peak_members <= 3
+    admits = [rid for ev, rid, _ in srv.log if ev == "admit"]
+    assert admits == sorted(admits)                       # first come, first served
+    for r in res:
+        assert r.arrival <= r.admitted <= r.finished
+
+
+def test_continuous_admission_while_running():
+    """A shot that arrives while a long one runs joins before the long one ends."""
+    clk = FakeClock()
+    be = FakeBackend(clk)
+    reqs = _reqs([(0.0, 1, 1000), (0.05, 1, 10)])
+    srv = Server(be, hbm_budget=100, ticks_per_round=16, clock=clk, sleep=clk.sleep)
+    res = srv.serve(reqs)
+    t_admit_1 = [t for ev, rid, t in srv.log if ev == "admit" and rid == 1][0]
+    t_finish_0 = [t for ev, rid, t in srv.log if ev == "finish" and rid == 0][0]
+    t_finish_1 = [t for ev, rid, t in srv.log if ev == "finish" and rid == 1][0]
+    assert t_admit_1 < t_finish_0 and t_finish_1 < t_finish_0
+    assert res[1].latency < 0.1
+
+
+def test_oversized_request_rejected_and_idle_wait():
+    clk = FakeClock()
+    be = FakeBackend(clk)
+    srv = Server(be, hbm_budget=5, clock=clk, sleep=clk.sleep)
+    try:
+        srv.serve(_reqs([(0.0, 6, 10)]))
+        raise AssertionError("oversized request accepted")
+    except ValueError:
+        pass
+    res = srv.serve(_reqs([(2.0, 1, 4)]))                 # server idles until the arrival
+    assert res[0].admitted >= 2.0
+    s = summarize(res)
+    assert s["shots"] == 1 and s["p99_s"] >= s["p50_s"] > 0
