@@ -252,8 +252,13 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     # ---------------- device-resident timed region ----------------
+    # one dedicated stream carries the library's work and the timing events
+    bench_stream = torch.cuda.Stream()
+    bench_stream.wait_stream(torch.cuda.current_stream())
+    torch.cuda.set_stream(bench_stream)
     s = Solver(p["shape"], p["spacing"], p["so"], p["dt"], "acoustic", device=True, profile=True,
                kernel=args.kernel)
+    assert s.stream.cuda_stream == bench_stream.cuda_stream
     s.set_sources(dev(p["src_coords"]), dev(p["wavelet"]))
     if w["nrec"]:
         s.set_receivers(dev(p["rec_coords"]))

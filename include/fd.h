@@ -156,6 +156,31 @@ int64_t fd_steps_done(const fd_ctx *ctx);
  */
 fd_status fd_profile(fd_ctx *ctx, int64_t *launches, double *stencil_ms);
 
+/*
+ * Full-waveform-inversion support (the spec differentiation pattern on
+ * the §6.2.1 operator).  Device fields in the library's padded layout:
+ * fd_field_elems floats each (zero halo included), device pointers.
+ *
+ * fd_snapshot: copy the current level u^n and the previous level u^{n-1} of
+ *   ctx into dst_cur / dst_prev (either may be NULL); asynchronous on the
+ *   context stream.  A checkpoint of the forward wavefield.
+ * fd_restore: copy them back (step counter unchanged: use fd_set_step).
+ * fd_imaging: imaging condition of the adjoint-state gradient,
+ *     g[i] += scale · ν(i) · (u_next(i) − 2 u_cur(i) + u_prev(i))
+ *   over the interior points, where ν is the current level of the adjoint
+ *   context adj and u_next/u_cur/u_prev are snapshots (padded) of the forward
+ *   context at steps n+1, n, n-1; g is dense [n0][n1][n2] float32 on the
+ *   device.  With adj stepping the adjoint recursion (the forward scheme run
+ *   backwards with the receiver residuals injected), scale = -1/dt² gives
+ *   dJ/dm for J = ½||traces - d_obs||² where damp = 0 at the sources and
+ *   receivers.
+ */
+int64_t fd_field_elems(const fd_ctx *ctx);
+fd_status fd_snapshot(fd_ctx *ctx, float *dst_cur, float *dst_prev);
+fd_status fd_restore(fd_ctx *ctx, const float *src_cur, const float *src_prev);
+fd_status fd_imaging(fd_ctx *adj, float *g, const float *u_next, const float *u_cur,
+                     const float *u_prev, double scale);
+
 /* Name of the stencil kernel variant fd_run launches (static string). */
 const char *fd_kernel_name(const fd_ctx *ctx);
 

@@ -58,6 +58,10 @@ SIGNATURES = {
     "fd_profile": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double)]),
     "fd_kernel_name": (ctypes.c_char_p, [_vp]),
     "fd_kernel_launches": (_i64, [_vp]),
+    "fd_field_elems": (_i64, [_vp]),
+    "fd_snapshot": (ctypes.c_int, [_vp, _vp, _vp]),
+    "fd_restore": (ctypes.c_int, [_vp, _vp, _vp]),
+    "fd_imaging": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_double]),
     "fd_destroy": (None, [_vp]),
     "fd_last_error": (ctypes.c_char_p, [_vp]),
     "fd_weights": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
@@ -265,6 +269,23 @@ def fd_footprint_bytes(shape, space_order, nrec, nt, nsrc=1):
     nd = len(shape)
     shp = (_i64 * nd)(*[int(x) for x in shape])
     return int(load().fd_footprint_bytes(nd, shp, int(space_order), int(nrec), int(nt), int(nsrc)))
+
+
+def fd_field_elems(ctx):
+    return int(load().fd_field_elems(ctx))
+
+
+def fd_snapshot(ctx, dst_cur, dst_prev=None):
+    _check(ctx, load().fd_snapshot(ctx, _out_ptr(dst_cur), _out_ptr(dst_prev)))
+
+
+def fd_restore(ctx, src_cur, src_prev):
+    _check(ctx, load().fd_restore(ctx, _ptr(src_cur, []), _ptr(src_prev, [])))
+
+
+def fd_imaging(adj, g, u_next, u_cur, u_prev, scale):
+    _check(adj, load().fd_imaging(adj, _out_ptr(g), _ptr(u_next, []), _ptr(u_cur, []),
+                                  _ptr(u_prev, []), float(scale)))
 
 
 def fd_destroy(ctx):

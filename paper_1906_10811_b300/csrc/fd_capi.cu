@@ -987,6 +987,41 @@ fd_status fd_profile(fd_ctx *c, int64_t *launches, double *stencil_ms) {
 
 const char *fd_kernel_name(const fd_ctx *c) { return c ? c->kernel_name : "none"; }
 
+int64_t fd_field_elems(const fd_ctx *c) { return c ? c->g.total : -1; }
+
+fd_status fd_snapshot(fd_ctx *c, float *dst_cur, float *dst_prev) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  const size_t bytes = (size_t)c->g.total * sizeof(float);
+  if (dst_cur) CU(cudaMemcpyAsync(dst_cur, c->u[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
+  if (dst_prev)
+    CU(cudaMemcpyAsync(dst_prev, c->u[c->cur ^ 1], bytes, cudaMemcpyDeviceToDevice, c->stream));
+  return FD_OK;
+}
+
+fd_status fd_restore(fd_ctx *c, const float *src_cur, const float *src_prev) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  if (!src_cur || !src_prev) return fail(c, FD_EINVAL, "both levels are needed");
+  const size_t bytes = (size_t)c->g.total * sizeof(float);
+  CU(cudaMemcpyAsync(c->u[c->cur], src_cur, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->u[c->cur ^ 1], src_prev, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  return FD_OK;
+}
+
+fd_status fd_imaging(fd_ctx *adj, float *g, const float *u_next, const float *u_cur,
+                     const float *u_prev, double scale) {
+  fd_ctx *c = adj;
+  fd_status st = check_usable(c);
+  if (st) return st;
+  if (!g || !u_next || !u_cur || !u_prev) return fail(c, FD_EINVAL, "NULL field");
+  const int64_t n = (int64_t)c->g.n0 * c->g.n1 * c->g.n2;
+  k_imaging<<<blocks_for(n, 256), 256, 0, c->stream>>>(g, c->u[c->cur], u_next, u_cur, u_prev,
+                                                        c->g, (float)scale);
+  CHECK_LAUNCH();
+  return FD_OK;
+}
+
 int64_t fd_kernel_launches(const fd_ctx *c) { return c ? c->launches : -1; }
 
 void fd_destroy(fd_ctx *c) {

@@ -270,3 +270,26 @@ __global__ void k_interp_batch(const int2 *__restrict__ e, int n, const MemberDe
 }
 
 }  // namespace fdk
+
+namespace fdk {
+
+// FWI imaging condition: g[i] += s · ν(i) · (u⁺(i) − 2u(i) + u⁻(i)) over the
+// interior points (g dense, the rest padded), the discrete cross-correlation
+// of the adjoint field with the second time difference of the forward field.
+__global__ void k_imaging(float *__restrict__ g, const float *__restrict__ nu,
+                          const float *__restrict__ up1, const float *__restrict__ u0,
+                          const float *__restrict__ um1, Geom geo, float scale) {
+  const int64_t n = (int64_t)geo.n0 * geo.n1 * geo.n2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % geo.n2);
+    const int64_t r = i / geo.n2;
+    const int y = (int)(r % geo.n1);
+    const int z = (int)(r / geo.n1);
+    const int64_t p = gidx(geo, z, y, x);
+    const float d2 = (up1[p] - u0[p]) - (u0[p] - um1[p]);
+    g[i] = fmaf(scale * nu[p], d2, g[i]);
+  }
+}
+
+}  // namespace fdk

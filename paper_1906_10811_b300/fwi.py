@@ -1,0 +1,194 @@
+"""Full-waveform-inversion gradient on the device (adjoint state, checkpointing).
+
+J(m) = ½ Σ_n ||P_r u^n(m) − d_obs^n||² for one acoustic shot.  The gradient
+comes from the exact adjoint of the discrete leapfrog: with ν = a·λ
+(a = dt²/(m+σ)) the adjoint recursion is the forward scheme run backwards,
+
+    ν^k = a·L ν^{k+1} + b·ν^{k+1} − c·ν^{k+2} + a·P_rᵀ r^k,     k = N .. 1,
+
+so the adjoint is the library's own solver with the receivers acting as
+sources (wavelet = the residual, time reversed; where damp = 0 the injection
+w·dt²/m equals a·w), and
+
+    dJ/dm = −(1/dt²) Σ_n ν^{n+1} ⊙ (u^{n+1} − 2u^n + u^{n−1}),
+
+accumulated by the library's imaging-condition kernel (fd_imaging).  The
+forward wavefield is needed backwards in time: it is checkpointed every k
+steps (fd_snapshot) and each block of k steps is recomputed from its
+checkpoint while the adjoint sweeps it.  ``choose_checkpoint_interval`` picks
+k from the device memory available.  Every arithmetic step runs in CUDA
+kernels; this module orders them.
+"""
+
+import math
+
+import numpy as np
+
+from . import binding as B
+from .solver import Solver
+
+
+def _dev():
+    import torch
+    return torch
+
+
+def choose_checkpoint_interval(nt, field_bytes, budget_bytes):
+    """Largest k whose memory fits: (k + 2) block levels + 2·ceil(nt/k) checkpoint levels.
+
+    k = nt keeps every level (no recompute beyond one pass)."""
+    best = 1
+    for k in range(1, nt + 1):
+        need = (k + 2 + 2 * math.ceil(nt / k)) * field_bytes
+        if need <= budget_bytes:
+            best = k
+    return best
+
+
+def _check_sparse_undamped(p):
+    """The adjoint identities used here need damp = 0 at every sparse corner node."""
+    damp = np.asarray(p["damp"]) if p.get("damp") is not None else None
+    if damp is None:
+        return
+    shape, h = p["shape"], p["spacing"]
+    for c in list(p["src_coords"]) + list(p["rec_coords"]):
+        idx, frac = [], []
+        for d, (n, hd) in enumerate(zip(shape, h)):
+            x = min(max(float(c[d]) / hd, 0.0), n - 1.0)
+            i = min(int(math.floor(x)), n - 2)
+            idx.append((i, i + 1))
+            frac.append((1.0 - (x - i), x - i))
+        for corner in np.ndindex(*(2,) * len(shape)):
+            if any(frac[d][corner[d]] == 0.0 for d in range(len(shape))):
+                continue                                   # zero-weight corner
+            node = tuple(idx[d][corner[d]] for d in range(len(shape)))
+            if damp[node] != 0.0:
+                raise ValueError("sources and receivers must lie where damp = 0")
+
+
+def forward_traces(p, m=None):
+    """Traces [nt+1][nrec] (torch, device) of shot p with model m (torch or numpy)."""
+    torch = _dev()
+    mm = p["m"] if m is None else m
+    with Solver(p["shape"], p["spacing"], p["so"], p["dt"], "acoustic", device=True) as s:
+        s.set_model(torch.as_tensor(mm, dtype=torch.float32, device="cuda"),
+                    torch.as_tensor(p["damp"], dtype=torch.float32, device="cuda"))
+        s.set_sources(torch.as_tensor(p["src_coords"], device="cuda"),
+                      torch.as_tensor(p["wavelet"], device="cuda"))
+        s.set_receivers(torch.as_tensor(p["rec_coords"], device="cuda"))
+        s.run(p["nt"])
+        _, rec = s.read(field=False)
+    return rec
+
+
+def gradient(p, d_obs, m=None, k=None, memory_budget=None):
+    """(J, dJ/dm) for shot p (fdsynth.acoustic_problem layout) against d_obs.
+
+    m: model (defaults to p["m"]); k: checkpoint interval (None: chosen from
+    the free device memory or ``memory_budget`` bytes).  Returns a float and a
+    torch tensor shaped like m on the device.
+    """
+    torch = _dev()
+    _check_sparse_undamped(p)
+    caller = torch.cuda.current_stream()
+    work = torch.cuda.Stream()            # both contexts and every copy on one stream
+    work.wait_stream(caller)
+    with torch.cuda.stream(work):
+        J, g = _gradient_on_stream(p, d_obs, m, k, memory_budget)
+    caller.wait_stream(work)
+    return J, g
+
+
+def _gradient_on_stream(p, d_obs, m, k, memory_budget):
+    torch = _dev()
+    nt, dt = p["nt"], p["dt"]
+    mm = torch.as_tensor(p["m"] if m is None else m, dtype=torch.float32, device="cuda")
+    damp = torch.as_tensor(p["damp"], dtype=torch.float32, device="cuda")
+    src = torch.as_tensor(p["src_coords"], device="cuda")
+    wav = torch.as_tensor(p["wavelet"], device="cuda")
+    rc = torch.as_tensor(p["rec_coords"], device="cuda")
+    d_obs = torch.as_tensor(d_obs, dtype=torch.float32, device="cuda")
+
+    fwd = Solver(p["shape"], p["spacing"], p["so"], dt, "acoustic", device=True)
+    adj = Solver(p["shape"], p["spacing"], p["so"], dt, "acoustic", device=True)
+    try:
+        fwd.set_model(mm, damp)
+        fwd.set_sources(src, wav)
+        fwd.set_receivers(rc)
+        elems = B.fd_field_elems(fwd.ctx)
+        if k is None:
+            if memory_budget is None:
+                free, _ = torch.cuda.mem_get_info()
+                memory_budget = int(0.6 * free)
+            k = choose_checkpoint_interval(nt, elems * 4, memory_budget)
+        k = max(1, min(int(k), nt))
+        nblk = math.ceil(nt / k)
+        ck = torch.empty((nblk, 2, elems), dtype=torch.float32, device="cuda")
+        # forward sweep with checkpoints (u^{ck}, u^{ck-1}) at the start of each block
+        for c in range(nblk):
+            B.fd_snapshot(fwd.ctx, ck[c, 0], ck[c, 1])
+            fwd.run(min(k, nt - c * k))
+        _, rec = fwd.read(field=False)
+        r = rec - d_obs
+        J = 0.5 * float(torch.sum(r.double() * r.double()))
+        # adjoint: sources at the receivers, wavelet row j = r[nt - j]
+        adj.set_model(mm, damp)
+        adj.set_sources(rc, torch.flip(r[1:], dims=(0,)).contiguous())
+        B.fd_set_receivers(fwd.ctx, 0, None)
+        g = torch.zeros(p["shape"], dtype=torch.float32, device="cuda")
+        blk = torch.empty((k + 2, elems), dtype=torch.float32, device="cuda")
+        scale = -1.0 / (dt * dt)
+        for c in range(nblk - 1, -1, -1):
+            n0, n1 = c * k, min((c + 1) * k, nt)
+            # recompute u^{n0-1} .. u^{n1} into blk[0 .. n1-n0+1]
+            B.fd_restore(fwd.ctx, ck[c, 0], ck[c, 1])
+            fwd.set_step(n0)
+            blk[0].copy_(ck[c, 1])
+            blk[1].copy_(ck[c, 0])
+            for t in range(n0, n1):
+                fwd.run(1)
+                B.fd_snapshot(fwd.ctx, blk[t - n0 + 2])
+            for n in range(n1 - 1, n0 - 1, -1):       # adjoint step nt-1-n gives ν^{n+1}
+                adj.run(1)
+                i = n - n0 + 1                          # blk[i] = u^n
+                B.fd_imaging(adj.ctx, g, blk[i + 1], blk[i], blk[i - 1], scale)
+        torch.cuda.current_stream().synchronize()
+        return J, g
+    finally:
+        fwd.close()
+        adj.close()
+
+
+class FWIObjective:
+    """``torch.autograd.Function`` wrapper: J = FWIObjective.apply(m, p, d_obs, k).
+
+    The forward pass computes J and, with it, dJ/dm (the adjoint sweep reuses
+    the checkpoints of the same forward run); backward scales the stored
+    gradient by the incoming gradient.
+    """
+
+    _fn = None
+
+    @classmethod
+    def function(cls):
+        if cls._fn is None:
+            torch = _dev()
+
+            class _F(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, m, p, d_obs, k):
+                    J, g = gradient(p, d_obs, m=m.detach(), k=k)
+                    ctx.save_for_backward(g)
+                    return torch.tensor(J, dtype=torch.float64, device=m.device)
+
+                @staticmethod
+                def backward(ctx, grad_out):
+                    (g,) = ctx.saved_tensors
+                    return (grad_out.to(g.dtype) * g), None, None, None
+
+            cls._fn = _F
+        return cls._fn
+
+    @classmethod
+    def apply(cls, m, p, d_obs, k=None):
+        return cls.function().apply(m, p, d_obs, k)

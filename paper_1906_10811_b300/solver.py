@@ -1,6 +1,10 @@
 """``Solver``: a Python object over one fd_ctx (marshalling only; all work runs in
 the CUDA library).  Host mode takes and returns numpy arrays; device mode
-(``device=True``) takes and returns torch CUDA tensors on a torch stream."""
+(``device=True``) takes and returns torch CUDA tensors.  Device mode runs on the
+caller's current torch stream, or, when that is the legacy default stream
+(which cannot be captured into graphs), on a private stream that is ordered
+after the caller's stream before every call and before the caller's stream
+after every call."""
 
 import numpy as np
 
@@ -25,10 +29,16 @@ class Solver:
         self.ndim = len(self.shape)
         self.device = bool(device)
         cuda_stream = None
+        self._private = False
         if self.device:
             import torch
             self._torch = torch
             s = stream if stream is not None else torch.cuda.current_stream()
+            if s.cuda_stream == 0:
+                # the legacy default stream cannot host graph capture: work on a
+                # private stream, ordered with the caller's stream at every call
+                s = torch.cuda.Stream()
+                self._private = True
             cuda_stream = s.cuda_stream
             self.stream = s
         opt = B.options(nu=nu, cuda_stream=cuda_stream, device_ptrs=self.device, use_graphs=graphs,
@@ -54,19 +64,35 @@ class Solver:
     def __exit__(self, *exc):
         self.close()
 
+    # -- stream ordering (device mode on a private stream) ------------------
+    def _in(self):
+        """The solver's stream waits for work already queued by the caller."""
+        if self._private:
+            self.stream.wait_stream(self._torch.cuda.current_stream())
+
+    def _out(self):
+        """The caller's stream waits for the solver's work."""
+        if self._private:
+            self._torch.cuda.current_stream().wait_stream(self.stream)
+
     # -- inputs ------------------------------------------------------------
     def set_model(self, m, damp=None):
+        self._in()
         B.fd_set_model(self.ctx, m, damp)
 
     def set_field(self, u, u_prev=None):
+        self._in()
         B.fd_set_field(self.ctx, u, u_prev)
+        self._out()
 
     def set_sources(self, coords, wavelets):
+        self._in()
         n = 0 if coords is None else len(coords)
         nt = 0 if wavelets is None else int(wavelets.shape[0])
         B.fd_set_sources(self.ctx, n, coords, nt, wavelets)
 
     def set_receivers(self, coords):
+        self._in()
         self.nrec = 0 if coords is None else len(coords)
         B.fd_set_receivers(self.ctx, self.nrec, coords)
 
@@ -75,7 +101,9 @@ class Solver:
 
     # -- run / outputs -----------------------------------------------------
     def run(self, nt):
+        self._in()
         B.fd_run(self.ctx, nt)
+        self._out()
         return self
 
     @property
@@ -97,14 +125,18 @@ class Solver:
 
     def read(self, field=True, traces=True):
         """(u^n, traces [n+1][nrec]); either is None when not requested or absent."""
+        self._in()
         u = self._empty(self.shape) if field else None
         rec = self._empty((self.steps + 1, self.nrec)) if traces and self.nrec else None
         B.fd_read(self.ctx, u, rec)
+        self._out()
         return u, rec
 
     def read_prev(self):
+        self._in()
         u = self._empty(self.shape)
         B.fd_read_prev(self.ctx, u)
+        self._out()
         return u
 
     def profile(self):

@@ -1,0 +1,124 @@
+"""FWI on the device: the adjoint solver passes the dot-product test against the
+forward modelling operator, the gradient matches the FP64 oracle's
+adjoint-state gradient (itself pinned by finite differences), passes a Taylor
+test, does not depend on the checkpoint interval, and comes back through
+torch.autograd."""
+
+import numpy as np
+import pytest
+
+import fdsynth
+from helpers import rel_l2
+from oracle import fwi as ofwi
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1906_10811_b300 import build
+    build.build()
+
+
+def _shot(shape=(30, 34, 38), nt=120, seed=0, nrec=16, nsrc=1):
+    nd = len(shape)
+    p = fdsynth.acoustic_problem(n=shape, ndim=nd, so=8, nbl=5, nt=nt, nrec=nrec, seed=seed, f0=0.03)
+    if nsrc > 1:
+        p["src_coords"] = fdsynth.random_points(shape, p["spacing"], nsrc, seed=seed + 5, margin=7.0)
+        p["wavelet"] = np.repeat(p["wavelet"], nsrc, axis=1) * np.linspace(0.5, 1.5, nsrc,
+                                                                            dtype=np.float32)
+    return p
+
+
+def _true_model(p):
+    """The observed data come from the model with a smooth positive anomaly."""
+    shape = p["shape"]
+    g = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")
+    r2 = sum((x - (n - 1) / 2.0) ** 2 for x, n in zip(g, shape))
+    return (p["m"] * (1.0 + 0.08 * np.exp(-r2 / 30.0))).astype(np.float32)
+
+
+def test_adjoint_dot_product():
+    """<F x, y> = <x, Fᵀ y> for F: source wavelets -> receiver traces."""
+    import torch
+    from paper_1906_10811_b300 import Solver
+    p = _shot(nsrc=3)
+    nt = p["nt"]
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((nt, 3)).astype(np.float32)
+    y = rng.standard_normal((nt + 1, len(p["rec_coords"]))).astype(np.float32)
+    with Solver(p["shape"], p["spacing"], 8, p["dt"], "acoustic") as s:
+        s.set_model(p["m"], p["damp"])
+        s.set_sources(p["src_coords"], x)
+        s.set_receivers(p["rec_coords"])
+        s.run(nt)
+        _, fx = s.read(field=False)
+    with Solver(p["shape"], p["spacing"], 8, p["dt"], "acoustic") as a:
+        a.set_model(p["m"], p["damp"])
+        a.set_sources(p["rec_coords"], np.ascontiguousarray(y[1:][::-1]))
+        a.set_receivers(p["src_coords"])
+        a.run(nt)
+        _, sa = a.read(field=False)
+    fty = sa[nt - np.arange(nt)]                       # s_n = rec_a[nt - n]
+    lhs = float(np.sum(fx.astype(np.float64) * y))
+    rhs = float(np.sum(x.astype(np.float64) * fty))
+    assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), abs(rhs))
+
+
+def test_gradient_matches_oracle():
+    from paper_1906_10811_b300 import fwi
+    p = _shot()
+    d_obs = fwi.forward_traces(p, _true_model(p)).cpu().numpy()
+    J, g = fwi.gradient(p, d_obs)
+    Jo, go = ofwi.gradient(p["m"], p["damp"], p["dt"], p["spacing"], 8, p["nt"], p["src_coords"],
+                           p["wavelet"], p["rec_coords"], d_obs)
+    assert abs(J - Jo) <= 1e-4 * Jo
+    assert rel_l2(g.cpu().numpy(), go) <= 1e-4
+
+
+def test_checkpoint_interval_does_not_change_the_gradient():
+    from paper_1906_10811_b300 import fwi
+    p = _shot(shape=(26, 24, 29), nt=60)
+    d_obs = fwi.forward_traces(p, _true_model(p)).cpu().numpy()
+    ref = fwi.gradient(p, d_obs, k=60)[1].cpu().numpy()
+    for k in (1, 7, 25):
+        assert np.array_equal(fwi.gradient(p, d_obs, k=k)[1].cpu().numpy(), ref)
+    assert fwi.choose_checkpoint_interval(1000, 100, 100 * 1004) == 1000   # nt + 2 + 2 levels
+    assert fwi.choose_checkpoint_interval(1000, 100, 100 * 100) < 100
+
+
+def test_taylor_second_order():
+    """J(m + h δm) − J(m) − h <g, δm> shrinks by about 4 when h halves."""
+    from paper_1906_10811_b300 import fwi
+    p = _shot(shape=(28, 26, 30), nt=100)
+    d_obs = fwi.forward_traces(p, _true_model(p)).cpu().numpy()
+    J0, g = fwi.gradient(p, d_obs)
+    g = g.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(4)
+    dm = (rng.standard_normal(p["shape"]) * p["m"] * 0.02).astype(np.float64)
+    rem = []
+    for h in (1.0, 0.5, 0.25):
+        mh = (p["m"] + h * dm).astype(np.float32)
+        r = fwi.forward_traces(p, mh).cpu().numpy().astype(np.float64) - d_obs
+        Jh = 0.5 * np.sum(r * r)
+        rem.append(abs(Jh - J0 - h * np.sum(g * dm)))
+    first = [abs(0.5 * np.sum((fwi.forward_traces(p, (p["m"] + h * dm).astype(np.float32)).cpu().numpy() - d_obs) ** 2) - J0)
+             for h in (1.0, 0.5, 0.25)]
+    for a, b in zip(rem, rem[1:]):
+        assert 3.0 < a / b < 5.0, rem
+    assert rem[-1] < 0.1 * first[-1]
+
+
+def test_autograd_returns_the_gradient():
+    import torch
+    from paper_1906_10811_b300 import fwi
+    p = _shot(shape=(22, 24, 26), nt=50)
+    d_obs = fwi.forward_traces(p, _true_model(p)).cpu().numpy()
+    m = torch.tensor(p["m"], device="cuda", requires_grad=True)
+    J = fwi.FWIObjective.apply(m, p, d_obs, None)
+    J.backward()
+    _, g = fwi.gradient(p, d_obs)
+    assert torch.equal(m.grad, g)
+    assert abs(float(J) - fwi.gradient(p, d_obs)[0]) <= 1e-12 * float(J)
