@@ -247,6 +247,15 @@ double fd_stability_symbol(int space_order);
 const char *fd_version(void);
 
 /*
+ * Failure-detection self-test: launch a kernel that waits, with the same
+ * bounded-wait routine the pipelined stencil uses on its mbarriers, on a
+ * barrier phase that nothing completes, with a budget of budget_ms (0, 10000]
+ * (converted with the SM clock rate).  *expired = 1 when the wait gave up as it
+ * must; *waited_ms (may be NULL) = how long it waited.  Faults nothing.
+ */
+fd_status fd_selftest_bounded_wait(double budget_ms, int *expired, double *waited_ms);
+
+/*
  * No-allocation acoustic run (the paper has no counterpart; this is a service
  * entry point of the library).
  *

@@ -67,6 +67,8 @@ SIGNATURES = {
     "fd_weights": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "fd_stability_symbol": (ctypes.c_double, [ctypes.c_int]),
     "fd_version": (ctypes.c_char_p, []),
+    "fd_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                                ctypes.POINTER(ctypes.c_double)]),
     "fd_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _vp]),
     "fd_batch_add": (ctypes.c_int, [_vp, _vp]),
     "fd_batch_remove": (ctypes.c_int, [_vp, _vp]),
@@ -307,6 +309,16 @@ def fd_weights(space_order):
 
 def fd_stability_symbol(space_order):
     return float(load().fd_stability_symbol(int(space_order)))
+
+
+def fd_selftest_bounded_wait(budget_ms):
+    """(expired, waited_ms) of a bounded wait on a barrier nothing completes."""
+    ex = ctypes.c_int()
+    ms = ctypes.c_double()
+    st = load().fd_selftest_bounded_wait(float(budget_ms), ctypes.byref(ex), ctypes.byref(ms))
+    if st != FD_OK:
+        raise FdError(st, load().fd_last_error(None).decode())
+    return bool(ex.value), float(ms.value)
 
 
 def fd_version():

@@ -573,6 +573,28 @@ void fd_options_default(fd_options *o) {
 
 const char *fd_version(void) { return "fd_b300 0.1 (sm_103a)"; }
 
+fd_status fd_selftest_bounded_wait(double budget_ms, int *expired, double *waited_ms) {
+  fd_ctx *c = nullptr;
+  if (!expired || !(budget_ms > 0.0) || budget_ms > 10000.0)
+    return fail(nullptr, FD_EINVAL, "budget_ms must be in (0, 10000]");
+  int dev = 0, khz = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+  int *d_out = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc((void **)&d_out, 2 * sizeof(int));
+  if (e == cudaSuccess) {
+    k_selftest_wait<<<1, 32>>>((long long)(budget_ms * (double)khz), d_out);
+    e = cudaGetLastError();
+  }
+  int out[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(out, d_out, sizeof out, cudaMemcpyDeviceToHost);
+  if (d_out) cudaFree(d_out);
+  if (e != cudaSuccess) return fail(c, FD_ECUDA, "self-test: %s", cudaGetErrorString(e));
+  *expired = out[0];
+  if (waited_ms) *waited_ms = (double)out[1] * 1024.0 / (double)khz;
+  return FD_OK;
+}
+
 fd_status fd_weights(int space_order, double *w) {
   if (!w) return FD_EINVAL;
   return lib_weights(space_order, w) ? FD_OK : FD_EINVAL;

@@ -87,12 +87,31 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait for the phase of the given parity; false if the budget ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          long long budget = kWaitBudget) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > kWaitBudget) return false;
+    if (clock64() - t0 > budget) return false;
   return true;
+}
+
+// Self-test of the bounded wait: phase 0 of a fresh barrier that nothing
+// arrives on never completes, so the wait must give up after `budget` cycles.
+__global__ void k_selftest_wait(long long budget, int *out) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const long long t0 = clock64();
+  const bool completed = mbar_wait(&bar, 0, budget);
+  const long long waited = clock64() - t0;
+  if (threadIdx.x == 0) {
+    out[0] = completed ? 0 : 1;
+    out[1] = (int)(waited >> 10);  // kilo-cycles
+  }
 }
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
                                             uint64_t *bar) {
