@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--so", type=int, default=None)
     ap.add_argument("--nt", type=int, default=None)
     ap.add_argument("--kernel", default="auto", choices=["auto", "plain", "tma"])
+    ap.add_argument("--tile", default="auto", choices=["auto", "default"],
+                    help="auto: the autotuner picks the pipelined kernel's tile configuration "
+                         "before the timed region; default: the built-in one")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -262,6 +265,13 @@ def run_ours(args):
     s.set_sources(dev(p["src_coords"]), dev(p["wavelet"]))
     if w["nrec"]:
         s.set_receivers(dev(p["rec_coords"]))
+    tile, tune_tried = None, None
+    if s.kernel_name.startswith("stencil3d_tma"):
+        if args.tile == "auto":
+            s.set_model(m_d, damp_d)
+            _, tried = s.autotune(reps=5)
+            tune_tried = len(tried)
+        tile = s.tile_config
 
     def shot():
         s.set_model(m_d, damp_d)
@@ -315,7 +325,7 @@ def run_ours(args):
         h2d = m_h.nbytes + damp_h.nbytes + zero_h.nbytes + src_h.nbytes + wav_h.nbytes + rc_h.nbytes
         d2h = (nt + 1) * w["nrec"] * 4
         se = Solver(p["shape"], p["spacing"], p["so"], p["dt"], "acoustic", device=False,
-                    kernel=args.kernel)
+                    kernel=args.kernel, autotune=tile is not None and args.tile == "auto")
         from paper_1906_10811_b300 import binding as B
 
         def shot_e2e():
@@ -350,7 +360,10 @@ def run_ours(args):
                 "unit": "GPts/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": config_of(args, w, kernel_name), "roofline": roofline,
+                "config": dict(config_of(args, w, kernel_name), tile=tile,
+                               tile_choice=("autotuned over %d configurations" % tune_tried
+                                            if tune_tried else "default")),
+                "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -82,6 +82,9 @@ typedef struct {
   int profile;        /* 1: time every stencil launch with CUDA events (fd_profile);
                          steps are launched one by one instead of by graph */
   int kernel;         /* fd_kernel; default FD_KERNEL_AUTO */
+  int autotune;       /* 1: fd_create runs fd_autotune on the pipelined kernel (its
+                         choice is cached per grid shape, space order and equation
+                         for the process); 0 (default): the default tile */
 } fd_options;
 
 /* Fill *opt with the defaults above. */
@@ -181,6 +184,54 @@ fd_status fd_restore(fd_ctx *ctx, const float *src_cur, const float *src_prev);
 fd_status fd_imaging(fd_ctx *adj, float *g, const float *u_next, const float *u_cur,
                      const float *u_prev, double scale);
 
+/*
+ * Tile configuration of the pipelined 3-D kernel (FD_KERNEL_TMA/AUTO on 3-D
+ * grids).  The paper leaves tiling strategy to the OPS library (§2.2) and
+ * cites stencil compilers that block the iteration space per thread to save
+ * shared-memory reads (§2.3.3, loop aggregation); here the tile shape and the
+ * z-streaming depth are chosen per problem by timing.  Every configuration computes
+ * bitwise the same result: a point's update is the same arithmetic whatever
+ * tile holds it.
+ *
+ *   tile_x       points per tile along x (32: one warp of lanes; fixed)
+ *   tile_y       points per tile along y: 8 consumer warps × rows per thread,
+ *                16 or 32
+ *   zblock       z-streaming depth: consecutive planes a CTA streams on one
+ *                tile before it moves to the next (the work is cut into
+ *                z-blocks of this height; each cut costs 2R re-read planes)
+ *   ctas_per_sm  resident CTAs per SM the persistent grid is sized for
+ *   us_per_step  stencil launch time measured by fd_autotune (µs; 0 when
+ *                the configuration was set, not measured)
+ *
+ * fd_get_tile_config: the configuration fd_run uses; FD_EUNSUPPORTED when the
+ *   context runs the plain kernel.
+ * fd_set_tile_config: use cfg (tile_x 32 or 0, tile_y 16 or 32 or 0 for the
+ *   default, zblock ≥ 0 with 0 meaning one CTA's share, ctas_per_sm ≥ 0 with
+ *   0 meaning as many as fit); FD_EINVAL for anything else, leaving the
+ *   current configuration in place.  Captured graphs are dropped.
+ * fd_autotune: time every configuration of the search space (tile_y in
+ *   {16, 32} × ctas_per_sm in 1..fit × zblock in {share/2, share, 2·share},
+ *   reps ≥ 1 timed launches each after two warm-up launches, median taken),
+ *   then use the fastest.  The candidate launches read the current fields
+ *   and write a scratch field allocated for the call, so the solution is not
+ *   disturbed; sources are not injected during the trials.  Synchronises the
+ *   context stream.  tried (may be NULL) receives up to max_tried measured
+ *   configurations, *ntried (may be NULL) their number; best (may be NULL)
+ *   the chosen one.  FD_ENOMEM when the scratch field does not fit.
+ */
+typedef struct {
+  int tile_x;
+  int tile_y;
+  int zblock;
+  int ctas_per_sm;
+  double us_per_step;
+} fd_tile_config;
+
+fd_status fd_get_tile_config(const fd_ctx *ctx, fd_tile_config *cfg);
+fd_status fd_set_tile_config(fd_ctx *ctx, const fd_tile_config *cfg);
+fd_status fd_autotune(fd_ctx *ctx, int reps, fd_tile_config *best, fd_tile_config *tried,
+                      int max_tried, int *ntried);
+
 /* Name of the stencil kernel variant fd_run launches (static string). */
 const char *fd_kernel_name(const fd_ctx *ctx);
 
@@ -208,7 +259,9 @@ void fd_destroy(fd_ctx *ctx);
  * fd_batch_add: ctx must be FD_ACOUSTIC, of the batch's space order, with a
  *   model set, on the batch's device; 3-D members need the pipelined kernel
  *   and must agree on whether their spacing is isotropic.  The batch borrows
- *   the context: remove it before fd_destroy.
+ *   the context: remove it before fd_destroy.  The batched kernel runs the
+ *   default tile, so fd_batch_run puts a 3-D member with another tile height
+ *   back to the default configuration (fd_set_tile_config) before its tick.
  * fd_batch_run: nticks ≥ 0 steps of every member (FD_EINVAL if a member would
  *   pass its wavelet); asynchronous on the batch stream.
  * fd_batch_remove: synchronises the batch stream and drops the member.

@@ -33,7 +33,16 @@ class FdError(RuntimeError):
 class fd_options(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
                 ("device_ptrs", ctypes.c_int), ("use_graphs", ctypes.c_int),
-                ("profile", ctypes.c_int), ("kernel", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
+
+
+class fd_tile_config(ctypes.Structure):
+    _fields_ = [("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("zblock", ctypes.c_int),
+                ("ctas_per_sm", ctypes.c_int), ("us_per_step", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _lib = None
@@ -57,6 +66,11 @@ SIGNATURES = {
     "fd_steps_done": (_i64, [_vp]),
     "fd_profile": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double)]),
     "fd_kernel_name": (ctypes.c_char_p, [_vp]),
+    "fd_get_tile_config": (ctypes.c_int, [_vp, ctypes.POINTER(fd_tile_config)]),
+    "fd_set_tile_config": (ctypes.c_int, [_vp, ctypes.POINTER(fd_tile_config)]),
+    "fd_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(fd_tile_config),
+                                   ctypes.POINTER(fd_tile_config), ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_int)]),
     "fd_kernel_launches": (_i64, [_vp]),
     "fd_field_elems": (_i64, [_vp]),
     "fd_snapshot": (ctypes.c_int, [_vp, _vp, _vp]),
@@ -141,7 +155,7 @@ def _out_ptr(x):
 
 
 def options(nu=0.5, cuda_stream=None, device_ptrs=False, use_graphs=True, profile=False,
-            kernel=FD_KERNEL_AUTO):
+            kernel=FD_KERNEL_AUTO, autotune=False):
     o = fd_options()
     load().fd_options_default(ctypes.byref(o))
     o.nu = nu
@@ -150,6 +164,7 @@ def options(nu=0.5, cuda_stream=None, device_ptrs=False, use_graphs=True, profil
     o.use_graphs = int(bool(use_graphs))
     o.profile = int(bool(profile))
     o.kernel = int(kernel)
+    o.autotune = int(bool(autotune))
     return o
 
 
@@ -223,6 +238,30 @@ def fd_profile(ctx):
 
 def fd_kernel_name(ctx):
     return load().fd_kernel_name(ctx).decode()
+
+
+def fd_get_tile_config(ctx):
+    """The pipelined kernel's tile configuration as a dict."""
+    cfg = fd_tile_config()
+    st = load().fd_get_tile_config(ctx, ctypes.byref(cfg))
+    if st != FD_OK:
+        raise FdError(st, "no tile configuration (plain kernel)")
+    return cfg.as_dict()
+
+
+def fd_set_tile_config(ctx, tile_y=0, zblock=0, ctas_per_sm=0, tile_x=0):
+    cfg = fd_tile_config(int(tile_x), int(tile_y), int(zblock), int(ctas_per_sm), 0.0)
+    _check(ctx, load().fd_set_tile_config(ctx, ctypes.byref(cfg)))
+
+
+def fd_autotune(ctx, reps=5, max_tried=64):
+    """Time the tile configurations and use the fastest: (best, tried) as dicts."""
+    best = fd_tile_config()
+    tried = (fd_tile_config * max_tried)()
+    n = ctypes.c_int()
+    _check(ctx, load().fd_autotune(ctx, int(reps), ctypes.byref(best), tried, int(max_tried),
+                                   ctypes.byref(n)))
+    return best.as_dict(), [tried[i].as_dict() for i in range(n.value)]
 
 
 def fd_kernel_launches(ctx):

@@ -13,8 +13,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/fd.h"
@@ -97,6 +100,8 @@ struct fd_ctx {
   StencilFn plain_fn = nullptr;
   TmaPlan tma{};
   bool use_tma = false;
+  bool iso = false;          // equal spacing on all axes (pipelined kernel variant)
+  double tune_us = 0.0;      // stencil µs of the current tile configuration, if measured
   const char *kernel_name = "none";
   // sources
   int nsrc = 0, nt_wav = 0;
@@ -498,7 +503,7 @@ fd_status prepare_fused(fd_ctx *c) {
     }
   }
   if (c->sp_dirty) {
-    const int ty = tma_ty(c->g.R), tiles_x = c->tma.args.tiles_x;
+    const int ty = tma_ty(c->tma.ny), tiles_x = c->tma.args.tiles_x;
     struct E { int64_t key; int idx, x, y, z; };
     std::vector<E> es;
     for (size_t i = 0; i < c->h_src_dense.size(); ++i) {
@@ -555,6 +560,54 @@ void select_kernel(fd_ctx *c) {
 #undef PICK
   c->kernel_name = three ? "stencil3d_plain" : "stencil2d_plain";
 }
+
+// Rebuild the pipelined kernel's plan for another tile configuration; on
+// failure the current plan stays.  Source tables are keyed by tile and the
+// captured graphs hold the old plan, so both are redone.
+fd_status replan(fd_ctx *c, int ny, int per_sm, int zblock) {
+  TmaPlan p{};
+  const char *why = nullptr;
+  cudaError_t e = plan_tma(p, c->g, c->eq == FD_ACOUSTIC ? kAcoustic : kDiffusion, c->iso, c->u,
+                           c->A, c->C, ny, per_sm, zblock, &why);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, e == cudaErrorInvalidValue ? FD_EINVAL : FD_EUNSUPPORTED,
+                "tile configuration: %s", why ? why : cudaGetErrorString(e));
+  }
+  CU(cudaStreamSynchronize(c->stream));
+  drop_graphs(c);
+  c->tma = p;
+  c->sp_dirty = true;
+  c->tune_us = 0.0;
+  return FD_OK;
+}
+
+void tile_of(const fd_ctx *c, fd_tile_config *cfg) {
+  cfg->tile_x = kTmaTX;
+  cfg->tile_y = tma_ty(c->tma.ny);
+  cfg->zblock = c->tma.args.zblock;
+  cfg->ctas_per_sm = c->tma.per_sm;
+  cfg->us_per_step = c->tune_us;
+}
+
+// Autotuner choices for the process, per device, grid, order and equation.
+struct TuneKey {
+  int device, so, eq, iso;
+  int64_t n0, n1, n2;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(device, so, eq, iso, n0, n1, n2) <
+           std::tie(o.device, o.so, o.eq, o.iso, o.n0, o.n1, o.n2);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, fd_tile_config> g_tune_cache;
+
+TuneKey tune_key(const fd_ctx *c) {
+  return TuneKey{c->device, c->so, (int)c->eq, c->iso ? 1 : 0, c->g.n0, c->g.n1, c->g.n2};
+}
+
+fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_config *tried,
+                        int max_tried, int *ntried);
 
 }  // namespace
 
@@ -729,12 +782,16 @@ fd_status fd_create(fd_ctx **out, int ndim, const int64_t *shape, const double *
   c->use_tma = false;
   if (ndim == 3 && o.kernel != FD_KERNEL_PLAIN) {
     const char *why = nullptr;
-    const bool iso = spacing[0] == spacing[1] && spacing[1] == spacing[2];
-    e = plan_tma(c->tma, c->g, eq == FD_ACOUSTIC ? kAcoustic : kDiffusion, iso, c->u, c->A, c->C,
-                 &why);
+    c->iso = spacing[0] == spacing[1] && spacing[1] == spacing[2];
+    e = plan_tma(c->tma, c->g, eq == FD_ACOUSTIC ? kAcoustic : kDiffusion, c->iso, c->u, c->A,
+                 c->C, 0, 0, 0, &why);
     if (e == cudaSuccess) {
       c->use_tma = true;
       c->kernel_name = c->tma.name;
+      if (o.autotune) {
+        st = autotune_impl(c, 5, nullptr, nullptr, 0, nullptr);
+        if (st) return bail(st);
+      }
     } else {
       cudaGetLastError();
       if (o.kernel == FD_KERNEL_TMA) {
@@ -1007,6 +1064,35 @@ fd_status fd_profile(fd_ctx *c, int64_t *launches, double *stencil_ms) {
   return FD_OK;
 }
 
+fd_status fd_get_tile_config(const fd_ctx *c, fd_tile_config *cfg) {
+  if (!c || !cfg) return FD_EINVAL;
+  if (!c->use_tma) return FD_EUNSUPPORTED;
+  tile_of(c, cfg);
+  return FD_OK;
+}
+
+fd_status fd_set_tile_config(fd_ctx *c, const fd_tile_config *cfg) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  if (!cfg) return fail(c, FD_EINVAL, "cfg is NULL");
+  if (!c->use_tma) return fail(c, FD_EUNSUPPORTED, "the plain kernel has no tile configuration");
+  if ((cfg->tile_x != 0 && cfg->tile_x != kTmaTX) || cfg->tile_y % kTmaNW ||
+      (cfg->tile_y != 0 && !tma_ny_supported(cfg->tile_y / kTmaNW)) || cfg->zblock < 0 ||
+      cfg->ctas_per_sm < 0)
+    return fail(c, FD_EINVAL, "tile configuration %dx%d, zblock %d, %d CTAs/SM is not offered",
+                cfg->tile_x, cfg->tile_y, cfg->zblock, cfg->ctas_per_sm);
+  return replan(c, cfg->tile_y / kTmaNW, cfg->ctas_per_sm, cfg->zblock);
+}
+
+fd_status fd_autotune(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_config *tried,
+                      int max_tried, int *ntried) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  if (reps < 1) return fail(c, FD_EINVAL, "reps must be >= 1");
+  if (!c->use_tma) return fail(c, FD_EUNSUPPORTED, "the plain kernel has no tile configuration");
+  return autotune_impl(c, reps, best, tried, max_tried, ntried);
+}
+
 const char *fd_kernel_name(const fd_ctx *c) { return c ? c->kernel_name : "none"; }
 
 int64_t fd_field_elems(const fd_ctx *c) { return c ? c->g.total : -1; }
@@ -1075,6 +1161,118 @@ const char *fd_last_error(const fd_ctx *c) {
 }
 
 }  // extern "C"
+
+namespace {
+
+// Median µs of reps launches of plan p (after two warm-up launches), reading
+// the context's current levels and writing `out`, without sources.
+fd_status time_plan(fd_ctx *c, const TmaPlan &p, float *out, int reps, cudaEvent_t *ev,
+                    double *us) {
+  const int cur = c->cur;
+  for (int i = 0; i < 2 + reps; ++i) {
+    if (i >= 2) CU(cudaEventRecord(ev[i - 2], c->stream));
+    cudaError_t e = launch_tma_step(p, cur, out, c->coef, c->d_err, SparseArgs{}, c->stream);
+    if (e != cudaSuccess) return fail(c, FD_ECUDA, "autotune launch: %s", cudaGetErrorString(e));
+    ++c->launches;
+  }
+  CU(cudaEventRecord(ev[reps], c->stream));
+  CU(cudaEventSynchronize(ev[reps]));
+  std::vector<double> t(reps);
+  for (int i = 0; i < reps; ++i) {
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+    t[i] = 1e3 * ms;
+  }
+  std::sort(t.begin(), t.end());
+  *us = t[reps / 2];
+  return FD_OK;
+}
+
+fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_config *tried,
+                        int max_tried, int *ntried) {
+  if (ntried) *ntried = 0;
+  const TuneKey key = tune_key(c);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end() && !tried) {
+      const fd_tile_config cfg = it->second;
+      fd_status st = replan(c, cfg.tile_y / kTmaNW, cfg.ctas_per_sm, cfg.zblock);
+      if (st) return st;
+      c->tune_us = cfg.us_per_step;
+      if (best) *best = cfg;
+      return FD_OK;
+    }
+  }
+  float *scratch = nullptr;
+  fd_status st = dalloc(c, &scratch, (size_t)c->g.total);
+  if (st) return st;
+  std::vector<cudaEvent_t> ev(reps + 1, nullptr);
+  for (auto &e : ev)
+    if (!st && cudaEventCreate(&e) != cudaSuccess) st = fail(c, FD_ECUDA, "event creation");
+  const int eq = c->eq == FD_ACOUSTIC ? kAcoustic : kDiffusion;
+  const int R = c->so / 2;
+  const int zmin = std::min<int>(c->g.n0, std::max(8, 2 * R));
+  fd_tile_config win{};
+  double win_us = 1e300;
+  int n = 0;
+  for (int ny : {2, 4}) {
+    TmaPlan p{};
+    const char *why = nullptr;
+    if (st || plan_tma(p, c->g, eq, c->iso, c->u, c->A, c->C, ny, 0, 0, &why) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    for (int cps = 1; !st && cps <= p.per_sm_max; ++cps) {
+      TmaPlan q{};
+      if (plan_tma(q, c->g, eq, c->iso, c->u, c->A, c->C, ny, cps, 0, &why) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      const int share = q.args.zblock;
+      int zbs[3] = {std::max(zmin, share / 2), share, std::min<int>(c->g.n0, 2 * share)};
+      for (int k = 0; !st && k < 3; ++k) {
+        if ((k == 0 && zbs[0] >= share) || (k == 2 && zbs[2] <= share)) continue;
+        TmaPlan r{};
+        if (plan_tma(r, c->g, eq, c->iso, c->u, c->A, c->C, ny, cps, zbs[k], &why) !=
+            cudaSuccess) {
+          cudaGetLastError();
+          continue;
+        }
+        double us = 0.0;
+        st = time_plan(c, r, scratch, reps, ev.data(), &us);
+        if (st) break;
+        fd_tile_config cfg{kTmaTX, tma_ty(ny), r.args.zblock, r.per_sm, us};
+        if (tried && n < max_tried) tried[n] = cfg;
+        ++n;
+        if (us < win_us) {
+          win_us = us;
+          win = cfg;
+        }
+      }
+    }
+  }
+  for (auto &e : ev)
+    if (e) cudaEventDestroy(e);
+  dfree(c, scratch);
+  if (st) return st;
+  // a candidate that gave up on a wait leaves its code in the error word
+  int err[2] = {0, 0};
+  CU(cudaMemcpyAsync(err, c->d_err, sizeof err, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (err[0]) return fail(c, FD_ETIMEOUT, "autotune: pipelined kernel wait expired (code %d)", err[0]);
+  if (n == 0) return fail(c, FD_EUNSUPPORTED, "autotune: no tile configuration could be planned");
+  if (ntried) *ntried = n;
+  st = replan(c, win.tile_y / kTmaNW, win.ctas_per_sm, win.zblock);
+  if (st) return st;
+  c->tune_us = win.us_per_step;
+  if (best) *best = win;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = win;
+  return FD_OK;
+}
+
+}  // namespace
 
 // ===========================================================================
 // Batches: many acoustic shots stepped together (continuous batching).
@@ -1242,7 +1440,9 @@ fd_status fd_batch_run(fd_batch *b, int nticks) {
     if (c->nsrc > 0 && c->step + nticks > c->nt_wav)
       return bfail(b, FD_EINVAL, "a member would pass its wavelet length");
     fd_status st = FD_OK;
-    if (c->nrec > 0) st = ensure_rec_capacity(c, c->step + nticks + 1);
+    // the batched kernel runs the default tile: a tuned member goes back to it
+    if (c->ndim == 3 && c->tma.ny != tma_ny(R)) st = replan(c, 0, 0, 0);
+    if (!st && c->nrec > 0) st = ensure_rec_capacity(c, c->step + nticks + 1);
     if (!st) st = prepare_sources(c);
     if (!st && c->ndim == 3) st = prepare_fused(c);
     if (st) return bfail(b, st, "member preparation: %s", c->err.c_str());
@@ -1382,7 +1582,7 @@ fd_status fd_batch_run(fd_batch *b, int nticks) {
   const StencilFn2D f2 = batch2d_fn(R);
   for (int t = 0; t < nticks; ++t) {
     if (n3) {
-      plan0.fn_multi<<<grid3, kTmaThreads, plan0.smem, b->stream>>>(
+      plan0.fn_multi<<<grid3, kTmaThreads, plan0.smem_multi, b->stream>>>(
           plan0.map_u[0], plan0.map_t[0], plan0.map_a, plan0.map_c, TmaArgs{}, ba);
       BCU(cudaGetLastError());
       ++b->launches;

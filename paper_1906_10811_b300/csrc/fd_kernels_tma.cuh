@@ -42,20 +42,28 @@ constexpr int kTmaThreads = (kTmaNW + 1) * 32;
 constexpr int kTmaDX = 4;         // slots of the u^{n-1}/A/C ring
 constexpr long long kWaitBudget = 1ll << 31;  // clock cycles (~1 s at 2 GHz)
 
-// rows per consumer thread: 4 up to radius 4, 2 above (register queue of 2R+1 planes per row)
-__host__ __device__ constexpr int tma_ny(int R) { return R <= 4 ? 4 : 2; }
-__host__ __device__ constexpr int tma_ty(int R) { return kTmaNW * tma_ny(R); }          // tile height
+// Tile shape: the consumer warps own NY rows each, so a tile is TX × (NW·NY)
+// points.  The register queue holds 2R+1 planes per row, so NY·(2R+1) bounds
+// the rows a thread can carry; the default is 4 rows up to radius 4 and 2
+// above, and the autotuner may pick the other of {2, 4}.
+__host__ __device__ constexpr int tma_ny(int R) { return R <= 4 ? 4 : 2; }   // default rows/thread
+__host__ __device__ constexpr int tma_ty(int NY) { return kTmaNW * NY; }      // tile height
 __host__ __device__ constexpr int tma_hxb(int R) { return (R + 3) / 4 * 4; }   // x halo, 16-B multiple
 __host__ __device__ constexpr int tma_du(int R) { return R + 4; }              // ring U slots
 __host__ __device__ constexpr int tma_bw(int R) { return kTmaTX + 2 * tma_hxb(R); }  // box width
-__host__ __device__ constexpr int tma_bh(int R) { return tma_ty(R) + 2 * R; }        // box height
-__host__ __device__ constexpr int tma_ubytes(int R) { return tma_bw(R) * tma_bh(R) * 4; }
-__host__ __device__ constexpr int tma_xbytes(int R) { return kTmaTX * tma_ty(R) * 4; }
+__host__ __device__ constexpr int tma_bh(int R, int NY) { return tma_ty(NY) + 2 * R; }  // box height
+__host__ __device__ constexpr int tma_ubytes(int R, int NY) { return tma_bw(R) * tma_bh(R, NY) * 4; }
+__host__ __device__ constexpr int tma_xbytes(int NY) { return kTmaTX * tma_ty(NY) * 4; }
 __host__ __device__ constexpr int tma_align128(int b) { return (b + 127) / 128 * 128; }
 // shared memory: barriers (1 KB) | ring U | ring X (three tiles per slot)
-__host__ __device__ constexpr int tma_smem_bytes(int R, bool acoustic) {
-  return 1024 + tma_du(R) * tma_align128(tma_ubytes(R)) +
-         (acoustic ? kTmaDX * 3 * tma_xbytes(R) : 0);
+__host__ __device__ constexpr int tma_smem_bytes(int R, int NY, bool acoustic) {
+  return 1024 + tma_du(R) * tma_align128(tma_ubytes(R, NY)) +
+         (acoustic ? kTmaDX * 3 * tma_xbytes(NY) : 0);
+}
+// CTAs per SM the register budget is sized for (launch bounds): the queue
+// (NY·(2R+1) floats) dominates a consumer thread's registers
+__host__ __device__ constexpr int tma_minb(int R, int NY) {
+  return NY * (2 * R + 1) <= 20 ? 3 : (NY * (2 * R + 1) <= 40 ? 2 : 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -205,16 +213,16 @@ struct BatchArgs {
 // six neighbours minus 6u (still exact for constants); otherwise one difference
 // per axis.  MULTI: the launch steps every shot of a batch (BatchArgs), taking
 // work items dynamically; one shot takes static contiguous ranges.
-template <int R, int EQ, bool ISO, bool MULTI>
-__global__ void __launch_bounds__(kTmaThreads, 2)
+template <int R, int NY, int EQ, bool ISO, bool MULTI>
+__global__ void __launch_bounds__(kTmaThreads, tma_minb(R, NY))
 k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
                 const __grid_constant__ CUtensorMap map_p,   // u^{n-1}, tile box
                 const __grid_constant__ CUtensorMap map_a,   // A, tile box
                 const __grid_constant__ CUtensorMap map_c,   // C, tile box
                 const TmaArgs args, const BatchArgs bat) {
-  constexpr int NY = tma_ny(R), TY = tma_ty(R);
+  constexpr int TY = tma_ty(NY);
   constexpr int HXB = tma_hxb(R), BW = tma_bw(R), DU = tma_du(R);
-  constexpr int USLOT = tma_align128(tma_ubytes(R)) / 4;  // floats per ring-U slot
+  constexpr int USLOT = tma_align128(tma_ubytes(R, NY)) / 4;  // floats per ring-U slot
   constexpr int XT = kTmaTX * TY;                          // floats per tile
   constexpr int Q = 2 * R + 1;                             // queue length
   constexpr bool AC = EQ == kAcoustic;
@@ -332,7 +340,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
             ok = false;
             break;
           }
-          mbar_expect_tx(&full_u[slot], tma_ubytes(R));
+          mbar_expect_tx(&full_u[slot], tma_ubytes(R, NY));
           tma_load_3d(ring_u + slot * USLOT, mu, x0 + kHaloX - HXB, y0, p + R, &full_u[slot]);
           ++su;
         }
@@ -567,6 +575,8 @@ timeout:
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
+using TmaKernelFn = void (*)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, TmaArgs, BatchArgs);
+
 struct TmaPlan {
   const char *name = "none";
   CUtensorMap map_u[2];   // u levels, halo box
@@ -574,11 +584,14 @@ struct TmaPlan {
   CUtensorMap map_a, map_c;
   TmaArgs args{};
   float *level[2] = {nullptr, nullptr};
-  void (*fn)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, TmaArgs, BatchArgs) = nullptr;
-  void (*fn_multi)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, TmaArgs, BatchArgs) = nullptr;
-  int grid_multi = 0;
-  int grid = 0;
-  int smem = 0;
+  TmaKernelFn fn = nullptr;        // one shot, tile height 8·ny
+  TmaKernelFn fn_multi = nullptr;  // batches (default tile height only)
+  int grid = 0, smem = 0;
+  int grid_multi = 0, smem_multi = 0;
+  int ny = 0;          // rows per consumer thread
+  int per_sm = 0;      // resident CTAs per SM the persistent grid is sized for
+  int per_sm_max = 0;  // occupancy limit of fn
+  int sms = 0;
 };
 
 using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
@@ -606,48 +619,63 @@ inline bool encode_map(EncodeFn enc, CUtensorMap *m, float *base, const Geom &g,
              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+template <int R, int NY, int EQ, bool ISO, bool MULTI>
+inline cudaError_t tma_instance(TmaKernelFn &fn, int &smem, int &per_sm) {
+  fn = k_stencil3d_tma<R, NY, EQ, ISO, MULTI>;
+  smem = tma_smem_bytes(R, NY, EQ == kAcoustic);
+  cudaError_t e = cudaFuncSetAttribute(k_stencil3d_tma<R, NY, EQ, ISO, MULTI>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil3d_tma<R, NY, EQ, ISO, MULTI>,
+                                                    kTmaThreads, smem);
+  if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+  return e;
+}
+
+// Kernel instances for rows-per-thread ny (2 or 4); batches use the default.
 template <int R, int EQ, bool ISO>
-inline cudaError_t tma_configure(TmaPlan &pl) {
-  pl.fn = k_stencil3d_tma<R, EQ, ISO, false>;
-  pl.fn_multi = (EQ == kAcoustic) ? k_stencil3d_tma<R, EQ, ISO, true> : nullptr;
-  pl.smem = tma_smem_bytes(R, EQ == kAcoustic);
-  cudaError_t e = cudaFuncSetAttribute(k_stencil3d_tma<R, EQ, ISO, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, pl.smem);
-  if (e == cudaSuccess && EQ == kAcoustic)
-    e = cudaFuncSetAttribute(k_stencil3d_tma<R, EQ, ISO, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, pl.smem);
+inline cudaError_t tma_configure(TmaPlan &pl, int ny) {
+  constexpr int NYD = tma_ny(R);
+  cudaError_t e = ny == 2 ? tma_instance<R, 2, EQ, ISO, false>(pl.fn, pl.smem, pl.per_sm_max)
+                          : tma_instance<R, 4, EQ, ISO, false>(pl.fn, pl.smem, pl.per_sm_max);
   if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil3d_tma<R, EQ, ISO, false>,
-                                                    kTmaThreads, pl.smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  int per_sm_multi = per_sm;
-  if (EQ == kAcoustic) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm_multi, k_stencil3d_tma<R, EQ, ISO, true>, kTmaThreads, pl.smem);
+  pl.fn_multi = nullptr;
+  pl.smem_multi = 0;
+  int per_sm_multi = 0;
+  if constexpr (EQ == kAcoustic) {
+    e = tma_instance<R, NYD, EQ, ISO, true>(pl.fn_multi, pl.smem_multi, per_sm_multi);
     if (e != cudaSuccess) return e;
   }
-  int dev = 0, sms = 0;
+  int dev = 0;
   cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  pl.grid = sms * per_sm;
-  pl.grid_multi = sms * std::max(per_sm_multi, 1);
+  cudaDeviceGetAttribute(&pl.sms, cudaDevAttrMultiProcessorCount, dev);
+  pl.grid_multi = pl.sms * std::max(per_sm_multi, 1);
   return cudaSuccess;
 }
 
-// Build the plan: tensor maps for both levels and the coefficient fields.
+// Tile configurations the pipelined kernel offers (the autotuner's space).
+inline bool tma_ny_supported(int ny) { return ny == 2 || ny == 4; }
+
+// Build the plan: tensor maps for both levels and the coefficient fields, for
+// ny rows per consumer thread (0: the default), a grid of per_sm CTAs per SM
+// (0: as many as fit) and z-blocks of zblock planes (0: about one CTA's share).
 inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float *const *level,
-                            float *A, float *C, const char **why) {
+                            float *A, float *C, int ny, int per_sm, int zblock, const char **why) {
   *why = nullptr;
   if (g.R0 == 0 || g.R < 1 || g.R > kMaxR) {
     *why = "3-D grids only";
     return cudaErrorNotSupported;
   }
+  const int R = g.R;
+  if (ny == 0) ny = tma_ny(R);
+  if (!tma_ny_supported(ny) || per_sm < 0 || zblock < 0) {
+    *why = "unsupported tile configuration";
+    return cudaErrorInvalidValue;
+  }
   // TMA rules: 16-B aligned bases and strides, inner box extent a 16-B multiple,
   // x coordinates multiples of 4 floats (x0 + kHaloX - HXB with x0 % 32 == 0).
-  if ((g.px * 4) % 16 || tma_hxb(g.R) % 4 || (tma_bw(g.R) * 4) % 16 || kHaloX % 4 ||
-      tma_bw(g.R) > 256 || tma_bh(g.R) > 256 || tma_ty(g.R) > 256 || (kTmaTX * 4) % 16) {
+  if ((g.px * 4) % 16 || tma_hxb(R) % 4 || (tma_bw(R) * 4) % 16 || kHaloX % 4 ||
+      tma_bw(R) > 256 || tma_bh(R, 4) > 256 || tma_ty(4) > 256 || (kTmaTX * 4) % 16) {
     *why = "layout violates the TMA alignment rules";
     return cudaErrorNotSupported;
   }
@@ -656,18 +684,18 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float 
     *why = "cuTensorMapEncodeTiled unavailable";
     return cudaErrorNotSupported;
   }
-  const int R = g.R;
+  const int ty = tma_ty(ny);
   for (int b = 0; b < 2; ++b) {
-    if (!encode_map(enc, &pl.map_u[b], level[b], g, tma_bw(R), tma_bh(R)) ||
-        !encode_map(enc, &pl.map_t[b], level[b], g, kTmaTX, tma_ty(R))) {
+    if (!encode_map(enc, &pl.map_u[b], level[b], g, tma_bw(R), tma_bh(R, ny)) ||
+        !encode_map(enc, &pl.map_t[b], level[b], g, kTmaTX, ty)) {
       *why = "tensor map encoding failed";
       return cudaErrorInvalidValue;
     }
     pl.level[b] = level[b];
   }
   if (eq == kAcoustic) {
-    if (!encode_map(enc, &pl.map_a, A, g, kTmaTX, tma_ty(R)) ||
-        !encode_map(enc, &pl.map_c, C, g, kTmaTX, tma_ty(R))) {
+    if (!encode_map(enc, &pl.map_a, A, g, kTmaTX, ty) ||
+        !encode_map(enc, &pl.map_c, C, g, kTmaTX, ty)) {
       *why = "tensor map encoding failed";
       return cudaErrorInvalidValue;
     }
@@ -679,10 +707,10 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float 
   const bool ac = eq == kAcoustic;
 #define TMA_CASE(RR)                                                                   \
   case RR:                                                                             \
-    e = ac ? (iso ? tma_configure<RR, kAcoustic, true>(pl)                             \
-                  : tma_configure<RR, kAcoustic, false>(pl))                           \
-           : (iso ? tma_configure<RR, kDiffusion, true>(pl)                            \
-                  : tma_configure<RR, kDiffusion, false>(pl));                         \
+    e = ac ? (iso ? tma_configure<RR, kAcoustic, true>(pl, ny)                         \
+                  : tma_configure<RR, kAcoustic, false>(pl, ny))                       \
+           : (iso ? tma_configure<RR, kDiffusion, true>(pl, ny)                        \
+                  : tma_configure<RR, kDiffusion, false>(pl, ny));                     \
     break;
   switch (R) { TMA_CASE(1) TMA_CASE(2) TMA_CASE(3) TMA_CASE(4) TMA_CASE(5) TMA_CASE(6) TMA_CASE(7) TMA_CASE(8) }
 #undef TMA_CASE
@@ -690,15 +718,23 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float 
     *why = "kernel configuration failed";
     return e;
   }
+  if (per_sm > pl.per_sm_max) {
+    *why = "more CTAs per SM than fit";
+    return cudaErrorInvalidValue;
+  }
+  pl.ny = ny;
+  pl.per_sm = per_sm ? per_sm : pl.per_sm_max;
+  pl.grid = pl.sms * pl.per_sm;
   pl.args.g = g;
   pl.args.tiles_x = (g.n2 + kTmaTX - 1) / kTmaTX;
-  const int tiles_y = (g.n1 + tma_ty(R) - 1) / tma_ty(R);
+  const int tiles_y = (g.n1 + ty - 1) / ty;
   pl.args.ntiles = pl.args.tiles_x * tiles_y;
   pl.args.W = (int64_t)pl.args.ntiles * g.n0;
   if (pl.grid > pl.args.W) pl.grid = (int)pl.args.W;
   // z-block height: about one CTA's share, so neighbouring tiles stream in step
   const int64_t share = (pl.args.W + pl.grid - 1) / pl.grid;
-  pl.args.zblock = (int)std::min<int64_t>(g.n0, std::max<int64_t>(1, share));
+  const int64_t zb = zblock ? zblock : std::max<int64_t>(1, share);
+  pl.args.zblock = (int)std::min<int64_t>(g.n0, zb);
   pl.name = ac ? "stencil3d_tma_acoustic" : "stencil3d_tma_diffusion";
   return cudaSuccess;
 }

@@ -23,7 +23,8 @@ class Solver:
     """
 
     def __init__(self, shape, spacing, space_order, dt, equation="acoustic", nu=0.5,
-                 device=False, stream=None, graphs=True, profile=False, kernel="auto"):
+                 device=False, stream=None, graphs=True, profile=False, kernel="auto",
+                 autotune=False):
         self.ctx = None
         self.shape = tuple(int(s) for s in shape)
         self.ndim = len(self.shape)
@@ -42,8 +43,10 @@ class Solver:
             cuda_stream = s.cuda_stream
             self.stream = s
         opt = B.options(nu=nu, cuda_stream=cuda_stream, device_ptrs=self.device, use_graphs=graphs,
-                        profile=profile, kernel=_KERNEL[kernel])
+                        profile=profile, kernel=_KERNEL[kernel], autotune=autotune)
+        self._in()
         self.ctx = B.fd_create(self.ndim, self.shape, spacing, space_order, dt, _EQ[equation], opt)
+        self._out()
         self.nrec = 0
 
     # -- lifecycle ---------------------------------------------------------
@@ -117,6 +120,24 @@ class Solver:
     @property
     def kernel_launches(self):
         return B.fd_kernel_launches(self.ctx)
+
+    # -- tile configuration of the pipelined 3-D kernel ----------------------
+    @property
+    def tile_config(self):
+        """{tile_x, tile_y, zblock, ctas_per_sm, us_per_step} of the pipelined kernel."""
+        return B.fd_get_tile_config(self.ctx)
+
+    def set_tile_config(self, tile_y=0, zblock=0, ctas_per_sm=0):
+        self._in()
+        B.fd_set_tile_config(self.ctx, tile_y=tile_y, zblock=zblock, ctas_per_sm=ctas_per_sm)
+        self._out()
+
+    def autotune(self, reps=5):
+        """Time every tile configuration and keep the fastest: (best, tried)."""
+        self._in()
+        out = B.fd_autotune(self.ctx, reps=reps)
+        self._out()
+        return out
 
     def _empty(self, shape):
         if self.device:

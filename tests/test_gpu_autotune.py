@@ -1,0 +1,174 @@
+"""Tile configurations of the pipelined 3-D kernel and the autotuner.
+
+A point's update is the same arithmetic whatever tile holds it, so every
+configuration the kernel offers (tile height 16 or 32, CTAs per SM, z-block
+height) must give bitwise the result of the default one, with sources and
+receivers; the autotuner must pick one of the configurations it timed, leave
+the solution untouched, and a tuned shot must still join a batch."""
+
+import numpy as np
+import pytest
+
+from helpers import oracle_acoustic, rel_l2, small_problem
+
+pytestmark = pytest.mark.gpu
+
+TOL_WAVE = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1906_10811_b300 import build
+    build.build()
+
+
+def _acoustic(p, nt, cfg=None, tune=False, chunks=None):
+    from paper_1906_10811_b300 import Solver
+    s = Solver(p["shape"], p["spacing"], p["so"], p["dt"], "acoustic", kernel="tma")
+    s.set_model(p["m"], p["damp"])
+    s.set_sources(p["src_coords"], p["wavelet"])
+    s.set_receivers(p["rec_coords"])
+    if cfg is not None:
+        s.set_tile_config(**cfg)
+    used = s.tile_config
+    for n in (chunks or [nt]):
+        s.run(n)
+        if tune:
+            s.autotune(reps=2)
+    u, rec = s.read()
+    up = s.read_prev()
+    s.close()
+    return u, up, rec, used
+
+
+def _configs(shape, so):
+    """Every (tile_y, ctas_per_sm, zblock) the plan accepts for this problem."""
+    from paper_1906_10811_b300 import Solver
+    from paper_1906_10811_b300.binding import FdError
+    out = []
+    s = Solver(shape, (10.0,) * 3, so, 0.1, "acoustic", kernel="tma")
+    for ty in (16, 32):
+        for cps in (1, 2, 3):
+            for zb in (0, 3, 11, shape[0]):
+                try:
+                    s.set_tile_config(tile_y=ty, ctas_per_sm=cps, zblock=zb)
+                except FdError:
+                    continue
+                out.append(dict(tile_y=ty, ctas_per_sm=cps, zblock=zb))
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("so,shape", [(4, (37, 45, 70)), (8, (33, 50, 41)), (16, (29, 38, 66))])
+def test_every_tile_configuration_is_bitwise_the_default(so, shape):
+    p = small_problem(shape, so, nt=60, nrec=11)
+    ref = _acoustic(p, 60)
+    cfgs = _configs(shape, so)
+    heights = {c["tile_y"] for c in cfgs}
+    assert heights == {16, 32}, cfgs
+    for cfg in cfgs:
+        u, up, rec, used = _acoustic(p, 60, cfg)
+        assert used["tile_y"] == cfg["tile_y"] and used["ctas_per_sm"] == cfg["ctas_per_sm"]
+        if cfg["zblock"]:
+            assert used["zblock"] == min(cfg["zblock"], shape[0])
+        assert np.array_equal(u, ref[0]), cfg
+        assert np.array_equal(up, ref[1]), cfg
+        assert np.array_equal(rec, ref[2]), cfg
+    o = oracle_acoustic(p, 60)
+    assert rel_l2(ref[0], o["u"]) <= TOL_WAVE
+    assert rel_l2(ref[2], o["rec"]) <= TOL_WAVE
+
+
+def test_diffusion_tile_configurations_agree():
+    from paper_1906_10811_b300 import Solver
+    rng = np.random.default_rng(3)
+    shape = (26, 41, 67)
+    u0 = rng.standard_normal(shape).astype(np.float32)
+    outs = []
+    for cfg in (None, dict(tile_y=16), dict(tile_y=32, zblock=5), dict(tile_y=16, ctas_per_sm=1)):
+        s = Solver(shape, (1.0 / 40,) * 3, 6, 0.1 * (1.0 / 40) ** 2, "diffusion", kernel="tma")
+        if cfg:
+            s.set_tile_config(**cfg)
+        s.set_field(u0)
+        s.run(25)
+        outs.append(s.read()[0])
+        s.close()
+    for u in outs[1:]:
+        assert np.array_equal(u, outs[0])
+
+
+def test_autotune_picks_a_timed_configuration_and_keeps_the_solution():
+    p = small_problem((48, 64, 96), 8, nt=80, nrec=16)
+    ref = _acoustic(p, 80)
+    # autotune between chunks of steps: the solution continues unchanged
+    u, up, rec, _ = _acoustic(p, 80, tune=True, chunks=[30, 25, 25])
+    assert np.array_equal(u, ref[0]) and np.array_equal(up, ref[1]) and np.array_equal(rec, ref[2])
+
+    from paper_1906_10811_b300 import Solver
+    s = Solver(p["shape"], p["spacing"], 8, p["dt"], "acoustic", kernel="tma")
+    s.set_model(p["m"], p["damp"])
+    best, tried = s.autotune(reps=3)
+    assert len(tried) >= 4
+    assert {t["tile_y"] for t in tried} == {16, 32}
+    assert all(t["us_per_step"] > 0 for t in tried)
+    key = lambda t: (t["tile_y"], t["zblock"], t["ctas_per_sm"])
+    assert key(best) in {key(t) for t in tried}
+    assert best["us_per_step"] == min(t["us_per_step"] for t in tried)
+    cur = s.tile_config
+    assert key(cur) == key(best) and cur["us_per_step"] == best["us_per_step"]
+    s.close()
+
+
+def test_autotune_option_at_creation_uses_the_process_cache():
+    from paper_1906_10811_b300 import Solver
+    p = small_problem((40, 44, 52), 6, nt=10)
+    a = Solver(p["shape"], p["spacing"], 6, p["dt"], "acoustic", autotune=True)
+    b = Solver(p["shape"], p["spacing"], 6, p["dt"], "acoustic", autotune=True)
+    ca, cb = a.tile_config, b.tile_config
+    assert ca["us_per_step"] > 0
+    assert ca == cb
+    a.close()
+    b.close()
+
+
+def test_bad_tile_configurations_are_rejected_and_keep_the_current_one():
+    from paper_1906_10811_b300 import Solver
+    from paper_1906_10811_b300.binding import FD_EINVAL, FD_EUNSUPPORTED, FdError
+    s = Solver((20, 24, 28), (10.0,) * 3, 8, 0.1, "acoustic", kernel="tma")
+    before = s.tile_config
+    for bad in (dict(tile_y=24), dict(tile_y=64), dict(zblock=-1), dict(ctas_per_sm=-2),
+                dict(ctas_per_sm=64)):
+        with pytest.raises(FdError) as e:
+            s.set_tile_config(**bad)
+        assert e.value.status == FD_EINVAL
+        assert s.tile_config == before
+    s.close()
+    s2 = Solver((40, 50), (10.0,) * 2, 8, 0.1, "acoustic")
+    with pytest.raises(FdError) as e:
+        s2.set_tile_config(tile_y=16)
+    assert e.value.status == FD_EUNSUPPORTED
+    s2.close()
+
+
+def test_a_tuned_shot_joins_a_batch_at_the_default_tile():
+    from paper_1906_10811_b300 import Batch, Solver
+    p = small_problem((31, 36, 45), 8, nt=50, nrec=7)
+    ref = _acoustic(p, 50)
+    s = Solver(p["shape"], p["spacing"], 8, p["dt"], "acoustic")
+    s.set_model(p["m"], p["damp"])
+    s.set_sources(p["src_coords"], p["wavelet"])
+    s.set_receivers(p["rec_coords"])
+    s.set_tile_config(tile_y=16, zblock=9)
+    s.run(20)
+    b = Batch(8)
+    b.add(s)
+    b.run(30)
+    b.remove(s)
+    assert s.tile_config["tile_y"] == 32
+    u, rec = s.read()
+    up = s.read_prev()
+    b.close()
+    s.close()
+    assert np.array_equal(u, ref[0]) and np.array_equal(up, ref[1]) and np.array_equal(rec, ref[2])
