@@ -49,10 +49,14 @@ WORKLOADS = {
 }
 
 # DRAM bytes per stencil launch from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum), keyed by (kernel name, workload, space order); the
-# captures are summarised in profiles/.  Absent (null) when not captured for the
-# kernel as it is now.
-NCU_TRAFFIC = {}
+# dram__bytes_write.sum, mean of the captured launches), keyed by (kernel name,
+# workload, space order, tile height, z-block height, CTAs per SM); the captures
+# are summarised in profiles/.  Absent (null) when not captured for the kernel
+# and tile configuration as they are now.
+NCU_TRAFFIC = {
+    # profiles/stencil3d_tma_acoustic256_so8.md: 3 launches, read 321.17 MB + write 46.42 MB
+    ("stencil3d_tma_acoustic", "acoustic256", 8, 32, 56, 2): 367.59e6,
+}
 
 
 def parse():
@@ -68,9 +72,10 @@ def parse():
     ap.add_argument("--so", type=int, default=None)
     ap.add_argument("--nt", type=int, default=None)
     ap.add_argument("--kernel", default="auto", choices=["auto", "plain", "tma"])
-    ap.add_argument("--tile", default="auto", choices=["auto", "default"],
+    ap.add_argument("--tile", default="auto",
                     help="auto: the autotuner picks the pipelined kernel's tile configuration "
-                         "before the timed region; default: the built-in one")
+                         "before the timed region; default: the built-in one; TY,ZB,CPS: tile "
+                         "height, z-block height and CTAs per SM given explicitly")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -271,6 +276,9 @@ def run_ours(args):
             s.set_model(m_d, damp_d)
             _, tried = s.autotune(reps=5)
             tune_tried = len(tried)
+        elif args.tile != "default":
+            ty, zb, cps = (int(v) for v in args.tile.split(","))
+            s.set_tile_config(tile_y=ty, zblock=zb, ctas_per_sm=cps)
         tile = s.tile_config
 
     def shot():
@@ -306,7 +314,8 @@ def run_ours(args):
     peak, peak_kind = load_peak()
     avg_launch_s = st_ms / max(n_st, 1) / 1e3
     achieved = BYTES_PER_POINT["acoustic"] * npts / avg_launch_s / 1e9
-    traffic = NCU_TRAFFIC.get((kernel_name, args.workload, w["so"]))
+    tkey = (tile["tile_y"], tile["zblock"], tile["ctas_per_sm"]) if tile else (0, 0, 0)
+    traffic = NCU_TRAFFIC.get((kernel_name, args.workload, w["so"]) + tkey)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "kernel": kernel_name, "bytes_per_point": BYTES_PER_POINT["acoustic"],
@@ -326,6 +335,9 @@ def run_ours(args):
         d2h = (nt + 1) * w["nrec"] * 4
         se = Solver(p["shape"], p["spacing"], p["so"], p["dt"], "acoustic", device=False,
                     kernel=args.kernel, autotune=tile is not None and args.tile == "auto")
+        if tile is not None and args.tile not in ("auto", "default"):
+            se.set_tile_config(tile_y=tile["tile_y"], zblock=tile["zblock"],
+                               ctas_per_sm=tile["ctas_per_sm"])
         from paper_1906_10811_b300 import binding as B
 
         def shot_e2e():
@@ -362,7 +374,8 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": dict(config_of(args, w, kernel_name), tile=tile,
                                tile_choice=("autotuned over %d configurations" % tune_tried
-                                            if tune_tried else "default")),
+                                            if tune_tried else
+                                            "default" if args.tile == "default" else "given")),
                 "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
         print(json.dumps(line), flush=True)

@@ -60,6 +60,11 @@ __host__ __device__ constexpr int tma_smem_bytes(int R, int NY, bool acoustic) {
   return 1024 + tma_du(R) * tma_align128(tma_ubytes(R, NY)) +
          (acoustic ? kTmaDX * 3 * tma_xbytes(NY) : 0);
 }
+// Consumer loop unrolling: up to radius 4 by the whole window (2R+1 phases,
+// queue slots taken mod 2R+1, no register moves); above, by 4 phases with a
+// slide of the queue after each group, which keeps the code small enough for
+// the instruction cache at the cost of 2R moves per 4 planes and row
+__host__ __device__ constexpr int tma_unroll(int R) { return R <= 4 ? 2 * R + 1 : 4; }
 // CTAs per SM the register budget is sized for (launch bounds): the queue
 // (NY·(2R+1) floats) dominates a consumer thread's registers
 __host__ __device__ constexpr int tma_minb(int R, int NY) {
@@ -209,6 +214,66 @@ struct BatchArgs {
   int *err;
 };
 
+// Queue slot of window offset o (0 .. 2R) in phase ph of an unrolled group.
+template <int U, int Q>
+__device__ __forceinline__ constexpr int tma_qslot(int ph, int o) {
+  return U == Q ? (ph + o) % Q : ph + o;
+}
+
+// Source corners at tile-plane zc (rare, so kept out of the unrolled loop):
+// entries [ecur, eend) are sorted by (tile, plane, source); 32 at a time, one
+// per lane, coefficients fetched in parallel; the lane that owns the point
+// adds them to its rows (v.x .. v.w) in entry order.  Returns the new cursor
+// and the plane of the next entry.
+struct SourceHits {
+  float4 v;
+  int ecur, nxt_z;
+};
+__device__ __forceinline__ SourceHits source_hits(const int4 *entries, const float *src_scale,
+                                                  const float *wav, int nsrc, int nc, int ecur,
+                                                  int eend, int zc, int ybase, int ny, int x,
+                                                  int lane, int64_t nstep, float4 v) {
+  while (true) {
+    const int e = ecur + lane;
+    const int4 en = e < eend ? entries[e] : make_int4(0, 0, INT_MAX, 0);
+    const int cnt = __popc(__ballot_sync(0xffffffffu, en.z == zc));  // a prefix
+    const int jr = en.y - ybase;
+    const bool here = en.z == zc && jr >= 0 && jr < ny;
+    float add = 0.f;
+    if (here) add = src_scale[en.w] * wav[nstep * nsrc + en.w / nc];
+    unsigned mine = __ballot_sync(0xffffffffu, here);
+    while (mine) {
+      const int b = __ffs(mine) - 1;
+      mine &= mine - 1;
+      const int ex = __shfl_sync(0xffffffffu, en.x, b);
+      const int ej = __shfl_sync(0xffffffffu, jr, b);
+      const float ad = __shfl_sync(0xffffffffu, add, b);
+      if (ex == x) {
+        if (ej == 0) v.x += ad;
+        else if (ej == 1) v.y += ad;
+        else if (ej == 2) v.z += ad;
+        else v.w += ad;
+      }
+    }
+    ecur += cnt;
+    if (cnt < 32) break;
+  }
+  SourceHits h;
+  h.v = v;
+  h.ecur = ecur;
+  h.nxt_z = ecur < eend ? entries[ecur].z : INT_MAX;
+  return h;
+}
+// Out-of-line copy for the large-radius kernels, whose loop body is the
+// biggest; inlined copies there would crowd the instruction cache.
+__device__ __noinline__ SourceHits source_hits_call(const int4 *entries, const float *src_scale,
+                                                    const float *wav, int nsrc, int nc, int ecur,
+                                                    int eend, int zc, int ybase, int ny, int x,
+                                                    int lane, int64_t nstep, float4 v) {
+  return source_hits(entries, src_scale, wav, nsrc, nc, ecur, eend, zc, ybase, ny, x, lane, nstep,
+                     v);
+}
+
 // ISO: equal spacing on all axes, so one weight per k multiplies the sum of the
 // six neighbours minus 6u (still exact for constants); otherwise one difference
 // per axis.  MULTI: the launch steps every shot of a batch (BatchArgs), taking
@@ -224,7 +289,10 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
   constexpr int HXB = tma_hxb(R), BW = tma_bw(R), DU = tma_du(R);
   constexpr int USLOT = tma_align128(tma_ubytes(R, NY)) / 4;  // floats per ring-U slot
   constexpr int XT = kTmaTX * TY;                          // floats per tile
-  constexpr int Q = 2 * R + 1;                             // queue length
+  constexpr int Q = 2 * R + 1;                             // window of planes
+  constexpr int U = tma_unroll(R);                         // phases per unrolled group
+  constexpr int QL = U == Q ? Q : Q + U - 1;               // queue registers per row
+  constexpr bool kSplit = R > 4;                           // two accumulation chains
   constexpr bool AC = EQ == kAcoustic;
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t *full_u = reinterpret_cast<uint64_t *>(smem);
@@ -365,7 +433,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
   // --------------------------------- consumers --------------------------------
   // Fill s of ring U is plane za-R+(s-s0) of the current segment (s0 = its first
   // fill); the queue slot of plane za-R+m is m mod Q.
-  float qz[NY][Q];
+  float qz[NY][QL];
   uint32_t su = 0, sx = 0;
   const int row0 = warp * NY;  // first tile row of this thread
   int64_t nstep = 0;
@@ -449,13 +517,16 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
       }
       ++su;
     }
-    // steady state: update zc = za + i after pushing plane zc + R (slot (i+2R) mod Q)
+    // steady state: update zc = za + i after pushing plane zc + R.  Phase ph
+    // of an unrolled group of U: the window of planes zc-R .. zc+R is queue
+    // slots ph .. ph+2R (U < Q: slots shift down by U after each group) or
+    // those slots mod Q (U = Q: no shifts).
     {
       const int nseg = zb - za;
       int i = 0;
       while (true) {
 #pragma unroll
-        for (int ph = 0; ph < Q; ++ph) {
+        for (int ph = 0; ph < U; ++ph) {
           if (i >= nseg) goto segment_done;
           {
             const int zc = za + i;
@@ -463,7 +534,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
             if (!mbar_wait(&full_u[slot], (su / DU) & 1)) goto timeout;
             const float *pl = ring_u + slot * USLOT + (R + row0) * BW + HXB + lane;
 #pragma unroll
-            for (int j = 0; j < NY; ++j) qz[j][(ph + 2 * R) % Q] = pl[j * BW];
+            for (int j = 0; j < NY; ++j) qz[j][tma_qslot<U, Q>(ph, 2 * R)] = pl[j * BW];
             const uint32_t cs = (su - R) % DU;  // ring-U slot holding plane zc
             const float *cp = ring_u + cs * USLOT + row0 * BW + HXB + lane;
             const float *xs = nullptr;
@@ -480,27 +551,40 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
 #pragma unroll
             for (int j = 0; j < NY; ++j) {
               const float *rowp = cp + (R + j) * BW;
-              const float uc = qz[j][(ph + R) % Q];
-              // difference form: the weights multiplying each k sum to zero exactly
-              float lap = 0.f;
+              const float uc = qz[j][tma_qslot<U, Q>(ph, R)];
+              // difference form: the weights multiplying each k sum to zero
+              // exactly; above radius 4, odd and even k accumulate in two chains
+              float lo = 0.f, le = 0.f;
               if (ISO) {
                 const float uc6 = 6.f * uc;
 #pragma unroll
                 for (int k = 1; k <= R; ++k) {
-                  const float s6 = ((rowp[k] + rowp[-k]) + (ycol[R + j + k] + ycol[R + j - k])) +
-                                   (qz[j][(ph + R + k) % Q] + qz[j][(ph + R - k + Q) % Q]);
-                  lap = fmaf(wk2[k], s6 - uc6, lap);
+                  const float s6 =
+                      ((rowp[k] + rowp[-k]) + (ycol[R + j + k] + ycol[R + j - k])) +
+                      (qz[j][tma_qslot<U, Q>(ph, R + k)] + qz[j][tma_qslot<U, Q>(ph, R - k)]);
+                  if ((k & 1) || !kSplit)
+                    lo = fmaf(wk2[k], s6 - uc6, lo);
+                  else
+                    le = fmaf(wk2[k], s6 - uc6, le);
                 }
               } else {
                 const float uc2 = uc + uc;
 #pragma unroll
                 for (int k = 1; k <= R; ++k) {
-                  lap = fmaf(wk2[k], (rowp[k] + rowp[-k]) - uc2, lap);
-                  lap = fmaf(wk1[k], (ycol[R + j + k] + ycol[R + j - k]) - uc2, lap);
-                  lap = fmaf(wk0[k], (qz[j][(ph + R + k) % Q] + qz[j][(ph + R - k + Q) % Q]) - uc2,
-                             lap);
+                  float acc = ((k & 1) || !kSplit) ? lo : le;
+                  acc = fmaf(wk2[k], (rowp[k] + rowp[-k]) - uc2, acc);
+                  acc = fmaf(wk1[k], (ycol[R + j + k] + ycol[R + j - k]) - uc2, acc);
+                  acc = fmaf(wk0[k],
+                             (qz[j][tma_qslot<U, Q>(ph, R + k)] + qz[j][tma_qslot<U, Q>(ph, R - k)]) -
+                                 uc2,
+                             acc);
+                  if ((k & 1) || !kSplit)
+                    lo = acc;
+                  else
+                    le = acc;
                 }
               }
+              const float lap = kSplit ? lo + le : lo;
               if (AC) {
                 const float up = xs[j * kTmaTX], a = xs[XT + j * kTmaTX],
                             cc = xs[2 * XT + j * kTmaTX];
@@ -510,35 +594,22 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
               }
             }
             if (AC && nxt_z == zc) {
-              // source corners at this tile-plane (most planes have none): 32 per
-              // batch, one per lane, coefficients fetched in parallel; the owner
-              // lane adds them in entry order
-              while (true) {
-                const int e = ecur + lane;
-                const int4 en = e < eend ? sp.entries[e] : make_int4(0, 0, INT_MAX, 0);
-                const int cnt = __popc(__ballot_sync(0xffffffffu, en.z == zc));  // a prefix
-                const int jr = en.y - ybase;
-                const bool here = en.z == zc && jr >= 0 && jr < NY;
-                float add = 0.f;
-                if (here)
-                  add = sp.src_scale[en.w] * sp.wav[nstep * sp.nsrc + en.w / sp.nc];
-                unsigned mine = __ballot_sync(0xffffffffu, here);
-                while (mine) {
-                  const int b = __ffs(mine) - 1;
-                  mine &= mine - 1;
-                  const int ex = __shfl_sync(0xffffffffu, en.x, b);
-                  const int ej = __shfl_sync(0xffffffffu, jr, b);
-                  const float ad = __shfl_sync(0xffffffffu, add, b);
-                  if (ex == x) {
-#pragma unroll
-                    for (int j = 0; j < NY; ++j)
-                      if (j == ej) val[j] += ad;
-                  }
-                }
-                ecur += cnt;
-                if (cnt < 32) break;
-              }
-              nxt_z = ecur < eend ? sp.entries[ecur].z : INT_MAX;
+              // source corners at this tile-plane (most planes have none)
+              float4 v = make_float4(val[0], 0.f, 0.f, 0.f);
+              if constexpr (NY > 1) v.y = val[1];
+              if constexpr (NY > 2) v.z = val[2];
+              if constexpr (NY > 3) v.w = val[3];
+              const SourceHits h =
+                  R > 4 ? source_hits_call(sp.entries, sp.src_scale, sp.wav, sp.nsrc, sp.nc, ecur,
+                                           eend, zc, ybase, NY, x, lane, nstep, v)
+                        : source_hits(sp.entries, sp.src_scale, sp.wav, sp.nsrc, sp.nc, ecur, eend,
+                                      zc, ybase, NY, x, lane, nstep, v);
+              val[0] = h.v.x;
+              if constexpr (NY > 1) val[1] = h.v.y;
+              if constexpr (NY > 2) val[2] = h.v.z;
+              if constexpr (NY > 3) val[3] = h.v.w;
+              ecur = h.ecur;
+              nxt_z = h.nxt_z;
             }
 #pragma unroll
             for (int j = 0; j < NY; ++j) {
@@ -559,6 +630,13 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
             ++su;
             ++i;
           }
+        }
+        if constexpr (U < Q) {
+          // slide the window: slots U .. U+2R-1 become 0 .. 2R-1
+#pragma unroll
+          for (int j = 0; j < NY; ++j)
+#pragma unroll
+            for (int m = 0; m < 2 * R; ++m) qz[j][m] = qz[j][m + U];
         }
       }
     }
