@@ -12,7 +12,10 @@ the C ABI with pinned host buffers (host->device copies of the shot's inputs and
 the device->host read of its traces inside the timed region).
 
 ``--workload roofline512 --so {4,8,12,16}`` runs the 512³ sweep (200 steps, one
-source, no receivers).  ``--workload serving`` serves a seeded Poisson stream of
+source, no receivers).  ``--workload fwi320`` times full-waveform-inversion
+gradients of a 320³, so 8, 1000-step shot (256 receivers) against traces of a
+seeded perturbed model: forward sweep with checkpoints every k steps (k tuned
+by timing the candidates), recompute, adjoint and imaging per step.  ``--workload serving`` serves a seeded Poisson stream of
 64 shots (2-D 200²-1000² and 3-D 128³-320³ grids, so 8, 300-1000 steps, one
 source and 128-512 receivers each) with the continuous-batching server under an
 HBM budget, and the same stream one shot at a time; it reports shots/s and
@@ -65,7 +68,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="acoustic256", choices=sorted(WORKLOADS) + ["serving"])
+    ap.add_argument("--workload", default="acoustic256",
+                    choices=sorted(WORKLOADS) + ["serving", "fwi320"])
+    ap.add_argument("--fwi-k", type=int, default=0,
+                    help="fwi320: checkpoint interval (0: tuned by timing the candidates)")
     ap.add_argument("--shots", type=int, default=64)
     ap.add_argument("--mean-gap", type=float, default=0.015)
     ap.add_argument("--hbm-budget-gb", type=float, default=8.0)
@@ -206,10 +212,41 @@ def cpu_baseline(p, budget_s):
                       f"{t:.1f} s), OpenMP over grid rows"}
 
 
+def run_reference_fwi(args):
+    """Reference arm of the FWI workload: the FP64 oracle gradient on a bounded sample."""
+    w, _ = fwi_problem(args)
+    for _ in range(args.warmup):
+        fwi_oracle_sample(0.0)
+    vals, sample = [], ""
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, sample = fwi_oracle_sample(0.0)
+        vals.append(v)
+    total = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": "FWI gradient GPts/s (space-time points of the shot per second)",
+            "value": round(value, 5), "unit": "GPts/s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": fwi_config(w),
+            "cpu_baseline": {"value": round(value, 5), "unit": "GPts/s", "cores": cpu_threads(),
+                             "kind": "oracle", "sample": "each step = " + sample},
+            "e2e": {"value": round(value, 5), "unit": "GPts/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     world, rank, _ = dist_setup(args)
     if rank != 0:
         return 0
+    if args.workload == "fwi320":
+        return run_reference_fwi(args)
+    if args.workload == "serving":
+        args.workload = "acoustic256"     # the oracle serves no stream: time its shot sample
     w, p = problem(args)
     _, t1 = time_oracle(p, 1)
     per_step = int(max(1, min(p["nt"], round(6.0 / max(t1, 1e-3)))))
@@ -233,6 +270,166 @@ def run_reference(args):
                     "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+FWI = dict(n=320, so=8, nt=1000, nrec=256, nbl=40)
+FWI_BYTES_PER_POINT_STEP = 92   # forward 20 + recompute 20 + snapshot 8 + adjoint 20 + imaging 24
+
+
+def fwi_problem(args):
+    w = dict(FWI)
+    if args.nt:
+        w["nt"] = args.nt
+    p = fdsynth.acoustic_problem(n=w["n"], ndim=3, so=w["so"], nbl=w["nbl"], nt=w["nt"],
+                                 nrec=w["nrec"], seed=0)
+    return w, p
+
+
+def fwi_config(w, k=None, tuning=None):
+    cfg = {"workload": f"fwi_gradient_acoustic3d_{w['n']}^3_so{w['so']}_nt{w['nt']}",
+           "grid": [w["n"]] * 3, "space_order": w["so"], "nt": w["nt"], "nrec": w["nrec"],
+           "nsrc": 1, "damping_layer": w["nbl"], "dx_m": 10.0,
+           "step": "one gradient dJ/dm: forward with checkpoints, recompute, adjoint, imaging",
+           "observed_data": "traces of a seeded perturbed model (4 Gaussian blobs, +5% in m)",
+           "l2": "inputs larger than L2 (each level %.0f MB)" %
+                 ((w["n"] + 8) ** 2 * (w["n"] + 64) * 4 / 1e6)}
+    if k is not None:
+        cfg["checkpoint_interval"] = k
+    if tuning is not None:
+        cfg["checkpoint_tuning"] = tuning
+    return cfg
+
+
+def fwi_oracle_sample(budget_s):
+    """Oracle gradient GPts/s on a bounded sample: 40³ grid of the same recipe."""
+    from oracle import fwi as ofwi
+    n, nt = 40, 60
+    q = fdsynth.acoustic_problem(n=n, ndim=3, so=8, nbl=8, nt=nt, nrec=64, seed=0)
+    m_true = fdsynth.perturbed_model(q["m"], 8)
+    from oracle import core as oracle
+    _, _, d_obs = oracle.acoustic(m_true, q["dt"], q["spacing"], 8, nt, damp=q["damp"],
+                                  src_coords=q["src_coords"], wavelet=q["wavelet"],
+                                  rec_coords=q["rec_coords"])
+    runs, total = 0, 0.0
+    while total < budget_s or runs == 0:
+        t0 = time.perf_counter()
+        ofwi.gradient(q["m"], q["damp"], q["dt"], q["spacing"], 8, nt, q["src_coords"],
+                      q["wavelet"], q["rec_coords"], d_obs)
+        total += time.perf_counter() - t0
+        runs += 1
+    value = n ** 3 * nt * runs / total / 1e9
+    return value, f"{runs} FP64 oracle gradients of a 40^3, so 8, 60-step shot of the same recipe ({total:.1f} s)"
+
+
+def run_fwi(args):
+    import torch
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1906_10811_b300 import build, fwi
+    build.build()
+    w, p = fwi_problem(args)
+    npts, nt = int(np.prod(p["shape"])), p["nt"]
+    m_true = fdsynth.perturbed_model(p["m"], w["nbl"])
+    d_obs = fwi.forward_traces(p, m_true)
+    m0 = torch.from_numpy(p["m"]).cuda()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    tuning = None
+    if args.fwi_k > 0:
+        k = args.fwi_k
+    else:
+        k, rows = fwi.tune_checkpoint_interval(p, d_obs, m=m0)
+        tuning = [{"k": r[0], "s": round(r[1], 4), "bytes": int(r[2])} for r in rows]
+    stats = {}
+    for _ in range(args.warmup):
+        fwi.gradient(p, d_obs, m=m0, k=k, stats=stats)
+    gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    clocks = ClockSampler(gpu_id)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        st = {}
+        fwi.gradient(p, d_obs, m=m0, k=k, stats=st)
+        launches += st["launches_forward"] + st["launches_adjoint"]
+    e1.record(stream)
+    barrier()
+    ms = reduce_max(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    value = whole_job_rate(npts * nt * args.steps, world, ms / 1e3) / 1e9
+
+    # stencil launches timed one by one (outside the timed region)
+    prof = {}
+    fwi.gradient(p, d_obs, m=m0, k=k, stats=prof, profile=True)
+    avg_s = prof["stencil_ms"] / max(prof["stencil_launches"], 1) / 1e3
+    peak, peak_kind = load_peak()
+    achieved = BYTES_PER_POINT["acoustic"] * npts / avg_s / 1e9
+    grad_gbs = FWI_BYTES_PER_POINT_STEP * npts * nt * args.steps / (ms / 1e3) / 1e9 / world
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": "stencil3d_tma_acoustic (forward, recompute and adjoint steps)",
+                "bytes_per_point": BYTES_PER_POINT["acoustic"], "points_per_launch": npts,
+                "avg_launch_us": round(avg_s * 1e6, 2),
+                "launches_timed": prof["stencil_launches"],
+                "stencil_share_of_step": round(prof["stencil_ms"] / (ms / args.steps), 4),
+                "peak_source": f"{peak_kind} HBM copy bandwidth (of {peak_kind})",
+                "whole_gradient": {"bytes_per_point_step": FWI_BYTES_PER_POINT_STEP,
+                                   "achieved_gbs": round(grad_gbs, 1),
+                                   "frac": round(grad_gbs / peak, 4)}}
+
+    e2e = None
+    if not args.no_e2e:
+        m_h = torch.from_numpy(p["m"]).pin_memory()
+        d_h = d_obs.cpu().pin_memory()
+        g_h = torch.empty(p["shape"], dtype=torch.float32).pin_memory()
+
+        def grad_e2e():
+            m_d = m_h.cuda(non_blocking=True)
+            d_d = d_h.cuda(non_blocking=True)
+            _, g = fwi.gradient(p, d_d, m=m_d, k=k)
+            g_h.copy_(g, non_blocking=True)
+
+        grad_e2e()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            grad_e2e()
+        barrier()
+        te = reduce_max(time.perf_counter() - t0)
+        e2e = {"value": round(whole_job_rate(npts * nt * args.steps, world, te) / 1e9, 3),
+               "unit": "GPts/s", "h2d_bytes_per_step": int(m_h.numel() * 4 + d_h.numel() * 4),
+               "d2h_bytes_per_step": int(g_h.numel() * 4)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, sample = fwi_oracle_sample(args.cpu_seconds)
+        cpu = {"value": round(v, 5), "unit": "GPts/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": sample}
+    if rank == 0:
+        line = {"metric": "FWI gradient GPts/s (space-time points of the shot per second)",
+                "value": round(value, 3), "unit": "GPts/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": dict(fwi_config(w, k, tuning),
+                               checkpoint_bytes=stats.get("checkpoint_bytes"),
+                               block_bytes=stats.get("block_bytes")),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
     return 0
 
 
@@ -427,6 +624,8 @@ def main():
         return run_reference(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "fwi320":
+        return run_fwi(args)
     return run_ours(args)
 
 

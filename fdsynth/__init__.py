@@ -188,6 +188,27 @@ def acoustic_problem(n=256, ndim=3, so=8, nbl=40, h=10.0, nt=500, nrec=256,
                 vel=v, src_coords=src, wavelet=wav, rec_coords=rec)
 
 
+def perturbed_model(m, nbl, seed=3, amp=0.05, nblobs=4, width=0.08):
+    """A seeded "true" model for inversion: m·(1 + amp·Σ_b exp(−|x − c_b|²/(2 s²))).
+
+    ``nblobs`` Gaussian blobs with centres uniform inside the region the
+    damping layer leaves (``nbl`` cells from every face) and width s =
+    ``width``·(smallest extent).  m only grows (the velocity only drops), so a
+    dt stable for m stays stable.  Float64, rounded once to float32.
+    """
+    shape = m.shape
+    rng = np.random.default_rng(seed)
+    s = width * min(shape)
+    grids = np.meshgrid(*[np.arange(n, dtype=np.float64) for n in shape], indexing="ij",
+                        sparse=True)
+    bump = np.zeros(shape)
+    for _ in range(nblobs):
+        c = [rng.uniform(min(nbl, n // 4), max(n - 1 - nbl, n - 1 - n // 4)) for n in shape]
+        r2 = sum((g - cc) ** 2 for g, cc in zip(grids, c))
+        bump += np.exp(-r2 / (2.0 * s * s))
+    return (m.astype(np.float64) * (1.0 + amp * bump)).astype(np.float32)
+
+
 def serving_stream(nshots=64, seed=2, mean_gap_s=0.01, sizes2d=(200, 1000), sizes3d=(128, 320),
                    nt_range=(300, 1000), nrec_range=(128, 512), so=8, frac3d=0.5, nbl=40):
     """A seeded Poisson stream of acoustic shots for the serving workload.

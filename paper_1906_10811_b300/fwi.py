@@ -16,7 +16,8 @@ accumulated by the library's imaging-condition kernel (fd_imaging).  The
 forward wavefield is needed backwards in time: it is checkpointed every k
 steps (fd_snapshot) and each block of k steps is recomputed from its
 checkpoint while the adjoint sweeps it.  ``choose_checkpoint_interval`` picks
-k from the device memory available.  Every arithmetic step runs in CUDA
+the largest k the device memory allows; ``tune_checkpoint_interval`` times
+the candidates and keeps the fastest (the least memory among near-ties).  Every arithmetic step runs in CUDA
 kernels; this module orders them.
 """
 
@@ -43,6 +44,53 @@ def choose_checkpoint_interval(nt, field_bytes, budget_bytes):
         if need <= budget_bytes:
             best = k
     return best
+
+
+def checkpoint_memory(nt, k, field_bytes):
+    """Device bytes of checkpoint-every-k: 2·ceil(nt/k) checkpoint levels + k+2 block levels."""
+    return (k + 2 + 2 * math.ceil(nt / k)) * field_bytes
+
+
+def checkpoint_candidates(nt, field_bytes, budget_bytes):
+    """Intervals worth timing: the least-memory k (about √(2 nt)), a few multiples of
+    it, nt/4, nt/2 and the largest k that fits the budget."""
+    kmax = choose_checkpoint_interval(nt, field_bytes, budget_bytes)
+    kmin = min(range(1, nt + 1), key=lambda k: (checkpoint_memory(nt, k, field_bytes), k))
+    cands = {kmin, 2 * kmin, 4 * kmin, nt // 4, nt // 2, kmax}
+    return sorted(c for c in cands if 1 <= c <= kmax)
+
+
+def tune_checkpoint_interval(p, d_obs, m=None, candidates=None, memory_budget=None, tol=0.03):
+    """Pick the checkpoint interval by timing one gradient per candidate.
+
+    The recompute work is one forward pass whatever k is, so the times are
+    close; the fastest k wins, except that a candidate within ``tol`` of it
+    that holds less memory is preferred.  Returns (k, [(k, seconds, bytes)]).
+    """
+    torch = _dev()
+    nt = p["nt"]
+    with Solver(p["shape"], p["spacing"], p["so"], p["dt"], "acoustic", device=True) as s:
+        field_bytes = B.fd_field_elems(s.ctx) * 4
+    if memory_budget is None:
+        free, _ = torch.cuda.mem_get_info()
+        memory_budget = int(0.6 * free)
+    if candidates is None:
+        candidates = checkpoint_candidates(nt, field_bytes, memory_budget)
+    gradient(p, d_obs, m=m, k=candidates[0])   # untimed: first-use costs (graphs, pools)
+    torch.cuda.empty_cache()
+    rows = []
+    for k in candidates:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        gradient(p, d_obs, m=m, k=k)
+        e1.record()
+        e1.synchronize()
+        rows.append((int(k), e0.elapsed_time(e1) / 1e3, checkpoint_memory(nt, k, field_bytes)))
+        torch.cuda.empty_cache()          # the next candidate's buffers differ in size
+    fastest = min(r[1] for r in rows)
+    ok = [r for r in rows if r[1] <= fastest * (1.0 + tol)]
+    best = min(ok, key=lambda r: (r[2], r[1]))
+    return best[0], rows
 
 
 def _check_sparse_undamped(p):
@@ -81,12 +129,16 @@ def forward_traces(p, m=None):
     return rec
 
 
-def gradient(p, d_obs, m=None, k=None, memory_budget=None):
+def gradient(p, d_obs, m=None, k=None, memory_budget=None, stats=None, profile=False):
     """(J, dJ/dm) for shot p (fdsynth.acoustic_problem layout) against d_obs.
 
     m: model (defaults to p["m"]); k: checkpoint interval (None: chosen from
     the free device memory or ``memory_budget`` bytes).  Returns a float and a
-    torch tensor shaped like m on the device.
+    torch tensor shaped like m on the device.  ``stats`` (a dict, optional)
+    receives k, the device bytes held for checkpoints and the recompute block,
+    and the kernel launches of the forward and adjoint contexts; with
+    ``profile`` also their stencil launches and summed stencil milliseconds
+    (CUDA events per launch; steps are then launched one by one).
     """
     torch = _dev()
     _check_sparse_undamped(p)
@@ -94,12 +146,12 @@ def gradient(p, d_obs, m=None, k=None, memory_budget=None):
     work = torch.cuda.Stream()            # both contexts and every copy on one stream
     work.wait_stream(caller)
     with torch.cuda.stream(work):
-        J, g = _gradient_on_stream(p, d_obs, m, k, memory_budget)
+        J, g = _gradient_on_stream(p, d_obs, m, k, memory_budget, stats, profile)
     caller.wait_stream(work)
     return J, g
 
 
-def _gradient_on_stream(p, d_obs, m, k, memory_budget):
+def _gradient_on_stream(p, d_obs, m, k, memory_budget, stats=None, profile=False):
     torch = _dev()
     nt, dt = p["nt"], p["dt"]
     mm = torch.as_tensor(p["m"] if m is None else m, dtype=torch.float32, device="cuda")
@@ -109,8 +161,8 @@ def _gradient_on_stream(p, d_obs, m, k, memory_budget):
     rc = torch.as_tensor(p["rec_coords"], device="cuda")
     d_obs = torch.as_tensor(d_obs, dtype=torch.float32, device="cuda")
 
-    fwd = Solver(p["shape"], p["spacing"], p["so"], dt, "acoustic", device=True)
-    adj = Solver(p["shape"], p["spacing"], p["so"], dt, "acoustic", device=True)
+    fwd = Solver(p["shape"], p["spacing"], p["so"], dt, "acoustic", device=True, profile=profile)
+    adj = Solver(p["shape"], p["spacing"], p["so"], dt, "acoustic", device=True, profile=profile)
     try:
         fwd.set_model(mm, damp)
         fwd.set_sources(src, wav)
@@ -152,6 +204,14 @@ def _gradient_on_stream(p, d_obs, m, k, memory_budget):
                 adj.run(1)
                 i = n - n0 + 1                          # blk[i] = u^n
                 B.fd_imaging(adj.ctx, g, blk[i + 1], blk[i], blk[i - 1], scale)
+        if stats is not None:
+            stats.update(k=k, checkpoint_bytes=int(ck.numel()) * 4,
+                         block_bytes=int(blk.numel()) * 4,
+                         launches_forward=fwd.kernel_launches, launches_adjoint=adj.kernel_launches)
+            if profile:
+                nf, msf = fwd.profile()
+                na, msa = adj.profile()
+                stats.update(stencil_launches=nf + na, stencil_ms=msf + msa)
         torch.cuda.current_stream().synchronize()
         return J, g
     finally:

@@ -122,3 +122,23 @@ def test_autograd_returns_the_gradient():
     _, g = fwi.gradient(p, d_obs)
     assert torch.equal(m.grad, g)
     assert abs(float(J) - fwi.gradient(p, d_obs)[0]) <= 1e-12 * float(J)
+
+
+def test_checkpoint_interval_tuner_times_candidates_and_keeps_the_gradient():
+    from paper_1906_10811_b300 import fwi
+    p = _shot(shape=(24, 22, 27), nt=48)
+    d_obs = fwi.forward_traces(p, _true_model(p)).cpu().numpy()
+    k, rows = fwi.tune_checkpoint_interval(p, d_obs, candidates=[4, 12, 48])
+    assert [r[0] for r in rows] == [4, 12, 48]
+    assert k in (4, 12, 48)
+    assert all(r[1] > 0 for r in rows)
+    fastest = min(r[1] for r in rows)
+    chosen = [r for r in rows if r[0] == k][0]
+    assert chosen[1] <= 1.03 * fastest
+    ref = fwi.gradient(p, d_obs, k=48)[1]
+    import torch
+    assert torch.equal(fwi.gradient(p, d_obs, k=k)[1], ref)
+    st = {}
+    fwi.gradient(p, d_obs, k=k, stats=st)
+    assert st["k"] == k and st["launches_forward"] > 0 and st["launches_adjoint"] > 0
+    assert st["checkpoint_bytes"] + st["block_bytes"] == fwi.checkpoint_memory(48, k, st["block_bytes"] // (k + 2))

@@ -52,3 +52,4 @@ def test_zero_residual_gives_zero_gradient():
     J, g = fwi.gradient(m, damp, dt, h, 4, 10, src, wav, rec, d)
     Jr, gr = fwi.gradient(m, damp, dt, h, 4, 10, src, wav, rec, d + 1e-3)
     assert J < 1e-25 and np.abs(g).max() <= 1e-12 * np.abs(gr).max()
+
