@@ -41,7 +41,8 @@ def _load():
         lib = ctypes.CDLL(build())
         lib.oracle_laplacian.argtypes = [ctypes.c_int, _i64p, _f64p, ctypes.c_int, _f64p, _f64p, _f64p]
         lib.oracle_diffusion.argtypes = [ctypes.c_int, _i64p, _f64p, ctypes.c_int, _f64p,
-                                         ctypes.c_double, ctypes.c_double, ctypes.c_int, _f64p]
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                         ctypes.c_int, _f64p]
         lib.oracle_corners.argtypes = [ctypes.c_int, _i64p, _f64p, _f64p, _i64p, _f64p]
         lib.oracle_acoustic.argtypes = [ctypes.c_int, _i64p, _f64p, ctypes.c_int, _f64p,
                                         ctypes.c_double, _f64p, _f64p, _f64p, _f64p,
@@ -85,13 +86,18 @@ def laplacian(u, spacing, so, weights=None):
     return out
 
 
-def diffusion(u0, spacing, so, nu, dt, nt, weights=None):
-    """Forward-Euler diffusion, interior update, boundary nodes held; returns u^nt."""
+def diffusion(u0, spacing, so, nu, dt, nt, weights=None, boundary="zero"):
+    """Forward-Euler diffusion, interior update, boundary nodes held; returns u^nt.
+
+    boundary "zero": zero outside the grid; "odd": outside values are the
+    negated mirror images about the boundary nodes."""
     u = _d(u0).copy()
     w = _d(weights if weights is not None else fd_weights(so))
     h = _d(spacing)
+    bc = {"zero": 0, "odd": 1}[boundary]
     _check(_load().oracle_diffusion(u.ndim, _ptr(_shape(u.shape), _i64p), _ptr(h), so, _ptr(w),
-                                    float(nu), float(dt), int(nt), _ptr(u)), "oracle_diffusion")
+                                    float(nu), float(dt), int(nt), bc, _ptr(u)),
+           "oracle_diffusion")
     return u
 
 

@@ -18,8 +18,10 @@ import numpy as np
 from .weights import fd_weights
 
 
-def second_diff_matrix(n, h, so, weights=None):
-    """1-D matrix of Σ_k w_|k| u_{i+k} / h² with zero outside 0..n-1."""
+def second_diff_matrix(n, h, so, weights=None, odd=False):
+    """1-D matrix of Σ_k w_|k| u_{i+k} / h² with zero outside 0..n-1, or with
+    ``odd``: a column i+k outside the grid folds onto its mirror node about the
+    boundary node (0 or n-1) with the weight negated."""
     w = weights if weights is not None else fd_weights(so)
     r = so // 2
     a = np.zeros((n, n))
@@ -28,12 +30,15 @@ def second_diff_matrix(n, h, so, weights=None):
             j = i + k
             if 0 <= j < n:
                 a[i, j] += w[abs(k)] / (h * h)
+            elif odd:
+                jm = -j if j < 0 else 2 * (n - 1) - j
+                a[i, jm] -= w[abs(k)] / (h * h)
     return a
 
 
-def laplacian_matrix(shape, spacing, so, weights=None):
+def laplacian_matrix(shape, spacing, so, weights=None, odd=False):
     """Kronecker sum over axes; row-major (C order) flattening."""
-    mats = [second_diff_matrix(n, h, so, weights) for n, h in zip(shape, spacing)]
+    mats = [second_diff_matrix(n, h, so, weights, odd) for n, h in zip(shape, spacing)]
     size = int(np.prod(shape))
     lap = np.zeros((size, size))
     for d, md in enumerate(mats):
@@ -53,9 +58,9 @@ def tent_row(shape, spacing, coord):
     return wt.reshape(-1)
 
 
-def diffusion(u0, spacing, so, nu, dt, nt, weights=None):
+def diffusion(u0, spacing, so, nu, dt, nt, weights=None, boundary="zero"):
     shape = u0.shape
-    lap = laplacian_matrix(shape, spacing, so, weights)
+    lap = laplacian_matrix(shape, spacing, so, weights, odd=boundary == "odd")
     interior = np.ones(shape, dtype=bool)
     for d, n in enumerate(shape):
         sl = [slice(None)] * len(shape)

@@ -11,7 +11,10 @@
  * Arrays are dense, C order, interior only (no halo):
  *   ndim = 3: [n0][n1][n2]     ndim = 2: [n0][n1]      (last axis contiguous)
  * Axis d has n[d] nodes at coordinates i*h[d], i = 0..n[d]-1.
- * Values outside the grid are taken as zero (zero halo).
+ * Values outside the grid are taken as zero (zero halo), or, in the diffusion
+ * sweep's odd-reflection mode (bc = 1), as the negated value mirrored about
+ * the nearest boundary node: u(-k) = -u(k) and u(n-1+k) = -u(n-1-k) along the
+ * axis that leaves the grid (the stencil is a star: one axis at a time).
  *
  * Method (thesis §5.1.2 for the diffusion problem; §6.2.1 names the acoustic
  * operator with sources and receivers as the seismic operator the OPS backend
@@ -80,21 +83,40 @@ static void point_index(const grid_t *g, int64_t a, int64_t b, int64_t c,
   else { idx[0] = b; idx[1] = c; }
 }
 
+/* value of u at axis-d index j of the line through flat index p (whose axis-d
+ * index is i): inside the grid the node value; outside, 0 (bc = 0) or the odd
+ * mirror image about the boundary node (bc = 1) */
+static double neighbour(const double *u, const grid_t *g, int d, int64_t i, int64_t j,
+                        int64_t p, int bc) {
+  const int64_t n = g->n[d];
+  if (j >= 0 && j < n) return u[p + (j - i) * g->st[d]];
+  if (bc == 0) return 0.0;
+  const int64_t m = j < 0 ? -j : 2 * (n - 1) - j;   /* mirror index */
+  return -u[p + (m - i) * g->st[d]];
+}
+
 /* L u at the point with multi-index idx and flat index p, straight from the
- * definition; neighbours outside the grid contribute zero */
+ * definition */
 static double lap_point(const double *u, const grid_t *g, const double *h,
-                        int r, const double *w, const int64_t *idx, int64_t p) {
+                        int r, const double *w, const int64_t *idx, int64_t p, int bc) {
   double s = 0.0;
   for (int d = 0; d < g->ndim; ++d) {
     double sd = w[0] * u[p];
     for (int k = 1; k <= r; ++k) {
-      double up = idx[d] + k < g->n[d] ? u[p + k * g->st[d]] : 0.0;
-      double dn = idx[d] - k >= 0 ? u[p - k * g->st[d]] : 0.0;
+      double up = neighbour(u, g, d, idx[d], idx[d] + k, p, bc);
+      double dn = neighbour(u, g, d, idx[d], idx[d] - k, p, bc);
       sd += w[k] * (up + dn);
     }
     s += sd / (h[d] * h[d]);
   }
   return s;
+}
+
+/* the odd mirror needs a node at distance k inside: n - 1 >= r on every axis */
+static int mirror_ok(const grid_t *g, int r) {
+  for (int d = 0; d < g->ndim; ++d)
+    if (g->n[d] - 1 < r) return 0;
+  return 1;
 }
 
 static int on_boundary(const grid_t *g, const int64_t *idx) {
@@ -114,17 +136,19 @@ int oracle_laplacian(int ndim, const int64_t *shape, const double *h, int so,
       for (int64_t c = 0; c < g.e[2]; ++c) {
         int64_t idx[3], p = (a * g.e[1] + b) * g.e[2] + c;
         point_index(&g, a, b, c, idx);
-        out[p] = lap_point(u, &g, h, r, w, idx, p);
+        out[p] = lap_point(u, &g, h, r, w, idx, p, 0);
       }
   return OR_OK;
 }
 
-/* Diffusion, forward Euler, interior update (u is overwritten by u^{nt}). */
+/* Diffusion, forward Euler, interior update (u is overwritten by u^{nt});
+ * bc = 0: zero outside the grid, bc = 1: odd reflection about the boundary nodes. */
 int oracle_diffusion(int ndim, const int64_t *shape, const double *h, int so,
-                     const double *w, double nu, double dt, int nt, double *u) {
+                     const double *w, double nu, double dt, int nt, int bc, double *u) {
   grid_t g;
   if (grid_init(&g, ndim, shape) || so < 2 || so % 2 || nt < 0) return OR_EINVAL;
   const int r = so / 2;
+  if (bc != 0 && (bc != 1 || !mirror_ok(&g, r))) return OR_EINVAL;
   double *v = (double *)malloc(sizeof(double) * (size_t)g.total);
   if (!v) return OR_ENOMEM;
   double *cur = u, *nxt = v;
@@ -138,7 +162,7 @@ int oracle_diffusion(int ndim, const int64_t *shape, const double *h, int so,
           if (on_boundary(&g, idx))
             nxt[p] = cur[p];
           else
-            nxt[p] = cur[p] + nu * dt * lap_point(cur, &g, h, r, w, idx, p);
+            nxt[p] = cur[p] + nu * dt * lap_point(cur, &g, h, r, w, idx, p, bc);
         }
     double *t = cur; cur = nxt; nxt = t;
   }
@@ -245,7 +269,7 @@ int oracle_acoustic(int ndim, const int64_t *shape, const double *h, int so,
           int64_t idx[3], p = (a * g.e[1] + b) * g.e[2] + c;
           point_index(&g, a, b, c, idx);
           double sigma = (damp ? damp[p] : 0.0) * dt / 2.0;
-          double lap = lap_point(cur, &g, h, r, w, idx, p);
+          double lap = lap_point(cur, &g, h, r, w, idx, p, 0);
           nxt[p] = (dt * dt * lap + 2.0 * m[p] * cur[p] -
                     (m[p] - sigma) * prv[p]) / (m[p] + sigma);
         }

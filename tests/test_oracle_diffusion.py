@@ -94,3 +94,65 @@ def test_bad_arguments_raise():
         core.diffusion(np.zeros((4, 4)), (1.0, 1.0), 3, 0.5, 0.1, 1, weights=[-2.0, 1.0])
     with pytest.raises(core.OracleError):
         core.diffusion(np.zeros((4, 4)), (1.0, 1.0), 2, 0.5, 0.1, -1)
+
+
+# ----------------------------------------------------------------------------
+# Odd-reflection boundary mode: values outside the grid are the negated mirror
+# images about the boundary nodes, which makes every sine mode an exact
+# eigenvector of the interior update at every space order.
+# ----------------------------------------------------------------------------
+def _odd_factor(so, n, ndim, k, nu, dt):
+    """Exact per-step factor of Π sin(k_d π x_d) under the odd-reflection update:
+    1 + ν dt Σ_d (w_0 + 2 Σ_j w_j cos(j k_d π h)) / h²  (h = 1/(n-1))."""
+    from oracle.weights import fd_weights
+    w = [float(x) for x in fd_weights(so)]
+    h = 1.0 / (n - 1)
+    lam = sum((w[0] + 2.0 * sum(w[j] * math.cos(j * kd * math.pi * h)
+                                for j in range(1, so // 2 + 1))) / (h * h) for kd in k[:ndim])
+    return 1.0 + nu * dt * lam
+
+
+@pytest.mark.parametrize("so", (2, 4, 6, 8, 10, 12, 14, 16))
+@pytest.mark.parametrize("ndim,n,k", [(2, 41, (1, 1)), (2, 30, (2, 3)), (3, 19, (1, 2, 1))])
+def test_odd_reflection_sine_mode_decays_by_exact_factor(so, ndim, n, k):
+    u0, h = _sine_mode(n, ndim, k)
+    nu, nt = 0.5, 40
+    dt = 0.05 * h * h / nu
+    g = _odd_factor(so, n, ndim, k, nu, dt)
+    u = core.diffusion(u0, (h,) * ndim, so, nu, dt, nt, boundary="odd")
+    assert np.abs(u - g ** nt * u0).max() < 1e-13
+    if so > 2:   # the zero halo breaks the eigenvector property above so = 2
+        z = core.diffusion(u0, (h,) * ndim, so, nu, dt, nt)
+        assert np.abs(z - g ** nt * u0).max() > 1e-9
+
+
+def test_odd_reflection_equals_zero_halo_at_second_order():
+    """At so = 2 the node next to a boundary reaches only the boundary node."""
+    rng = np.random.default_rng(11)
+    u0 = rng.standard_normal((9, 10, 11))
+    for d in range(3):
+        for i in (0, u0.shape[d] - 1):
+            sl = [slice(None)] * 3
+            sl[d] = i
+            u0[tuple(sl)] = 0.0
+    a = core.diffusion(u0, (0.3, 0.25, 0.2), 2, 0.5, 0.002, 7, boundary="odd")
+    b = core.diffusion(u0, (0.3, 0.25, 0.2), 2, 0.5, 0.002, 7)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("so", (4, 8, 12))
+@pytest.mark.parametrize("shape", [(9, 11), (7, 8, 9)])
+def test_odd_reflection_matches_dense_brute_force(so, shape):
+    rng = np.random.default_rng(so + len(shape))
+    u0 = rng.standard_normal(shape)
+    spacing = tuple(rng.uniform(0.2, 0.4, len(shape)))
+    if max(shape) - 1 < so // 2 or min(shape) - 1 < so // 2:
+        pytest.skip("grid too small for the mirror")
+    a = core.diffusion(u0, spacing, so, 0.7, 0.002, 5, boundary="odd")
+    b = dense.diffusion(u0, spacing, so, 0.7, 0.002, 5, boundary="odd")
+    assert np.abs(a - b).max() < 1e-12
+
+
+def test_odd_reflection_needs_room_for_the_mirror():
+    with pytest.raises(core.OracleError):
+        core.diffusion(np.zeros((5, 9)), (1.0, 1.0), 10, 0.5, 0.01, 1, boundary="odd")
