@@ -43,7 +43,8 @@ import numpy as np  # noqa: E402
 
 import fdsynth  # noqa: E402
 
-BYTES_PER_POINT = {"acoustic": 20}   # read u^n, u^{n-1}, A, C; write u^{n+1} (FP32)
+BYTES_PER_POINT = {"acoustic": 20,   # read u^n, u^{n-1}, A, C; write u^{n+1} (FP32)
+                   "diffusion": 8}   # read u^n, write u^{n+1}
 FALLBACK_HBM_GBS = 6400.0
 
 WORKLOADS = {
@@ -69,7 +70,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="acoustic256",
-                    choices=sorted(WORKLOADS) + ["serving", "fwi320"])
+                    choices=sorted(WORKLOADS) + ["serving", "fwi320", "diffusion512"])
+    ap.add_argument("--boundary", default="zero", choices=["zero", "odd"],
+                    help="diffusion512: values outside the grid (zero halo or odd reflection)")
     ap.add_argument("--fwi-k", type=int, default=0,
                     help="fwi320: checkpoint interval (0: tuned by timing the candidates)")
     ap.add_argument("--shots", type=int, default=64)
@@ -245,8 +248,8 @@ def run_reference(args):
         return 0
     if args.workload == "fwi320":
         return run_reference_fwi(args)
-    if args.workload == "serving":
-        args.workload = "acoustic256"     # the oracle serves no stream: time its shot sample
+    if args.workload in ("serving", "diffusion512"):
+        args.workload = "acoustic256"     # the oracle's timed sample: the acoustic shot
     w, p = problem(args)
     _, t1 = time_oracle(p, 1)
     per_step = int(max(1, min(p["nt"], round(6.0 / max(t1, 1e-3)))))
@@ -425,6 +428,141 @@ def run_fwi(args):
                 "config": dict(fwi_config(w, k, tuning),
                                checkpoint_bytes=stats.get("checkpoint_bytes"),
                                block_bytes=stats.get("block_bytes")),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_diffusion(args):
+    """3-D diffusion sweep at 512³ (sine-mode data, ν dt/h² = 0.05, interior update)."""
+    import torch
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1906_10811_b300 import Solver, build
+    build.build()
+    n, so, nt = 512, args.so or 8, args.nt or 200
+    q = fdsynth.diffusion_problem(n, ndim=3, courant=0.05)
+    npts = n ** 3
+    u0_d = torch.from_numpy(q["u0"]).cuda()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    bench_stream = torch.cuda.Stream()
+    bench_stream.wait_stream(torch.cuda.current_stream())
+    torch.cuda.set_stream(bench_stream)
+    s = Solver((n,) * 3, q["spacing"], so, q["dt"], "diffusion", nu=q["nu"], device=True,
+               profile=True, kernel=args.kernel, boundary=args.boundary)
+    tile, tune_tried = None, None
+    if s.kernel_name.startswith("stencil3d_tma"):
+        s.set_field(u0_d)
+        if args.tile == "auto":
+            tune_tried = len(s.autotune(reps=5)[1])
+        elif args.tile != "default":
+            ty, zb, cps = (int(v) for v in args.tile.split(","))
+            s.set_tile_config(tile_y=ty, zblock=zb, ctas_per_sm=cps)
+        tile = s.tile_config
+
+    def sweep():
+        s.set_field(u0_d)
+        s.set_step(0)
+        s.run(nt)
+
+    for _ in range(args.warmup):
+        sweep()
+    s.profile()
+    launches0 = s.kernel_launches
+    clocks = ClockSampler("GPU-" + str(torch.cuda.get_device_properties(local).uuid))
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        sweep()
+    e1.record(stream)
+    barrier()
+    ms = reduce_max(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    launches = s.kernel_launches - launches0
+    n_st, st_ms = s.profile()
+    kernel_name = s.kernel_name
+    s.close()
+    value = whole_job_rate(npts * nt * args.steps, world, ms / 1e3) / 1e9
+    peak, peak_kind = load_peak()
+    avg_s = st_ms / max(n_st, 1) / 1e3
+    achieved = BYTES_PER_POINT["diffusion"] * npts / avg_s / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "kernel": kernel_name,
+                "bytes_per_point": BYTES_PER_POINT["diffusion"], "points_per_launch": npts,
+                "avg_launch_us": round(avg_s * 1e6, 2), "launches_timed": n_st,
+                "stencil_share_of_step": round(st_ms / ms, 4),
+                "peak_source": f"{peak_kind} HBM copy bandwidth (of {peak_kind})",
+                "gpts_per_s_kernel": round(npts / avg_s / 1e9, 2)}
+    e2e = None
+    if not args.no_e2e:
+        u0_h = torch.from_numpy(q["u0"]).pin_memory().numpy()
+        out_h = torch.empty((n,) * 3, dtype=torch.float32).pin_memory().numpy()
+        se = Solver((n,) * 3, q["spacing"], so, q["dt"], "diffusion", nu=q["nu"],
+                    kernel=args.kernel, boundary=args.boundary)
+        if tile is not None:
+            se.set_tile_config(tile_y=tile["tile_y"], zblock=tile["zblock"],
+                               ctas_per_sm=tile["ctas_per_sm"])
+        from paper_1906_10811_b300 import binding as B
+
+        def sweep_e2e():
+            se.set_field(u0_h)
+            se.set_step(0)
+            se.run(nt)
+            B.fd_read(se.ctx, out_h, None)
+
+        sweep_e2e()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sweep_e2e()
+        barrier()
+        te = reduce_max(time.perf_counter() - t0)
+        se.close()
+        e2e = {"value": round(whole_job_rate(npts * nt * args.steps, world, te) / 1e9, 3),
+               "unit": "GPts/s", "h2d_bytes_per_step": int(u0_h.nbytes),
+               "d2h_bytes_per_step": int(out_h.nbytes)}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import core as oracle
+        t0 = time.perf_counter()
+        k = 0
+        while time.perf_counter() - t0 < args.cpu_seconds or k == 0:
+            oracle.diffusion(q["u0"], q["spacing"], so, q["nu"], q["dt"], 1,
+                             boundary=args.boundary)
+            k += 1
+        tc = time.perf_counter() - t0
+        cpu = {"value": round(npts * k / tc / 1e9, 4), "unit": "GPts/s", "cores": cpu_threads(),
+               "kind": "oracle", "sample": f"{k} single time steps of the same 512^3 sweep "
+                                           f"(FP64, {tc:.1f} s), OpenMP over grid rows"}
+    if rank == 0:
+        line = {"metric": "GPts/s & % HBM roofline per stencil", "value": round(value, 3),
+                "unit": "GPts/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"diffusion3d_{n}^3_so{so}_nt{nt}", "grid": [n] * 3,
+                           "space_order": so, "nt": nt, "nu": q["nu"],
+                           "nu_dt_over_h2": 0.05, "boundary": args.boundary,
+                           "initial_data": "sin(pi x) sin(pi y) sin(pi z), boundary nodes 0",
+                           "step": "one sweep: field reset + nt time steps",
+                           "l2": "inputs larger than L2 (u^n, u^{n+1} = 2 x %.0f MB)" %
+                                 ((n + so) ** 2 * (n + 64) * 4 / 1e6),
+                           "kernel": kernel_name, "tile": tile,
+                           "tile_choice": ("autotuned over %d configurations" % tune_tried
+                                           if tune_tried else args.tile)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk}
         print(json.dumps(line), flush=True)
@@ -626,6 +764,8 @@ def main():
         return run_serving(args)
     if args.workload == "fwi320":
         return run_fwi(args)
+    if args.workload == "diffusion512":
+        return run_diffusion(args)
     return run_ours(args)
 
 

@@ -73,6 +73,17 @@ typedef enum {
   FD_KERNEL_TMA = 2    /* 3-D: TMA-fed shared-memory plane ring, z streamed in registers */
 } fd_kernel;
 
+/*
+ * Values outside the grid.  FD_BOUNDARY_ZERO: the zero halo (every equation).
+ * FD_BOUNDARY_ODD (FD_DIFFUSION only): before each step the halo takes the
+ * negated mirror image of the interior about the boundary nodes, u(-k) =
+ * -u(k) and u(n-1+k) = -u(n-1-k) along each axis, so every sine mode
+ * Π sin(k_d π x_d) is an exact eigenvector of the interior update at every
+ * space order (the closed-form decay of §5.1.2's problem then holds beyond
+ * so = 2).  Needs n_d - 1 >= space_order/2 on every axis (FD_EINVAL).
+ */
+typedef enum { FD_BOUNDARY_ZERO = 0, FD_BOUNDARY_ODD = 1 } fd_boundary;
+
 typedef struct {
   double nu;          /* diffusion coefficient ν (FD_DIFFUSION only); default 0.5,
                          the benchmark value of §5.1.2 */
@@ -85,6 +96,7 @@ typedef struct {
   int autotune;       /* 1: fd_create runs fd_autotune on the pipelined kernel (its
                          choice is cached per grid shape, space order and equation
                          for the process); 0 (default): the default tile */
+  int boundary;       /* fd_boundary; default FD_BOUNDARY_ZERO */
 } fd_options;
 
 /* Fill *opt with the defaults above. */

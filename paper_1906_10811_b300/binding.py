@@ -21,6 +21,7 @@ STATUS_NAMES = ["FD_OK", "FD_EINVAL", "FD_ENOMEM", "FD_ECUDA", "FD_ESTATE", "FD_
                 "FD_EUNSUPPORTED"]
 FD_DIFFUSION, FD_ACOUSTIC = 0, 1
 FD_KERNEL_AUTO, FD_KERNEL_PLAIN, FD_KERNEL_TMA = 0, 1, 2
+FD_BOUNDARY_ZERO, FD_BOUNDARY_ODD = 0, 1
 
 
 class FdError(RuntimeError):
@@ -34,7 +35,7 @@ class fd_options(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
                 ("device_ptrs", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("profile", ctypes.c_int), ("kernel", ctypes.c_int),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("boundary", ctypes.c_int)]
 
 
 class fd_tile_config(ctypes.Structure):
@@ -155,7 +156,7 @@ def _out_ptr(x):
 
 
 def options(nu=0.5, cuda_stream=None, device_ptrs=False, use_graphs=True, profile=False,
-            kernel=FD_KERNEL_AUTO, autotune=False):
+            kernel=FD_KERNEL_AUTO, autotune=False, boundary=FD_BOUNDARY_ZERO):
     o = fd_options()
     load().fd_options_default(ctypes.byref(o))
     o.nu = nu
@@ -165,6 +166,7 @@ def options(nu=0.5, cuda_stream=None, device_ptrs=False, use_graphs=True, profil
     o.profile = int(bool(profile))
     o.kernel = int(kernel)
     o.autotune = int(bool(autotune))
+    o.boundary = int(boundary)
     return o
 
 

@@ -396,6 +396,15 @@ fd_status enqueue_chunk(fd_ctx *c, int parity, int len, bool timed) {
     const int b = parity ^ (j & 1);
     float *ucur = c->u[b], *unext = c->u[b ^ 1];
     if (overlap && j >= 2) CU(cudaStreamWaitEvent(c->stream, c->ev_rec[j & 1], 0));
+    if (c->opt.boundary == FD_BOUNDARY_ODD) {
+      // halo of u^n = odd mirror of the interior about the boundary nodes
+      const int64_t cells = 2LL * c->g.R *
+                            ((c->g.R0 ? (int64_t)c->g.n1 * c->g.n2 : 0) +
+                             (int64_t)c->g.n0 * c->g.n2 + (int64_t)c->g.n0 * c->g.n1);
+      k_odd_halo<<<(unsigned)std::min<int64_t>((cells + 255) / 256, 4096), 256, 0, c->stream>>>(
+          ucur, c->g);
+      CHECK_LAUNCH();
+    }
     if (timed) {
       if (c->ev_used + 2 > c->ev.size()) {
         for (int k = 0; k < 64; ++k) {
@@ -683,6 +692,16 @@ fd_status fd_create(fd_ctx **out, int ndim, const int64_t *shape, const double *
   if (opt) o = *opt;
   if (o.kernel < FD_KERNEL_AUTO || o.kernel > FD_KERNEL_TMA)
     return fail(nullptr, FD_EINVAL, "unknown kernel selector %d", o.kernel);
+  if (o.boundary != FD_BOUNDARY_ZERO && o.boundary != FD_BOUNDARY_ODD)
+    return fail(nullptr, FD_EINVAL, "unknown boundary mode %d", o.boundary);
+  if (o.boundary == FD_BOUNDARY_ODD) {
+    if (eq != FD_DIFFUSION)
+      return fail(nullptr, FD_EUNSUPPORTED, "FD_BOUNDARY_ODD is for FD_DIFFUSION");
+    for (int d = 0; d < ndim; ++d)
+      if (shape[d] - 1 < space_order / 2)
+        return fail(nullptr, FD_EINVAL,
+                    "FD_BOUNDARY_ODD needs shape[%d] - 1 >= space_order/2 for the mirror", d);
+  }
   const double S = lib_symbol(space_order);
   if (eq == FD_DIFFUSION) {
     if (!(o.nu > 0.0) || !std::isfinite(o.nu)) return fail(nullptr, FD_EINVAL, "nu must be positive");

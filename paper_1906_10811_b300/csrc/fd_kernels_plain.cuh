@@ -273,6 +273,55 @@ __global__ void k_interp_batch(const int2 *__restrict__ e, int n, const MemberDe
 
 namespace fdk {
 
+// Odd-reflection boundary (diffusion): before a step, every halo cell at
+// distance k = 1..R beyond a boundary node along one axis takes the negated
+// value at distance k inside it, u(-k) = -u(k), u(n-1+k) = -u(n-1-k).  Only
+// the faces are filled (over the interior of the other axes): the star
+// stencil never reads an edge or corner of the halo.  One thread per cell,
+// grid-stride; threads run x fastest within a face so rows stay coalesced.
+__global__ void k_odd_halo(float *__restrict__ u, Geom g) {
+  const int R = g.R;
+  const int64_t n0 = g.n0, n1 = g.n1, n2 = g.n2;
+  const int64_t f0 = g.R0 ? 2LL * R * n1 * n2 : 0;  // axis-0 faces (3-D only)
+  const int64_t f1 = 2LL * R * n0 * n2;             // axis-1 faces
+  const int64_t f2 = 2LL * R * n0 * n1;             // axis-2 faces
+  const int64_t total = f0 + f1 + f2;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t s = t;
+    int z, y, x, zs, ys, xs;
+    if (s < f0) {  // [side][k][y][x]
+      x = (int)(s % n2); s /= n2;
+      y = (int)(s % n1); s /= n1;
+      const int k = (int)(s % R) + 1, side = (int)(s / R);
+      z = side ? (int)n0 - 1 + k : -k;
+      zs = side ? (int)n0 - 1 - k : k;
+      ys = y;
+      xs = x;
+    } else if ((s -= f0) < f1) {  // [z][side][k][x]
+      x = (int)(s % n2); s /= n2;
+      const int k = (int)(s % R) + 1; s /= R;
+      const int side = (int)(s % 2);
+      z = (int)(s / 2);
+      y = side ? (int)n1 - 1 + k : -k;
+      ys = side ? (int)n1 - 1 - k : k;
+      zs = z;
+      xs = x;
+    } else {  // [z][y][side][k]
+      s -= f1;
+      const int k = (int)(s % R) + 1; s /= R;
+      const int side = (int)(s % 2); s /= 2;
+      y = (int)(s % n1);
+      z = (int)(s / n1);
+      x = side ? (int)n2 - 1 + k : -k;
+      xs = side ? (int)n2 - 1 - k : k;
+      zs = z;
+      ys = y;
+    }
+    u[gidx(g, z, y, x)] = -u[gidx(g, zs, ys, xs)];
+  }
+}
+
 // FWI imaging condition: g[i] += s · ν(i) · (u⁺(i) − 2u(i) + u⁻(i)) over the
 // interior points (g dense, the rest padded), the discrete cross-correlation
 // of the adjoint field with the second time difference of the forward field.

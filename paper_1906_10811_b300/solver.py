@@ -12,6 +12,7 @@ from . import binding as B
 
 _EQ = {"diffusion": B.FD_DIFFUSION, "acoustic": B.FD_ACOUSTIC}
 _KERNEL = {"auto": B.FD_KERNEL_AUTO, "plain": B.FD_KERNEL_PLAIN, "tma": B.FD_KERNEL_TMA}
+_BOUNDARY = {"zero": B.FD_BOUNDARY_ZERO, "odd": B.FD_BOUNDARY_ODD}
 
 
 class Solver:
@@ -24,7 +25,7 @@ class Solver:
 
     def __init__(self, shape, spacing, space_order, dt, equation="acoustic", nu=0.5,
                  device=False, stream=None, graphs=True, profile=False, kernel="auto",
-                 autotune=False):
+                 autotune=False, boundary="zero"):
         self.ctx = None
         self.shape = tuple(int(s) for s in shape)
         self.ndim = len(self.shape)
@@ -43,7 +44,8 @@ class Solver:
             cuda_stream = s.cuda_stream
             self.stream = s
         opt = B.options(nu=nu, cuda_stream=cuda_stream, device_ptrs=self.device, use_graphs=graphs,
-                        profile=profile, kernel=_KERNEL[kernel], autotune=autotune)
+                        profile=profile, kernel=_KERNEL[kernel], autotune=autotune,
+                        boundary=_BOUNDARY[boundary])
         self._in()
         self.ctx = B.fd_create(self.ndim, self.shape, spacing, space_order, dt, _EQ[equation], opt)
         self._out()

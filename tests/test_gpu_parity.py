@@ -69,6 +69,63 @@ def test_diffusion_parity(so, shape):
     assert rel_l2(u, ref) <= TOL_DIFF
 
 
+@pytest.mark.parametrize("so", (2, 4, 8, 12, 16))
+@pytest.mark.parametrize("kernel", ("plain", "auto"))
+@pytest.mark.parametrize("shape", [(30, 41), (17, 23, 41), (9, 34, 33)])
+def test_diffusion_odd_reflection_parity(so, kernel, shape):
+    """Odd-reflection boundary: random data against the oracle's odd mode."""
+    from paper_1906_10811_b300 import Solver, fd_stability_symbol
+    nd = len(shape)
+    u0 = fdsynth.random_field(shape, seed=so + 1)
+    for d in range(nd):                       # boundary nodes hold 0
+        for i in (0, shape[d] - 1):
+            sl = [slice(None)] * nd
+            sl[d] = i
+            u0[tuple(sl)] = 0.0
+    h = (0.8,) * nd
+    lam = sum(fd_stability_symbol(so) / hd ** 2 for hd in h)
+    nu = 0.6
+    dt = fdsynth.f32(0.9 * 2 / (nu * lam))
+    with Solver(shape, h, so, dt, "diffusion", nu=nu, kernel=kernel, boundary="odd") as s:
+        s.set_field(u0)
+        s.run(30)
+        u, _ = s.read()
+    ref = oracle.diffusion(u0, h, so, nu, dt, 30, boundary="odd")
+    assert rel_l2(u, ref) <= TOL_DIFF
+    zero = oracle.diffusion(u0, h, so, nu, dt, 30)
+    if so > 2:
+        assert rel_l2(u, zero) > 10 * TOL_DIFF      # the mode really changed the result
+
+
+@pytest.mark.parametrize("so", (4, 8, 16))
+def test_diffusion_odd_reflection_sine_mode_closed_form(so):
+    """3-D sine mode under the odd-reflection boundary decays by the exact discrete
+    factor 1 + ν dt Σ_d (w_0 + 2 Σ_j w_j cos(j π h)) / h² at every order."""
+    from paper_1906_10811_b300 import Solver, fd_weights
+    n = 48
+    p = fdsynth.diffusion_problem(n, ndim=3, courant=0.05)
+    h = p["spacing"][0]
+    w = fd_weights(so)
+    lam = (w[0] + 2 * sum(w[j] * math.cos(j * math.pi * h) for j in range(1, so // 2 + 1))) / h ** 2
+    g = 1 + 0.5 * p["dt"] * 3 * lam
+    with Solver((n,) * 3, p["spacing"], so, p["dt"], "diffusion", nu=0.5, boundary="odd") as s:
+        s.set_field(p["u0"])
+        s.run(60)
+        u, _ = s.read()
+    assert rel_l2(u, g ** 60 * p["u0"].astype(np.float64)) <= TOL_DIFF
+
+
+def test_odd_reflection_is_rejected_where_it_does_not_apply():
+    from paper_1906_10811_b300 import Solver
+    from paper_1906_10811_b300.binding import FD_EINVAL, FD_EUNSUPPORTED, FdError
+    with pytest.raises(FdError) as e:
+        Solver((20, 20, 20), (10.0,) * 3, 8, 0.1, "acoustic", boundary="odd")
+    assert e.value.status == FD_EUNSUPPORTED
+    with pytest.raises(FdError) as e:
+        Solver((20, 4), (1.0, 1.0), 8, 0.01, "diffusion", boundary="odd")
+    assert e.value.status == FD_EINVAL
+
+
 def test_diffusion_boundary_held_and_plain_vs_auto():
     from paper_1906_10811_b300 import Solver
     shape = (21, 18, 40)
