@@ -197,6 +197,26 @@ fd_status fd_imaging(fd_ctx *adj, float *g, const float *u_next, const float *u_
                      const float *u_prev, double scale);
 
 /*
+ * The same FWI operations fused into a time step of the pipelined kernel (3-D
+ * FD_ACOUSTIC, default tile height; FD_EUNSUPPORTED otherwise), so that the
+ * backward sweep neither copies the recomputed wavefield nor re-reads ν:
+ *
+ * fd_step_fwi: advance ctx one step exactly as fd_run(ctx, 1) does, and in the
+ *   stencil's epilogue, at every interior point (padded layout, device,
+ *   fd_field_elems floats each):
+ *     d2_out (may be NULL):  d2_out = (u^{n+1} − u^n) − (u^n − u^{n−1})
+ *     img_g  (may be NULL):  img_g += scale · u^{n+1} · img_d2
+ *   with the arithmetic of fd_imaging, so a gradient accumulated this way is
+ *   bitwise the one fd_snapshot + fd_imaging give (img_g then padded).
+ *   FD_EINVAL if img_g is set without img_d2.  Asynchronous on the stream.
+ * fd_field_to_dense: copy the interior of a padded field of ctx into a dense
+ *   [n0][n1][n2] device array (asynchronous).
+ */
+fd_status fd_step_fwi(fd_ctx *ctx, float *d2_out, float *img_g, const float *img_d2,
+                      double scale);
+fd_status fd_field_to_dense(fd_ctx *ctx, const float *padded, float *dense);
+
+/*
  * Tile configuration of the pipelined 3-D kernel (FD_KERNEL_TMA/AUTO on 3-D
  * grids).  The paper leaves tiling strategy to the OPS library (§2.2) and
  * cites stencil compilers that block the iteration space per thread to save

@@ -77,6 +77,8 @@ SIGNATURES = {
     "fd_snapshot": (ctypes.c_int, [_vp, _vp, _vp]),
     "fd_restore": (ctypes.c_int, [_vp, _vp, _vp]),
     "fd_imaging": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_double]),
+    "fd_step_fwi": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_double]),
+    "fd_field_to_dense": (ctypes.c_int, [_vp, _vp, _vp]),
     "fd_destroy": (None, [_vp]),
     "fd_last_error": (ctypes.c_char_p, [_vp]),
     "fd_weights": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
@@ -329,6 +331,16 @@ def fd_restore(ctx, src_cur, src_prev):
 def fd_imaging(adj, g, u_next, u_cur, u_prev, scale):
     _check(adj, load().fd_imaging(adj, _out_ptr(g), _ptr(u_next, []), _ptr(u_cur, []),
                                   _ptr(u_prev, []), float(scale)))
+
+
+def fd_step_fwi(ctx, d2_out=None, img_g=None, img_d2=None, scale=0.0):
+    keep = []
+    _check(ctx, load().fd_step_fwi(ctx, _out_ptr(d2_out), _out_ptr(img_g), _ptr(img_d2, keep),
+                                   float(scale)))
+
+
+def fd_field_to_dense(ctx, padded, dense):
+    _check(ctx, load().fd_field_to_dense(ctx, _ptr(padded, []), _out_ptr(dense)))
 
 
 def fd_destroy(ctx):

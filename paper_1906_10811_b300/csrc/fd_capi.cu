@@ -102,6 +102,11 @@ struct fd_ctx {
   bool use_tma = false;
   bool iso = false;          // equal spacing on all axes (pipelined kernel variant)
   double tune_us = 0.0;      // stencil µs of the current tile configuration, if measured
+  // FWI epilogue of the step fd_step_fwi launches (see launch_stencil)
+  bool fwi_on = false;
+  float *fwi_d2 = nullptr, *fwi_img = nullptr;
+  const float *fwi_img_d2 = nullptr;
+  float fwi_scale = 0.f;
   const char *kernel_name = "none";
   // sources
   int nsrc = 0, nt_wav = 0;
@@ -307,8 +312,11 @@ fd_status launch_stencil(fd_ctx *c, const float *ucur, float *unext, int j) {
       sp.nsrc = c->nsrc;
       sp.nc = c->nc;
     }
-    cudaError_t e = launch_tma_step(c->tma, ucur == c->u[0] ? 0 : 1, unext, c->coef, c->d_err, sp,
-                                    c->stream);
+    const int cur = ucur == c->u[0] ? 0 : 1;
+    cudaError_t e =
+        c->fwi_on ? launch_tma_step_fwi(c->tma, cur, unext, c->coef, c->d_err, sp, c->fwi_d2,
+                                        c->fwi_img, c->fwi_img_d2, c->fwi_scale, c->stream)
+                  : launch_tma_step(c->tma, cur, unext, c->coef, c->d_err, sp, c->stream);
     if (e != cudaSuccess) return fail(c, FD_ECUDA, "TMA stencil launch: %s", cudaGetErrorString(e));
     ++c->launches;
     return FD_OK;
@@ -961,10 +969,14 @@ fd_status fd_set_receivers(fd_ctx *c, int nrec, const float *coords) {
   return FD_OK;
 }
 
-fd_status fd_run(fd_ctx *c, int nt) {
-  fd_status st = check_usable(c);
-  if (st) return st;
-  if (nt < 0) return fail(c, FD_EINVAL, "nt must be >= 0");
+}  // extern "C"
+
+namespace {
+
+// The time loop: nt steps from the current state, by graph replay (graphs)
+// or by launching each step.
+fd_status run_steps(fd_ctx *c, int nt, bool graphs) {
+  fd_status st = FD_OK;
   if (c->eq == FD_ACOUSTIC && !c->model_set)
     return fail(c, FD_ESTATE, "fd_set_model has not succeeded");
   if (c->nsrc > 0 && c->step + nt > c->nt_wav)
@@ -989,7 +1001,7 @@ fd_status fd_run(fd_ctx *c, int nt) {
   }
   for (int done = 0; done < nt;) {
     const int len = std::min(kGraphChunk, nt - done);
-    if (c->opt.use_graphs && !c->opt.profile) {
+    if (graphs && c->opt.use_graphs && !c->opt.profile) {
       cudaGraphExec_t exec;
       int64_t kernels = 0;
       st = get_graph(c, c->cur, len, &exec, &kernels);
@@ -1005,6 +1017,44 @@ fd_status fd_run(fd_ctx *c, int nt) {
   }
   c->step += nt;
   if (c->nrec > 0) c->rec_rows = c->step + 1;
+  return FD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fd_status fd_run(fd_ctx *c, int nt) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  if (nt < 0) return fail(c, FD_EINVAL, "nt must be >= 0");
+  return run_steps(c, nt, true);
+}
+
+fd_status fd_step_fwi(fd_ctx *c, float *d2_out, float *img_g, const float *img_d2, double scale) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  if (c->eq != FD_ACOUSTIC || !c->use_tma || !c->tma.fn_fwi)
+    return fail(c, FD_EUNSUPPORTED,
+                "fd_step_fwi needs the pipelined 3-D acoustic kernel at its default tile");
+  if (img_g && !img_d2) return fail(c, FD_EINVAL, "img_g needs img_d2");
+  c->fwi_d2 = d2_out;
+  c->fwi_img = img_g;
+  c->fwi_img_d2 = img_d2;
+  c->fwi_scale = (float)scale;
+  c->fwi_on = true;
+  st = run_steps(c, 1, false);
+  c->fwi_on = false;
+  return st;
+}
+
+fd_status fd_field_to_dense(fd_ctx *c, const float *padded, float *dense) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  if (!padded || !dense) return fail(c, FD_EINVAL, "NULL field");
+  const int64_t n = (int64_t)c->g.n0 * c->g.n1 * c->g.n2;
+  k_gather<<<blocks_for(n, 256), 256, 0, c->stream>>>(padded, dense, c->g);
+  CHECK_LAUNCH();
   return FD_OK;
 }
 
@@ -1602,7 +1652,8 @@ fd_status fd_batch_run(fd_batch *b, int nticks) {
   for (int t = 0; t < nticks; ++t) {
     if (n3) {
       plan0.fn_multi<<<grid3, kTmaThreads, plan0.smem_multi, b->stream>>>(
-          plan0.map_u[0], plan0.map_t[0], plan0.map_a, plan0.map_c, TmaArgs{}, ba);
+          plan0.map_u[0], plan0.map_t[0], plan0.map_a, plan0.map_c, plan0.map_c, plan0.map_c,
+          TmaArgs{}, ba);
       BCU(cudaGetLastError());
       ++b->launches;
     }

@@ -55,10 +55,14 @@ __host__ __device__ constexpr int tma_bh(int R, int NY) { return tma_ty(NY) + 2 
 __host__ __device__ constexpr int tma_ubytes(int R, int NY) { return tma_bw(R) * tma_bh(R, NY) * 4; }
 __host__ __device__ constexpr int tma_xbytes(int NY) { return kTmaTX * tma_ty(NY) * 4; }
 __host__ __device__ constexpr int tma_align128(int b) { return (b + 127) / 128 * 128; }
-// shared memory: barriers (1 KB) | ring U | ring X (three tiles per slot)
-__host__ __device__ constexpr int tma_smem_bytes(int R, int NY, bool acoustic) {
+// ring X: kTmaDX slots of (u^{n-1}, A, C); with the FWI epilogue 2 slots of
+// (u^{n-1}, A, C, d2, g) so two CTAs still fit on an SM
+__host__ __device__ constexpr int tma_dx(bool fwi) { return fwi ? 2 : kTmaDX; }
+__host__ __device__ constexpr int tma_xn(bool fwi) { return fwi ? 5 : 3; }
+// shared memory: barriers (1 KB) | ring U | ring X
+__host__ __device__ constexpr int tma_smem_bytes(int R, int NY, bool acoustic, bool fwi = false) {
   return 1024 + tma_du(R) * tma_align128(tma_ubytes(R, NY)) +
-         (acoustic ? kTmaDX * 3 * tma_xbytes(NY) : 0);
+         (acoustic ? tma_dx(fwi) * tma_xn(fwi) * tma_xbytes(NY) : 0);
 }
 // Consumer loop unrolling: up to radius 4 by the whole window (2R+1 phases,
 // queue slots taken mod 2R+1, no register moves); above, by 4 phases with a
@@ -181,6 +185,11 @@ struct TmaArgs {
   float *out;        // u^{n+1} (padded layout; the buffer that held u^{n-1})
   int *err;          // err[0] = code, err[1] = block
   SparseArgs sp;
+  // FWI epilogue (instances with FWI = true; padded layout, interior points):
+  float *d2;           // if set: u^{n+1} - 2u^n + u^{n-1} of this step
+  float *img;          // if set: img += img_scale * u^{n+1} * img_d2 (imaging condition)
+  const float *img_d2;
+  float img_scale;
 };
 
 // One shot of a batch (device memory, one per member).  At batch tick t the
@@ -278,12 +287,14 @@ __device__ __noinline__ SourceHits source_hits_call(const int4 *entries, const f
 // six neighbours minus 6u (still exact for constants); otherwise one difference
 // per axis.  MULTI: the launch steps every shot of a batch (BatchArgs), taking
 // work items dynamically; one shot takes static contiguous ranges.
-template <int R, int NY, int EQ, bool ISO, bool MULTI>
+template <int R, int NY, int EQ, bool ISO, bool MULTI, bool FWI = false>
 __global__ void __launch_bounds__(kTmaThreads, tma_minb(R, NY))
 k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
                 const __grid_constant__ CUtensorMap map_p,   // u^{n-1}, tile box
                 const __grid_constant__ CUtensorMap map_a,   // A, tile box
                 const __grid_constant__ CUtensorMap map_c,   // C, tile box
+                const __grid_constant__ CUtensorMap map_e,   // FWI: img_d2, tile box
+                const __grid_constant__ CUtensorMap map_g,   // FWI: img, tile box
                 const TmaArgs args, const BatchArgs bat) {
   constexpr int TY = tma_ty(NY);
   constexpr int HXB = tma_hxb(R), BW = tma_bw(R), DU = tma_du(R);
@@ -293,13 +304,15 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
   constexpr int U = tma_unroll(R);                         // phases per unrolled group
   constexpr int QL = U == Q ? Q : Q + U - 1;               // queue registers per row
   constexpr bool kSplit = R > 4;                           // two accumulation chains
+  constexpr int DX = tma_dx(FWI), XN = tma_xn(FWI);        // ring X slots, tiles per slot
+  const bool img = FWI && args.img != nullptr;             // imaging inputs in ring X
   constexpr bool AC = EQ == kAcoustic;
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t *full_u = reinterpret_cast<uint64_t *>(smem);
   uint64_t *empty_u = full_u + DU;
   uint64_t *full_x = empty_u + DU;
-  uint64_t *empty_x = full_x + kTmaDX;
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(empty_x + kTmaDX);
+  uint64_t *empty_x = full_x + DX;
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(empty_x + DX);
   volatile int4 *item_ring = reinterpret_cast<volatile int4 *>(smem + 512);  // batches: 4 items
   float *ring_u = reinterpret_cast<float *>(smem + 1024);
   float *ring_x = ring_u + DU * USLOT;
@@ -311,7 +324,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
       mbar_init(&full_u[i], 1);
       mbar_init(&empty_u[i], kTmaNW);
     }
-    for (int i = 0; i < kTmaDX; ++i) {
+    for (int i = 0; i < DX; ++i) {
       mbar_init(&full_x[i], 1);
       mbar_init(&empty_x[i], kTmaNW);
     }
@@ -391,16 +404,20 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
           if (*abort_flag) { ok = false; break; }
           const int zc = p - R;
           if (AC && zc >= za) {
-            const uint32_t slot = sx % kTmaDX;
-            if (sx >= (uint32_t)kTmaDX && !mbar_wait(&empty_x[slot], ((sx / kTmaDX) - 1) & 1)) {
+            const uint32_t slot = sx % DX;
+            if (sx >= (uint32_t)DX && !mbar_wait(&empty_x[slot], ((sx / DX) - 1) & 1)) {
               ok = false;
               break;
             }
-            float *dst = ring_x + slot * 3 * XT;
-            mbar_expect_tx(&full_x[slot], 3 * XT * 4);
+            float *dst = ring_x + slot * XN * XT;
+            mbar_expect_tx(&full_x[slot], (img ? 5 : 3) * XT * 4);
             tma_load_3d(dst, mp, x0 + kHaloX, y0 + R, zc + R, &full_x[slot]);
             tma_load_3d(dst + XT, ma, x0 + kHaloX, y0 + R, zc + R, &full_x[slot]);
             tma_load_3d(dst + 2 * XT, mc, x0 + kHaloX, y0 + R, zc + R, &full_x[slot]);
+            if (img) {
+              tma_load_3d(dst + 3 * XT, &map_e, x0 + kHaloX, y0 + R, zc + R, &full_x[slot]);
+              tma_load_3d(dst + 4 * XT, &map_g, x0 + kHaloX, y0 + R, zc + R, &full_x[slot]);
+            }
             ++sx;
           }
           const uint32_t slot = su % DU;
@@ -421,9 +438,9 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
         const uint32_t last = su - 1 - ((su - 1 - i) % DU);  // last fill of slot i
         drained &= mbar_wait(&full_u[last % DU], (last / DU) & 1);
       }
-      for (uint32_t i = 0; i < (uint32_t)kTmaDX && i < sx; ++i) {
-        const uint32_t last = sx - 1 - ((sx - 1 - i) % kTmaDX);
-        drained &= mbar_wait(&full_x[last % kTmaDX], (last / kTmaDX) & 1);
+      for (uint32_t i = 0; i < (uint32_t)DX && i < sx; ++i) {
+        const uint32_t last = sx - 1 - ((sx - 1 - i) % DX);
+        drained &= mbar_wait(&full_x[last % DX], (last / DX) & 1);
       }
       if (!drained && atomicCAS(err, 0, 3) == 0) err[1] = blockIdx.x;
     }
@@ -540,9 +557,9 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
             const float *xs = nullptr;
             uint32_t xslot = 0;
             if (AC) {
-              xslot = sx % kTmaDX;
-              if (!mbar_wait(&full_x[xslot], (sx / kTmaDX) & 1)) goto timeout;
-              xs = ring_x + xslot * 3 * XT + row0 * kTmaTX + lane;
+              xslot = sx % DX;
+              if (!mbar_wait(&full_x[xslot], (sx / DX) & 1)) goto timeout;
+              xs = ring_x + xslot * XN * XT + row0 * kTmaTX + lane;
             }
             float ycol[NY + 2 * R];  // this thread's column, rows row0-R .. row0+NY-1+R
 #pragma unroll
@@ -614,7 +631,21 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
 #pragma unroll
             for (int j = 0; j < NY; ++j) {
               if (AC) {
-                if (rows_ok & (1u << j)) optr[j * g.px] = val[j];
+                if (rows_ok & (1u << j)) {
+                  optr[j * g.px] = val[j];
+                  if constexpr (FWI) {
+                    // second time difference for the imaging condition, in the
+                    // order the standalone imaging kernel uses
+                    const int64_t off = (optr - out) + (int64_t)j * g.px;
+                    if (args.d2) {
+                      const float uc = qz[j][tma_qslot<U, Q>(ph, R)], up = xs[j * kTmaTX];
+                      args.d2[off] = (val[j] - uc) - (uc - up);
+                    }
+                    if (img)  // img_d2 and the old img from ring X
+                      args.img[off] = fmaf(args.img_scale * val[j], xs[3 * XT + j * kTmaTX],
+                                           xs[4 * XT + j * kTmaTX]);
+                  }
+                }
               } else {
                 if ((rows_ok & (1u << j)) && zc > 0 && zc < n0 - 1) optr[j * g.px] = val[j];
               }
@@ -653,7 +684,8 @@ timeout:
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-using TmaKernelFn = void (*)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, TmaArgs, BatchArgs);
+using TmaKernelFn = void (*)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap,
+                             CUtensorMap, TmaArgs, BatchArgs);
 
 struct TmaPlan {
   const char *name = "none";
@@ -664,11 +696,14 @@ struct TmaPlan {
   float *level[2] = {nullptr, nullptr};
   TmaKernelFn fn = nullptr;        // one shot, tile height 8·ny
   TmaKernelFn fn_multi = nullptr;  // batches (default tile height only)
+  TmaKernelFn fn_fwi = nullptr;    // one shot with the FWI epilogue (acoustic, this tile)
   int grid = 0, smem = 0;
   int grid_multi = 0, smem_multi = 0;
   int ny = 0;          // rows per consumer thread
   int per_sm = 0;      // resident CTAs per SM the persistent grid is sized for
   int per_sm_max = 0;  // occupancy limit of fn
+  int per_sm_fwi = 0;  // occupancy limit of fn_fwi
+  int smem_fwi = 0;
   int sms = 0;
 };
 
@@ -697,15 +732,15 @@ inline bool encode_map(EncodeFn enc, CUtensorMap *m, float *base, const Geom &g,
              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int R, int NY, int EQ, bool ISO, bool MULTI>
+template <int R, int NY, int EQ, bool ISO, bool MULTI, bool FWI = false>
 inline cudaError_t tma_instance(TmaKernelFn &fn, int &smem, int &per_sm) {
-  fn = k_stencil3d_tma<R, NY, EQ, ISO, MULTI>;
-  smem = tma_smem_bytes(R, NY, EQ == kAcoustic);
-  cudaError_t e = cudaFuncSetAttribute(k_stencil3d_tma<R, NY, EQ, ISO, MULTI>,
+  fn = k_stencil3d_tma<R, NY, EQ, ISO, MULTI, FWI>;
+  smem = tma_smem_bytes(R, NY, EQ == kAcoustic, FWI);
+  cudaError_t e = cudaFuncSetAttribute(k_stencil3d_tma<R, NY, EQ, ISO, MULTI, FWI>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil3d_tma<R, NY, EQ, ISO, MULTI>,
-                                                    kTmaThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, k_stencil3d_tma<R, NY, EQ, ISO, MULTI, FWI>, kTmaThreads, smem);
   if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
   return e;
 }
@@ -718,11 +753,18 @@ inline cudaError_t tma_configure(TmaPlan &pl, int ny) {
                           : tma_instance<R, 4, EQ, ISO, false>(pl.fn, pl.smem, pl.per_sm_max);
   if (e != cudaSuccess) return e;
   pl.fn_multi = nullptr;
+  pl.fn_fwi = nullptr;
   pl.smem_multi = 0;
   int per_sm_multi = 0;
   if constexpr (EQ == kAcoustic) {
     e = tma_instance<R, NYD, EQ, ISO, true>(pl.fn_multi, pl.smem_multi, per_sm_multi);
     if (e != cudaSuccess) return e;
+    // the FWI epilogue exists for the default tile; its occupancy must match the
+    // plan's grid, so other tiles go without it
+    if (ny == NYD) {
+      e = tma_instance<R, NYD, EQ, ISO, false, true>(pl.fn_fwi, pl.smem_fwi, pl.per_sm_fwi);
+      if (e != cudaSuccess) return e;
+    }
   }
   int dev = 0;
   cudaGetDevice(&dev);
@@ -803,6 +845,7 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float 
   pl.ny = ny;
   pl.per_sm = per_sm ? per_sm : pl.per_sm_max;
   pl.grid = pl.sms * pl.per_sm;
+  if (pl.fn_fwi && pl.per_sm_fwi < pl.per_sm) pl.fn_fwi = nullptr;  // would not all be resident
   pl.args.g = g;
   pl.args.tiles_x = (g.n2 + kTmaTX - 1) / kTmaTX;
   const int tiles_y = (g.n1 + ty - 1) / ty;
@@ -826,7 +869,33 @@ inline cudaError_t launch_tma_step(const TmaPlan &pl, int cur, float *out, const
   a.err = err;
   a.sp = sp;
   pl.fn<<<pl.grid, kTmaThreads, pl.smem, s>>>(pl.map_u[cur], pl.map_t[cur ^ 1], pl.map_a,
-                                              pl.map_c, a, BatchArgs{});
+                                              pl.map_c, pl.map_c, pl.map_c, a, BatchArgs{});
+  return cudaGetLastError();
+}
+
+// The same step with the FWI epilogue (plan.fn_fwi must be set).
+inline cudaError_t launch_tma_step_fwi(const TmaPlan &pl, int cur, float *out, const Coef &c,
+                                       int *err, const SparseArgs &sp, float *d2, float *img,
+                                       const float *img_d2, float img_scale, cudaStream_t s) {
+  TmaArgs a = pl.args;
+  a.c = c;
+  a.out = out;
+  a.err = err;
+  a.sp = sp;
+  a.d2 = d2;
+  a.img = img;
+  a.img_d2 = img_d2;
+  a.img_scale = img_scale;
+  CUtensorMap me = pl.map_c, mg = pl.map_c;
+  if (img) {
+    EncodeFn enc = tma_encoder();
+    if (!enc || !encode_map(enc, &me, const_cast<float *>(img_d2), pl.args.g, kTmaTX,
+                            tma_ty(pl.ny)) ||
+        !encode_map(enc, &mg, img, pl.args.g, kTmaTX, tma_ty(pl.ny)))
+      return cudaErrorInvalidValue;
+  }
+  pl.fn_fwi<<<pl.grid, kTmaThreads, pl.smem_fwi, s>>>(pl.map_u[cur], pl.map_t[cur ^ 1], pl.map_a,
+                                                      pl.map_c, me, mg, a, BatchArgs{});
   return cudaGetLastError();
 }
 

@@ -129,7 +129,8 @@ def forward_traces(p, m=None):
     return rec
 
 
-def gradient(p, d_obs, m=None, k=None, memory_budget=None, stats=None, profile=False):
+def gradient(p, d_obs, m=None, k=None, memory_budget=None, stats=None, profile=False,
+             fused=None):
     """(J, dJ/dm) for shot p (fdsynth.acoustic_problem layout) against d_obs.
 
     m: model (defaults to p["m"]); k: checkpoint interval (None: chosen from
@@ -138,7 +139,10 @@ def gradient(p, d_obs, m=None, k=None, memory_budget=None, stats=None, profile=F
     receives k, the device bytes held for checkpoints and the recompute block,
     and the kernel launches of the forward and adjoint contexts; with
     ``profile`` also their stencil launches and summed stencil milliseconds
-    (CUDA events per launch; steps are then launched one by one).
+    (CUDA events per launch; steps are then launched one by one).  ``fused``
+    (default: wherever the pipelined 3-D kernel runs) takes the backward sweep
+    through fd_step_fwi, the second time difference and the imaging condition
+    computed in the stencil epilogues; the result is bitwise the same.
     """
     torch = _dev()
     _check_sparse_undamped(p)
@@ -146,12 +150,12 @@ def gradient(p, d_obs, m=None, k=None, memory_budget=None, stats=None, profile=F
     work = torch.cuda.Stream()            # both contexts and every copy on one stream
     work.wait_stream(caller)
     with torch.cuda.stream(work):
-        J, g = _gradient_on_stream(p, d_obs, m, k, memory_budget, stats, profile)
+        J, g = _gradient_on_stream(p, d_obs, m, k, memory_budget, stats, profile, fused)
     caller.wait_stream(work)
     return J, g
 
 
-def _gradient_on_stream(p, d_obs, m, k, memory_budget, stats=None, profile=False):
+def _gradient_on_stream(p, d_obs, m, k, memory_budget, stats=None, profile=False, fused=None):
     torch = _dev()
     nt, dt = p["nt"], p["dt"]
     mm = torch.as_tensor(p["m"] if m is None else m, dtype=torch.float32, device="cuda")
@@ -187,26 +191,30 @@ def _gradient_on_stream(p, d_obs, m, k, memory_budget, stats=None, profile=False
         adj.set_model(mm, damp)
         adj.set_sources(rc, torch.flip(r[1:], dims=(0,)).contiguous())
         B.fd_set_receivers(fwd.ctx, 0, None)
-        g = torch.zeros(p["shape"], dtype=torch.float32, device="cuda")
-        blk = torch.empty((k + 2, elems), dtype=torch.float32, device="cuda")
         scale = -1.0 / (dt * dt)
-        for c in range(nblk - 1, -1, -1):
-            n0, n1 = c * k, min((c + 1) * k, nt)
-            # recompute u^{n0-1} .. u^{n1} into blk[0 .. n1-n0+1]
-            B.fd_restore(fwd.ctx, ck[c, 0], ck[c, 1])
-            fwd.set_step(n0)
-            blk[0].copy_(ck[c, 1])
-            blk[1].copy_(ck[c, 0])
-            for t in range(n0, n1):
-                fwd.run(1)
-                B.fd_snapshot(fwd.ctx, blk[t - n0 + 2])
-            for n in range(n1 - 1, n0 - 1, -1):       # adjoint step nt-1-n gives ν^{n+1}
-                adj.run(1)
-                i = n - n0 + 1                          # blk[i] = u^n
-                B.fd_imaging(adj.ctx, g, blk[i + 1], blk[i], blk[i - 1], scale)
+        if fused is None:
+            fused = len(p["shape"]) == 3 and fwd.kernel_name == "stencil3d_tma_acoustic"
+        if fused:
+            # the recompute writes u^{n+1} − 2u^n + u^{n−1} from its own epilogue and
+            # the adjoint step accumulates the imaging condition from its epilogue
+            g = torch.empty(p["shape"], dtype=torch.float32, device="cuda")
+            gp = torch.zeros(elems, dtype=torch.float32, device="cuda")
+            blk = torch.empty((k, elems), dtype=torch.float32, device="cuda")
+            for c in range(nblk - 1, -1, -1):
+                n0, n1 = c * k, min((c + 1) * k, nt)
+                B.fd_restore(fwd.ctx, ck[c, 0], ck[c, 1])
+                fwd.set_step(n0)
+                for t in range(n0, n1):
+                    B.fd_step_fwi(fwd.ctx, d2_out=blk[t - n0])
+                for n in range(n1 - 1, n0 - 1, -1):   # adjoint step nt-1-n gives ν^{n+1}
+                    B.fd_step_fwi(adj.ctx, img_g=gp, img_d2=blk[n - n0], scale=scale)
+            B.fd_field_to_dense(fwd.ctx, gp, g)
+            blk_bytes = int(blk.numel() + gp.numel()) * 4
+        else:
+            g, blk_bytes = _backward_unfused(p, fwd, adj, ck, k, nblk, elems, scale)
         if stats is not None:
-            stats.update(k=k, checkpoint_bytes=int(ck.numel()) * 4,
-                         block_bytes=int(blk.numel()) * 4,
+            stats.update(k=k, checkpoint_bytes=int(ck.numel()) * 4, block_bytes=blk_bytes,
+                         fused=bool(fused),
                          launches_forward=fwd.kernel_launches, launches_adjoint=adj.kernel_launches)
             if profile:
                 nf, msf = fwd.profile()
@@ -217,6 +225,29 @@ def _gradient_on_stream(p, d_obs, m, k, memory_budget, stats=None, profile=False
     finally:
         fwd.close()
         adj.close()
+
+
+def _backward_unfused(p, fwd, adj, ck, k, nblk, elems, scale):
+    """Backward sweep with separate kernels: recompute + snapshot, adjoint step, imaging."""
+    torch = _dev()
+    nt = p["nt"]
+    g = torch.zeros(p["shape"], dtype=torch.float32, device="cuda")
+    blk = torch.empty((k + 2, elems), dtype=torch.float32, device="cuda")
+    for c in range(nblk - 1, -1, -1):
+        n0, n1 = c * k, min((c + 1) * k, nt)
+        # recompute u^{n0-1} .. u^{n1} into blk[0 .. n1-n0+1]
+        B.fd_restore(fwd.ctx, ck[c, 0], ck[c, 1])
+        fwd.set_step(n0)
+        blk[0].copy_(ck[c, 1])
+        blk[1].copy_(ck[c, 0])
+        for t in range(n0, n1):
+            fwd.run(1)
+            B.fd_snapshot(fwd.ctx, blk[t - n0 + 2])
+        for n in range(n1 - 1, n0 - 1, -1):       # adjoint step nt-1-n gives ν^{n+1}
+            adj.run(1)
+            i = n - n0 + 1                          # blk[i] = u^n
+            B.fd_imaging(adj.ctx, g, blk[i + 1], blk[i], blk[i - 1], scale)
+    return g, int(blk.numel()) * 4
 
 
 class FWIObjective:

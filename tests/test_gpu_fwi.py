@@ -141,4 +141,47 @@ def test_checkpoint_interval_tuner_times_candidates_and_keeps_the_gradient():
     st = {}
     fwi.gradient(p, d_obs, k=k, stats=st)
     assert st["k"] == k and st["launches_forward"] > 0 and st["launches_adjoint"] > 0
-    assert st["checkpoint_bytes"] + st["block_bytes"] == fwi.checkpoint_memory(48, k, st["block_bytes"] // (k + 2))
+    import math
+    fb = st["checkpoint_bytes"] // (2 * math.ceil(48 / k))       # bytes of one padded level
+    levels = k + 1 if st["fused"] else k + 2                      # d2 levels + padded gradient
+    assert st["block_bytes"] == levels * fb
+    assert st["checkpoint_bytes"] + st["block_bytes"] <= fwi.checkpoint_memory(48, k, fb)
+
+
+def test_fused_backward_sweep_is_bitwise_the_separate_kernels():
+    """fd_step_fwi computes the second time difference in the recompute's epilogue and
+    the imaging condition in the adjoint's: the same arithmetic as fd_snapshot +
+    fd_imaging, so the same gradient bit for bit, for several k."""
+    import torch
+    from paper_1906_10811_b300 import fwi
+    p = _shot(shape=(29, 33, 40), nt=70)
+    d_obs = fwi.forward_traces(p, _true_model(p)).cpu().numpy()
+    for k in (9, 70):
+        st = {}
+        Ja, ga = fwi.gradient(p, d_obs, k=k, fused=False)
+        Jb, gb = fwi.gradient(p, d_obs, k=k, fused=True, stats=st)
+        assert st["fused"]
+        assert Ja == Jb
+        assert torch.equal(ga, gb)
+
+
+def test_fused_step_is_refused_where_it_does_not_apply():
+    from paper_1906_10811_b300 import Solver
+    from paper_1906_10811_b300 import binding as B
+    import torch
+    p = _shot(shape=(40, 44), nt=10)
+    with Solver(p["shape"], p["spacing"], 8, p["dt"], "acoustic", device=True) as s:
+        s.set_model(torch.as_tensor(p["m"], device="cuda"))
+        buf = torch.empty(B.fd_field_elems(s.ctx), device="cuda")
+        with pytest.raises(B.FdError) as e:
+            B.fd_step_fwi(s.ctx, d2_out=buf)
+        assert e.value.status == B.FD_EUNSUPPORTED
+    q = _shot(shape=(20, 22, 24), nt=10)
+    with Solver(q["shape"], q["spacing"], 8, q["dt"], "acoustic", device=True) as s:
+        s.set_model(torch.as_tensor(q["m"], device="cuda"))
+        buf = torch.empty(B.fd_field_elems(s.ctx), device="cuda")
+        with pytest.raises(B.FdError) as e:
+            B.fd_step_fwi(s.ctx, img_g=buf)
+        assert e.value.status == B.FD_EINVAL
+        B.fd_step_fwi(s.ctx, d2_out=buf)
+        assert s.steps == 1
