@@ -130,13 +130,26 @@ __global__ void k_selftest_wait(long long budget, int *out) {
     out[1] = (int)(waited >> 10);  // kilo-cycles
   }
 }
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
-                                            uint64_t *bar) {
+// TMA load of one box into shared memory, completing on an mbarrier, with an L2
+// eviction-priority policy (createpolicy): the halo'd u^n planes are re-read
+// by the neighbouring tiles, the u^{n-1}/A/C tiles are not.
+__device__ __forceinline__ void tma_load_3d_hint(void *dst, const CUtensorMap *map, int x, int y,
+                                                 int z, uint64_t *bar, uint64_t policy) {
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      ".L2::cache_hint [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)), "l"(policy)
       : "memory");
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
 }
 __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap *map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
@@ -354,6 +367,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
         }
       }
       uint32_t su = 0, sx = 0;  // fills issued to rings U and X
+      const uint64_t keep = l2_policy_evict_last(), once = l2_policy_evict_first();
       bool ok = true;
       int64_t q = q0;
       unsigned nitem = 0;        // batches: items taken by this block
@@ -411,12 +425,14 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
             }
             float *dst = ring_x + slot * XN * XT;
             mbar_expect_tx(&full_x[slot], (img ? 5 : 3) * XT * 4);
-            tma_load_3d(dst, mp, x0 + kHaloX, y0 + R, zc + R, &full_x[slot]);
-            tma_load_3d(dst + XT, ma, x0 + kHaloX, y0 + R, zc + R, &full_x[slot]);
-            tma_load_3d(dst + 2 * XT, mc, x0 + kHaloX, y0 + R, zc + R, &full_x[slot]);
+            tma_load_3d_hint(dst, mp, x0 + kHaloX, y0 + R, zc + R, &full_x[slot], once);
+            tma_load_3d_hint(dst + XT, ma, x0 + kHaloX, y0 + R, zc + R, &full_x[slot], once);
+            tma_load_3d_hint(dst + 2 * XT, mc, x0 + kHaloX, y0 + R, zc + R, &full_x[slot], once);
             if (img) {
-              tma_load_3d(dst + 3 * XT, &map_e, x0 + kHaloX, y0 + R, zc + R, &full_x[slot]);
-              tma_load_3d(dst + 4 * XT, &map_g, x0 + kHaloX, y0 + R, zc + R, &full_x[slot]);
+              tma_load_3d_hint(dst + 3 * XT, &map_e, x0 + kHaloX, y0 + R, zc + R, &full_x[slot],
+                               once);
+              tma_load_3d_hint(dst + 4 * XT, &map_g, x0 + kHaloX, y0 + R, zc + R, &full_x[slot],
+                               once);
             }
             ++sx;
           }
@@ -426,7 +442,8 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
             break;
           }
           mbar_expect_tx(&full_u[slot], tma_ubytes(R, NY));
-          tma_load_3d(ring_u + slot * USLOT, mu, x0 + kHaloX - HXB, y0, p + R, &full_u[slot]);
+          tma_load_3d_hint(ring_u + slot * USLOT, mu, x0 + kHaloX - HXB, y0, p + R, &full_u[slot],
+                           keep);
           ++su;
         }
       }
@@ -632,7 +649,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
             for (int j = 0; j < NY; ++j) {
               if (AC) {
                 if (rows_ok & (1u << j)) {
-                  optr[j * g.px] = val[j];
+                  __stcs(optr + j * g.px, val[j]);  // streaming: not re-read by this launch
                   if constexpr (FWI) {
                     // second time difference for the imaging condition, in the
                     // order the standalone imaging kernel uses
@@ -647,7 +664,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
                   }
                 }
               } else {
-                if ((rows_ok & (1u << j)) && zc > 0 && zc < n0 - 1) optr[j * g.px] = val[j];
+                if ((rows_ok & (1u << j)) && zc > 0 && zc < n0 - 1) __stcs(optr + j * g.px, val[j]);
               }
             }
             optr += g.plane;
