@@ -54,13 +54,10 @@ WORKLOADS = {
 
 # DRAM bytes per stencil launch from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum, mean of the captured launches), keyed by (kernel name,
-# workload, space order, tile height, z-block height, CTAs per SM); the captures
+# workload, space order, tile height, z-block height, CTAs per SM, aligned); the captures
 # are summarised in profiles/.  Absent (null) when not captured for the kernel
 # and tile configuration as they are now.
-NCU_TRAFFIC = {
-    # profiles/stencil3d_tma_acoustic256_so8.md: 3 launches, read 321.17 MB + write 46.42 MB
-    ("stencil3d_tma_acoustic", "acoustic256", 8, 32, 56, 2): 367.59e6,
-}
+NCU_TRAFFIC = {}
 
 
 def parse():
@@ -83,8 +80,9 @@ def parse():
     ap.add_argument("--kernel", default="auto", choices=["auto", "plain", "tma"])
     ap.add_argument("--tile", default="auto",
                     help="auto: the autotuner picks the pipelined kernel's tile configuration "
-                         "before the timed region; default: the built-in one; TY,ZB,CPS: tile "
-                         "height, z-block height and CTAs per SM given explicitly")
+                         "before the timed region; default: the built-in one; TY,ZB,CPS[,AL]: "
+                         "tile height, z-block height, CTAs per SM and whole-segment split "
+                         "given explicitly")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -476,8 +474,8 @@ def run_diffusion(args):
         if args.tile == "auto":
             tune_tried = len(s.autotune(reps=5)[1])
         elif args.tile != "default":
-            ty, zb, cps = (int(v) for v in args.tile.split(","))
-            s.set_tile_config(tile_y=ty, zblock=zb, ctas_per_sm=cps)
+            ty, zb, cps, al = ([int(v) for v in args.tile.split(",")] + [0])[:4]
+            s.set_tile_config(tile_y=ty, zblock=zb, ctas_per_sm=cps, aligned=al)
         tile = s.tile_config
 
     def sweep():
@@ -523,7 +521,7 @@ def run_diffusion(args):
                     kernel=args.kernel, boundary=args.boundary)
         if tile is not None:
             se.set_tile_config(tile_y=tile["tile_y"], zblock=tile["zblock"],
-                               ctas_per_sm=tile["ctas_per_sm"])
+                               ctas_per_sm=tile["ctas_per_sm"], aligned=tile["aligned"])
         from paper_1906_10811_b300 import binding as B
 
         def sweep_e2e():
@@ -620,8 +618,8 @@ def run_ours(args):
             _, tried = s.autotune(reps=5)
             tune_tried = len(tried)
         elif args.tile != "default":
-            ty, zb, cps = (int(v) for v in args.tile.split(","))
-            s.set_tile_config(tile_y=ty, zblock=zb, ctas_per_sm=cps)
+            ty, zb, cps, al = ([int(v) for v in args.tile.split(",")] + [0])[:4]
+            s.set_tile_config(tile_y=ty, zblock=zb, ctas_per_sm=cps, aligned=al)
         tile = s.tile_config
 
     def shot():
@@ -657,7 +655,8 @@ def run_ours(args):
     peak, peak_kind = load_peak()
     avg_launch_s = st_ms / max(n_st, 1) / 1e3
     achieved = BYTES_PER_POINT["acoustic"] * npts / avg_launch_s / 1e9
-    tkey = (tile["tile_y"], tile["zblock"], tile["ctas_per_sm"]) if tile else (0, 0, 0)
+    tkey = ((tile["tile_y"], tile["zblock"], tile["ctas_per_sm"], tile["aligned"]) if tile
+            else (0, 0, 0, 0))
     traffic = NCU_TRAFFIC.get((kernel_name, args.workload, w["so"]) + tkey)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
@@ -680,7 +679,7 @@ def run_ours(args):
                     kernel=args.kernel, autotune=tile is not None and args.tile == "auto")
         if tile is not None and args.tile not in ("auto", "default"):
             se.set_tile_config(tile_y=tile["tile_y"], zblock=tile["zblock"],
-                               ctas_per_sm=tile["ctas_per_sm"])
+                               ctas_per_sm=tile["ctas_per_sm"], aligned=tile["aligned"])
         from paper_1906_10811_b300 import binding as B
 
         def shot_e2e():

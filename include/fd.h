@@ -232,17 +232,25 @@ fd_status fd_field_to_dense(fd_ctx *ctx, const float *padded, float *dense);
  *                tile before it moves to the next (the work is cut into
  *                z-blocks of this height; each cut costs 2R re-read planes)
  *   ctas_per_sm  resident CTAs per SM the persistent grid is sized for
+ *   aligned      work split: 0 = every CTA gets an equal run of tile-planes in
+ *                z-block-major order (a run may start or end inside a
+ *                segment); 1 = CTAs get whole (z-block, tile) segments, at
+ *                most one CTA per segment, so that the CTAs holding
+ *                neighbouring tiles start their segments together
  *   us_per_step  stencil launch time measured by fd_autotune (µs; 0 when
  *                the configuration was set, not measured)
  *
  * fd_get_tile_config: the configuration fd_run uses; FD_EUNSUPPORTED when the
  *   context runs the plain kernel.
  * fd_set_tile_config: use cfg (tile_x 32 or 0, tile_y 16 or 32 or 0 for the
- *   default, zblock ≥ 0 with 0 meaning one CTA's share, ctas_per_sm ≥ 0 with
- *   0 meaning as many as fit); FD_EINVAL for anything else, leaving the
- *   current configuration in place.  Captured graphs are dropped.
+ *   default, zblock ≥ 0 with 0 meaning one CTA's share (aligned = 0) or the
+ *   height that makes about as many segments as CTAs (aligned = 1),
+ *   ctas_per_sm ≥ 0 with 0 meaning as many as fit, aligned 0 or 1);
+ *   FD_EINVAL for anything else, leaving the current configuration in
+ *   place.  Captured graphs are dropped.
  * fd_autotune: time every configuration of the search space (tile_y in
- *   {16, 32} × ctas_per_sm in 1..fit × zblock in {share/2, share, 2·share},
+ *   {16, 32} × ctas_per_sm in 1..fit × (aligned 0 with zblock in {share/2,
+ *   share, 2·share} | aligned 1 with m or 2m z-blocks, m = CTAs / tiles),
  *   reps ≥ 1 timed launches each after two warm-up launches, median taken),
  *   then use the fastest.  The candidate launches read the current fields
  *   and write a scratch field allocated for the call, so the solution is not
@@ -256,6 +264,7 @@ typedef struct {
   int tile_y;
   int zblock;
   int ctas_per_sm;
+  int aligned;
   double us_per_step;
 } fd_tile_config;
 

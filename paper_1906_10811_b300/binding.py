@@ -40,7 +40,8 @@ class fd_options(ctypes.Structure):
 
 class fd_tile_config(ctypes.Structure):
     _fields_ = [("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("zblock", ctypes.c_int),
-                ("ctas_per_sm", ctypes.c_int), ("us_per_step", ctypes.c_double)]
+                ("ctas_per_sm", ctypes.c_int), ("aligned", ctypes.c_int),
+                ("us_per_step", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -253,8 +254,9 @@ def fd_get_tile_config(ctx):
     return cfg.as_dict()
 
 
-def fd_set_tile_config(ctx, tile_y=0, zblock=0, ctas_per_sm=0, tile_x=0):
-    cfg = fd_tile_config(int(tile_x), int(tile_y), int(zblock), int(ctas_per_sm), 0.0)
+def fd_set_tile_config(ctx, tile_y=0, zblock=0, ctas_per_sm=0, tile_x=0, aligned=0):
+    cfg = fd_tile_config(int(tile_x), int(tile_y), int(zblock), int(ctas_per_sm), int(aligned),
+                         0.0)
     _check(ctx, load().fd_set_tile_config(ctx, ctypes.byref(cfg)))
 
 

@@ -581,11 +581,11 @@ void select_kernel(fd_ctx *c) {
 // Rebuild the pipelined kernel's plan for another tile configuration; on
 // failure the current plan stays.  Source tables are keyed by tile and the
 // captured graphs hold the old plan, so both are redone.
-fd_status replan(fd_ctx *c, int ny, int per_sm, int zblock) {
+fd_status replan(fd_ctx *c, int ny, int per_sm, int zblock, int aligned) {
   TmaPlan p{};
   const char *why = nullptr;
   cudaError_t e = plan_tma(p, c->g, c->eq == FD_ACOUSTIC ? kAcoustic : kDiffusion, c->iso, c->u,
-                           c->A, c->C, ny, per_sm, zblock, &why);
+                           c->A, c->C, ny, per_sm, zblock, aligned, &why);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(c, e == cudaErrorInvalidValue ? FD_EINVAL : FD_EUNSUPPORTED,
@@ -604,8 +604,12 @@ void tile_of(const fd_ctx *c, fd_tile_config *cfg) {
   cfg->tile_y = tma_ty(c->tma.ny);
   cfg->zblock = c->tma.args.zblock;
   cfg->ctas_per_sm = c->tma.per_sm;
+  cfg->aligned = c->tma.args.aligned;
   cfg->us_per_step = c->tune_us;
 }
+
+// Work split of the pipelined kernel a new context starts with (fd_tile_config.aligned).
+constexpr int kDefaultAligned = 0;
 
 // Autotuner choices for the process, per device, grid, order and equation.
 struct TuneKey {
@@ -811,7 +815,7 @@ fd_status fd_create(fd_ctx **out, int ndim, const int64_t *shape, const double *
     const char *why = nullptr;
     c->iso = spacing[0] == spacing[1] && spacing[1] == spacing[2];
     e = plan_tma(c->tma, c->g, eq == FD_ACOUSTIC ? kAcoustic : kDiffusion, c->iso, c->u, c->A,
-                 c->C, 0, 0, 0, &why);
+                 c->C, 0, 0, 0, kDefaultAligned, &why);
     if (e == cudaSuccess) {
       c->use_tma = true;
       c->kernel_name = c->tma.name;
@@ -1147,10 +1151,11 @@ fd_status fd_set_tile_config(fd_ctx *c, const fd_tile_config *cfg) {
   if (!c->use_tma) return fail(c, FD_EUNSUPPORTED, "the plain kernel has no tile configuration");
   if ((cfg->tile_x != 0 && cfg->tile_x != kTmaTX) || cfg->tile_y % kTmaNW ||
       (cfg->tile_y != 0 && !tma_ny_supported(cfg->tile_y / kTmaNW)) || cfg->zblock < 0 ||
-      cfg->ctas_per_sm < 0)
-    return fail(c, FD_EINVAL, "tile configuration %dx%d, zblock %d, %d CTAs/SM is not offered",
-                cfg->tile_x, cfg->tile_y, cfg->zblock, cfg->ctas_per_sm);
-  return replan(c, cfg->tile_y / kTmaNW, cfg->ctas_per_sm, cfg->zblock);
+      cfg->ctas_per_sm < 0 || (cfg->aligned != 0 && cfg->aligned != 1))
+    return fail(c, FD_EINVAL,
+                "tile configuration %dx%d, zblock %d, %d CTAs/SM, aligned %d is not offered",
+                cfg->tile_x, cfg->tile_y, cfg->zblock, cfg->ctas_per_sm, cfg->aligned);
+  return replan(c, cfg->tile_y / kTmaNW, cfg->ctas_per_sm, cfg->zblock, cfg->aligned);
 }
 
 fd_status fd_autotune(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_config *tried,
@@ -1266,7 +1271,7 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end() && !tried) {
       const fd_tile_config cfg = it->second;
-      fd_status st = replan(c, cfg.tile_y / kTmaNW, cfg.ctas_per_sm, cfg.zblock);
+      fd_status st = replan(c, cfg.tile_y / kTmaNW, cfg.ctas_per_sm, cfg.zblock, cfg.aligned);
       if (st) return st;
       c->tune_us = cfg.us_per_step;
       if (best) *best = cfg;
@@ -1282,43 +1287,62 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
   const int eq = c->eq == FD_ACOUSTIC ? kAcoustic : kDiffusion;
   const int R = c->so / 2;
   const int zmin = std::min<int>(c->g.n0, std::max(8, 2 * R));
-  fd_tile_config win{};
-  double win_us = 1e300;
-  int n = 0;
+  // candidates: tile height × CTAs per SM × (equal tile-plane ranges with z-blocks of
+  // share/2, share, 2·share | whole segments with z-blocks that make m or 2m
+  // segments per tile, m = CTAs / tiles)
+  struct Cand {
+    int ny, cps, zb, aligned;
+  };
+  std::vector<Cand> cands;
   for (int ny : {2, 4}) {
     TmaPlan p{};
     const char *why = nullptr;
-    if (st || plan_tma(p, c->g, eq, c->iso, c->u, c->A, c->C, ny, 0, 0, &why) != cudaSuccess) {
+    if (st || plan_tma(p, c->g, eq, c->iso, c->u, c->A, c->C, ny, 0, 0, 0, &why) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
-    for (int cps = 1; !st && cps <= p.per_sm_max; ++cps) {
+    for (int cps = 1; cps <= p.per_sm_max; ++cps) {
       TmaPlan q{};
-      if (plan_tma(q, c->g, eq, c->iso, c->u, c->A, c->C, ny, cps, 0, &why) != cudaSuccess) {
+      if (plan_tma(q, c->g, eq, c->iso, c->u, c->A, c->C, ny, cps, 0, 0, &why) != cudaSuccess) {
         cudaGetLastError();
         continue;
       }
       const int share = q.args.zblock;
-      int zbs[3] = {std::max(zmin, share / 2), share, std::min<int>(c->g.n0, 2 * share)};
-      for (int k = 0; !st && k < 3; ++k) {
-        if ((k == 0 && zbs[0] >= share) || (k == 2 && zbs[2] <= share)) continue;
-        TmaPlan r{};
-        if (plan_tma(r, c->g, eq, c->iso, c->u, c->A, c->C, ny, cps, zbs[k], &why) !=
-            cudaSuccess) {
-          cudaGetLastError();
-          continue;
-        }
-        double us = 0.0;
-        st = time_plan(c, r, scratch, reps, ev.data(), &us);
-        if (st) break;
-        fd_tile_config cfg{kTmaTX, tma_ty(ny), r.args.zblock, r.per_sm, us};
-        if (tried && n < max_tried) tried[n] = cfg;
-        ++n;
-        if (us < win_us) {
-          win_us = us;
-          win = cfg;
-        }
+      cands.push_back({ny, cps, share, 0});
+      if (share / 2 > zmin) cands.push_back({ny, cps, share / 2, 0});
+      if (2 * share <= c->g.n0) cands.push_back({ny, cps, 2 * share, 0});
+      // segments no shorter than zmin planes
+      const int mcap = std::max(1, c->g.n0 / zmin);
+      const int m1 = std::max(1, (q.sms * cps) / q.args.ntiles);
+      for (int m : {std::min(m1, mcap), std::min(2 * m1, mcap)}) {
+        const int zb = (c->g.n0 + m - 1) / m;
+        bool dup = false;
+        for (const Cand &d : cands) dup |= d.ny == ny && d.cps == cps && d.zb == zb && d.aligned;
+        if (!dup) cands.push_back({ny, cps, zb, 1});
       }
+    }
+  }
+  fd_tile_config win{};
+  double win_us = 1e300;
+  int n = 0;
+  for (const Cand &cd : cands) {
+    if (st) break;
+    TmaPlan r{};
+    const char *why = nullptr;
+    if (plan_tma(r, c->g, eq, c->iso, c->u, c->A, c->C, cd.ny, cd.cps, cd.zb, cd.aligned, &why) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    double us = 0.0;
+    st = time_plan(c, r, scratch, reps, ev.data(), &us);
+    if (st) break;
+    fd_tile_config cfg{kTmaTX, tma_ty(cd.ny), r.args.zblock, r.per_sm, cd.aligned, us};
+    if (tried && n < max_tried) tried[n] = cfg;
+    ++n;
+    if (us < win_us) {
+      win_us = us;
+      win = cfg;
     }
   }
   for (auto &e : ev)
@@ -1332,7 +1356,7 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
   if (err[0]) return fail(c, FD_ETIMEOUT, "autotune: pipelined kernel wait expired (code %d)", err[0]);
   if (n == 0) return fail(c, FD_EUNSUPPORTED, "autotune: no tile configuration could be planned");
   if (ntried) *ntried = n;
-  st = replan(c, win.tile_y / kTmaNW, win.ctas_per_sm, win.zblock);
+  st = replan(c, win.tile_y / kTmaNW, win.ctas_per_sm, win.zblock, win.aligned);
   if (st) return st;
   c->tune_us = win.us_per_step;
   if (best) *best = win;
@@ -1510,7 +1534,7 @@ fd_status fd_batch_run(fd_batch *b, int nticks) {
       return bfail(b, FD_EINVAL, "a member would pass its wavelet length");
     fd_status st = FD_OK;
     // the batched kernel runs the default tile: a tuned member goes back to it
-    if (c->ndim == 3 && c->tma.ny != tma_ny(R)) st = replan(c, 0, 0, 0);
+    if (c->ndim == 3 && c->tma.ny != tma_ny(R)) st = replan(c, 0, 0, 0, kDefaultAligned);
     if (!st && c->nrec > 0) st = ensure_rec_capacity(c, c->step + nticks + 1);
     if (!st) st = prepare_sources(c);
     if (!st && c->ndim == 3) st = prepare_fused(c);

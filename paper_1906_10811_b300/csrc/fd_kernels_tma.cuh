@@ -194,6 +194,7 @@ struct TmaArgs {
   int tiles_x;       // tiles along x
   int ntiles;        // tiles in a plane
   int zblock;        // planes per z-block of the work order
+  int aligned;       // 1: CTAs take whole (z-block, tile) segments; 0: equal tile-plane ranges
   int64_t W;         // tile-planes
   float *out;        // u^{n+1} (padded layout; the buffer that held u^{n-1})
   int *err;          // err[0] = code, err[1] = block
@@ -204,6 +205,22 @@ struct TmaArgs {
   const float *img_d2;
   float img_scale;
 };
+
+// The segment at work position q of a CTA's range [q, q1), advancing q.
+// Equal tile-plane ranges (aligned = 0): a range may start or end inside a
+// segment.  Whole segments (aligned = 1): q counts segments, z-block-major.
+__device__ __forceinline__ void next_segment(const TmaArgs &a, int64_t &q, int64_t q1, int &tile,
+                                             int &za, int &zb) {
+  if (a.aligned) {
+    tile = (int)(q % a.ntiles);
+    za = (int)(q / a.ntiles) * a.zblock;
+    zb = min(a.g.n0, za + a.zblock);
+    ++q;
+  } else {
+    segment_at(q, q1, a.ntiles, a.zblock, a.g.n0, tile, za, zb);
+    q += zb - za;
+  }
+}
 
 // One shot of a batch (device memory, one per member).  At batch tick t the
 // shot is at global step step0 + t with u^n in level[cur0 ^ (t & 1)].
@@ -348,7 +365,13 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
   __syncthreads();
 
   int64_t q0 = 0, q1 = 0;
-  if constexpr (!MULTI) cta_range(args.W, blockIdx.x, gridDim.x, q0, q1);
+  if constexpr (!MULTI) {
+    if (args.aligned)  // whole segments: q counts (z-block, tile) segments
+      cta_range((int64_t)args.ntiles * ((args.g.n0 + args.zblock - 1) / args.zblock), blockIdx.x,
+                gridDim.x, q0, q1);
+    else
+      cta_range(args.W, blockIdx.x, gridDim.x, q0, q1);
+  }
   const int64_t tick = MULTI ? *bat.tick : 0;
   if constexpr (MULTI) {
     if (blockIdx.x == 0 && threadIdx.x == 0) bat.ticket[(tick + 1) & 1] = 0u;  // next tick's
@@ -400,8 +423,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
           tiles_x = bat.shots[shot].tiles_x;
         } else {
           if (q >= q1) break;
-          segment_at(q, q1, args.ntiles, args.zblock, args.g.n0, tile, za, zb);
-          q += zb - za;
+          next_segment(args, q, q1, tile, za, zb);
           tiles_x = args.tiles_x;
         }
         const int x0 = (tile % tiles_x) * kTmaTX, y0 = (tile / tiles_x) * TY;
@@ -496,8 +518,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
       n0 = bat.shots[shot].g.n0;
     } else {
       if (q >= q1) break;
-      segment_at(q, q1, args.ntiles, args.zblock, args.g.n0, tile, za, zb);
-      q += zb - za;
+      next_segment(args, q, q1, tile, za, zb);
       tiles_x = args.tiles_x;
       n0 = args.g.n0;
     }
@@ -797,7 +818,8 @@ inline bool tma_ny_supported(int ny) { return ny == 2 || ny == 4; }
 // ny rows per consumer thread (0: the default), a grid of per_sm CTAs per SM
 // (0: as many as fit) and z-blocks of zblock planes (0: about one CTA's share).
 inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float *const *level,
-                            float *A, float *C, int ny, int per_sm, int zblock, const char **why) {
+                            float *A, float *C, int ny, int per_sm, int zblock, int aligned,
+                            const char **why) {
   *why = nullptr;
   if (g.R0 == 0 || g.R < 1 || g.R > kMaxR) {
     *why = "3-D grids only";
@@ -805,7 +827,7 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float 
   }
   const int R = g.R;
   if (ny == 0) ny = tma_ny(R);
-  if (!tma_ny_supported(ny) || per_sm < 0 || zblock < 0) {
+  if (!tma_ny_supported(ny) || per_sm < 0 || zblock < 0 || (aligned != 0 && aligned != 1)) {
     *why = "unsupported tile configuration";
     return cudaErrorInvalidValue;
   }
@@ -868,11 +890,25 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float 
   const int tiles_y = (g.n1 + ty - 1) / ty;
   pl.args.ntiles = pl.args.tiles_x * tiles_y;
   pl.args.W = (int64_t)pl.args.ntiles * g.n0;
-  if (pl.grid > pl.args.W) pl.grid = (int)pl.args.W;
-  // z-block height: about one CTA's share, so neighbouring tiles stream in step
-  const int64_t share = (pl.args.W + pl.grid - 1) / pl.grid;
-  const int64_t zb = zblock ? zblock : std::max<int64_t>(1, share);
-  pl.args.zblock = (int)std::min<int64_t>(g.n0, zb);
+  pl.args.aligned = aligned;
+  if (aligned) {
+    // whole segments: z-blocks of zblock planes (0: as many blocks as make the
+    // segments about fill the grid), at most one CTA per segment
+    int zb = zblock;
+    if (!zb) {
+      const int m = std::max(1, pl.grid / pl.args.ntiles);
+      zb = (g.n0 + m - 1) / m;
+    }
+    pl.args.zblock = std::min(g.n0, zb);
+    const int64_t S = (int64_t)pl.args.ntiles * ((g.n0 + pl.args.zblock - 1) / pl.args.zblock);
+    if (pl.grid > S) pl.grid = (int)S;
+  } else {
+    if (pl.grid > pl.args.W) pl.grid = (int)pl.args.W;
+    // z-block height: about one CTA's share, so neighbouring tiles stream in step
+    const int64_t share = (pl.args.W + pl.grid - 1) / pl.grid;
+    const int64_t zb = zblock ? zblock : std::max<int64_t>(1, share);
+    pl.args.zblock = (int)std::min<int64_t>(g.n0, zb);
+  }
   pl.name = ac ? "stencil3d_tma_acoustic" : "stencil3d_tma_diffusion";
   return cudaSuccess;
 }

@@ -52,11 +52,12 @@ def _configs(shape, so):
     for ty in (16, 32):
         for cps in (1, 2, 3):
             for zb in (0, 3, 11, shape[0]):
-                try:
-                    s.set_tile_config(tile_y=ty, ctas_per_sm=cps, zblock=zb)
-                except FdError:
-                    continue
-                out.append(dict(tile_y=ty, ctas_per_sm=cps, zblock=zb))
+                for al in (0, 1):
+                    try:
+                        s.set_tile_config(tile_y=ty, ctas_per_sm=cps, zblock=zb, aligned=al)
+                    except FdError:
+                        continue
+                    out.append(dict(tile_y=ty, ctas_per_sm=cps, zblock=zb, aligned=al))
     s.close()
     return out
 
@@ -71,6 +72,7 @@ def test_every_tile_configuration_is_bitwise_the_default(so, shape):
     for cfg in cfgs:
         u, up, rec, used = _acoustic(p, 60, cfg)
         assert used["tile_y"] == cfg["tile_y"] and used["ctas_per_sm"] == cfg["ctas_per_sm"]
+        assert used["aligned"] == cfg["aligned"]
         if cfg["zblock"]:
             assert used["zblock"] == min(cfg["zblock"], shape[0])
         assert np.array_equal(u, ref[0]), cfg
@@ -87,7 +89,8 @@ def test_diffusion_tile_configurations_agree():
     shape = (26, 41, 67)
     u0 = rng.standard_normal(shape).astype(np.float32)
     outs = []
-    for cfg in (None, dict(tile_y=16), dict(tile_y=32, zblock=5), dict(tile_y=16, ctas_per_sm=1)):
+    for cfg in (None, dict(tile_y=16), dict(tile_y=32, zblock=5), dict(tile_y=16, ctas_per_sm=1),
+                dict(aligned=1), dict(tile_y=16, zblock=9, aligned=1)):
         s = Solver(shape, (1.0 / 40,) * 3, 6, 0.1 * (1.0 / 40) ** 2, "diffusion", kernel="tma")
         if cfg:
             s.set_tile_config(**cfg)
@@ -112,8 +115,9 @@ def test_autotune_picks_a_timed_configuration_and_keeps_the_solution():
     best, tried = s.autotune(reps=3)
     assert len(tried) >= 4
     assert {t["tile_y"] for t in tried} == {16, 32}
+    assert {t["aligned"] for t in tried} == {0, 1}
     assert all(t["us_per_step"] > 0 for t in tried)
-    key = lambda t: (t["tile_y"], t["zblock"], t["ctas_per_sm"])
+    key = lambda t: (t["tile_y"], t["zblock"], t["ctas_per_sm"], t["aligned"])
     assert key(best) in {key(t) for t in tried}
     assert best["us_per_step"] == min(t["us_per_step"] for t in tried)
     cur = s.tile_config
@@ -139,7 +143,7 @@ def test_bad_tile_configurations_are_rejected_and_keep_the_current_one():
     s = Solver((20, 24, 28), (10.0,) * 3, 8, 0.1, "acoustic", kernel="tma")
     before = s.tile_config
     for bad in (dict(tile_y=24), dict(tile_y=64), dict(zblock=-1), dict(ctas_per_sm=-2),
-                dict(ctas_per_sm=64)):
+                dict(ctas_per_sm=64), dict(aligned=2)):
         with pytest.raises(FdError) as e:
             s.set_tile_config(**bad)
         assert e.value.status == FD_EINVAL
