@@ -198,7 +198,7 @@ fd_status fd_imaging(fd_ctx *adj, float *g, const float *u_next, const float *u_
 
 /*
  * The same FWI operations fused into a time step of the pipelined kernel (3-D
- * FD_ACOUSTIC, default tile height; FD_EUNSUPPORTED otherwise), so that the
+ * FD_ACOUSTIC; FD_EUNSUPPORTED otherwise), so that the
  * backward sweep neither copies the recomputed wavefield nor re-reads ν:
  *
  * fd_step_fwi: advance ctx one step exactly as fd_run(ctx, 1) does, and in the

@@ -1039,8 +1039,7 @@ fd_status fd_step_fwi(fd_ctx *c, float *d2_out, float *img_g, const float *img_d
   fd_status st = check_usable(c);
   if (st) return st;
   if (c->eq != FD_ACOUSTIC || !c->use_tma || !c->tma.fn_fwi)
-    return fail(c, FD_EUNSUPPORTED,
-                "fd_step_fwi needs the pipelined 3-D acoustic kernel at its default tile");
+    return fail(c, FD_EUNSUPPORTED, "fd_step_fwi needs the pipelined 3-D acoustic kernel");
   if (img_g && !img_d2) return fail(c, FD_EINVAL, "img_g needs img_d2");
   c->fwi_d2 = d2_out;
   c->fwi_img = img_g;

@@ -734,7 +734,7 @@ struct TmaPlan {
   float *level[2] = {nullptr, nullptr};
   TmaKernelFn fn = nullptr;        // one shot, tile height 8·ny
   TmaKernelFn fn_multi = nullptr;  // batches (default tile height only)
-  TmaKernelFn fn_fwi = nullptr;    // one shot with the FWI epilogue (acoustic, this tile)
+  TmaKernelFn fn_fwi = nullptr;    // one shot with the FWI epilogue (acoustic)
   int grid = 0, smem = 0;
   int grid_multi = 0, smem_multi = 0;
   int ny = 0;          // rows per consumer thread
@@ -797,12 +797,11 @@ inline cudaError_t tma_configure(TmaPlan &pl, int ny) {
   if constexpr (EQ == kAcoustic) {
     e = tma_instance<R, NYD, EQ, ISO, true>(pl.fn_multi, pl.smem_multi, per_sm_multi);
     if (e != cudaSuccess) return e;
-    // the FWI epilogue exists for the default tile; its occupancy must match the
-    // plan's grid, so other tiles go without it
-    if (ny == NYD) {
-      e = tma_instance<R, NYD, EQ, ISO, false, true>(pl.fn_fwi, pl.smem_fwi, pl.per_sm_fwi);
-      if (e != cudaSuccess) return e;
-    }
+    // the FWI epilogue instance of this tile; its occupancy must cover the plan's
+    // grid (checked once the grid is known)
+    e = ny == 2 ? tma_instance<R, 2, EQ, ISO, false, true>(pl.fn_fwi, pl.smem_fwi, pl.per_sm_fwi)
+                : tma_instance<R, 4, EQ, ISO, false, true>(pl.fn_fwi, pl.smem_fwi, pl.per_sm_fwi);
+    if (e != cudaSuccess) return e;
   }
   int dev = 0;
   cudaGetDevice(&dev);
@@ -895,8 +894,9 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float 
     // whole segments: z-blocks of zblock planes (0: as many blocks as make the
     // segments about fill the grid), at most one CTA per segment
     int zb = zblock;
-    if (!zb) {
-      const int m = std::max(1, pl.grid / pl.args.ntiles);
+    if (!zb) {  // no segment shorter than max(8, 2R) planes
+      const int mcap = std::max(1, g.n0 / std::max(8, 2 * R));
+      const int m = std::min(mcap, std::max(1, pl.grid / pl.args.ntiles));
       zb = (g.n0 + m - 1) / m;
     }
     pl.args.zblock = std::min(g.n0, zb);

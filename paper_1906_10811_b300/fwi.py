@@ -165,8 +165,11 @@ def _gradient_on_stream(p, d_obs, m, k, memory_budget, stats=None, profile=False
     rc = torch.as_tensor(p["rec_coords"], device="cuda")
     d_obs = torch.as_tensor(d_obs, dtype=torch.float32, device="cuda")
 
-    fwd = Solver(p["shape"], p["spacing"], p["so"], dt, "acoustic", device=True, profile=profile)
-    adj = Solver(p["shape"], p["spacing"], p["so"], dt, "acoustic", device=True, profile=profile)
+    # both contexts take the autotuner's tile (timed once per grid and order, cached)
+    fwd = Solver(p["shape"], p["spacing"], p["so"], dt, "acoustic", device=True, profile=profile,
+                 autotune=len(p["shape"]) == 3)
+    adj = Solver(p["shape"], p["spacing"], p["so"], dt, "acoustic", device=True, profile=profile,
+                 autotune=len(p["shape"]) == 3)
     try:
         fwd.set_model(mm, damp)
         fwd.set_sources(src, wav)
