@@ -236,7 +236,8 @@ fd_status fd_field_to_dense(fd_ctx *ctx, const float *padded, float *dense);
  *                z-block-major order (a run may start or end inside a
  *                segment); 1 = CTAs get whole (z-block, tile) segments, at
  *                most one CTA per segment, so that the CTAs holding
- *                neighbouring tiles start their segments together
+ *                neighbouring tiles start their segments together.  A new
+ *                context starts with 1 for FD_ACOUSTIC, 0 for FD_DIFFUSION
  *   us_per_step  stencil launch time measured by fd_autotune (µs; 0 when
  *                the configuration was set, not measured)
  *

@@ -70,7 +70,7 @@ struct GraphEntry {
 };
 
 using StencilFn = void (*)(const float *, float *, const float *, const float *, Geom, Coef);
-using StencilFn2D = void (*)(const MemberDesc *, int, const int64_t *);
+using StencilFn2D = void (*)(const MemberDesc *, int, const int64_t *, int);
 
 }  // namespace
 
@@ -608,8 +608,10 @@ void tile_of(const fd_ctx *c, fd_tile_config *cfg) {
   cfg->us_per_step = c->tune_us;
 }
 
-// Work split of the pipelined kernel a new context starts with (fd_tile_config.aligned).
-constexpr int kDefaultAligned = 0;
+// Work split a new context starts with (fd_tile_config.aligned): whole segments
+// for the acoustic step (measured best or within 3% of it at 128³-512³, so 4-16),
+// equal tile-plane ranges for diffusion (6% ahead at 512³ so 8).
+inline int default_aligned(fd_equation eq) { return eq == FD_ACOUSTIC ? 1 : 0; }
 
 // Autotuner choices for the process, per device, grid, order and equation.
 struct TuneKey {
@@ -815,7 +817,7 @@ fd_status fd_create(fd_ctx **out, int ndim, const int64_t *shape, const double *
     const char *why = nullptr;
     c->iso = spacing[0] == spacing[1] && spacing[1] == spacing[2];
     e = plan_tma(c->tma, c->g, eq == FD_ACOUSTIC ? kAcoustic : kDiffusion, c->iso, c->u, c->A,
-                 c->C, 0, 0, 0, kDefaultAligned, &why);
+                 c->C, 0, 0, 0, default_aligned(eq), &why);
     if (e == cudaSuccess) {
       c->use_tma = true;
       c->kernel_name = c->tma.name;
@@ -1394,6 +1396,14 @@ struct fd_batch {
   std::vector<int2> h_src, h_rec;
   std::vector<int4> h_items;
   cudaEvent_t ev = nullptr;
+  // captured chunks of ticks, valid while the launch parameters are unchanged
+  struct Graph {
+    int len;
+    int64_t kernels;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
+  std::vector<int64_t> graph_sig;
   int64_t launches = 0;
   bool failed = false;
   std::string err;
@@ -1533,7 +1543,7 @@ fd_status fd_batch_run(fd_batch *b, int nticks) {
       return bfail(b, FD_EINVAL, "a member would pass its wavelet length");
     fd_status st = FD_OK;
     // the batched kernel runs the default tile: a tuned member goes back to it
-    if (c->ndim == 3 && c->tma.ny != tma_ny(R)) st = replan(c, 0, 0, 0, kDefaultAligned);
+    if (c->ndim == 3 && c->tma.ny != tma_ny(R)) st = replan(c, 0, 0, 0, default_aligned(c->eq));
     if (!st && c->nrec > 0) st = ensure_rec_capacity(c, c->step + nticks + 1);
     if (!st) st = prepare_sources(c);
     if (!st && c->ndim == 3) st = prepare_fused(c);
@@ -1591,30 +1601,69 @@ fd_status fd_batch_run(fd_batch *b, int nticks) {
     }
     for (int k = 0; k < c->nrec; ++k) b->h_rec.push_back(make_int2((int)i, k));
   }
-  // work items: z-layers over all 3-D members, thick while much work remains
-  // and thinner towards the end (guided), tile by tile within a shot
+  // work items {shot, tile, za, zb}, z-layer by z-layer over all 3-D members,
+  // tile by tile within a shot, so that CTAs taking consecutive tickets hold
+  // neighbouring tiles at the same depth.  A batch whose work is at most 128
+  // planes per CTA is cut into at most one item per CTA (each shot into layers
+  // of about the average share, at least max(8, 2R) planes); a larger batch
+  // into layers that are thick while much work remains and thinner towards the
+  // end (guided), so the last items are short.
   const TmaPlan &plan0 = n3 ? m3[0]->tma : TmaPlan();
   b->h_items.clear();
   int grid3 = 0;
   if (n3) {
+    const int G = std::max(plan0.grid_multi, 1);
+    const int zmin = std::max(8, 2 * R);
+    int64_t W = 0;
     int zmax = 0;
-    for (fd_ctx *c : m3) zmax = std::max(zmax, c->g.n0);
-    for (int z = 0; z < zmax;) {
-      int64_t tiles_here = 0, rem = 0;
-      for (fd_ctx *c : m3)
-        if (c->g.n0 > z) {
-          tiles_here += c->tma.args.ntiles;
-          rem += (int64_t)c->tma.args.ntiles * (c->g.n0 - z);
-        }
-      const int64_t per_tile = rem / std::max<int64_t>(tiles_here, 1);
-      const int h = (int)std::min<int64_t>(128, std::max<int64_t>(16, per_tile / 2));
+    for (fd_ctx *c : m3) {
+      W += (int64_t)c->tma.args.ntiles * c->g.n0;
+      zmax = std::max(zmax, c->g.n0);
+    }
+    const int64_t share = W / G;
+    if (share <= 128) {
+      // shot i gets floor(n0_i G / W) layers (so there are no more items than
+      // CTAs), none thinner than zmin planes
+      std::vector<int> height(n3), layers(n3);
+      int kmax = 0;
       for (size_t i = 0; i < n3; ++i) {
-        fd_ctx *c = m3[i];
-        if (c->g.n0 <= z) continue;
-        const int zb = std::min(c->g.n0, z + h);
-        for (int t = 0; t < c->tma.args.ntiles; ++t) b->h_items.push_back(make_int4((int)i, t, z, zb));
+        const int n0 = m3[i]->g.n0;
+        const int64_t fit = (int64_t)n0 * G / std::max<int64_t>(W, 1);
+        layers[i] = (int)std::max<int64_t>(1, std::min<int64_t>(n0 / zmin, fit));
+        height[i] = (n0 + layers[i] - 1) / layers[i];
+        kmax = std::max(kmax, layers[i]);
       }
-      z += h;
+      for (int k = 0; k < kmax; ++k)
+        for (size_t i = 0; i < n3; ++i) {
+          const int za = k * height[i];
+          if (za >= m3[i]->g.n0) continue;
+          const int zb = std::min(m3[i]->g.n0, za + height[i]);
+          for (int t = 0; t < m3[i]->tma.args.ntiles; ++t)
+            b->h_items.push_back(make_int4((int)i, t, za, zb));
+        }
+    } else {
+      for (int z = 0; z < zmax;) {
+        int64_t tiles_here = 0, rem = 0;
+        for (fd_ctx *c : m3)
+          if (c->g.n0 > z) {
+            tiles_here += c->tma.args.ntiles;
+            rem += (int64_t)c->tma.args.ntiles * (c->g.n0 - z);
+          }
+        // layer height: half a tile's remaining depth, no more than makes the
+        // remaining work about two items per CTA, between 16 and 128 planes
+        const int64_t per_tile = rem / std::max<int64_t>(tiles_here, 1);
+        const int64_t fill = rem / (2 * (int64_t)G);
+        const int h =
+            (int)std::min<int64_t>(128, std::max<int64_t>(16, std::min(per_tile / 2, fill)));
+        for (size_t i = 0; i < n3; ++i) {
+          fd_ctx *c = m3[i];
+          if (c->g.n0 <= z) continue;
+          const int zb = std::min(c->g.n0, z + h);
+          for (int t = 0; t < c->tma.args.ntiles; ++t)
+            b->h_items.push_back(make_int4((int)i, t, z, zb));
+        }
+        z += h;
+      }
     }
     grid3 = (int)std::min<int64_t>(plan0.grid_multi, (int64_t)b->h_items.size());
   }
@@ -1668,36 +1717,80 @@ fd_status fd_batch_run(fd_batch *b, int nticks) {
   BCU(cudaGetLastError());
   ++b->launches;
   // error word of the pipelined kernel: the first 3-D member's
-  BatchArgs ba{b->d_shots, b->d_items, (int)b->h_items.size(), b->d_ticket, b->d_tick,
-               n3 ? m3[0]->d_err : nullptr};
   const int nsrc_e = (int)b->h_src.size(), nrec_e = (int)b->h_rec.size();
   const StencilFn2D f2 = batch2d_fn(R);
-  for (int t = 0; t < nticks; ++t) {
-    if (n3) {
-      plan0.fn_multi<<<grid3, kTmaThreads, plan0.smem_multi, b->stream>>>(
-          plan0.map_u[0], plan0.map_t[0], plan0.map_a, plan0.map_c, plan0.map_c, plan0.map_c,
-          TmaArgs{}, ba);
-      BCU(cudaGetLastError());
-      ++b->launches;
+  int *const err3 = n3 ? m3[0]->d_err : nullptr;
+  // the kernels of `len` ticks (tick *d_tick + j, j < len), then the counter moves
+  auto enqueue = [&](int len, int64_t *kernels) -> cudaError_t {
+    int64_t k = 0;
+    for (int j = 0; j < len; ++j) {
+      if (n3) {
+        BatchArgs ba{b->d_shots, b->d_items, (int)b->h_items.size(), b->d_ticket, b->d_tick, j,
+                     err3};
+        plan0.fn_multi<<<grid3, kTmaThreads, plan0.smem_multi, b->stream>>>(
+            plan0.map_u[0], plan0.map_t[0], plan0.map_a, plan0.map_c, plan0.map_c, plan0.map_c,
+            TmaArgs{}, ba);
+        ++k;
+      }
+      if (blk > 0) {
+        f2<<<(unsigned)blk, dim3(32, 8), 0, b->stream>>>(b->d_mem, (int)nm, b->d_tick, j);
+        ++k;
+      }
+      if (nsrc_e) {
+        k_inject_batch<<<(nsrc_e + 255) / 256, 256, 0, b->stream>>>(b->d_src, nsrc_e, b->d_mem,
+                                                                    b->d_tick, j);
+        ++k;
+      }
+      if (nrec_e) {
+        k_interp_batch<<<(nrec_e * 8 + 255) / 256, 256, 0, b->stream>>>(b->d_rec, nrec_e,
+                                                                        b->d_mem, b->d_tick, j);
+        ++k;
+      }
     }
-    if (blk > 0) {
-      f2<<<(unsigned)blk, dim3(32, 8), 0, b->stream>>>(b->d_mem, (int)nm, b->d_tick);
-      BCU(cudaGetLastError());
-      ++b->launches;
+    k_advance_step<<<1, 1, 0, b->stream>>>(b->d_tick, len);
+    *kernels = k + 1;
+    return cudaGetLastError();
+  };
+  // chunks of ticks replayed from captured graphs, keyed by everything a launch
+  // takes as a parameter (tables are rewritten in place, so pointers repeat)
+  const std::vector<int64_t> sig = {
+      (int64_t)nm, (int64_t)n3, (int64_t)b->h_items.size(), grid3, blk, nsrc_e, nrec_e,
+      (int64_t)(uintptr_t)b->d_shots, (int64_t)(uintptr_t)b->d_items,
+      (int64_t)(uintptr_t)b->d_mem, (int64_t)(uintptr_t)b->d_src, (int64_t)(uintptr_t)b->d_rec,
+      (int64_t)(uintptr_t)(n3 ? (void *)plan0.fn_multi : nullptr), plan0.smem_multi,
+      (int64_t)(uintptr_t)err3};
+  if (sig != b->graph_sig) {
+    for (auto &gph : b->graphs) cudaGraphExecDestroy(gph.exec);
+    b->graphs.clear();
+    b->graph_sig = sig;
+  }
+  for (int done = 0; done < nticks;) {
+    const int len = std::min(kGraphChunk, nticks - done);
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;
+    for (auto &gph : b->graphs)
+      if (gph.len == len) {
+        exec = gph.exec;
+        kernels = gph.kernels;
+      }
+    if (!exec) {
+      cudaGraph_t graph = nullptr;
+      BCU(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = enqueue(len, &kernels);
+      cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return bfail(b, FD_ECUDA, "batch graph capture: %s",
+                     cudaGetErrorString(e != cudaSuccess ? e : e2));
+      }
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return bfail(b, FD_ECUDA, "batch graph: %s", cudaGetErrorString(e));
+      b->graphs.push_back({len, kernels, exec});
     }
-    if (nsrc_e) {
-      k_inject_batch<<<(nsrc_e + 255) / 256, 256, 0, b->stream>>>(b->d_src, nsrc_e, b->d_mem, b->d_tick);
-      BCU(cudaGetLastError());
-      ++b->launches;
-    }
-    if (nrec_e) {
-      k_interp_batch<<<(nrec_e * 8 + 255) / 256, 256, 0, b->stream>>>(b->d_rec, nrec_e, b->d_mem, b->d_tick);
-      BCU(cudaGetLastError());
-      ++b->launches;
-    }
-    k_advance_step<<<1, 1, 0, b->stream>>>(b->d_tick, 1);
-    BCU(cudaGetLastError());
-    ++b->launches;
+    BCU(cudaGraphLaunch(exec, b->stream));
+    b->launches += kernels;
+    done += len;
   }
   BCU(cudaEventRecord(b->ev, b->stream));
   for (fd_ctx *c : b->members) {
@@ -1719,6 +1812,7 @@ void fd_batch_destroy(fd_batch *b) {
   if (b->d_src) cudaFree(b->d_src);
   if (b->d_rec) cudaFree(b->d_rec);
   if (b->d_tick) cudaFree(b->d_tick);
+  for (auto &gph : b->graphs) cudaGraphExecDestroy(gph.exec);
   if (b->ev) cudaEventDestroy(b->ev);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;

@@ -217,10 +217,11 @@ struct MemberDesc {
 };
 
 // One step of every 2-D member: blocks of 32 × 8 points, block -> member by
-// binary search over blk0.
+// binary search over blk0.  The batch kernels run tick *tick + j (j: the tick's
+// place in a captured chunk).
 template <int R>
 __global__ void __launch_bounds__(256)
-k_stencil2d_batch(const MemberDesc *__restrict__ d, int n, const int64_t *tick) {
+k_stencil2d_batch(const MemberDesc *__restrict__ d, int n, const int64_t *tick, int j) {
   int lo = 0, hi = n - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) / 2;
@@ -231,18 +232,18 @@ k_stencil2d_batch(const MemberDesc *__restrict__ d, int n, const int64_t *tick) 
   const int x = (int)(b % m.blocks_x) * 32 + threadIdx.x;
   const int y = (int)(b / m.blocks_x) * 8 + threadIdx.y;
   if (x >= m.g.n2 || y >= m.g.n1) return;
-  const int par = m.cur0 ^ (int)(*tick & 1);
+  const int par = m.cur0 ^ (int)((*tick + j) & 1);
   plain_point<R, kAcoustic, false>(m.level[par], m.level[par ^ 1], m.A, m.C, m.g, m.c, 0, y, x);
 }
 
 // Source corners of the 2-D members: entry = (member, corner).
 __global__ void k_inject_batch(const int2 *__restrict__ e, int n, const MemberDesc *__restrict__ d,
-                               const int64_t *tick) {
+                               const int64_t *tick, int j) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const MemberDesc &m = d[e[i].x];
   const int k = e[i].y;
-  const int64_t t = *tick;
+  const int64_t t = *tick + j;
   float *un = m.level[m.cur0 ^ (int)(t & 1) ^ 1];
   atomicAdd(un + m.src_off[k], m.src_scale[k] * m.wav[(m.step0 + t) * m.nsrc + k / m.nc]);
 }
@@ -250,7 +251,8 @@ __global__ void k_inject_batch(const int2 *__restrict__ e, int n, const MemberDe
 // Receivers of every member: entry = (member, receiver); 8 lanes per receiver
 // (lanes beyond the member's 2^D corners add zero), shuffle reduction.
 __global__ void k_interp_batch(const int2 *__restrict__ e, int n, const MemberDesc *__restrict__ d,
-                               const int64_t *tick) {
+                               const int64_t *tick, int j) {
+  const int64_t tk = *tick + j;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = t >> 3, c = t & 7;
   float v = 0.f;
@@ -260,13 +262,13 @@ __global__ void k_interp_batch(const int2 *__restrict__ e, int n, const MemberDe
     m = &d[e[r].x];
     k = e[r].y;
     if (c < m->nc) {
-      const float *un = m->level[m->cur0 ^ (int)(*tick & 1) ^ 1];
+      const float *un = m->level[m->cur0 ^ (int)(tk & 1) ^ 1];
       v = m->rec_w[k * m->nc + c] * un[m->rec_off[k * m->nc + c]];
     }
   }
 #pragma unroll
   for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if (r < n && c == 0) m->rec[(m->step0 + *tick + 1) * m->nrec + k] = v;
+  if (r < n && c == 0) m->rec[(m->step0 + tk + 1) * m->nrec + k] = v;
 }
 
 }  // namespace fdk

@@ -249,7 +249,8 @@ struct BatchArgs {
   const int4 *items;
   int nitems;
   unsigned *ticket;        // [2]: counter of this tick (tick & 1); the other is reset
-  const int64_t *tick;     // device tick counter of the batch
+  const int64_t *tick;     // device tick counter of the batch; this launch runs *tick + j
+  int j;
   int *err;
 };
 
@@ -372,7 +373,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
     else
       cta_range(args.W, blockIdx.x, gridDim.x, q0, q1);
   }
-  const int64_t tick = MULTI ? *bat.tick : 0;
+  const int64_t tick = MULTI ? *bat.tick + bat.j : 0;
   if constexpr (MULTI) {
     if (blockIdx.x == 0 && threadIdx.x == 0) bat.ticket[(tick + 1) & 1] = 0u;  // next tick's
   }
@@ -496,6 +497,11 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
   if constexpr (!MULTI) nstep = (AC && args.sp.first) ? *args.sp.step + args.sp.j : 0;
   // per-shot parameters (for one shot they stay the kernel's own arguments)
   const float *wk0 = args.c.w[0], *wk1 = args.c.w[1], *wk2 = args.c.w[2];
+  // batches on isotropic grids: the current shot's weights in registers (they
+  // would otherwise be global loads inside the stencil loop)
+  float wiso[R + 1];
+#pragma unroll
+  for (int k = 0; k <= R; ++k) wiso[k] = 0.f;
   SparseArgs sp = args.sp;
   Geom g = args.g;
   float *out = args.out;
@@ -528,6 +534,10 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
       wk0 = d.c.w[0];
       wk1 = d.c.w[1];
       wk2 = d.c.w[2];
+      if constexpr (ISO) {
+#pragma unroll
+        for (int k = 1; k <= R; ++k) wiso[k] = wk2[k];
+      }
       out = d.level[d.cur0 ^ (int)(tick & 1) ^ 1];
       sp.entries = d.entries;
       sp.first = d.first;
@@ -617,10 +627,11 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
                   const float s6 =
                       ((rowp[k] + rowp[-k]) + (ycol[R + j + k] + ycol[R + j - k])) +
                       (qz[j][tma_qslot<U, Q>(ph, R + k)] + qz[j][tma_qslot<U, Q>(ph, R - k)]);
+                  const float w = MULTI ? wiso[k] : wk2[k];
                   if ((k & 1) || !kSplit)
-                    lo = fmaf(wk2[k], s6 - uc6, lo);
+                    lo = fmaf(w, s6 - uc6, lo);
                   else
-                    le = fmaf(wk2[k], s6 - uc6, le);
+                    le = fmaf(w, s6 - uc6, le);
                 }
               } else {
                 const float uc2 = uc + uc;
