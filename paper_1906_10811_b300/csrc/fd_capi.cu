@@ -763,7 +763,10 @@ fd_status fd_create(fd_ctx **out, int ndim, const int64_t *shape, const double *
   for (int d = 0; d < ndim; ++d) {
     const int ax = d + 3 - ndim;
     const double s = scale / (spacing[d] * spacing[d]);
-    for (int k = 1; k <= R; ++k) c->coef.w[ax][k] = (float)(w[k] * s);
+    for (int k = 1; k <= R; ++k) {
+      c->coef.w[ax][k] = (float)(w[k] * s);
+      c->coef.wp[ax][k] = make_float2(c->coef.w[ax][k], c->coef.w[ax][k]);
+    }
     wc += w[0] * s;
   }
   c->coef.wc = (float)wc;
@@ -2001,7 +2004,10 @@ extern "C" fd_status fd_acoustic_run_noalloc(int ndim, const int64_t *shape, con
   for (int d = 0; d < ndim; ++d) {
     const int ax = d + 3 - ndim;
     const double s = 1.0 / (spacing[d] * spacing[d]);
-    for (int k = 1; k <= R; ++k) coef.w[ax][k] = (float)(w[k] * s);
+    for (int k = 1; k <= R; ++k) {
+      coef.w[ax][k] = (float)(w[k] * s);
+      coef.wp[ax][k] = make_float2(coef.w[ax][k], coef.w[ax][k]);
+    }
     wc += w[0] * s;
   }
   coef.wc = (float)wc;

@@ -335,6 +335,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
   constexpr int U = tma_unroll(R);                         // phases per unrolled group
   constexpr int QL = U == Q ? Q : Q + U - 1;               // queue registers per row
   constexpr bool kSplit = R > 4;                           // two accumulation chains
+  static_assert(NY % 2 == 0, "rows are updated in pairs (packed FP32x2 arithmetic)");
   constexpr int DX = tma_dx(FWI), XN = tma_xn(FWI);        // ring X slots, tiles per slot
   const bool img = FWI && args.img != nullptr;             // imaging inputs in ring X
   constexpr bool AC = EQ == kAcoustic;
@@ -490,18 +491,18 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
   // --------------------------------- consumers --------------------------------
   // Fill s of ring U is plane za-R+(s-s0) of the current segment (s0 = its first
   // fill); the queue slot of plane za-R+m is m mod Q.
-  float qz[NY][QL];
+  float2 qp[NY / 2][QL];  // queue, rows paired: .x row 2h, .y row 2h+1
   uint32_t su = 0, sx = 0;
   const int row0 = warp * NY;  // first tile row of this thread
   int64_t nstep = 0;
   if constexpr (!MULTI) nstep = (AC && args.sp.first) ? *args.sp.step + args.sp.j : 0;
   // per-shot parameters (for one shot they stay the kernel's own arguments)
-  const float *wk0 = args.c.w[0], *wk1 = args.c.w[1], *wk2 = args.c.w[2];
+  const float2 *wp0 = args.c.wp[0], *wp1 = args.c.wp[1], *wp2 = args.c.wp[2];
   // batches on isotropic grids: the current shot's weights in registers (they
   // would otherwise be global loads inside the stencil loop)
-  float wiso[R + 1];
+  float2 wiso[R + 1];
 #pragma unroll
-  for (int k = 0; k <= R; ++k) wiso[k] = 0.f;
+  for (int k = 0; k <= R; ++k) wiso[k] = make_float2(0.f, 0.f);
   SparseArgs sp = args.sp;
   Geom g = args.g;
   float *out = args.out;
@@ -531,12 +532,12 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
     if constexpr (MULTI) {
       const ShotDesc &d = bat.shots[shot];
       g = d.g;
-      wk0 = d.c.w[0];
-      wk1 = d.c.w[1];
-      wk2 = d.c.w[2];
+      wp0 = d.c.wp[0];
+      wp1 = d.c.wp[1];
+      wp2 = d.c.wp[2];
       if constexpr (ISO) {
 #pragma unroll
-        for (int k = 1; k <= R; ++k) wiso[k] = wk2[k];
+        for (int k = 1; k <= R; ++k) wiso[k] = wp2[k];
       }
       out = d.level[d.cur0 ^ (int)(tick & 1) ^ 1];
       sp.entries = d.entries;
@@ -575,7 +576,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
       if (!mbar_wait(&full_u[slot], (su / DU) & 1)) goto timeout;
       const float *pl = ring_u + slot * USLOT + (R + row0) * BW + HXB + lane;
 #pragma unroll
-      for (int j = 0; j < NY; ++j) qz[j][m] = pl[j * BW];
+      for (int h = 0; h < NY / 2; ++h) qp[h][m] = make_float2(pl[2 * h * BW], pl[(2 * h + 1) * BW]);
       if (p < za || p >= zb) {  // plane used for the queue only
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty_u[slot]);
@@ -599,7 +600,8 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
             if (!mbar_wait(&full_u[slot], (su / DU) & 1)) goto timeout;
             const float *pl = ring_u + slot * USLOT + (R + row0) * BW + HXB + lane;
 #pragma unroll
-            for (int j = 0; j < NY; ++j) qz[j][tma_qslot<U, Q>(ph, 2 * R)] = pl[j * BW];
+            for (int h = 0; h < NY / 2; ++h)
+              qp[h][tma_qslot<U, Q>(ph, 2 * R)] = make_float2(pl[2 * h * BW], pl[(2 * h + 1) * BW]);
             const uint32_t cs = (su - R) % DU;  // ring-U slot holding plane zc
             const float *cp = ring_u + cs * USLOT + row0 * BW + HXB + lane;
             const float *xs = nullptr;
@@ -614,49 +616,70 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
             for (int r = 0; r < NY + 2 * R; ++r) ycol[r] = cp[r * BW];
             float val[NY];
 #pragma unroll
-            for (int j = 0; j < NY; ++j) {
-              const float *rowp = cp + (R + j) * BW;
-              const float uc = qz[j][tma_qslot<U, Q>(ph, R)];
-              // difference form: the weights multiplying each k sum to zero
-              // exactly; above radius 4, odd and even k accumulate in two chains
-              float lo = 0.f, le = 0.f;
+            for (int h = 0; h < NY / 2; ++h) {
+              // rows j and j+1 in packed FP32x2 arithmetic (each lane the scalar
+              // operation sequence, round to nearest, nothing fused beyond it)
+              const int j = 2 * h;
+              const float *r0 = cp + (R + j) * BW, *r1 = r0 + BW;
+              const float2 uc = qp[h][tma_qslot<U, Q>(ph, R)];
+              float2 lo = make_float2(0.f, 0.f), le = lo;
               if (ISO) {
-                const float uc6 = 6.f * uc;
+                const float2 nuc6 = __fmul2_rn(make_float2(-6.f, -6.f), uc);
 #pragma unroll
                 for (int k = 1; k <= R; ++k) {
-                  const float s6 =
-                      ((rowp[k] + rowp[-k]) + (ycol[R + j + k] + ycol[R + j - k])) +
-                      (qz[j][tma_qslot<U, Q>(ph, R + k)] + qz[j][tma_qslot<U, Q>(ph, R - k)]);
-                  const float w = MULTI ? wiso[k] : wk2[k];
+                  const float2 sx =
+                      __fadd2_rn(make_float2(r0[k], r1[k]), make_float2(r0[-k], r1[-k]));
+                  const float2 sy = __fadd2_rn(make_float2(ycol[R + j + k], ycol[R + j + 1 + k]),
+                                               make_float2(ycol[R + j - k], ycol[R + j + 1 - k]));
+                  const float2 sz = __fadd2_rn(qp[h][tma_qslot<U, Q>(ph, R + k)],
+                                               qp[h][tma_qslot<U, Q>(ph, R - k)]);
+                  const float2 dd = __fadd2_rn(__fadd2_rn(__fadd2_rn(sx, sy), sz), nuc6);
+                  const float2 w = MULTI ? wiso[k] : wp2[k];
                   if ((k & 1) || !kSplit)
-                    lo = fmaf(w, s6 - uc6, lo);
+                    lo = __ffma2_rn(w, dd, lo);
                   else
-                    le = fmaf(w, s6 - uc6, le);
+                    le = __ffma2_rn(w, dd, le);
                 }
               } else {
-                const float uc2 = uc + uc;
+                const float2 nuc2 = __fmul2_rn(make_float2(-2.f, -2.f), uc);
 #pragma unroll
                 for (int k = 1; k <= R; ++k) {
-                  float acc = ((k & 1) || !kSplit) ? lo : le;
-                  acc = fmaf(wk2[k], (rowp[k] + rowp[-k]) - uc2, acc);
-                  acc = fmaf(wk1[k], (ycol[R + j + k] + ycol[R + j - k]) - uc2, acc);
-                  acc = fmaf(wk0[k],
-                             (qz[j][tma_qslot<U, Q>(ph, R + k)] + qz[j][tma_qslot<U, Q>(ph, R - k)]) -
-                                 uc2,
-                             acc);
+                  float2 acc = ((k & 1) || !kSplit) ? lo : le;
+                  acc = __ffma2_rn(
+                      wp2[k],
+                      __fadd2_rn(__fadd2_rn(make_float2(r0[k], r1[k]), make_float2(r0[-k], r1[-k])),
+                                 nuc2),
+                      acc);
+                  acc = __ffma2_rn(
+                      wp1[k],
+                      __fadd2_rn(__fadd2_rn(make_float2(ycol[R + j + k], ycol[R + j + 1 + k]),
+                                            make_float2(ycol[R + j - k], ycol[R + j + 1 - k])),
+                                 nuc2),
+                      acc);
+                  acc = __ffma2_rn(wp0[k],
+                                   __fadd2_rn(__fadd2_rn(qp[h][tma_qslot<U, Q>(ph, R + k)],
+                                                         qp[h][tma_qslot<U, Q>(ph, R - k)]),
+                                              nuc2),
+                                   acc);
                   if ((k & 1) || !kSplit)
                     lo = acc;
                   else
                     le = acc;
                 }
               }
-              const float lap = kSplit ? lo + le : lo;
+              const float2 lap = kSplit ? __fadd2_rn(lo, le) : lo;
               if (AC) {
-                const float up = xs[j * kTmaTX], a = xs[XT + j * kTmaTX],
-                            cc = xs[2 * XT + j * kTmaTX];
-                val[j] = fmaf(a, lap, fmaf(1.f + cc, uc, -cc * up));
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                  const float up = xs[(j + i) * kTmaTX], a = xs[XT + (j + i) * kTmaTX],
+                              cc = xs[2 * XT + (j + i) * kTmaTX];
+                  const float u = i ? uc.y : uc.x, l = i ? lap.y : lap.x;
+                  val[j + i] = fmaf(a, l, fmaf(1.f + cc, u, -cc * up));
+                }
               } else {
-                val[j] = uc + lap;
+                const float2 v = __fadd2_rn(uc, lap);
+                val[j] = v.x;
+                val[j + 1] = v.y;
               }
             }
             if (AC && nxt_z == zc) {
@@ -687,7 +710,8 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
                     // order the standalone imaging kernel uses
                     const int64_t off = (optr - out) + (int64_t)j * g.px;
                     if (args.d2) {
-                      const float uc = qz[j][tma_qslot<U, Q>(ph, R)], up = xs[j * kTmaTX];
+                      const float2 q2 = qp[j >> 1][tma_qslot<U, Q>(ph, R)];
+                      const float uc = (j & 1) ? q2.y : q2.x, up = xs[j * kTmaTX];
                       args.d2[off] = (val[j] - uc) - (uc - up);
                     }
                     if (img)  // img_d2 and the old img from ring X
@@ -714,9 +738,9 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
         if constexpr (U < Q) {
           // slide the window: slots U .. U+2R-1 become 0 .. 2R-1
 #pragma unroll
-          for (int j = 0; j < NY; ++j)
+          for (int h = 0; h < NY / 2; ++h)
 #pragma unroll
-            for (int m = 0; m < 2 * R; ++m) qz[j][m] = qz[j][m + U];
+            for (int m = 0; m < 2 * R; ++m) qp[h][m] = qp[h][m + U];
         }
       }
     }
