@@ -300,13 +300,15 @@ void fd_destroy(fd_ctx *ctx);
  *   with events.
  * fd_batch_add: ctx must be FD_ACOUSTIC, of the batch's space order, with a
  *   model set, on the batch's device; 3-D members need the pipelined kernel
- *   and must agree on whether their spacing is isotropic.  The batch borrows
+ *   and must share their grid spacing (their weights are one kernel
+ *   parameter); FD_EUNSUPPORTED otherwise.  The batch borrows
  *   the context: remove it before fd_destroy.  The batched kernel runs the
  *   default tile, so fd_batch_run puts a 3-D member with another tile height
  *   back to the default configuration (fd_set_tile_config) before its tick.
  * fd_batch_run: nticks ≥ 0 steps of every member (FD_EINVAL if a member would
  *   pass its wavelet); asynchronous on the batch stream.
- * fd_batch_remove: synchronises the batch stream and drops the member.
+ * fd_batch_remove: drops the member (no wait: its stream already waits for
+ *   the batch's last run).
  */
 typedef struct fd_batch fd_batch;
 fd_status fd_batch_create(fd_batch **out, int space_order, void *cuda_stream);

@@ -13,6 +13,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <new>
@@ -1407,6 +1408,7 @@ struct fd_batch {
   };
   std::vector<Graph> graphs;
   std::vector<int64_t> graph_sig;
+  std::vector<int> seen_len;  // chunk lengths launched once with graph_sig
   int64_t launches = 0;
   bool failed = false;
   std::string err;
@@ -1510,8 +1512,9 @@ fd_status fd_batch_add(fd_batch *b, fd_ctx *c) {
     return bfail(b, FD_EINVAL, "already a member");
   if (c->ndim == 3 && !b->members.empty()) {
     for (fd_ctx *o : b->members)
-      if (o->ndim == 3 && o->tma.fn_multi != c->tma.fn_multi)
-        return bfail(b, FD_EUNSUPPORTED, "3-D members must share spacing isotropy");
+      if (o->ndim == 3 && (o->tma.fn_multi != c->tma.fn_multi ||
+                           std::memcmp(o->coef.wp, c->coef.wp, sizeof c->coef.wp) != 0))
+        return bfail(b, FD_EUNSUPPORTED, "3-D members must share their grid spacing");
   }
   b->members.push_back(c);
   return FD_OK;
@@ -1521,7 +1524,8 @@ fd_status fd_batch_remove(fd_batch *b, fd_ctx *c) {
   if (!b || !c) return FD_EINVAL;
   auto it = std::find(b->members.begin(), b->members.end(), c);
   if (it == b->members.end()) return bfail(b, FD_EINVAL, "not a member");
-  cudaStreamSynchronize(b->stream);
+  // no wait: the member's stream already waits for the batch's last run, and the
+  // next run rewrites the device tables in stream order
   b->members.erase(it);
   return FD_OK;
 }
@@ -1723,13 +1727,22 @@ fd_status fd_batch_run(fd_batch *b, int nticks) {
   const int nsrc_e = (int)b->h_src.size(), nrec_e = (int)b->h_rec.size();
   const StencilFn2D f2 = batch2d_fn(R);
   int *const err3 = n3 ? m3[0]->d_err : nullptr;
+  // the 3-D shots share their weights (fd_batch_add): a kernel parameter
+  BatchArgs bargs{};
+  bargs.shots = b->d_shots;
+  bargs.items = b->d_items;
+  bargs.nitems = (int)b->h_items.size();
+  bargs.ticket = b->d_ticket;
+  bargs.tick = b->d_tick;
+  bargs.err = err3;
+  if (n3) std::memcpy(bargs.wp, m3[0]->coef.wp, sizeof bargs.wp);
   // the kernels of `len` ticks (tick *d_tick + j, j < len), then the counter moves
   auto enqueue = [&](int len, int64_t *kernels) -> cudaError_t {
     int64_t k = 0;
     for (int j = 0; j < len; ++j) {
       if (n3) {
-        BatchArgs ba{b->d_shots, b->d_items, (int)b->h_items.size(), b->d_ticket, b->d_tick, j,
-                     err3};
+        BatchArgs ba = bargs;
+        ba.j = j;
         plan0.fn_multi<<<grid3, kTmaThreads, plan0.smem_multi, b->stream>>>(
             plan0.map_u[0], plan0.map_t[0], plan0.map_a, plan0.map_c, plan0.map_c, plan0.map_c,
             TmaArgs{}, ba);
@@ -1761,14 +1774,20 @@ fd_status fd_batch_run(fd_batch *b, int nticks) {
       (int64_t)(uintptr_t)b->d_shots, (int64_t)(uintptr_t)b->d_items,
       (int64_t)(uintptr_t)b->d_mem, (int64_t)(uintptr_t)b->d_src, (int64_t)(uintptr_t)b->d_rec,
       (int64_t)(uintptr_t)(n3 ? (void *)plan0.fn_multi : nullptr), plan0.smem_multi,
-      (int64_t)(uintptr_t)err3};
+      (int64_t)(uintptr_t)err3,
+      (int64_t)std::hash<std::string>()(
+          std::string(reinterpret_cast<const char *>(bargs.wp), sizeof bargs.wp))};
   if (sig != b->graph_sig) {
     for (auto &gph : b->graphs) cudaGraphExecDestroy(gph.exec);
     b->graphs.clear();
+    b->seen_len.clear();
     b->graph_sig = sig;
   }
+  // chunks of power-of-two lengths; a length is captured the second time it
+  // runs with these parameters (a serving loop changes them often)
   for (int done = 0; done < nticks;) {
-    const int len = std::min(kGraphChunk, nticks - done);
+    int len = 1;
+    while (2 * len <= std::min(kGraphChunk, nticks - done)) len *= 2;
     cudaGraphExec_t exec = nullptr;
     int64_t kernels = 0;
     for (auto &gph : b->graphs)
@@ -1776,6 +1795,13 @@ fd_status fd_batch_run(fd_batch *b, int nticks) {
         exec = gph.exec;
         kernels = gph.kernels;
       }
+    if (!exec && std::find(b->seen_len.begin(), b->seen_len.end(), len) == b->seen_len.end()) {
+      b->seen_len.push_back(len);
+      BCU(enqueue(len, &kernels));
+      b->launches += kernels;
+      done += len;
+      continue;
+    }
     if (!exec) {
       cudaGraph_t graph = nullptr;
       BCU(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));

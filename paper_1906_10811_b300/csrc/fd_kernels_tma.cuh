@@ -252,6 +252,7 @@ struct BatchArgs {
   const int64_t *tick;     // device tick counter of the batch; this launch runs *tick + j
   int j;
   int *err;
+  float2 wp[3][kMaxR + 1];  // weight pairs of every 3-D shot (they share the spacing)
 };
 
 // Queue slot of window offset o (0 .. 2R) in phase ph of an unrolled group.
@@ -498,11 +499,12 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
   if constexpr (!MULTI) nstep = (AC && args.sp.first) ? *args.sp.step + args.sp.j : 0;
   // per-shot parameters (for one shot they stay the kernel's own arguments)
   const float2 *wp0 = args.c.wp[0], *wp1 = args.c.wp[1], *wp2 = args.c.wp[2];
-  // batches on isotropic grids: the current shot's weights in registers (they
-  // would otherwise be global loads inside the stencil loop)
-  float2 wiso[R + 1];
-#pragma unroll
-  for (int k = 0; k <= R; ++k) wiso[k] = make_float2(0.f, 0.f);
+  // weight pair of axis a and offset k, a kernel parameter (the 3-D shots of a
+  // batch share their spacing and so their weights)
+  auto weight = [&](int a, int k) -> float2 {
+    if constexpr (MULTI) return bat.wp[a][k];
+    return a == 0 ? wp0[k] : (a == 1 ? wp1[k] : wp2[k]);
+  };
   SparseArgs sp = args.sp;
   Geom g = args.g;
   float *out = args.out;
@@ -532,13 +534,6 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
     if constexpr (MULTI) {
       const ShotDesc &d = bat.shots[shot];
       g = d.g;
-      wp0 = d.c.wp[0];
-      wp1 = d.c.wp[1];
-      wp2 = d.c.wp[2];
-      if constexpr (ISO) {
-#pragma unroll
-        for (int k = 1; k <= R; ++k) wiso[k] = wp2[k];
-      }
       out = d.level[d.cur0 ^ (int)(tick & 1) ^ 1];
       sp.entries = d.entries;
       sp.first = d.first;
@@ -634,7 +629,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
                   const float2 sz = __fadd2_rn(qp[h][tma_qslot<U, Q>(ph, R + k)],
                                                qp[h][tma_qslot<U, Q>(ph, R - k)]);
                   const float2 dd = __fadd2_rn(__fadd2_rn(__fadd2_rn(sx, sy), sz), nuc6);
-                  const float2 w = MULTI ? wiso[k] : wp2[k];
+                  const float2 w = weight(2, k);
                   if ((k & 1) || !kSplit)
                     lo = __ffma2_rn(w, dd, lo);
                   else
@@ -646,17 +641,17 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
                 for (int k = 1; k <= R; ++k) {
                   float2 acc = ((k & 1) || !kSplit) ? lo : le;
                   acc = __ffma2_rn(
-                      wp2[k],
+                      weight(2, k),
                       __fadd2_rn(__fadd2_rn(make_float2(r0[k], r1[k]), make_float2(r0[-k], r1[-k])),
                                  nuc2),
                       acc);
                   acc = __ffma2_rn(
-                      wp1[k],
+                      weight(1, k),
                       __fadd2_rn(__fadd2_rn(make_float2(ycol[R + j + k], ycol[R + j + 1 + k]),
                                             make_float2(ycol[R + j - k], ycol[R + j + 1 - k])),
                                  nuc2),
                       acc);
-                  acc = __ffma2_rn(wp0[k],
+                  acc = __ffma2_rn(weight(0, k),
                                    __fadd2_rn(__fadd2_rn(qp[h][tma_qslot<U, Q>(ph, R + k)],
                                                          qp[h][tma_qslot<U, Q>(ph, R - k)]),
                                               nuc2),

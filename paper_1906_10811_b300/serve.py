@@ -6,8 +6,9 @@ device and steps them together (``fd_batch_run``); between rounds it admits
 requests that have arrived, first come first served, while their device
 footprint (``fd_footprint_bytes``) fits the HBM budget and a member slot is
 free, and retires shots that have finished (their traces are read back and
-their memory freed).  New shots are set up on their own CUDA streams while the
-batch is running, so admission overlaps the device work.
+their memory freed, while the next round already runs).  New shots are set up
+on their own CUDA streams while the batch is running, so admission overlaps
+the device work.
 
 Scheduling is separate from execution: :class:`Server` drives any backend with
 the small interface of :class:`DeviceBackend`, which lets the policy be tested
@@ -71,9 +72,12 @@ class DeviceBackend:
     def run(self, nticks):
         self.batch.run(nticks)
 
-    def finish(self, handle):
-        """Leave the batch, read the traces (waits for the shot's last step), free it."""
+    def leave(self, handle):
+        """Take a finished shot out of the batch (no wait: later runs skip it)."""
         self.batch.remove(handle)
+
+    def collect(self, handle):
+        """Read the traces of a shot that left (waits for its last step) and free it."""
         _, rec = handle.read(field=False)
         handle.close()
         return rec
@@ -106,10 +110,11 @@ class Server:
             if self.backend.footprint(r) > self.budget:
                 raise ValueError(f"shot {r.id} needs more device memory than the budget")
         active = {}            # id -> [request, handle, steps done, footprint, admitted time]
-        used = 0
+        left = []              # shots that left the batch in the last round, to collect
+        used = 0               # footprint held on the device (freed when collected)
         results = []
         t0 = self.clock()
-        while pending or active:
+        while pending or active or left:
             now = self.clock() - t0
             # admit arrivals, first come first served, while memory and slots allow
             while (pending and pending[0].arrival <= now and len(active) < self.max_members):
@@ -123,22 +128,30 @@ class Server:
                 used += fp
                 active[r.id] = [r, h, 0, fp, self.clock() - t0]
                 self.log.append(("admit", r.id, self.clock() - t0))
-            if not active:
+            if not active and not left:
                 wait = pending[0].arrival - (self.clock() - t0)
                 if wait > 0:
                     self.sleep(min(wait, 0.05))
                 continue
-            n = min([self.ticks] + [a[0].problem["nt"] - a[2] for a in active.values()])
-            self.backend.run(n)
-            for a in active.values():
-                a[2] += n
-            for rid in [rid for rid, a in active.items() if a[2] == a[0].problem["nt"]]:
-                r, h, _, fp, adm = active.pop(rid)
-                rec = self.backend.finish(h)
+            # queue the next round first, then collect the shots that finished in
+            # the previous one: reading their traces overlaps this round's work
+            finished = []
+            if active:
+                n = min([self.ticks] + [a[0].problem["nt"] - a[2] for a in active.values()])
+                self.backend.run(n)
+                for a in active.values():
+                    a[2] += n
+                for rid in [rid for rid, a in active.items() if a[2] == a[0].problem["nt"]]:
+                    r, h, _, fp, adm = active.pop(rid)
+                    self.backend.leave(h)
+                    finished.append((r, h, fp, adm))
+            for r, h, fp, adm in left:
+                rec = self.backend.collect(h)
                 used -= fp
                 t = self.clock() - t0
                 results.append(ShotResult(r.id, rec, r.arrival, adm, t))
                 self.log.append(("finish", r.id, t))
+            left = finished
         return sorted(results, key=lambda x: x.id)
 
 

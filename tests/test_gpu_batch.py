@@ -109,6 +109,20 @@ def test_batch_rejects_wrong_members():
         with pytest.raises(FdError):
             batch.add(d)
         d.close()
+        # 3-D members share their spacing (their weights are one kernel parameter)
+        q = small_problem((20, 21, 22), 8, 10)
+        a = Solver(q["shape"], q["spacing"], 8, q["dt"], "acoustic")
+        a.set_model(q["m"], q["damp"])
+        batch.add(a)
+        h2 = tuple(1.1 * h for h in q["spacing"])
+        b = Solver(q["shape"], h2, 8, q["dt"], "acoustic")
+        b.set_model(q["m"], q["damp"])
+        with pytest.raises(FdError) as e:
+            batch.add(b)
+        assert "spacing" in str(e.value)
+        batch.remove(a)
+        a.close()
+        b.close()
 
 
 def test_footprint_covers_allocations():

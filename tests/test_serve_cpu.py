@@ -23,6 +23,7 @@ class FakeBackend:
     def __init__(self, clock):
         self.clock = clock
         self.members = {}
+        self.left = {}
         self.used = 0
         self.peak_used = 0
         self.peak_members = 0
@@ -45,9 +46,13 @@ class FakeBackend:
             assert m[1] <= m[0].problem["nt"], "a shot ran past its end"
         self.clock.t += 1e-3 * n * len(self.members)
 
-    def finish(self, h):
+    def leave(self, h):
         steps = self.members.pop(h.id)[1]
         assert steps == h.problem["nt"]
+        self.left[h.id] = steps
+
+    def collect(self, h):
+        steps = self.left.pop(h.id)
         self.used -= h.problem["size"]
         return steps
 
