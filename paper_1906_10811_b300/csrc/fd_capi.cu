@@ -759,7 +759,6 @@ fd_status fd_create(fd_ctx **out, int ndim, const int64_t *shape, const double *
   double w[kMaxR + 1];
   lib_weights(space_order, w);
   const double scale = eq == FD_DIFFUSION ? o.nu * dt : 1.0;
-  double wc = 0.0;
   std::memset(&c->coef, 0, sizeof c->coef);
   for (int d = 0; d < ndim; ++d) {
     const int ax = d + 3 - ndim;
@@ -768,9 +767,7 @@ fd_status fd_create(fd_ctx **out, int ndim, const int64_t *shape, const double *
       c->coef.w[ax][k] = (float)(w[k] * s);
       c->coef.wp[ax][k] = make_float2(c->coef.w[ax][k], c->coef.w[ax][k]);
     }
-    wc += w[0] * s;
   }
-  c->coef.wc = (float)wc;
   select_kernel(c);
 
   auto bail = [&](fd_status st) {
@@ -2026,7 +2023,6 @@ extern "C" fd_status fd_acoustic_run_noalloc(int ndim, const int64_t *shape, con
   std::memset(&coef, 0, sizeof coef);
   double w[kMaxR + 1];
   lib_weights(space_order, w);
-  double wc = 0.0;
   for (int d = 0; d < ndim; ++d) {
     const int ax = d + 3 - ndim;
     const double s = 1.0 / (spacing[d] * spacing[d]);
@@ -2034,9 +2030,7 @@ extern "C" fd_status fd_acoustic_run_noalloc(int ndim, const int64_t *shape, con
       coef.w[ax][k] = (float)(w[k] * s);
       coef.wp[ax][k] = make_float2(coef.w[ax][k], coef.w[ax][k]);
     }
-    wc += w[0] * s;
   }
-  coef.wc = (float)wc;
   StencilFn fn = plain_acoustic_fn(R, ndim == 3);
   float *cur = lev0, *prev = lev1;
   dim3 block(32, 8);

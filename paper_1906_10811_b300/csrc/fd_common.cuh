@@ -45,7 +45,6 @@ __host__ __device__ inline int64_t gidx(const Geom &g, int z, int y, int x) {
 struct Coef {
   float w[3][kMaxR + 1];  // w[axis][k] for k = 1..R; axis 0 unused in 2-D
   float2 wp[3][kMaxR + 1];  // the same weights as pairs (w, w) for packed FP32x2 arithmetic
-  float wc;               // Σ_axes w_0 / h_axis² (kept for reference; not used by the kernels)
 };
 
 }  // namespace fdk

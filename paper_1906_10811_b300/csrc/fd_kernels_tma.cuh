@@ -1,25 +1,29 @@
 // fd_kernels_tma.cuh -- pipelined 3-D stencil kernel: TMA plane ring + register z-queue.
 //
 // Work: the grid's (x, y) extent is cut into TX × TY tiles; a "tile-plane" is one
-// tile at one z.  The W = tiles × n0 tile-planes are ordered z-block-major (z
-// blocks of ZB planes; inside a block tile by tile, x fastest, then z) and split
-// into G contiguous ranges, one per persistent CTA (G = SMs × resident CTAs), so
-// every CTA gets the same number of planes to within one.  With ZB about W/G,
-// CTAs that hold neighbouring tiles start at the same z and stream in step, so
-// the halo rows one tile shares with the next are still in L2 when the other
-// reads them.  A range is a few z-segments of single tiles; a CTA streams each
-// segment along z.
+// tile at one z, a "segment" the planes of one tile inside one z-block (ZB
+// planes).  Work is ordered z-block-major (inside a block tile by tile, x
+// fastest, then z) and shared out over G persistent CTAs (G = SMs × resident
+// CTAs) in one of two ways:
+//   - equal ranges: every CTA gets the same number of tile-planes to within one
+//     (a range may start or end inside a segment);
+//   - whole segments: every CTA gets whole segments, at most one CTA per segment.
+// Either way CTAs that hold neighbouring tiles stream the same z at about the same
+// time, so the halo rows one tile shares with the next are still in L2 when the
+// other reads them.  A batch launch (MULTI) takes items {shot, tile, za, zb} from
+// a ticket counter instead.
 //
 // Per CTA: warp NW (the last) is the producer; one lane issues
 //   - a TMA load of the u^n plane p (tile plus halo: (TX+2·HXB) × (TY+2R)) into
 //     ring U (DU slots), for every p in [za-R, zb+R) of a segment [za, zb);
 //   - TMA loads of the u^{n-1}, A, C tiles (TX × TY) of plane p-R into ring X
 //     (DX slots) when p-R is a plane the CTA updates (acoustic only).
-// The NW consumer warps own NY rows each (lane = x; TY = NW·NY).  For every plane p they
-// push u^n(p) at their points into a register queue of 2R+1 planes, and once
-// the queue holds p-2R..p they update plane zc = p-R: z-neighbours from the
-// queue, x- and y-neighbours from the shared copy of plane zc (still in ring U),
-// then store u^{n+1} with coalesced 128-byte rows.
+// The NW consumer warps own NY rows each (lane = x; TY = NW·NY), updated in pairs
+// with packed FP32x2 arithmetic.  For every plane p they push u^n(p) at their
+// points into a register queue of 2R+1 planes, and once the queue holds
+// p-2R..p they update plane zc = p-R: z-neighbours from the queue, x- and
+// y-neighbours from the shared copy of plane zc (still in ring U), then store
+// u^{n+1} with coalesced 128-byte rows.
 //
 // Every mbarrier wait is bounded (clock64 budget).  On expiry the kernel writes
 // an error code and its block index into err[0..1], stops, waits (bounded) for
@@ -491,7 +495,8 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
 
   // --------------------------------- consumers --------------------------------
   // Fill s of ring U is plane za-R+(s-s0) of the current segment (s0 = its first
-  // fill); the queue slot of plane za-R+m is m mod Q.
+  // fill); the warm-up puts planes za-R .. za+R-1 in queue slots 0 .. 2R-1, and
+  // the steady loop addresses the window through tma_qslot.
   float2 qp[NY / 2][QL];  // queue, rows paired: .x row 2h, .y row 2h+1
   uint32_t su = 0, sx = 0;
   const int row0 = warp * NY;  // first tile row of this thread
