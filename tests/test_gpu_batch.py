@@ -142,3 +142,29 @@ def test_footprint_covers_allocations():
     s.close()
     assert fp > 0
     assert used <= fp * 1.1 + (64 << 20)
+
+
+def test_batch_runs_of_every_length_match_alone():
+    """Runs of 1..64+ ticks (launched, then replayed from captured graphs) give
+    bitwise the alone results."""
+    from paper_1906_10811_b300 import Batch
+    probs = [small_problem(shape, 8, nt, nrec=6, seed=seed)
+             for shape, nt, seed in [((27, 33, 38), 160, 11), ((45, 52), 160, 12)]]
+    refs = [_alone(p, p["nt"]) for p in probs]
+    batch = Batch(8)
+    solvers = [_solver(p) for p in probs]
+    for s in solvers:
+        batch.add(s)
+    done = 0
+    for n in (1, 2, 3, 2, 5, 8, 13, 8, 21, 33, 64):
+        batch.run(n)
+        done += n
+    assert done == 160
+    for s, ref in zip(solvers, refs):
+        batch.remove(s)
+        u, rec = s.read()
+        up = s.read_prev()
+        assert np.array_equal(u, ref[0]) and np.array_equal(up, ref[1])
+        assert np.array_equal(rec, ref[2])
+        s.close()
+    batch.close()

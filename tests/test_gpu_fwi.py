@@ -185,3 +185,50 @@ def test_fused_step_is_refused_where_it_does_not_apply():
         assert e.value.status == B.FD_EINVAL
         B.fd_step_fwi(s.ctx, d2_out=buf)
         assert s.steps == 1
+
+
+@pytest.mark.parametrize("cfg", [dict(tile_y=16), dict(tile_y=32, aligned=1),
+                                 dict(tile_y=32, zblock=9, ctas_per_sm=1, aligned=0)])
+def test_fused_epilogues_match_snapshots_and_imaging_for_every_tile(cfg):
+    """fd_step_fwi's d2 equals the second difference of snapshots, and its imaging
+    accumulation equals fd_imaging, bit for bit, whatever the tile configuration."""
+    import torch
+    from paper_1906_10811_b300 import Solver
+    from paper_1906_10811_b300 import binding as B
+    p = _shot(shape=(26, 30, 37), nt=40)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    # one stream for the library calls and the torch ops between them (the binding
+    # calls below do not order a private solver stream with torch's)
+    work = torch.cuda.Stream()
+    with torch.cuda.stream(work), \
+            Solver(p["shape"], p["spacing"], 8, p["dt"], "acoustic", device=True) as f, \
+            Solver(p["shape"], p["spacing"], 8, p["dt"], "acoustic", device=True) as a:
+        for s in (f, a):
+            s.set_model(dev(p["m"]), dev(p["damp"]))
+            s.set_tile_config(**cfg)
+        f.set_sources(dev(p["src_coords"]), dev(p["wavelet"]))
+        a.set_sources(dev(p["rec_coords"][:3]), dev(np.ones((40, 3), np.float32)))
+        n = B.fd_field_elems(f.ctx)
+        f.run(7)
+        a.run(7)
+        cur, prev = torch.empty(n, device="cuda"), torch.empty(n, device="cuda")
+        nxt, d2 = torch.empty(n, device="cuda"), torch.empty(n, device="cuda")
+        g_pad = torch.zeros(n, device="cuda")
+        for _ in range(5):
+            B.fd_snapshot(f.ctx, cur, prev)
+            B.fd_step_fwi(f.ctx, d2_out=d2)
+            B.fd_snapshot(f.ctx, nxt)
+            want = torch.empty(p["shape"], device="cuda")
+            got = torch.empty(p["shape"], device="cuda")
+            B.fd_field_to_dense(f.ctx, (nxt - cur) - (cur - prev), want)
+            B.fd_field_to_dense(f.ctx, d2, got)
+            assert torch.equal(got, want)
+            # the fused imaging against fd_imaging after the same adjoint step
+            gd = torch.zeros(p["shape"], device="cuda")
+            g_pad.zero_()
+            B.fd_step_fwi(a.ctx, img_g=g_pad, img_d2=d2, scale=-0.37)
+            B.fd_imaging(a.ctx, gd, nxt, cur, prev, -0.37)
+            gfused = torch.empty(p["shape"], device="cuda")
+            B.fd_field_to_dense(a.ctx, g_pad, gfused)
+            assert torch.equal(gfused, gd)
+        torch.cuda.synchronize()
