@@ -438,7 +438,8 @@ def run_fwi(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": dict(fwi_config(w, k, tuning),
                                checkpoint_bytes=stats.get("checkpoint_bytes"),
-                               block_bytes=stats.get("block_bytes")),
+                               block_bytes=stats.get("block_bytes"), tile=stats.get("tile"),
+                               tile_choice="fd_autotune_fwi (plain + d2 + imaging steps)"),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk}
         print(json.dumps(line), flush=True)

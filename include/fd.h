@@ -273,6 +273,16 @@ fd_status fd_get_tile_config(const fd_ctx *ctx, fd_tile_config *cfg);
 fd_status fd_set_tile_config(fd_ctx *ctx, const fd_tile_config *cfg);
 fd_status fd_autotune(fd_ctx *ctx, int reps, fd_tile_config *best, fd_tile_config *tried,
                       int max_tried, int *ntried);
+/*
+ * fd_autotune_fwi: the same search for the FWI sweep (FD_ACOUSTIC, pipelined
+ * kernel): a candidate's time is one plain step plus one fd_step_fwi step
+ * writing the second difference plus one accumulating the imaging condition
+ * (two more scratch fields), the kernels of one backward step; configurations
+ * without an FWI instance that fits the grid are skipped.  Cached separately
+ * from fd_autotune's choice.
+ */
+fd_status fd_autotune_fwi(fd_ctx *ctx, int reps, fd_tile_config *best, fd_tile_config *tried,
+                          int max_tried, int *ntried);
 
 /* Name of the stencil kernel variant fd_run launches (static string). */
 const char *fd_kernel_name(const fd_ctx *ctx);

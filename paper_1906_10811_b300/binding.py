@@ -73,6 +73,9 @@ SIGNATURES = {
     "fd_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(fd_tile_config),
                                    ctypes.POINTER(fd_tile_config), ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_int)]),
+    "fd_autotune_fwi": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(fd_tile_config),
+                                       ctypes.POINTER(fd_tile_config), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int)]),
     "fd_kernel_launches": (_i64, [_vp]),
     "fd_field_elems": (_i64, [_vp]),
     "fd_snapshot": (ctypes.c_int, [_vp, _vp, _vp]),
@@ -260,14 +263,17 @@ def fd_set_tile_config(ctx, tile_y=0, zblock=0, ctas_per_sm=0, tile_x=0, aligned
     _check(ctx, load().fd_set_tile_config(ctx, ctypes.byref(cfg)))
 
 
-def fd_autotune(ctx, reps=5, max_tried=64):
-    """Time the tile configurations and use the fastest: (best, tried) as dicts."""
+def fd_autotune(ctx, reps=5, max_tried=64, fwi=False):
+    """Time the tile configurations and use the fastest: (best, tried) as dicts.
+
+    fwi: time them as the FWI sweep's kernels (fd_autotune_fwi).  max_tried = 0
+    passes no list, so an earlier choice for the same problem is reused."""
     best = fd_tile_config()
-    tried = (fd_tile_config * max_tried)()
+    tried = (fd_tile_config * max_tried)() if max_tried > 0 else None
     n = ctypes.c_int()
-    _check(ctx, load().fd_autotune(ctx, int(reps), ctypes.byref(best), tried, int(max_tried),
-                                   ctypes.byref(n)))
-    return best.as_dict(), [tried[i].as_dict() for i in range(n.value)]
+    fn = load().fd_autotune_fwi if fwi else load().fd_autotune
+    _check(ctx, fn(ctx, int(reps), ctypes.byref(best), tried, int(max_tried), ctypes.byref(n)))
+    return best.as_dict(), [tried[i].as_dict() for i in range(n.value)] if tried else []
 
 
 def fd_kernel_launches(ctx):

@@ -616,22 +616,23 @@ inline int default_aligned(fd_equation eq) { return eq == FD_ACOUSTIC ? 1 : 0; }
 
 // Autotuner choices for the process, per device, grid, order and equation.
 struct TuneKey {
-  int device, so, eq, iso;
+  int device, so, eq, iso, fwi;
   int64_t n0, n1, n2;
   bool operator<(const TuneKey &o) const {
-    return std::tie(device, so, eq, iso, n0, n1, n2) <
-           std::tie(o.device, o.so, o.eq, o.iso, o.n0, o.n1, o.n2);
+    return std::tie(device, so, eq, iso, fwi, n0, n1, n2) <
+           std::tie(o.device, o.so, o.eq, o.iso, o.fwi, o.n0, o.n1, o.n2);
   }
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, fd_tile_config> g_tune_cache;
 
-TuneKey tune_key(const fd_ctx *c) {
-  return TuneKey{c->device, c->so, (int)c->eq, c->iso ? 1 : 0, c->g.n0, c->g.n1, c->g.n2};
+TuneKey tune_key(const fd_ctx *c, bool fwi) {
+  return TuneKey{c->device, c->so, (int)c->eq, c->iso ? 1 : 0, fwi ? 1 : 0,
+                 c->g.n0, c->g.n1, c->g.n2};
 }
 
 fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_config *tried,
-                        int max_tried, int *ntried);
+                        int max_tried, int *ntried, bool fwi = false);
 
 }  // namespace
 
@@ -1169,6 +1170,16 @@ fd_status fd_autotune(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_config 
   return autotune_impl(c, reps, best, tried, max_tried, ntried);
 }
 
+fd_status fd_autotune_fwi(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_config *tried,
+                          int max_tried, int *ntried) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  if (reps < 1) return fail(c, FD_EINVAL, "reps must be >= 1");
+  if (c->eq != FD_ACOUSTIC || !c->use_tma)
+    return fail(c, FD_EUNSUPPORTED, "fd_autotune_fwi needs the pipelined 3-D acoustic kernel");
+  return autotune_impl(c, reps, best, tried, max_tried, ntried, true);
+}
+
 const char *fd_kernel_name(const fd_ctx *c) { return c ? c->kernel_name : "none"; }
 
 int64_t fd_field_elems(const fd_ctx *c) { return c ? c->g.total : -1; }
@@ -1242,14 +1253,24 @@ namespace {
 
 // Median µs of reps launches of plan p (after two warm-up launches), reading
 // the context's current levels and writing `out`, without sources.
+// With fwi, one repetition is a plain step, a step with the second-difference
+// epilogue (into fwi_buf[0]) and a step with the imaging epilogue (reading
+// fwi_buf[0], accumulating into fwi_buf[1]): the kernels of one backward step of
+// the FWI sweep.
 fd_status time_plan(fd_ctx *c, const TmaPlan &p, float *out, int reps, cudaEvent_t *ev,
-                    double *us) {
+                    double *us, float *const *fwi_buf = nullptr) {
   const int cur = c->cur;
   for (int i = 0; i < 2 + reps; ++i) {
     if (i >= 2) CU(cudaEventRecord(ev[i - 2], c->stream));
     cudaError_t e = launch_tma_step(p, cur, out, c->coef, c->d_err, SparseArgs{}, c->stream);
+    if (e == cudaSuccess && fwi_buf)
+      e = launch_tma_step_fwi(p, cur, out, c->coef, c->d_err, SparseArgs{}, fwi_buf[0], nullptr,
+                              nullptr, 0.f, c->stream);
+    if (e == cudaSuccess && fwi_buf)
+      e = launch_tma_step_fwi(p, cur, out, c->coef, c->d_err, SparseArgs{}, nullptr, fwi_buf[1],
+                              fwi_buf[0], 1.f, c->stream);
     if (e != cudaSuccess) return fail(c, FD_ECUDA, "autotune launch: %s", cudaGetErrorString(e));
-    ++c->launches;
+    c->launches += fwi_buf ? 3 : 1;
   }
   CU(cudaEventRecord(ev[reps], c->stream));
   CU(cudaEventSynchronize(ev[reps]));
@@ -1265,9 +1286,9 @@ fd_status time_plan(fd_ctx *c, const TmaPlan &p, float *out, int reps, cudaEvent
 }
 
 fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_config *tried,
-                        int max_tried, int *ntried) {
+                        int max_tried, int *ntried, bool fwi) {
   if (ntried) *ntried = 0;
-  const TuneKey key = tune_key(c);
+  const TuneKey key = tune_key(c, fwi);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -1280,9 +1301,18 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
       return FD_OK;
     }
   }
-  float *scratch = nullptr;
+  float *scratch = nullptr, *fbuf[2] = {nullptr, nullptr};
   fd_status st = dalloc(c, &scratch, (size_t)c->g.total);
-  if (st) return st;
+  if (!st && fwi) st = dalloc(c, &fbuf[0], (size_t)c->g.total);
+  if (!st && fwi) st = dalloc(c, &fbuf[1], (size_t)c->g.total);
+  if (!st && fwi) CU(cudaMemsetAsync(fbuf[0], 0, c->g.total * sizeof(float), c->stream));
+  if (!st && fwi) CU(cudaMemsetAsync(fbuf[1], 0, c->g.total * sizeof(float), c->stream));
+  if (st) {
+    dfree(c, scratch);
+    dfree(c, fbuf[0]);
+    dfree(c, fbuf[1]);
+    return st;
+  }
   std::vector<cudaEvent_t> ev(reps + 1, nullptr);
   for (auto &e : ev)
     if (!st && cudaEventCreate(&e) != cudaSuccess) st = fail(c, FD_ECUDA, "event creation");
@@ -1336,8 +1366,9 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
       cudaGetLastError();
       continue;
     }
+    if (fwi && !r.fn_fwi) continue;  // no FWI instance fits this grid
     double us = 0.0;
-    st = time_plan(c, r, scratch, reps, ev.data(), &us);
+    st = time_plan(c, r, scratch, reps, ev.data(), &us, fwi ? fbuf : nullptr);
     if (st) break;
     fd_tile_config cfg{kTmaTX, tma_ty(cd.ny), r.args.zblock, r.per_sm, cd.aligned, us};
     if (tried && n < max_tried) tried[n] = cfg;
@@ -1350,6 +1381,8 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
   for (auto &e : ev)
     if (e) cudaEventDestroy(e);
   dfree(c, scratch);
+  dfree(c, fbuf[0]);
+  dfree(c, fbuf[1]);
   if (st) return st;
   // a candidate that gave up on a wait leaves its code in the error word
   int err[2] = {0, 0};

@@ -165,11 +165,14 @@ def _gradient_on_stream(p, d_obs, m, k, memory_budget, stats=None, profile=False
     rc = torch.as_tensor(p["rec_coords"], device="cuda")
     d_obs = torch.as_tensor(d_obs, dtype=torch.float32, device="cuda")
 
-    # both contexts take the autotuner's tile (timed once per grid and order, cached)
-    fwd = Solver(p["shape"], p["spacing"], p["so"], dt, "acoustic", device=True, profile=profile,
-                 autotune=len(p["shape"]) == 3)
-    adj = Solver(p["shape"], p["spacing"], p["so"], dt, "acoustic", device=True, profile=profile,
-                 autotune=len(p["shape"]) == 3)
+    fwd = Solver(p["shape"], p["spacing"], p["so"], dt, "acoustic", device=True, profile=profile)
+    adj = Solver(p["shape"], p["spacing"], p["so"], dt, "acoustic", device=True, profile=profile)
+    if fwd.kernel_name == "stencil3d_tma_acoustic":
+        # both contexts take the tile timed on the sweep's own kernels (cached per grid)
+        fwd.autotune(fwi=True, cached=True)
+        t = fwd.tile_config
+        adj.set_tile_config(tile_y=t["tile_y"], zblock=t["zblock"], ctas_per_sm=t["ctas_per_sm"],
+                            aligned=t["aligned"])
     try:
         fwd.set_model(mm, damp)
         fwd.set_sources(src, wav)
@@ -218,6 +221,8 @@ def _gradient_on_stream(p, d_obs, m, k, memory_budget, stats=None, profile=False
         if stats is not None:
             stats.update(k=k, checkpoint_bytes=int(ck.numel()) * 4, block_bytes=blk_bytes,
                          fused=bool(fused),
+                         tile=fwd.tile_config if fwd.kernel_name.startswith("stencil3d_tma")
+                         else None,
                          launches_forward=fwd.kernel_launches, launches_adjoint=adj.kernel_launches)
             if profile:
                 nf, msf = fwd.profile()

@@ -135,10 +135,14 @@ class Solver:
                              aligned=aligned)
         self._out()
 
-    def autotune(self, reps=5):
-        """Time every tile configuration and keep the fastest: (best, tried)."""
+    def autotune(self, reps=5, fwi=False, cached=False):
+        """Time every tile configuration and keep the fastest: (best, tried).
+
+        fwi: time them as one backward step of the FWI sweep (fd_autotune_fwi);
+        cached: reuse the process's earlier choice for this problem if there is
+        one (``tried`` is then empty)."""
         self._in()
-        out = B.fd_autotune(self.ctx, reps=reps)
+        out = B.fd_autotune(self.ctx, reps=reps, fwi=fwi, max_tried=0 if cached else 64)
         self._out()
         return out
 

@@ -176,3 +176,21 @@ def test_a_tuned_shot_joins_a_batch_at_the_default_tile():
     b.close()
     s.close()
     assert np.array_equal(u, ref[0]) and np.array_equal(up, ref[1]) and np.array_equal(rec, ref[2])
+
+
+def test_fwi_autotune_times_the_sweep_kernels_and_caches():
+    from paper_1906_10811_b300 import Solver
+    p = small_problem((36, 40, 70), 8, nt=10)
+    s = Solver(p["shape"], p["spacing"], 8, p["dt"], "acoustic", kernel="tma")
+    s.set_model(p["m"], p["damp"])
+    best, tried = s.autotune(reps=2, fwi=True)
+    assert len(tried) >= 4 and all(t["us_per_step"] > 0 for t in tried)
+    key = lambda t: (t["tile_y"], t["zblock"], t["ctas_per_sm"], t["aligned"])
+    assert key(best) in {key(t) for t in tried}
+    assert best["us_per_step"] == min(t["us_per_step"] for t in tried)
+    s2 = Solver(p["shape"], p["spacing"], 8, p["dt"], "acoustic", kernel="tma")
+    again, none = s2.autotune(fwi=True, cached=True)
+    assert none == [] and key(again) == key(best)
+    assert key(s2.tile_config) == key(best)
+    s.close()
+    s2.close()
