@@ -59,9 +59,9 @@ WORKLOADS = {
 # and tile configuration as they are now.
 NCU_TRAFFIC = {
     # profiles/stencil3d_tma_acoustic256_so8.md: mean of 3 launches, read 298.54 MB + write 27.47 MB
-    ("stencil3d_tma_acoustic", "acoustic256", 8, 32, 64, 2, 1): 326.01e6,
+    ("stencil3d_tma_acoustic", "acoustic256", 8, 32, 64, 2, 1, 0): 326.01e6,
     # profiles/stencil3d_tma_roofline512.md: mean of 2 launches, read 2239.31 MB + write 495.77 MB
-    ("stencil3d_tma_acoustic", "roofline512", 8, 32, 512, 2, 1): 2735.08e6,
+    ("stencil3d_tma_acoustic", "roofline512", 8, 32, 512, 2, 1, 0): 2735.08e6,
 }
 
 
@@ -85,9 +85,9 @@ def parse():
     ap.add_argument("--kernel", default="auto", choices=["auto", "plain", "tma"])
     ap.add_argument("--tile", default="auto",
                     help="auto: the autotuner picks the pipelined kernel's tile configuration "
-                         "before the timed region; default: the built-in one; TY,ZB,CPS[,AL]: "
-                         "tile height, z-block height, CTAs per SM and whole-segment split "
-                         "given explicitly")
+                         "before the timed region; default: the built-in one; TY,ZB,CPS[,AL[,SK]]: "
+                         "tile height, z-block height, CTAs per SM, whole-segment split and "
+                         "C-tile skipping given explicitly")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -480,8 +480,8 @@ def run_diffusion(args):
         if args.tile == "auto":
             tune_tried = len(s.autotune(reps=5)[1])
         elif args.tile != "default":
-            ty, zb, cps, al = ([int(v) for v in args.tile.split(",")] + [0])[:4]
-            s.set_tile_config(tile_y=ty, zblock=zb, ctas_per_sm=cps, aligned=al)
+            ty, zb, cps, al, sk = ([int(v) for v in args.tile.split(",")] + [0, 0])[:5]
+            s.set_tile_config(tile_y=ty, zblock=zb, ctas_per_sm=cps, aligned=al, skip_c=sk)
         tile = s.tile_config
 
     def sweep():
@@ -527,7 +527,8 @@ def run_diffusion(args):
                     kernel=args.kernel, boundary=args.boundary)
         if tile is not None:
             se.set_tile_config(tile_y=tile["tile_y"], zblock=tile["zblock"],
-                               ctas_per_sm=tile["ctas_per_sm"], aligned=tile["aligned"])
+                               ctas_per_sm=tile["ctas_per_sm"], aligned=tile["aligned"],
+                               skip_c=tile["skip_c"])
         from paper_1906_10811_b300 import binding as B
 
         def sweep_e2e():
@@ -624,8 +625,8 @@ def run_ours(args):
             _, tried = s.autotune(reps=5)
             tune_tried = len(tried)
         elif args.tile != "default":
-            ty, zb, cps, al = ([int(v) for v in args.tile.split(",")] + [0])[:4]
-            s.set_tile_config(tile_y=ty, zblock=zb, ctas_per_sm=cps, aligned=al)
+            ty, zb, cps, al, sk = ([int(v) for v in args.tile.split(",")] + [0, 0])[:5]
+            s.set_tile_config(tile_y=ty, zblock=zb, ctas_per_sm=cps, aligned=al, skip_c=sk)
         tile = s.tile_config
 
     def shot():
@@ -661,8 +662,8 @@ def run_ours(args):
     peak, peak_kind = load_peak()
     avg_launch_s = st_ms / max(n_st, 1) / 1e3
     achieved = BYTES_PER_POINT["acoustic"] * npts / avg_launch_s / 1e9
-    tkey = ((tile["tile_y"], tile["zblock"], tile["ctas_per_sm"], tile["aligned"]) if tile
-            else (0, 0, 0, 0))
+    tkey = ((tile["tile_y"], tile["zblock"], tile["ctas_per_sm"], tile["aligned"], tile["skip_c"])
+            if tile else (0, 0, 0, 0, 0))
     traffic = NCU_TRAFFIC.get((kernel_name, args.workload, w["so"]) + tkey)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
@@ -685,7 +686,8 @@ def run_ours(args):
                     kernel=args.kernel, autotune=tile is not None and args.tile == "auto")
         if tile is not None and args.tile not in ("auto", "default"):
             se.set_tile_config(tile_y=tile["tile_y"], zblock=tile["zblock"],
-                               ctas_per_sm=tile["ctas_per_sm"], aligned=tile["aligned"])
+                               ctas_per_sm=tile["ctas_per_sm"], aligned=tile["aligned"],
+                               skip_c=tile["skip_c"])
         from paper_1906_10811_b300 import binding as B
 
         def shot_e2e():

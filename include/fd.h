@@ -238,6 +238,10 @@ fd_status fd_field_to_dense(fd_ctx *ctx, const float *padded, float *dense);
  *                most one CTA per segment, so that the CTAs holding
  *                neighbouring tiles start their segments together.  A new
  *                context starts with 1 for FD_ACOUSTIC, 0 for FD_DIFFUSION
+ *   skip_c       FD_ACOUSTIC up to space order 8: 1 = tile-planes where C =
+ *                (m−σ)/(m+σ) is 1 at every point (no damping) take C = 1 instead
+ *                of loading it (4 of the 20 bytes per point; flags recomputed
+ *                after fd_set_model); ignored elsewhere.  New contexts: 0
  *   us_per_step  stencil launch time measured by fd_autotune (µs; 0 when
  *                the configuration was set, not measured)
  *
@@ -246,12 +250,13 @@ fd_status fd_field_to_dense(fd_ctx *ctx, const float *padded, float *dense);
  * fd_set_tile_config: use cfg (tile_x 32 or 0, tile_y 16 or 32 or 0 for the
  *   default, zblock ≥ 0 with 0 meaning one CTA's share (aligned = 0) or the
  *   height that makes about as many segments as CTAs (aligned = 1),
- *   ctas_per_sm ≥ 0 with 0 meaning as many as fit, aligned 0 or 1);
+ *   ctas_per_sm ≥ 0 with 0 meaning as many as fit, aligned and skip_c 0 or 1);
  *   FD_EINVAL for anything else, leaving the current configuration in
  *   place.  Captured graphs are dropped.
  * fd_autotune: time every configuration of the search space (tile_y in
  *   {16, 32} × ctas_per_sm in 1..fit × (aligned 0 with zblock in {share/2,
- *   share, 2·share} | aligned 1 with m or 2m z-blocks, m = CTAs / tiles),
+ *   share, 2·share} | aligned 1 with m or 2m z-blocks, m = CTAs / tiles)
+ *   × skip_c {0, 1} where it applies,
  *   reps ≥ 1 timed launches each after two warm-up launches, median taken),
  *   then use the fastest.  The candidate launches read the current fields
  *   and write a scratch field allocated for the call, so the solution is not
@@ -266,6 +271,7 @@ typedef struct {
   int zblock;
   int ctas_per_sm;
   int aligned;
+  int skip_c;
   double us_per_step;
 } fd_tile_config;
 

@@ -41,7 +41,7 @@ class fd_options(ctypes.Structure):
 class fd_tile_config(ctypes.Structure):
     _fields_ = [("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("zblock", ctypes.c_int),
                 ("ctas_per_sm", ctypes.c_int), ("aligned", ctypes.c_int),
-                ("us_per_step", ctypes.c_double)]
+                ("skip_c", ctypes.c_int), ("us_per_step", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -257,9 +257,9 @@ def fd_get_tile_config(ctx):
     return cfg.as_dict()
 
 
-def fd_set_tile_config(ctx, tile_y=0, zblock=0, ctas_per_sm=0, tile_x=0, aligned=0):
+def fd_set_tile_config(ctx, tile_y=0, zblock=0, ctas_per_sm=0, tile_x=0, aligned=0, skip_c=0):
     cfg = fd_tile_config(int(tile_x), int(tile_y), int(zblock), int(ctas_per_sm), int(aligned),
-                         0.0)
+                         int(skip_c), 0.0)
     _check(ctx, load().fd_set_tile_config(ctx, ctypes.byref(cfg)))
 
 

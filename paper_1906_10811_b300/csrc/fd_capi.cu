@@ -127,6 +127,11 @@ struct fd_ctx {
   int4 *sp_entries = nullptr;
   int *sp_first = nullptr;
   bool sp_dirty = true;
+  // tile-planes of the pipelined kernel where C = 1 (no damping): their C tile is skipped
+  unsigned char *unit_c = nullptr;
+  size_t unit_c_cap = 0;
+  bool unit_c_dirty = true;
+  bool skip_c = false;  // fd_tile_config.skip_c
   bool fused = false;                // this run uses the fused/overlapped sparse path
   cudaStream_t side = nullptr;
   cudaEvent_t ev_step[2] = {nullptr, nullptr}, ev_rec[2] = {nullptr, nullptr};
@@ -314,10 +319,11 @@ fd_status launch_stencil(fd_ctx *c, const float *ucur, float *unext, int j) {
       sp.nc = c->nc;
     }
     const int cur = ucur == c->u[0] ? 0 : 1;
+    const unsigned char *uc = c->skip_c ? c->unit_c : nullptr;
     cudaError_t e =
         c->fwi_on ? launch_tma_step_fwi(c->tma, cur, unext, c->coef, c->d_err, sp, c->fwi_d2,
-                                        c->fwi_img, c->fwi_img_d2, c->fwi_scale, c->stream)
-                  : launch_tma_step(c->tma, cur, unext, c->coef, c->d_err, sp, c->stream);
+                                        c->fwi_img, c->fwi_img_d2, c->fwi_scale, c->stream, uc)
+                  : launch_tma_step(c->tma, cur, unext, c->coef, c->d_err, sp, c->stream, uc);
     if (e != cudaSuccess) return fail(c, FD_ECUDA, "TMA stencil launch: %s", cudaGetErrorString(e));
     ++c->launches;
     return FD_OK;
@@ -561,6 +567,26 @@ fd_status prepare_fused(fd_ctx *c) {
   return FD_OK;
 }
 
+// Flags of the tile-planes where C = 1 for the current plan (acoustic pipelined
+// kernel); recomputed after fd_set_model or a new tile configuration.
+fd_status prepare_unit_c(fd_ctx *c) {
+  if (!c->use_tma || !c->skip_c || !c->unit_c_dirty) return FD_OK;
+  const size_t n = (size_t)c->tma.args.ntiles * c->g.n0;
+  if (n > c->unit_c_cap) {
+    dfree(c, c->unit_c);
+    c->unit_c_cap = 0;
+    fd_status st = dalloc(c, &c->unit_c, n);
+    if (st) return st;
+    c->unit_c_cap = n;
+  }
+  drop_graphs(c);  // the captured launches hold the flags pointer
+  k_unit_c<<<(unsigned)n, 128, 0, c->stream>>>(c->C, c->g, c->tma.args.tiles_x, kTmaTX,
+                                               tma_ty(c->tma.ny), c->unit_c);
+  CHECK_LAUNCH();
+  c->unit_c_dirty = false;
+  return FD_OK;
+}
+
 void select_kernel(fd_ctx *c) {
   const int R = c->so / 2;
   const bool three = c->ndim == 3;
@@ -582,7 +608,7 @@ void select_kernel(fd_ctx *c) {
 // Rebuild the pipelined kernel's plan for another tile configuration; on
 // failure the current plan stays.  Source tables are keyed by tile and the
 // captured graphs hold the old plan, so both are redone.
-fd_status replan(fd_ctx *c, int ny, int per_sm, int zblock, int aligned) {
+fd_status replan(fd_ctx *c, int ny, int per_sm, int zblock, int aligned, int skip_c = 0) {
   TmaPlan p{};
   const char *why = nullptr;
   cudaError_t e = plan_tma(p, c->g, c->eq == FD_ACOUSTIC ? kAcoustic : kDiffusion, c->iso, c->u,
@@ -595,7 +621,9 @@ fd_status replan(fd_ctx *c, int ny, int per_sm, int zblock, int aligned) {
   CU(cudaStreamSynchronize(c->stream));
   drop_graphs(c);
   c->tma = p;
+  c->skip_c = skip_c && c->eq == FD_ACOUSTIC && c->g.R <= 4;
   c->sp_dirty = true;
+  c->unit_c_dirty = true;
   c->tune_us = 0.0;
   return FD_OK;
 }
@@ -606,6 +634,7 @@ void tile_of(const fd_ctx *c, fd_tile_config *cfg) {
   cfg->zblock = c->tma.args.zblock;
   cfg->ctas_per_sm = c->tma.per_sm;
   cfg->aligned = c->tma.args.aligned;
+  cfg->skip_c = c->skip_c ? 1 : 0;
   cfg->us_per_step = c->tune_us;
 }
 
@@ -880,6 +909,7 @@ fd_status fd_set_model(fd_ctx *c, const float *m, const float *damp) {
                 dtmax, (double)mmin);
   c->model_set = true;
   c->src_dirty = c->nsrc > 0;
+  c->unit_c_dirty = true;
   return FD_OK;
 }
 
@@ -1001,6 +1031,8 @@ fd_status run_steps(fd_ctx *c, int nt, bool graphs) {
   st = prepare_fused(c);
   if (st) return st;
   if (was_fused != c->fused) drop_graphs(c);
+  st = prepare_unit_c(c);
+  if (st) return st;
   k_set_step<<<1, 1, 0, c->stream>>>(c->d_step, c->step);
   CHECK_LAUNCH();
   if (c->nrec > 0 && c->rec_rows == 0 && c->step == 0) {
@@ -1154,11 +1186,12 @@ fd_status fd_set_tile_config(fd_ctx *c, const fd_tile_config *cfg) {
   if (!c->use_tma) return fail(c, FD_EUNSUPPORTED, "the plain kernel has no tile configuration");
   if ((cfg->tile_x != 0 && cfg->tile_x != kTmaTX) || cfg->tile_y % kTmaNW ||
       (cfg->tile_y != 0 && !tma_ny_supported(cfg->tile_y / kTmaNW)) || cfg->zblock < 0 ||
-      cfg->ctas_per_sm < 0 || (cfg->aligned != 0 && cfg->aligned != 1))
+      cfg->ctas_per_sm < 0 || (cfg->aligned != 0 && cfg->aligned != 1) ||
+      (cfg->skip_c != 0 && cfg->skip_c != 1))
     return fail(c, FD_EINVAL,
-                "tile configuration %dx%d, zblock %d, %d CTAs/SM, aligned %d is not offered",
-                cfg->tile_x, cfg->tile_y, cfg->zblock, cfg->ctas_per_sm, cfg->aligned);
-  return replan(c, cfg->tile_y / kTmaNW, cfg->ctas_per_sm, cfg->zblock, cfg->aligned);
+                "tile configuration %dx%d, zblock %d, %d CTAs/SM, aligned %d, skip_c %d is not offered",
+                cfg->tile_x, cfg->tile_y, cfg->zblock, cfg->ctas_per_sm, cfg->aligned, cfg->skip_c);
+  return replan(c, cfg->tile_y / kTmaNW, cfg->ctas_per_sm, cfg->zblock, cfg->aligned, cfg->skip_c);
 }
 
 fd_status fd_autotune(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_config *tried,
@@ -1229,7 +1262,7 @@ void fd_destroy(fd_ctx *c) {
   dfree(c, c->d_step); dfree(c, c->d_stats); dfree(c, c->d_err);
   dfree(c, c->wav); dfree(c, c->src_scale); dfree(c, c->src_off); dfree(c, c->src_dense); dfree(c, c->src_w);
   dfree(c, c->rec_off); dfree(c, c->rec_w); dfree(c, c->rec);
-  dfree(c, c->sp_entries); dfree(c, c->sp_first);
+  dfree(c, c->sp_entries); dfree(c, c->sp_first); dfree(c, c->unit_c);
   for (int i = 0; i < 2; ++i) {
     if (c->ev_step[i]) cudaEventDestroy(c->ev_step[i]);
     if (c->ev_rec[i]) cudaEventDestroy(c->ev_rec[i]);
@@ -1258,17 +1291,19 @@ namespace {
 // fwi_buf[0], accumulating into fwi_buf[1]): the kernels of one backward step of
 // the FWI sweep.
 fd_status time_plan(fd_ctx *c, const TmaPlan &p, float *out, int reps, cudaEvent_t *ev,
-                    double *us, float *const *fwi_buf = nullptr) {
+                    double *us, float *const *fwi_buf = nullptr,
+                    const unsigned char *unit_c = nullptr) {
   const int cur = c->cur;
   for (int i = 0; i < 2 + reps; ++i) {
     if (i >= 2) CU(cudaEventRecord(ev[i - 2], c->stream));
-    cudaError_t e = launch_tma_step(p, cur, out, c->coef, c->d_err, SparseArgs{}, c->stream);
+    cudaError_t e =
+        launch_tma_step(p, cur, out, c->coef, c->d_err, SparseArgs{}, c->stream, unit_c);
     if (e == cudaSuccess && fwi_buf)
       e = launch_tma_step_fwi(p, cur, out, c->coef, c->d_err, SparseArgs{}, fwi_buf[0], nullptr,
-                              nullptr, 0.f, c->stream);
+                              nullptr, 0.f, c->stream, unit_c);
     if (e == cudaSuccess && fwi_buf)
       e = launch_tma_step_fwi(p, cur, out, c->coef, c->d_err, SparseArgs{}, nullptr, fwi_buf[1],
-                              fwi_buf[0], 1.f, c->stream);
+                              fwi_buf[0], 1.f, c->stream, unit_c);
     if (e != cudaSuccess) return fail(c, FD_ECUDA, "autotune launch: %s", cudaGetErrorString(e));
     c->launches += fwi_buf ? 3 : 1;
   }
@@ -1294,7 +1329,8 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end() && !tried) {
       const fd_tile_config cfg = it->second;
-      fd_status st = replan(c, cfg.tile_y / kTmaNW, cfg.ctas_per_sm, cfg.zblock, cfg.aligned);
+      fd_status st =
+          replan(c, cfg.tile_y / kTmaNW, cfg.ctas_per_sm, cfg.zblock, cfg.aligned, cfg.skip_c);
       if (st) return st;
       c->tune_us = cfg.us_per_step;
       if (best) *best = cfg;
@@ -1354,6 +1390,10 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
       }
     }
   }
+  // each candidate once more skipping the C tiles where C = 1 (acoustic, R <= 4)
+  const bool try_skip = c->eq == FD_ACOUSTIC && R <= 4;
+  unsigned char *flags = nullptr;
+  if (!st && try_skip) st = dalloc(c, &flags, (size_t)c->tma.args.ntiles * c->g.n0 * 2 + 64);
   fd_tile_config win{};
   double win_us = 1e300;
   int n = 0;
@@ -1367,17 +1407,30 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
       continue;
     }
     if (fwi && !r.fn_fwi) continue;  // no FWI instance fits this grid
-    double us = 0.0;
-    st = time_plan(c, r, scratch, reps, ev.data(), &us, fwi ? fbuf : nullptr);
-    if (st) break;
-    fd_tile_config cfg{kTmaTX, tma_ty(cd.ny), r.args.zblock, r.per_sm, cd.aligned, us};
-    if (tried && n < max_tried) tried[n] = cfg;
-    ++n;
-    if (us < win_us) {
-      win_us = us;
-      win = cfg;
+    for (int sk = 0; sk <= (try_skip ? 1 : 0) && !st; ++sk) {
+      if (sk) {
+        const int64_t nf = (int64_t)r.args.ntiles * c->g.n0;
+        k_unit_c<<<(unsigned)nf, 128, 0, c->stream>>>(c->C, c->g, r.args.tiles_x, kTmaTX,
+                                                       tma_ty(cd.ny), flags);
+        if (cudaGetLastError() != cudaSuccess) {
+          st = fail(c, FD_ECUDA, "autotune: flags kernel");
+          break;
+        }
+      }
+      double us = 0.0;
+      st = time_plan(c, r, scratch, reps, ev.data(), &us, fwi ? fbuf : nullptr,
+                     sk ? flags : nullptr);
+      if (st) break;
+      fd_tile_config cfg{kTmaTX, tma_ty(cd.ny), r.args.zblock, r.per_sm, cd.aligned, sk, us};
+      if (tried && n < max_tried) tried[n] = cfg;
+      ++n;
+      if (us < win_us) {
+        win_us = us;
+        win = cfg;
+      }
     }
   }
+  dfree(c, flags);
   for (auto &e : ev)
     if (e) cudaEventDestroy(e);
   dfree(c, scratch);
@@ -1391,7 +1444,7 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
   if (err[0]) return fail(c, FD_ETIMEOUT, "autotune: pipelined kernel wait expired (code %d)", err[0]);
   if (n == 0) return fail(c, FD_EUNSUPPORTED, "autotune: no tile configuration could be planned");
   if (ntried) *ntried = n;
-  st = replan(c, win.tile_y / kTmaNW, win.ctas_per_sm, win.zblock, win.aligned);
+  st = replan(c, win.tile_y / kTmaNW, win.ctas_per_sm, win.zblock, win.aligned, win.skip_c);
   if (st) return st;
   c->tune_us = win.us_per_step;
   if (best) *best = win;

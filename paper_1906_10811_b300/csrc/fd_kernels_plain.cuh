@@ -275,6 +275,24 @@ __global__ void k_interp_batch(const int2 *__restrict__ e, int n, const MemberDe
 
 namespace fdk {
 
+// Tile-planes of the pipelined kernel on which C = (m-σ)/(m+σ) is exactly 1
+// (σ = 0 at every point: no damping there): flags[tile·n0 + z] = 1.  The kernel
+// then skips the C tile and uses 1, which is the value it would have read.
+// One block per tile-plane (tile tx × ty points).
+__global__ void k_unit_c(const float *__restrict__ C, Geom g, int tiles_x, int tx, int ty,
+                         unsigned char *__restrict__ flags) {
+  const int64_t tp = blockIdx.x;  // tile * n0 + z
+  const int z = (int)(tp % g.n0), tile = (int)(tp / g.n0);
+  const int x0 = (tile % tiles_x) * tx, y0 = (tile / tiles_x) * ty;
+  int ok = 1;
+  for (int i = threadIdx.x; i < tx * ty; i += blockDim.x) {
+    const int x = x0 + i % tx, y = y0 + i / tx;
+    if (x < g.n2 && y < g.n1 && C[gidx(g, z, y, x)] != 1.f) ok = 0;
+  }
+  ok = __syncthreads_and(ok);
+  if (threadIdx.x == 0) flags[tp] = (unsigned char)ok;
+}
+
 // Odd-reflection boundary (diffusion): before a step, every halo cell at
 // distance k = 1..R beyond a boundary node along one axis takes the negated
 // value at distance k inside it, u(-k) = -u(k), u(n-1+k) = -u(n-1-k).  Only

@@ -203,6 +203,8 @@ struct TmaArgs {
   float *out;        // u^{n+1} (padded layout; the buffer that held u^{n-1})
   int *err;          // err[0] = code, err[1] = block
   SparseArgs sp;
+  const unsigned char *unit_c;  // [ntiles * n0]: 1 where C = 1 on the whole tile-plane (or null;
+                                // used up to radius 4)
   // FWI epilogue (instances with FWI = true; padded layout, interior points):
   float *d2;           // if set: u^{n+1} - 2u^n + u^{n-1} of this step
   float *img;          // if set: img += img_scale * u^{n+1} * img_d2 (imaging condition)
@@ -341,6 +343,9 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
   constexpr int QL = U == Q ? Q : Q + U - 1;               // queue registers per row
   constexpr bool kSplit = R > 4;                           // two accumulation chains
   static_assert(NY % 2 == 0, "rows are updated in pairs (packed FP32x2 arithmetic)");
+  // skipping the C tile where C = 1 pays on one shot up to radius 4; above, and in
+  // the batched kernel, the extra live registers cost more than the bytes saved
+  constexpr bool kUnitC = EQ == kAcoustic && !MULTI && R <= 4;
   constexpr int DX = tma_dx(FWI), XN = tma_xn(FWI);        // ring X slots, tiles per slot
   const bool img = FWI && args.img != nullptr;             // imaging inputs in ring X
   constexpr bool AC = EQ == kAcoustic;
@@ -435,6 +440,8 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
         }
         const int x0 = (tile % tiles_x) * kTmaTX, y0 = (tile / tiles_x) * TY;
         const CUtensorMap *mu = &map_u, *mp = &map_p, *ma = &map_a, *mc = &map_c;
+        const unsigned char *uc_flags = kUnitC ? args.unit_c : nullptr;
+        const int n0p = args.g.n0;
         if constexpr (MULTI) {
           const ShotDesc &d = bat.shots[shot];
           const int par = d.cur0 ^ (int)(tick & 1);
@@ -453,10 +460,13 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
               break;
             }
             float *dst = ring_x + slot * XN * XT;
-            mbar_expect_tx(&full_x[slot], (img ? 5 : 3) * XT * 4);
+            // where C = 1 on the whole tile-plane its tile is not loaded
+            const bool cone = kUnitC && uc_flags && uc_flags[(int64_t)tile * n0p + zc];
+            mbar_expect_tx(&full_x[slot], ((img ? 5 : 3) - (cone ? 1 : 0)) * XT * 4);
             tma_load_3d_hint(dst, mp, x0 + kHaloX, y0 + R, zc + R, &full_x[slot], once);
             tma_load_3d_hint(dst + XT, ma, x0 + kHaloX, y0 + R, zc + R, &full_x[slot], once);
-            tma_load_3d_hint(dst + 2 * XT, mc, x0 + kHaloX, y0 + R, zc + R, &full_x[slot], once);
+            if (!cone)
+              tma_load_3d_hint(dst + 2 * XT, mc, x0 + kHaloX, y0 + R, zc + R, &full_x[slot], once);
             if (img) {
               tma_load_3d_hint(dst + 3 * XT, &map_e, x0 + kHaloX, y0 + R, zc + R, &full_x[slot],
                                once);
@@ -550,6 +560,8 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
     }
     const int x = (tile % tiles_x) * kTmaTX + lane;
     const int ybase = (tile / tiles_x) * TY + row0;
+    // tile-planes whose C tile the producer skipped (C = 1 there)
+    const unsigned char *ucf = kUnitC ? args.unit_c : nullptr;
     // which of this thread's rows it stores (diffusion: interior nodes only)
     unsigned rows_ok = 0;
 #pragma unroll
@@ -611,6 +623,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
               if (!mbar_wait(&full_x[xslot], (sx / DX) & 1)) goto timeout;
               xs = ring_x + xslot * XN * XT + row0 * kTmaTX + lane;
             }
+            const bool cone = kUnitC && ucf && ucf[(int64_t)tile * n0 + zc];
             float ycol[NY + 2 * R];  // this thread's column, rows row0-R .. row0+NY-1+R
 #pragma unroll
             for (int r = 0; r < NY + 2 * R; ++r) ycol[r] = cp[r * BW];
@@ -672,7 +685,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
                   const float up = xs[(j + i) * kTmaTX], a = xs[XT + (j + i) * kTmaTX],
-                              cc = xs[2 * XT + (j + i) * kTmaTX];
+                              cc = cone ? 1.f : xs[2 * XT + (j + i) * kTmaTX];
                   const float u = i ? uc.y : uc.x, l = i ? lap.y : lap.x;
                   val[j + i] = fmaf(a, l, fmaf(1.f + cc, u, -cc * up));
                 }
@@ -950,12 +963,14 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float 
 
 // One step with u^n in level[cur]; writes u^{n+1} into out (= level[cur ^ 1]).
 inline cudaError_t launch_tma_step(const TmaPlan &pl, int cur, float *out, const Coef &c, int *err,
-                                   const SparseArgs &sp, cudaStream_t s) {
+                                   const SparseArgs &sp, cudaStream_t s,
+                                   const unsigned char *unit_c = nullptr) {
   TmaArgs a = pl.args;
   a.c = c;
   a.out = out;
   a.err = err;
   a.sp = sp;
+  a.unit_c = unit_c;
   pl.fn<<<pl.grid, kTmaThreads, pl.smem, s>>>(pl.map_u[cur], pl.map_t[cur ^ 1], pl.map_a,
                                               pl.map_c, pl.map_c, pl.map_c, a, BatchArgs{});
   return cudaGetLastError();
@@ -964,12 +979,14 @@ inline cudaError_t launch_tma_step(const TmaPlan &pl, int cur, float *out, const
 // The same step with the FWI epilogue (plan.fn_fwi must be set).
 inline cudaError_t launch_tma_step_fwi(const TmaPlan &pl, int cur, float *out, const Coef &c,
                                        int *err, const SparseArgs &sp, float *d2, float *img,
-                                       const float *img_d2, float img_scale, cudaStream_t s) {
+                                       const float *img_d2, float img_scale, cudaStream_t s,
+                                       const unsigned char *unit_c = nullptr) {
   TmaArgs a = pl.args;
   a.c = c;
   a.out = out;
   a.err = err;
   a.sp = sp;
+  a.unit_c = unit_c;
   a.d2 = d2;
   a.img = img;
   a.img_d2 = img_d2;

@@ -172,7 +172,7 @@ def _gradient_on_stream(p, d_obs, m, k, memory_budget, stats=None, profile=False
         fwd.autotune(fwi=True, cached=True)
         t = fwd.tile_config
         adj.set_tile_config(tile_y=t["tile_y"], zblock=t["zblock"], ctas_per_sm=t["ctas_per_sm"],
-                            aligned=t["aligned"])
+                            aligned=t["aligned"], skip_c=t["skip_c"])
     try:
         fwd.set_model(mm, damp)
         fwd.set_sources(src, wav)

@@ -126,13 +126,13 @@ class Solver:
     # -- tile configuration of the pipelined 3-D kernel ----------------------
     @property
     def tile_config(self):
-        """{tile_x, tile_y, zblock, ctas_per_sm, aligned, us_per_step} of the pipelined kernel."""
+        """{tile_x, tile_y, zblock, ctas_per_sm, aligned, skip_c, us_per_step} of the pipelined kernel."""
         return B.fd_get_tile_config(self.ctx)
 
-    def set_tile_config(self, tile_y=0, zblock=0, ctas_per_sm=0, aligned=0):
+    def set_tile_config(self, tile_y=0, zblock=0, ctas_per_sm=0, aligned=0, skip_c=0):
         self._in()
         B.fd_set_tile_config(self.ctx, tile_y=tile_y, zblock=zblock, ctas_per_sm=ctas_per_sm,
-                             aligned=aligned)
+                             aligned=aligned, skip_c=skip_c)
         self._out()
 
     def autotune(self, reps=5, fwi=False, cached=False):

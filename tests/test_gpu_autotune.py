@@ -53,11 +53,14 @@ def _configs(shape, so):
         for cps in (1, 2, 3):
             for zb in (0, 3, 11, shape[0]):
                 for al in (0, 1):
-                    try:
-                        s.set_tile_config(tile_y=ty, ctas_per_sm=cps, zblock=zb, aligned=al)
-                    except FdError:
-                        continue
-                    out.append(dict(tile_y=ty, ctas_per_sm=cps, zblock=zb, aligned=al))
+                    for sk in ((0, 1) if so <= 8 else (0,)):
+                        try:
+                            s.set_tile_config(tile_y=ty, ctas_per_sm=cps, zblock=zb, aligned=al,
+                                              skip_c=sk)
+                        except FdError:
+                            continue
+                        out.append(dict(tile_y=ty, ctas_per_sm=cps, zblock=zb, aligned=al,
+                                        skip_c=sk))
     s.close()
     return out
 
@@ -72,7 +75,7 @@ def test_every_tile_configuration_is_bitwise_the_default(so, shape):
     for cfg in cfgs:
         u, up, rec, used = _acoustic(p, 60, cfg)
         assert used["tile_y"] == cfg["tile_y"] and used["ctas_per_sm"] == cfg["ctas_per_sm"]
-        assert used["aligned"] == cfg["aligned"]
+        assert used["aligned"] == cfg["aligned"] and used["skip_c"] == cfg["skip_c"]
         if cfg["zblock"]:
             assert used["zblock"] == min(cfg["zblock"], shape[0])
         assert np.array_equal(u, ref[0]), cfg
@@ -117,7 +120,8 @@ def test_autotune_picks_a_timed_configuration_and_keeps_the_solution():
     assert {t["tile_y"] for t in tried} == {16, 32}
     assert {t["aligned"] for t in tried} == {0, 1}
     assert all(t["us_per_step"] > 0 for t in tried)
-    key = lambda t: (t["tile_y"], t["zblock"], t["ctas_per_sm"], t["aligned"])
+    key = lambda t: (t["tile_y"], t["zblock"], t["ctas_per_sm"], t["aligned"], t["skip_c"])
+    assert {t["skip_c"] for t in tried} == {0, 1}
     assert key(best) in {key(t) for t in tried}
     assert best["us_per_step"] == min(t["us_per_step"] for t in tried)
     cur = s.tile_config
@@ -143,7 +147,7 @@ def test_bad_tile_configurations_are_rejected_and_keep_the_current_one():
     s = Solver((20, 24, 28), (10.0,) * 3, 8, 0.1, "acoustic", kernel="tma")
     before = s.tile_config
     for bad in (dict(tile_y=24), dict(tile_y=64), dict(zblock=-1), dict(ctas_per_sm=-2),
-                dict(ctas_per_sm=64), dict(aligned=2)):
+                dict(ctas_per_sm=64), dict(aligned=2), dict(skip_c=3)):
         with pytest.raises(FdError) as e:
             s.set_tile_config(**bad)
         assert e.value.status == FD_EINVAL
@@ -185,7 +189,7 @@ def test_fwi_autotune_times_the_sweep_kernels_and_caches():
     s.set_model(p["m"], p["damp"])
     best, tried = s.autotune(reps=2, fwi=True)
     assert len(tried) >= 4 and all(t["us_per_step"] > 0 for t in tried)
-    key = lambda t: (t["tile_y"], t["zblock"], t["ctas_per_sm"], t["aligned"])
+    key = lambda t: (t["tile_y"], t["zblock"], t["ctas_per_sm"], t["aligned"], t["skip_c"])
     assert key(best) in {key(t) for t in tried}
     assert best["us_per_step"] == min(t["us_per_step"] for t in tried)
     s2 = Solver(p["shape"], p["spacing"], 8, p["dt"], "acoustic", kernel="tma")
