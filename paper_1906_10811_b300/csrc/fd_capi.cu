@@ -573,13 +573,13 @@ fd_status prepare_unit_c(fd_ctx *c) {
   if (!c->use_tma || !c->skip_c || !c->unit_c_dirty) return FD_OK;
   const size_t n = (size_t)c->tma.args.ntiles * c->g.n0;
   if (n > c->unit_c_cap) {
+    drop_graphs(c);  // the captured launches hold the flags pointer
     dfree(c, c->unit_c);
     c->unit_c_cap = 0;
     fd_status st = dalloc(c, &c->unit_c, n);
     if (st) return st;
     c->unit_c_cap = n;
   }
-  drop_graphs(c);  // the captured launches hold the flags pointer
   k_unit_c<<<(unsigned)n, 128, 0, c->stream>>>(c->C, c->g, c->tma.args.tiles_x, kTmaTX,
                                                tma_ty(c->tma.ny), c->unit_c);
   CHECK_LAUNCH();
