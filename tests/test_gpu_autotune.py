@@ -198,3 +198,16 @@ def test_fwi_autotune_times_the_sweep_kernels_and_caches():
     assert key(s2.tile_config) == key(best)
     s.close()
     s2.close()
+
+
+def test_skipping_c_is_bitwise_on_a_grid_with_a_real_damping_layer():
+    """160³, 40-point layer: about a fifth of the tile-planes are undamped; the step with
+    their C tiles skipped is bitwise the step that reads them."""
+    import fdsynth
+    p = fdsynth.acoustic_problem(n=160, so=8, nbl=40, nt=40, nrec=32, seed=5)
+    ref = _acoustic(p, 40, dict(tile_y=32, aligned=1, skip_c=0))
+    got = _acoustic(p, 40, dict(tile_y=32, aligned=1, skip_c=1))
+    assert got[3]["skip_c"] == 1
+    for a, b in zip(got[:3], ref[:3]):
+        assert np.array_equal(a, b)
+    assert np.abs(ref[2]).max() > 0
