@@ -256,7 +256,7 @@ fd_status fd_field_to_dense(fd_ctx *ctx, const float *padded, float *dense);
  * fd_autotune: time every configuration of the search space (tile_y in
  *   {16, 32} × ctas_per_sm in 1..fit × (aligned 0 with zblock in {share/2,
  *   share, 2·share} | aligned 1 with m or 2m z-blocks, m = CTAs / tiles)
- *   × skip_c {0, 1} where it applies,
+ *   × skip_c {0, 1} where it applies (once a model is set),
  *   reps ≥ 1 timed launches each after two warm-up launches, median taken),
  *   then use the fastest.  The candidate launches read the current fields
  *   and write a scratch field allocated for the call, so the solution is not

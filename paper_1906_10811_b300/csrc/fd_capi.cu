@@ -1390,8 +1390,9 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
       }
     }
   }
-  // each candidate once more skipping the C tiles where C = 1 (acoustic, R <= 4)
-  const bool try_skip = c->eq == FD_ACOUSTIC && R <= 4;
+  // each candidate once more skipping the C tiles where C = 1 (acoustic, R <= 4;
+  // only with a model set: before it C is 0 everywhere and nothing would be skipped)
+  const bool try_skip = c->eq == FD_ACOUSTIC && R <= 4 && c->model_set;
   unsigned char *flags = nullptr;
   if (!st && try_skip) st = dalloc(c, &flags, (size_t)c->tma.args.ntiles * c->g.n0 * 2 + 64);
   fd_tile_config win{};

@@ -167,14 +167,15 @@ def _gradient_on_stream(p, d_obs, m, k, memory_budget, stats=None, profile=False
 
     fwd = Solver(p["shape"], p["spacing"], p["so"], dt, "acoustic", device=True, profile=profile)
     adj = Solver(p["shape"], p["spacing"], p["so"], dt, "acoustic", device=True, profile=profile)
-    if fwd.kernel_name == "stencil3d_tma_acoustic":
-        # both contexts take the tile timed on the sweep's own kernels (cached per grid)
-        fwd.autotune(fwi=True, cached=True)
-        t = fwd.tile_config
-        adj.set_tile_config(tile_y=t["tile_y"], zblock=t["zblock"], ctas_per_sm=t["ctas_per_sm"],
-                            aligned=t["aligned"], skip_c=t["skip_c"])
     try:
         fwd.set_model(mm, damp)
+        if fwd.kernel_name == "stencil3d_tma_acoustic":
+            # both contexts take the tile timed on the sweep's own kernels (cached per grid)
+            fwd.autotune(fwi=True, cached=True)
+            t = fwd.tile_config
+            adj.set_tile_config(tile_y=t["tile_y"], zblock=t["zblock"],
+                                ctas_per_sm=t["ctas_per_sm"], aligned=t["aligned"],
+                                skip_c=t["skip_c"])
         fwd.set_sources(src, wav)
         fwd.set_receivers(rc)
         elems = B.fd_field_elems(fwd.ctx)
