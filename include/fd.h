@@ -62,7 +62,7 @@ typedef enum {
   FD_ECUDA = 3,        /* CUDA error; the context is failed from now on */
   FD_ESTATE = 4,       /* call out of order (e.g. fd_run before fd_set_model) */
   FD_ETIMEOUT = 5,     /* a kernel's bounded wait expired (reported by fd_read) */
-  FD_EUNSUPPORTED = 6  /* valid request this build does not provide */
+  FD_EUNSUPPORTED = 6  /* valid request the library does not provide */
 } fd_status;
 
 typedef enum { FD_DIFFUSION = 0, FD_ACOUSTIC = 1 } fd_equation;
@@ -172,8 +172,8 @@ int64_t fd_steps_done(const fd_ctx *ctx);
 fd_status fd_profile(fd_ctx *ctx, int64_t *launches, double *stencil_ms);
 
 /*
- * Full-waveform-inversion support (the spec differentiation pattern on
- * the §6.2.1 operator).  Device fields in the library's padded layout:
+ * Full-waveform-inversion support (gradient of a shot's misfit with
+ * respect to m for the §6.2.1 operator).  Device fields in the library's padded layout:
  * fd_field_elems floats each (zero halo included), device pointers.
  *
  * fd_snapshot: copy the current level u^n and the previous level u^{n-1} of
@@ -303,7 +303,7 @@ void fd_destroy(fd_ctx *ctx);
 /*
  * Batches: many FD_ACOUSTIC shots of one space order stepped together, as a
  * serving loop that admits and retires shots between runs needs (continuous
- * batching; the spec serving pattern built on the §6.2.1 operator).
+ * batching, built on the §6.2.1 operator).
  * A batch tick advances every member one step with one persistent pipelined
  * kernel for all 3-D members (their tile-planes shared out over the CTAs), one
  * kernel for all 2-D members, one source-injection kernel for the 2-D members

@@ -1,7 +1,7 @@
 """GPU parity through the C ABI against the FP64 oracle, on sizes the oracle
 finishes in seconds that still span several tiles and ragged edges.
 
-Tolerances (spec accuracy targets, FP32 GPU vs FP64 oracle, relative
+Tolerances (the accuracy targets of the path, FP32 GPU vs FP64 oracle, relative
 L2 over all values): diffusion 1e-5, acoustic wavefield and traces 1e-4.
 Where two GPU runs must agree exactly (graphs vs eager launches, chunked runs,
 host vs device pointers, resume from a checkpoint), the comparison is bitwise:
