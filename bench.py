@@ -607,7 +607,6 @@ def run_ours(args):
     nt = p["nt"]
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     m_d, damp_d = dev(p["m"]), dev(p["damp"])
-    zeros_d = torch.zeros(p["shape"], dtype=torch.float32, device="cuda")
 
     def barrier():
         torch.cuda.synchronize()
@@ -639,8 +638,7 @@ def run_ours(args):
 
     def shot():
         s.set_model(m_d, damp_d)
-        s.set_field(zeros_d)
-        s.set_step(0)
+        s.reset()
         s.run(nt)
 
     for _ in range(args.warmup):
@@ -685,10 +683,10 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
-        m_h, damp_h, zero_h = pin(p["m"]), pin(p["damp"]), pin(np.zeros(p["shape"], np.float32))
+        m_h, damp_h = pin(p["m"]), pin(p["damp"])
         src_h, wav_h, rc_h = pin(p["src_coords"]), pin(p["wavelet"]), pin(p["rec_coords"])
         rec_out = torch.empty((nt + 1, max(w["nrec"], 1)), dtype=torch.float32).pin_memory().numpy()
-        h2d = m_h.nbytes + damp_h.nbytes + zero_h.nbytes + src_h.nbytes + wav_h.nbytes + rc_h.nbytes
+        h2d = m_h.nbytes + damp_h.nbytes + src_h.nbytes + wav_h.nbytes + rc_h.nbytes
         d2h = (nt + 1) * w["nrec"] * 4
         se = Solver(p["shape"], p["spacing"], p["so"], p["dt"], "acoustic", device=False,
                     kernel=args.kernel, autotune=tile is not None and args.tile == "auto")
@@ -703,8 +701,7 @@ def run_ours(args):
             se.set_sources(src_h, wav_h)
             if w["nrec"]:
                 se.set_receivers(rc_h)
-            se.set_field(zero_h)
-            se.set_step(0)
+            se.reset()  # the shot starts from rest
             se.run(nt)
             B.fd_read(se.ctx, None, rec_out if w["nrec"] else None)
 

@@ -124,13 +124,24 @@ fd_status fd_set_model(fd_ctx *ctx, const float *m, const float *damp);
  * Set the current time level(s).  FD_ACOUSTIC: u_cur = u^n, u_prev = u^{n-1}
  * (NULL: equal to u_cur).  FD_DIFFUSION: u_cur only (u_prev ignored); the
  * boundary values given here are held.  Does not change the step counter.
+ * With u_prev NULL (or equal to u_cur) the field is uploaded once for both levels.
  */
 fd_status fd_set_field(fd_ctx *ctx, const float *u_cur, const float *u_prev);
+
+/*
+ * Start over from rest without uploading a field: u^n = u^{n-1} = 0 on every
+ * node (boundary values 0 for FD_DIFFUSION), step counter 0, recorded traces
+ * cleared (the next fd_run records row 0 afresh).  Model, sources, receivers
+ * and the tile configuration stay.  Asynchronous on the context stream.
+ */
+fd_status fd_reset(fd_ctx *ctx);
 
 /*
  * FD_ACOUSTIC: nsrc point sources at coords [nsrc][ndim] with wavelets
  * [nt][nsrc] (row n = s(t_n) for global step n).  Replaces earlier sources;
  * nsrc = 0 removes them.  fd_run fails with FD_EINVAL if it would pass step nt.
+ * With the same nsrc and nt as before, the device buffers are refilled in place
+ * and the captured step graphs are kept (a survey's next shot).
  */
 fd_status fd_set_sources(fd_ctx *ctx, int nsrc, const float *coords, int nt,
                          const float *wavelets);
@@ -139,7 +150,8 @@ fd_status fd_set_sources(fd_ctx *ctx, int nsrc, const float *coords, int nt,
  * FD_ACOUSTIC: nrec receivers at coords [nrec][ndim].  Traces are recorded
  * for every step run afterwards: row 0 = interpolation of u at step 0, row
  * n+1 after step n (the library grows the trace buffer as needed).
- * Replaces earlier receivers and clears recorded traces.
+ * Replaces earlier receivers and clears recorded traces; with the same nrec
+ * as before the device buffers (and the captured step graphs) are kept.
  */
 fd_status fd_set_receivers(fd_ctx *ctx, int nrec, const float *coords);
 

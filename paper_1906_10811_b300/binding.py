@@ -65,6 +65,7 @@ SIGNATURES = {
     "fd_read": (ctypes.c_int, [_vp, _vp, _vp]),
     "fd_read_prev": (ctypes.c_int, [_vp, _vp]),
     "fd_set_step": (ctypes.c_int, [_vp, _i64]),
+    "fd_reset": (ctypes.c_int, [_vp]),
     "fd_steps_done": (_i64, [_vp]),
     "fd_profile": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double)]),
     "fd_kernel_name": (ctypes.c_char_p, [_vp]),
@@ -230,6 +231,10 @@ def fd_read_prev(ctx, u_prev):
 
 def fd_set_step(ctx, n):
     _check(ctx, load().fd_set_step(ctx, int(n)))
+
+
+def fd_reset(ctx):
+    _check(ctx, load().fd_reset(ctx))
 
 
 def fd_steps_done(ctx):

@@ -126,6 +126,7 @@ struct fd_ctx {
   std::vector<int64_t> h_src_dense;  // source corner nodes (dense index)
   int4 *sp_entries = nullptr;
   int *sp_first = nullptr;
+  size_t sp_entries_n = 0, sp_first_n = 0;  // their lengths
   bool sp_dirty = true;
   // tile-planes of the pipelined kernel where C = 1 (no damping): their C tile is skipped
   unsigned char *unit_c = nullptr;
@@ -241,7 +242,9 @@ int blocks_for(int64_t n, int threads) {
 }
 
 // Scatter a dense interior array (host or device) into a padded field.
-fd_status load_field(fd_ctx *c, float *padded, const float *user) {
+// User field -> padded level(s): one upload, scattered into `padded` and, if
+// given, into `padded2` as well.
+fd_status load_field(fd_ctx *c, float *padded, const float *user, float *padded2 = nullptr) {
   const size_t n = (size_t)c->g.n0 * c->g.n1 * c->g.n2;
   const float *src = user;
   if (!c->opt.device_ptrs) {
@@ -250,6 +253,10 @@ fd_status load_field(fd_ctx *c, float *padded, const float *user) {
   }
   k_scatter<<<blocks_for(n, 256), 256, 0, c->stream>>>(src, padded, c->g);
   CHECK_LAUNCH();
+  if (padded2) {
+    k_scatter<<<blocks_for(n, 256), 256, 0, c->stream>>>(src, padded2, c->g);
+    CHECK_LAUNCH();
+  }
   return FD_OK;
 }
 
@@ -548,13 +555,21 @@ fd_status prepare_fused(fd_ctx *c) {
     std::vector<int4> ent(es.size());
     for (size_t i = 0; i < es.size(); ++i) ent[i] = make_int4(es[i].x, es[i].y, es[i].z, es[i].idx);
     CU(cudaStreamSynchronize(c->stream));
-    dfree(c, c->sp_entries);
-    dfree(c, c->sp_first);
-    drop_graphs(c);
+    const size_t nfirst = es.empty() ? 0 : first.size();
+    if (ent.size() != c->sp_entries_n || nfirst != c->sp_first_n) {
+      dfree(c, c->sp_entries);
+      dfree(c, c->sp_first);
+      c->sp_entries_n = c->sp_first_n = 0;
+      drop_graphs(c);
+      if (!es.empty()) {
+        fd_status st = dalloc(c, &c->sp_entries, ent.size());
+        if (!st) st = dalloc(c, &c->sp_first, first.size());
+        if (st) return st;
+        c->sp_entries_n = ent.size();
+        c->sp_first_n = first.size();
+      }
+    }
     if (!es.empty()) {
-      fd_status st = dalloc(c, &c->sp_entries, ent.size());
-      if (!st) st = dalloc(c, &c->sp_first, first.size());
-      if (st) return st;
       CU(cudaMemcpyAsync(c->sp_entries, ent.data(), ent.size() * sizeof(int4),
                          cudaMemcpyHostToDevice, c->stream));
       CU(cudaMemcpyAsync(c->sp_first, first.data(), first.size() * sizeof(int),
@@ -917,14 +932,26 @@ fd_status fd_set_field(fd_ctx *c, const float *u_cur, const float *u_prev) {
   fd_status st = check_usable(c);
   if (st) return st;
   if (!u_cur) return fail(c, FD_EINVAL, "u_cur is NULL");
-  if (c->eq == FD_DIFFUSION) {
-    st = load_field(c, c->u[c->cur], u_cur);
-    if (!st) st = load_field(c, c->u[c->cur ^ 1], u_cur);  // boundary values in both levels
-    return st;
-  }
+  // diffusion: the boundary values go to both levels
+  if (c->eq == FD_DIFFUSION || !u_prev || u_prev == u_cur)
+    return load_field(c, c->u[c->cur], u_cur, c->u[c->cur ^ 1]);
   st = load_field(c, c->u[c->cur], u_cur);
-  if (!st) st = load_field(c, c->u[c->cur ^ 1], u_prev ? u_prev : u_cur);
+  if (!st) st = load_field(c, c->u[c->cur ^ 1], u_prev);
   return st;
+}
+
+fd_status fd_reset(fd_ctx *c) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  const size_t bytes = (size_t)c->g.total * sizeof(float);
+  CU(cudaMemsetAsync(c->u[0], 0, bytes, c->stream));
+  CU(cudaMemsetAsync(c->u[1], 0, bytes, c->stream));
+  c->step = 0;
+  if (c->nrec > 0) {
+    if (c->rec) CU(cudaMemsetAsync(c->rec, 0, (size_t)c->rec_cap * c->nrec * sizeof(float), c->stream));
+    c->rec_rows = 0;
+  }
+  return FD_OK;
 }
 
 fd_status fd_set_sources(fd_ctx *c, int nsrc, const float *coords, int nt, const float *wavelets) {
@@ -944,17 +971,21 @@ fd_status fd_set_sources(fd_ctx *c, int nsrc, const float *coords, int nt, const
                  &w[(size_t)j * c->nc]))
       return fail(c, FD_EINVAL, "source %d lies outside the grid", j);
   CU(cudaStreamSynchronize(c->stream));
-  dfree(c, c->src_off); dfree(c, c->src_dense); dfree(c, c->src_w); dfree(c, c->src_scale); dfree(c, c->wav);
-  drop_graphs(c);
-  c->nsrc = 0;
-  c->nt_wav = 0;
-  c->h_src_dense.clear();
-  c->sp_dirty = true;
-  if (nsrc == 0) return FD_OK;
-  if ((st = dalloc(c, &c->src_off, n)) || (st = dalloc(c, &c->src_dense, n)) ||
-      (st = dalloc(c, &c->src_w, n)) || (st = dalloc(c, &c->src_scale, n)) ||
-      (st = dalloc(c, &c->wav, (size_t)nt * nsrc)))
-    return st;
+  // The same counts as before (the next shot of a survey): the buffers are
+  // refilled in place, so the captured graphs, which hold their addresses, stay.
+  if (nsrc == 0 || nsrc != c->nsrc || nt != c->nt_wav) {
+    dfree(c, c->src_off); dfree(c, c->src_dense); dfree(c, c->src_w); dfree(c, c->src_scale); dfree(c, c->wav);
+    drop_graphs(c);
+    c->nsrc = 0;
+    c->nt_wav = 0;
+    c->h_src_dense.clear();
+    c->sp_dirty = true;
+    if (nsrc == 0) return FD_OK;
+    if ((st = dalloc(c, &c->src_off, n)) || (st = dalloc(c, &c->src_dense, n)) ||
+        (st = dalloc(c, &c->src_w, n)) || (st = dalloc(c, &c->src_scale, n)) ||
+        (st = dalloc(c, &c->wav, (size_t)nt * nsrc)))
+      return st;
+  }
   CU(cudaMemcpyAsync(c->src_off, off.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
   CU(cudaMemcpyAsync(c->src_dense, dense.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
   CU(cudaMemcpyAsync(c->src_w, w.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
@@ -988,13 +1019,21 @@ fd_status fd_set_receivers(fd_ctx *c, int nrec, const float *coords) {
       return fail(c, FD_EINVAL, "receiver %d lies outside the grid", k);
   for (int i = 0; i < n; ++i) wf[i] = (float)w[i];
   CU(cudaStreamSynchronize(c->stream));
-  dfree(c, c->rec_off); dfree(c, c->rec_w); dfree(c, c->rec);
-  drop_graphs(c);
-  c->nrec = 0;
-  c->rec_cap = 0;
-  c->rec_rows = 0;
-  if (nrec == 0) return FD_OK;
-  if ((st = dalloc(c, &c->rec_off, n)) || (st = dalloc(c, &c->rec_w, n))) return st;
+  if (nrec > 0 && nrec == c->nrec) {
+    // same count: refill in place and keep the (cleared) trace buffer, so the
+    // captured graphs stay valid
+    if (c->rec)
+      CU(cudaMemsetAsync(c->rec, 0, (size_t)c->rec_cap * nrec * sizeof(float), c->stream));
+    c->rec_rows = 0;
+  } else {
+    dfree(c, c->rec_off); dfree(c, c->rec_w); dfree(c, c->rec);
+    drop_graphs(c);
+    c->nrec = 0;
+    c->rec_cap = 0;
+    c->rec_rows = 0;
+    if (nrec == 0) return FD_OK;
+    if ((st = dalloc(c, &c->rec_off, n)) || (st = dalloc(c, &c->rec_w, n))) return st;
+  }
   CU(cudaMemcpyAsync(c->rec_off, off.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
   CU(cudaMemcpyAsync(c->rec_w, wf.data(), n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
   CU(cudaStreamSynchronize(c->stream));

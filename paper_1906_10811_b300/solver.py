@@ -104,6 +104,12 @@ class Solver:
     def set_step(self, n):
         B.fd_set_step(self.ctx, n)
 
+    def reset(self):
+        """Back to rest: both levels zero, step 0, traces cleared (no upload)."""
+        self._in()
+        B.fd_reset(self.ctx)
+        self._out()
+
     # -- run / outputs -----------------------------------------------------
     def run(self, nt):
         self._in()
