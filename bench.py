@@ -696,21 +696,25 @@ def run_ours(args):
                                skip_c=tile["skip_c"])
         from paper_1906_10811_b300 import binding as B
 
-        def shot_e2e():
-            se.set_model(m_h, damp_h)
-            se.set_sources(src_h, wav_h)
-            if w["nrec"]:
-                se.set_receivers(rc_h)
-            se.reset()  # the shot starts from rest
-            se.run(nt)
+        def survey(n):
+            """n shots back to back, as a survey runs them: a shot's model upload
+            overlaps the previous shot's steps (fd_set_model with host buffers),
+            whose traces are read before the next shot's receivers replace them."""
+            for i in range(n):
+                se.set_model(m_h, damp_h)
+                if i:
+                    B.fd_read(se.ctx, None, rec_out if w["nrec"] else None)
+                se.set_sources(src_h, wav_h)
+                if w["nrec"]:
+                    se.set_receivers(rc_h)
+                se.reset()  # the shot starts from rest
+                se.run(nt)
             B.fd_read(se.ctx, None, rec_out if w["nrec"] else None)
 
-        for _ in range(args.warmup):
-            shot_e2e()
+        survey(args.warmup)
         barrier()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            shot_e2e()
+        survey(args.steps)
         barrier()
         te = time.perf_counter() - t0
         se.close()

@@ -90,8 +90,9 @@ typedef struct {
   void *cuda_stream;  /* cudaStream_t for all work; NULL: the library creates one */
   int device_ptrs;    /* 1: array arguments are device pointers (see Ownership) */
   int use_graphs;     /* 1 (default): fd_run replays captured CUDA graphs of the step loop */
-  int profile;        /* 1: time every stencil launch with CUDA events (fd_profile);
-                         steps are launched one by one instead of by graph */
+  int profile;        /* 1: time the stencil launches with CUDA events (fd_profile):
+                         each replayed graph chunk as a whole, or, with
+                         use_graphs = 0 and in fd_step_fwi, each launch */
   int kernel;         /* fd_kernel; default FD_KERNEL_AUTO */
   int autotune;       /* 1: fd_create runs fd_autotune on the pipelined kernel (its
                          choice is cached per grid shape, space order and equation
@@ -116,7 +117,11 @@ fd_status fd_create(fd_ctx **out, int ndim, const int64_t *shape,
 /*
  * FD_ACOUSTIC: squared slowness m (> 0 everywhere) and damping coefficient
  * damp (≥ 0; NULL means 0).  Rejects dt above the leapfrog limit
- * 2 / sqrt(max(1/m) · Σ_d S/h_d²) with FD_EINVAL.  May be called again.
+ * 2 / sqrt(max(1/m) · Σ_d S/h_d²) with FD_EINVAL.  May be called again,
+ * also while steps are in flight: with host pointers the upload runs on a copy
+ * stream of the context and overlaps them; the new coefficients are computed on
+ * the context stream after them (steps already queued keep the old ones).
+ * Returns once they are computed and checked.
  */
 fd_status fd_set_model(fd_ctx *ctx, const float *m, const float *damp);
 
@@ -178,8 +183,9 @@ fd_status fd_set_step(fd_ctx *ctx, int64_t n);
 int64_t fd_steps_done(const fd_ctx *ctx);
 
 /*
- * Profiling (fd_options.profile = 1): number of stencil launches and their
- * summed CUDA-event time in ms since the last call; synchronises and resets.
+ * Profiling (fd_options.profile = 1): number of stencil launches timed and
+ * their summed CUDA-event time in ms since the last call (a graph chunk's time
+ * covers its launches and the gaps between them); synchronises and resets.
  */
 fd_status fd_profile(fd_ctx *ctx, int64_t *launches, double *stencil_ms);
 

@@ -135,6 +135,11 @@ struct fd_ctx {
   bool skip_c = false;  // fd_tile_config.skip_c
   bool fused = false;                // this run uses the fused/overlapped sparse path
   cudaStream_t side = nullptr;
+  // host mode: model uploads run on their own stream, so that they overlap steps
+  // still in flight on the context stream; ev_model_free is recorded after every
+  // queued reader of m_dense and stage, ev_copied after an upload
+  cudaStream_t copy = nullptr;
+  cudaEvent_t ev_model_free = nullptr, ev_copied = nullptr;
   cudaEvent_t ev_step[2] = {nullptr, nullptr}, ev_rec[2] = {nullptr, nullptr};
   // state
   bool model_set = false;
@@ -145,6 +150,7 @@ struct fd_ctx {
   // profiling
   std::vector<cudaEvent_t> ev;
   size_t ev_used = 0;
+  std::vector<int> ev_launches;  // stencil launches between event pair i (ev[2i], ev[2i+1])
   int64_t launches = 0;  // kernels this context has launched (graph nodes included)
 };
 
@@ -242,6 +248,12 @@ int blocks_for(int64_t n, int threads) {
 }
 
 // Scatter a dense interior array (host or device) into a padded field.
+// Host mode: the work queued so far that reads m_dense or stage ends here.
+fd_status model_readers_queued(fd_ctx *c) {
+  if (c->ev_model_free) CU(cudaEventRecord(c->ev_model_free, c->stream));
+  return FD_OK;
+}
+
 // User field -> padded level(s): one upload, scattered into `padded` and, if
 // given, into `padded2` as well.
 fd_status load_field(fd_ctx *c, float *padded, const float *user, float *padded2 = nullptr) {
@@ -257,7 +269,7 @@ fd_status load_field(fd_ctx *c, float *padded, const float *user, float *padded2
     k_scatter<<<blocks_for(n, 256), 256, 0, c->stream>>>(src, padded2, c->g);
     CHECK_LAUNCH();
   }
-  return FD_OK;
+  return model_readers_queued(c);
 }
 
 fd_status store_field(fd_ctx *c, const float *padded, float *user) {
@@ -267,7 +279,7 @@ fd_status store_field(fd_ctx *c, const float *padded, float *user) {
   CHECK_LAUNCH();
   if (!c->opt.device_ptrs)
     CU(cudaMemcpyAsync(user, c->stage, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
-  return FD_OK;
+  return model_readers_queued(c);
 }
 
 // Multilinear corners of one point (the rule documented in fd.h).
@@ -412,6 +424,24 @@ fd_status launch_receivers_side(fd_ctx *c, float *unext, int j) {
   return FD_OK;
 }
 
+// Profile mode: an event pair around a stretch of `launches` stencil launches.
+fd_status profile_mark(fd_ctx *c, bool end, int launches) {
+  if (!end && c->ev_used + 2 > c->ev.size()) {
+    for (int k = 0; k < 64; ++k) {
+      cudaEvent_t e;
+      CU(cudaEventCreate(&e));
+      c->ev.push_back(e);
+    }
+  }
+  CU(cudaEventRecord(c->ev[c->ev_used + (end ? 1 : 0)], c->stream));
+  if (end) {
+    c->ev_launches.resize(c->ev_used / 2 + 1);
+    c->ev_launches[c->ev_used / 2] = launches;
+    c->ev_used += 2;
+  }
+  return FD_OK;
+}
+
 fd_status enqueue_chunk(fd_ctx *c, int parity, int len, bool timed) {
   const bool overlap = c->fused && c->nrec > 0;
   for (int j = 0; j < len; ++j) {
@@ -427,22 +457,12 @@ fd_status enqueue_chunk(fd_ctx *c, int parity, int len, bool timed) {
           ucur, c->g);
       CHECK_LAUNCH();
     }
-    if (timed) {
-      if (c->ev_used + 2 > c->ev.size()) {
-        for (int k = 0; k < 64; ++k) {
-          cudaEvent_t e;
-          CU(cudaEventCreate(&e));
-          c->ev.push_back(e);
-        }
-      }
-      CU(cudaEventRecord(c->ev[c->ev_used], c->stream));
-    }
-    fd_status st = launch_stencil(c, ucur, unext, j);
+    fd_status st = timed ? profile_mark(c, false, 0) : FD_OK;
     if (st) return st;
-    if (timed) {
-      CU(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
-      c->ev_used += 2;
-    }
+    st = launch_stencil(c, ucur, unext, j);
+    if (st) return st;
+    st = timed ? profile_mark(c, true, 1) : FD_OK;
+    if (st) return st;
     st = overlap ? launch_receivers_side(c, unext, j) : launch_sparse(c, unext, j);
     if (st) return st;
   }
@@ -518,7 +538,7 @@ fd_status prepare_sources(fd_ctx *c) {
                                                            c->src_scale, n, c->dt);
   CHECK_LAUNCH();
   c->src_dirty = false;
-  return FD_OK;
+  return model_readers_queued(c);
 }
 
 // Pipelined path: the source corners as entries keyed by (tile, plane) of the
@@ -853,6 +873,13 @@ fd_status fd_create(fd_ctx **out, int ndim, const int64_t *shape, const double *
   }
   if (!e) e = cudaMemsetAsync(c->d_err, 0, 4 * sizeof(int), c->stream);
   if (!e) e = cudaMemsetAsync(c->d_step, 0, sizeof(int64_t), c->stream);
+  if (!e && !o.device_ptrs && eq == FD_ACOUSTIC) {
+    e = cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking);
+    if (!e) e = cudaEventCreateWithFlags(&c->ev_model_free, cudaEventDisableTiming);
+    if (!e) e = cudaEventCreateWithFlags(&c->ev_copied, cudaEventDisableTiming);
+    // the buffers were allocated and cleared on the context stream
+    if (!e) e = cudaEventRecord(c->ev_model_free, c->stream);
+  }
   if (e) {
     fail(c, FD_ECUDA, "initialisation: %s", cudaGetErrorString(e));
     return bail(FD_ECUDA);
@@ -893,21 +920,30 @@ fd_status fd_set_model(fd_ctx *c, const float *m, const float *damp) {
   if (!m) return fail(c, FD_EINVAL, "m is NULL");
   const size_t n = (size_t)c->g.n0 * c->g.n1 * c->g.n2;
   float *damp_dev = nullptr;
-  st = to_device(c, c->m_dense, m, n);
-  if (st) return st;
-  if (damp) {
-    if (c->opt.device_ptrs) {
-      damp_dev = const_cast<float *>(damp);
-    } else {
-      CU(cudaMemcpyAsync(c->stage, damp, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  if (c->opt.device_ptrs) {
+    st = to_device(c, c->m_dense, m, n);
+    if (st) return st;
+    damp_dev = const_cast<float *>(damp);
+  } else {
+    // upload on the copy stream once the queued readers of m_dense and stage
+    // have run (steps in flight do not read them); the coefficients follow in
+    // stream order, after the steps queued before this call
+    CU(cudaStreamWaitEvent(c->copy, c->ev_model_free, 0));
+    CU(cudaMemcpyAsync(c->m_dense, m, n * sizeof(float), cudaMemcpyHostToDevice, c->copy));
+    if (damp) {
+      CU(cudaMemcpyAsync(c->stage, damp, n * sizeof(float), cudaMemcpyHostToDevice, c->copy));
       damp_dev = c->stage;
     }
+    CU(cudaEventRecord(c->ev_copied, c->copy));
+    CU(cudaStreamWaitEvent(c->stream, c->ev_copied, 0));
   }
   unsigned init[2] = {0x7f800000u, 0u};
   CU(cudaMemcpyAsync(c->d_stats, init, sizeof init, cudaMemcpyHostToDevice, c->stream));
   k_coefficients<<<blocks_for(n, 256), 256, 0, c->stream>>>(c->m_dense, damp_dev, c->A, c->C,
                                                             c->g, c->dt, c->d_stats);
   CHECK_LAUNCH();
+  st = model_readers_queued(c);
+  if (st) return st;
   unsigned stats[2];
   CU(cudaMemcpyAsync(stats, c->d_stats, sizeof stats, cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
@@ -1080,12 +1116,16 @@ fd_status run_steps(fd_ctx *c, int nt, bool graphs) {
   }
   for (int done = 0; done < nt;) {
     const int len = std::min(kGraphChunk, nt - done);
-    if (graphs && c->opt.use_graphs && !c->opt.profile) {
+    if (graphs && c->opt.use_graphs) {
       cudaGraphExec_t exec;
       int64_t kernels = 0;
       st = get_graph(c, c->cur, len, &exec, &kernels);
       if (st) return st;
+      // profile mode: the replayed chunk is timed as a whole (its len stencil
+      // launches and the gaps between them)
+      if (c->opt.profile && (st = profile_mark(c, false, 0))) return st;
       CU(cudaGraphLaunch(exec, c->stream));
+      if (c->opt.profile && (st = profile_mark(c, true, len))) return st;
       c->launches += kernels;
     } else {
       st = enqueue_chunk(c, c->cur, len, c->opt.profile != 0);
@@ -1200,12 +1240,14 @@ fd_status fd_profile(fd_ctx *c, int64_t *launches, double *stencil_ms) {
   if (st) return st;
   CU(cudaStreamSynchronize(c->stream));
   double total = 0.0;
+  int64_t n = 0;
   for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
     float ms = 0.f;
     CU(cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]));
     total += ms;
+    n += c->ev_launches[i / 2];
   }
-  if (launches) *launches = (int64_t)(c->ev_used / 2);
+  if (launches) *launches = n;
   if (stencil_ms) *stencil_ms = total;
   c->ev_used = 0;
   return FD_OK;
@@ -1310,6 +1352,12 @@ void fd_destroy(fd_ctx *c) {
     cudaStreamSynchronize(c->side);
     cudaStreamDestroy(c->side);
   }
+  if (c->copy) {
+    cudaStreamSynchronize(c->copy);
+    cudaStreamDestroy(c->copy);
+  }
+  if (c->ev_model_free) cudaEventDestroy(c->ev_model_free);
+  if (c->ev_copied) cudaEventDestroy(c->ev_copied);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }

@@ -98,3 +98,28 @@ def test_reset_diffusion_zero_field():
         s.run(2)
         u, _ = s.read()
     assert not u.any()
+
+
+@pytest.mark.parametrize("shape", [(34, 31, 40), (90, 77)])
+def test_model_upload_overlapping_a_run(shape):
+    """fd_set_model while a shot's steps are in flight: they finish with the old
+    coefficients, and the next shot runs on the new model."""
+    from paper_1906_10811_b300 import Solver
+    nt = 90
+    a = small_problem(shape, 8, nt, nrec=6, seed=21)
+    b = small_problem(shape, 8, nt, nrec=6, seed=22)
+    assert not np.array_equal(a["m"], b["m"])
+    ref_a, ref_b = _fresh(a, nt), _fresh(b, nt)
+    with Solver(a["shape"], a["spacing"], 8, a["dt"], "acoustic") as s:
+        _load(s, a)
+        s.reset()
+        s.run(nt)                      # queued; not waited for
+        s.set_model(b["m"], b["damp"])
+        u, rec = s.read()
+        assert np.array_equal(u, ref_a[0]) and np.array_equal(rec, ref_a[1])
+        s.set_sources(b["src_coords"], b["wavelet"])
+        s.set_receivers(b["rec_coords"])
+        s.reset()
+        s.run(nt)
+        u, rec = s.read()
+        assert np.array_equal(u, ref_b[0]) and np.array_equal(rec, ref_b[1])
