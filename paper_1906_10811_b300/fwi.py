@@ -15,7 +15,9 @@ w·dt²/m equals a·w), and
 accumulated by the library's imaging-condition kernel (fd_imaging).  The
 forward wavefield is needed backwards in time: it is checkpointed every k
 steps (fd_snapshot) and each block of k steps is recomputed from its
-checkpoint while the adjoint sweeps it.  ``choose_checkpoint_interval`` picks
+checkpoint while the adjoint sweeps it; on the pipelined kernel the forward
+sweep writes the last block's second differences itself, so that block is not
+recomputed (and with k = nt nothing is).  ``choose_checkpoint_interval`` picks
 the largest k the device memory allows; ``tune_checkpoint_interval`` times
 the candidates and keeps the fastest (the least memory among near-ties).  Every arithmetic step runs in CUDA
 kernels; this module orders them.
@@ -46,6 +48,15 @@ def choose_checkpoint_interval(nt, field_bytes, budget_bytes):
     return best
 
 
+def blocks(nt, k):
+    """Checkpoint blocks [(n0, n1)] of at most k steps: the short one first, so that
+    the last block, whose second differences the forward sweep writes itself (no
+    recompute), is a full k steps."""
+    nblk = math.ceil(nt / k)
+    starts = [max(0, nt - (nblk - c) * k) for c in range(nblk)]
+    return list(zip(starts, starts[1:] + [nt]))
+
+
 def checkpoint_memory(nt, k, field_bytes):
     """Device bytes of checkpoint-every-k: 2·ceil(nt/k) checkpoint levels + k+2 block levels."""
     return (k + 2 + 2 * math.ceil(nt / k)) * field_bytes
@@ -63,9 +74,12 @@ def checkpoint_candidates(nt, field_bytes, budget_bytes):
 def tune_checkpoint_interval(p, d_obs, m=None, candidates=None, memory_budget=None, tol=0.03):
     """Pick the checkpoint interval by timing one gradient per candidate.
 
-    The recompute work is one forward pass whatever k is, so the times are
-    close; the fastest k wins, except that a candidate within ``tol`` of it
-    that holds less memory is preferred.  Returns (k, [(k, seconds, bytes)]).
+    Every block but the last is recomputed (nt minus the last block's steps),
+    so larger k recompute less but hold more memory; the fastest k wins, except
+    that a candidate within ``tol`` of it that holds less memory is preferred.
+    Each candidate's time includes mapping its buffers (one gradient from a
+    clean allocator): at 320³ × 1000 steps the candidates above ~80 GB were
+    slower even on repeated gradients.  Returns (k, [(k, seconds, bytes)]).
     """
     torch = _dev()
     nt = p["nt"]
@@ -185,12 +199,22 @@ def _gradient_on_stream(p, d_obs, m, k, memory_budget, stats=None, profile=False
                 memory_budget = int(0.6 * free)
             k = choose_checkpoint_interval(nt, elems * 4, memory_budget)
         k = max(1, min(int(k), nt))
-        nblk = math.ceil(nt / k)
+        blk_range = blocks(nt, k)
+        nblk = len(blk_range)
+        if fused is None:
+            fused = len(p["shape"]) == 3 and fwd.kernel_name == "stencil3d_tma_acoustic"
         ck = torch.empty((nblk, 2, elems), dtype=torch.float32, device="cuda")
-        # forward sweep with checkpoints (u^{ck}, u^{ck-1}) at the start of each block
-        for c in range(nblk):
+        # fused: the second differences of one block, u^{n+1} − 2u^n + u^{n−1}
+        blk = torch.empty((k, elems), dtype=torch.float32, device="cuda") if fused else None
+        # forward sweep with checkpoints (u^{ck}, u^{ck-1}) at the start of each block;
+        # fused, the last block's steps also write its second differences
+        for c, (n0, n1) in enumerate(blk_range):
             B.fd_snapshot(fwd.ctx, ck[c, 0], ck[c, 1])
-            fwd.run(min(k, nt - c * k))
+            if fused and c == nblk - 1:
+                for t in range(n0, n1):
+                    B.fd_step_fwi(fwd.ctx, d2_out=blk[t - n0])
+            else:
+                fwd.run(n1 - n0)
         _, rec = fwd.read(field=False)
         r = rec - d_obs
         J = 0.5 * float(torch.sum(r.double() * r.double()))
@@ -199,26 +223,24 @@ def _gradient_on_stream(p, d_obs, m, k, memory_budget, stats=None, profile=False
         adj.set_sources(rc, torch.flip(r[1:], dims=(0,)).contiguous())
         B.fd_set_receivers(fwd.ctx, 0, None)
         scale = -1.0 / (dt * dt)
-        if fused is None:
-            fused = len(p["shape"]) == 3 and fwd.kernel_name == "stencil3d_tma_acoustic"
         if fused:
             # the recompute writes u^{n+1} − 2u^n + u^{n−1} from its own epilogue and
             # the adjoint step accumulates the imaging condition from its epilogue
             g = torch.empty(p["shape"], dtype=torch.float32, device="cuda")
             gp = torch.zeros(elems, dtype=torch.float32, device="cuda")
-            blk = torch.empty((k, elems), dtype=torch.float32, device="cuda")
             for c in range(nblk - 1, -1, -1):
-                n0, n1 = c * k, min((c + 1) * k, nt)
-                B.fd_restore(fwd.ctx, ck[c, 0], ck[c, 1])
-                fwd.set_step(n0)
-                for t in range(n0, n1):
-                    B.fd_step_fwi(fwd.ctx, d2_out=blk[t - n0])
+                n0, n1 = blk_range[c]
+                if c < nblk - 1:   # the last block's differences are in blk already
+                    B.fd_restore(fwd.ctx, ck[c, 0], ck[c, 1])
+                    fwd.set_step(n0)
+                    for t in range(n0, n1):
+                        B.fd_step_fwi(fwd.ctx, d2_out=blk[t - n0])
                 for n in range(n1 - 1, n0 - 1, -1):   # adjoint step nt-1-n gives ν^{n+1}
                     B.fd_step_fwi(adj.ctx, img_g=gp, img_d2=blk[n - n0], scale=scale)
             B.fd_field_to_dense(fwd.ctx, gp, g)
             blk_bytes = int(blk.numel() + gp.numel()) * 4
         else:
-            g, blk_bytes = _backward_unfused(p, fwd, adj, ck, k, nblk, elems, scale)
+            g, blk_bytes = _backward_unfused(p, fwd, adj, ck, k, blk_range, elems, scale)
         if stats is not None:
             stats.update(k=k, checkpoint_bytes=int(ck.numel()) * 4, block_bytes=blk_bytes,
                          fused=bool(fused),
@@ -236,14 +258,13 @@ def _gradient_on_stream(p, d_obs, m, k, memory_budget, stats=None, profile=False
         adj.close()
 
 
-def _backward_unfused(p, fwd, adj, ck, k, nblk, elems, scale):
+def _backward_unfused(p, fwd, adj, ck, k, blk_range, elems, scale):
     """Backward sweep with separate kernels: recompute + snapshot, adjoint step, imaging."""
     torch = _dev()
-    nt = p["nt"]
     g = torch.zeros(p["shape"], dtype=torch.float32, device="cuda")
     blk = torch.empty((k + 2, elems), dtype=torch.float32, device="cuda")
-    for c in range(nblk - 1, -1, -1):
-        n0, n1 = c * k, min((c + 1) * k, nt)
+    for c in range(len(blk_range) - 1, -1, -1):
+        n0, n1 = blk_range[c]
         # recompute u^{n0-1} .. u^{n1} into blk[0 .. n1-n0+1]
         B.fd_restore(fwd.ctx, ck[c, 0], ck[c, 1])
         fwd.set_step(n0)
