@@ -247,15 +247,14 @@ int blocks_for(int64_t n, int threads) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, 148 * 32));
 }
 
-// Scatter a dense interior array (host or device) into a padded field.
 // Host mode: the work queued so far that reads m_dense or stage ends here.
 fd_status model_readers_queued(fd_ctx *c) {
   if (c->ev_model_free) CU(cudaEventRecord(c->ev_model_free, c->stream));
   return FD_OK;
 }
 
-// User field -> padded level(s): one upload, scattered into `padded` and, if
-// given, into `padded2` as well.
+// Scatter a dense interior array (host or device) into a padded field: one
+// upload, scattered into `padded` and, if given, into `padded2` as well.
 fd_status load_field(fd_ctx *c, float *padded, const float *user, float *padded2 = nullptr) {
   const size_t n = (size_t)c->g.n0 * c->g.n1 * c->g.n2;
   const float *src = user;
