@@ -628,6 +628,17 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
 #pragma unroll
             for (int r = 0; r < NY + 2 * R; ++r) ycol[r] = cp[r * BW];
             float val[NY];
+            // y-neighbours at ±k of the row pair (j, j+1).  Where R + j + k is even
+            // the operands are the column's aligned register pairs and one packed
+            // add sums them; otherwise they straddle two pairs and two scalar adds
+            // (the same round-to-nearest results) avoid moving them into pairs.
+            auto ysum = [&](int j, int k) -> float2 {
+              if (((R + j + k) & 1) == 0)
+                return __fadd2_rn(make_float2(ycol[R + j + k], ycol[R + j + 1 + k]),
+                                  make_float2(ycol[R + j - k], ycol[R + j + 1 - k]));
+              return make_float2(__fadd_rn(ycol[R + j + k], ycol[R + j - k]),
+                                 __fadd_rn(ycol[R + j + 1 + k], ycol[R + j + 1 - k]));
+            };
 #pragma unroll
             for (int h = 0; h < NY / 2; ++h) {
               // rows j and j+1 in packed FP32x2 arithmetic (each lane the scalar
@@ -642,8 +653,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
                 for (int k = 1; k <= R; ++k) {
                   const float2 sx =
                       __fadd2_rn(make_float2(r0[k], r1[k]), make_float2(r0[-k], r1[-k]));
-                  const float2 sy = __fadd2_rn(make_float2(ycol[R + j + k], ycol[R + j + 1 + k]),
-                                               make_float2(ycol[R + j - k], ycol[R + j + 1 - k]));
+                  const float2 sy = ysum(j, k);
                   const float2 sz = __fadd2_rn(qp[h][tma_qslot<U, Q>(ph, R + k)],
                                                qp[h][tma_qslot<U, Q>(ph, R - k)]);
                   const float2 dd = __fadd2_rn(__fadd2_rn(__fadd2_rn(sx, sy), sz), nuc6);
@@ -665,9 +675,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
                       acc);
                   acc = __ffma2_rn(
                       weight(1, k),
-                      __fadd2_rn(__fadd2_rn(make_float2(ycol[R + j + k], ycol[R + j + 1 + k]),
-                                            make_float2(ycol[R + j - k], ycol[R + j + 1 - k])),
-                                 nuc2),
+                      __fadd2_rn(ysum(j, k), nuc2),
                       acc);
                   acc = __ffma2_rn(weight(0, k),
                                    __fadd2_rn(__fadd2_rn(qp[h][tma_qslot<U, Q>(ph, R + k)],
