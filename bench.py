@@ -58,12 +58,12 @@ WORKLOADS = {
 # are summarised in profiles/.  Absent (null) when not captured for the kernel
 # and tile configuration as they are now.
 NCU_TRAFFIC = {
-    # profiles/stencil3d_tma_acoustic256_so8.md: mean of 3 launches, read 298.53 MB + write 27.46 MB
-    ("stencil3d_tma_acoustic", "acoustic256", 8, 32, 64, 2, 1, 0): 325.98e6,
-    # same file, C skipped where it is 1: mean of 3 launches, read 287.03 MB + write 26.60 MB
-    ("stencil3d_tma_acoustic", "acoustic256", 8, 32, 64, 2, 1, 1): 313.63e6,
-    # profiles/stencil3d_tma_roofline512.md: mean of 2 launches, read 1996.40 MB + write 497.32 MB
-    ("stencil3d_tma_acoustic", "roofline512", 8, 32, 512, 2, 1, 1): 2493.71e6,
+    # profiles/stencil3d_tma_acoustic256_so8.md: mean of 3 launches, read 298.56 MB + write 26.53 MB
+    ("stencil3d_tma_acoustic", "acoustic256", 8, 32, 64, 2, 1, 0): 325.08e6,
+    # same file, C skipped where it is 1: mean of 3 launches, read 287.03 MB + write 26.52 MB
+    ("stencil3d_tma_acoustic", "acoustic256", 8, 32, 64, 2, 1, 1): 313.55e6,
+    # profiles/stencil3d_tma_roofline512.md: mean of 2 launches, read 1996.73 MB + write 496.41 MB
+    ("stencil3d_tma_acoustic", "roofline512", 8, 32, 512, 2, 1, 1): 2493.14e6,
 }
 
 
