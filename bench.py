@@ -543,7 +543,7 @@ def run_diffusion(args):
         if tile is not None:
             se.set_tile_config(tile_y=tile["tile_y"], zblock=tile["zblock"],
                                ctas_per_sm=tile["ctas_per_sm"], aligned=tile["aligned"],
-                               skip_c=tile["skip_c"])
+                               skip_c=tile["skip_c"], tile_x=tile["tile_x"])
         from paper_1906_10811_b300 import binding as B
 
         def sweep_e2e():
@@ -700,7 +700,7 @@ def run_ours(args):
         if tile is not None and args.tile not in ("auto", "default"):
             se.set_tile_config(tile_y=tile["tile_y"], zblock=tile["zblock"],
                                ctas_per_sm=tile["ctas_per_sm"], aligned=tile["aligned"],
-                               skip_c=tile["skip_c"])
+                               skip_c=tile["skip_c"], tile_x=tile["tile_x"])
         from paper_1906_10811_b300 import binding as B
 
         def survey(n):

@@ -642,11 +642,12 @@ void select_kernel(fd_ctx *c) {
 // Rebuild the pipelined kernel's plan for another tile configuration; on
 // failure the current plan stays.  Source tables are keyed by tile and the
 // captured graphs hold the old plan, so both are redone.
-fd_status replan(fd_ctx *c, int ny, int per_sm, int zblock, int aligned, int skip_c = 0) {
+fd_status replan(fd_ctx *c, int ny, int per_sm, int zblock, int aligned, int skip_c = 0,
+                 int tx = kTmaTX) {
   TmaPlan p{};
   const char *why = nullptr;
   cudaError_t e = plan_tma(p, c->g, c->eq == FD_ACOUSTIC ? kAcoustic : kDiffusion, c->iso, c->u,
-                           c->A, c->C, ny, per_sm, zblock, aligned, &why);
+                           c->A, c->C, ny, per_sm, zblock, aligned, &why, tx);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(c, e == cudaErrorInvalidValue ? FD_EINVAL : FD_EUNSUPPORTED,
@@ -663,7 +664,7 @@ fd_status replan(fd_ctx *c, int ny, int per_sm, int zblock, int aligned, int ski
 }
 
 void tile_of(const fd_ctx *c, fd_tile_config *cfg) {
-  cfg->tile_x = kTmaTX;
+  cfg->tile_x = c->tma.tx;
   cfg->tile_y = tma_ty(c->tma.ny);
   cfg->zblock = c->tma.args.zblock;
   cfg->ctas_per_sm = c->tma.per_sm;
@@ -1264,14 +1265,16 @@ fd_status fd_set_tile_config(fd_ctx *c, const fd_tile_config *cfg) {
   if (st) return st;
   if (!cfg) return fail(c, FD_EINVAL, "cfg is NULL");
   if (!c->use_tma) return fail(c, FD_EUNSUPPORTED, "the plain kernel has no tile configuration");
-  if ((cfg->tile_x != 0 && cfg->tile_x != kTmaTX) || cfg->tile_y % kTmaNW ||
+  const int tx = cfg->tile_x ? cfg->tile_x : kTmaTX;
+  if (!tma_tx_supported(tx, c->eq == FD_ACOUSTIC ? kAcoustic : kDiffusion) || cfg->tile_y % kTmaNW ||
       (cfg->tile_y != 0 && !tma_ny_supported(cfg->tile_y / kTmaNW)) || cfg->zblock < 0 ||
       cfg->ctas_per_sm < 0 || (cfg->aligned != 0 && cfg->aligned != 1) ||
       (cfg->skip_c != 0 && cfg->skip_c != 1))
     return fail(c, FD_EINVAL,
                 "tile configuration %dx%d, zblock %d, %d CTAs/SM, aligned %d, skip_c %d is not offered",
                 cfg->tile_x, cfg->tile_y, cfg->zblock, cfg->ctas_per_sm, cfg->aligned, cfg->skip_c);
-  return replan(c, cfg->tile_y / kTmaNW, cfg->ctas_per_sm, cfg->zblock, cfg->aligned, cfg->skip_c);
+  return replan(c, cfg->tile_y / kTmaNW, cfg->ctas_per_sm, cfg->zblock, cfg->aligned, cfg->skip_c,
+                tx);
 }
 
 fd_status fd_autotune(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_config *tried,
@@ -1416,7 +1419,8 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
     if (it != g_tune_cache.end() && !tried) {
       const fd_tile_config cfg = it->second;
       fd_status st =
-          replan(c, cfg.tile_y / kTmaNW, cfg.ctas_per_sm, cfg.zblock, cfg.aligned, cfg.skip_c);
+          replan(c, cfg.tile_y / kTmaNW, cfg.ctas_per_sm, cfg.zblock, cfg.aligned, cfg.skip_c,
+                 cfg.tile_x);
       if (st) return st;
       c->tune_us = cfg.us_per_step;
       if (best) *best = cfg;
@@ -1445,34 +1449,40 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
   // share/2, share, 2·share | whole segments with z-blocks that make m or 2m
   // segments per tile, m = CTAs / tiles)
   struct Cand {
-    int ny, cps, zb, aligned;
+    int ny, cps, zb, aligned, tx;
   };
   std::vector<Cand> cands;
+  // diffusion also tries the x-pair kernel (tiles kXpTX wide); the FWI sweep is acoustic
+  const std::vector<int> widths =
+      c->eq == FD_DIFFUSION ? std::vector<int>{kTmaTX, kXpTX} : std::vector<int>{kTmaTX};
+  for (int tx : widths)
   for (int ny : {2, 4}) {
     TmaPlan p{};
     const char *why = nullptr;
-    if (st || plan_tma(p, c->g, eq, c->iso, c->u, c->A, c->C, ny, 0, 0, 0, &why) != cudaSuccess) {
+    if (st || plan_tma(p, c->g, eq, c->iso, c->u, c->A, c->C, ny, 0, 0, 0, &why, tx) !=
+                  cudaSuccess) {
       cudaGetLastError();
       continue;
     }
     for (int cps = 1; cps <= p.per_sm_max; ++cps) {
       TmaPlan q{};
-      if (plan_tma(q, c->g, eq, c->iso, c->u, c->A, c->C, ny, cps, 0, 0, &why) != cudaSuccess) {
+      if (plan_tma(q, c->g, eq, c->iso, c->u, c->A, c->C, ny, cps, 0, 0, &why, tx) != cudaSuccess) {
         cudaGetLastError();
         continue;
       }
       const int share = q.args.zblock;
-      cands.push_back({ny, cps, share, 0});
-      if (share / 2 > zmin) cands.push_back({ny, cps, share / 2, 0});
-      if (2 * share <= c->g.n0) cands.push_back({ny, cps, 2 * share, 0});
+      cands.push_back({ny, cps, share, 0, tx});
+      if (share / 2 > zmin) cands.push_back({ny, cps, share / 2, 0, tx});
+      if (2 * share <= c->g.n0) cands.push_back({ny, cps, 2 * share, 0, tx});
       // segments no shorter than zmin planes
       const int mcap = std::max(1, c->g.n0 / zmin);
       const int m1 = std::max(1, (q.sms * cps) / q.args.ntiles);
       for (int m : {std::min(m1, mcap), std::min(2 * m1, mcap)}) {
         const int zb = (c->g.n0 + m - 1) / m;
         bool dup = false;
-        for (const Cand &d : cands) dup |= d.ny == ny && d.cps == cps && d.zb == zb && d.aligned;
-        if (!dup) cands.push_back({ny, cps, zb, 1});
+        for (const Cand &d : cands)
+          dup |= d.ny == ny && d.cps == cps && d.zb == zb && d.aligned && d.tx == tx;
+        if (!dup) cands.push_back({ny, cps, zb, 1, tx});
       }
     }
   }
@@ -1488,8 +1498,8 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
     if (st) break;
     TmaPlan r{};
     const char *why = nullptr;
-    if (plan_tma(r, c->g, eq, c->iso, c->u, c->A, c->C, cd.ny, cd.cps, cd.zb, cd.aligned, &why) !=
-        cudaSuccess) {
+    if (plan_tma(r, c->g, eq, c->iso, c->u, c->A, c->C, cd.ny, cd.cps, cd.zb, cd.aligned, &why,
+                 cd.tx) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
@@ -1508,7 +1518,7 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
       st = time_plan(c, r, scratch, reps, ev.data(), &us, fwi ? fbuf : nullptr,
                      sk ? flags : nullptr);
       if (st) break;
-      fd_tile_config cfg{kTmaTX, tma_ty(cd.ny), r.args.zblock, r.per_sm, cd.aligned, sk, us};
+      fd_tile_config cfg{cd.tx, tma_ty(cd.ny), r.args.zblock, r.per_sm, cd.aligned, sk, us};
       if (tried && n < max_tried) tried[n] = cfg;
       ++n;
       if (us < win_us) {
@@ -1531,7 +1541,8 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
   if (err[0]) return fail(c, FD_ETIMEOUT, "autotune: pipelined kernel wait expired (code %d)", err[0]);
   if (n == 0) return fail(c, FD_EUNSUPPORTED, "autotune: no tile configuration could be planned");
   if (ntried) *ntried = n;
-  st = replan(c, win.tile_y / kTmaNW, win.ctas_per_sm, win.zblock, win.aligned, win.skip_c);
+  st = replan(c, win.tile_y / kTmaNW, win.ctas_per_sm, win.zblock, win.aligned, win.skip_c,
+              win.tile_x);
   if (st) return st;
   c->tune_us = win.us_per_step;
   if (best) *best = win;

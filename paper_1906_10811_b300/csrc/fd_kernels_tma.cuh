@@ -776,6 +776,255 @@ timeout:
 }
 
 // ---------------------------------------------------------------------------
+// Diffusion step with two adjacent x points per lane (tiles kXpTX = 64 wide).
+// Same pipeline as k_stencil3d_tma (producer warp, ring U of halo'd u^n planes,
+// register z-queue, whole-segment or equal-range split), but a consumer lane
+// owns the x pair (x0 + 2·lane, x0 + 2·lane + 1) of NY rows: every shared-memory
+// read is an 8-byte pair, so a point needs about 5 of them instead of 12 (radius
+// 4), and the packed FP32x2 arithmetic runs over the x pair.  The per-point
+// operation sequence is that of k_stencil3d_tma (the same sums in the same
+// order, round to nearest), so results are bitwise the same.
+// ---------------------------------------------------------------------------
+constexpr int kXpTX = 64;
+__host__ __device__ constexpr int xp_bw(int R) { return kXpTX + 2 * tma_hxb(R); }
+__host__ __device__ constexpr int xp_ubytes(int R, int NY) { return xp_bw(R) * tma_bh(R, NY) * 4; }
+__host__ __device__ constexpr int xp_smem_bytes(int R, int NY) {
+  return 1024 + tma_du(R) * tma_align128(xp_ubytes(R, NY));
+}
+// the queue holds 2·NY·(2R+1) floats a thread
+__host__ __device__ constexpr int xp_minb(int R, int NY) { return tma_minb(R, 2 * NY); }
+
+template <int R, int NY, bool ISO>
+__global__ void __launch_bounds__(kTmaThreads, xp_minb(R, NY))
+k_diffusion3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXpTX + 2·HXB wide)
+                 const __grid_constant__ CUtensorMap, const __grid_constant__ CUtensorMap,
+                 const __grid_constant__ CUtensorMap, const __grid_constant__ CUtensorMap,
+                 const __grid_constant__ CUtensorMap, const TmaArgs args, const BatchArgs) {
+  constexpr int TY = tma_ty(NY);
+  constexpr int HXB = tma_hxb(R), BW = xp_bw(R), DU = tma_du(R);
+  constexpr int USLOT = tma_align128(xp_ubytes(R, NY)) / 4;  // floats per ring-U slot
+  constexpr int Q = 2 * R + 1;
+  constexpr int U = tma_unroll(R);
+  constexpr int QL = U == Q ? Q : Q + U - 1;
+  constexpr bool kSplit = R > 4;
+  constexpr int PH = (R + 1) / 2;  // x pairs each side of the lane's own
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t *full_u = reinterpret_cast<uint64_t *>(smem);
+  uint64_t *empty_u = full_u + DU;
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(empty_u + DU);
+  float *ring_u = reinterpret_cast<float *>(smem + 1024);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int *const err = args.err;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < DU; ++i) {
+      mbar_init(&full_u[i], 1);
+      mbar_init(&empty_u[i], kTmaNW);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+
+  int64_t q0 = 0, q1 = 0;
+  if (args.aligned)
+    cta_range((int64_t)args.ntiles * ((args.g.n0 + args.zblock - 1) / args.zblock), blockIdx.x,
+              gridDim.x, q0, q1);
+  else
+    cta_range(args.W, blockIdx.x, gridDim.x, q0, q1);
+
+  if (warp == kTmaNW) {
+    // ------------------------------- producer -------------------------------
+    if (lane == 0) {
+      tma_prefetch_desc(&map_u);
+      uint32_t su = 0;
+      const uint64_t keep = l2_policy_evict_last();
+      bool ok = true;
+      int64_t q = q0;
+      while (ok && q < q1) {
+        int tile, za, zb;
+        next_segment(args, q, q1, tile, za, zb);
+        const int x0 = (tile % args.tiles_x) * kXpTX, y0 = (tile / args.tiles_x) * TY;
+        for (int p = za - R; p < zb + R; ++p) {
+          if (*abort_flag) { ok = false; break; }
+          const uint32_t slot = su % DU;
+          if (su >= (uint32_t)DU && !mbar_wait(&empty_u[slot], ((su / DU) - 1) & 1)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full_u[slot], xp_ubytes(R, NY));
+          tma_load_3d_hint(ring_u + slot * USLOT, &map_u, x0 + kHaloX - HXB, y0, p + R,
+                           &full_u[slot], keep);
+          ++su;
+        }
+      }
+      if (!ok && atomicCAS(err, 0, 2) == 0) err[1] = blockIdx.x;
+      if (!ok) *abort_flag = 1;
+      bool drained = true;
+      for (uint32_t i = 0; i < (uint32_t)DU && i < su; ++i) {
+        const uint32_t last = su - 1 - ((su - 1 - i) % DU);  // last fill of slot i
+        drained &= mbar_wait(&full_u[last % DU], (last / DU) & 1);
+      }
+      if (!drained && atomicCAS(err, 0, 3) == 0) err[1] = blockIdx.x;
+    }
+    return;
+  }
+
+  // --------------------------------- consumers --------------------------------
+  float2 qp[NY][QL];  // queue: row j, the lane's x pair
+  uint32_t su = 0;
+  const int row0 = warp * NY;
+  const float2 *wp0 = args.c.wp[0], *wp1 = args.c.wp[1], *wp2 = args.c.wp[2];
+  const Geom g = args.g;
+  float *const out = args.out;
+  int64_t q = q0;
+  while (q < q1) {
+    int tile, za, zb;
+    next_segment(args, q, q1, tile, za, zb);
+    const int x = (tile % args.tiles_x) * kXpTX + 2 * lane;
+    const int ybase = (tile / args.tiles_x) * TY + row0;
+    const bool xin0 = x > 0 && x < g.n2 - 1, xin1 = x + 1 > 0 && x + 1 < g.n2 - 1;
+    unsigned rows_ok = 0;
+#pragma unroll
+    for (int j = 0; j < NY; ++j) {
+      const int y = ybase + j;
+      rows_ok |= ((y > 0 && y < g.n1 - 1) ? 1u : 0u) << j;
+    }
+    float *optr = out + gidx(g, za, ybase, x);
+    // warm-up: planes za-R .. za+R-1 fill queue slots 0 .. 2R-1
+#pragma unroll
+    for (int m = 0; m < 2 * R; ++m) {
+      const int p = za - R + m;
+      const uint32_t slot = su % DU;
+      if (!mbar_wait(&full_u[slot], (su / DU) & 1)) goto timeout;
+      const float *pl = ring_u + slot * USLOT + (R + row0) * BW + HXB + 2 * lane;
+#pragma unroll
+      for (int j = 0; j < NY; ++j) qp[j][m] = *reinterpret_cast<const float2 *>(pl + j * BW);
+      if (p < za || p >= zb) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty_u[slot]);
+      }
+      ++su;
+    }
+    {
+      const int nseg = zb - za;
+      int i = 0;
+      while (true) {
+#pragma unroll
+        for (int ph = 0; ph < U; ++ph) {
+          if (i >= nseg) goto segment_done;
+          {
+            const int zc = za + i;
+            const uint32_t slot = su % DU;
+            if (!mbar_wait(&full_u[slot], (su / DU) & 1)) goto timeout;
+            const float *pl = ring_u + slot * USLOT + (R + row0) * BW + HXB + 2 * lane;
+#pragma unroll
+            for (int j = 0; j < NY; ++j)
+              qp[j][tma_qslot<U, Q>(ph, 2 * R)] = *reinterpret_cast<const float2 *>(pl + j * BW);
+            const uint32_t cs = (su - R) % DU;  // ring-U slot holding plane zc
+            const float *cp = ring_u + cs * USLOT + row0 * BW + HXB + 2 * lane;
+            float2 ycol[NY + 2 * R];  // the lane's pair, rows row0-R .. row0+NY-1+R
+#pragma unroll
+            for (int r = 0; r < NY + 2 * R; ++r) ycol[r] = *reinterpret_cast<const float2 *>(cp + r * BW);
+            float2 val[NY];
+#pragma unroll
+            for (int j = 0; j < NY; ++j) {
+              // the row's x pairs around the lane's own (pair d starts at x + 2d)
+              const float *rp = cp + (R + j) * BW;
+              float2 xpr[2 * PH + 1];
+#pragma unroll
+              for (int d = -PH; d <= PH; ++d)
+                xpr[d + PH] = d == 0 ? ycol[R + j] : *reinterpret_cast<const float2 *>(rp + 2 * d);
+              // u(x+k) + u(x-k) for the pair: aligned pairs for even k, halves of
+              // the neighbouring pairs for odd k
+              auto xsum = [&](int k) -> float2 {
+                if ((k & 1) == 0) return __fadd2_rn(xpr[PH + k / 2], xpr[PH - k / 2]);
+                return make_float2(__fadd_rn(xpr[PH + (k - 1) / 2].y, xpr[PH - (k + 1) / 2].y),
+                                   __fadd_rn(xpr[PH + (k + 1) / 2].x, xpr[PH - (k - 1) / 2].x));
+              };
+              const float2 uc = qp[j][tma_qslot<U, Q>(ph, R)];
+              float2 lo = make_float2(0.f, 0.f), le = lo;
+              if (ISO) {
+                const float2 nuc6 = __fmul2_rn(make_float2(-6.f, -6.f), uc);
+#pragma unroll
+                for (int k = 1; k <= R; ++k) {
+                  const float2 sx = xsum(k);
+                  const float2 sy = __fadd2_rn(ycol[R + j + k], ycol[R + j - k]);
+                  const float2 sz = __fadd2_rn(qp[j][tma_qslot<U, Q>(ph, R + k)],
+                                               qp[j][tma_qslot<U, Q>(ph, R - k)]);
+                  const float2 dd = __fadd2_rn(__fadd2_rn(__fadd2_rn(sx, sy), sz), nuc6);
+                  if ((k & 1) || !kSplit)
+                    lo = __ffma2_rn(wp2[k], dd, lo);
+                  else
+                    le = __ffma2_rn(wp2[k], dd, le);
+                }
+              } else {
+                const float2 nuc2 = __fmul2_rn(make_float2(-2.f, -2.f), uc);
+#pragma unroll
+                for (int k = 1; k <= R; ++k) {
+                  float2 acc = ((k & 1) || !kSplit) ? lo : le;
+                  acc = __ffma2_rn(wp2[k], __fadd2_rn(xsum(k), nuc2), acc);
+                  acc = __ffma2_rn(wp1[k],
+                                   __fadd2_rn(__fadd2_rn(ycol[R + j + k], ycol[R + j - k]), nuc2),
+                                   acc);
+                  acc = __ffma2_rn(wp0[k],
+                                   __fadd2_rn(__fadd2_rn(qp[j][tma_qslot<U, Q>(ph, R + k)],
+                                                         qp[j][tma_qslot<U, Q>(ph, R - k)]),
+                                              nuc2),
+                                   acc);
+                  if ((k & 1) || !kSplit)
+                    lo = acc;
+                  else
+                    le = acc;
+                }
+              }
+              const float2 lap = kSplit ? __fadd2_rn(lo, le) : lo;
+              val[j] = __fadd2_rn(uc, lap);
+            }
+            // interior nodes only: boundary values stay as set
+            if (zc > 0 && zc < g.n0 - 1) {
+#pragma unroll
+              for (int j = 0; j < NY; ++j) {
+                if (!(rows_ok & (1u << j))) continue;
+                float *o = optr + j * g.px;
+                if (xin0 && xin1)
+                  __stcs(reinterpret_cast<float2 *>(o), val[j]);
+                else {
+                  if (xin0) __stcs(o, val[j].x);
+                  if (xin1) __stcs(o + 1, val[j].y);
+                }
+              }
+            }
+            optr += g.plane;
+            __syncwarp();
+            if (lane == 0) {
+              mbar_arrive(&empty_u[cs]);
+              if (zc + R >= zb) mbar_arrive(&empty_u[slot]);  // trailing plane: queue only
+            }
+            ++su;
+            ++i;
+          }
+        }
+        if constexpr (U < Q) {
+#pragma unroll
+          for (int j = 0; j < NY; ++j)
+#pragma unroll
+            for (int m = 0; m < 2 * R; ++m) qp[j][m] = qp[j][m + U];
+        }
+      }
+    }
+  segment_done:;
+  }
+  return;
+timeout:
+  if (lane == 0) {
+    if (atomicCAS(err, 0, 1) == 0) err[1] = blockIdx.x;
+    *abort_flag = 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 using TmaKernelFn = void (*)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap,
@@ -799,6 +1048,7 @@ struct TmaPlan {
   int per_sm_fwi = 0;  // occupancy limit of fn_fwi
   int smem_fwi = 0;
   int sms = 0;
+  int tx = kTmaTX;     // tile width: kTmaTX, or kXpTX (diffusion, two x points a lane)
 };
 
 using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
@@ -866,15 +1116,41 @@ inline cudaError_t tma_configure(TmaPlan &pl, int ny) {
   return cudaSuccess;
 }
 
+// The x-pair diffusion kernel for rows-per-thread ny.
+template <int R, bool ISO>
+inline cudaError_t xp_configure(TmaPlan &pl, int ny) {
+  TmaKernelFn fn = ny == 2 ? k_diffusion3d_xp<R, 2, ISO> : k_diffusion3d_xp<R, 4, ISO>;
+  const int smem = ny == 2 ? xp_smem_bytes(R, 2) : xp_smem_bytes(R, 4);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl.per_sm_max, fn, kTmaThreads, smem);
+  if (e == cudaSuccess && pl.per_sm_max < 1) e = cudaErrorInvalidConfiguration;
+  if (e != cudaSuccess) return e;
+  pl.fn = fn;
+  pl.smem = smem;
+  pl.fn_multi = nullptr;
+  pl.fn_fwi = nullptr;
+  pl.smem_multi = 0;
+  pl.per_sm_fwi = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&pl.sms, cudaDevAttrMultiProcessorCount, dev);
+  pl.grid_multi = 0;
+  return cudaSuccess;
+}
+
 // Tile configurations the pipelined kernel offers (the autotuner's space).
 inline bool tma_ny_supported(int ny) { return ny == 2 || ny == 4; }
+inline bool tma_tx_supported(int tx, int eq) {
+  return tx == kTmaTX || (tx == kXpTX && eq == kDiffusion);
+}
 
 // Build the plan: tensor maps for both levels and the coefficient fields, for
 // ny rows per consumer thread (0: the default), a grid of per_sm CTAs per SM
 // (0: as many as fit) and z-blocks of zblock planes (0: about one CTA's share).
 inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float *const *level,
                             float *A, float *C, int ny, int per_sm, int zblock, int aligned,
-                            const char **why) {
+                            const char **why, int tx = kTmaTX) {
   *why = nullptr;
   if (g.R0 == 0 || g.R < 1 || g.R > kMaxR) {
     *why = "3-D grids only";
@@ -882,14 +1158,16 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float 
   }
   const int R = g.R;
   if (ny == 0) ny = tma_ny(R);
-  if (!tma_ny_supported(ny) || per_sm < 0 || zblock < 0 || (aligned != 0 && aligned != 1)) {
+  if (!tma_ny_supported(ny) || !tma_tx_supported(tx, eq) || per_sm < 0 || zblock < 0 ||
+      (aligned != 0 && aligned != 1)) {
     *why = "unsupported tile configuration";
     return cudaErrorInvalidValue;
   }
   // TMA rules: 16-B aligned bases and strides, inner box extent a 16-B multiple,
   // x coordinates multiples of 4 floats (x0 + kHaloX - HXB with x0 % 32 == 0).
   if ((g.px * 4) % 16 || tma_hxb(R) % 4 || (tma_bw(R) * 4) % 16 || kHaloX % 4 ||
-      tma_bw(R) > 256 || tma_bh(R, 4) > 256 || tma_ty(4) > 256 || (kTmaTX * 4) % 16) {
+      tma_bw(R) > 256 || tma_bh(R, 4) > 256 || tma_ty(4) > 256 || (kTmaTX * 4) % 16 ||
+      (xp_bw(R) * 4) % 16 || xp_bw(R) > 256 || kXpTX % 4) {
     *why = "layout violates the TMA alignment rules";
     return cudaErrorNotSupported;
   }
@@ -899,8 +1177,9 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float 
     return cudaErrorNotSupported;
   }
   const int ty = tma_ty(ny);
+  const bool xp = tx == kXpTX;
   for (int b = 0; b < 2; ++b) {
-    if (!encode_map(enc, &pl.map_u[b], level[b], g, tma_bw(R), tma_bh(R, ny)) ||
+    if (!encode_map(enc, &pl.map_u[b], level[b], g, xp ? xp_bw(R) : tma_bw(R), tma_bh(R, ny)) ||
         !encode_map(enc, &pl.map_t[b], level[b], g, kTmaTX, ty)) {
       *why = "tensor map encoding failed";
       return cudaErrorInvalidValue;
@@ -926,7 +1205,16 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float 
            : (iso ? tma_configure<RR, kDiffusion, true>(pl, ny)                        \
                   : tma_configure<RR, kDiffusion, false>(pl, ny));                     \
     break;
-  switch (R) { TMA_CASE(1) TMA_CASE(2) TMA_CASE(3) TMA_CASE(4) TMA_CASE(5) TMA_CASE(6) TMA_CASE(7) TMA_CASE(8) }
+#define XP_CASE(RR)                                                                    \
+  case RR:                                                                             \
+    e = iso ? xp_configure<RR, true>(pl, ny) : xp_configure<RR, false>(pl, ny);        \
+    break;
+  if (xp) {
+    switch (R) { XP_CASE(1) XP_CASE(2) XP_CASE(3) XP_CASE(4) XP_CASE(5) XP_CASE(6) XP_CASE(7) XP_CASE(8) }
+  } else {
+    switch (R) { TMA_CASE(1) TMA_CASE(2) TMA_CASE(3) TMA_CASE(4) TMA_CASE(5) TMA_CASE(6) TMA_CASE(7) TMA_CASE(8) }
+  }
+#undef XP_CASE
 #undef TMA_CASE
   if (e != cudaSuccess) {
     *why = "kernel configuration failed";
@@ -941,7 +1229,8 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float 
   pl.grid = pl.sms * pl.per_sm;
   if (pl.fn_fwi && pl.per_sm_fwi < pl.per_sm) pl.fn_fwi = nullptr;  // would not all be resident
   pl.args.g = g;
-  pl.args.tiles_x = (g.n2 + kTmaTX - 1) / kTmaTX;
+  pl.tx = tx;
+  pl.args.tiles_x = (g.n2 + tx - 1) / tx;
   const int tiles_y = (g.n1 + ty - 1) / ty;
   pl.args.ntiles = pl.args.tiles_x * tiles_y;
   pl.args.W = (int64_t)pl.args.ntiles * g.n0;

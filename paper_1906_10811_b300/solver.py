@@ -135,10 +135,10 @@ class Solver:
         """{tile_x, tile_y, zblock, ctas_per_sm, aligned, skip_c, us_per_step} of the pipelined kernel."""
         return B.fd_get_tile_config(self.ctx)
 
-    def set_tile_config(self, tile_y=0, zblock=0, ctas_per_sm=0, aligned=0, skip_c=0):
+    def set_tile_config(self, tile_y=0, zblock=0, ctas_per_sm=0, aligned=0, skip_c=0, tile_x=0):
         self._in()
         B.fd_set_tile_config(self.ctx, tile_y=tile_y, zblock=zblock, ctas_per_sm=ctas_per_sm,
-                             aligned=aligned, skip_c=skip_c)
+                             aligned=aligned, skip_c=skip_c, tile_x=tile_x)
         self._out()
 
     def autotune(self, reps=5, fwi=False, cached=False):

@@ -211,3 +211,50 @@ def test_skipping_c_is_bitwise_on_a_grid_with_a_real_damping_layer():
     for a, b in zip(got[:3], ref[:3]):
         assert np.array_equal(a, b)
     assert np.abs(ref[2]).max() > 0
+
+
+@pytest.mark.parametrize("so,spacing,boundary", [(2, (1.0 / 40,) * 3, "zero"),
+                                                 (4, (0.021, 0.025, 0.03), "zero"),
+                                                 (8, (1.0 / 40,) * 3, "zero"),
+                                                 (8, (1.0 / 40,) * 3, "odd"),
+                                                 (12, (0.021, 0.025, 0.03), "zero"),
+                                                 (16, (1.0 / 40,) * 3, "zero")])
+def test_diffusion_x_pair_tiles_are_bitwise_the_default(so, spacing, boundary):
+    """tile_x = 64 (a lane per pair of adjacent x points) runs the same arithmetic per
+    point: bitwise the default kernel, for ragged x extents, both splits and both heights."""
+    from paper_1906_10811_b300 import Solver
+    rng = np.random.default_rng(so)
+    shape = (23, 37, 131)                      # x: two full 64-wide tiles and 3 points
+    u0 = rng.standard_normal(shape).astype(np.float32)
+    dt = 0.05 * min(spacing) ** 2
+    outs, used = [], []
+    for cfg in (None, dict(tile_x=64, tile_y=16), dict(tile_x=64, tile_y=32),
+                dict(tile_x=64, tile_y=16, aligned=1, zblock=7),
+                dict(tile_x=64, tile_y=16, ctas_per_sm=1, zblock=3)):
+        with Solver(shape, spacing, so, dt, "diffusion", kernel="tma", boundary=boundary) as s:
+            if cfg:
+                s.set_tile_config(**cfg)
+            used.append(s.tile_config["tile_x"])
+            s.set_field(u0)
+            s.run(9)
+            outs.append(s.read()[0])
+    assert used == [32, 64, 64, 64, 64]
+    for u in outs[1:]:
+        assert np.array_equal(u, outs[0])
+
+
+def test_x_pair_tiles_only_for_diffusion_and_tuned_there():
+    from paper_1906_10811_b300 import Solver
+    from paper_1906_10811_b300.binding import FdError
+    p = small_problem((30, 33, 35), 8, 10, nrec=3)
+    with Solver(p["shape"], p["spacing"], 8, p["dt"], "acoustic", kernel="tma") as s:
+        with pytest.raises(FdError):
+            s.set_tile_config(tile_x=64)
+        with pytest.raises(FdError):
+            s.set_tile_config(tile_x=48)
+    with Solver((40, 48, 150), (1.0 / 40,) * 3, 8, 0.1 * (1.0 / 40) ** 2, "diffusion",
+                kernel="tma") as s:
+        s.set_field(np.ones((40, 48, 150), np.float32))
+        best, tried = s.autotune(reps=2)
+        assert {t["tile_x"] for t in tried} == {32, 64}
+        assert s.tile_config["tile_x"] == best["tile_x"]
