@@ -87,9 +87,10 @@ def parse():
     ap.add_argument("--kernel", default="auto", choices=["auto", "plain", "tma"])
     ap.add_argument("--tile", default="auto",
                     help="auto: the autotuner picks the pipelined kernel's tile configuration "
-                         "before the timed region; default: the built-in one; TY,ZB,CPS[,AL[,SK]]: "
-                         "tile height, z-block height, CTAs per SM, whole-segment split and "
-                         "C-tile skipping given explicitly")
+                         "before the timed region; default: the built-in one; "
+                         "TY,ZB,CPS[,AL[,SK[,TX]]]: tile height, z-block height, CTAs per SM, "
+                         "whole-segment split, C-tile skipping and tile width (64: the "
+                         "diffusion x-pair kernel) given explicitly")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -495,8 +496,9 @@ def run_diffusion(args):
         if args.tile == "auto":
             tune_tried = len(s.autotune(reps=5)[1])
         elif args.tile != "default":
-            ty, zb, cps, al, sk = ([int(v) for v in args.tile.split(",")] + [0, 0])[:5]
-            s.set_tile_config(tile_y=ty, zblock=zb, ctas_per_sm=cps, aligned=al, skip_c=sk)
+            ty, zb, cps, al, sk, tx = ([int(v) for v in args.tile.split(",")] + [0, 0, 0])[:6]
+            s.set_tile_config(tile_y=ty, zblock=zb, ctas_per_sm=cps, aligned=al, skip_c=sk,
+                              tile_x=tx)
         tile = s.tile_config
 
     def sweep():
@@ -639,8 +641,9 @@ def run_ours(args):
             _, tried = s.autotune(reps=5)
             tune_tried = len(tried)
         elif args.tile != "default":
-            ty, zb, cps, al, sk = ([int(v) for v in args.tile.split(",")] + [0, 0])[:5]
-            s.set_tile_config(tile_y=ty, zblock=zb, ctas_per_sm=cps, aligned=al, skip_c=sk)
+            ty, zb, cps, al, sk, tx = ([int(v) for v in args.tile.split(",")] + [0, 0, 0])[:6]
+            s.set_tile_config(tile_y=ty, zblock=zb, ctas_per_sm=cps, aligned=al, skip_c=sk,
+                              tile_x=tx)
         tile = s.tile_config
 
     def shot():
