@@ -706,8 +706,8 @@ def run_ours(args):
                                skip_c=tile["skip_c"], tile_x=tile["tile_x"])
         from paper_1906_10811_b300 import binding as B
 
-        def survey(n):
-            """n shots back to back, as a survey runs them: a shot's model upload
+        def shot_sequence(n):
+            """n shots back to back, as a seismic acquisition runs them: a shot's model upload
             overlaps the previous shot's steps (fd_set_model with host buffers),
             whose traces are read before the next shot's receivers replace them."""
             for i in range(n):
@@ -721,10 +721,10 @@ def run_ours(args):
                 se.run(nt)
             B.fd_read(se.ctx, None, rec_out if w["nrec"] else None)
 
-        survey(args.warmup)
+        shot_sequence(args.warmup)
         barrier()
         t0 = time.perf_counter()
-        survey(args.steps)
+        shot_sequence(args.steps)
         barrier()
         te = time.perf_counter() - t0
         se.close()

@@ -146,7 +146,7 @@ fd_status fd_reset(fd_ctx *ctx);
  * [nt][nsrc] (row n = s(t_n) for global step n).  Replaces earlier sources;
  * nsrc = 0 removes them.  fd_run fails with FD_EINVAL if it would pass step nt.
  * With the same nsrc and nt as before, the device buffers are refilled in place
- * and the captured step graphs are kept (a survey's next shot).
+ * and the captured step graphs are kept (an acquisition's next shot).
  */
 fd_status fd_set_sources(fd_ctx *ctx, int nsrc, const float *coords, int nt,
                          const float *wavelets);

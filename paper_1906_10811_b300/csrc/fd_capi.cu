@@ -1007,7 +1007,7 @@ fd_status fd_set_sources(fd_ctx *c, int nsrc, const float *coords, int nt, const
                  &w[(size_t)j * c->nc]))
       return fail(c, FD_EINVAL, "source %d lies outside the grid", j);
   CU(cudaStreamSynchronize(c->stream));
-  // The same counts as before (the next shot of a survey): the buffers are
+  // The same counts as before (the next shot of a seismic acquisition): the buffers are
   // refilled in place, so the captured graphs, which hold their addresses, stay.
   if (nsrc == 0 || nsrc != c->nsrc || nt != c->nt_wav) {
     dfree(c, c->src_off); dfree(c, c->src_dense); dfree(c, c->src_w); dfree(c, c->src_scale); dfree(c, c->wav);

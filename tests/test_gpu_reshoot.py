@@ -1,4 +1,4 @@
-"""A survey's shots through one context: after fd_reset and new model, sources
+"""The shots of a seismic acquisition through one context: after fd_reset and new model, sources
 and receivers (the same counts, so the device buffers and the captured step
 graphs are reused; or other counts, so they are rebuilt) a shot gives bitwise
 the result of a fresh context, and that result matches the FP64 oracle."""
