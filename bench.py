@@ -54,16 +54,17 @@ WORKLOADS = {
 
 # DRAM bytes per stencil launch from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum, mean of the captured launches), keyed by (kernel name,
-# workload, space order, tile height, z-block height, CTAs per SM, aligned); the captures
+# workload, space order, tile width, tile height, z-block height, CTAs per SM, aligned,
+# skip_c); the captures
 # are summarised in profiles/.  Absent (null) when not captured for the kernel
 # and tile configuration as they are now.
 NCU_TRAFFIC = {
     # profiles/stencil3d_tma_acoustic256_so8.md: mean of 3 launches, read 298.56 MB + write 26.53 MB
-    ("stencil3d_tma_acoustic", "acoustic256", 8, 32, 64, 2, 1, 0): 325.08e6,
+    ("stencil3d_tma_acoustic", "acoustic256", 8, 32, 32, 64, 2, 1, 0): 325.08e6,
     # same file, C skipped where it is 1: mean of 3 launches, read 287.03 MB + write 26.52 MB
-    ("stencil3d_tma_acoustic", "acoustic256", 8, 32, 64, 2, 1, 1): 313.55e6,
+    ("stencil3d_tma_acoustic", "acoustic256", 8, 32, 32, 64, 2, 1, 1): 313.55e6,
     # profiles/stencil3d_tma_roofline512.md: mean of 2 launches, read 1996.73 MB + write 496.41 MB
-    ("stencil3d_tma_acoustic", "roofline512", 8, 32, 512, 2, 1, 1): 2493.14e6,
+    ("stencil3d_tma_acoustic", "roofline512", 8, 32, 32, 512, 2, 1, 1): 2493.14e6,
 }
 
 
@@ -678,8 +679,8 @@ def run_ours(args):
     peak, peak_kind = load_peak()
     avg_launch_s = st_ms / max(n_st, 1) / 1e3
     achieved = BYTES_PER_POINT["acoustic"] * npts / avg_launch_s / 1e9
-    tkey = ((tile["tile_y"], tile["zblock"], tile["ctas_per_sm"], tile["aligned"], tile["skip_c"])
-            if tile else (0, 0, 0, 0, 0))
+    tkey = ((tile["tile_x"], tile["tile_y"], tile["zblock"], tile["ctas_per_sm"], tile["aligned"],
+             tile["skip_c"]) if tile else (0, 0, 0, 0, 0, 0))
     traffic = NCU_TRAFFIC.get((kernel_name, args.workload, w["so"]) + tkey)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,

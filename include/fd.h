@@ -243,9 +243,11 @@ fd_status fd_field_to_dense(fd_ctx *ctx, const float *padded, float *dense);
  * bitwise the same result: a point's update is the same arithmetic whatever
  * tile holds it.
  *
- *   tile_x       points per tile along x: 32 (a lane per point), or 64 for
- *                FD_DIFFUSION (a lane per pair of adjacent points, 8-byte
- *                shared-memory reads; the same arithmetic per point)
+ *   tile_x       points per tile along x: 32 (a lane per point), or 64 (a lane
+ *                per pair of adjacent points, 8-byte shared-memory reads; the
+ *                same arithmetic per point).  fd_step_fwi and batches run 32:
+ *                fd_step_fwi refuses a 64-wide configuration (FD_EUNSUPPORTED)
+ *                and fd_batch_add puts the member back to the default
  *   tile_y       points per tile along y: 8 consumer warps × rows per thread,
  *                16 or 32
  *   zblock       z-streaming depth: consecutive planes a CTA streams on one
@@ -267,14 +269,14 @@ fd_status fd_field_to_dense(fd_ctx *ctx, const float *padded, float *dense);
  *
  * fd_get_tile_config: the configuration fd_run uses; FD_EUNSUPPORTED when the
  *   context runs the plain kernel.
- * fd_set_tile_config: use cfg (tile_x 32 or 0, or 64 for FD_DIFFUSION, tile_y 16 or 32 or 0 for the
+ * fd_set_tile_config: use cfg (tile_x 32 or 0, or 64, tile_y 16 or 32 or 0 for the
  *   default, zblock ≥ 0 with 0 meaning one CTA's share (aligned = 0) or the
  *   height that makes about as many segments as CTAs (aligned = 1),
  *   ctas_per_sm ≥ 0 with 0 meaning as many as fit, aligned and skip_c 0 or 1);
  *   FD_EINVAL for anything else, leaving the current configuration in
  *   place.  Captured graphs are dropped.
  * fd_autotune: time every configuration of the search space (tile_x in {32, 64}
- *   for FD_DIFFUSION, 32 otherwise × tile_y in
+ *   (32 only for fd_autotune_fwi) × tile_y in
  *   {16, 32} × ctas_per_sm in 1..fit × (aligned 0 with zblock in {share/2,
  *   share, 2·share} | aligned 1 with m or 2m z-blocks, m = CTAs / tiles)
  *   × skip_c {0, 1} where it applies (once a model is set),
@@ -283,7 +285,8 @@ fd_status fd_field_to_dense(fd_ctx *ctx, const float *padded, float *dense);
  *   and write a scratch field allocated for the call, so the solution is not
  *   disturbed; sources are not injected during the trials.  Synchronises the
  *   context stream.  tried (may be NULL) receives up to max_tried measured
- *   configurations, *ntried (may be NULL) their number; best (may be NULL)
+ *   configurations, *ntried (may be NULL) how many were measured (which may
+ *   exceed max_tried); best (may be NULL)
  *   the chosen one.  FD_ENOMEM when the scratch field does not fit.
  */
 typedef struct {

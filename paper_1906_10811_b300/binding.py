@@ -268,7 +268,7 @@ def fd_set_tile_config(ctx, tile_y=0, zblock=0, ctas_per_sm=0, tile_x=0, aligned
     _check(ctx, load().fd_set_tile_config(ctx, ctypes.byref(cfg)))
 
 
-def fd_autotune(ctx, reps=5, max_tried=64, fwi=False):
+def fd_autotune(ctx, reps=5, max_tried=256, fwi=False):
     """Time the tile configurations and use the fastest: (best, tried) as dicts.
 
     fwi: time them as the FWI sweep's kernels (fd_autotune_fwi).  max_tried = 0
@@ -278,7 +278,8 @@ def fd_autotune(ctx, reps=5, max_tried=64, fwi=False):
     n = ctypes.c_int()
     fn = load().fd_autotune_fwi if fwi else load().fd_autotune
     _check(ctx, fn(ctx, int(reps), ctypes.byref(best), tried, int(max_tried), ctypes.byref(n)))
-    return best.as_dict(), [tried[i].as_dict() for i in range(n.value)] if tried else []
+    return best.as_dict(), ([tried[i].as_dict() for i in range(min(n.value, max_tried))]
+                            if tried else [])
 
 
 def fd_kernel_launches(ctx):

@@ -561,7 +561,7 @@ fd_status prepare_fused(fd_ctx *c) {
       const int x = (int)(d % c->g.n2);
       const int y = (int)((d / c->g.n2) % c->g.n1);
       const int z = (int)(d / ((int64_t)c->g.n1 * c->g.n2));
-      const int tile = (y / ty) * tiles_x + x / kTmaTX;
+      const int tile = (y / ty) * tiles_x + x / c->tma.tx;
       es.push_back({(int64_t)tile * c->g.n0 + z, (int)i, x, y, z});
     }
     std::sort(es.begin(), es.end(), [](const E &a, const E &b) {
@@ -614,7 +614,7 @@ fd_status prepare_unit_c(fd_ctx *c) {
     if (st) return st;
     c->unit_c_cap = n;
   }
-  k_unit_c<<<(unsigned)n, 128, 0, c->stream>>>(c->C, c->g, c->tma.args.tiles_x, kTmaTX,
+  k_unit_c<<<(unsigned)n, 128, 0, c->stream>>>(c->C, c->g, c->tma.args.tiles_x, c->tma.tx,
                                                tma_ty(c->tma.ny), c->unit_c);
   CHECK_LAUNCH();
   c->unit_c_dirty = false;
@@ -1154,7 +1154,8 @@ fd_status fd_step_fwi(fd_ctx *c, float *d2_out, float *img_g, const float *img_d
   fd_status st = check_usable(c);
   if (st) return st;
   if (c->eq != FD_ACOUSTIC || !c->use_tma || !c->tma.fn_fwi)
-    return fail(c, FD_EUNSUPPORTED, "fd_step_fwi needs the pipelined 3-D acoustic kernel");
+    return fail(c, FD_EUNSUPPORTED,
+                "fd_step_fwi needs the pipelined 3-D acoustic kernel with 32-wide tiles");
   if (img_g && !img_d2) return fail(c, FD_EINVAL, "img_g needs img_d2");
   c->fwi_d2 = d2_out;
   c->fwi_img = img_g;
@@ -1452,9 +1453,9 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
     int ny, cps, zb, aligned, tx;
   };
   std::vector<Cand> cands;
-  // diffusion also tries the x-pair kernel (tiles kXpTX wide); the FWI sweep is acoustic
+  // the x-pair kernel (tiles kXpTX wide) too, except for the FWI sweep (no FWI instance)
   const std::vector<int> widths =
-      c->eq == FD_DIFFUSION ? std::vector<int>{kTmaTX, kXpTX} : std::vector<int>{kTmaTX};
+      fwi ? std::vector<int>{kTmaTX} : std::vector<int>{kTmaTX, kXpTX};
   for (int tx : widths)
   for (int ny : {2, 4}) {
     TmaPlan p{};
@@ -1507,7 +1508,7 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
     for (int sk = 0; sk <= (try_skip ? 1 : 0) && !st; ++sk) {
       if (sk) {
         const int64_t nf = (int64_t)r.args.ntiles * c->g.n0;
-        k_unit_c<<<(unsigned)nf, 128, 0, c->stream>>>(c->C, c->g, r.args.tiles_x, kTmaTX,
+        k_unit_c<<<(unsigned)nf, 128, 0, c->stream>>>(c->C, c->g, r.args.tiles_x, cd.tx,
                                                        tma_ty(cd.ny), flags);
         if (cudaGetLastError() != cudaSuccess) {
           st = fail(c, FD_ECUDA, "autotune: flags kernel");
@@ -1691,6 +1692,11 @@ fd_status fd_batch_add(fd_batch *b, fd_ctx *c) {
   if (c->device != b->device) return bfail(b, FD_EINVAL, "member lives on another device");
   if (std::find(b->members.begin(), b->members.end(), c) != b->members.end())
     return bfail(b, FD_EINVAL, "already a member");
+  if (c->ndim == 3 && c->tma.tx != kTmaTX) {
+    // the batched kernel has 32-wide tiles only: back to the default configuration
+    fd_status st = replan(c, 0, 0, 0, default_aligned(c->eq));
+    if (st) return bfail(b, st, "member replan: %s", c->err.c_str());
+  }
   if (c->ndim == 3 && !b->members.empty()) {
     for (fd_ctx *o : b->members)
       if (o->ndim == 3 && (o->tma.fn_multi != c->tma.fn_multi ||
@@ -1731,7 +1737,8 @@ fd_status fd_batch_run(fd_batch *b, int nticks) {
       return bfail(b, FD_EINVAL, "a member would pass its wavelet length");
     fd_status st = FD_OK;
     // the batched kernel runs the default tile: a tuned member goes back to it
-    if (c->ndim == 3 && c->tma.ny != tma_ny(R)) st = replan(c, 0, 0, 0, default_aligned(c->eq));
+    if (c->ndim == 3 && (c->tma.ny != tma_ny(R) || c->tma.tx != kTmaTX))
+      st = replan(c, 0, 0, 0, default_aligned(c->eq));
     if (!st && c->nrec > 0) st = ensure_rec_capacity(c, c->step + nticks + 1);
     if (!st) st = prepare_sources(c);
     if (!st && c->ndim == 3) st = prepare_fused(c);

@@ -776,43 +776,111 @@ timeout:
 }
 
 // ---------------------------------------------------------------------------
-// Diffusion step with two adjacent x points per lane (tiles kXpTX = 64 wide).
-// Same pipeline as k_stencil3d_tma (producer warp, ring U of halo'd u^n planes,
-// register z-queue, whole-segment or equal-range split), but a consumer lane
-// owns the x pair (x0 + 2·lane, x0 + 2·lane + 1) of NY rows: every shared-memory
-// read is an 8-byte pair, so a point needs about 5 of them instead of 12 (radius
-// 4), and the packed FP32x2 arithmetic runs over the x pair.  The per-point
-// operation sequence is that of k_stencil3d_tma (the same sums in the same
-// order, round to nearest), so results are bitwise the same.
+// Step with two adjacent x points per lane (tiles kXpTX = 64 wide).  Same
+// pipeline as k_stencil3d_tma (producer warp, ring U of halo'd u^n planes, ring
+// X of (u^{n-1}, A, C) tiles for the acoustic step, register z-queue, whole-
+// segment or equal-range split, fused source injection, skip_c), but a consumer
+// lane owns the x pair (x0 + 2·lane, x0 + 2·lane + 1) of NY rows: every
+// shared-memory read is an 8-byte pair, so a point needs about 5 neighbour reads
+// instead of 12 (radius 4), and the packed FP32x2 arithmetic runs over the x
+// pair.  The per-point operation sequence is that of k_stencil3d_tma (the same
+// sums in the same order, round to nearest; sources added in entry order), so
+// results are bitwise the same.  No batched or FWI instances.
 // ---------------------------------------------------------------------------
 constexpr int kXpTX = 64;
 __host__ __device__ constexpr int xp_bw(int R) { return kXpTX + 2 * tma_hxb(R); }
 __host__ __device__ constexpr int xp_ubytes(int R, int NY) { return xp_bw(R) * tma_bh(R, NY) * 4; }
-__host__ __device__ constexpr int xp_smem_bytes(int R, int NY) {
-  return 1024 + tma_du(R) * tma_align128(xp_ubytes(R, NY));
+__host__ __device__ constexpr int xp_xbytes(int NY) { return kXpTX * tma_ty(NY) * 4; }
+__host__ __device__ constexpr int xp_smem_bytes(int R, int NY, bool acoustic) {
+  return 1024 + tma_du(R) * tma_align128(xp_ubytes(R, NY)) +
+         (acoustic ? kTmaDX * 3 * xp_xbytes(NY) : 0);
 }
 // the queue holds 2·NY·(2R+1) floats a thread
 __host__ __device__ constexpr int xp_minb(int R, int NY) { return tma_minb(R, 2 * NY); }
 
-template <int R, int NY, bool ISO>
+// Source corners at plane zc of this tile for the lane's x pair: vx holds rows
+// 0..3 at x, vy rows 0..3 at x + 1 (see source_hits).
+struct SourceHitsXp {
+  float4 vx, vy;
+  int ecur, nxt_z;
+};
+__device__ __forceinline__ void add_row(float4 &v, int j, float a) {
+  if (j == 0) v.x += a;
+  else if (j == 1) v.y += a;
+  else if (j == 2) v.z += a;
+  else v.w += a;
+}
+__device__ __forceinline__ SourceHitsXp source_hits_xp(const int4 *entries, const float *src_scale,
+                                                       const float *wav, int nsrc, int nc,
+                                                       int ecur, int eend, int zc, int ybase,
+                                                       int ny, int x, int lane, int64_t nstep,
+                                                       float4 vx, float4 vy) {
+  while (true) {
+    const int e = ecur + lane;
+    const int4 en = e < eend ? entries[e] : make_int4(0, 0, INT_MAX, 0);
+    const int cnt = __popc(__ballot_sync(0xffffffffu, en.z == zc));  // a prefix
+    const int jr = en.y - ybase;
+    const bool here = en.z == zc && jr >= 0 && jr < ny;
+    float add = 0.f;
+    if (here) add = src_scale[en.w] * wav[nstep * nsrc + en.w / nc];
+    unsigned mine = __ballot_sync(0xffffffffu, here);
+    while (mine) {
+      const int b = __ffs(mine) - 1;
+      mine &= mine - 1;
+      const int ex = __shfl_sync(0xffffffffu, en.x, b);
+      const int ej = __shfl_sync(0xffffffffu, jr, b);
+      const float ad = __shfl_sync(0xffffffffu, add, b);
+      if (ex == x) add_row(vx, ej, ad);
+      else if (ex == x + 1) add_row(vy, ej, ad);
+    }
+    ecur += cnt;
+    if (cnt < 32) break;
+  }
+  SourceHitsXp h;
+  h.vx = vx;
+  h.vy = vy;
+  h.ecur = ecur;
+  h.nxt_z = ecur < eend ? entries[ecur].z : INT_MAX;
+  return h;
+}
+__device__ __noinline__ SourceHitsXp source_hits_xp_call(const int4 *entries,
+                                                         const float *src_scale, const float *wav,
+                                                         int nsrc, int nc, int ecur, int eend,
+                                                         int zc, int ybase, int ny, int x,
+                                                         int lane, int64_t nstep, float4 vx,
+                                                         float4 vy) {
+  return source_hits_xp(entries, src_scale, wav, nsrc, nc, ecur, eend, zc, ybase, ny, x, lane,
+                        nstep, vx, vy);
+}
+
+template <int R, int NY, int EQ, bool ISO>
 __global__ void __launch_bounds__(kTmaThreads, xp_minb(R, NY))
-k_diffusion3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXpTX + 2·HXB wide)
-                 const __grid_constant__ CUtensorMap, const __grid_constant__ CUtensorMap,
-                 const __grid_constant__ CUtensorMap, const __grid_constant__ CUtensorMap,
-                 const __grid_constant__ CUtensorMap, const TmaArgs args, const BatchArgs) {
+k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXpTX + 2·HXB wide)
+               const __grid_constant__ CUtensorMap map_p,  // u^{n-1}, tile box (kXpTX wide)
+               const __grid_constant__ CUtensorMap map_a,  // A, tile box
+               const __grid_constant__ CUtensorMap map_c,  // C, tile box
+               const __grid_constant__ CUtensorMap, const __grid_constant__ CUtensorMap,
+               const TmaArgs args, const BatchArgs) {
+  constexpr bool AC = EQ == kAcoustic;
   constexpr int TY = tma_ty(NY);
-  constexpr int HXB = tma_hxb(R), BW = xp_bw(R), DU = tma_du(R);
+  constexpr int HXB = tma_hxb(R), BW = xp_bw(R), DU = tma_du(R), DX = kTmaDX;
   constexpr int USLOT = tma_align128(xp_ubytes(R, NY)) / 4;  // floats per ring-U slot
+  constexpr int XT = kXpTX * TY;                              // floats per ring-X tile
   constexpr int Q = 2 * R + 1;
   constexpr int U = tma_unroll(R);
   constexpr int QL = U == Q ? Q : Q + U - 1;
   constexpr bool kSplit = R > 4;
+  constexpr bool kUnitC = AC && R <= 4;
   constexpr int PH = (R + 1) / 2;  // x pairs each side of the lane's own
+  static_assert(NY <= 4, "source rows are carried in a float4");
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t *full_u = reinterpret_cast<uint64_t *>(smem);
   uint64_t *empty_u = full_u + DU;
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(empty_u + DU);
+  uint64_t *full_x = empty_u + DU;
+  uint64_t *empty_x = full_x + DX;
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(empty_x + DX);
   float *ring_u = reinterpret_cast<float *>(smem + 1024);
+  float *ring_x = ring_u + DU * USLOT;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int *const err = args.err;
@@ -820,6 +888,10 @@ k_diffusion3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (k
     for (int i = 0; i < DU; ++i) {
       mbar_init(&full_u[i], 1);
       mbar_init(&empty_u[i], kTmaNW);
+    }
+    for (int i = 0; i < DX; ++i) {
+      mbar_init(&full_x[i], 1);
+      mbar_init(&empty_x[i], kTmaNW);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -833,13 +905,19 @@ k_diffusion3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (k
               gridDim.x, q0, q1);
   else
     cta_range(args.W, blockIdx.x, gridDim.x, q0, q1);
+  const unsigned char *ucf = kUnitC ? args.unit_c : nullptr;
 
   if (warp == kTmaNW) {
     // ------------------------------- producer -------------------------------
     if (lane == 0) {
       tma_prefetch_desc(&map_u);
-      uint32_t su = 0;
-      const uint64_t keep = l2_policy_evict_last();
+      if (AC) {
+        tma_prefetch_desc(&map_p);
+        tma_prefetch_desc(&map_a);
+        tma_prefetch_desc(&map_c);
+      }
+      uint32_t su = 0, sx = 0;
+      const uint64_t keep = l2_policy_evict_last(), once = l2_policy_evict_first();
       bool ok = true;
       int64_t q = q0;
       while (ok && q < q1) {
@@ -848,6 +926,23 @@ k_diffusion3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (k
         const int x0 = (tile % args.tiles_x) * kXpTX, y0 = (tile / args.tiles_x) * TY;
         for (int p = za - R; p < zb + R; ++p) {
           if (*abort_flag) { ok = false; break; }
+          const int zc = p - R;
+          if (AC && zc >= za) {
+            const uint32_t slot = sx % DX;
+            if (sx >= (uint32_t)DX && !mbar_wait(&empty_x[slot], ((sx / DX) - 1) & 1)) {
+              ok = false;
+              break;
+            }
+            float *dst = ring_x + slot * 3 * XT;
+            const bool cone = kUnitC && ucf && ucf[(int64_t)tile * args.g.n0 + zc];
+            mbar_expect_tx(&full_x[slot], (3 - (cone ? 1 : 0)) * XT * 4);
+            tma_load_3d_hint(dst, &map_p, x0 + kHaloX, y0 + R, zc + R, &full_x[slot], once);
+            tma_load_3d_hint(dst + XT, &map_a, x0 + kHaloX, y0 + R, zc + R, &full_x[slot], once);
+            if (!cone)
+              tma_load_3d_hint(dst + 2 * XT, &map_c, x0 + kHaloX, y0 + R, zc + R, &full_x[slot],
+                               once);
+            ++sx;
+          }
           const uint32_t slot = su % DU;
           if (su >= (uint32_t)DU && !mbar_wait(&empty_u[slot], ((su / DU) - 1) & 1)) {
             ok = false;
@@ -866,6 +961,10 @@ k_diffusion3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (k
         const uint32_t last = su - 1 - ((su - 1 - i) % DU);  // last fill of slot i
         drained &= mbar_wait(&full_u[last % DU], (last / DU) & 1);
       }
+      for (uint32_t i = 0; i < (uint32_t)DX && i < sx; ++i) {
+        const uint32_t last = sx - 1 - ((sx - 1 - i) % DX);
+        drained &= mbar_wait(&full_x[last % DX], (last / DX) & 1);
+      }
       if (!drained && atomicCAS(err, 0, 3) == 0) err[1] = blockIdx.x;
     }
     return;
@@ -873,25 +972,37 @@ k_diffusion3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (k
 
   // --------------------------------- consumers --------------------------------
   float2 qp[NY][QL];  // queue: row j, the lane's x pair
-  uint32_t su = 0;
+  uint32_t su = 0, sx = 0;
   const int row0 = warp * NY;
   const float2 *wp0 = args.c.wp[0], *wp1 = args.c.wp[1], *wp2 = args.c.wp[2];
   const Geom g = args.g;
+  const SparseArgs sp = args.sp;
+  const int64_t nstep = (AC && sp.step) ? *sp.step + sp.j : 0;
   float *const out = args.out;
   int64_t q = q0;
   while (q < q1) {
     int tile, za, zb;
     next_segment(args, q, q1, tile, za, zb);
+    const int n0 = g.n0;
     const int x = (tile % args.tiles_x) * kXpTX + 2 * lane;
     const int ybase = (tile / args.tiles_x) * TY + row0;
-    const bool xin0 = x > 0 && x < g.n2 - 1, xin1 = x + 1 > 0 && x + 1 < g.n2 - 1;
+    // which of the pair's points a row stores: acoustic every node, diffusion
+    // interior nodes only
+    const bool xin0 = AC ? x < g.n2 : (x > 0 && x < g.n2 - 1);
+    const bool xin1 = AC ? x + 1 < g.n2 : (x + 1 > 0 && x + 1 < g.n2 - 1);
     unsigned rows_ok = 0;
 #pragma unroll
     for (int j = 0; j < NY; ++j) {
       const int y = ybase + j;
-      rows_ok |= ((y > 0 && y < g.n1 - 1) ? 1u : 0u) << j;
+      rows_ok |= ((AC ? y < g.n1 : (y > 0 && y < g.n1 - 1)) ? 1u : 0u) << j;
     }
     float *optr = out + gidx(g, za, ybase, x);
+    int ecur = 0, eend = 0, nxt_z = INT_MAX;
+    if (AC && sp.first) {
+      ecur = sp.first[tile * n0 + za];
+      eend = sp.first[tile * n0 + zb];
+      if (ecur < eend) nxt_z = sp.entries[ecur].z;
+    }
     // warm-up: planes za-R .. za+R-1 fill queue slots 0 .. 2R-1
 #pragma unroll
     for (int m = 0; m < 2 * R; ++m) {
@@ -924,6 +1035,14 @@ k_diffusion3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (k
               qp[j][tma_qslot<U, Q>(ph, 2 * R)] = *reinterpret_cast<const float2 *>(pl + j * BW);
             const uint32_t cs = (su - R) % DU;  // ring-U slot holding plane zc
             const float *cp = ring_u + cs * USLOT + row0 * BW + HXB + 2 * lane;
+            const float *xs = nullptr;
+            uint32_t xslot = 0;
+            if (AC) {
+              xslot = sx % DX;
+              if (!mbar_wait(&full_x[xslot], (sx / DX) & 1)) goto timeout;
+              xs = ring_x + xslot * 3 * XT + row0 * kXpTX + 2 * lane;
+            }
+            const bool cone = kUnitC && ucf && ucf[(int64_t)tile * n0 + zc];
             float2 ycol[NY + 2 * R];  // the lane's pair, rows row0-R .. row0+NY-1+R
 #pragma unroll
             for (int r = 0; r < NY + 2 * R; ++r) ycol[r] = *reinterpret_cast<const float2 *>(cp + r * BW);
@@ -949,11 +1068,11 @@ k_diffusion3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (k
                 const float2 nuc6 = __fmul2_rn(make_float2(-6.f, -6.f), uc);
 #pragma unroll
                 for (int k = 1; k <= R; ++k) {
-                  const float2 sx = xsum(k);
+                  const float2 sx2 = xsum(k);
                   const float2 sy = __fadd2_rn(ycol[R + j + k], ycol[R + j - k]);
                   const float2 sz = __fadd2_rn(qp[j][tma_qslot<U, Q>(ph, R + k)],
                                                qp[j][tma_qslot<U, Q>(ph, R - k)]);
-                  const float2 dd = __fadd2_rn(__fadd2_rn(__fadd2_rn(sx, sy), sz), nuc6);
+                  const float2 dd = __fadd2_rn(__fadd2_rn(__fadd2_rn(sx2, sy), sz), nuc6);
                   if ((k & 1) || !kSplit)
                     lo = __ffma2_rn(wp2[k], dd, lo);
                   else
@@ -980,10 +1099,38 @@ k_diffusion3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (k
                 }
               }
               const float2 lap = kSplit ? __fadd2_rn(lo, le) : lo;
-              val[j] = __fadd2_rn(uc, lap);
+              if (AC) {
+                // u^{n+1} = A·lap + (1 + C)·u − C·u^{n−1}, per point as k_stencil3d_tma
+                const float2 up = *reinterpret_cast<const float2 *>(xs + j * kXpTX);
+                const float2 a = *reinterpret_cast<const float2 *>(xs + XT + j * kXpTX);
+                const float2 cc = cone ? make_float2(1.f, 1.f)
+                                       : *reinterpret_cast<const float2 *>(xs + 2 * XT + j * kXpTX);
+                val[j].x = fmaf(a.x, lap.x, fmaf(1.f + cc.x, uc.x, -cc.x * up.x));
+                val[j].y = fmaf(a.y, lap.y, fmaf(1.f + cc.y, uc.y, -cc.y * up.y));
+              } else {
+                val[j] = __fadd2_rn(uc, lap);
+              }
             }
-            // interior nodes only: boundary values stay as set
-            if (zc > 0 && zc < g.n0 - 1) {
+            if (AC && nxt_z == zc) {
+              // source corners at this tile-plane (most planes have none)
+              float4 vx = make_float4(val[0].x, 0.f, 0.f, 0.f), vy = make_float4(val[0].y, 0.f, 0.f, 0.f);
+              if constexpr (NY > 1) { vx.y = val[1].x; vy.y = val[1].y; }
+              if constexpr (NY > 2) { vx.z = val[2].x; vy.z = val[2].y; }
+              if constexpr (NY > 3) { vx.w = val[3].x; vy.w = val[3].y; }
+              const SourceHitsXp h =
+                  R > 4 ? source_hits_xp_call(sp.entries, sp.src_scale, sp.wav, sp.nsrc, sp.nc,
+                                              ecur, eend, zc, ybase, NY, x, lane, nstep, vx, vy)
+                        : source_hits_xp(sp.entries, sp.src_scale, sp.wav, sp.nsrc, sp.nc, ecur,
+                                         eend, zc, ybase, NY, x, lane, nstep, vx, vy);
+              val[0] = make_float2(h.vx.x, h.vy.x);
+              if constexpr (NY > 1) val[1] = make_float2(h.vx.y, h.vy.y);
+              if constexpr (NY > 2) val[2] = make_float2(h.vx.z, h.vy.z);
+              if constexpr (NY > 3) val[3] = make_float2(h.vx.w, h.vy.w);
+              ecur = h.ecur;
+              nxt_z = h.nxt_z;
+            }
+            // diffusion: interior planes only (boundary values stay as set)
+            if (AC || (zc > 0 && zc < n0 - 1)) {
 #pragma unroll
               for (int j = 0; j < NY; ++j) {
                 if (!(rows_ok & (1u << j))) continue;
@@ -999,9 +1146,11 @@ k_diffusion3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (k
             optr += g.plane;
             __syncwarp();
             if (lane == 0) {
+              if (AC) mbar_arrive(&empty_x[xslot]);
               mbar_arrive(&empty_u[cs]);
               if (zc + R >= zb) mbar_arrive(&empty_u[slot]);  // trailing plane: queue only
             }
+            if (AC) ++sx;
             ++su;
             ++i;
           }
@@ -1116,11 +1265,11 @@ inline cudaError_t tma_configure(TmaPlan &pl, int ny) {
   return cudaSuccess;
 }
 
-// The x-pair diffusion kernel for rows-per-thread ny.
-template <int R, bool ISO>
+// The x-pair kernel for rows-per-thread ny.
+template <int R, int EQ, bool ISO>
 inline cudaError_t xp_configure(TmaPlan &pl, int ny) {
-  TmaKernelFn fn = ny == 2 ? k_diffusion3d_xp<R, 2, ISO> : k_diffusion3d_xp<R, 4, ISO>;
-  const int smem = ny == 2 ? xp_smem_bytes(R, 2) : xp_smem_bytes(R, 4);
+  TmaKernelFn fn = ny == 2 ? k_stencil3d_xp<R, 2, EQ, ISO> : k_stencil3d_xp<R, 4, EQ, ISO>;
+  const int smem = xp_smem_bytes(R, ny, EQ == kAcoustic);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl.per_sm_max, fn, kTmaThreads, smem);
@@ -1141,9 +1290,7 @@ inline cudaError_t xp_configure(TmaPlan &pl, int ny) {
 
 // Tile configurations the pipelined kernel offers (the autotuner's space).
 inline bool tma_ny_supported(int ny) { return ny == 2 || ny == 4; }
-inline bool tma_tx_supported(int tx, int eq) {
-  return tx == kTmaTX || (tx == kXpTX && eq == kDiffusion);
-}
+inline bool tma_tx_supported(int tx, int) { return tx == kTmaTX || tx == kXpTX; }
 
 // Build the plan: tensor maps for both levels and the coefficient fields, for
 // ny rows per consumer thread (0: the default), a grid of per_sm CTAs per SM
@@ -1180,15 +1327,15 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float 
   const bool xp = tx == kXpTX;
   for (int b = 0; b < 2; ++b) {
     if (!encode_map(enc, &pl.map_u[b], level[b], g, xp ? xp_bw(R) : tma_bw(R), tma_bh(R, ny)) ||
-        !encode_map(enc, &pl.map_t[b], level[b], g, kTmaTX, ty)) {
+        !encode_map(enc, &pl.map_t[b], level[b], g, tx, ty)) {
       *why = "tensor map encoding failed";
       return cudaErrorInvalidValue;
     }
     pl.level[b] = level[b];
   }
   if (eq == kAcoustic) {
-    if (!encode_map(enc, &pl.map_a, A, g, kTmaTX, ty) ||
-        !encode_map(enc, &pl.map_c, C, g, kTmaTX, ty)) {
+    if (!encode_map(enc, &pl.map_a, A, g, tx, ty) ||
+        !encode_map(enc, &pl.map_c, C, g, tx, ty)) {
       *why = "tensor map encoding failed";
       return cudaErrorInvalidValue;
     }
@@ -1207,7 +1354,10 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float 
     break;
 #define XP_CASE(RR)                                                                    \
   case RR:                                                                             \
-    e = iso ? xp_configure<RR, true>(pl, ny) : xp_configure<RR, false>(pl, ny);        \
+    e = ac ? (iso ? xp_configure<RR, kAcoustic, true>(pl, ny)                          \
+                  : xp_configure<RR, kAcoustic, false>(pl, ny))                        \
+           : (iso ? xp_configure<RR, kDiffusion, true>(pl, ny)                         \
+                  : xp_configure<RR, kDiffusion, false>(pl, ny));                      \
     break;
   if (xp) {
     switch (R) { XP_CASE(1) XP_CASE(2) XP_CASE(3) XP_CASE(4) XP_CASE(5) XP_CASE(6) XP_CASE(7) XP_CASE(8) }

@@ -148,7 +148,7 @@ class Solver:
         cached: reuse the process's earlier choice for this problem if there is
         one (``tried`` is then empty)."""
         self._in()
-        out = B.fd_autotune(self.ctx, reps=reps, fwi=fwi, max_tried=0 if cached else 64)
+        out = B.fd_autotune(self.ctx, reps=reps, fwi=fwi, max_tried=0 if cached else 256)
         self._out()
         return out
 

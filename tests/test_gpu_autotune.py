@@ -49,18 +49,19 @@ def _configs(shape, so):
     from paper_1906_10811_b300.binding import FdError
     out = []
     s = Solver(shape, (10.0,) * 3, so, 0.1, "acoustic", kernel="tma")
-    for ty in (16, 32):
-        for cps in (1, 2, 3):
-            for zb in (0, 3, 11, shape[0]):
-                for al in (0, 1):
-                    for sk in ((0, 1) if so <= 8 else (0,)):
-                        try:
-                            s.set_tile_config(tile_y=ty, ctas_per_sm=cps, zblock=zb, aligned=al,
-                                              skip_c=sk)
-                        except FdError:
-                            continue
-                        out.append(dict(tile_y=ty, ctas_per_sm=cps, zblock=zb, aligned=al,
-                                        skip_c=sk))
+    for tx in (32, 64):
+        for ty in (16, 32):
+            for cps in (1, 2, 3):
+                for zb in (0, 3, 11, shape[0]):
+                    for al in (0, 1):
+                        for sk in ((0, 1) if so <= 8 else (0,)):
+                            try:
+                                s.set_tile_config(tile_y=ty, ctas_per_sm=cps, zblock=zb,
+                                                  aligned=al, skip_c=sk, tile_x=tx)
+                            except FdError:
+                                continue
+                            out.append(dict(tile_y=ty, ctas_per_sm=cps, zblock=zb, aligned=al,
+                                            skip_c=sk, tile_x=tx))
     s.close()
     return out
 
@@ -72,9 +73,11 @@ def test_every_tile_configuration_is_bitwise_the_default(so, shape):
     cfgs = _configs(shape, so)
     heights = {c["tile_y"] for c in cfgs}
     assert heights == {16, 32}, cfgs
+    assert {c["tile_x"] for c in cfgs} == {32, 64}, cfgs
     for cfg in cfgs:
         u, up, rec, used = _acoustic(p, 60, cfg)
         assert used["tile_y"] == cfg["tile_y"] and used["ctas_per_sm"] == cfg["ctas_per_sm"]
+        assert used["tile_x"] == cfg["tile_x"]
         assert used["aligned"] == cfg["aligned"] and used["skip_c"] == cfg["skip_c"]
         if cfg["zblock"]:
             assert used["zblock"] == min(cfg["zblock"], shape[0])
@@ -147,7 +150,8 @@ def test_bad_tile_configurations_are_rejected_and_keep_the_current_one():
     s = Solver((20, 24, 28), (10.0,) * 3, 8, 0.1, "acoustic", kernel="tma")
     before = s.tile_config
     for bad in (dict(tile_y=24), dict(tile_y=64), dict(zblock=-1), dict(ctas_per_sm=-2),
-                dict(ctas_per_sm=64), dict(aligned=2), dict(skip_c=3)):
+                dict(ctas_per_sm=64), dict(aligned=2), dict(skip_c=3), dict(tile_x=48),
+                dict(tile_x=16)):
         with pytest.raises(FdError) as e:
             s.set_tile_config(**bad)
         assert e.value.status == FD_EINVAL
@@ -168,13 +172,13 @@ def test_a_tuned_shot_joins_a_batch_at_the_default_tile():
     s.set_model(p["m"], p["damp"])
     s.set_sources(p["src_coords"], p["wavelet"])
     s.set_receivers(p["rec_coords"])
-    s.set_tile_config(tile_y=16, zblock=9)
+    s.set_tile_config(tile_y=16, zblock=9, tile_x=64)
     s.run(20)
     b = Batch(8)
     b.add(s)
     b.run(30)
     b.remove(s)
-    assert s.tile_config["tile_y"] == 32
+    assert s.tile_config["tile_y"] == 32 and s.tile_config["tile_x"] == 32
     u, rec = s.read()
     up = s.read_prev()
     b.close()
@@ -243,15 +247,16 @@ def test_diffusion_x_pair_tiles_are_bitwise_the_default(so, spacing, boundary):
         assert np.array_equal(u, outs[0])
 
 
-def test_x_pair_tiles_only_for_diffusion_and_tuned_there():
+def test_x_pair_tiles_are_tuned():
     from paper_1906_10811_b300 import Solver
-    from paper_1906_10811_b300.binding import FdError
-    p = small_problem((30, 33, 35), 8, 10, nrec=3)
-    with Solver(p["shape"], p["spacing"], 8, p["dt"], "acoustic", kernel="tma") as s:
-        with pytest.raises(FdError):
-            s.set_tile_config(tile_x=64)
-        with pytest.raises(FdError):
-            s.set_tile_config(tile_x=48)
+    p = small_problem((48, 64, 150), 12, 10, nrec=3)
+    with Solver(p["shape"], p["spacing"], 12, p["dt"], "acoustic", kernel="tma") as s:
+        s.set_model(p["m"], p["damp"])
+        best, tried = s.autotune(reps=2)
+        assert {t["tile_x"] for t in tried} == {32, 64}
+        assert s.tile_config["tile_x"] == best["tile_x"]
+        _, tried = s.autotune(reps=2, fwi=True)   # the FWI sweep has no x-pair instance
+        assert {t["tile_x"] for t in tried} == {32}
     with Solver((40, 48, 150), (1.0 / 40,) * 3, 8, 0.1 * (1.0 / 40) ** 2, "diffusion",
                 kernel="tma") as s:
         s.set_field(np.ones((40, 48, 150), np.float32))
