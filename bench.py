@@ -65,7 +65,7 @@ NCU_TRAFFIC = {
     ("stencil3d_tma_acoustic", "acoustic256", 8, 32, 32, 64, 2, 1, 1): 313.55e6,
     # same file, the x-pair kernel (64 x 32 tiles, 1 CTA/SM): mean of 3 launches, read 298.58 MB
     # + write 26.29 MB
-    ("stencil3d_tma_acoustic", "acoustic256", 8, 64, 32, 64, 1, 1, 0): 324.87e6,
+    ("stencil3d_xp_acoustic", "acoustic256", 8, 64, 32, 64, 1, 1, 0): 324.87e6,
     # profiles/stencil3d_tma_roofline512.md: mean of 2 launches, read 1996.73 MB + write 496.41 MB
     ("stencil3d_tma_acoustic", "roofline512", 8, 32, 32, 512, 2, 1, 1): 2493.14e6,
 }

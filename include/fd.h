@@ -314,8 +314,18 @@ fd_status fd_autotune(fd_ctx *ctx, int reps, fd_tile_config *best, fd_tile_confi
 fd_status fd_autotune_fwi(fd_ctx *ctx, int reps, fd_tile_config *best, fd_tile_config *tried,
                           int max_tried, int *ntried);
 
-/* Name of the stencil kernel variant fd_run launches (static string). */
+/* Name of the stencil kernel variant fd_run launches (static string):
+ * "stencil3d_tma_<equation>" (32-wide tiles), "stencil3d_xp_<equation>"
+ * (64-wide tiles, two x points a lane), "stencil3d_plain" or "stencil2d_plain". */
 const char *fd_kernel_name(const fd_ctx *ctx);
+
+/*
+ * Tile-planes of the current tile configuration whose C tile the pipelined
+ * kernel skips (fd_tile_config.skip_c = 1: C = 1 on the whole tile-plane):
+ * *flagged of *total.  Both 0 when skip_c is off, no model is set or the plain
+ * kernel runs.  Synchronises the context stream.
+ */
+fd_status fd_skip_c_planes(fd_ctx *ctx, int64_t *flagged, int64_t *total);
 
 /* CUDA kernels this context has launched so far (kernel nodes of replayed
  * graphs included); -1 for NULL. */

@@ -69,6 +69,7 @@ SIGNATURES = {
     "fd_steps_done": (_i64, [_vp]),
     "fd_profile": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double)]),
     "fd_kernel_name": (ctypes.c_char_p, [_vp]),
+    "fd_skip_c_planes": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "fd_get_tile_config": (ctypes.c_int, [_vp, ctypes.POINTER(fd_tile_config)]),
     "fd_set_tile_config": (ctypes.c_int, [_vp, ctypes.POINTER(fd_tile_config)]),
     "fd_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(fd_tile_config),
@@ -253,6 +254,13 @@ def fd_kernel_name(ctx):
     return load().fd_kernel_name(ctx).decode()
 
 
+def fd_skip_c_planes(ctx):
+    """(flagged, total): tile-planes whose C tile the pipelined kernel skips."""
+    f, t = _i64(), _i64()
+    _check(ctx, load().fd_skip_c_planes(ctx, ctypes.byref(f), ctypes.byref(t)))
+    return int(f.value), int(t.value)
+
+
 def fd_get_tile_config(ctx):
     """The pipelined kernel's tile configuration as a dict."""
     cfg = fd_tile_config()
@@ -396,19 +404,43 @@ def fd_acoustic_run_noalloc(shape, spacing, space_order, dt, m, damp, u_cur, u_p
                             u_prev_out=None, cuda_stream=None):
     """No-allocation acoustic run on caller-owned device tensors (see include/fd.h).
 
-    For callers that cannot allocate GPU memory; all array arguments are torch
-    CUDA tensors (float32, contiguous) or raw device addresses.
+    For callers that cannot allocate GPU memory.  Every array argument is a
+    float32, C-contiguous torch CUDA tensor on the current device holding
+    prod(shape) elements (damp, u_prev and u_prev_out may be None); anything
+    else raises before the library is called, since the library receives bare
+    pointers and cannot check sizes itself.  Nothing is converted or copied
+    here.  cuda_stream: a torch stream or a cudaStream_t handle; default the
+    current torch stream, so that work queued there before the call (the
+    tensors' producers) is ordered before it.
     """
-    for x in (m, damp, u_cur, u_prev, u_out, u_prev_out):
-        if x is not None and not (hasattr(x, "is_cuda") and x.is_cuda):
-            raise TypeError("fd_acoustic_run_noalloc takes torch CUDA tensors only")
+    import torch
+    n = int(np.prod([int(x) for x in shape])) if len(shape) else 0
+    dev = torch.cuda.current_device()
+    args = dict(m=m, damp=damp, u_cur=u_cur, u_prev=u_prev, u_out=u_out, u_prev_out=u_prev_out)
+    for name, x in args.items():
+        if x is None:
+            if name in ("m", "u_cur", "u_out"):
+                raise ValueError(f"{name} is required")
+            continue
+        if not isinstance(x, torch.Tensor) or not x.is_cuda:
+            raise TypeError(f"{name}: fd_acoustic_run_noalloc takes torch CUDA tensors only")
+        if x.dtype != torch.float32 or not x.is_contiguous():
+            raise TypeError(f"{name}: must be float32 and contiguous (no conversion is made)")
+        if x.device.index != dev:
+            raise ValueError(f"{name} is on cuda:{x.device.index}, the current device is cuda:{dev}")
+        if x.numel() != n:
+            raise ValueError(f"{name} holds {x.numel()} elements, the grid has {n}")
+    if cuda_stream is None:
+        cuda_stream = torch.cuda.current_stream().cuda_stream
+    elif hasattr(cuda_stream, "cuda_stream"):
+        cuda_stream = cuda_stream.cuda_stream
     lib = load()
     nd = len(shape)
     shp = (_i64 * nd)(*[int(x) for x in shape])
     sp = (ctypes.c_double * nd)(*[float(h) for h in spacing])
-    keep = []
-    st = lib.fd_acoustic_run_noalloc(nd, shp, sp, int(space_order), float(dt), _ptr(m, keep),
-                                     _ptr(damp, keep), _ptr(u_cur, keep), _ptr(u_prev, keep),
-                                     int(nt), _out_ptr(u_out), _out_ptr(u_prev_out), cuda_stream)
+    ptr = lambda x: None if x is None else x.data_ptr()
+    st = lib.fd_acoustic_run_noalloc(nd, shp, sp, int(space_order), float(dt), ptr(m), ptr(damp),
+                                     ptr(u_cur), ptr(u_prev), int(nt), ptr(u_out),
+                                     ptr(u_prev_out), cuda_stream)
     if st != FD_OK:
         raise FdError(st, lib.fd_last_error(None).decode())

@@ -656,6 +656,7 @@ fd_status replan(fd_ctx *c, int ny, int per_sm, int zblock, int aligned, int ski
   CU(cudaStreamSynchronize(c->stream));
   drop_graphs(c);
   c->tma = p;
+  c->kernel_name = c->tma.name;  // the variant fd_run now launches (tile width)
   c->skip_c = skip_c && c->eq == FD_ACOUSTIC && c->g.R <= 4;
   c->sp_dirty = true;
   c->unit_c_dirty = true;
@@ -1298,6 +1299,26 @@ fd_status fd_autotune_fwi(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_con
 }
 
 const char *fd_kernel_name(const fd_ctx *c) { return c ? c->kernel_name : "none"; }
+
+fd_status fd_skip_c_planes(fd_ctx *c, int64_t *flagged, int64_t *total) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  if (!flagged || !total) return fail(c, FD_EINVAL, "flagged/total is NULL");
+  *flagged = 0;
+  *total = 0;
+  if (!c->use_tma || !c->skip_c || !c->model_set) return FD_OK;
+  st = prepare_unit_c(c);
+  if (st) return st;
+  const size_t n = (size_t)c->tma.args.ntiles * c->g.n0;
+  std::vector<unsigned char> h(n);
+  CU(cudaMemcpyAsync(h.data(), c->unit_c, n, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  int64_t k = 0;
+  for (unsigned char f : h) k += f ? 1 : 0;
+  *flagged = k;
+  *total = (int64_t)n;
+  return FD_OK;
+}
 
 int64_t fd_field_elems(const fd_ctx *c) { return c ? c->g.total : -1; }
 
@@ -2128,7 +2149,10 @@ extern "C" fd_status fd_acoustic_run_noalloc(int ndim, const int64_t *shape, con
     if (!(spacing[d] > 0.0) || !std::isfinite(spacing[d]))
       return fail(nullptr, FD_EINVAL, "spacing[%d] must be positive and finite", d);
   }
-  // every array argument must be device memory (a host address would fault the kernels)
+  // every array argument must be device memory of the current device (a host
+  // address, or another GPU's memory, would be read and written from the wrong place)
+  int cur_dev = 0;
+  NA_CU(cudaGetDevice(&cur_dev));
   const void *ptrs[6] = {m, damp, u_cur, u_prev, u_out, u_prev_out};
   for (const void *q : ptrs) {
     if (!q) continue;
@@ -2138,6 +2162,9 @@ extern "C" fd_status fd_acoustic_run_noalloc(int ndim, const int64_t *shape, con
       cudaGetLastError();
       return fail(nullptr, FD_EINVAL, "array arguments must be device pointers");
     }
+    if (at.type == cudaMemoryTypeDevice && at.device != cur_dev)
+      return fail(nullptr, FD_EINVAL, "array argument on device %d, the current device is %d",
+                  at.device, cur_dev);
   }
   const int R = space_order / 2;
   Geom g{};

@@ -1404,7 +1404,8 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float 
     const int64_t zb = zblock ? zblock : std::max<int64_t>(1, share);
     pl.args.zblock = (int)std::min<int64_t>(g.n0, zb);
   }
-  pl.name = ac ? "stencil3d_tma_acoustic" : "stencil3d_tma_diffusion";
+  pl.name = ac ? (xp ? "stencil3d_xp_acoustic" : "stencil3d_tma_acoustic")
+              : (xp ? "stencil3d_xp_diffusion" : "stencil3d_tma_diffusion");
   return cudaSuccess;
 }
 

@@ -129,6 +129,13 @@ class Solver:
     def kernel_launches(self):
         return B.fd_kernel_launches(self.ctx)
 
+    def skipped_c_planes(self):
+        """(flagged, total): tile-planes whose C tile the pipelined kernel skips."""
+        self._in()
+        out = B.fd_skip_c_planes(self.ctx)
+        self._out()
+        return out
+
     # -- tile configuration of the pipelined 3-D kernel ----------------------
     @property
     def tile_config(self):

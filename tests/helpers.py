@@ -14,8 +14,11 @@ def rel_l2(a, b):
 
 
 def gpu_acoustic(p, nt, kernel="auto", graphs=True, profile=False, device=False, damp=True,
-                 with_src=True, with_rec=True, chunks=None):
-    """Run a problem dict from fdsynth.acoustic_problem through the C ABI."""
+                 with_src=True, with_rec=True, chunks=None, tile=None):
+    """Run a problem dict from fdsynth.acoustic_problem through the C ABI.
+
+    tile: a tile configuration for the pipelined kernel (Solver.set_tile_config
+    keywords), set once sources and receivers are in place."""
     from paper_1906_10811_b300 import Solver
     s = Solver(p["shape"], p["spacing"], p["so"], p["dt"], "acoustic", kernel=kernel,
                graphs=graphs, profile=profile, device=device)
@@ -25,6 +28,10 @@ def gpu_acoustic(p, nt, kernel="auto", graphs=True, profile=False, device=False,
         s.set_sources(conv(p["src_coords"]), conv(p["wavelet"]))
     if with_rec:
         s.set_receivers(conv(p["rec_coords"]))
+    if tile is not None:
+        s.set_tile_config(**tile)
+    used = s.tile_config if s.kernel_name.startswith("stencil3d_") and \
+        s.kernel_name != "stencil3d_plain" else None
     for n in (chunks or [nt]):
         s.run(n)
     u, rec = s.read()
@@ -35,7 +42,7 @@ def gpu_acoustic(p, nt, kernel="auto", graphs=True, profile=False, device=False,
     if device:
         u, up = u.cpu().numpy(), up.cpu().numpy()
         rec = rec.cpu().numpy() if rec is not None else None
-    return dict(u=u, u_prev=up, rec=rec, kernel=name, profile=prof)
+    return dict(u=u, u_prev=up, rec=rec, kernel=name, profile=prof, tile=used)
 
 
 def oracle_acoustic(p, nt, damp=True, with_src=True, with_rec=True):

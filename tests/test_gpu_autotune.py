@@ -255,6 +255,8 @@ def test_x_pair_tiles_are_tuned():
         best, tried = s.autotune(reps=2)
         assert {t["tile_x"] for t in tried} == {32, 64}
         assert s.tile_config["tile_x"] == best["tile_x"]
+        assert s.kernel_name == ("stencil3d_xp_acoustic" if best["tile_x"] == 64 else
+                                 "stencil3d_tma_acoustic")
         _, tried = s.autotune(reps=2, fwi=True)   # the FWI sweep has no x-pair instance
         assert {t["tile_x"] for t in tried} == {32}
     with Solver((40, 48, 150), (1.0 / 40,) * 3, 8, 0.1 * (1.0 / 40) ** 2, "diffusion",
@@ -263,3 +265,49 @@ def test_x_pair_tiles_are_tuned():
         best, tried = s.autotune(reps=2)
         assert {t["tile_x"] for t in tried} == {32, 64}
         assert s.tile_config["tile_x"] == best["tile_x"]
+
+
+def _undamped_tile_planes(m, damp, dt, tx, ty):
+    """Tile-planes (tx × ty tiles, z by z) where C = (m − σ)/(m + σ), σ = damp·dt/2,
+    evaluated in float32 with correctly rounded operations, is 1 at every point."""
+    sig = damp.astype(np.float32) * np.float32(0.5 * dt)
+    mf = m.astype(np.float32)
+    one = ((mf - sig) / (mf + sig)) == np.float32(1.0)
+    n0, n1, n2 = m.shape
+    k = 0
+    for z in range(n0):
+        for y0 in range(0, n1, ty):
+            for x0 in range(0, n2, tx):
+                k += int(np.all(one[z, y0:y0 + ty, x0:x0 + tx]))
+    return k
+
+
+@pytest.mark.parametrize("so", (4, 8))
+def test_x_pair_tiles_skip_c_where_tile_planes_are_undamped(so):
+    """64-wide tiles with the C tile really skipped: a grid wide enough that whole
+    64 x 32 tile-planes lie inside the damping layer's inner region.  The flags the
+    library computes are the tile-planes where damp = 0 everywhere, and the run is
+    bitwise the one that reads C (x-pair and 32-wide) and within tolerance of the
+    oracle."""
+    import fdsynth
+    from paper_1906_10811_b300 import Solver
+    shape = (40, 80, 200)          # y tile rows 32..63 and x tiles 64..191 are undamped
+    p = fdsynth.acoustic_problem(n=shape, ndim=3, so=so, nbl=6, nt=50, nrec=24, seed=7, f0=0.03)
+    ref = _acoustic(p, 50)                                        # 32-wide default tile
+    noskip = _acoustic(p, 50, dict(tile_x=64, tile_y=32, aligned=1, skip_c=0))
+    cfg = dict(tile_x=64, tile_y=32, aligned=1, skip_c=1)
+    got = _acoustic(p, 50, cfg)
+    assert got[3]["tile_x"] == 64 and got[3]["skip_c"] == 1
+    with Solver(p["shape"], p["spacing"], so, p["dt"], "acoustic", kernel="tma") as s:
+        s.set_model(p["m"], p["damp"])
+        s.set_tile_config(**cfg)
+        flagged, total = s.skipped_c_planes()
+    expect = _undamped_tile_planes(p["m"], p["damp"], p["dt"], 64, 32)
+    assert total == 40 * 3 * 4
+    assert flagged == expect and flagged > 0, (flagged, expect)
+    for a, b, c in zip(got[:3], noskip[:3], ref[:3]):
+        assert np.array_equal(a, b)
+        assert np.array_equal(a, c)
+    o = oracle_acoustic(p, 50)
+    assert rel_l2(got[0], o["u"]) <= TOL_WAVE
+    assert rel_l2(got[2], o["rec"]) <= TOL_WAVE

@@ -1,8 +1,12 @@
-"""Parity at full benchmark sizes, in the launch configuration bench.py times.
+"""Parity at full benchmark sizes, in the launch configurations bench.py times.
 
 * 256³ so 8 shot (damping layer 40, layered model, Ricker source at the centre,
-  256 receivers, 500 steps) against the FP64 oracle on the whole grid: the
-  wavefield and the traces within 1e-4 relative L2.
+  256 receivers, 500 steps) against one FP64 oracle run on the whole grid: the
+  wavefield and the traces within 1e-4 relative L2, for the default 32-wide
+  tile, the tile bench.py's autotuner picked on the B300 (64 x 32 x-pair tiles,
+  64-plane segments, 1 CTA per SM, whole-segment split), the same with the C
+  tile skipped on undamped tile-planes, and whatever the autotuner picks on the
+  box the test runs on.
 * 512³ at so 4/8/12/16: one step from random fields, checked on sampled points
   (random, grid corners, tile and z-block seams) against the oracle evaluated
   point by point on (2R+1)³ windows; and 20 steps at so 8 and 16 against the
@@ -29,22 +33,55 @@ def _lib():
     build.build()
 
 
-def test_full_shot_256_so8_500_steps():
-    from paper_1906_10811_b300 import Solver
+# The tile the bench's autotuner chose for this shot on the B300 (64-wide x-pair
+# tiles, 32 rows, 64-plane segments, one CTA per SM, whole segments).
+BENCH_TILE = dict(tile_x=64, tile_y=32, zblock=64, ctas_per_sm=1, aligned=1, skip_c=0)
+TILES_256 = {
+    "default": None,
+    "bench_xp": BENCH_TILE,
+    "bench_xp_skip_c": dict(BENCH_TILE, skip_c=1),
+    "autotuned": "autotune",
+}
+
+
+@pytest.fixture(scope="module")
+def shot256():
     p = fdsynth.acoustic_problem(n=256, ndim=3, so=8, nbl=40, nt=500, nrec=256, seed=0)
-    with Solver(p["shape"], p["spacing"], 8, p["dt"], "acoustic") as s:
-        s.set_model(p["m"], p["damp"])
-        s.set_sources(p["src_coords"], p["wavelet"])
-        s.set_receivers(p["rec_coords"])
-        s.run(500)
-        u, rec = s.read()
-        assert s.kernel_name == "stencil3d_tma_acoustic"
     ou, _, orec = oracle.acoustic(p["m"], p["dt"], p["spacing"], 8, 500, damp=p["damp"],
                                   src_coords=p["src_coords"], wavelet=p["wavelet"],
                                   rec_coords=p["rec_coords"])
     assert np.abs(orec).max() > 0
-    assert rel_l2(u, ou) <= TOL_WAVE
-    assert rel_l2(rec, orec) <= TOL_WAVE
+    return p, ou, orec
+
+
+@pytest.mark.parametrize("name", list(TILES_256))
+def test_full_shot_256_so8_500_steps(shot256, name):
+    from paper_1906_10811_b300 import Solver
+    p, ou, orec = shot256
+    tile = TILES_256[name]
+    with Solver(p["shape"], p["spacing"], 8, p["dt"], "acoustic") as s:
+        s.set_model(p["m"], p["damp"])
+        s.set_sources(p["src_coords"], p["wavelet"])
+        s.set_receivers(p["rec_coords"])
+        if tile == "autotune":
+            s.autotune(reps=3)
+        elif tile is not None:
+            s.set_tile_config(**tile)
+        used = s.tile_config
+        s.run(500)
+        u, rec = s.read()
+        kname = s.kernel_name
+        skipped = s.skipped_c_planes()
+    if isinstance(tile, dict):
+        for k, v in tile.items():
+            assert used[k] == v, (k, used)
+    assert kname == ("stencil3d_xp_acoustic" if used["tile_x"] == 64 else
+                     "stencil3d_tma_acoustic"), (kname, used)
+    if used["skip_c"]:
+        assert skipped[0] > 0, skipped        # undamped tile-planes really skip C
+    ew, er = rel_l2(u, ou), rel_l2(rec, orec)
+    assert ew <= TOL_WAVE, (used, ew)
+    assert er <= TOL_WAVE, (used, er)
 
 
 def _model_512(so):

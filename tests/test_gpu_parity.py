@@ -187,21 +187,39 @@ def test_acoustic_parity_2d(so, shape):
     assert rel_l2(g["rec"], o["rec"]) <= TOL_WAVE
 
 
-@pytest.mark.parametrize("kernel", ("plain", "auto"))
-def test_acoustic_kernels_many_sources_and_receivers(kernel):
+XP_TILES = {"xp16": dict(tile_x=64, tile_y=16), "xp32_aligned": dict(tile_x=64, tile_y=32, aligned=1,
+                                                                       zblock=7)}
+
+
+@pytest.mark.parametrize("kernel,shape", [("plain", (26, 31, 35)), ("auto", (26, 31, 35)),
+                                          ("xp16", (26, 31, 35)), ("xp16", (21, 40, 131)),
+                                          ("xp32_aligned", (21, 40, 131))])
+def test_acoustic_kernels_many_sources_and_receivers(kernel, shape):
     """Random sources (two sharing a node) and receivers, including points on
-    the grid boundary; enough of them to take the multi-block sparse path."""
-    shape, so, nt = (26, 31, 35), 8, 60
+    the grid boundary; enough of them to take the multi-block sparse path.  The
+    x-pair tiles (a lane per two adjacent x points) also get sources on both
+    points of one lane's pair, on several planes, and x extents of one tile and
+    of two full tiles plus a ragged one."""
+    so, nt = 8, 60
     p = small_problem(shape, so, nt)
     pts = fdsynth.random_points(shape, p["spacing"], 300, seed=5)
     pts[1] = pts[0]
     ext = np.array([(n - 1) * h for n, h in zip(shape, p["spacing"])], dtype=np.float32)
     pts[2] = ext
     pts[3] = 0
+    h = np.array(p["spacing"], dtype=np.float32)
+    for i, (z, y, x) in enumerate([(5, 7, 10), (5, 7, 11), (12, 20, 64), (12, 20, 65),
+                                   (12, 21, 63), (3, 30, 34)]):
+        pts[4 + i] = np.array([z, min(y, shape[1] - 1), min(x, shape[2] - 1)], np.float32) * h
     p["src_coords"] = pts
     p["wavelet"] = np.repeat(p["wavelet"], 300, axis=1) * np.linspace(0.5, 1.5, 300, dtype=np.float32)
     p["rec_coords"] = np.vstack([fdsynth.random_points(shape, p["spacing"], 400, seed=6), ext[None], np.zeros((1, 3), np.float32)])
-    g = gpu_acoustic(p, nt, kernel=kernel)
+    tile = XP_TILES.get(kernel)
+    g = gpu_acoustic(p, nt, kernel="auto" if tile else kernel, tile=tile)
+    if tile:
+        assert g["kernel"] == "stencil3d_xp_acoustic" and g["tile"]["tile_x"] == 64, g["tile"]
+        ref = gpu_acoustic(p, nt, kernel="auto")          # 32-wide: bitwise the same
+        assert np.array_equal(g["u"], ref["u"]) and np.array_equal(g["rec"], ref["rec"])
     o = oracle_acoustic(p, nt)
     assert rel_l2(g["u"], o["u"]) <= TOL_WAVE
     assert rel_l2(g["rec"], o["rec"]) <= TOL_WAVE
