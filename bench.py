@@ -53,7 +53,9 @@ WORKLOADS = {
 }
 
 # DRAM bytes per stencil launch from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum, mean of the captured launches), keyed by (kernel name,
+# dram__bytes_write.sum, mean of the captured launches; the captures with ncu's default
+# L2 flush count only the writes that leave L2 during the launch, the warm capture also
+# the previous step's write-backs), keyed by (kernel name,
 # workload, space order, tile width, tile height, z-block height, CTAs per SM, aligned,
 # skip_c); the captures
 # are summarised in profiles/.  Absent (null) when not captured for the kernel
@@ -63,9 +65,10 @@ NCU_TRAFFIC = {
     ("stencil3d_tma_acoustic", "acoustic256", 8, 32, 32, 64, 2, 1, 0): 325.08e6,
     # same file, C skipped where it is 1: mean of 3 launches, read 287.03 MB + write 26.52 MB
     ("stencil3d_tma_acoustic", "acoustic256", 8, 32, 32, 64, 2, 1, 1): 313.55e6,
-    # same file, the x-pair kernel (64 x 32 tiles, 1 CTA/SM): mean of 3 launches, read 298.58 MB
-    # + write 26.29 MB
-    ("stencil3d_xp_acoustic", "acoustic256", 8, 64, 32, 64, 1, 1, 0): 324.87e6,
+    # profiles/stencil3d_xp_acoustic256_so8.md, the x-pair kernel (64 x 32 tiles, 1 CTA/SM),
+    # L2 not flushed between launches (the bench's conditions): mean of 3 launches, read
+    # 289.07 MB + write 67.57 MB
+    ("stencil3d_xp_acoustic", "acoustic256", 8, 64, 32, 64, 1, 1, 0): 356.64e6,
     # profiles/stencil3d_tma_roofline512.md: mean of 2 launches, read 1996.73 MB + write 496.41 MB
     ("stencil3d_tma_acoustic", "roofline512", 8, 32, 32, 512, 2, 1, 1): 2493.14e6,
 }
@@ -97,6 +100,9 @@ def parse():
                          "diffusion x-pair kernel) given explicitly")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--extras", default="sweep512,serving,fwi320,c1,oracle",
+                    help="default workload, one GPU: legs measured after the main timed region "
+                         "and added to its line (comma list; empty for none)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
 
@@ -352,13 +358,9 @@ def fwi_oracle_sample(budget_s):
     return value, f"{runs} FP64 oracle gradients of a 40^3, so 8, 60-step shot of the same recipe ({total:.1f} s)"
 
 
-def run_fwi(args):
+def fwi_result(args, world=1, rank=0, local=0):
+    """Whole FWI gradients of the 320³ shot, timed: the result line."""
     import torch
-    world, rank, local = dist_setup(args)
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1906_10811_b300 import build, fwi
     build.build()
     w, p = fwi_problem(args)
@@ -450,18 +452,29 @@ def run_fwi(args):
         v, sample = fwi_oracle_sample(args.cpu_seconds)
         cpu = {"value": round(v, 5), "unit": "GPts/s", "cores": cpu_threads(), "kind": "oracle",
                "sample": sample}
+    line = {"metric": "FWI gradient GPts/s (space-time points of the shot per second)",
+            "value": round(value, 3), "unit": "GPts/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(fwi_config(w, k, tuning),
+                           checkpoint_bytes=stats.get("checkpoint_bytes"),
+                           block_bytes=stats.get("block_bytes"), tile=stats.get("tile"),
+                           tile_choice="fd_autotune_fwi (plain + d2 + imaging steps)"),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches), "clocks": clk}
+    return line
+
+
+def run_fwi(args):
+    import torch
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    line = fwi_result(args, world, rank, local)
     if rank == 0:
-        line = {"metric": "FWI gradient GPts/s (space-time points of the shot per second)",
-                "value": round(value, 3), "unit": "GPts/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": dict(fwi_config(w, k, tuning),
-                               checkpoint_bytes=stats.get("checkpoint_bytes"),
-                               block_bytes=stats.get("block_bytes"), tile=stats.get("tile"),
-                               tile_choice="fd_autotune_fwi (plain + d2 + imaging steps)"),
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(launches), "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -603,6 +616,205 @@ def run_diffusion(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+SWEEP_ORDERS = (4, 8, 12, 16)
+
+
+def _gpu_uuid():
+    import torch
+    return "GPU-" + str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+
+
+def sweep512_result(reps=2, orders=SWEEP_ORDERS):
+    """512³ roofline sweep on the current torch stream: per space order the autotuned
+    tile, µs per stencil launch (graph-chunk events), the fraction of the measured HBM
+    copy bandwidth at the algorithmic bytes per point, and GPts/s of whole shots
+    (acoustic: coefficient set-up, reset and 200 steps with one source; diffusion:
+    field reset and 200 steps of the sine-mode problem at ν dt/h² = 0.05)."""
+    import torch
+    from paper_1906_10811_b300 import Solver
+    n, nt = 512, 200
+    npts = n ** 3
+    peak, peak_kind = load_peak()
+    stream = torch.cuda.current_stream()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+    def measure(s, shot, bpp):
+        shot()
+        s.profile()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            shot()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        n_st, st_ms = s.profile()
+        avg = st_ms / max(n_st, 1) / 1e3
+        ach = bpp * npts / avg / 1e9
+        t = s.tile_config
+        return {"us_per_launch": round(avg * 1e6, 2), "achieved_gbs": round(ach, 1),
+                "frac": round(ach / peak, 4), "gpts_per_s_kernel": round(npts / avg / 1e9, 2),
+                "gpts_per_s_shot": round(npts * nt * reps / (ms / 1e3) / 1e9, 2),
+                "kernel": s.kernel_name,
+                "tile": {k: t[k] for k in ("tile_x", "tile_y", "zblock", "ctas_per_sm",
+                                           "aligned", "skip_c")}}
+
+    clocks = ClockSampler(_gpu_uuid())
+    p = fdsynth.acoustic_problem(n=n, ndim=3, so=8, nbl=40, nt=nt, nrec=0, seed=0)
+    m_d, damp_d = dev(p["m"]), dev(p["damp"])
+    src_d, wav_d = dev(p["src_coords"]), dev(p["wavelet"])
+    acoustic = {}
+    for so in orders:
+        s = Solver((n,) * 3, p["spacing"], so, p["dt"], "acoustic", device=True, profile=True)
+        s.set_sources(src_d, wav_d)
+        s.set_model(m_d, damp_d)
+        tried = len(s.autotune(reps=3)[1])
+
+        def shot():
+            s.set_model(m_d, damp_d)
+            s.reset()
+            s.run(nt)
+
+        acoustic[f"so{so}"] = dict(measure(s, shot, BYTES_PER_POINT["acoustic"]),
+                                   configs_tried=tried)
+        s.close()
+    del m_d, damp_d
+    torch.cuda.empty_cache()
+    q = fdsynth.diffusion_problem(n, ndim=3, courant=0.05)
+    u0_d = dev(q["u0"])
+    diffusion = {}
+    for so in orders:
+        s = Solver((n,) * 3, q["spacing"], so, q["dt"], "diffusion", nu=q["nu"], device=True,
+                   profile=True)
+        s.set_field(u0_d)
+        tried = len(s.autotune(reps=3)[1])
+
+        def sweep():
+            s.set_field(u0_d)
+            s.set_step(0)
+            s.run(nt)
+
+        diffusion[f"so{so}"] = dict(measure(s, sweep, BYTES_PER_POINT["diffusion"]),
+                                    configs_tried=tried)
+        s.close()
+    del u0_d
+    torch.cuda.empty_cache()
+    return {"grid": [n] * 3, "nt": nt, "shots_timed": reps, "acoustic": acoustic,
+            "diffusion": diffusion, "peak": peak,
+            "peak_source": f"{peak_kind} HBM copy bandwidth (of {peak_kind})",
+            "bytes_per_point": dict(BYTES_PER_POINT),
+            "note": "frac counts the algorithmic bytes per point; with skip_c the undamped "
+                    "tile-planes move 16 of the acoustic 20 B/pt",
+            "clocks": clocks.stop()}
+
+
+def c1_result(reps=20):
+    """Config 1 on the device: 128² diffusion, so 2, 100 steps (L2-resident, launch-bound):
+    latency of one whole run (field upload from device memory, 100 steps, read back)."""
+    import torch
+    from paper_1906_10811_b300 import Solver
+    q = fdsynth.diffusion_problem(128)
+    u0_d = torch.from_numpy(q["u0"]).cuda()
+    with Solver(q["u0"].shape, q["spacing"], 2, q["dt"], "diffusion", nu=q["nu"],
+                device=True) as s:
+        out = torch.empty_like(u0_d)
+        from paper_1906_10811_b300 import binding as B
+
+        def run():
+            s.set_field(u0_d)
+            s.set_step(0)
+            s.run(100)
+            B.fd_read(s.ctx, out, None)
+
+        run()
+        t = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            run()
+            t.append(time.perf_counter() - t0)
+        kname = s.kernel_name
+    ms = 1e3 * statistics.median(t)
+    return {"workload": "diffusion2d_128^2_so2_nt100", "kernel": kname,
+            "ms_per_run_median": round(ms, 4), "us_per_step": round(1e3 * ms / 100, 3),
+            "runs": reps, "note": "host-timed: set_field + 100 graph-replayed steps + read "
+                                  "(synchronising); 64 KB per level, L2-resident"}
+
+
+def oracle_legs(p256):
+    """The oracle timed on the host: single-threaded on the 256³ shot, on config 1 and on
+    the 512³ so 8 step (bounded samples; a subprocess gives the single-thread run its own
+    OpenMP runtime)."""
+    legs = {}
+    code = ("import sys,time,json; sys.path.insert(0, %r); import fdsynth; "
+            "from oracle import core as o; "
+            "p=fdsynth.acoustic_problem(n=256,ndim=3,so=8,nbl=40,nt=500,nrec=256,seed=0); "
+            "k=3; t=time.perf_counter(); "
+            "o.acoustic(p['m'],p['dt'],p['spacing'],8,k,damp=p['damp'],src_coords=p['src_coords'],"
+            "wavelet=p['wavelet'],rec_coords=p['rec_coords']); "
+            "dt=time.perf_counter()-t; print(json.dumps({'steps':k,'s':dt}))" % ROOT)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=600)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        legs["acoustic256_so8_1thread"] = {
+            "value": round(256 ** 3 * d["steps"] / d["s"] / 1e9, 5), "unit": "GPts/s", "cores": 1,
+            "sample": f"first {d['steps']} of 500 time steps of the 256^3 shot ({d['s']:.1f} s, "
+                      f"set-up included)",
+            "extrapolated_shot_s": round(d["s"] / d["steps"] * 500, 1)}
+    except Exception as e:                                   # pragma: no cover
+        legs["acoustic256_so8_1thread"] = {"error": str(e)[:200]}
+    from oracle import core as oracle
+    q = fdsynth.diffusion_problem(128)
+    t0 = time.perf_counter()
+    oracle.diffusion(q["u0"], q["spacing"], 2, q["nu"], q["dt"], 100)
+    tc = time.perf_counter() - t0
+    legs["c1_diffusion128_so2_nt100"] = {"value": round(128 ** 2 * 100 / tc / 1e9, 5),
+                                        "unit": "GPts/s", "cores": cpu_threads(),
+                                        "seconds": round(tc, 4), "sample": "whole run (100 steps)"}
+    p = fdsynth.acoustic_problem(n=512, ndim=3, so=8, nbl=40, nt=200, nrec=0, seed=0)
+    k = 3
+    t0 = time.perf_counter()
+    oracle.acoustic(p["m"], p["dt"], p["spacing"], 8, k, damp=p["damp"],
+                    src_coords=p["src_coords"], wavelet=p["wavelet"])
+    tc = time.perf_counter() - t0
+    legs["c3_acoustic512_so8"] = {"value": round(512 ** 3 * k / tc / 1e9, 5), "unit": "GPts/s",
+                                  "cores": cpu_threads(), "sample": f"first {k} of 200 steps "
+                                  f"({tc:.1f} s, set-up included)",
+                                  "extrapolated_200_steps_s": round(tc / k * 200, 1),
+                                  "extrapolated": True}
+    return legs
+
+
+def run_extras(args, line, p256):
+    """The rest of the headline metric, measured after the main timed region (one GPU)."""
+    import argparse as _ap
+    t_start = time.perf_counter()
+    extras = [e for e in args.extras.split(",") if e]
+    if "sweep512" in extras:
+        line["sweep512"] = sweep512_result()
+    if "serving" in extras:
+        sv = serving_result(args)
+        line["serving"] = {k: sv[k] for k in ("serving", "sequential", "speedup_vs_sequential",
+                                              "p99_vs_sequential", "gpts_per_s", "config",
+                                              "clocks")}
+    if "fwi320" in extras:
+        ns = _ap.Namespace(**vars(args))
+        ns.steps, ns.warmup, ns.nt, ns.no_cpu_baseline = 2, 1, None, True
+        fw = fwi_result(ns)
+        line["fwi320"] = {"ms_per_gradient": fw["ms_per_step"], "gpts_per_s": fw["value"],
+                          "checkpoint_interval": fw["config"].get("checkpoint_interval"),
+                          "tile": fw["config"].get("tile"), "roofline": fw["roofline"],
+                          "e2e": fw["e2e"], "gradients_timed": ns.steps,
+                          "gpu_launches": fw["gpu_launches"], "clocks": fw["clocks"]}
+    if "c1" in extras:
+        line["c1_diffusion128"] = c1_result()
+    if "oracle" in extras and line.get("cpu_baseline") is not None:
+        line["cpu_baseline"]["legs"] = oracle_legs(p256)
+    line["extras_seconds"] = round(time.perf_counter() - t_start, 1)
 
 
 def run_ours(args):
@@ -751,16 +963,16 @@ def run_ours(args):
                                             "default" if args.tile == "default" else "given")),
                 "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
+        if world == 1 and args.workload == "acoustic256":
+            run_extras(args, line, p)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
 
 
-def run_serving(args):
-    import torch
-    world, rank, local = dist_setup(args)
-    torch.cuda.set_device(local)
+def serving_result(args, rank=0, world=1):
+    """Serve the seeded Poisson stream batched and one shot at a time: the result line."""
     from paper_1906_10811_b300 import build
     from paper_1906_10811_b300.serve import (DeviceBackend, Server, ShotRequest, serve_sequential,
                                              summarize)
@@ -772,15 +984,21 @@ def run_serving(args):
     warm = fdsynth.serving_stream(nshots=2, seed=99, sizes2d=(64, 64), sizes3d=(32, 32),
                                   nt_range=(10, 10), nrec_range=(8, 8))
     serve_sequential([ShotRequest(i, 0.0, p) for i, _, p in warm])
+    import torch
+    gpu_id = "GPU-" + str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+    clocks = ClockSampler(gpu_id)
     be = DeviceBackend(8)
-    srv = Server(be, hbm_budget=int(args.hbm_budget_gb * 2 ** 30), max_members=64, ticks_per_round=32)
+    srv = Server(be, hbm_budget=int(args.hbm_budget_gb * 2 ** 30), max_members=64,
+                 ticks_per_round=32)
     batched = summarize(srv.serve(reqs))
     be.close()
     seq = summarize(serve_sequential(reqs))
-    line = {"metric": "served shots/s", "value": round(batched["shots_per_s"], 3), "unit": "shots/s",
-            "n_gpus": world, "steps": args.shots, "warmup": 1,
-            "ms_per_step": round(1e3 * batched["seconds"] / args.shots, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+    clk = clocks.stop()
+    return {"metric": "served shots/s", "value": round(batched["shots_per_s"], 3),
+            "unit": "shots/s", "n_gpus": world, "steps": args.shots, "warmup": 1,
+            "ms_per_step": round(1e3 * batched["seconds"] / args.shots, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
             "config": {"workload": f"poisson stream of {args.shots} acoustic shots, so 8",
                        "grids": "2-D 200^2-1000^2, 3-D 128^3-320^3", "nt": "300-1000",
                        "receivers": "128-512", "mean_gap_s": args.mean_gap,
@@ -788,7 +1006,15 @@ def run_serving(args):
             "serving": {k: round(v, 4) for k, v in batched.items()},
             "sequential": {k: round(v, 4) for k, v in seq.items()},
             "speedup_vs_sequential": round(batched["shots_per_s"] / seq["shots_per_s"], 3),
-            "gpts_per_s": round(pts / batched["seconds"] / 1e9, 2)}
+            "p99_vs_sequential": round(batched["p99_s"] / seq["p99_s"], 3),
+            "gpts_per_s": round(pts / batched["seconds"] / 1e9, 2), "clocks": clk}
+
+
+def run_serving(args):
+    import torch
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    line = serving_result(args, rank, world)
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0

@@ -331,6 +331,53 @@ fd_status fd_skip_c_planes(fd_ctx *ctx, int64_t *flagged, int64_t *total);
  * graphs included); -1 for NULL. */
 int64_t fd_kernel_launches(const fd_ctx *ctx);
 
+/*
+ * z-slab sub-domains: one 3-D FD_ACOUSTIC grid split along axis 0 into slabs,
+ * each an ordinary context over its own planes, stepped in lockstep with an
+ * R-plane halo exchange after every step (the distributed-memory partitioning
+ * of a structured block that the paper's OPS backend leaves to its library,
+ * §2.2).  Results are bitwise those of the whole grid: a point's update reads
+ * the same values, a source corner is injected by the slab that holds its node
+ * (in the same order), and a receiver's trace is the sum of the slabs' partial
+ * sums over the corners each holds, which the receiver kernel's reduction order
+ * (the two halves along axis 0 added last) makes exactly the whole-grid sum.
+ *
+ * fd_set_subdomain: ctx (3-D FD_ACOUSTIC, shape[0] planes) holds global planes
+ *   [z_origin, z_origin + shape[0]) of a grid with z_global planes.  Source and
+ *   receiver coordinates are then global (validated against the global extent);
+ *   corners in other slabs are left to them, and the traces fd_read returns are
+ *   this slab's partial sums.  Call before fd_set_sources / fd_set_receivers
+ *   (FD_ESTATE otherwise); (0, 0) makes the context whole again.  m, damp and
+ *   fields given to the context are its own planes only.  Batches refuse
+ *   sub-domain contexts.  FD_EUNSUPPORTED for other equations and 2-D.
+ * fd_halo_elems: floats in one exchanged face, R · (padded plane); -1 for 2-D.
+ * fd_halo_copy: copy src's boundary planes of its current level into dst's own
+ *   halo of its current level: side 0 = dst's halo below its first plane from
+ *   src's last R planes (src is the slab below), side 1 = dst's halo above its
+ *   last plane from src's first R planes.  Ordered after src's queued work and
+ *   before src's later work when the contexts have different streams; a peer
+ *   copy when they live on different devices.  Both slabs need ≥ R planes.
+ * fd_halo_export / fd_halo_import: the same faces through a caller buffer of
+ *   fd_halo_elems floats (device pointer), for exchanges the caller carries
+ *   between processes (e.g. NCCL send/recv): export side 0 = the first R planes,
+ *   1 = the last R; import side 0 = the halo below, 1 = the halo above.
+ *   Asynchronous on the context stream.
+ * fd_run_slabs: advance every slab (slabs[0] at z = 0 upwards, contiguous,
+ *   covering the grid) nt steps: exchange halos, then per step run each slab
+ *   one step (fd_run) and exchange.  FD_EINVAL if the slabs do not tile the grid,
+ *   FD_ESTATE if they are at different steps.
+ * fd_accumulate_traces: acc += this context's recorded traces (device pointer,
+ *   [steps+1][nrec] floats), on the context stream: adding every slab's partial
+ *   traces into a zeroed buffer, slab by slab, gives the whole grid's traces.
+ */
+fd_status fd_set_subdomain(fd_ctx *ctx, int64_t z_origin, int64_t z_global);
+int64_t fd_halo_elems(const fd_ctx *ctx);
+fd_status fd_halo_copy(fd_ctx *dst, int side, fd_ctx *src);
+fd_status fd_halo_export(fd_ctx *ctx, int side, float *dst);
+fd_status fd_halo_import(fd_ctx *ctx, int side, const float *src);
+fd_status fd_run_slabs(fd_ctx *const *slabs, int nslabs, int nt);
+fd_status fd_accumulate_traces(fd_ctx *ctx, float *acc);
+
 /* Release everything.  NULL is a no-op. */
 void fd_destroy(fd_ctx *ctx);
 

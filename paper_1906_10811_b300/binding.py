@@ -70,6 +70,13 @@ SIGNATURES = {
     "fd_profile": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double)]),
     "fd_kernel_name": (ctypes.c_char_p, [_vp]),
     "fd_skip_c_planes": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "fd_set_subdomain": (ctypes.c_int, [_vp, _i64, _i64]),
+    "fd_halo_elems": (_i64, [_vp]),
+    "fd_halo_copy": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+    "fd_halo_export": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+    "fd_halo_import": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+    "fd_run_slabs": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int]),
+    "fd_accumulate_traces": (ctypes.c_int, [_vp, _vp]),
     "fd_get_tile_config": (ctypes.c_int, [_vp, ctypes.POINTER(fd_tile_config)]),
     "fd_set_tile_config": (ctypes.c_int, [_vp, ctypes.POINTER(fd_tile_config)]),
     "fd_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(fd_tile_config),
@@ -259,6 +266,39 @@ def fd_skip_c_planes(ctx):
     f, t = _i64(), _i64()
     _check(ctx, load().fd_skip_c_planes(ctx, ctypes.byref(f), ctypes.byref(t)))
     return int(f.value), int(t.value)
+
+
+def fd_set_subdomain(ctx, z_origin, z_global):
+    _check(ctx, load().fd_set_subdomain(ctx, int(z_origin), int(z_global)))
+
+
+def fd_halo_elems(ctx):
+    return int(load().fd_halo_elems(ctx))
+
+
+def fd_halo_copy(dst, side, src):
+    _check(dst, load().fd_halo_copy(dst, int(side), src))
+
+
+def fd_halo_export(ctx, side, dst):
+    _check(ctx, load().fd_halo_export(ctx, int(side), _out_ptr(dst)))
+
+
+def fd_halo_import(ctx, side, src):
+    _check(ctx, load().fd_halo_import(ctx, int(side), _ptr(src, [])))
+
+
+def fd_run_slabs(ctxs, nt):
+    arr = (_vp * len(ctxs))(*ctxs)
+    st = load().fd_run_slabs(arr, len(ctxs), int(nt))
+    if st != FD_OK:
+        bad = [c for c in ctxs if load().fd_last_error(c)]
+        msg = load().fd_last_error(bad[-1] if bad else None)
+        raise FdError(st, msg.decode() if msg else "")
+
+
+def fd_accumulate_traces(ctx, acc):
+    _check(ctx, load().fd_accumulate_traces(ctx, _out_ptr(acc)))
 
 
 def fd_get_tile_config(ctx):

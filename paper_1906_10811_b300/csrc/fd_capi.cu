@@ -141,6 +141,10 @@ struct fd_ctx {
   cudaStream_t copy = nullptr;
   cudaEvent_t ev_model_free = nullptr, ev_copied = nullptr;
   cudaEvent_t ev_step[2] = {nullptr, nullptr}, ev_rec[2] = {nullptr, nullptr};
+  // z-slab sub-domain (fd_set_subdomain): this context holds global z nodes
+  // [z_origin, z_origin + n0) of a grid of z_global nodes (0: the whole grid)
+  int64_t z_origin = 0, z_global = 0;
+  cudaEvent_t ev_halo = nullptr;  // orders halo copies with a neighbour on another stream
   // state
   bool model_set = false;
   int64_t step = 0;
@@ -282,11 +286,14 @@ fd_status store_field(fd_ctx *c, const float *padded, float *user) {
 }
 
 // Multilinear corners of one point (the rule documented in fd.h).
+// In a z-slab sub-domain the point is placed on the global grid and a corner
+// whose node lies in another slab gets dense index -1, padded offset 0 and
+// weight 0 (its owner adds it).
 bool corners(const fd_ctx *c, const float *pt, int64_t *pad_off, int64_t *dense_idx, double *w) {
   int64_t i[3] = {0, 0, 0};
   double f[3] = {0, 0, 0};
   for (int d = 0; d < c->ndim; ++d) {
-    const int64_t n = c->shape[d];
+    const int64_t n = (d == 0 && c->z_global > 0) ? c->z_global : c->shape[d];
     if (n < 2) return false;
     double x = (double)pt[d] / c->h[d];
     const double last = (double)(n - 1), tol = 1e-9 * last;
@@ -309,9 +316,15 @@ bool corners(const fd_ctx *c, const float *pt, int64_t *pad_off, int64_t *dense_
     }
     int z, y, x;
     if (c->ndim == 3) {
-      z = (int)node[0]; y = (int)node[1]; x = (int)node[2];
+      z = (int)(node[0] - c->z_origin); y = (int)node[1]; x = (int)node[2];
     } else {
       z = 0; y = (int)node[0]; x = (int)node[1];
+    }
+    if (c->z_global > 0 && (z < 0 || z >= c->g.n0)) {  // another slab's node
+      pad_off[b] = 0;
+      dense_idx[b] = -1;
+      w[b] = 0.0;
+      continue;
     }
     pad_off[b] = gidx(c->g, z, y, x);
     dense_idx[b] = ((int64_t)z * c->g.n1 + y) * c->g.n2 + x;
@@ -558,6 +571,7 @@ fd_status prepare_fused(fd_ctx *c) {
     std::vector<E> es;
     for (size_t i = 0; i < c->h_src_dense.size(); ++i) {
       const int64_t d = c->h_src_dense[i];
+      if (d < 0) continue;  // a corner another z-slab owns
       const int x = (int)(d % c->g.n2);
       const int y = (int)((d / c->g.n2) % c->g.n1);
       const int z = (int)(d / ((int64_t)c->g.n1 * c->g.n2));
@@ -1023,8 +1037,12 @@ fd_status fd_set_sources(fd_ctx *c, int nsrc, const float *coords, int nt, const
         (st = dalloc(c, &c->wav, (size_t)nt * nsrc)))
       return st;
   }
+  // corners another slab owns: weight 0 at a valid node (their scale is 0)
+  std::vector<int64_t> dense_dev(dense);
+  for (int64_t &d : dense_dev) d = std::max<int64_t>(d, 0);
   CU(cudaMemcpyAsync(c->src_off, off.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
-  CU(cudaMemcpyAsync(c->src_dense, dense.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->src_dense, dense_dev.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice,
+                     c->stream));
   CU(cudaMemcpyAsync(c->src_w, w.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   st = to_device(c, c->wav, wavelets, (size_t)nt * nsrc);
   if (st) return st;
@@ -1299,6 +1317,157 @@ fd_status fd_autotune_fwi(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_con
 }
 
 const char *fd_kernel_name(const fd_ctx *c) { return c ? c->kernel_name : "none"; }
+
+// ---------------------------------------------------------------------------
+// z-slab sub-domains (one grid split along z; the paper's OPS backend leaves
+// the distributed-memory partitioning of a structured block to the library,
+// thesis §2.2).  Halo planes of the current level are refreshed from the
+// neighbours' boundary planes after every step.
+// ---------------------------------------------------------------------------
+fd_status fd_set_subdomain(fd_ctx *c, int64_t z_origin, int64_t z_global) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  if (c->ndim != 3 || c->eq != FD_ACOUSTIC)
+    return fail(c, FD_EUNSUPPORTED, "z-slab sub-domains are for 3-D FD_ACOUSTIC contexts");
+  if (c->nsrc > 0 || c->nrec > 0)
+    return fail(c, FD_ESTATE, "set the sub-domain before the sources and receivers");
+  if (z_origin == 0 && z_global == 0) {
+    c->z_origin = c->z_global = 0;
+    return FD_OK;
+  }
+  if (z_origin < 0 || z_global < 2 || z_origin + c->shape[0] > z_global)
+    return fail(c, FD_EINVAL, "slab [%lld, %lld) does not fit a grid of %lld z nodes",
+                (long long)z_origin, (long long)(z_origin + c->shape[0]), (long long)z_global);
+  c->z_origin = z_origin;
+  c->z_global = z_global;
+  return FD_OK;
+}
+
+int64_t fd_halo_elems(const fd_ctx *c) {
+  return (c && c->ndim == 3) ? (int64_t)c->g.R * c->g.plane : -1;
+}
+
+namespace {
+// Padded offset of the R planes a halo exchange reads (face: 0 = the first R
+// interior planes, 1 = the last R) or writes (halo: 0 = below the interior, 1 = above).
+int64_t face_offset(const fd_ctx *c, int side) {
+  return side == 0 ? (int64_t)c->g.R * c->g.plane : (int64_t)c->g.n0 * c->g.plane;
+}
+int64_t halo_offset(const fd_ctx *c, int side) {
+  return side == 0 ? 0 : (int64_t)(c->g.n0 + c->g.R) * c->g.plane;
+}
+fd_status halo_args_ok(fd_ctx *c, int side) {
+  if (c->ndim != 3) return fail(c, FD_EUNSUPPORTED, "halo exchange is along z of a 3-D grid");
+  if (side != 0 && side != 1) return fail(c, FD_EINVAL, "side must be 0 or 1");
+  if (c->g.n0 < c->g.R)
+    return fail(c, FD_EINVAL, "a slab of %d planes is thinner than the halo (%d)", c->g.n0, c->g.R);
+  return FD_OK;
+}
+}  // namespace
+
+fd_status fd_halo_export(fd_ctx *c, int side, float *dst) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  if ((st = halo_args_ok(c, side))) return st;
+  if (!dst) return fail(c, FD_EINVAL, "dst is NULL");
+  CU(cudaMemcpyAsync(dst, c->u[c->cur] + face_offset(c, side),
+                     (size_t)fd_halo_elems(c) * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+  return FD_OK;
+}
+
+fd_status fd_halo_import(fd_ctx *c, int side, const float *src) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  if ((st = halo_args_ok(c, side))) return st;
+  if (!src) return fail(c, FD_EINVAL, "src is NULL");
+  CU(cudaMemcpyAsync(c->u[c->cur] + halo_offset(c, side), src,
+                     (size_t)fd_halo_elems(c) * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+  return FD_OK;
+}
+
+fd_status fd_halo_copy(fd_ctx *dst, int side, fd_ctx *src) {
+  fd_status st = check_usable(src);
+  if (st) return st;
+  if ((st = check_usable(dst))) return st;
+  fd_ctx *c = dst;  // errors are reported on the receiving context
+  if ((st = halo_args_ok(dst, side))) return st;
+  if ((st = halo_args_ok(src, side ^ 1))) {
+    dst->err = src->err;
+    return st;
+  }
+  if (src->g.R != dst->g.R || src->g.plane != dst->g.plane || src->g.n1 != dst->g.n1 ||
+      src->g.n2 != dst->g.n2)
+    return fail(c, FD_EINVAL, "neighbouring slabs must share order and plane layout");
+  // the lower halo takes the neighbour's last R planes, the upper its first R
+  const size_t bytes = (size_t)fd_halo_elems(dst) * sizeof(float);
+  float *to = dst->u[dst->cur] + halo_offset(dst, side);
+  const float *from = src->u[src->cur] + face_offset(src, side ^ 1);
+  const bool cross = src->stream != dst->stream;
+  if (cross) {
+    if (!src->ev_halo) {
+      CU(cudaSetDevice(src->device));
+      CU(cudaEventCreateWithFlags(&src->ev_halo, cudaEventDisableTiming));
+      CU(cudaSetDevice(dst->device));
+    }
+    if (!dst->ev_halo) CU(cudaEventCreateWithFlags(&dst->ev_halo, cudaEventDisableTiming));
+    CU(cudaEventRecord(src->ev_halo, src->stream));  // the neighbour's step is done
+    CU(cudaStreamWaitEvent(dst->stream, src->ev_halo, 0));
+  }
+  if (src->device == dst->device)
+    CU(cudaMemcpyAsync(to, from, bytes, cudaMemcpyDeviceToDevice, dst->stream));
+  else
+    CU(cudaMemcpyPeerAsync(to, dst->device, from, src->device, bytes, dst->stream));
+  if (cross) {
+    // the neighbour overwrites this level two steps on: after the copy
+    CU(cudaEventRecord(dst->ev_halo, dst->stream));
+    CU(cudaStreamWaitEvent(src->stream, dst->ev_halo, 0));
+  }
+  return FD_OK;
+}
+
+fd_status fd_run_slabs(fd_ctx *const *slabs, int nslabs, int nt) {
+  if (!slabs || nslabs < 1 || nt < 0) return FD_EINVAL;
+  for (int s = 0; s < nslabs; ++s) {
+    fd_ctx *c = slabs[s];
+    fd_status st = check_usable(c);
+    if (st) return st;
+    const int64_t want = s == 0 ? 0 : slabs[s - 1]->z_origin + slabs[s - 1]->shape[0];
+    if (nslabs > 1 && (c->z_global == 0 || c->z_origin != want ||
+                       c->z_global != slabs[0]->z_global ||
+                       (s == nslabs - 1 && c->z_origin + c->shape[0] != c->z_global)))
+      return fail(c, FD_EINVAL, "slab %d does not continue the z-slabs before it", s);
+    if (c->step != slabs[0]->step) return fail(c, FD_ESTATE, "slabs are at different steps");
+  }
+  auto exchange = [&]() -> fd_status {
+    for (int s = 0; s + 1 < nslabs; ++s) {
+      fd_status st = fd_halo_copy(slabs[s + 1], 0, slabs[s]);
+      if (!st) st = fd_halo_copy(slabs[s], 1, slabs[s + 1]);
+      if (st) return st;
+    }
+    return FD_OK;
+  };
+  fd_status st = exchange();  // the current level's halos (after fd_set_field, fd_reset)
+  for (int n = 0; n < nt && !st; ++n) {
+    for (int s = 0; s < nslabs && !st; ++s) {
+      fd_ctx *c = slabs[s];
+      st = check_usable(c);
+      if (!st) st = run_steps(c, 1, true);
+    }
+    if (!st) st = exchange();
+  }
+  return st;
+}
+
+fd_status fd_accumulate_traces(fd_ctx *c, float *acc) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  if (!acc) return fail(c, FD_EINVAL, "acc is NULL");
+  const int64_t n = c->nrec > 0 ? c->rec_rows * c->nrec : 0;
+  if (n == 0) return FD_OK;
+  k_accumulate<<<blocks_for(n, 256), 256, 0, c->stream>>>(acc, c->rec, n);
+  CHECK_LAUNCH();
+  return FD_OK;
+}
 
 fd_status fd_skip_c_planes(fd_ctx *c, int64_t *flagged, int64_t *total) {
   fd_status st = check_usable(c);
@@ -1710,6 +1879,8 @@ fd_status fd_batch_add(fd_batch *b, fd_ctx *c) {
   if (!c->model_set) return bfail(b, FD_ESTATE, "member has no model (fd_set_model)");
   if (c->ndim == 3 && !c->use_tma)
     return bfail(b, FD_EUNSUPPORTED, "3-D members need the pipelined kernel (FD_KERNEL_AUTO/TMA)");
+  if (c->z_global > 0)
+    return bfail(b, FD_EUNSUPPORTED, "z-slab sub-domains exchange halos (fd_run_slabs), not batches");
   if (c->device != b->device) return bfail(b, FD_EINVAL, "member lives on another device");
   if (std::find(b->members.begin(), b->members.end(), c) != b->members.end())
     return bfail(b, FD_EINVAL, "already a member");

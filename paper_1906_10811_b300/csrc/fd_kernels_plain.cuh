@@ -149,8 +149,11 @@ __device__ __forceinline__ void interp_group_store(const float *un, const int64_
                                                    int64_t row, int nrec, int k, int c) {
   float v = 0.f;
   if (k < nrec) v = rw[k * NC + c] * un[roff[k * NC + c]];
+  // lanes are corners, axis 0 the highest bit: pairs along the last axis first,
+  // the two halves along axis 0 last, so a sum split between two z-slabs (each
+  // adding only its own corners, zero for the others) is exactly this sum
 #pragma unroll
-  for (int o = NC / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 1; o < NC; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if (c == 0 && k < nrec) rec[row * nrec + k] = v;
 }
 
@@ -178,6 +181,13 @@ __global__ void k_inject(float *un, const int64_t *__restrict__ step, int j, int
   const int64_t n = *step + j;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < nsrc * NC) atomicAdd(un + soff[i], sscale[i] * wav[n * nsrc + i / NC]);
+}
+
+// acc[i] += part[i] (the partial traces of one z-slab added into the whole grid's).
+__global__ void k_accumulate(float *__restrict__ acc, const float *__restrict__ part, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    acc[i] += part[i];
 }
 
 // rec row = *step + j + 1 (j = -1 with *step = 0 records row 0).
@@ -266,8 +276,9 @@ __global__ void k_interp_batch(const int2 *__restrict__ e, int n, const MemberDe
       v = m->rec_w[k * m->nc + c] * un[m->rec_off[k * m->nc + c]];
     }
   }
+  // the order of interp_group_store (lanes past a 2-D member's corners add zero last)
 #pragma unroll
-  for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 1; o < 8; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if (r < n && c == 0) m->rec[(m->step0 + tk + 1) * m->nrec + k] = v;
 }
 
