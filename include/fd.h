@@ -100,10 +100,13 @@ typedef struct {
   int boundary;       /* fd_boundary; default FD_BOUNDARY_ZERO */
 } fd_options;
 
-/* Fill *opt with the defaults above. */
+/* Fill *opt with the defaults above.  (Library service; no counterpart in the paper.) */
 void fd_options_default(fd_options *opt);
 
 /*
+ * Paper: §2.1.1 (Grid(shape, extent) and TimeFunction(time_order, space_order)
+ * define the problem; op(time=nt, dt=dt) fixes dt) and §5.1.2 (the benchmark
+ * problem's grid, order and time step).
  * Create a context.  ndim ∈ {2,3}; shape[d] ≥ 1 (FD_ACOUSTIC: ≥ 2);
  * spacing[d] > 0; space_order even in [2,16]; dt > 0.  FD_DIFFUSION checks
  * stability here: ν dt Σ_d S/h_d² ≤ 2 with S = -(w_0 + 2 Σ_k (-1)^k w_k);
@@ -115,6 +118,8 @@ fd_status fd_create(fd_ctx **out, int ndim, const int64_t *shape,
                     fd_equation eq, const fd_options *opt);
 
 /*
+ * Paper: §6.2.1 (the seismic acoustic operator, whose model is the squared
+ * slowness m and an absorbing damping term).
  * FD_ACOUSTIC: squared slowness m (> 0 everywhere) and damping coefficient
  * damp (≥ 0; NULL means 0).  Rejects dt above the leapfrog limit
  * 2 / sqrt(max(1/m) · Σ_d S/h_d²) with FD_EINVAL.  May be called again,
@@ -126,6 +131,8 @@ fd_status fd_create(fd_ctx **out, int ndim, const int64_t *shape,
 fd_status fd_set_model(fd_ctx *ctx, const float *m, const float *damp);
 
 /*
+ * Paper: §2.1.1 (initial data written into u.data[0] before the operator runs)
+ * and §5.1.2 (the benchmark's initial condition).
  * Set the current time level(s).  FD_ACOUSTIC: u_cur = u^n, u_prev = u^{n-1}
  * (NULL: equal to u_cur).  FD_DIFFUSION: u_cur only (u_prev ignored); the
  * boundary values given here are held.  Does not change the step counter.
@@ -134,6 +141,7 @@ fd_status fd_set_model(fd_ctx *ctx, const float *m, const float *damp);
 fd_status fd_set_field(fd_ctx *ctx, const float *u_cur, const float *u_prev);
 
 /*
+ * (Library service for repeated shots; no counterpart in the paper.)
  * Start over from rest without uploading a field: u^n = u^{n-1} = 0 on every
  * node (boundary values 0 for FD_DIFFUSION), step counter 0, recorded traces
  * cleared (the next fd_run records row 0 afresh).  Model, sources, receivers
@@ -142,6 +150,8 @@ fd_status fd_set_field(fd_ctx *ctx, const float *u_cur, const float *u_prev);
 fd_status fd_reset(fd_ctx *ctx);
 
 /*
+ * Paper: §6.2.1 (point sources injected into the wavefield: the sparse
+ * operation the OPS backend could not offload) and §2.1.1 (sparse functions).
  * FD_ACOUSTIC: nsrc point sources at coords [nsrc][ndim] with wavelets
  * [nt][nsrc] (row n = s(t_n) for global step n).  Replaces earlier sources;
  * nsrc = 0 removes them.  fd_run fails with FD_EINVAL if it would pass step nt.
@@ -152,6 +162,8 @@ fd_status fd_set_sources(fd_ctx *ctx, int nsrc, const float *coords, int nt,
                          const float *wavelets);
 
 /*
+ * Paper: §6.2.1 (receivers interpolating the wavefield) and §2.1.1 (sparse
+ * functions).
  * FD_ACOUSTIC: nrec receivers at coords [nrec][ndim].  Traces are recorded
  * for every step run afterwards: row 0 = interpolation of u at step 0, row
  * n+1 after step n (the library grows the trace buffer as needed).
@@ -160,10 +172,13 @@ fd_status fd_set_sources(fd_ctx *ctx, int nsrc, const float *coords, int nt,
  */
 fd_status fd_set_receivers(fd_ctx *ctx, int nrec, const float *coords);
 
-/* Advance nt ≥ 0 steps (asynchronous on the context stream). */
+/* Paper: §2.1.1 (op(time=nt, dt=dt) applies the update nt times) and §3.3.3
+ * (one parallel loop per time step, levels t0/t1 rotating).
+ * Advance nt ≥ 0 steps (asynchronous on the context stream). */
 fd_status fd_run(fd_ctx *ctx, int nt);
 
 /*
+ * Paper: §2.1.1 (the solution is read from u.data after the operator ran).
  * Copy results out and synchronise the stream.  u: current level u^n
  * (dense, interior), NULL to skip.  rec: traces [n+1][nrec] for the steps
  * run so far (n = fd_steps_done), NULL to skip.  Returns FD_ETIMEOUT if a
@@ -171,10 +186,12 @@ fd_status fd_run(fd_ctx *ctx, int nt);
  */
 fd_status fd_read(fd_ctx *ctx, float *u, float *rec);
 
-/* Previous level u^{n-1} (FD_ACOUSTIC), for checkpoint/resume; syncs. */
+/* Previous level u^{n-1} (FD_ACOUSTIC), for checkpoint/resume; syncs.  (Library
+ * service; the paper has no counterpart.) */
 fd_status fd_read_prev(fd_ctx *ctx, float *u_prev);
 
-/* Set the global step counter (resume from a checkpoint at step n ≥ 0).
+/* (Library service; no counterpart in the paper.)
+ * Set the global step counter (resume from a checkpoint at step n ≥ 0).
  * Trace rows 0..n keep their contents (zero in a context that has not run);
  * n = 0 makes the next fd_run record row 0 afresh. */
 fd_status fd_set_step(fd_ctx *ctx, int64_t n);
@@ -183,6 +200,7 @@ fd_status fd_set_step(fd_ctx *ctx, int64_t n);
 int64_t fd_steps_done(const fd_ctx *ctx);
 
 /*
+ * Paper: §5.1.3-§5.1.4 (timed runs of the operator and their roofline).
  * Profiling (fd_options.profile = 1): number of stencil launches timed and
  * their summed CUDA-event time in ms since the last call (a graph chunk's time
  * covers its launches and the gaps between them); synchronises and resets.
@@ -190,6 +208,7 @@ int64_t fd_steps_done(const fd_ctx *ctx);
 fd_status fd_profile(fd_ctx *ctx, int64_t *launches, double *stencil_ms);
 
 /*
+ * (No counterpart in the paper: inversion built on the §6.2.1 operator.)
  * Full-waveform-inversion support (gradient of a shot's misfit with
  * respect to m for the §6.2.1 operator).  Device fields in the library's padded layout:
  * fd_field_elems floats each (zero halo included), device pointers.
@@ -232,9 +251,29 @@ fd_status fd_imaging(fd_ctx *adj, float *g, const float *u_next, const float *u_
  */
 fd_status fd_step_fwi(fd_ctx *ctx, float *d2_out, float *img_g, const float *img_d2,
                       double scale);
+
+/*
+ * fd_run_fwi: nt ≥ 0 steps of fd_step_fwi in one call, replayed from captured
+ *   CUDA graphs (chunks of up to 64 steps, cached per pointer set): step i uses
+ *   d2_out = d2_base + s·stride and img_d2 = img_d2_base + s·stride with s = i,
+ *   or s = nt−1−i when reverse = 1 (the adjoint sweep reads a block of second
+ *   differences backwards); NULL bases skip that output; img_g as in
+ *   fd_step_fwi.  stride (floats) ≥ fd_field_elems when a base is given.
+ *   Bitwise the nt single calls.  Asynchronous on the stream.
+ * fd_residual: the misfit of ctx's recorded traces against observed data
+ *   d_obs [n+1][nrec] (device; n = fd_steps_done): r = traces − d_obs (float),
+ *   adj_wav [n][nrec] (device, may be NULL) row j = r row n−j (the adjoint
+ *   source wavelet: the residual time reversed, for an adjoint run of n steps),
+ *   *J (host, may be NULL; then nothing synchronises) = ½ Σ r² accumulated in
+ *   double in a fixed order.  FD_ESTATE without recorded traces.
+ */
+fd_status fd_run_fwi(fd_ctx *ctx, int nt, float *d2_base, const float *img_d2_base,
+                     int64_t stride, int reverse, float *img_g, double scale);
+fd_status fd_residual(fd_ctx *ctx, const float *d_obs, float *adj_wav, double *J);
 fd_status fd_field_to_dense(fd_ctx *ctx, const float *padded, float *dense);
 
 /*
+ * Paper: §2.2 and §2.3.3 (see below).
  * Tile configuration of the pipelined 3-D kernel (FD_KERNEL_TMA/AUTO on 3-D
  * grids).  The paper leaves tiling strategy to the OPS library (§2.2) and
  * cites stencil compilers that block the iteration space per thread to save
@@ -314,12 +353,13 @@ fd_status fd_autotune(fd_ctx *ctx, int reps, fd_tile_config *best, fd_tile_confi
 fd_status fd_autotune_fwi(fd_ctx *ctx, int reps, fd_tile_config *best, fd_tile_config *tried,
                           int max_tried, int *ntried);
 
-/* Name of the stencil kernel variant fd_run launches (static string):
+/* (Library service.)  Name of the stencil kernel variant fd_run launches (static string):
  * "stencil3d_tma_<equation>" (32-wide tiles), "stencil3d_xp_<equation>"
  * (64-wide tiles, two x points a lane), "stencil3d_plain" or "stencil2d_plain". */
 const char *fd_kernel_name(const fd_ctx *ctx);
 
 /*
+ * (Library service.)
  * Tile-planes of the current tile configuration whose C tile the pipelined
  * kernel skips (fd_tile_config.skip_c = 1: C = 1 on the whole tile-plane):
  * *flagged of *total.  Both 0 when skip_c is off, no model is set or the plain
@@ -327,7 +367,7 @@ const char *fd_kernel_name(const fd_ctx *ctx);
  */
 fd_status fd_skip_c_planes(fd_ctx *ctx, int64_t *flagged, int64_t *total);
 
-/* CUDA kernels this context has launched so far (kernel nodes of replayed
+/* (Library service.)  CUDA kernels this context has launched so far (kernel nodes of replayed
  * graphs included); -1 for NULL. */
 int64_t fd_kernel_launches(const fd_ctx *ctx);
 
@@ -382,6 +422,7 @@ fd_status fd_accumulate_traces(fd_ctx *ctx, float *acc);
 void fd_destroy(fd_ctx *ctx);
 
 /*
+ * (No counterpart in the paper: serving built on the §6.2.1 operator.)
  * Batches: many FD_ACOUSTIC shots of one space order stepped together, as a
  * serving loop that admits and retires shots between runs needs (continuous
  * batching, built on the §6.2.1 operator).
@@ -418,6 +459,7 @@ const char *fd_batch_last_error(const fd_batch *b);
 void fd_batch_destroy(fd_batch *b);
 
 /*
+ * (No counterpart in the paper: the admission measure of serving.)
  * Device bytes fd_create + fd_set_* + fd_run allocate for an FD_ACOUSTIC shot
  * (fields with halo, coefficients, m, staging, traces for nt steps, sparse
  * tables) -- the admission measure of a serving loop.  -1 for bad arguments.
@@ -425,10 +467,13 @@ void fd_batch_destroy(fd_batch *b);
 int64_t fd_footprint_bytes(int ndim, const int64_t *shape, int space_order, int nrec, int nt,
                            int nsrc);
 
-/* Text of the last error on ctx (or of the last failed fd_create when ctx is NULL). */
+/* (Library service.)  Text of the last error on ctx (or of the last failed fd_create when ctx is NULL). */
 const char *fd_last_error(const fd_ctx *ctx);
 
 /*
+ * Paper: §2.1.1 (u.dx2 at space order so: the central second-derivative
+ * stencil whose weights these are) and §5.1.5 (the coefficients computed once,
+ * outside the kernel).
  * Host-only helpers (no GPU needed).
  * fd_weights: w_0..w_r (r = space_order/2) of the central second-derivative
  *   stencil, as the library uses them; returns FD_EINVAL for a bad order.
@@ -437,10 +482,11 @@ const char *fd_last_error(const fd_ctx *ctx);
 fd_status fd_weights(int space_order, double *w);
 double fd_stability_symbol(int space_order);
 
-/* Library version string. */
+/* Library version string.  (Library service.) */
 const char *fd_version(void);
 
 /*
+ * (No counterpart in the paper: failure detection of the pipelined kernel.)
  * Failure-detection self-test: launch a kernel that waits, with the same
  * bounded-wait routine the pipelined stencil uses on its mbarriers, on a
  * barrier phase that nothing completes, with a budget of budget_ms (0, 10000]

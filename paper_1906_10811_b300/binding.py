@@ -91,6 +91,9 @@ SIGNATURES = {
     "fd_restore": (ctypes.c_int, [_vp, _vp, _vp]),
     "fd_imaging": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_double]),
     "fd_step_fwi": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_double]),
+    "fd_run_fwi": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _i64, ctypes.c_int, _vp,
+                                  ctypes.c_double]),
+    "fd_residual": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
     "fd_field_to_dense": (ctypes.c_int, [_vp, _vp, _vp]),
     "fd_destroy": (None, [_vp]),
     "fd_last_error": (ctypes.c_char_p, [_vp]),
@@ -399,6 +402,21 @@ def fd_step_fwi(ctx, d2_out=None, img_g=None, img_d2=None, scale=0.0):
     keep = []
     _check(ctx, load().fd_step_fwi(ctx, _out_ptr(d2_out), _out_ptr(img_g), _ptr(img_d2, keep),
                                    float(scale)))
+
+
+def fd_run_fwi(ctx, nt, d2_base=None, img_d2_base=None, stride=0, reverse=False, img_g=None,
+               scale=0.0):
+    """nt FWI-epilogue steps; step i uses row s of the [nt][stride] bases, s = i or nt-1-i."""
+    _check(ctx, load().fd_run_fwi(ctx, int(nt), _out_ptr(d2_base), _ptr(img_d2_base, []),
+                                  int(stride), int(bool(reverse)), _out_ptr(img_g), float(scale)))
+
+
+def fd_residual(ctx, d_obs, adj_wav=None):
+    """J = ½||traces − d_obs||² (float); adj_wav (if given) receives the residual time
+    reversed, the adjoint run's source wavelet."""
+    J = ctypes.c_double()
+    _check(ctx, load().fd_residual(ctx, _ptr(d_obs, []), _out_ptr(adj_wav), ctypes.byref(J)))
+    return float(J.value)
 
 
 def fd_field_to_dense(ctx, padded, dense):

@@ -31,7 +31,7 @@ using namespace fdk;
 namespace {
 
 constexpr int kGraphChunk = 64;  // steps per captured graph
-constexpr int kGraphCacheMax = 6;
+constexpr int kGraphCacheMax = 12;
 thread_local std::string g_create_error;  // fd_last_error(NULL)
 
 // ---------------------------------------------------------------------------
@@ -63,14 +63,35 @@ double lib_symbol(int so) {
   return -s;
 }
 
+// A sequence of FWI-epilogue steps (fd_run_fwi): step i of nt writes the second
+// difference into d2_base + s(i)·stride and/or accumulates the imaging condition
+// into img reading img_d2_base + s(i)·stride, s(i) = i or nt-1-i (reverse).
+struct FwiSeq {
+  float *d2_base = nullptr;
+  const float *img_d2_base = nullptr;
+  float *img = nullptr;
+  int64_t stride = 0;
+  int64_t nt = 0, i0 = 0;  // steps in the sequence; index of the chunk's first step
+  int reverse = 0;
+  float scale = 0.f;
+  bool operator==(const FwiSeq &o) const {
+    return d2_base == o.d2_base && img_d2_base == o.img_d2_base && img == o.img &&
+           stride == o.stride && nt == o.nt && i0 == o.i0 && reverse == o.reverse &&
+           std::memcmp(&scale, &o.scale, sizeof scale) == 0;
+  }
+};
+
 struct GraphEntry {
   int parity;
   int len;
   int64_t kernels;  // kernel nodes in the graph
   cudaGraphExec_t exec;
+  bool fwi;         // captured with an FWI-epilogue sequence (key below)
+  FwiSeq seq;
 };
 
 using StencilFn = void (*)(const float *, float *, const float *, const float *, Geom, Coef);
+using StencilFnTile = void (*)(const float *, float *, const float *, const float *, Geom, Coef);
 using StencilFn2D = void (*)(const MemberDesc *, int, const int64_t *, int);
 
 }  // namespace
@@ -99,6 +120,7 @@ struct fd_ctx {
   int *d_err = nullptr;
   // kernel selection
   StencilFn plain_fn = nullptr;
+  StencilFnTile tile2d_fn = nullptr;  // 2-D grids: the shared-memory-staged kernel
   TmaPlan tma{};
   bool use_tma = false;
   bool iso = false;          // equal spacing on all axes (pipelined kernel variant)
@@ -107,6 +129,9 @@ struct fd_ctx {
   bool fwi_on = false;
   float *fwi_d2 = nullptr, *fwi_img = nullptr;
   const float *fwi_img_d2 = nullptr;
+  bool fwi_seq_on = false;  // fd_run_fwi: per-step pointers from fwi_seq
+  FwiSeq fwi_seq;
+  double *fwi_partial = nullptr;  // fd_residual's per-block sums
   float fwi_scale = 0.f;
   const char *kernel_name = "none";
   // sources
@@ -337,6 +362,14 @@ bool corners(const fd_ctx *c, const float *pt, int64_t *pad_off, int64_t *dense_
 // Launching one step.
 // ---------------------------------------------------------------------------
 fd_status launch_stencil(fd_ctx *c, const float *ucur, float *unext, int j) {
+  if (c->fwi_seq_on) {  // step j of the chunk: pointers of sequence step i0 + j
+    const FwiSeq &q = c->fwi_seq;
+    const int64_t i = q.i0 + j, s = q.reverse ? q.nt - 1 - i : i;
+    c->fwi_d2 = q.d2_base ? q.d2_base + s * q.stride : nullptr;
+    c->fwi_img_d2 = q.img_d2_base ? q.img_d2_base + s * q.stride : nullptr;
+    c->fwi_img = q.img;
+    c->fwi_scale = q.scale;
+  }
   if (c->use_tma) {
     SparseArgs sp{};
     if (c->fused && c->nsrc > 0) {
@@ -360,6 +393,12 @@ fd_status launch_stencil(fd_ctx *c, const float *ucur, float *unext, int j) {
     return FD_OK;
   }
   dim3 block(32, 8);
+  if (c->tile2d_fn) {
+    dim3 tiles((c->g.n2 + 31) / 32, (c->g.n1 + kT2TY - 1) / kT2TY);
+    c->tile2d_fn<<<tiles, block, 0, c->stream>>>(ucur, unext, c->A, c->C, c->g, c->coef);
+    CHECK_LAUNCH();
+    return FD_OK;
+  }
   dim3 grid((c->g.n2 + 31) / 32, (c->g.n1 + 7) / 8, c->g.n0);
   c->plain_fn<<<grid, block, 0, c->stream>>>(ucur, unext, c->A, c->C, c->g, c->coef);
   CHECK_LAUNCH();
@@ -489,7 +528,8 @@ fd_status enqueue_chunk(fd_ctx *c, int parity, int len, bool timed) {
 
 fd_status get_graph(fd_ctx *c, int parity, int len, cudaGraphExec_t *out, int64_t *kernels) {
   for (auto &gph : c->graphs)
-    if (gph.parity == parity && gph.len == len) {
+    if (gph.parity == parity && gph.len == len && gph.fwi == c->fwi_seq_on &&
+        (!gph.fwi || gph.seq == c->fwi_seq)) {
       *out = gph.exec;
       *kernels = gph.kernels;
       return FD_OK;
@@ -514,7 +554,7 @@ fd_status get_graph(fd_ctx *c, int parity, int len, cudaGraphExec_t *out, int64_
   e = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return fail(c, FD_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
-  c->graphs.push_back({parity, len, captured, exec});
+  c->graphs.push_back({parity, len, captured, exec, c->fwi_seq_on, c->fwi_seq});
   *out = exec;
   *kernels = captured;
   return FD_OK;
@@ -651,6 +691,18 @@ void select_kernel(fd_ctx *c) {
   }
 #undef PICK
   c->kernel_name = three ? "stencil3d_plain" : "stencil2d_plain";
+  c->tile2d_fn = nullptr;
+  if (!three && c->opt.kernel != FD_KERNEL_PLAIN) {
+#define PICK2(RR)                                                                      \
+  case RR:                                                                             \
+    c->tile2d_fn = ac ? k_stencil2d_tile<RR, kAcoustic> : k_stencil2d_tile<RR, kDiffusion>; \
+    break;
+    switch (R) {
+      PICK2(1) PICK2(2) PICK2(3) PICK2(4) PICK2(5) PICK2(6) PICK2(7) PICK2(8)
+    }
+#undef PICK2
+    c->kernel_name = "stencil2d_tile";
+  }
 }
 
 // Rebuild the pipelined kernel's plan for another tile configuration; on
@@ -1135,6 +1187,7 @@ fd_status run_steps(fd_ctx *c, int nt, bool graphs) {
   }
   for (int done = 0; done < nt;) {
     const int len = std::min(kGraphChunk, nt - done);
+    if (c->fwi_seq_on) c->fwi_seq.i0 = done;
     if (graphs && c->opt.use_graphs) {
       cudaGraphExec_t exec;
       int64_t kernels = 0;
@@ -1184,6 +1237,58 @@ fd_status fd_step_fwi(fd_ctx *c, float *d2_out, float *img_g, const float *img_d
   st = run_steps(c, 1, false);
   c->fwi_on = false;
   return st;
+}
+
+fd_status fd_run_fwi(fd_ctx *c, int nt, float *d2_base, const float *img_d2_base,
+                     int64_t stride, int reverse, float *img_g, double scale) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  if (c->eq != FD_ACOUSTIC || !c->use_tma || !c->tma.fn_fwi)
+    return fail(c, FD_EUNSUPPORTED,
+                "fd_run_fwi needs the pipelined 3-D acoustic kernel with 32-wide tiles");
+  if (nt < 0) return fail(c, FD_EINVAL, "nt must be >= 0");
+  if (img_g && !img_d2_base) return fail(c, FD_EINVAL, "img_g needs img_d2_base");
+  if ((d2_base || img_d2_base) && stride < c->g.total)
+    return fail(c, FD_EINVAL, "stride %lld is below fd_field_elems", (long long)stride);
+  if (reverse != 0 && reverse != 1) return fail(c, FD_EINVAL, "reverse must be 0 or 1");
+  FwiSeq q;
+  q.d2_base = d2_base;
+  q.img_d2_base = img_d2_base;
+  q.img = img_g;
+  q.stride = stride;
+  q.nt = nt;
+  q.reverse = reverse;
+  q.scale = (float)scale;
+  c->fwi_seq = q;
+  c->fwi_seq_on = true;
+  c->fwi_on = true;
+  st = run_steps(c, nt, true);
+  c->fwi_on = false;
+  c->fwi_seq_on = false;
+  return st;
+}
+
+fd_status fd_residual(fd_ctx *c, const float *d_obs, float *adj_wav, double *J) {
+  fd_status st = check_usable(c);
+  if (st) return st;
+  if (c->eq != FD_ACOUSTIC || c->nrec == 0 || c->rec_rows < 1)
+    return fail(c, FD_ESTATE, "fd_residual needs recorded traces");
+  if (!d_obs) return fail(c, FD_EINVAL, "d_obs is NULL");
+  const int64_t rows = c->rec_rows, n = rows * c->nrec;
+  constexpr int kBlocks = 512, kThreads = 256;
+  if (!c->fwi_partial && (st = dalloc(c, &c->fwi_partial, kBlocks + 1))) return st;
+  k_residual<<<kBlocks, kThreads, 0, c->stream>>>(c->rec, d_obs, adj_wav, rows, c->nrec,
+                                                  c->fwi_partial);
+  CHECK_LAUNCH();
+  k_sum_partials<<<1, kThreads, 0, c->stream>>>(c->fwi_partial, kBlocks, c->fwi_partial + kBlocks);
+  CHECK_LAUNCH();
+  if (J) {
+    CU(cudaMemcpyAsync(J, c->fwi_partial + kBlocks, sizeof(double), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+  }
+  (void)n;
+  return FD_OK;
 }
 
 fd_status fd_field_to_dense(fd_ctx *c, const float *padded, float *dense) {
@@ -1536,7 +1641,7 @@ void fd_destroy(fd_ctx *c) {
   dfree(c, c->d_step); dfree(c, c->d_stats); dfree(c, c->d_err);
   dfree(c, c->wav); dfree(c, c->src_scale); dfree(c, c->src_off); dfree(c, c->src_dense); dfree(c, c->src_w);
   dfree(c, c->rec_off); dfree(c, c->rec_w); dfree(c, c->rec);
-  dfree(c, c->sp_entries); dfree(c, c->sp_first); dfree(c, c->unit_c);
+  dfree(c, c->sp_entries); dfree(c, c->sp_first); dfree(c, c->unit_c); dfree(c, c->fwi_partial);
   for (int i = 0; i < 2; ++i) {
     if (c->ev_step[i]) cudaEventDestroy(c->ev_step[i]);
     if (c->ev_rec[i]) cudaEventDestroy(c->ev_rec[i]);
@@ -1551,6 +1656,7 @@ void fd_destroy(fd_ctx *c) {
   }
   if (c->ev_model_free) cudaEventDestroy(c->ev_model_free);
   if (c->ev_copied) cudaEventDestroy(c->ev_copied);
+  if (c->ev_halo) cudaEventDestroy(c->ev_halo);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -1983,7 +2089,7 @@ fd_status fd_batch_run(fd_batch *b, int nticks) {
     d.blk0 = blk;  // non-decreasing over members; 3-D members own no 2-D blocks
     if (c->ndim == 2) {
       d.blocks_x = (c->g.n2 + 31) / 32;
-      blk += (int64_t)d.blocks_x * ((c->g.n1 + 7) / 8);
+      blk += (int64_t)d.blocks_x * ((c->g.n1 + kT2TY - 1) / kT2TY);
       for (int k = 0; k < c->nsrc * c->nc; ++k) b->h_src.push_back(make_int2((int)i, k));
     }
     for (int k = 0; k < c->nrec; ++k) b->h_rec.push_back(make_int2((int)i, k));

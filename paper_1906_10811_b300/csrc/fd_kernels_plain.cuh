@@ -17,6 +17,28 @@ namespace fdk {
 //   acoustic : un = A·(L u) + (1 + C)·u − C·un   (un holds u^{n-1} on entry)
 // with A = dt²/(m+σ), C = (m−σ)/(m+σ): the leapfrog update solved for u^{n+1}.
 // ---------------------------------------------------------------------------
+// L u at one point from its centre value and neighbour reads nb(axis, ±k): the
+// operation sequence every plain-order kernel shares (so they agree bitwise).
+// Difference form: the weights of every pair sum to zero exactly, so the FP32
+// operator annihilates constants (no drift from rounded weights).
+template <int R, bool THREE_D, typename NB>
+__device__ __forceinline__ float plain_lap(float uc, const Coef &c, NB nb) {
+  const float uc2 = uc + uc;
+  float lap = 0.f;
+#pragma unroll
+  for (int k = 1; k <= R; ++k) {
+    lap = fmaf(c.w[2][k], (nb(2, k) + nb(2, -k)) - uc2, lap);
+    lap = fmaf(c.w[1][k], (nb(1, k) + nb(1, -k)) - uc2, lap);
+    if (THREE_D) lap = fmaf(c.w[0][k], (nb(0, k) + nb(0, -k)) - uc2, lap);
+  }
+  return lap;
+}
+
+// The acoustic update from the Laplacian: A·lap + (1 + C)·u − C·u^{n−1}.
+__device__ __forceinline__ float leapfrog(float a, float cc, float uc, float prev, float lap) {
+  return fmaf(a, lap, fmaf(1.f + cc, uc, -cc * prev));
+}
+
 template <int R, int EQ, bool THREE_D>
 __device__ __forceinline__ void plain_point(const float *__restrict__ u, float *un,
                                             const float *__restrict__ A,
@@ -24,26 +46,74 @@ __device__ __forceinline__ void plain_point(const float *__restrict__ u, float *
                                             const Coef &c, int z, int y, int x) {
   const int64_t p = gidx(g, z, y, x);
   const float uc = u[p];
-  const float uc2 = uc + uc;
-  // difference form: the weights of every pair sum to zero exactly, so the
-  // FP32 operator annihilates constants (no drift from rounded weights)
-  float lap = 0.f;
-#pragma unroll
-  for (int k = 1; k <= R; ++k) {
-    lap = fmaf(c.w[2][k], (u[p + k] + u[p - k]) - uc2, lap);
-    lap = fmaf(c.w[1][k], (u[p + (int64_t)k * g.px] + u[p - (int64_t)k * g.px]) - uc2, lap);
-    if (THREE_D)
-      lap = fmaf(c.w[0][k], (u[p + k * g.plane] + u[p - k * g.plane]) - uc2, lap);
-  }
+  const float lap = plain_lap<R, THREE_D>(uc, c, [&](int ax, int k) {
+    return u[p + (ax == 2 ? (int64_t)k : ax == 1 ? (int64_t)k * g.px : (int64_t)k * g.plane)];
+  });
   if (EQ == kAcoustic) {
-    const float a = A[p], cc = C[p];
-    const float prev = un[p];
-    un[p] = fmaf(a, lap, fmaf(1.f + cc, uc, -cc * prev));
+    un[p] = leapfrog(A[p], C[p], uc, un[p], lap);
   } else {
     const bool interior = x > 0 && x < g.n2 - 1 && y > 0 && y < g.n1 - 1 &&
                           (!THREE_D || (z > 0 && z < g.n0 - 1));
     if (interior) un[p] = uc + lap;
   }
+}
+
+// ---------------------------------------------------------------------------
+// 2-D step staged through shared memory.  A block of 32 × 8 threads updates a
+// tile of 32 × kT2TY points: the tile's u^n with its R-wide halo, (32 + 2R) ×
+// (kT2TY + 2R) floats, is loaded once with coalesced rows (the padded layout
+// holds the zero halo, so every staged row lies in the field) and every
+// neighbour read comes from shared memory.  A thread owns column x of rows
+// ty, ty + 8, ... (a warp reads one row: no bank conflicts).  The per-point
+// operation sequence is plain_point's, so the result is bitwise the plain
+// kernel's.  2-D fields of the serving sizes (≤ 1000², 4 MB a level) live in
+// L2, so the bound here is L2 bandwidth and launch latency, not HBM.
+// ---------------------------------------------------------------------------
+constexpr int kT2TY = 32;  // tile rows (4 per thread)
+
+template <int R, int EQ>
+__device__ __forceinline__ void tile2d_update(const float *__restrict__ u, float *un,
+                                              const float *__restrict__ A,
+                                              const float *__restrict__ C, const Geom &g,
+                                              const Coef &c, int x0, int y0, float *sm) {
+  constexpr int SW = 32 + 2 * R, SH = kT2TY + 2 * R;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  // stage rows y0-R .. y0+kT2TY+R-1 (those past the field's halo are not read),
+  // columns x0-R .. x0+32+R-1
+  const int ymax = g.n1 + R;  // padded rows run from -R to n1+R-1
+  for (int i = tid; i < SH * SW; i += 256) {
+    const int r = i / SW, q = i - r * SW;
+    const int y = y0 - R + r;
+    const int x = x0 - R + q;
+    sm[i] = (y < ymax && x < g.n2 + R) ? u[gidx(g, 0, y, x)] : 0.f;
+  }
+  __syncthreads();
+  const int x = x0 + tx;
+  if (x >= g.n2) return;
+#pragma unroll
+  for (int j = 0; j < kT2TY / 8; ++j) {
+    const int yl = ty + 8 * j, y = y0 + yl;
+    if (y >= g.n1) break;
+    const float *s = sm + (yl + R) * SW + tx + R;
+    const float uc = *s;
+    const float lap = plain_lap<R, false>(uc, c, [&](int ax, int k) {
+      return s[ax == 2 ? k : k * SW];
+    });
+    const int64_t p = gidx(g, 0, y, x);
+    if (EQ == kAcoustic) {
+      un[p] = leapfrog(A[p], C[p], uc, un[p], lap);
+    } else {
+      if (x > 0 && x < g.n2 - 1 && y > 0 && y < g.n1 - 1) un[p] = uc + lap;
+    }
+  }
+}
+
+template <int R, int EQ>
+__global__ void __launch_bounds__(256)
+k_stencil2d_tile(const float *__restrict__ u, float *un, const float *__restrict__ A,
+                 const float *__restrict__ C, Geom g, Coef c) {
+  __shared__ float sm[(32 + 2 * R) * (kT2TY + 2 * R)];
+  tile2d_update<R, EQ>(u, un, A, C, g, c, blockIdx.x * 32, blockIdx.y * kT2TY, sm);
 }
 
 template <int R, int EQ, bool THREE_D>
@@ -183,6 +253,46 @@ __global__ void k_inject(float *un, const int64_t *__restrict__ step, int j, int
   if (i < nsrc * NC) atomicAdd(un + soff[i], sscale[i] * wav[n * nsrc + i / NC]);
 }
 
+// FWI misfit of one shot over `rows` trace rows of nrec receivers: r = rec − d_obs
+// (float, as recorded), adj_wav row j = r row rows−1−j for j = 0..rows−2 (the adjoint
+// source: the residual time reversed; may be null), and part[block] = Σ r² in double
+// over the elements the block visits, in a fixed order (blockDim must be 256).
+__global__ void k_residual(const float *__restrict__ rec, const float *__restrict__ d_obs,
+                           float *__restrict__ adj_wav, int64_t rows, int nrec,
+                           double *__restrict__ part) {
+  __shared__ double sh[256];
+  const int64_t n = rows * nrec;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float r = __fsub_rn(rec[i], d_obs[i]);
+    acc = fma((double)r, (double)r, acc);
+    const int64_t row = i / nrec;
+    if (adj_wav && row >= 1) adj_wav[(rows - 1 - row) * nrec + (i - row * nrec)] = r;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// *out = ½ Σ part[0..n) in a fixed order (one block of 256 threads): J = ½ ||r||².
+__global__ void k_sum_partials(const double *__restrict__ part, int n, double *out) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = 0.5 * sh[0];
+}
+
 // acc[i] += part[i] (the partial traces of one z-slab added into the whole grid's).
 __global__ void k_accumulate(float *__restrict__ acc, const float *__restrict__ part, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -226,24 +336,24 @@ struct MemberDesc {
   int nrec;
 };
 
-// One step of every 2-D member: blocks of 32 × 8 points, block -> member by
-// binary search over blk0.  The batch kernels run tick *tick + j (j: the tick's
+// One step of every 2-D member: blocks of 32 × 8 threads, block -> member by
+// binary search over blk0; a block is one staged 32 × kT2TY tile of a member (the
+// 2-D kernel above).  The batch kernels run tick *tick + j (j: the tick's
 // place in a captured chunk).
 template <int R>
 __global__ void __launch_bounds__(256)
 k_stencil2d_batch(const MemberDesc *__restrict__ d, int n, const int64_t *tick, int j) {
+  __shared__ float sm[(32 + 2 * R) * (kT2TY + 2 * R)];
   int lo = 0, hi = n - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) / 2;
     if (d[mid].blk0 <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
   }
   const MemberDesc &m = d[lo];
-  const int64_t b = blockIdx.x - m.blk0;
-  const int x = (int)(b % m.blocks_x) * 32 + threadIdx.x;
-  const int y = (int)(b / m.blocks_x) * 8 + threadIdx.y;
-  if (x >= m.g.n2 || y >= m.g.n1) return;
+  const int64_t b = blockIdx.x - m.blk0;  // the member's tile (32 × kT2TY points)
   const int par = m.cur0 ^ (int)((*tick + j) & 1);
-  plain_point<R, kAcoustic, false>(m.level[par], m.level[par ^ 1], m.A, m.C, m.g, m.c, 0, y, x);
+  tile2d_update<R, kAcoustic>(m.level[par], m.level[par ^ 1], m.A, m.C, m.g, m.c,
+                              (int)(b % m.blocks_x) * 32, (int)(b / m.blocks_x) * kT2TY, sm);
 }
 
 // Source corners of the 2-D members: entry = (member, corner).

@@ -12,15 +12,18 @@ w·dt²/m equals a·w), and
 
     dJ/dm = −(1/dt²) Σ_n ν^{n+1} ⊙ (u^{n+1} − 2u^n + u^{n−1}),
 
-accumulated by the library's imaging-condition kernel (fd_imaging).  The
+accumulated by the library's imaging-condition kernel (fd_imaging, or the
+stencil epilogue through fd_step_fwi / fd_run_fwi).  The residual, the misfit J
+and the time-reversed adjoint wavelet come from fd_residual.  The
 forward wavefield is needed backwards in time: it is checkpointed every k
 steps (fd_snapshot) and each block of k steps is recomputed from its
 checkpoint while the adjoint sweeps it; on the pipelined kernel the forward
 sweep writes the last block's second differences itself, so that block is not
 recomputed (and with k = nt nothing is).  ``choose_checkpoint_interval`` picks
 the largest k the device memory allows; ``tune_checkpoint_interval`` times
-the candidates and keeps the fastest (the least memory among near-ties).  Every arithmetic step runs in CUDA
-kernels; this module orders them.
+the candidates and keeps the fastest (the least memory among near-ties).  Every
+arithmetic step runs in CUDA kernels; this module orders them (torch holds the
+device memory and the stream).
 """
 
 import math
@@ -153,10 +156,11 @@ def gradient(p, d_obs, m=None, k=None, memory_budget=None, stats=None, profile=F
     receives k, the device bytes held for checkpoints and the recompute block,
     and the kernel launches of the forward and adjoint contexts; with
     ``profile`` also their stencil launches and summed stencil milliseconds
-    (CUDA events per launch; steps are then launched one by one).  ``fused``
-    (default: wherever the pipelined 3-D kernel runs) takes the backward sweep
-    through fd_step_fwi, the second time difference and the imaging condition
-    computed in the stencil epilogues; the result is bitwise the same.
+    (CUDA events around each replayed chunk of steps).  ``fused`` (default:
+    wherever the pipelined 3-D kernel runs) takes the backward sweep through
+    fd_run_fwi, the second time difference and the imaging condition computed
+    in the stencil epilogues and the steps of a block replayed from CUDA graphs;
+    the result is bitwise the same.
     """
     torch = _dev()
     _check_sparse_undamped(p)
@@ -183,7 +187,7 @@ def _gradient_on_stream(p, d_obs, m, k, memory_budget, stats=None, profile=False
     adj = Solver(p["shape"], p["spacing"], p["so"], dt, "acoustic", device=True, profile=profile)
     try:
         fwd.set_model(mm, damp)
-        if fwd.kernel_name == "stencil3d_tma_acoustic":
+        if fwd.kernel_name in ("stencil3d_tma_acoustic", "stencil3d_xp_acoustic"):
             # both contexts take the tile timed on the sweep's own kernels (cached per grid)
             fwd.autotune(fwi=True, cached=True)
             t = fwd.tile_config
@@ -210,17 +214,17 @@ def _gradient_on_stream(p, d_obs, m, k, memory_budget, stats=None, profile=False
         # fused, the last block's steps also write its second differences
         for c, (n0, n1) in enumerate(blk_range):
             B.fd_snapshot(fwd.ctx, ck[c, 0], ck[c, 1])
-            if fused and c == nblk - 1:
-                for t in range(n0, n1):
-                    B.fd_step_fwi(fwd.ctx, d2_out=blk[t - n0])
+            if fused and c == nblk - 1:      # step t writes its second difference to blk[t - n0]
+                B.fd_run_fwi(fwd.ctx, n1 - n0, d2_base=blk, stride=elems)
             else:
                 fwd.run(n1 - n0)
-        _, rec = fwd.read(field=False)
-        r = rec - d_obs
-        J = 0.5 * float(torch.sum(r.double() * r.double()))
-        # adjoint: sources at the receivers, wavelet row j = r[nt - j]
+        # residual r = traces − d_obs, J = ½||r||² and the adjoint source wavelet
+        # (row j = r[nt − j]) in the library
+        adj_wav = torch.empty((nt, rc.shape[0]), dtype=torch.float32, device="cuda")
+        J = B.fd_residual(fwd.ctx, d_obs, adj_wav)
+        # adjoint: sources at the receivers
         adj.set_model(mm, damp)
-        adj.set_sources(rc, torch.flip(r[1:], dims=(0,)).contiguous())
+        adj.set_sources(rc, adj_wav)
         B.fd_set_receivers(fwd.ctx, 0, None)
         scale = -1.0 / (dt * dt)
         if fused:
@@ -233,10 +237,10 @@ def _gradient_on_stream(p, d_obs, m, k, memory_budget, stats=None, profile=False
                 if c < nblk - 1:   # the last block's differences are in blk already
                     B.fd_restore(fwd.ctx, ck[c, 0], ck[c, 1])
                     fwd.set_step(n0)
-                    for t in range(n0, n1):
-                        B.fd_step_fwi(fwd.ctx, d2_out=blk[t - n0])
-                for n in range(n1 - 1, n0 - 1, -1):   # adjoint step nt-1-n gives ν^{n+1}
-                    B.fd_step_fwi(adj.ctx, img_g=gp, img_d2=blk[n - n0], scale=scale)
+                    B.fd_run_fwi(fwd.ctx, n1 - n0, d2_base=blk, stride=elems)
+                # adjoint step nt-1-n gives ν^{n+1} and reads blk[n - n0]: the block backwards
+                B.fd_run_fwi(adj.ctx, n1 - n0, img_d2_base=blk, stride=elems, reverse=True,
+                             img_g=gp, scale=scale)
             B.fd_field_to_dense(fwd.ctx, gp, g)
             blk_bytes = int(blk.numel() + gp.numel()) * 4
         else:

@@ -86,23 +86,65 @@ class DeviceBackend:
         self.batch.close()
 
 
+def shot_work(req):
+    """Grid-point updates of a shot (points × steps): the service-time estimate."""
+    return shot_points(req) * int(req.problem["nt"])
+
+
+def shot_points(req):
+    """Grid points one tick of the shot updates (its share of a batch tick)."""
+    p = req.problem
+    return int(np.prod(p["shape"])) if "shape" in p else int(p.get("points", 1))
+
+
 class Server:
     """Continuous-batching server.
 
     ``hbm_budget``: device bytes the admitted shots may hold together;
     ``max_members``: batch slots; ``ticks_per_round``: most steps per batch run
     between admission points (a round also ends when a member finishes).
+
+    Admission order (``policy``): "fcfs" admits arrived requests in arrival
+    order and stops at the first that does not fit; "shortest" admits the
+    arrived request with the least work (points × steps) first, except that a
+    request waiting longer than ``max_wait_s`` goes ahead of all younger ones
+    (oldest first) and, if it does not fit, holds admission until it does, so
+    no request waits without bound.  ``work_cap`` (grid points, 0 = none)
+    bounds the points one batch tick updates: every member advances once per
+    tick, so the tick time, and with it every member's latency, grows with the
+    work admitted beside it; a request is admitted while the batch stays under
+    the cap (always when the batch is empty).
     """
 
     def __init__(self, backend, hbm_budget, max_members=64, ticks_per_round=32,
-                 clock=time.perf_counter, sleep=time.sleep):
+                 clock=time.perf_counter, sleep=time.sleep, policy="fcfs", max_wait_s=0.25,
+                 work_cap=0, setup_workers=0):
+        if policy not in ("fcfs", "shortest"):
+            raise ValueError(f"unknown admission policy {policy!r}")
         self.backend = backend
         self.budget = int(hbm_budget)
         self.max_members = int(max_members)
         self.ticks = int(ticks_per_round)
         self.clock = clock
         self.sleep = sleep
+        self.policy = policy
+        self.max_wait = float(max_wait_s)
+        self.work_cap = int(work_cap)
+        self.setup_workers = int(setup_workers)
         self.log = []          # (event, request id, time) for tests and traces
+
+    def _candidates(self, pending, now):
+        """Arrived requests in the order admission considers them, and how many at
+        the head of that order no later request may pass (all of them under fcfs;
+        the aged ones under shortest-first)."""
+        arrived = [r for r in pending if r.arrival <= now]
+        if self.policy == "fcfs":
+            return arrived, len(arrived)
+        aged = sorted((r for r in arrived if now - r.arrival > self.max_wait),
+                      key=lambda r: (r.arrival, r.id))
+        young = sorted((r for r in arrived if now - r.arrival <= self.max_wait),
+                       key=lambda r: (shot_work(r), r.arrival, r.id))
+        return aged + young, len(aged)
 
     def serve(self, requests):
         pending = collections.deque(sorted(requests, key=lambda r: (r.arrival, r.id)))
@@ -110,48 +152,82 @@ class Server:
             if self.backend.footprint(r) > self.budget:
                 raise ValueError(f"shot {r.id} needs more device memory than the budget")
         active = {}            # id -> [request, handle, steps done, footprint, admitted time]
+        starting = {}          # id -> [request, future of its set-up, footprint]
         left = []              # shots that left the batch in the last round, to collect
         used = 0               # footprint held on the device (freed when collected)
+        points = 0             # grid points one tick of the admitted shots updates
         results = []
+        pool = None
+        if self.setup_workers > 0:
+            import concurrent.futures
+            pool = concurrent.futures.ThreadPoolExecutor(max_workers=self.setup_workers)
         t0 = self.clock()
-        while pending or active or left:
-            now = self.clock() - t0
-            # admit arrivals, first come first served, while memory and slots allow
-            while (pending and pending[0].arrival <= now and len(active) < self.max_members):
-                r = pending[0]
-                fp = self.backend.footprint(r)
-                if used + fp > self.budget:
-                    break
-                pending.popleft()
-                h = self.backend.start(r)
-                self.backend.add(h)
-                used += fp
-                active[r.id] = [r, h, 0, fp, self.clock() - t0]
-                self.log.append(("admit", r.id, self.clock() - t0))
-            if not active and not left:
-                wait = pending[0].arrival - (self.clock() - t0)
-                if wait > 0:
-                    self.sleep(min(wait, 0.05))
-                continue
-            # queue the next round first, then collect the shots that finished in
-            # the previous one: reading their traces overlaps this round's work
-            finished = []
-            if active:
-                n = min([self.ticks] + [a[0].problem["nt"] - a[2] for a in active.values()])
-                self.backend.run(n)
-                for a in active.values():
-                    a[2] += n
-                for rid in [rid for rid, a in active.items() if a[2] == a[0].problem["nt"]]:
-                    r, h, _, fp, adm = active.pop(rid)
-                    self.backend.leave(h)
-                    finished.append((r, h, fp, adm))
-            for r, h, fp, adm in left:
-                rec = self.backend.collect(h)
-                used -= fp
-                t = self.clock() - t0
-                results.append(ShotResult(r.id, rec, r.arrival, adm, t))
-                self.log.append(("finish", r.id, t))
-            left = finished
+
+        def join(r, h):
+            self.backend.add(h)
+            active[r.id] = [r, h, 0, self.backend.footprint(r), self.clock() - t0]
+            self.log.append(("admit", r.id, self.clock() - t0))
+
+        try:
+            while pending or active or left or starting:
+                # shots whose set-up finished join the batch
+                for rid in [rid for rid, st in starting.items() if st[1].done()]:
+                    r, fut, _ = starting.pop(rid)
+                    join(r, fut.result())
+                now = self.clock() - t0
+                # admit arrivals in policy order while memory, slots and the work cap allow
+                cands, nblock = self._candidates(pending, now)
+                for i, r in enumerate(cands):
+                    if len(active) + len(starting) >= self.max_members:
+                        break
+                    fp = self.backend.footprint(r)
+                    pts = shot_points(r)
+                    busy = active or starting
+                    fits = used + fp <= self.budget and (
+                        not self.work_cap or not busy or points + pts <= self.work_cap)
+                    if not fits:
+                        if i < nblock:
+                            break          # a request nobody may pass waits for room
+                        continue
+                    pending.remove(r)
+                    used += fp
+                    points += pts
+                    if pool is None:
+                        join(r, self.backend.start(r))
+                    else:              # set up on a worker while the batch runs
+                        starting[r.id] = [r, pool.submit(self.backend.start, r), fp]
+                if not active and not left:
+                    if starting:       # nothing to run until a set-up finishes
+                        next(iter(starting.values()))[1].result()
+                        continue
+                    if pending:
+                        wait = min(r.arrival for r in pending) - (self.clock() - t0)
+                        if wait > 0:
+                            self.sleep(min(wait, 0.05))
+                    continue
+                # queue the next round first, then collect the shots that finished in
+                # the previous one: reading their traces overlaps this round's work
+                finished = []
+                if active:
+                    n = min([self.ticks] + [a[0].problem["nt"] - a[2] for a in active.values()])
+                    self.backend.run(n)
+                    for a in active.values():
+                        a[2] += n
+                    for rid in [rid for rid, a in active.items() if a[2] == a[0].problem["nt"]]:
+                        r, h, _, fp, adm = active.pop(rid)
+                        self.backend.leave(h)
+                        points -= shot_points(r)
+                        finished.append((r, h, fp, adm))
+                for r, h, fp, adm in left:
+                    rec = self.backend.collect(h)
+                    used -= fp
+                    t = self.clock() - t0
+                    results.append(ShotResult(r.id, rec, r.arrival, adm, t))
+                    self.log.append(("finish", r.id, t))
+                left = finished
+        finally:
+            if pool is not None:
+                pool.shutdown(wait=True)
         return sorted(results, key=lambda x: x.id)
 
 

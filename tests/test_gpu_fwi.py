@@ -232,3 +232,70 @@ def test_fused_epilogues_match_snapshots_and_imaging_for_every_tile(cfg):
             B.fd_field_to_dense(a.ctx, g_pad, gfused)
             assert torch.equal(gfused, gd)
         torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("reverse", (False, True))
+def test_run_fwi_sequence_is_bitwise_the_single_steps(reverse):
+    """fd_run_fwi (graph-replayed chunks; 70 steps = a 64-step chunk and a 6-step one)
+    writes and reads the same rows as fd_step_fwi called step by step."""
+    import torch
+    from paper_1906_10811_b300 import Solver
+    from paper_1906_10811_b300 import binding as B
+    p = _shot(shape=(26, 30, 41), nt=160)        # wavelet long enough for 10 + 2 × 70 steps
+    nt = 70
+    out = []
+    for seq in (False, True):
+        with Solver(p["shape"], p["spacing"], 8, p["dt"], "acoustic", device=True) as s:
+            dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+            s.set_model(dev(p["m"]), dev(p["damp"]))
+            s.set_sources(dev(p["src_coords"]), dev(p["wavelet"]))
+            s.run(10)
+            elems = B.fd_field_elems(s.ctx)
+            d2 = torch.full((nt, elems), float("nan"), device="cuda")
+            g = torch.zeros(elems, device="cuda")
+            src = torch.randn((nt, elems), device="cuda",
+                              generator=torch.Generator("cuda").manual_seed(3))
+            if seq:
+                B.fd_run_fwi(s.ctx, nt, d2_base=d2, stride=elems, reverse=reverse)
+                B.fd_run_fwi(s.ctx, nt, img_d2_base=src, stride=elems, reverse=reverse,
+                             img_g=g, scale=-0.5)
+            else:
+                for i in range(nt):
+                    r = nt - 1 - i if reverse else i
+                    B.fd_step_fwi(s.ctx, d2_out=d2[r])
+                for i in range(nt):
+                    r = nt - 1 - i if reverse else i
+                    B.fd_step_fwi(s.ctx, img_g=g, img_d2=src[r], scale=-0.5)
+            u, _ = s.read()
+            out.append((u.cpu().numpy(), d2.cpu().numpy(), g.cpu().numpy()))
+    for a, b in zip(*out):
+        assert np.array_equal(a, b, equal_nan=True)
+
+
+def test_residual_misfit_and_adjoint_wavelet():
+    """fd_residual: the residual of the recorded traces, time reversed into the adjoint
+    wavelet, and J = ½||r||² accumulated in double."""
+    import torch
+    from paper_1906_10811_b300 import Solver
+    from paper_1906_10811_b300 import binding as B
+    p = _shot(shape=(24, 28, 30), nt=77, nrec=37)
+    rng = np.random.default_rng(8)
+    with Solver(p["shape"], p["spacing"], 8, p["dt"], "acoustic", device=True) as s:
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        s.set_model(dev(p["m"]), dev(p["damp"]))
+        s.set_sources(dev(p["src_coords"]), dev(p["wavelet"]))
+        s.set_receivers(dev(p["rec_coords"]))
+        with pytest.raises(B.FdError) as e:
+            B.fd_residual(s.ctx, torch.zeros((1, 37), device="cuda"))   # nothing recorded yet
+        assert e.value.status == B.FD_ESTATE
+        s.run(77)
+        _, rec = s.read(field=False)
+        d_obs = dev(rng.standard_normal((78, 37)).astype(np.float32) * float(rec.abs().max()))
+        wav = torch.full((77, 37), float("nan"), device="cuda")
+        J = B.fd_residual(s.ctx, d_obs, wav)
+        J2 = B.fd_residual(s.ctx, d_obs)                  # no wavelet: J only, same value
+    r = (rec - d_obs).cpu().numpy()                       # float32 subtraction, as recorded
+    assert np.array_equal(wav.cpu().numpy(), r[1:][::-1])
+    Jref = 0.5 * float(np.sum(r.astype(np.float64) ** 2))
+    assert J == J2
+    assert abs(J - Jref) <= 1e-12 * Jref

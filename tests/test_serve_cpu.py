@@ -103,3 +103,96 @@ def test_oversized_request_rejected_and_idle_wait():
     assert res[0].admitted >= 2.0
     s = summarize(res)
     assert s["shots"] == 1 and s["p99_s"] >= s["p50_s"] > 0
+
+
+def _reqs_pts(spec):
+    """(arrival, size, nt, points) per request."""
+    return [ShotRequest(i, a, {"size": s, "nt": nt, "points": pts})
+            for i, (a, s, nt, pts) in enumerate(spec)]
+
+
+def test_shortest_work_first_admission():
+    clk = FakeClock()
+    be = FakeBackend(clk)
+    # all arrived at once, one slot: admitted by least points x steps
+    reqs = _reqs_pts([(0.0, 1, 100, 50), (0.0, 1, 10, 10), (0.0, 1, 40, 20), (0.0, 1, 5, 1000)])
+    srv = Server(be, hbm_budget=100, max_members=1, ticks_per_round=8, clock=clk,
+                 sleep=clk.sleep, policy="shortest", max_wait_s=100.0)
+    res = srv.serve(reqs)
+    admits = [rid for ev, rid, _ in srv.log if ev == "admit"]
+    assert admits == [1, 2, 0, 3]                 # work 100, 800, 5000, 5000 (tie: arrival, id)
+    assert all(r.traces == reqs[r.id].problem["nt"] for r in res)
+
+
+def test_ageing_bounds_the_wait_of_large_shots():
+    """A large shot among a steady stream of small ones: shortest-first alone would
+    keep passing it over; past max_wait it goes first and holds admission."""
+    clk = FakeClock()
+    be = FakeBackend(clk)
+    spec = [(0.0, 1, 200, 100)] + [(0.001 * i, 1, 20, 1) for i in range(1, 200)]
+    reqs = _reqs_pts(spec)
+    srv = Server(be, hbm_budget=1000, max_members=2, ticks_per_round=4, clock=clk,
+                 sleep=clk.sleep, policy="shortest", max_wait_s=0.05)
+    res = srv.serve(reqs)
+    t_admit_big = [t for ev, rid, t in srv.log if ev == "admit" and rid == 0][0]
+    # admitted within max_wait plus the round in which it aged (a round here is at most
+    # 4 ticks of 2 members = 8 ms)
+    assert t_admit_big <= 0.05 + 0.01
+    assert len(res) == 200
+
+
+def test_work_cap_bounds_the_points_of_a_tick():
+    clk = FakeClock()
+
+    class PointBackend(FakeBackend):
+        def __init__(self, clock):
+            super().__init__(clock)
+            self.points = 0
+            self.peak_points = 0
+
+        def add(self, h):
+            super().add(h)
+            self.points += h.problem["points"]
+            self.peak_points = max(self.peak_points, self.points)
+            if len(self.members) > 1:
+                assert self.points <= 100, "a tick over the work cap"
+
+        def leave(self, h):
+            super().leave(h)
+            self.points -= h.problem["points"]
+
+    be = PointBackend(clk)
+    reqs = _reqs_pts([(0.0, 1, 30, 60), (0.0, 1, 30, 50), (0.0, 1, 30, 30), (0.0, 1, 30, 200)])
+    srv = Server(be, hbm_budget=1000, max_members=8, ticks_per_round=8, clock=clk,
+                 sleep=clk.sleep, work_cap=100)
+    res = srv.serve(reqs)
+    assert len(res) == 4
+    # the 200-point shot exceeds the cap alone: it runs only in an empty batch
+    assert be.peak_points == 200
+    admits = [rid for ev, rid, _ in srv.log if ev == "admit"]
+    assert admits == [0, 1, 2, 3]                     # fcfs order kept under the cap
+
+
+def test_setup_on_a_worker_keeps_budget_slots_and_results():
+    """Shots set up on a worker thread while the batch runs: memory of shots being
+    set up counts against the budget, every shot runs exactly its steps."""
+    import threading
+    clk = FakeClock()
+    lock = threading.Lock()
+
+    class SlowStart(FakeBackend):
+        def start(self, req):
+            with lock:
+                return req
+
+    be = SlowStart(clk)
+    reqs = _reqs_pts([(0.0, 4, 50, 10), (0.0, 4, 30, 10), (0.0, 4, 20, 10), (0.001, 2, 10, 10),
+                      (0.5, 1, 5, 10)])
+    srv = Server(be, hbm_budget=10, max_members=3, ticks_per_round=8, clock=clk, sleep=clk.sleep,
+                 setup_workers=1)
+    res = srv.serve(reqs)
+    assert [r.id for r in res] == [0, 1, 2, 3, 4]
+    assert all(r.traces == reqs[r.id].problem["nt"] for r in res)
+    assert be.peak_used <= 10 and be.peak_members <= 3
+    for r in res:
+        assert r.arrival <= r.admitted <= r.finished
