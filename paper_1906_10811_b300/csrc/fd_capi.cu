@@ -705,6 +705,11 @@ void select_kernel(fd_ctx *c) {
   }
 }
 
+// Tensor-map origin of the context's fields (see map_origin).
+MapOrigin ctx_origin(const fd_ctx *c) {
+  return map_origin(c->g, c->opt.boundary == FD_BOUNDARY_ODD, c->z_global > 0);
+}
+
 // Rebuild the pipelined kernel's plan for another tile configuration; on
 // failure the current plan stays.  Source tables are keyed by tile and the
 // captured graphs hold the old plan, so both are redone.
@@ -713,7 +718,7 @@ fd_status replan(fd_ctx *c, int ny, int per_sm, int zblock, int aligned, int ski
   TmaPlan p{};
   const char *why = nullptr;
   cudaError_t e = plan_tma(p, c->g, c->eq == FD_ACOUSTIC ? kAcoustic : kDiffusion, c->iso, c->u,
-                           c->A, c->C, ny, per_sm, zblock, aligned, &why, tx);
+                           c->A, c->C, ny, per_sm, zblock, aligned, &why, tx, ctx_origin(c));
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(c, e == cudaErrorInvalidValue ? FD_EINVAL : FD_EUNSUPPORTED,
@@ -957,7 +962,7 @@ fd_status fd_create(fd_ctx **out, int ndim, const int64_t *shape, const double *
     const char *why = nullptr;
     c->iso = spacing[0] == spacing[1] && spacing[1] == spacing[2];
     e = plan_tma(c->tma, c->g, eq == FD_ACOUSTIC ? kAcoustic : kDiffusion, c->iso, c->u, c->A,
-                 c->C, 0, 0, 0, default_aligned(eq), &why);
+                 c->C, 0, 0, 0, default_aligned(eq), &why, kTmaTX, ctx_origin(c));
     if (e == cudaSuccess) {
       c->use_tma = true;
       c->kernel_name = c->tma.name;
@@ -1437,7 +1442,11 @@ fd_status fd_set_subdomain(fd_ctx *c, int64_t z_origin, int64_t z_global) {
   if (c->nsrc > 0 || c->nrec > 0)
     return fail(c, FD_ESTATE, "set the sub-domain before the sources and receivers");
   if (z_origin == 0 && z_global == 0) {
+    const bool was = c->z_global > 0;
     c->z_origin = c->z_global = 0;
+    if (was && c->use_tma)
+      return replan(c, c->tma.ny, c->tma.per_sm, c->tma.args.zblock, c->tma.args.aligned,
+                    c->skip_c ? 1 : 0, c->tma.tx);
     return FD_OK;
   }
   if (z_origin < 0 || z_global < 2 || z_origin + c->shape[0] > z_global)
@@ -1445,6 +1454,10 @@ fd_status fd_set_subdomain(fd_ctx *c, int64_t z_origin, int64_t z_global) {
                 (long long)z_origin, (long long)(z_origin + c->shape[0]), (long long)z_global);
   c->z_origin = z_origin;
   c->z_global = z_global;
+  // the z halo now holds the neighbours' planes: the tensor maps read it from memory
+  if (c->use_tma)
+    return replan(c, c->tma.ny, c->tma.per_sm, c->tma.args.zblock, c->tma.args.aligned,
+                  c->skip_c ? 1 : 0, c->tma.tx);
   return FD_OK;
 }
 
@@ -1756,14 +1769,15 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
   for (int ny : {2, 4}) {
     TmaPlan p{};
     const char *why = nullptr;
-    if (st || plan_tma(p, c->g, eq, c->iso, c->u, c->A, c->C, ny, 0, 0, 0, &why, tx) !=
-                  cudaSuccess) {
+    if (st || plan_tma(p, c->g, eq, c->iso, c->u, c->A, c->C, ny, 0, 0, 0, &why, tx,
+                       ctx_origin(c)) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
     for (int cps = 1; cps <= p.per_sm_max; ++cps) {
       TmaPlan q{};
-      if (plan_tma(q, c->g, eq, c->iso, c->u, c->A, c->C, ny, cps, 0, 0, &why, tx) != cudaSuccess) {
+      if (plan_tma(q, c->g, eq, c->iso, c->u, c->A, c->C, ny, cps, 0, 0, &why, tx,
+                   ctx_origin(c)) != cudaSuccess) {
         cudaGetLastError();
         continue;
       }
@@ -1796,7 +1810,7 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
     TmaPlan r{};
     const char *why = nullptr;
     if (plan_tma(r, c->g, eq, c->iso, c->u, c->A, c->C, cd.ny, cd.cps, cd.zb, cd.aligned, &why,
-                 cd.tx) != cudaSuccess) {
+                 cd.tx, ctx_origin(c)) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
@@ -2170,6 +2184,7 @@ fd_status fd_batch_run(fd_batch *b, int nticks) {
     d.map_t[1] = c->tma.map_t[1];
     d.map_a = c->tma.map_a;
     d.map_c = c->tma.map_c;
+    d.org = c->tma.args.org;
     d.g = c->g;
     d.c = c->coef;
     d.level[0] = c->u[0];

@@ -192,9 +192,20 @@ struct SparseArgs {
   int nsrc, nc;
 };
 
+// Where a tensor map's coordinate 0 lies, per axis: the kernels address every
+// box by interior coordinates plus these offsets.  Maps over the interior
+// (offset 0) let TMA fill the values outside the grid with zeros without reading
+// the zero halo from DRAM; a padded axis (offset kHaloX in x, R in y and z) reads
+// the halo from memory, where it holds data: the odd-reflection mirror
+// (diffusion) or, along z, a neighbouring slab's planes.
+struct MapOrigin {
+  int ox, oy, oz;
+};
+
 struct TmaArgs {
   Geom g;
   Coef c;
+  MapOrigin org;     // tensor-map origin of every map of this launch
   int tiles_x;       // tiles along x
   int ntiles;        // tiles in a plane
   int zblock;        // planes per z-block of the work order
@@ -236,6 +247,7 @@ struct alignas(64) ShotDesc {
   CUtensorMap map_a, map_c;
   Geom g;
   Coef c;
+  MapOrigin org;
   float *level[2];
   int tiles_x, ntiles, zblock, cur0;
   int64_t step0;
@@ -442,6 +454,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
         const CUtensorMap *mu = &map_u, *mp = &map_p, *ma = &map_a, *mc = &map_c;
         const unsigned char *uc_flags = kUnitC ? args.unit_c : nullptr;
         const int n0p = args.g.n0;
+        MapOrigin o = args.org;
         if constexpr (MULTI) {
           const ShotDesc &d = bat.shots[shot];
           const int par = d.cur0 ^ (int)(tick & 1);
@@ -449,6 +462,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
           mp = &d.map_t[par ^ 1];
           ma = &d.map_a;
           mc = &d.map_c;
+          o = d.org;
         }
         for (int p = za - R; p < zb + R; ++p) {
           if (*abort_flag) { ok = false; break; }
@@ -463,15 +477,13 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
             // where C = 1 on the whole tile-plane its tile is not loaded
             const bool cone = kUnitC && uc_flags && uc_flags[(int64_t)tile * n0p + zc];
             mbar_expect_tx(&full_x[slot], ((img ? 5 : 3) - (cone ? 1 : 0)) * XT * 4);
-            tma_load_3d_hint(dst, mp, x0 + kHaloX, y0 + R, zc + R, &full_x[slot], once);
-            tma_load_3d_hint(dst + XT, ma, x0 + kHaloX, y0 + R, zc + R, &full_x[slot], once);
-            if (!cone)
-              tma_load_3d_hint(dst + 2 * XT, mc, x0 + kHaloX, y0 + R, zc + R, &full_x[slot], once);
+            const int tx = x0 + o.ox, ty = y0 + o.oy, tz = zc + o.oz;  // tile box
+            tma_load_3d_hint(dst, mp, tx, ty, tz, &full_x[slot], once);
+            tma_load_3d_hint(dst + XT, ma, tx, ty, tz, &full_x[slot], once);
+            if (!cone) tma_load_3d_hint(dst + 2 * XT, mc, tx, ty, tz, &full_x[slot], once);
             if (img) {
-              tma_load_3d_hint(dst + 3 * XT, &map_e, x0 + kHaloX, y0 + R, zc + R, &full_x[slot],
-                               once);
-              tma_load_3d_hint(dst + 4 * XT, &map_g, x0 + kHaloX, y0 + R, zc + R, &full_x[slot],
-                               once);
+              tma_load_3d_hint(dst + 3 * XT, &map_e, tx, ty, tz, &full_x[slot], once);
+              tma_load_3d_hint(dst + 4 * XT, &map_g, tx, ty, tz, &full_x[slot], once);
             }
             ++sx;
           }
@@ -481,8 +493,9 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
             break;
           }
           mbar_expect_tx(&full_u[slot], tma_ubytes(R, NY));
-          tma_load_3d_hint(ring_u + slot * USLOT, mu, x0 + kHaloX - HXB, y0, p + R, &full_u[slot],
-                           keep);
+          // halo'd box: x from x0 - HXB, y from y0 - R (interior coordinates)
+          tma_load_3d_hint(ring_u + slot * USLOT, mu, x0 - HXB + o.ox, y0 - R + o.oy, p + o.oz,
+                           &full_u[slot], keep);
           ++su;
         }
       }
@@ -936,11 +949,11 @@ k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXp
             float *dst = ring_x + slot * 3 * XT;
             const bool cone = kUnitC && ucf && ucf[(int64_t)tile * args.g.n0 + zc];
             mbar_expect_tx(&full_x[slot], (3 - (cone ? 1 : 0)) * XT * 4);
-            tma_load_3d_hint(dst, &map_p, x0 + kHaloX, y0 + R, zc + R, &full_x[slot], once);
-            tma_load_3d_hint(dst + XT, &map_a, x0 + kHaloX, y0 + R, zc + R, &full_x[slot], once);
-            if (!cone)
-              tma_load_3d_hint(dst + 2 * XT, &map_c, x0 + kHaloX, y0 + R, zc + R, &full_x[slot],
-                               once);
+            const MapOrigin &o = args.org;
+            const int tx = x0 + o.ox, ty = y0 + o.oy, tz = zc + o.oz;  // tile box
+            tma_load_3d_hint(dst, &map_p, tx, ty, tz, &full_x[slot], once);
+            tma_load_3d_hint(dst + XT, &map_a, tx, ty, tz, &full_x[slot], once);
+            if (!cone) tma_load_3d_hint(dst + 2 * XT, &map_c, tx, ty, tz, &full_x[slot], once);
             ++sx;
           }
           const uint32_t slot = su % DU;
@@ -949,8 +962,8 @@ k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXp
             break;
           }
           mbar_expect_tx(&full_u[slot], xp_ubytes(R, NY));
-          tma_load_3d_hint(ring_u + slot * USLOT, &map_u, x0 + kHaloX - HXB, y0, p + R,
-                           &full_u[slot], keep);
+          tma_load_3d_hint(ring_u + slot * USLOT, &map_u, x0 - HXB + args.org.ox,
+                           y0 - R + args.org.oy, p + args.org.oz, &full_u[slot], keep);
           ++su;
         }
       }
@@ -1215,8 +1228,15 @@ inline EncodeFn tma_encoder() {
   return fn;
 }
 
-inline bool encode_map(EncodeFn enc, CUtensorMap *m, float *base, const Geom &g, int bw, int bh) {
-  const cuuint64_t dims[3] = {(cuuint64_t)g.px, (cuuint64_t)g.py, (cuuint64_t)(g.n0 + 2 * g.R0)};
+// A map of one padded field (base = its first padded element) with coordinate 0
+// of each axis at the origin o (see MapOrigin): an interior axis spans the n
+// interior nodes, a padded one the whole padded extent.
+inline bool encode_map(EncodeFn enc, CUtensorMap *m, float *field, const Geom &g, int bw, int bh,
+                       const MapOrigin &o) {
+  float *base = field + (int64_t)(g.R0 - o.oz) * g.plane + (int64_t)(g.R - o.oy) * g.px +
+                (kHaloX - o.ox);
+  const cuuint64_t dims[3] = {(cuuint64_t)(o.ox ? g.px : g.n2), (cuuint64_t)(o.oy ? g.py : g.n1),
+                              (cuuint64_t)(o.oz ? g.n0 + 2 * g.R0 : g.n0)};
   const cuuint64_t strides[2] = {(cuuint64_t)g.px * 4, (cuuint64_t)g.plane * 4};
   const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
@@ -1295,9 +1315,18 @@ inline bool tma_tx_supported(int tx, int) { return tx == kTmaTX || tx == kXpTX; 
 // Build the plan: tensor maps for both levels and the coefficient fields, for
 // ny rows per consumer thread (0: the default), a grid of per_sm CTAs per SM
 // (0: as many as fit) and z-blocks of zblock planes (0: about one CTA's share).
+// Map origin of a context: interior maps (zeros outside the grid from TMA's fill)
+// unless the halo holds data: padded in every axis for the odd-reflection
+// boundary, padded along z for a z-slab sub-domain (the neighbours' planes).
+inline MapOrigin map_origin(const Geom &g, bool odd_halo, bool z_halo) {
+  if (odd_halo) return MapOrigin{kHaloX, g.R, g.R0};
+  return MapOrigin{0, 0, z_halo ? g.R0 : 0};
+}
+
 inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float *const *level,
                             float *A, float *C, int ny, int per_sm, int zblock, int aligned,
-                            const char **why, int tx = kTmaTX) {
+                            const char **why, int tx = kTmaTX,
+                            MapOrigin org = MapOrigin{0, 0, 0}) {
   *why = nullptr;
   if (g.R0 == 0 || g.R < 1 || g.R > kMaxR) {
     *why = "3-D grids only";
@@ -1311,7 +1340,7 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float 
     return cudaErrorInvalidValue;
   }
   // TMA rules: 16-B aligned bases and strides, inner box extent a 16-B multiple,
-  // x coordinates multiples of 4 floats (x0 + kHaloX - HXB with x0 % 32 == 0).
+  // x coordinates multiples of 4 floats (x0 - HXB + ox with x0 % 32 == 0, ox 0 or kHaloX).
   if ((g.px * 4) % 16 || tma_hxb(R) % 4 || (tma_bw(R) * 4) % 16 || kHaloX % 4 ||
       tma_bw(R) > 256 || tma_bh(R, 4) > 256 || tma_ty(4) > 256 || (kTmaTX * 4) % 16 ||
       (xp_bw(R) * 4) % 16 || xp_bw(R) > 256 || kXpTX % 4) {
@@ -1326,16 +1355,17 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float 
   const int ty = tma_ty(ny);
   const bool xp = tx == kXpTX;
   for (int b = 0; b < 2; ++b) {
-    if (!encode_map(enc, &pl.map_u[b], level[b], g, xp ? xp_bw(R) : tma_bw(R), tma_bh(R, ny)) ||
-        !encode_map(enc, &pl.map_t[b], level[b], g, tx, ty)) {
+    if (!encode_map(enc, &pl.map_u[b], level[b], g, xp ? xp_bw(R) : tma_bw(R), tma_bh(R, ny),
+                    org) ||
+        !encode_map(enc, &pl.map_t[b], level[b], g, tx, ty, org)) {
       *why = "tensor map encoding failed";
       return cudaErrorInvalidValue;
     }
     pl.level[b] = level[b];
   }
   if (eq == kAcoustic) {
-    if (!encode_map(enc, &pl.map_a, A, g, tx, ty) ||
-        !encode_map(enc, &pl.map_c, C, g, tx, ty)) {
+    if (!encode_map(enc, &pl.map_a, A, g, tx, ty, org) ||
+        !encode_map(enc, &pl.map_c, C, g, tx, ty, org)) {
       *why = "tensor map encoding failed";
       return cudaErrorInvalidValue;
     }
@@ -1379,6 +1409,7 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float 
   pl.grid = pl.sms * pl.per_sm;
   if (pl.fn_fwi && pl.per_sm_fwi < pl.per_sm) pl.fn_fwi = nullptr;  // would not all be resident
   pl.args.g = g;
+  pl.args.org = org;
   pl.tx = tx;
   pl.args.tiles_x = (g.n2 + tx - 1) / tx;
   const int tiles_y = (g.n1 + ty - 1) / ty;
@@ -1443,8 +1474,8 @@ inline cudaError_t launch_tma_step_fwi(const TmaPlan &pl, int cur, float *out, c
   if (img) {
     EncodeFn enc = tma_encoder();
     if (!enc || !encode_map(enc, &me, const_cast<float *>(img_d2), pl.args.g, kTmaTX,
-                            tma_ty(pl.ny)) ||
-        !encode_map(enc, &mg, img, pl.args.g, kTmaTX, tma_ty(pl.ny)))
+                            tma_ty(pl.ny), pl.args.org) ||
+        !encode_map(enc, &mg, img, pl.args.g, kTmaTX, tma_ty(pl.ny), pl.args.org))
       return cudaErrorInvalidValue;
   }
   pl.fn_fwi<<<pl.grid, kTmaThreads, pl.smem_fwi, s>>>(pl.map_u[cur], pl.map_t[cur ^ 1], pl.map_a,
