@@ -61,16 +61,13 @@ WORKLOADS = {
 # are summarised in profiles/.  Absent (null) when not captured for the kernel
 # and tile configuration as they are now.
 NCU_TRAFFIC = {
-    # profiles/stencil3d_tma_acoustic256_so8.md: mean of 3 launches, read 298.56 MB + write 26.53 MB
-    ("stencil3d_tma_acoustic", "acoustic256", 8, 32, 32, 64, 2, 1, 0): 325.08e6,
-    # same file, C skipped where it is 1: mean of 3 launches, read 287.03 MB + write 26.52 MB
-    ("stencil3d_tma_acoustic", "acoustic256", 8, 32, 32, 64, 2, 1, 1): 313.55e6,
-    # profiles/stencil3d_xp_acoustic256_so8.md, the x-pair kernel (64 x 32 tiles, 1 CTA/SM),
-    # L2 not flushed between launches (the bench's conditions): mean of 3 launches, read
-    # 289.07 MB + write 67.57 MB
-    ("stencil3d_xp_acoustic", "acoustic256", 8, 64, 32, 64, 1, 1, 0): 356.64e6,
-    # profiles/stencil3d_tma_roofline512.md: mean of 2 launches, read 1996.73 MB + write 496.41 MB
-    ("stencil3d_tma_acoustic", "roofline512", 8, 32, 32, 512, 2, 1, 1): 2493.14e6,
+    # profiles/stencil3d_xp_acoustic256_so8.md ("interior tensor maps"): the x-pair kernel
+    # (64 x 32 tiles, 1 CTA/SM), L2 not flushed between launches (the bench's conditions):
+    # mean of 3 launches, read 261.36 MB + write 68.56 MB
+    ("stencil3d_xp_acoustic", "acoustic256", 8, 64, 32, 64, 1, 1, 0): 329.92e6,
+    # profiles/stencil3d_tma_acoustic256_so8.md ("interior tensor maps"): the 32-wide kernel
+    # (32 x 32 tiles, 2 CTAs/SM), same conditions: read 259.39 MB + write 66.86 MB
+    ("stencil3d_tma_acoustic", "acoustic256", 8, 32, 32, 64, 2, 1, 0): 326.25e6,
 }
 
 
@@ -89,6 +86,10 @@ def parse():
     ap.add_argument("--shots", type=int, default=64)
     ap.add_argument("--mean-gap", type=float, default=0.015)
     ap.add_argument("--hbm-budget-gb", type=float, default=8.0)
+    ap.add_argument("--work-cap", type=int, default=65_000_000,
+                    help="serving: most grid points one batch tick updates (0: no cap); "
+                         "65 M (about four 256^3 shots) keeps the GPU saturated while a "
+                         "long shot is not stretched by everything admitted beside it")
     ap.add_argument("--so", type=int, default=None)
     ap.add_argument("--nt", type=int, default=None)
     ap.add_argument("--kernel", default="auto", choices=["auto", "plain", "tma"])
@@ -989,7 +990,7 @@ def serving_result(args, rank=0, world=1):
     clocks = ClockSampler(gpu_id)
     be = DeviceBackend(8)
     srv = Server(be, hbm_budget=int(args.hbm_budget_gb * 2 ** 30), max_members=64,
-                 ticks_per_round=32)
+                 ticks_per_round=32, work_cap=args.work_cap)
     batched = summarize(srv.serve(reqs))
     be.close()
     seq = summarize(serve_sequential(reqs))
@@ -1002,7 +1003,9 @@ def serving_result(args, rank=0, world=1):
             "config": {"workload": f"poisson stream of {args.shots} acoustic shots, so 8",
                        "grids": "2-D 200^2-1000^2, 3-D 128^3-320^3", "nt": "300-1000",
                        "receivers": "128-512", "mean_gap_s": args.mean_gap,
-                       "hbm_budget_gb": args.hbm_budget_gb, "grid_point_updates": pts},
+                       "hbm_budget_gb": args.hbm_budget_gb, "grid_point_updates": pts,
+                       "admission": "first come first served, tick work cap %d points" %
+                                    args.work_cap},
             "serving": {k: round(v, 4) for k, v in batched.items()},
             "sequential": {k: round(v, 4) for k, v in seq.items()},
             "speedup_vs_sequential": round(batched["shots_per_s"] / seq["shots_per_s"], 3),
