@@ -50,6 +50,9 @@ FALLBACK_HBM_GBS = 6400.0
 WORKLOADS = {
     "acoustic256": dict(n=256, so=8, nt=500, nrec=256, nbl=40),
     "roofline512": dict(n=512, so=8, nt=200, nrec=0, nbl=40),
+    # the largest 2-D shot of the serving stream: 1000², so 8, 1000 steps, 512 receivers
+    # (a level is 4 MB: the fields stay in L2, so HBM is not the bound)
+    "acoustic2d": dict(n=1000, so=8, nt=1000, nrec=512, nbl=40, ndim=2),
 }
 
 # DRAM bytes per stencil launch from one ncu capture (dram__bytes_read.sum +
@@ -114,18 +117,22 @@ def problem(args):
         w["so"] = args.so
     if args.nt:
         w["nt"] = args.nt
-    p = fdsynth.acoustic_problem(n=w["n"], ndim=3, so=w["so"], nbl=w["nbl"], nt=w["nt"],
-                                 nrec=w["nrec"], seed=0)
+    p = fdsynth.acoustic_problem(n=w["n"], ndim=w.get("ndim", 3), so=w["so"], nbl=w["nbl"],
+                                 nt=w["nt"], nrec=w["nrec"], seed=0)
     return w, p
 
 
 def config_of(args, w, kernel_name=None):
-    cfg = {"workload": f"acoustic3d_{w['n']}^3_so{w['so']}_nt{w['nt']}",
-           "grid": [w["n"]] * 3, "space_order": w["so"], "nt": w["nt"], "nrec": w["nrec"],
+    nd = w.get("ndim", 3)
+    cfg = {"workload": f"acoustic{nd}d_{w['n']}^{nd}_so{w['so']}_nt{w['nt']}",
+           "grid": [w["n"]] * nd, "space_order": w["so"], "nt": w["nt"], "nrec": w["nrec"],
            "nsrc": 1, "damping_layer": w["nbl"], "dx_m": 10.0,
            "step": "one shot: coefficient setup + field reset + nt time steps",
-           "l2": "inputs larger than L2 (u^n, u^{n-1}, A, C = 4 x %.0f MB)" %
-                 ((w["n"] + 8) ** 2 * (w["n"] + 64) * 4 / 1e6)}
+           "l2": ("inputs larger than L2 (u^n, u^{n-1}, A, C = 4 x %.0f MB)" %
+                  ((w["n"] + 8) ** 2 * (w["n"] + 64) * 4 / 1e6)) if nd == 3 else
+                 ("fields L2-resident (4 levels of %.1f MB): the per-launch time is bound by "
+                  "L2 bandwidth and launch latency, not HBM" %
+                  ((w["n"] + 8) * (w["n"] + 64) * 4 / 1e6))}
     if kernel_name:
         cfg["kernel"] = kernel_name
     return cfg
@@ -318,8 +325,8 @@ def fwi_problem(args):
     w = dict(FWI)
     if args.nt:
         w["nt"] = args.nt
-    p = fdsynth.acoustic_problem(n=w["n"], ndim=3, so=w["so"], nbl=w["nbl"], nt=w["nt"],
-                                 nrec=w["nrec"], seed=0)
+    p = fdsynth.acoustic_problem(n=w["n"], ndim=w.get("ndim", 3), so=w["so"], nbl=w["nbl"],
+                                 nt=w["nt"], nrec=w["nrec"], seed=0)
     return w, p
 
 

@@ -44,10 +44,16 @@ class ShotResult:
 
 
 class DeviceBackend:
-    """Shots as library contexts in one ``fd_batch`` (the real device)."""
+    """Shots as library contexts in one ``fd_batch`` (the real device).
 
-    def __init__(self, space_order):
+    ``device``: the CUDA device the shots run on, made current on the calling
+    thread (the library creates contexts on the current device)."""
+
+    def __init__(self, space_order, device=None):
         from .solver import Batch
+        if device is not None:
+            import torch
+            torch.cuda.set_device(device)
         self.batch = Batch(space_order)
 
     def footprint(self, req):
@@ -229,6 +235,50 @@ class Server:
             if pool is not None:
                 pool.shutdown(wait=True)
         return sorted(results, key=lambda x: x.id)
+
+
+def dispatch(requests, ndev, rate=None):
+    """Place each request on one of ``ndev`` devices: the one predicted to be free
+    first when it arrives (join the least-loaded queue).  A device's predicted free
+    time moves to max(free, arrival) + work / rate, with work = points × steps
+    (:func:`shot_work`) and ``rate`` its update rate (1 when not given: only the
+    order matters).  Returns one device index per request, in request order."""
+    rate = float(rate or 1.0)
+    free = [0.0] * ndev
+    out = {}
+    for r in sorted(requests, key=lambda r: (r.arrival, r.id)):
+        d = min(range(ndev), key=lambda k: (max(free[k], r.arrival), k))
+        free[d] = max(free[d], r.arrival) + shot_work(r) / rate
+        out[r.id] = d
+    return [out[r.id] for r in requests]
+
+
+def serve_multi(requests, make_server, ndev, rate=None):
+    """Serve a stream on ``ndev`` devices, shots being replicas: :func:`dispatch`
+    splits the requests, ``make_server(d)`` builds device d's :class:`Server`
+    (called on d's worker thread, so a backend can make d current there), and the
+    servers run concurrently, one host thread per device.  Returns every result,
+    sorted by request id."""
+    import threading
+    where = dispatch(requests, ndev, rate)
+    parts = [[r for r, d in zip(requests, where) if d == k] for k in range(ndev)]
+    results, errors = [None] * ndev, []
+
+    def work(k):
+        try:
+            srv = make_server(k)
+            results[k] = srv.serve(parts[k]) if parts[k] else []
+        except BaseException as e:          # re-raised on the calling thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(k,)) for k in range(ndev)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    if errors:
+        raise errors[0]
+    return sorted((x for part in results for x in part), key=lambda x: x.id)
 
 
 def serve_sequential(requests, clock=time.perf_counter, sleep=time.sleep):

@@ -196,3 +196,35 @@ def test_setup_on_a_worker_keeps_budget_slots_and_results():
     assert be.peak_used <= 10 and be.peak_members <= 3
     for r in res:
         assert r.arrival <= r.admitted <= r.finished
+
+
+def test_dispatch_joins_the_least_loaded_device():
+    from paper_1906_10811_b300.serve import dispatch
+    # work = points x steps; rate 1: device d is free at the sum of its shots' work
+    reqs = _reqs_pts([(0.0, 1, 10, 10), (0.0, 1, 10, 1), (0.0, 1, 10, 1), (0.5, 1, 10, 1),
+                      (200.0, 1, 10, 1)])
+    where = dispatch(reqs, 2)
+    assert where[0] == 0 and where[1] == 1   # both free at t = 0: the lower index, then the other
+    assert where[2] == 1                     # device 1 frees at 10, device 0 at 100
+    assert where[3] == 1                     # device 1 frees at 20 < 100
+    assert where[4] == 0                     # both free by t = 200: the lower index
+    assert dispatch(reqs, 1) == [0] * 5
+
+
+def test_serve_multi_runs_every_shot_once_on_its_device():
+    from paper_1906_10811_b300.serve import dispatch, serve_multi
+    reqs = _reqs_pts([(0.0, 1, 20 + i, 1 + i % 3) for i in range(9)])
+    backends = {}
+
+    def make(d):
+        clk = FakeClock()
+        be = FakeBackend(clk)
+        backends[d] = be
+        return Server(be, hbm_budget=100, max_members=4, ticks_per_round=8, clock=clk,
+                      sleep=clk.sleep)
+
+    res = serve_multi(reqs, make, 3)
+    assert [r.id for r in res] == list(range(9))
+    assert all(r.traces == reqs[r.id].problem["nt"] for r in res)
+    where = dispatch(reqs, 3)
+    assert set(backends) == {d for d in where}
