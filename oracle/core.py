@@ -42,7 +42,7 @@ def _load():
         lib.oracle_laplacian.argtypes = [ctypes.c_int, _i64p, _f64p, ctypes.c_int, _f64p, _f64p, _f64p]
         lib.oracle_diffusion.argtypes = [ctypes.c_int, _i64p, _f64p, ctypes.c_int, _f64p,
                                          ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                         ctypes.c_int, _f64p]
+                                         ctypes.c_int, ctypes.c_int, _f64p]
         lib.oracle_corners.argtypes = [ctypes.c_int, _i64p, _f64p, _f64p, _i64p, _f64p]
         lib.oracle_acoustic.argtypes = [ctypes.c_int, _i64p, _f64p, ctypes.c_int, _f64p,
                                         ctypes.c_double, _f64p, _f64p, _f64p, _f64p,
@@ -86,17 +86,20 @@ def laplacian(u, spacing, so, weights=None):
     return out
 
 
-def diffusion(u0, spacing, so, nu, dt, nt, weights=None, boundary="zero"):
-    """Forward-Euler diffusion, interior update, boundary nodes held; returns u^nt.
+def diffusion(u0, spacing, so, nu, dt, nt, weights=None, boundary="zero", interior=True):
+    """Forward-Euler diffusion; returns u^nt.
 
+    interior True: interior nodes updated, boundary nodes held (§2.1.1's
+    grid.interior subdomain, the §5.1.2 benchmark); False: every node updated.
     boundary "zero": zero outside the grid; "odd": outside values are the
-    negated mirror images about the boundary nodes."""
+    negated mirror images about the boundary nodes (interior update only)."""
     u = _d(u0).copy()
     w = _d(weights if weights is not None else fd_weights(so))
     h = _d(spacing)
     bc = {"zero": 0, "odd": 1}[boundary]
     _check(_load().oracle_diffusion(u.ndim, _ptr(_shape(u.shape), _i64p), _ptr(h), so, _ptr(w),
-                                    float(nu), float(dt), int(nt), bc, _ptr(u)),
+                                    float(nu), float(dt), int(nt), bc, int(bool(interior)),
+                                    _ptr(u)),
            "oracle_diffusion")
     return u
 

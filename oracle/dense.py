@@ -58,11 +58,13 @@ def tent_row(shape, spacing, coord):
     return wt.reshape(-1)
 
 
-def diffusion(u0, spacing, so, nu, dt, nt, weights=None, boundary="zero"):
+def diffusion(u0, spacing, so, nu, dt, nt, weights=None, boundary="zero", interior_only=True):
     shape = u0.shape
     lap = laplacian_matrix(shape, spacing, so, weights, odd=boundary == "odd")
     interior = np.ones(shape, dtype=bool)
     for d, n in enumerate(shape):
+        if not interior_only:
+            break
         sl = [slice(None)] * len(shape)
         sl[d] = 0
         interior[tuple(sl)] = False

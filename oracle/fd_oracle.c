@@ -22,7 +22,9 @@
  *
  *   L u (i)  = Σ_d  (1/h_d²) Σ_{k=-r..r} w_|k| u(i + k e_d)        (r = so/2)
  *
- *   diffusion (forward Euler, interior nodes only, boundary nodes fixed):
+ *   diffusion (forward Euler; §2.1.1's `subdomain=grid.interior`: interior nodes
+ *   only, boundary nodes fixed; or, without that subdomain (interior = 0), every
+ *   node, the values outside the grid zero):
  *     u^{n+1} = u^n + ν dt L u^n
  *
  *   acoustic (all nodes, σ = damp·dt/2):
@@ -144,11 +146,12 @@ int oracle_laplacian(int ndim, const int64_t *shape, const double *h, int so,
 /* Diffusion, forward Euler, interior update (u is overwritten by u^{nt});
  * bc = 0: zero outside the grid, bc = 1: odd reflection about the boundary nodes. */
 int oracle_diffusion(int ndim, const int64_t *shape, const double *h, int so,
-                     const double *w, double nu, double dt, int nt, int bc, double *u) {
+                     const double *w, double nu, double dt, int nt, int bc, int interior,
+                     double *u) {
   grid_t g;
   if (grid_init(&g, ndim, shape) || so < 2 || so % 2 || nt < 0) return OR_EINVAL;
   const int r = so / 2;
-  if (bc != 0 && (bc != 1 || !mirror_ok(&g, r))) return OR_EINVAL;
+  if (bc != 0 && (bc != 1 || !mirror_ok(&g, r) || !interior)) return OR_EINVAL;
   double *v = (double *)malloc(sizeof(double) * (size_t)g.total);
   if (!v) return OR_ENOMEM;
   double *cur = u, *nxt = v;
@@ -159,7 +162,7 @@ int oracle_diffusion(int ndim, const int64_t *shape, const double *h, int so,
         for (int64_t c = 0; c < g.e[2]; ++c) {
           int64_t idx[3], p = (a * g.e[1] + b) * g.e[2] + c;
           point_index(&g, a, b, c, idx);
-          if (on_boundary(&g, idx))
+          if (interior && on_boundary(&g, idx))
             nxt[p] = cur[p];
           else
             nxt[p] = cur[p] + nu * dt * lap_point(cur, &g, h, r, w, idx, p, bc);

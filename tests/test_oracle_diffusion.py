@@ -156,3 +156,45 @@ def test_odd_reflection_matches_dense_brute_force(so, shape):
 def test_odd_reflection_needs_room_for_the_mirror():
     with pytest.raises(core.OracleError):
         core.diffusion(np.zeros((5, 9)), (1.0, 1.0), 10, 0.5, 0.01, 1, boundary="odd")
+
+
+# --- every node updated (§2.1.1's operator without the grid.interior subdomain) ---
+
+@pytest.mark.parametrize("ndim,n,k", [(2, 40, (1, 1)), (2, 31, (3, 2)), (3, 18, (1, 2, 3))])
+def test_all_node_update_sine_mode_decays_by_exact_factor(ndim, n, k):
+    """Every node updated with zero values outside: the mode Π sin(k_d π (i+1)/(n+1)),
+    i = 0..n-1, vanishes on the first outside layer, so at so 2 it is an exact
+    eigenvector: u^n = g^n u^0 with g = 1 + ν dt Σ_d (-4/h²) sin²(k_d π / (2(n+1)))."""
+    h = 1.0 / (n + 1)
+    u0 = np.ones(())
+    for d in range(ndim):
+        u0 = np.multiply.outer(u0, np.sin(k[d] * math.pi * (np.arange(n) + 1) / (n + 1)))
+    nu, nt = 0.5, 80
+    dt = 0.1 * h * h / nu
+    g = 1.0 + nu * dt * sum(-4.0 / h ** 2 * math.sin(kd * math.pi / (2 * (n + 1))) ** 2
+                            for kd in k[:ndim])
+    u = core.diffusion(u0, (h,) * ndim, 2, nu, dt, nt, interior=False)
+    assert np.abs(u - g ** nt * u0).max() < 1e-13
+    # the interior update holds the boundary nodes instead: a different sweep
+    assert np.abs(core.diffusion(u0, (h,) * ndim, 2, nu, dt, nt) - u).max() > 1e-3
+
+
+@pytest.mark.parametrize("so", (2, 4, 8, 12, 16))
+@pytest.mark.parametrize("shape", [(9, 11), (6, 7, 8)])
+def test_all_node_update_matches_dense_brute_force(so, shape):
+    rng = np.random.default_rng(so + len(shape))
+    u0 = rng.standard_normal(shape)
+    h = tuple(1.0 / (n + 1) for n in shape)
+    nu = 0.5
+    dt = 0.02 * min(h) ** 2
+    got = core.diffusion(u0, h, so, nu, dt, 12, interior=False)
+    ref = dense.diffusion(u0, h, so, nu, dt, 12, interior_only=False)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+    edge = got[0]
+    assert np.abs(edge - u0[0]).max() > 0          # boundary nodes move
+
+
+def test_odd_reflection_needs_the_interior_update():
+    u0 = np.ones((12, 12))
+    with pytest.raises(core.OracleError):
+        core.diffusion(u0, (0.1, 0.1), 4, 0.5, 1e-4, 1, boundary="odd", interior=False)
