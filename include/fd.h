@@ -16,7 +16,7 @@
  *   FD_DIFFUSION  (§5.1.2, u_t = ν Σ_d u_dd, forward Euler, time order 1):
  *       u^{n+1} = u^n + ν dt L u^n     on interior nodes (index 1..n_d-2 on
  *       every axis, §2.1.1's grid.interior); boundary nodes keep the values
- *       given to fd_set_field.
+ *       given to fd_set_field (fd_options.dirichlet_interior = 0: on every node).
  *   FD_ACOUSTIC   (the seismic operator of §6.2.1, m u_tt + damp u_t = L u + src,
  *       second-order leapfrog on every node, σ = damp·dt/2):
  *       u^{n+1} = [dt² L u^n + 2m u^n - (m-σ) u^{n-1}] / (m+σ)
@@ -98,6 +98,10 @@ typedef struct {
                          choice is cached per grid shape, space order and equation
                          for the process); 0 (default): the default tile */
   int boundary;       /* fd_boundary; default FD_BOUNDARY_ZERO */
+  int dirichlet_interior; /* FD_DIFFUSION: 1 (default) = update the interior nodes and
+                         hold the boundary nodes (§2.1.1's `subdomain=grid.interior`, the
+                         §5.1.2 benchmark); 0 = update every node, the values outside
+                         the grid given by `boundary` (FD_BOUNDARY_ZERO only) */
 } fd_options;
 
 /* Fill *opt with the defaults above.  (Library service; no counterpart in the paper.) */
@@ -135,7 +139,7 @@ fd_status fd_set_model(fd_ctx *ctx, const float *m, const float *damp);
  * and §5.1.2 (the benchmark's initial condition).
  * Set the current time level(s).  FD_ACOUSTIC: u_cur = u^n, u_prev = u^{n-1}
  * (NULL: equal to u_cur).  FD_DIFFUSION: u_cur only (u_prev ignored); the
- * boundary values given here are held.  Does not change the step counter.
+ * boundary values given here are held (with dirichlet_interior = 1).  Does not change the step counter.
  * With u_prev NULL (or equal to u_cur) the field is uploaded once for both levels.
  */
 fd_status fd_set_field(fd_ctx *ctx, const float *u_cur, const float *u_prev);

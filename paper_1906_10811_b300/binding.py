@@ -35,7 +35,8 @@ class fd_options(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
                 ("device_ptrs", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("profile", ctypes.c_int), ("kernel", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("boundary", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("boundary", ctypes.c_int),
+                ("dirichlet_interior", ctypes.c_int)]
 
 
 class fd_tile_config(ctypes.Structure):
@@ -144,7 +145,11 @@ def _check(ctx, st):
 
 
 def _ptr(x, keep):
-    """Address of a float32 C-contiguous array (numpy host array or torch tensor)."""
+    """Address of a float32 C-contiguous array (numpy host array or torch tensor, or an
+    int taken as a raw address).  A torch tensor of another dtype or layout is
+    converted on torch's current stream: a caller whose library work runs on another
+    stream must order that stream after the conversion (``Solver`` converts before
+    it orders its stream)."""
     if x is None:
         return None
     if isinstance(x, int):
@@ -174,7 +179,8 @@ def _out_ptr(x):
 
 
 def options(nu=0.5, cuda_stream=None, device_ptrs=False, use_graphs=True, profile=False,
-            kernel=FD_KERNEL_AUTO, autotune=False, boundary=FD_BOUNDARY_ZERO):
+            kernel=FD_KERNEL_AUTO, autotune=False, boundary=FD_BOUNDARY_ZERO,
+            dirichlet_interior=True):
     o = fd_options()
     load().fd_options_default(ctypes.byref(o))
     o.nu = nu
@@ -185,6 +191,7 @@ def options(nu=0.5, cuda_stream=None, device_ptrs=False, use_graphs=True, profil
     o.kernel = int(kernel)
     o.autotune = int(bool(autotune))
     o.boundary = int(boundary)
+    o.dirichlet_interior = int(bool(dirichlet_interior))
     return o
 
 

@@ -783,6 +783,7 @@ void fd_options_default(fd_options *o) {
   o->nu = 0.5;
   o->use_graphs = 1;
   o->kernel = FD_KERNEL_AUTO;
+  o->dirichlet_interior = 1;
 }
 
 const char *fd_version(void) { return "fd_b300 0.1 (sm_103a)"; }
@@ -846,9 +847,14 @@ fd_status fd_create(fd_ctx **out, int ndim, const int64_t *shape, const double *
     return fail(nullptr, FD_EINVAL, "unknown kernel selector %d", o.kernel);
   if (o.boundary != FD_BOUNDARY_ZERO && o.boundary != FD_BOUNDARY_ODD)
     return fail(nullptr, FD_EINVAL, "unknown boundary mode %d", o.boundary);
+  if (o.dirichlet_interior != 0 && o.dirichlet_interior != 1)
+    return fail(nullptr, FD_EINVAL, "dirichlet_interior must be 0 or 1");
   if (o.boundary == FD_BOUNDARY_ODD) {
     if (eq != FD_DIFFUSION)
       return fail(nullptr, FD_EUNSUPPORTED, "FD_BOUNDARY_ODD is for FD_DIFFUSION");
+    if (!o.dirichlet_interior)
+      return fail(nullptr, FD_EINVAL, "FD_BOUNDARY_ODD mirrors about held boundary nodes "
+                                      "(dirichlet_interior = 1)");
     for (int d = 0; d < ndim; ++d)
       if (shape[d] - 1 < space_order / 2)
         return fail(nullptr, FD_EINVAL,
@@ -891,6 +897,7 @@ fd_status fd_create(fd_ctx **out, int ndim, const int64_t *shape, const double *
   g.py = g.n1 + 2 * R;
   g.plane = (int64_t)g.px * g.py;
   g.total = g.plane * (g.n0 + 2 * g.R0);
+  g.hold = (eq == FD_DIFFUSION && o.dirichlet_interior) ? 1 : 0;
 
   // coefficients (axis mapping: user axis d -> internal axis d + 3 - ndim)
   double w[kMaxR + 1];

@@ -29,6 +29,7 @@ struct Geom {
   int py;            // rows per plane = n1 + 2R
   int64_t plane;     // px * py
   int64_t total;     // px * py * (n0 + 2 R0)
+  int hold;          // diffusion: 1 = boundary nodes held (interior update), 0 = every node
 };
 
 __host__ __device__ inline int64_t gidx(const Geom &g, int z, int y, int x) {

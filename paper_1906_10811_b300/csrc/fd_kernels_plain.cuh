@@ -52,8 +52,8 @@ __device__ __forceinline__ void plain_point(const float *__restrict__ u, float *
   if (EQ == kAcoustic) {
     un[p] = leapfrog(A[p], C[p], uc, un[p], lap);
   } else {
-    const bool interior = x > 0 && x < g.n2 - 1 && y > 0 && y < g.n1 - 1 &&
-                          (!THREE_D || (z > 0 && z < g.n0 - 1));
+    const bool interior = !g.hold || (x > 0 && x < g.n2 - 1 && y > 0 && y < g.n1 - 1 &&
+                                      (!THREE_D || (z > 0 && z < g.n0 - 1)));
     if (interior) un[p] = uc + lap;
   }
 }
@@ -103,7 +103,7 @@ __device__ __forceinline__ void tile2d_update(const float *__restrict__ u, float
     if (EQ == kAcoustic) {
       un[p] = leapfrog(A[p], C[p], uc, un[p], lap);
     } else {
-      if (x > 0 && x < g.n2 - 1 && y > 0 && y < g.n1 - 1) un[p] = uc + lap;
+      if (!g.hold || (x > 0 && x < g.n2 - 1 && y > 0 && y < g.n1 - 1)) un[p] = uc + lap;
     }
   }
 }

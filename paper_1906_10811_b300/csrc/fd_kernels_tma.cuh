@@ -580,8 +580,8 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
 #pragma unroll
     for (int j = 0; j < NY; ++j) {
       const int y = ybase + j;
-      const bool in = AC ? (x < g.n2 && y < g.n1)
-                         : (x > 0 && x < g.n2 - 1 && y > 0 && y < g.n1 - 1);
+      const bool in = (AC || !g.hold) ? (x < g.n2 && y < g.n1)
+                                      : (x > 0 && x < g.n2 - 1 && y > 0 && y < g.n1 - 1);
       rows_ok |= (in ? 1u : 0u) << j;
     }
     float *optr = out + gidx(g, za, ybase, x);
@@ -754,7 +754,8 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
                   }
                 }
               } else {
-                if ((rows_ok & (1u << j)) && zc > 0 && zc < n0 - 1) __stcs(optr + j * g.px, val[j]);
+                if ((rows_ok & (1u << j)) && (!g.hold || (zc > 0 && zc < n0 - 1)))
+                  __stcs(optr + j * g.px, val[j]);
               }
             }
             optr += g.plane;
@@ -1000,14 +1001,15 @@ k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXp
     const int x = (tile % args.tiles_x) * kXpTX + 2 * lane;
     const int ybase = (tile / args.tiles_x) * TY + row0;
     // which of the pair's points a row stores: acoustic every node, diffusion
-    // interior nodes only
-    const bool xin0 = AC ? x < g.n2 : (x > 0 && x < g.n2 - 1);
-    const bool xin1 = AC ? x + 1 < g.n2 : (x + 1 > 0 && x + 1 < g.n2 - 1);
+    // interior nodes only (every node without the held boundary)
+    const bool all = AC || !g.hold;
+    const bool xin0 = all ? x < g.n2 : (x > 0 && x < g.n2 - 1);
+    const bool xin1 = all ? x + 1 < g.n2 : (x + 1 > 0 && x + 1 < g.n2 - 1);
     unsigned rows_ok = 0;
 #pragma unroll
     for (int j = 0; j < NY; ++j) {
       const int y = ybase + j;
-      rows_ok |= ((AC ? y < g.n1 : (y > 0 && y < g.n1 - 1)) ? 1u : 0u) << j;
+      rows_ok |= ((all ? y < g.n1 : (y > 0 && y < g.n1 - 1)) ? 1u : 0u) << j;
     }
     float *optr = out + gidx(g, za, ybase, x);
     int ecur = 0, eend = 0, nxt_z = INT_MAX;
@@ -1143,7 +1145,7 @@ k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXp
               nxt_z = h.nxt_z;
             }
             // diffusion: interior planes only (boundary values stay as set)
-            if (AC || (zc > 0 && zc < n0 - 1)) {
+            if (all || (zc > 0 && zc < n0 - 1)) {
 #pragma unroll
               for (int j = 0; j < NY; ++j) {
                 if (!(rows_ok & (1u << j))) continue;

@@ -25,7 +25,7 @@ class Solver:
 
     def __init__(self, shape, spacing, space_order, dt, equation="acoustic", nu=0.5,
                  device=False, stream=None, graphs=True, profile=False, kernel="auto",
-                 autotune=False, boundary="zero"):
+                 autotune=False, boundary="zero", dirichlet_interior=True):
         self.ctx = None
         self.shape = tuple(int(s) for s in shape)
         self.ndim = len(self.shape)
@@ -45,7 +45,7 @@ class Solver:
             self.stream = s
         opt = B.options(nu=nu, cuda_stream=cuda_stream, device_ptrs=self.device, use_graphs=graphs,
                         profile=profile, kernel=_KERNEL[kernel], autotune=autotune,
-                        boundary=_BOUNDARY[boundary])
+                        boundary=_BOUNDARY[boundary], dirichlet_interior=dirichlet_interior)
         self._in()
         self.ctx = B.fd_create(self.ndim, self.shape, spacing, space_order, dt, _EQ[equation], opt)
         self._out()
@@ -81,22 +81,37 @@ class Solver:
             self._torch.cuda.current_stream().wait_stream(self.stream)
 
     # -- inputs ------------------------------------------------------------
+    def _f32(self, x):
+        """Device mode: a float32 contiguous tensor, converted on the caller's stream
+        before the solver's stream is ordered after it (so the library reads the
+        converted copy, not memory still being written)."""
+        if x is None or not self.device or not hasattr(x, "data_ptr"):
+            return x
+        torch = self._torch
+        if x.dtype != torch.float32 or not x.is_contiguous():
+            x = x.to(torch.float32).contiguous()
+        return x
+
     def set_model(self, m, damp=None):
+        m, damp = self._f32(m), self._f32(damp)
         self._in()
         B.fd_set_model(self.ctx, m, damp)
 
     def set_field(self, u, u_prev=None):
+        u, u_prev = self._f32(u), self._f32(u_prev)
         self._in()
         B.fd_set_field(self.ctx, u, u_prev)
         self._out()
 
     def set_sources(self, coords, wavelets):
+        coords, wavelets = self._f32(coords), self._f32(wavelets)
         self._in()
         n = 0 if coords is None else len(coords)
         nt = 0 if wavelets is None else int(wavelets.shape[0])
         B.fd_set_sources(self.ctx, n, coords, nt, wavelets)
 
     def set_receivers(self, coords):
+        coords = self._f32(coords)
         self._in()
         self.nrec = 0 if coords is None else len(coords)
         B.fd_set_receivers(self.ctx, self.nrec, coords)

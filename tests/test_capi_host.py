@@ -73,6 +73,7 @@ def test_options_default(lib):
     o = fd_options_default()
     assert o.nu == 0.5 and o.use_graphs == 1 and o.device_ptrs == 0 and o.profile == 0
     assert o.kernel == 0 and o.cuda_stream is None
+    assert o.dirichlet_interior == 1           # the §5.1.2 benchmark's interior update
 
 
 @pytest.mark.parametrize("args,msg", [

@@ -370,3 +370,29 @@ def test_2d_staged_tiles_are_bitwise_the_plain_kernel(so, shape):
             outs.append(s.read()[0])
     assert np.array_equal(outs[0], outs[1])
     assert np.array_equal(outs[0][0], u0[0]) and np.array_equal(outs[0][:, -1], u0[:, -1])
+
+
+@pytest.mark.parametrize("kernel,shape,tile", [
+    ("plain", (41, 37), None), ("auto", (41, 37), None), ("plain", (23, 29, 70), None),
+    ("tma", (23, 29, 70), None), ("tma", (23, 29, 131), dict(tile_x=64, tile_y=16)),
+    ("tma", (23, 29, 70), dict(tile_y=16, aligned=1, zblock=7))])
+@pytest.mark.parametrize("so", (2, 8, 16))
+def test_diffusion_every_node_updated(kernel, shape, tile, so):
+    """dirichlet_interior = 0: every node updated with zeros outside the grid (§2.1.1's
+    operator without the interior subdomain), against the oracle's all-node sweep."""
+    from paper_1906_10811_b300 import Solver
+    rng = np.random.default_rng(so + len(shape))
+    u0 = rng.standard_normal(shape).astype(np.float32)
+    h = tuple(1.0 / (n + 1) for n in shape)
+    dt = 0.05 * min(h) ** 2
+    with Solver(shape, h, so, dt, "diffusion", kernel=kernel, dirichlet_interior=False) as s:
+        if tile:
+            s.set_tile_config(**tile)
+        s.set_field(u0)
+        s.run(30)
+        u, _ = s.read()
+    ref = oracle.diffusion(u0, h, so, 0.5, dt, 30, interior=False)
+    assert rel_l2(u, ref) <= 1e-5
+    assert np.abs(u[0] - u0[0]).max() > 0          # boundary nodes move
+    held = oracle.diffusion(u0, h, so, 0.5, dt, 30)
+    assert rel_l2(held, ref) > 1e-4                # the two sweeps differ measurably
