@@ -121,6 +121,7 @@ struct fd_ctx {
   // kernel selection
   StencilFn plain_fn = nullptr;
   StencilFnTile tile2d_fn = nullptr;  // 2-D grids: the shared-memory-staged kernel
+  int tile2d_ty = 0;                  // its tile height (rows)
   TmaPlan tma{};
   bool use_tma = false;
   bool iso = false;          // equal spacing on all axes (pipelined kernel variant)
@@ -394,7 +395,7 @@ fd_status launch_stencil(fd_ctx *c, const float *ucur, float *unext, int j) {
   }
   dim3 block(32, 8);
   if (c->tile2d_fn) {
-    dim3 tiles((c->g.n2 + 31) / 32, (c->g.n1 + kT2TY - 1) / kT2TY);
+    dim3 tiles((c->g.n2 + 31) / 32, (c->g.n1 + c->tile2d_ty - 1) / c->tile2d_ty);
     c->tile2d_fn<<<tiles, block, 0, c->stream>>>(ucur, unext, c->A, c->C, c->g, c->coef);
     CHECK_LAUNCH();
     return FD_OK;
@@ -693,9 +694,23 @@ void select_kernel(fd_ctx *c) {
   c->kernel_name = three ? "stencil3d_plain" : "stencil2d_plain";
   c->tile2d_fn = nullptr;
   if (!three && c->opt.kernel != FD_KERNEL_PLAIN) {
+    // 32-row tiles (four rows a thread) once they give two blocks per SM, else 8-row
+    // tiles: a small grid needs the blocks more than the halo savings
+    const int64_t tiles32 = (int64_t)((c->g.n2 + 31) / 32) * ((c->g.n1 + 31) / 32);
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      sms = 148;
+    }
+    c->tile2d_ty = tiles32 >= 2 * sms ? 32 : 8;
+    const bool t32 = c->tile2d_ty == 32;
 #define PICK2(RR)                                                                      \
   case RR:                                                                             \
-    c->tile2d_fn = ac ? k_stencil2d_tile<RR, kAcoustic> : k_stencil2d_tile<RR, kDiffusion>; \
+    c->tile2d_fn = ac ? (t32 ? k_stencil2d_tile<RR, kAcoustic, 32>                     \
+                             : k_stencil2d_tile<RR, kAcoustic, 8>)                     \
+                      : (t32 ? k_stencil2d_tile<RR, kDiffusion, 32>                    \
+                             : k_stencil2d_tile<RR, kDiffusion, 8>);                   \
     break;
     switch (R) {
       PICK2(1) PICK2(2) PICK2(3) PICK2(4) PICK2(5) PICK2(6) PICK2(7) PICK2(8)

@@ -60,8 +60,8 @@ __device__ __forceinline__ void plain_point(const float *__restrict__ u, float *
 
 // ---------------------------------------------------------------------------
 // 2-D step staged through shared memory.  A block of 32 × 8 threads updates a
-// tile of 32 × kT2TY points: the tile's u^n with its R-wide halo, (32 + 2R) ×
-// (kT2TY + 2R) floats, is loaded once with coalesced rows (the padded layout
+// tile of 32 × TY points: the tile's u^n with its R-wide halo, (32 + 2R) ×
+// (TY + 2R) floats, is loaded once with coalesced rows (the padded layout
 // holds the zero halo, so every staged row lies in the field) and every
 // neighbour read comes from shared memory.  A thread owns column x of rows
 // ty, ty + 8, ... (a warp reads one row: no bank conflicts).  The per-point
@@ -69,14 +69,15 @@ __device__ __forceinline__ void plain_point(const float *__restrict__ u, float *
 // kernel's.  2-D fields of the serving sizes (≤ 1000², 4 MB a level) live in
 // L2, so the bound here is L2 bandwidth and launch latency, not HBM.
 // ---------------------------------------------------------------------------
-constexpr int kT2TY = 32;  // tile rows (4 per thread)
+constexpr int kT2TY = 32;  // tile rows of the batched kernel (4 per thread)
 
-template <int R, int EQ>
+// TY: tile rows, 8 (one per thread: small grids, more blocks) or 32 (four per thread)
+template <int R, int EQ, int TY = kT2TY>
 __device__ __forceinline__ void tile2d_update(const float *__restrict__ u, float *un,
                                               const float *__restrict__ A,
                                               const float *__restrict__ C, const Geom &g,
                                               const Coef &c, int x0, int y0, float *sm) {
-  constexpr int SW = 32 + 2 * R, SH = kT2TY + 2 * R;
+  constexpr int SW = 32 + 2 * R, SH = TY + 2 * R;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   // stage rows y0-R .. y0+kT2TY+R-1 (those past the field's halo are not read),
   // columns x0-R .. x0+32+R-1
@@ -91,7 +92,7 @@ __device__ __forceinline__ void tile2d_update(const float *__restrict__ u, float
   const int x = x0 + tx;
   if (x >= g.n2) return;
 #pragma unroll
-  for (int j = 0; j < kT2TY / 8; ++j) {
+  for (int j = 0; j < TY / 8; ++j) {
     const int yl = ty + 8 * j, y = y0 + yl;
     if (y >= g.n1) break;
     const float *s = sm + (yl + R) * SW + tx + R;
@@ -108,12 +109,12 @@ __device__ __forceinline__ void tile2d_update(const float *__restrict__ u, float
   }
 }
 
-template <int R, int EQ>
+template <int R, int EQ, int TY>
 __global__ void __launch_bounds__(256)
 k_stencil2d_tile(const float *__restrict__ u, float *un, const float *__restrict__ A,
                  const float *__restrict__ C, Geom g, Coef c) {
-  __shared__ float sm[(32 + 2 * R) * (kT2TY + 2 * R)];
-  tile2d_update<R, EQ>(u, un, A, C, g, c, blockIdx.x * 32, blockIdx.y * kT2TY, sm);
+  __shared__ float sm[(32 + 2 * R) * (TY + 2 * R)];
+  tile2d_update<R, EQ, TY>(u, un, A, C, g, c, blockIdx.x * 32, blockIdx.y * TY, sm);
 }
 
 template <int R, int EQ, bool THREE_D>

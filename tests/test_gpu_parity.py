@@ -348,9 +348,10 @@ def test_errors_are_reported():
 
 
 @pytest.mark.parametrize("so", (2, 8, 16))
-@pytest.mark.parametrize("shape", [(61, 53), (17, 130), (100, 37)])
+@pytest.mark.parametrize("shape", [(61, 53), (17, 130), (100, 37), (530, 601)])
 def test_2d_staged_tiles_are_bitwise_the_plain_kernel(so, shape):
-    """2-D grids run the shared-memory-staged tile kernel (32 × 32 tiles, ragged edges);
+    """2-D grids run the shared-memory-staged tile kernel (32 × 8 tiles on small grids,
+    32 × 32 once there are two tiles per SM: the last shape; ragged edges);
     its per-point arithmetic is the plain kernel's, so both give the same bits, with
     sources and receivers (acoustic) and with the held boundary (diffusion)."""
     from paper_1906_10811_b300 import Solver
