@@ -68,9 +68,11 @@ typedef enum {
 typedef enum { FD_DIFFUSION = 0, FD_ACOUSTIC = 1 } fd_equation;
 
 typedef enum {
-  FD_KERNEL_AUTO = 0,  /* pipelined kernel where available, else plain */
+  FD_KERNEL_AUTO = 0,  /* 3-D: the pipelined kernel where it applies, else plain;
+                          2-D: plain (measured fastest on these L2-resident grids) */
   FD_KERNEL_PLAIN = 1, /* one thread per point, neighbours through L1/L2 */
-  FD_KERNEL_TMA = 2    /* 3-D: TMA-fed shared-memory plane ring, z streamed in registers */
+  FD_KERNEL_TMA = 2    /* 3-D: TMA-fed shared-memory plane ring, z streamed in registers;
+                          2-D: tiles staged in shared memory (bitwise the plain kernel) */
 } fd_kernel;
 
 /*

@@ -406,41 +406,16 @@ fd_status launch_stencil(fd_ctx *c, const float *ucur, float *unext, int j) {
   return FD_OK;
 }
 
-fd_status launch_sparse(fd_ctx *c, float *unext, int j) {
-  if (c->eq != FD_ACOUSTIC || (c->nsrc == 0 && c->nrec == 0) || c->fused) return FD_OK;
-  const bool small = c->nsrc * c->nc <= 2048 && c->nrec * c->nc <= 2048;
-  if (small) {
-    if (c->nc == 8)
-      k_sparse_fused<8><<<1, 512, 0, c->stream>>>(unext, c->d_step, j, c->nsrc, c->src_off,
-                                                   c->src_scale, c->wav, c->nrec, c->rec_off,
-                                                   c->rec_w, c->rec);
-    else
-      k_sparse_fused<4><<<1, 512, 0, c->stream>>>(unext, c->d_step, j, c->nsrc, c->src_off,
-                                                   c->src_scale, c->wav, c->nrec, c->rec_off,
-                                                   c->rec_w, c->rec);
-    CHECK_LAUNCH();
-    return FD_OK;
-  }
-  if (c->nsrc) {
-    const int n = c->nsrc * c->nc;
-    if (c->nc == 8)
-      k_inject<8><<<(n + 255) / 256, 256, 0, c->stream>>>(unext, c->d_step, j, c->nsrc,
-                                                           c->src_off, c->src_scale, c->wav);
-    else
-      k_inject<4><<<(n + 255) / 256, 256, 0, c->stream>>>(unext, c->d_step, j, c->nsrc,
-                                                           c->src_off, c->src_scale, c->wav);
-    CHECK_LAUNCH();
-  }
-  if (c->nrec) {
-    const int n = c->nrec * c->nc;
-    if (c->nc == 8)
-      k_interp<8><<<(n + 255) / 256, 256, 0, c->stream>>>(unext, c->d_step, j, c->nrec,
-                                                           c->rec_off, c->rec_w, c->rec);
-    else
-      k_interp<4><<<(n + 255) / 256, 256, 0, c->stream>>>(unext, c->d_step, j, c->nrec,
-                                                           c->rec_off, c->rec_w, c->rec);
-    CHECK_LAUNCH();
-  }
+// Source injection of step j into unext (kernels without the fused epilogue).
+fd_status launch_inject(fd_ctx *c, float *unext, int j) {
+  const int n = c->nsrc * c->nc;
+  if (c->nc == 8)
+    k_inject<8><<<(n + 255) / 256, 256, 0, c->stream>>>(unext, c->d_step, j, c->nsrc, c->src_off,
+                                                         c->src_scale, c->wav);
+  else
+    k_inject<4><<<(n + 255) / 256, 256, 0, c->stream>>>(unext, c->d_step, j, c->nsrc, c->src_off,
+                                                         c->src_scale, c->wav);
+  CHECK_LAUNCH();
   return FD_OK;
 }
 
@@ -515,7 +490,9 @@ fd_status enqueue_chunk(fd_ctx *c, int parity, int len, bool timed) {
     if (st) return st;
     st = timed ? profile_mark(c, true, 1) : FD_OK;
     if (st) return st;
-    st = overlap ? launch_receivers_side(c, unext, j) : launch_sparse(c, unext, j);
+    if (c->fused && !c->use_tma && c->nsrc)
+      st = launch_inject(c, unext, j);  // the stencil has no injection epilogue here
+    if (!st && overlap) st = launch_receivers_side(c, unext, j);
     if (st) return st;
   }
   if (overlap) {  // join the side stream before the step counter moves
@@ -596,9 +573,11 @@ fd_status prepare_sources(fd_ctx *c) {
 
 // Pipelined path: the source corners as entries keyed by (tile, plane) of the
 // pipelined kernel; receivers need only the side stream and its events.
+// Other kernels (2-D, plain): receivers on the side stream as well, sources by
+// k_inject after the stencil (no entry table).
 fd_status prepare_fused(fd_ctx *c) {
   c->fused = false;
-  if (!c->use_tma || c->eq != FD_ACOUSTIC || (c->nsrc == 0 && c->nrec == 0)) return FD_OK;
+  if (c->eq != FD_ACOUSTIC || (c->nsrc == 0 && c->nrec == 0)) return FD_OK;
   if (!c->side) {
     CU(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
     for (int i = 0; i < 2; ++i) {
@@ -606,7 +585,7 @@ fd_status prepare_fused(fd_ctx *c) {
       CU(cudaEventCreateWithFlags(&c->ev_rec[i], cudaEventDisableTiming));
     }
   }
-  if (c->sp_dirty) {
+  if (c->sp_dirty && c->use_tma) {
     const int ty = tma_ty(c->tma.ny), tiles_x = c->tma.args.tiles_x;
     struct E { int64_t key; int idx, x, y, z; };
     std::vector<E> es;
@@ -693,7 +672,7 @@ void select_kernel(fd_ctx *c) {
 #undef PICK
   c->kernel_name = three ? "stencil3d_plain" : "stencil2d_plain";
   c->tile2d_fn = nullptr;
-  if (!three && c->opt.kernel != FD_KERNEL_PLAIN) {
+  if (!three && c->opt.kernel == FD_KERNEL_TMA) {
     // 32-row tiles (four rows a thread) once they give two blocks per SM, else 8-row
     // tiles: a small grid needs the blocks more than the halo savings
     const int64_t tiles32 = (int64_t)((c->g.n2 + 31) / 32) * ((c->g.n1 + 31) / 32);
@@ -999,9 +978,6 @@ fd_status fd_create(fd_ctx **out, int ndim, const int64_t *shape, const double *
         return bail(FD_EUNSUPPORTED);
       }
     }
-  } else if (o.kernel == FD_KERNEL_TMA) {
-    fail(c, FD_EUNSUPPORTED, "the TMA kernel is 3-D only");
-    return bail(FD_EUNSUPPORTED);
   }
   *out = c;
   return FD_OK;
@@ -2125,7 +2101,7 @@ fd_status fd_batch_run(fd_batch *b, int nticks) {
     d.blk0 = blk;  // non-decreasing over members; 3-D members own no 2-D blocks
     if (c->ndim == 2) {
       d.blocks_x = (c->g.n2 + 31) / 32;
-      blk += (int64_t)d.blocks_x * ((c->g.n1 + kT2TY - 1) / kT2TY);
+      blk += (int64_t)d.blocks_x * ((c->g.n1 + 7) / 8);
       for (int k = 0; k < c->nsrc * c->nc; ++k) b->h_src.push_back(make_int2((int)i, k));
     }
     for (int k = 0; k < c->nrec; ++k) b->h_rec.push_back(make_int2((int)i, k));

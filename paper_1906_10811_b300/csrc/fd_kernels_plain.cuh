@@ -59,7 +59,10 @@ __device__ __forceinline__ void plain_point(const float *__restrict__ u, float *
 }
 
 // ---------------------------------------------------------------------------
-// 2-D step staged through shared memory.  A block of 32 × 8 threads updates a
+// 2-D step staged through shared memory (FD_KERNEL_TMA on a 2-D grid; the plain
+// kernel is the default there: measured on the B300, L1 serves the neighbour
+// re-reads of these L2-resident grids faster than a staged tile behind a barrier,
+// e.g. 8.5 vs 9.9 µs a step at 1000², so 8).  A block of 32 × 8 threads updates a
 // tile of 32 × TY points: the tile's u^n with its R-wide halo, (32 + 2R) ×
 // (TY + 2R) floats, is loaded once with coalesced rows (the padded layout
 // holds the zero halo, so every staged row lies in the field) and every
@@ -69,7 +72,7 @@ __device__ __forceinline__ void plain_point(const float *__restrict__ u, float *
 // kernel's.  2-D fields of the serving sizes (≤ 1000², 4 MB a level) live in
 // L2, so the bound here is L2 bandwidth and launch latency, not HBM.
 // ---------------------------------------------------------------------------
-constexpr int kT2TY = 32;  // tile rows of the batched kernel (4 per thread)
+constexpr int kT2TY = 32;  // default tile rows (4 per thread)
 
 // TY: tile rows, 8 (one per thread: small grids, more blocks) or 32 (four per thread)
 template <int R, int EQ, int TY = kT2TY>
@@ -228,23 +231,6 @@ __device__ __forceinline__ void interp_group_store(const float *un, const int64_
   if (c == 0 && k < nrec) rec[row * nrec + k] = v;
 }
 
-// Single block: injection, block barrier, interpolation (small source/receiver sets).
-template <int NC>
-__global__ void __launch_bounds__(512)
-k_sparse_fused(float *un, const int64_t *__restrict__ step, int j, int nsrc,
-               const int64_t *__restrict__ soff, const float *__restrict__ sscale,
-               const float *__restrict__ wav, int nrec, const int64_t *__restrict__ roff,
-               const float *__restrict__ rw, float *rec) {
-  const int64_t n = *step + j;
-  for (int i = threadIdx.x; i < nsrc * NC; i += blockDim.x)
-    atomicAdd(un + soff[i], sscale[i] * wav[n * nsrc + i / NC]);
-  __syncthreads();
-  const int groups = blockDim.x / NC;
-  for (int base = 0; base < nrec; base += groups)
-    interp_group_store<NC>(un, roff, rw, rec, n + 1, nrec, base + threadIdx.x / NC,
-                           threadIdx.x % NC);
-}
-
 template <int NC>
 __global__ void k_inject(float *un, const int64_t *__restrict__ step, int j, int nsrc,
                          const int64_t *__restrict__ soff, const float *__restrict__ sscale,
@@ -337,24 +323,26 @@ struct MemberDesc {
   int nrec;
 };
 
-// One step of every 2-D member: blocks of 32 × 8 threads, block -> member by
-// binary search over blk0; a block is one staged 32 × kT2TY tile of a member (the
-// 2-D kernel above).  The batch kernels run tick *tick + j (j: the tick's
+// One step of every 2-D member: blocks of 32 × 8 points, block -> member by
+// binary search over blk0 (the plain per-point update: on these L2-resident grids
+// it is faster than the staged tile kernel).  The batch kernels run tick *tick + j
+// (j: the tick's
 // place in a captured chunk).
 template <int R>
 __global__ void __launch_bounds__(256)
 k_stencil2d_batch(const MemberDesc *__restrict__ d, int n, const int64_t *tick, int j) {
-  __shared__ float sm[(32 + 2 * R) * (kT2TY + 2 * R)];
   int lo = 0, hi = n - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) / 2;
     if (d[mid].blk0 <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
   }
   const MemberDesc &m = d[lo];
-  const int64_t b = blockIdx.x - m.blk0;  // the member's tile (32 × kT2TY points)
+  const int64_t b = blockIdx.x - m.blk0;
+  const int x = (int)(b % m.blocks_x) * 32 + threadIdx.x;
+  const int y = (int)(b / m.blocks_x) * 8 + threadIdx.y;
+  if (x >= m.g.n2 || y >= m.g.n1) return;
   const int par = m.cur0 ^ (int)((*tick + j) & 1);
-  tile2d_update<R, kAcoustic>(m.level[par], m.level[par ^ 1], m.A, m.C, m.g, m.c,
-                              (int)(b % m.blocks_x) * 32, (int)(b / m.blocks_x) * kT2TY, sm);
+  plain_point<R, kAcoustic, false>(m.level[par], m.level[par ^ 1], m.A, m.C, m.g, m.c, 0, y, x);
 }
 
 // Source corners of the 2-D members: entry = (member, corner).

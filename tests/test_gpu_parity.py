@@ -350,21 +350,22 @@ def test_errors_are_reported():
 @pytest.mark.parametrize("so", (2, 8, 16))
 @pytest.mark.parametrize("shape", [(61, 53), (17, 130), (100, 37), (530, 601)])
 def test_2d_staged_tiles_are_bitwise_the_plain_kernel(so, shape):
-    """2-D grids run the shared-memory-staged tile kernel (32 × 8 tiles on small grids,
-    32 × 32 once there are two tiles per SM: the last shape; ragged edges);
-    its per-point arithmetic is the plain kernel's, so both give the same bits, with
-    sources and receivers (acoustic) and with the held boundary (diffusion)."""
+    """FD_KERNEL_TMA on 2-D grids runs the shared-memory-staged tile kernel (32 × 8 tiles
+    on small grids, 32 × 32 once there are two tiles per SM: the last shape; ragged
+    edges); its per-point arithmetic is the plain kernel's (the 2-D default), so both
+    give the same bits, with sources and receivers (acoustic) and with the held
+    boundary (diffusion)."""
     from paper_1906_10811_b300 import Solver
     p = small_problem(shape, so, nt=90)
-    staged = gpu_acoustic(p, 90)
-    plain = gpu_acoustic(p, 90, kernel="plain")
+    staged = gpu_acoustic(p, 90, kernel="tma")
+    plain = gpu_acoustic(p, 90)
     assert staged["kernel"] == "stencil2d_tile" and plain["kernel"] == "stencil2d_plain"
     assert np.array_equal(staged["u"], plain["u"]) and np.array_equal(staged["rec"], plain["rec"])
     rng = np.random.default_rng(so)
     u0 = rng.standard_normal(shape).astype(np.float32)
     h = (1.0 / 40, 1.0 / 30)
     outs = []
-    for kernel in ("auto", "plain"):
+    for kernel in ("tma", "auto"):
         with Solver(shape, h, so, 0.05 * min(h) ** 2, "diffusion", kernel=kernel) as s:
             s.set_field(u0)
             s.run(40)
@@ -374,7 +375,7 @@ def test_2d_staged_tiles_are_bitwise_the_plain_kernel(so, shape):
 
 
 @pytest.mark.parametrize("kernel,shape,tile", [
-    ("plain", (41, 37), None), ("auto", (41, 37), None), ("plain", (23, 29, 70), None),
+    ("plain", (41, 37), None), ("tma", (41, 37), None), ("plain", (23, 29, 70), None),
     ("tma", (23, 29, 70), None), ("tma", (23, 29, 131), dict(tile_x=64, tile_y=16)),
     ("tma", (23, 29, 70), dict(tile_y=16, aligned=1, zblock=7))])
 @pytest.mark.parametrize("so", (2, 8, 16))
