@@ -94,6 +94,8 @@ def parse():
                          "65 M (about four 256^3 shots) keeps the GPU saturated while a "
                          "long shot is not stretched by everything admitted beside it")
     ap.add_argument("--so", type=int, default=None)
+    ap.add_argument("--n", type=int, default=None,
+                    help="acoustic workloads: grid points per axis instead of the workload's")
     ap.add_argument("--nt", type=int, default=None)
     ap.add_argument("--kernel", default="auto", choices=["auto", "plain", "tma"])
     ap.add_argument("--tile", default="auto",
@@ -115,6 +117,9 @@ def problem(args):
     w = dict(WORKLOADS[args.workload])
     if args.so:
         w["so"] = args.so
+    if args.n:
+        w["n"] = args.n
+        w["nbl"] = min(w["nbl"], max(4, args.n // 8))
     if args.nt:
         w["nt"] = args.nt
     p = fdsynth.acoustic_problem(n=w["n"], ndim=w.get("ndim", 3), so=w["so"], nbl=w["nbl"],

@@ -1890,6 +1890,10 @@ struct fd_batch {
   std::vector<int2> h_src, h_rec;
   std::vector<int4> h_items;
   cudaEvent_t ev = nullptr;
+  // receivers of tick j on a side stream, overlapping tick j+1; tick j+2 (which
+  // overwrites the level they read) waits for them
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_step[2] = {nullptr, nullptr}, ev_rec[2] = {nullptr, nullptr};
   // captured chunks of ticks, valid while the launch parameters are unchanged
   struct Graph {
     int len;
@@ -2236,9 +2240,19 @@ fd_status fd_batch_run(fd_batch *b, int nticks) {
   bargs.err = err3;
   if (n3) std::memcpy(bargs.wp, m3[0]->coef.wp, sizeof bargs.wp);
   // the kernels of `len` ticks (tick *d_tick + j, j < len), then the counter moves
+  if (nrec_e && !b->side) {
+    BCU(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+      BCU(cudaEventCreateWithFlags(&b->ev_step[i], cudaEventDisableTiming));
+      BCU(cudaEventCreateWithFlags(&b->ev_rec[i], cudaEventDisableTiming));
+    }
+  }
   auto enqueue = [&](int len, int64_t *kernels) -> cudaError_t {
     int64_t k = 0;
-    for (int j = 0; j < len; ++j) {
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < len && e == cudaSuccess; ++j) {
+      // tick j overwrites the level tick j-2's receivers read
+      if (nrec_e && j >= 2) e = cudaStreamWaitEvent(b->stream, b->ev_rec[j & 1], 0);
       if (n3) {
         BatchArgs ba = bargs;
         ba.j = j;
@@ -2256,12 +2270,20 @@ fd_status fd_batch_run(fd_batch *b, int nticks) {
                                                                     b->d_tick, j);
         ++k;
       }
-      if (nrec_e) {
-        k_interp_batch<<<(nrec_e * 8 + 255) / 256, 256, 0, b->stream>>>(b->d_rec, nrec_e,
-                                                                        b->d_mem, b->d_tick, j);
+      if (nrec_e) {  // on the side stream, after this tick's stencils and injection
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev_step[j & 1], b->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->ev_step[j & 1], 0);
+        k_interp_batch<<<(nrec_e * 8 + 255) / 256, 256, 0, b->side>>>(b->d_rec, nrec_e,
+                                                                      b->d_mem, b->d_tick, j);
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev_rec[j & 1], b->side);
         ++k;
       }
     }
+    if (nrec_e && e == cudaSuccess) {  // join the side stream before the tick counter moves
+      e = cudaStreamWaitEvent(b->stream, b->ev_rec[(len - 1) & 1], 0);
+      if (e == cudaSuccess && len >= 2) e = cudaStreamWaitEvent(b->stream, b->ev_rec[len & 1], 0);
+    }
+    if (e != cudaSuccess) return e;
     k_advance_step<<<1, 1, 0, b->stream>>>(b->d_tick, len);
     *kernels = k + 1;
     return cudaGetLastError();
@@ -2342,6 +2364,14 @@ void fd_batch_destroy(fd_batch *b) {
   if (b->d_tick) cudaFree(b->d_tick);
   for (auto &gph : b->graphs) cudaGraphExecDestroy(gph.exec);
   if (b->ev) cudaEventDestroy(b->ev);
+  for (int i = 0; i < 2; ++i) {
+    if (b->ev_step[i]) cudaEventDestroy(b->ev_step[i]);
+    if (b->ev_rec[i]) cudaEventDestroy(b->ev_rec[i]);
+  }
+  if (b->side) {
+    cudaStreamSynchronize(b->side);
+    cudaStreamDestroy(b->side);
+  }
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
