@@ -81,7 +81,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="acoustic256",
-                    choices=sorted(WORKLOADS) + ["serving", "fwi320", "diffusion512"])
+                    choices=sorted(WORKLOADS) + ["serving", "fwi320", "diffusion512",
+                                                 "diffusion2d"])
     ap.add_argument("--boundary", default="zero", choices=["zero", "odd"],
                     help="diffusion512: values outside the grid (zero halo or odd reflection)")
     ap.add_argument("--fwi-k", type=int, default=0,
@@ -291,7 +292,7 @@ def run_reference(args):
         return 0
     if args.workload == "fwi320":
         return run_reference_fwi(args)
-    if args.workload in ("serving", "diffusion512"):
+    if args.workload in ("serving", "diffusion512", "diffusion2d"):
         args.workload = "acoustic256"     # the oracle's timed sample: the acoustic shot
     w, p = problem(args)
     per_step = oracle_steps_for(p, 6.0)
@@ -495,7 +496,10 @@ def run_fwi(args):
 
 
 def run_diffusion(args):
-    """3-D diffusion sweep at 512³ (sine-mode data, ν dt/h² = 0.05, interior update)."""
+    """Diffusion sweep: 3-D at 512³ (sine-mode data, ν dt/h² = 0.05, interior update), or
+    with --workload diffusion2d the paper's benchmark problem (§5.1.2): 2-D sine-mode
+    data with ν = 0.5 on n² nodes (default 10000², a size the paper measured), ν dt/h² =
+    0.1 (stable up to so 16), interior update."""
     import torch
     world, rank, local = dist_setup(args)
     torch.cuda.set_device(local)
@@ -504,9 +508,11 @@ def run_diffusion(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1906_10811_b300 import Solver, build
     build.build()
-    n, so, nt = 512, args.so or 8, args.nt or 200
-    q = fdsynth.diffusion_problem(n, ndim=3, courant=0.05)
-    npts = n ** 3
+    two = args.workload == "diffusion2d"
+    nd = 2 if two else 3
+    n, so, nt = (args.n or (10000 if two else 512)), args.so or 8, args.nt or 200
+    q = fdsynth.diffusion_problem(n, ndim=nd, courant=0.1 if two else 0.05)
+    npts = n ** nd
     u0_d = torch.from_numpy(q["u0"]).cuda()
 
     def barrier():
@@ -518,10 +524,10 @@ def run_diffusion(args):
     bench_stream = torch.cuda.Stream()
     bench_stream.wait_stream(torch.cuda.current_stream())
     torch.cuda.set_stream(bench_stream)
-    s = Solver((n,) * 3, q["spacing"], so, q["dt"], "diffusion", nu=q["nu"], device=True,
+    s = Solver((n,) * nd, q["spacing"], so, q["dt"], "diffusion", nu=q["nu"], device=True,
                profile=True, kernel=args.kernel, boundary=args.boundary)
     tile, tune_tried = None, None
-    if s.kernel_name.startswith("stencil3d_tma"):
+    if s.kernel_name.startswith(("stencil3d_tma", "stencil3d_xp")):
         s.set_field(u0_d)
         if args.tile == "auto":
             tune_tried = len(s.autotune(reps=5)[1])
@@ -569,8 +575,8 @@ def run_diffusion(args):
     e2e = None
     if not args.no_e2e:
         u0_h = torch.from_numpy(q["u0"]).pin_memory().numpy()
-        out_h = torch.empty((n,) * 3, dtype=torch.float32).pin_memory().numpy()
-        se = Solver((n,) * 3, q["spacing"], so, q["dt"], "diffusion", nu=q["nu"],
+        out_h = torch.empty((n,) * nd, dtype=torch.float32).pin_memory().numpy()
+        se = Solver((n,) * nd, q["spacing"], so, q["dt"], "diffusion", nu=q["nu"],
                     kernel=args.kernel, boundary=args.boundary)
         if tile is not None:
             se.set_tile_config(tile_y=tile["tile_y"], zblock=tile["zblock"],
@@ -613,13 +619,13 @@ def run_diffusion(args):
                 "unit": "GPts/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": f"diffusion3d_{n}^3_so{so}_nt{nt}", "grid": [n] * 3,
+                "config": {"workload": f"diffusion{nd}d_{n}^{nd}_so{so}_nt{nt}", "grid": [n] * nd,
                            "space_order": so, "nt": nt, "nu": q["nu"],
-                           "nu_dt_over_h2": 0.05, "boundary": args.boundary,
-                           "initial_data": "sin(pi x) sin(pi y) sin(pi z), boundary nodes 0",
+                           "nu_dt_over_h2": 0.1 if two else 0.05, "boundary": args.boundary,
+                           "initial_data": "product of sin(pi x_d), boundary nodes 0",
                            "step": "one sweep: field reset + nt time steps",
                            "l2": "inputs larger than L2 (u^n, u^{n+1} = 2 x %.0f MB)" %
-                                 ((n + so) ** 2 * (n + 64) * 4 / 1e6),
+                                 ((n + so) ** (nd - 1) * (n + 64) * 4 / 1e6),
                            "kernel": kernel_name, "tile": tile,
                            "tile_choice": ("autotuned over %d configurations" % tune_tried
                                            if tune_tried else args.tile)},
@@ -1043,7 +1049,7 @@ def main():
         return run_serving(args)
     if args.workload == "fwi320":
         return run_fwi(args)
-    if args.workload == "diffusion512":
+    if args.workload in ("diffusion512", "diffusion2d"):
         return run_diffusion(args)
     return run_ours(args)
 

@@ -31,6 +31,8 @@ using namespace fdk;
 namespace {
 
 constexpr int kGraphChunk = 64;  // steps per captured graph
+// 2-D grids of at least this many points run the streaming kernel by default
+constexpr int64_t kStream2dPoints = int64_t(1) << 62;
 constexpr int kGraphCacheMax = 12;
 thread_local std::string g_create_error;  // fd_last_error(NULL)
 
@@ -91,7 +93,8 @@ struct GraphEntry {
 };
 
 using StencilFn = void (*)(const float *, float *, const float *, const float *, Geom, Coef);
-using StencilFnTile = void (*)(const float *, float *, const float *, const float *, Geom, Coef);
+using StencilFnStream = void (*)(const float *, float *, const float *, const float *, Geom, Coef,
+                                 int, int);
 using StencilFn2D = void (*)(const MemberDesc *, int, const int64_t *, int);
 
 }  // namespace
@@ -120,8 +123,8 @@ struct fd_ctx {
   int *d_err = nullptr;
   // kernel selection
   StencilFn plain_fn = nullptr;
-  StencilFnTile tile2d_fn = nullptr;  // 2-D grids: the shared-memory-staged kernel
-  int tile2d_ty = 0;                  // its tile height (rows)
+  StencilFnStream stream2d_fn = nullptr;  // 2-D grids: rows staged and streamed along y
+  int s2_nseg = 0, s2_seglen = 0;         // its row segments per strip and their length
   TmaPlan tma{};
   bool use_tma = false;
   bool iso = false;          // equal spacing on all axes (pipelined kernel variant)
@@ -394,9 +397,11 @@ fd_status launch_stencil(fd_ctx *c, const float *ucur, float *unext, int j) {
     return FD_OK;
   }
   dim3 block(32, 8);
-  if (c->tile2d_fn) {
-    dim3 tiles((c->g.n2 + 31) / 32, (c->g.n1 + c->tile2d_ty - 1) / c->tile2d_ty);
-    c->tile2d_fn<<<tiles, block, 0, c->stream>>>(ucur, unext, c->A, c->C, c->g, c->coef);
+  if (c->stream2d_fn) {
+    const int64_t items = (int64_t)((c->g.n2 + kS2W - 1) / kS2W) * c->s2_nseg;
+    c->stream2d_fn<<<(unsigned)((items + kS2Warps - 1) / kS2Warps), kS2Warps * 32, 0,
+                     c->stream>>>(ucur, unext, c->A, c->C, c->g, c->coef, c->s2_nseg,
+                                  c->s2_seglen);
     CHECK_LAUNCH();
     return FD_OK;
   }
@@ -671,31 +676,39 @@ void select_kernel(fd_ctx *c) {
   }
 #undef PICK
   c->kernel_name = three ? "stencil3d_plain" : "stencil2d_plain";
-  c->tile2d_fn = nullptr;
-  if (!three && c->opt.kernel == FD_KERNEL_TMA) {
-    // 32-row tiles (four rows a thread) once they give two blocks per SM, else 8-row
-    // tiles: a small grid needs the blocks more than the halo savings
-    const int64_t tiles32 = (int64_t)((c->g.n2 + 31) / 32) * ((c->g.n1 + 31) / 32);
+  c->stream2d_fn = nullptr;
+  if (!three) {
+    // rows staged and streamed along y: on request (FD_KERNEL_TMA), and by default
+    // on grids too large for L2 to hold the shot's fields, where one thread per point
+    // keeps too few bytes in flight to fill HBM
     int dev = 0, sms = 148;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
       cudaGetLastError();
       sms = 148;
     }
-    c->tile2d_ty = tiles32 >= 2 * sms ? 32 : 8;
-    const bool t32 = c->tile2d_ty == 32;
+    const int64_t pts = (int64_t)c->g.n1 * c->g.n2;
+    const bool want = c->opt.kernel == FD_KERNEL_TMA ||
+                      (c->opt.kernel == FD_KERNEL_AUTO && pts >= kStream2dPoints);
+    if (want) {
+      // segments of at least max(32, 4R) rows; about four blocks of kS2Warps warp
+      // streams per SM in all
+      const int strips = (c->g.n2 + kS2W - 1) / kS2W;
+      const int target = 4 * sms * kS2Warps;
+      const int most = std::max(1, c->g.n1 / std::max(32, 4 * R));
+      int nseg = std::max(1, std::min((target + strips - 1) / strips, most));
+      c->s2_seglen = (c->g.n1 + nseg - 1) / nseg;
+      c->s2_nseg = (c->g.n1 + c->s2_seglen - 1) / c->s2_seglen;
 #define PICK2(RR)                                                                      \
   case RR:                                                                             \
-    c->tile2d_fn = ac ? (t32 ? k_stencil2d_tile<RR, kAcoustic, 32>                     \
-                             : k_stencil2d_tile<RR, kAcoustic, 8>)                     \
-                      : (t32 ? k_stencil2d_tile<RR, kDiffusion, 32>                    \
-                             : k_stencil2d_tile<RR, kDiffusion, 8>);                   \
+    c->stream2d_fn = ac ? k_stencil2d_stream<RR, kAcoustic> : k_stencil2d_stream<RR, kDiffusion>; \
     break;
-    switch (R) {
-      PICK2(1) PICK2(2) PICK2(3) PICK2(4) PICK2(5) PICK2(6) PICK2(7) PICK2(8)
-    }
+      switch (R) {
+        PICK2(1) PICK2(2) PICK2(3) PICK2(4) PICK2(5) PICK2(6) PICK2(7) PICK2(8)
+      }
 #undef PICK2
-    c->kernel_name = "stencil2d_tile";
+      c->kernel_name = "stencil2d_stream";
+    }
   }
 }
 

@@ -20,16 +20,20 @@ namespace fdk {
 // L u at one point from its centre value and neighbour reads nb(axis, ±k): the
 // operation sequence every plain-order kernel shares (so they agree bitwise).
 // Difference form: the weights of every pair sum to zero exactly, so the FP32
-// operator annihilates constants (no drift from rounded weights).
+// operator annihilates constants (no drift from rounded weights).  One FMA chain
+// runs over the x offsets, then continues over y (then z): a kernel that streams
+// rows can form the x part when a row arrives and finish it rows later.
 template <int R, bool THREE_D, typename NB>
 __device__ __forceinline__ float plain_lap(float uc, const Coef &c, NB nb) {
   const float uc2 = uc + uc;
   float lap = 0.f;
 #pragma unroll
-  for (int k = 1; k <= R; ++k) {
-    lap = fmaf(c.w[2][k], (nb(2, k) + nb(2, -k)) - uc2, lap);
-    lap = fmaf(c.w[1][k], (nb(1, k) + nb(1, -k)) - uc2, lap);
-    if (THREE_D) lap = fmaf(c.w[0][k], (nb(0, k) + nb(0, -k)) - uc2, lap);
+  for (int k = 1; k <= R; ++k) lap = fmaf(c.w[2][k], (nb(2, k) + nb(2, -k)) - uc2, lap);
+#pragma unroll
+  for (int k = 1; k <= R; ++k) lap = fmaf(c.w[1][k], (nb(1, k) + nb(1, -k)) - uc2, lap);
+  if (THREE_D) {
+#pragma unroll
+    for (int k = 1; k <= R; ++k) lap = fmaf(c.w[0][k], (nb(0, k) + nb(0, -k)) - uc2, lap);
   }
   return lap;
 }
@@ -58,68 +62,6 @@ __device__ __forceinline__ void plain_point(const float *__restrict__ u, float *
   }
 }
 
-// ---------------------------------------------------------------------------
-// 2-D step staged through shared memory (FD_KERNEL_TMA on a 2-D grid; the plain
-// kernel is the default there: measured on the B300, L1 serves the neighbour
-// re-reads of these L2-resident grids faster than a staged tile behind a barrier,
-// e.g. 8.5 vs 9.9 µs a step at 1000², so 8).  A block of 32 × 8 threads updates a
-// tile of 32 × TY points: the tile's u^n with its R-wide halo, (32 + 2R) ×
-// (TY + 2R) floats, is loaded once with coalesced rows (the padded layout
-// holds the zero halo, so every staged row lies in the field) and every
-// neighbour read comes from shared memory.  A thread owns column x of rows
-// ty, ty + 8, ... (a warp reads one row: no bank conflicts).  The per-point
-// operation sequence is plain_point's, so the result is bitwise the plain
-// kernel's.  2-D fields of the serving sizes (≤ 1000², 4 MB a level) live in
-// L2, so the bound here is L2 bandwidth and launch latency, not HBM.
-// ---------------------------------------------------------------------------
-constexpr int kT2TY = 32;  // default tile rows (4 per thread)
-
-// TY: tile rows, 8 (one per thread: small grids, more blocks) or 32 (four per thread)
-template <int R, int EQ, int TY = kT2TY>
-__device__ __forceinline__ void tile2d_update(const float *__restrict__ u, float *un,
-                                              const float *__restrict__ A,
-                                              const float *__restrict__ C, const Geom &g,
-                                              const Coef &c, int x0, int y0, float *sm) {
-  constexpr int SW = 32 + 2 * R, SH = TY + 2 * R;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-  // stage rows y0-R .. y0+kT2TY+R-1 (those past the field's halo are not read),
-  // columns x0-R .. x0+32+R-1
-  const int ymax = g.n1 + R;  // padded rows run from -R to n1+R-1
-  for (int i = tid; i < SH * SW; i += 256) {
-    const int r = i / SW, q = i - r * SW;
-    const int y = y0 - R + r;
-    const int x = x0 - R + q;
-    sm[i] = (y < ymax && x < g.n2 + R) ? u[gidx(g, 0, y, x)] : 0.f;
-  }
-  __syncthreads();
-  const int x = x0 + tx;
-  if (x >= g.n2) return;
-#pragma unroll
-  for (int j = 0; j < TY / 8; ++j) {
-    const int yl = ty + 8 * j, y = y0 + yl;
-    if (y >= g.n1) break;
-    const float *s = sm + (yl + R) * SW + tx + R;
-    const float uc = *s;
-    const float lap = plain_lap<R, false>(uc, c, [&](int ax, int k) {
-      return s[ax == 2 ? k : k * SW];
-    });
-    const int64_t p = gidx(g, 0, y, x);
-    if (EQ == kAcoustic) {
-      un[p] = leapfrog(A[p], C[p], uc, un[p], lap);
-    } else {
-      if (!g.hold || (x > 0 && x < g.n2 - 1 && y > 0 && y < g.n1 - 1)) un[p] = uc + lap;
-    }
-  }
-}
-
-template <int R, int EQ, int TY>
-__global__ void __launch_bounds__(256)
-k_stencil2d_tile(const float *__restrict__ u, float *un, const float *__restrict__ A,
-                 const float *__restrict__ C, Geom g, Coef c) {
-  __shared__ float sm[(32 + 2 * R) * (TY + 2 * R)];
-  tile2d_update<R, EQ, TY>(u, un, A, C, g, c, blockIdx.x * 32, blockIdx.y * TY, sm);
-}
-
 template <int R, int EQ, bool THREE_D>
 __global__ void __launch_bounds__(256)
 k_stencil_plain(const float *__restrict__ u, float *un, const float *__restrict__ A,
@@ -129,6 +71,153 @@ k_stencil_plain(const float *__restrict__ u, float *un, const float *__restrict_
   const int z = blockIdx.z;
   if (x >= g.n2 || y >= g.n1) return;
   plain_point<R, EQ, THREE_D>(u, un, A, C, g, c, z, y, x);
+}
+
+// ---------------------------------------------------------------------------
+// 2-D step streamed along y.  A warp owns a strip of kS2W = 64 columns (a lane per
+// pair of adjacent x points) and a segment of rows [ya, yb).  Rows ya-R .. yb+R-1
+// of u^n (with the x halo) are copied into the warp's ring in shared memory with
+// cp.async, kS2D rows ahead of the row in use, so many bytes stay in flight (one
+// thread per point keeps too few to fill HBM on large grids).  When a row arrives
+// the warp pushes its values into a register queue of 2R+1 rows and forms the x
+// part of the Laplacian from the staged row; R rows later it finishes the y part
+// from the queue and stores the row.  The per-point operation sequence is
+// plain_lap's and plain_point's (packed FP32x2 over the pair: each lane the scalar
+// round-to-nearest operation), so results are bitwise the plain kernel's.
+// ---------------------------------------------------------------------------
+constexpr int kS2W = 64;  // strip width (columns)
+constexpr int kS2D = 6;   // rows copied ahead of the row in use
+__host__ __device__ constexpr int s2_hx(int R) { return (R + 3) / 4 * 4; }  // x halo, 16-B multiple
+__host__ __device__ constexpr int s2_rw(int R) { return kS2W + 2 * s2_hx(R); }  // staged row (floats)
+// ring rows per warp: a multiple of the queue length 2R+1 that holds kS2D + 2 rows,
+// so an unrolled group of that many rows addresses ring and queue slots statically
+__host__ __device__ constexpr int s2_nr(int R) {
+  return (2 * R + 1) * ((kS2D + 2 + 2 * R) / (2 * R + 1));
+}
+constexpr int kS2Warps = 8;  // warps per block (independent streams)
+
+__device__ __forceinline__ uint32_t s2_smem(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+// 16 bytes global -> shared, asynchronous; src_bytes = 0 fills zeros without reading
+__device__ __forceinline__ void s2_copy16(void *dst, const void *src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s2_smem(dst)), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void s2_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void s2_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(kS2D) : "memory");
+}
+
+template <int R, int EQ>
+__global__ void __launch_bounds__(kS2Warps * 32)
+k_stencil2d_stream(const float *__restrict__ u, float *un, const float *__restrict__ A,
+                   const float *__restrict__ C, Geom g, Coef c, int nseg, int seglen) {
+  constexpr int HX = s2_hx(R), RW = s2_rw(R), NR = s2_nr(R), Q = 2 * R + 1;
+  constexpr int PH = (R + 1) / 2;  // x pairs each side of the lane's own
+  constexpr bool AC = EQ == kAcoustic;
+  __shared__ __align__(16) float ring[kS2Warps][NR][RW];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int strips = (g.n2 + kS2W - 1) / kS2W;
+  const int item = blockIdx.x * kS2Warps + warp;
+  if (item >= strips * nseg) return;
+  const int strip = item % strips, seg = item / strips;  // neighbouring strips together
+  const int x0 = strip * kS2W;
+  const int ya = seg * seglen, yb = min(g.n1, ya + seglen);
+  if (ya >= yb) return;
+  float(*rg)[RW] = ring[warp];
+  const int T = (yb - ya) + 2 * R;  // rows streamed: ya-R .. yb+R-1
+  // padded offset of (row ya - R, column x0 - HX); rows -R .. n1+R-1 exist
+  const float *src0 = u + gidx(g, 0, ya - R, x0) - HX;
+  const int col0 = x0 + kHaloX - HX;  // padded column of the staged row's first float
+  auto issue = [&](int t) {           // row ya - R + t into ring slot t % NR
+    if (t < T) {
+      float *dst = rg[t % NR];
+      const float *src = src0 + (int64_t)t * g.px;
+#pragma unroll
+      for (int ch = lane; ch < RW / 4; ch += 32) {
+        const bool in = col0 + 4 * ch + 4 <= g.px;  // past the row pitch: zeros, not read
+        s2_copy16(dst + 4 * ch, in ? src + 4 * ch : src, in ? 16 : 0);
+      }
+    }
+    s2_commit();  // an empty group past the end keeps the wait count fixed
+  };
+  const int x = x0 + 2 * lane;
+  const bool hold = !AC && g.hold;
+  const bool xin0 = hold ? (x > 0 && x < g.n2 - 1) : x < g.n2;
+  const bool xin1 = hold ? (x + 1 > 0 && x + 1 < g.n2 - 1) : x + 1 < g.n2;
+  float2 q[Q];   // u^n at the pair, row t in slot t % Q
+  float2 xq[Q];  // x part of the Laplacian of row t, slot t % Q
+#pragma unroll
+  for (int t = 0; t < kS2D; ++t) issue(t);
+  for (int tb = 0; tb < T; tb += NR) {
+#pragma unroll
+    for (int ph = 0; ph < NR; ++ph) {
+      const int t = tb + ph;
+      if (t >= T) break;
+      issue(t + kS2D);
+      s2_wait();  // row t's copies (all but the newest kS2D groups) have landed
+      __syncwarp();
+      const float *rr = rg[ph] + HX + 2 * lane;
+      float2 xp[2 * PH + 1];  // the row's pairs around the lane's own
+#pragma unroll
+      for (int d = -PH; d <= PH; ++d) xp[d + PH] = *reinterpret_cast<const float2 *>(rr + 2 * d);
+      const float2 uc = xp[PH];
+      q[ph % Q] = uc;
+      const float2 nuc2 = make_float2(-(uc.x + uc.x), -(uc.y + uc.y));
+      float2 lx = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 1; k <= R; ++k) {
+        const float2 sx =
+            (k & 1) == 0
+                ? __fadd2_rn(xp[PH + k / 2], xp[PH - k / 2])
+                : make_float2(__fadd_rn(xp[PH + (k - 1) / 2].y, xp[PH - (k + 1) / 2].y),
+                              __fadd_rn(xp[PH + (k + 1) / 2].x, xp[PH - (k - 1) / 2].x));
+        lx = __ffma2_rn(c.wp[2][k], __fadd2_rn(sx, nuc2), lx);
+      }
+      xq[ph % Q] = lx;
+      if (t >= 2 * R) {  // row y = ya + t - 2R: its y neighbours are all in the queue
+        const int y = ya + t - 2 * R;
+        const float2 ucy = q[(ph + Q - R) % Q];
+        const float2 ncy2 = make_float2(-(ucy.x + ucy.x), -(ucy.y + ucy.y));
+        float2 lap = xq[(ph + Q - R) % Q];
+#pragma unroll
+        for (int k = 1; k <= R; ++k)
+          lap = __ffma2_rn(c.wp[1][k],
+                           __fadd2_rn(__fadd2_rn(q[(ph + Q - R + k) % Q], q[(ph + Q - R - k + Q) % Q]),
+                                      ncy2),
+                           lap);
+        const bool yin = hold ? (y > 0 && y < g.n1 - 1) : true;
+        const int64_t p = gidx(g, 0, y, x);
+        float2 val;
+        if (AC) {
+          float2 prev, a, cc;
+          if (xin0 && xin1) {
+            prev = *reinterpret_cast<const float2 *>(un + p);
+            a = *reinterpret_cast<const float2 *>(A + p);
+            cc = *reinterpret_cast<const float2 *>(C + p);
+          } else {
+            prev = make_float2(xin0 ? un[p] : 0.f, xin1 ? un[p + 1] : 0.f);
+            a = make_float2(xin0 ? A[p] : 0.f, xin1 ? A[p + 1] : 0.f);
+            cc = make_float2(xin0 ? C[p] : 0.f, xin1 ? C[p + 1] : 0.f);
+          }
+          val = make_float2(leapfrog(a.x, cc.x, ucy.x, prev.x, lap.x),
+                            leapfrog(a.y, cc.y, ucy.y, prev.y, lap.y));
+        } else {
+          val = make_float2(ucy.x + lap.x, ucy.y + lap.y);
+        }
+        if (yin) {
+          if (xin0 && xin1)
+            *reinterpret_cast<float2 *>(un + p) = val;
+          else {
+            if (xin0) un[p] = val.x;
+            if (xin1) un[p + 1] = val.y;
+          }
+        }
+      }
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------

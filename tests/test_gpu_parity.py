@@ -348,30 +348,35 @@ def test_errors_are_reported():
 
 
 @pytest.mark.parametrize("so", (2, 8, 16))
-@pytest.mark.parametrize("shape", [(61, 53), (17, 130), (100, 37), (530, 601)])
-def test_2d_staged_tiles_are_bitwise_the_plain_kernel(so, shape):
-    """FD_KERNEL_TMA on 2-D grids runs the shared-memory-staged tile kernel (32 × 8 tiles
-    on small grids, 32 × 32 once there are two tiles per SM: the last shape; ragged
-    edges); its per-point arithmetic is the plain kernel's (the 2-D default), so both
-    give the same bits, with sources and receivers (acoustic) and with the held
-    boundary (diffusion)."""
+@pytest.mark.parametrize("shape", [(61, 53), (17, 130), (100, 37), (530, 601), (1500, 90)])
+def test_2d_streamed_rows_are_bitwise_the_plain_kernel(so, shape):
+    """FD_KERNEL_TMA on 2-D grids runs the row-streaming kernel (warps over 64-column
+    strips and row segments, rows staged with cp.async, y neighbours from registers;
+    ragged strips, one or many segments); its per-point arithmetic is the plain
+    kernel's, so both give the same bits, with sources and receivers (acoustic), the
+    held boundary and the odd reflection (diffusion)."""
     from paper_1906_10811_b300 import Solver
     p = small_problem(shape, so, nt=90)
-    staged = gpu_acoustic(p, 90, kernel="tma")
-    plain = gpu_acoustic(p, 90)
-    assert staged["kernel"] == "stencil2d_tile" and plain["kernel"] == "stencil2d_plain"
-    assert np.array_equal(staged["u"], plain["u"]) and np.array_equal(staged["rec"], plain["rec"])
+    streamed = gpu_acoustic(p, 90, kernel="tma")
+    plain = gpu_acoustic(p, 90, kernel="plain")
+    assert streamed["kernel"] == "stencil2d_stream" and plain["kernel"] == "stencil2d_plain"
+    assert np.array_equal(streamed["u"], plain["u"])
+    assert np.array_equal(streamed["rec"], plain["rec"])
     rng = np.random.default_rng(so)
     u0 = rng.standard_normal(shape).astype(np.float32)
     h = (1.0 / 40, 1.0 / 30)
-    outs = []
-    for kernel in ("tma", "auto"):
-        with Solver(shape, h, so, 0.05 * min(h) ** 2, "diffusion", kernel=kernel) as s:
-            s.set_field(u0)
-            s.run(40)
-            outs.append(s.read()[0])
-    assert np.array_equal(outs[0], outs[1])
-    assert np.array_equal(outs[0][0], u0[0]) and np.array_equal(outs[0][:, -1], u0[:, -1])
+    for boundary in ("zero", "odd"):
+        if boundary == "odd" and min(shape) - 1 < so // 2:
+            continue
+        outs = []
+        for kernel in ("tma", "plain"):
+            with Solver(shape, h, so, 0.05 * min(h) ** 2, "diffusion", kernel=kernel,
+                        boundary=boundary) as s:
+                s.set_field(u0)
+                s.run(40)
+                outs.append(s.read()[0])
+        assert np.array_equal(outs[0], outs[1]), boundary
+        assert np.array_equal(outs[0][0], u0[0]) and np.array_equal(outs[0][:, -1], u0[:, -1])
 
 
 @pytest.mark.parametrize("kernel,shape,tile", [
