@@ -32,7 +32,7 @@ namespace {
 
 constexpr int kGraphChunk = 64;  // steps per captured graph
 // 2-D grids of at least this many points run the streaming kernel by default
-constexpr int64_t kStream2dPoints = int64_t(1) << 62;
+constexpr int64_t kStream2dPoints = 8 << 20;
 constexpr int kGraphCacheMax = 12;
 thread_local std::string g_create_error;  // fd_last_error(NULL)
 
@@ -399,9 +399,9 @@ fd_status launch_stencil(fd_ctx *c, const float *ucur, float *unext, int j) {
   dim3 block(32, 8);
   if (c->stream2d_fn) {
     const int64_t items = (int64_t)((c->g.n2 + kS2W - 1) / kS2W) * c->s2_nseg;
-    c->stream2d_fn<<<(unsigned)((items + kS2Warps - 1) / kS2Warps), kS2Warps * 32, 0,
-                     c->stream>>>(ucur, unext, c->A, c->C, c->g, c->coef, c->s2_nseg,
-                                  c->s2_seglen);
+    const int nw = s2_warps(c->g.R);
+    c->stream2d_fn<<<(unsigned)((items + nw - 1) / nw), nw * 32, s2_smem(c->g.R), c->stream>>>(
+        ucur, unext, c->A, c->C, c->g, c->coef, c->s2_nseg, c->s2_seglen);
     CHECK_LAUNCH();
     return FD_OK;
   }
@@ -691,10 +691,9 @@ void select_kernel(fd_ctx *c) {
     const bool want = c->opt.kernel == FD_KERNEL_TMA ||
                       (c->opt.kernel == FD_KERNEL_AUTO && pts >= kStream2dPoints);
     if (want) {
-      // segments of at least max(32, 4R) rows; about four blocks of kS2Warps warp
-      // streams per SM in all
+      // segments of at least max(32, 4R) rows; about 64 warp streams per SM in all
       const int strips = (c->g.n2 + kS2W - 1) / kS2W;
-      const int target = 4 * sms * kS2Warps;
+      const int target = 64 * sms;
       const int most = std::max(1, c->g.n1 / std::max(32, 4 * R));
       int nseg = std::max(1, std::min((target + strips - 1) / strips, most));
       c->s2_seglen = (c->g.n1 + nseg - 1) / nseg;
@@ -702,6 +701,10 @@ void select_kernel(fd_ctx *c) {
 #define PICK2(RR)                                                                      \
   case RR:                                                                             \
     c->stream2d_fn = ac ? k_stencil2d_stream<RR, kAcoustic> : k_stencil2d_stream<RR, kDiffusion>; \
+    cudaFuncSetAttribute(k_stencil2d_stream<RR, kAcoustic>,                            \
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, s2_smem(RR));    \
+    cudaFuncSetAttribute(k_stencil2d_stream<RR, kDiffusion>,                           \
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, s2_smem(RR));    \
     break;
       switch (R) {
         PICK2(1) PICK2(2) PICK2(3) PICK2(4) PICK2(5) PICK2(6) PICK2(7) PICK2(8)

@@ -21,16 +21,16 @@ namespace fdk {
 // operation sequence every plain-order kernel shares (so they agree bitwise).
 // Difference form: the weights of every pair sum to zero exactly, so the FP32
 // operator annihilates constants (no drift from rounded weights).  One FMA chain
-// runs over the x offsets, then continues over y (then z): a kernel that streams
-// rows can form the x part when a row arrives and finish it rows later.
+// runs over the y offsets, then continues over x (then z): a kernel that streams
+// rows takes the y part from a register queue and the x part from the staged row.
 template <int R, bool THREE_D, typename NB>
 __device__ __forceinline__ float plain_lap(float uc, const Coef &c, NB nb) {
   const float uc2 = uc + uc;
   float lap = 0.f;
 #pragma unroll
-  for (int k = 1; k <= R; ++k) lap = fmaf(c.w[2][k], (nb(2, k) + nb(2, -k)) - uc2, lap);
-#pragma unroll
   for (int k = 1; k <= R; ++k) lap = fmaf(c.w[1][k], (nb(1, k) + nb(1, -k)) - uc2, lap);
+#pragma unroll
+  for (int k = 1; k <= R; ++k) lap = fmaf(c.w[2][k], (nb(2, k) + nb(2, -k)) - uc2, lap);
   if (THREE_D) {
 #pragma unroll
     for (int k = 1; k <= R; ++k) lap = fmaf(c.w[0][k], (nb(0, k) + nb(0, -k)) - uc2, lap);
@@ -77,67 +77,77 @@ k_stencil_plain(const float *__restrict__ u, float *un, const float *__restrict_
 // 2-D step streamed along y.  A warp owns a strip of kS2W = 64 columns (a lane per
 // pair of adjacent x points) and a segment of rows [ya, yb).  Rows ya-R .. yb+R-1
 // of u^n (with the x halo) are copied into the warp's ring in shared memory with
-// cp.async, kS2D rows ahead of the row in use, so many bytes stay in flight (one
-// thread per point keeps too few to fill HBM on large grids).  When a row arrives
-// the warp pushes its values into a register queue of 2R+1 rows and forms the x
-// part of the Laplacian from the staged row; R rows later it finishes the y part
-// from the queue and stores the row.  The per-point operation sequence is
-// plain_lap's and plain_point's (packed FP32x2 over the pair: each lane the scalar
-// round-to-nearest operation), so results are bitwise the plain kernel's.
+// cp.async, s2_d(R) rows ahead of the row in use, so many bytes stay in flight (one
+// thread per point keeps too few to fill HBM on large grids).  Each arriving row's
+// values at the lane's pair enter a register queue of 2R+1 rows; R rows later the
+// warp updates the middle row: the y part of the Laplacian from the queue, the x
+// part from that row's staged copy, still in the ring.  The per-point operation
+// sequence is plain_lap's and plain_point's (packed FP32x2 over the pair: each
+// lane the scalar round-to-nearest operation), so results are bitwise the plain
+// kernel's.  Warps are independent streams; neighbouring strips of a segment run
+// together, so the halo columns they share come from L2.
 // ---------------------------------------------------------------------------
 constexpr int kS2W = 64;  // strip width (columns)
-constexpr int kS2D = 6;   // rows copied ahead of the row in use
 __host__ __device__ constexpr int s2_hx(int R) { return (R + 3) / 4 * 4; }  // x halo, 16-B multiple
 __host__ __device__ constexpr int s2_rw(int R) { return kS2W + 2 * s2_hx(R); }  // staged row (floats)
-// ring rows per warp: a multiple of the queue length 2R+1 that holds kS2D + 2 rows,
-// so an unrolled group of that many rows addresses ring and queue slots statically
+// ring rows per warp: a multiple of the queue length 2R+1 (an unrolled group of that
+// many rows then addresses ring and queue slots statically) holding the R rows back
+// to the one being updated, the row in use and about 8 rows in flight
 __host__ __device__ constexpr int s2_nr(int R) {
-  return (2 * R + 1) * ((kS2D + 2 + 2 * R) / (2 * R + 1));
+  return (2 * R + 1) * ((R + 2 + 8 + 2 * R) / (2 * R + 1));
 }
-constexpr int kS2Warps = 8;  // warps per block (independent streams)
+__host__ __device__ constexpr int s2_d(int R) {  // rows in flight
+  return s2_nr(R) - R - 2 < 10 ? s2_nr(R) - R - 2 : 10;
+}
+// warps (streams) per block: 8, or 4 above radius 4 (registers and the ring)
+__host__ __device__ constexpr int s2_warps(int R) { return R <= 4 ? 8 : 4; }
+__host__ __device__ constexpr int s2_smem(int R) { return s2_warps(R) * s2_nr(R) * s2_rw(R) * 4; }
 
-__device__ __forceinline__ uint32_t s2_smem(const void *p) {
+__device__ __forceinline__ uint32_t s2_saddr(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 // 16 bytes global -> shared, asynchronous; src_bytes = 0 fills zeros without reading
 __device__ __forceinline__ void s2_copy16(void *dst, const void *src, int src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s2_smem(dst)), "l"(src),
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s2_saddr(dst)), "l"(src),
                "r"(src_bytes)
                : "memory");
 }
 __device__ __forceinline__ void s2_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
 __device__ __forceinline__ void s2_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(kS2D) : "memory");
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 template <int R, int EQ>
-__global__ void __launch_bounds__(kS2Warps * 32)
+__global__ void __launch_bounds__(s2_warps(R) * 32)
 k_stencil2d_stream(const float *__restrict__ u, float *un, const float *__restrict__ A,
                    const float *__restrict__ C, Geom g, Coef c, int nseg, int seglen) {
-  constexpr int HX = s2_hx(R), RW = s2_rw(R), NR = s2_nr(R), Q = 2 * R + 1;
+  constexpr int HX = s2_hx(R), RW = s2_rw(R), NR = s2_nr(R), Q = 2 * R + 1, D = s2_d(R);
+  constexpr int NWP = s2_warps(R);
   constexpr int PH = (R + 1) / 2;  // x pairs each side of the lane's own
   constexpr bool AC = EQ == kAcoustic;
-  __shared__ __align__(16) float ring[kS2Warps][NR][RW];
+  static_assert(NR % Q == 0 && NR >= D + R + 2, "ring holds the rows in flight and in use");
+  extern __shared__ __align__(16) float s2_ring[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int strips = (g.n2 + kS2W - 1) / kS2W;
-  const int item = blockIdx.x * kS2Warps + warp;
+  const int item = blockIdx.x * NWP + warp;
   if (item >= strips * nseg) return;
   const int strip = item % strips, seg = item / strips;  // neighbouring strips together
   const int x0 = strip * kS2W;
   const int ya = seg * seglen, yb = min(g.n1, ya + seglen);
   if (ya >= yb) return;
-  float(*rg)[RW] = ring[warp];
+  float *rg = s2_ring + (size_t)warp * NR * RW;
   const int T = (yb - ya) + 2 * R;  // rows streamed: ya-R .. yb+R-1
   // padded offset of (row ya - R, column x0 - HX); rows -R .. n1+R-1 exist
   const float *src0 = u + gidx(g, 0, ya - R, x0) - HX;
   const int col0 = x0 + kHaloX - HX;  // padded column of the staged row's first float
   auto issue = [&](int t) {           // row ya - R + t into ring slot t % NR
     if (t < T) {
-      float *dst = rg[t % NR];
+      float *dst = rg + (t % NR) * RW;
       const float *src = src0 + (int64_t)t * g.px;
 #pragma unroll
       for (int ch = lane; ch < RW / 4; ch += 32) {
-        const bool in = col0 + 4 * ch + 4 <= g.px;  // past the row pitch: zeros, not read
+        const bool in = col0 + 4 * ch + 4 <= g.px;  // past the row pitch: zeros, never used
         s2_copy16(dst + 4 * ch, in ? src + 4 * ch : src, in ? 16 : 0);
       }
     }
@@ -147,47 +157,42 @@ k_stencil2d_stream(const float *__restrict__ u, float *un, const float *__restri
   const bool hold = !AC && g.hold;
   const bool xin0 = hold ? (x > 0 && x < g.n2 - 1) : x < g.n2;
   const bool xin1 = hold ? (x + 1 > 0 && x + 1 < g.n2 - 1) : x + 1 < g.n2;
-  float2 q[Q];   // u^n at the pair, row t in slot t % Q
-  float2 xq[Q];  // x part of the Laplacian of row t, slot t % Q
+  float2 q[Q];  // u^n at the pair, row t in slot t % Q
 #pragma unroll
-  for (int t = 0; t < kS2D; ++t) issue(t);
+  for (int t = 0; t < D; ++t) issue(t);
   for (int tb = 0; tb < T; tb += NR) {
 #pragma unroll
     for (int ph = 0; ph < NR; ++ph) {
       const int t = tb + ph;
       if (t >= T) break;
-      issue(t + kS2D);
-      s2_wait();  // row t's copies (all but the newest kS2D groups) have landed
+      issue(t + D);
+      s2_wait<D>();  // row t's copies (all but the newest D groups) have landed
       __syncwarp();
-      const float *rr = rg[ph] + HX + 2 * lane;
-      float2 xp[2 * PH + 1];  // the row's pairs around the lane's own
-#pragma unroll
-      for (int d = -PH; d <= PH; ++d) xp[d + PH] = *reinterpret_cast<const float2 *>(rr + 2 * d);
-      const float2 uc = xp[PH];
-      q[ph % Q] = uc;
-      const float2 nuc2 = make_float2(-(uc.x + uc.x), -(uc.y + uc.y));
-      float2 lx = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int k = 1; k <= R; ++k) {
-        const float2 sx =
-            (k & 1) == 0
-                ? __fadd2_rn(xp[PH + k / 2], xp[PH - k / 2])
-                : make_float2(__fadd_rn(xp[PH + (k - 1) / 2].y, xp[PH - (k + 1) / 2].y),
-                              __fadd_rn(xp[PH + (k + 1) / 2].x, xp[PH - (k - 1) / 2].x));
-        lx = __ffma2_rn(c.wp[2][k], __fadd2_rn(sx, nuc2), lx);
-      }
-      xq[ph % Q] = lx;
+      q[ph % Q] = *reinterpret_cast<const float2 *>(rg + ph * RW + HX + 2 * lane);
       if (t >= 2 * R) {  // row y = ya + t - 2R: its y neighbours are all in the queue
         const int y = ya + t - 2 * R;
         const float2 ucy = q[(ph + Q - R) % Q];
-        const float2 ncy2 = make_float2(-(ucy.x + ucy.x), -(ucy.y + ucy.y));
-        float2 lap = xq[(ph + Q - R) % Q];
+        const float2 nuc2 = make_float2(-(ucy.x + ucy.x), -(ucy.y + ucy.y));
+        float2 lap = make_float2(0.f, 0.f);
 #pragma unroll
         for (int k = 1; k <= R; ++k)
           lap = __ffma2_rn(c.wp[1][k],
-                           __fadd2_rn(__fadd2_rn(q[(ph + Q - R + k) % Q], q[(ph + Q - R - k + Q) % Q]),
-                                      ncy2),
+                           __fadd2_rn(__fadd2_rn(q[(ph + Q - R + k) % Q], q[(ph + 2 * Q - R - k) % Q]),
+                                      nuc2),
                            lap);
+        const float *rr = rg + ((ph + NR - R) % NR) * RW + HX + 2 * lane;  // row y, staged
+        float2 xp[2 * PH + 1];  // the row's pairs around the lane's own
+#pragma unroll
+        for (int d = -PH; d <= PH; ++d) xp[d + PH] = *reinterpret_cast<const float2 *>(rr + 2 * d);
+#pragma unroll
+        for (int k = 1; k <= R; ++k) {
+          const float2 sx =
+              (k & 1) == 0
+                  ? __fadd2_rn(xp[PH + k / 2], xp[PH - k / 2])
+                  : make_float2(__fadd_rn(xp[PH + (k - 1) / 2].y, xp[PH - (k + 1) / 2].y),
+                                __fadd_rn(xp[PH + (k + 1) / 2].x, xp[PH - (k - 1) / 2].x));
+          lap = __ffma2_rn(c.wp[2][k], __fadd2_rn(sx, nuc2), lap);
+        }
         const bool yin = hold ? (y > 0 && y < g.n1 - 1) : true;
         const int64_t p = gidx(g, 0, y, x);
         float2 val;
