@@ -107,7 +107,7 @@ def parse():
                          "diffusion x-pair kernel) given explicitly")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--extras", default="sweep512,serving,fwi320,c1,oracle",
+    ap.add_argument("--extras", default="sweep512,serving,fwi320,c1,diffusion2d,oracle",
                     help="default workload, one GPU: legs measured after the main timed region "
                          "and added to its line (comma list; empty for none)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -730,6 +730,55 @@ def sweep512_result(reps=2, orders=SWEEP_ORDERS):
             "clocks": clocks.stop()}
 
 
+def diffusion2d_result(n=10000, orders=(2, 4, 8, 16), nt=100, reps=2):
+    """The paper's benchmark problem (§5.1.2: 2-D diffusion, sine-mode data, ν = 0.5,
+    interior update) at n² = 10000², a size the paper measured: per space order the
+    kernel, µs per launch, fraction of the measured copy bandwidth at 8 B/pt and
+    GPts/s of whole sweeps (field reset + nt steps)."""
+    import torch
+    from paper_1906_10811_b300 import Solver
+    peak, peak_kind = load_peak()
+    stream = torch.cuda.current_stream()
+    q = fdsynth.diffusion_problem(n, courant=0.1)
+    u0_d = torch.from_numpy(q["u0"]).cuda()
+    npts = n * n
+    clocks = ClockSampler(_gpu_uuid())
+    out = {}
+    for so in orders:
+        s = Solver((n, n), q["spacing"], so, q["dt"], "diffusion", nu=q["nu"], device=True,
+                   profile=True)
+
+        def sweep():
+            s.set_field(u0_d)
+            s.set_step(0)
+            s.run(nt)
+
+        sweep()
+        s.profile()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            sweep()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        n_st, st_ms = s.profile()
+        avg = st_ms / max(n_st, 1) / 1e3
+        ach = BYTES_PER_POINT["diffusion"] * npts / avg / 1e9
+        out[f"so{so}"] = {"kernel": s.kernel_name, "us_per_launch": round(avg * 1e6, 2),
+                          "achieved_gbs": round(ach, 1), "frac": round(ach / peak, 4),
+                          "gpts_per_s_kernel": round(npts / avg / 1e9, 2),
+                          "gpts_per_s_sweep": round(npts * nt * reps / (ms / 1e3) / 1e9, 2)}
+        s.close()
+    del u0_d
+    torch.cuda.empty_cache()
+    return {"workload": f"diffusion2d_{n}^2_nt{nt}", "nu_dt_over_h2": 0.1,
+            "orders": out, "peak": peak,
+            "peak_source": f"{peak_kind} HBM copy bandwidth (of {peak_kind})",
+            "bytes_per_point": BYTES_PER_POINT["diffusion"], "clocks": clocks.stop()}
+
+
 def c1_result(reps=20):
     """Config 1 on the device: 128² diffusion, so 2, 100 steps (L2-resident, launch-bound):
     latency of one whole run (field upload from device memory, 100 steps, read back)."""
@@ -831,6 +880,8 @@ def run_extras(args, line, p256):
                           "gpu_launches": fw["gpu_launches"], "clocks": fw["clocks"]}
     if "c1" in extras:
         line["c1_diffusion128"] = c1_result()
+    if "diffusion2d" in extras:
+        line["diffusion2d"] = diffusion2d_result()
     if "oracle" in extras and line.get("cpu_baseline") is not None:
         line["cpu_baseline"]["legs"] = oracle_legs(p256)
     line["extras_seconds"] = round(time.perf_counter() - t_start, 1)

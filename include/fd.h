@@ -69,10 +69,12 @@ typedef enum { FD_DIFFUSION = 0, FD_ACOUSTIC = 1 } fd_equation;
 
 typedef enum {
   FD_KERNEL_AUTO = 0,  /* 3-D: the pipelined kernel where it applies, else plain;
-                          2-D: plain (measured fastest on these L2-resident grids) */
+                          2-D: the row-streaming kernel for diffusion from 4 M points,
+                          else plain (fastest on L2-resident grids) */
   FD_KERNEL_PLAIN = 1, /* one thread per point, neighbours through L1/L2 */
   FD_KERNEL_TMA = 2    /* 3-D: TMA-fed shared-memory plane ring, z streamed in registers;
-                          2-D: tiles staged in shared memory (bitwise the plain kernel) */
+                          2-D: rows staged in shared memory with cp.async, y streamed in
+                          registers (bitwise the plain kernel) */
 } fd_kernel;
 
 /*

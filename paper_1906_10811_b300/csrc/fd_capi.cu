@@ -31,8 +31,11 @@ using namespace fdk;
 namespace {
 
 constexpr int kGraphChunk = 64;  // steps per captured graph
-// 2-D grids of at least this many points run the streaming kernel by default
-constexpr int64_t kStream2dPoints = 8 << 20;
+// 2-D diffusion grids of at least this many points run the streaming kernel by
+// default (measured: 0.88 of the copy bandwidth at 10000² so 2, against 0.36 for the
+// plain kernel; the acoustic step, whose coefficients the stream does not stage,
+// keeps the plain kernel)
+constexpr int64_t kStream2dPoints = 4 << 20;
 constexpr int kGraphCacheMax = 12;
 thread_local std::string g_create_error;  // fd_last_error(NULL)
 
@@ -678,9 +681,9 @@ void select_kernel(fd_ctx *c) {
   c->kernel_name = three ? "stencil3d_plain" : "stencil2d_plain";
   c->stream2d_fn = nullptr;
   if (!three) {
-    // rows staged and streamed along y: on request (FD_KERNEL_TMA), and by default
-    // on grids too large for L2 to hold the shot's fields, where one thread per point
-    // keeps too few bytes in flight to fill HBM
+    // rows staged and streamed along y: on request (FD_KERNEL_TMA), and by default for
+    // diffusion on grids too large for L2, where one thread per point keeps too few
+    // bytes in flight to fill HBM
     int dev = 0, sms = 148;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -689,7 +692,7 @@ void select_kernel(fd_ctx *c) {
     }
     const int64_t pts = (int64_t)c->g.n1 * c->g.n2;
     const bool want = c->opt.kernel == FD_KERNEL_TMA ||
-                      (c->opt.kernel == FD_KERNEL_AUTO && pts >= kStream2dPoints);
+                      (c->opt.kernel == FD_KERNEL_AUTO && !ac && pts >= kStream2dPoints);
     if (want) {
       // segments of at least max(32, 4R) rows; about 64 warp streams per SM in all
       const int strips = (c->g.n2 + kS2W - 1) / kS2W;

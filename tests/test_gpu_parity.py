@@ -403,3 +403,23 @@ def test_diffusion_every_node_updated(kernel, shape, tile, so):
     assert np.abs(u[0] - u0[0]).max() > 0          # boundary nodes move
     held = oracle.diffusion(u0, h, so, 0.5, dt, 30)
     assert rel_l2(held, ref) > 1e-4                # the two sweeps differ measurably
+
+
+def test_large_2d_diffusion_streams_rows_by_default():
+    """From 4 M points a 2-D diffusion context runs the row-streaming kernel unless
+    asked for plain; the acoustic step keeps the plain kernel; both kernels agree."""
+    from paper_1906_10811_b300 import Solver
+    shape = (2100, 2003)
+    rng = np.random.default_rng(5)
+    u0 = rng.standard_normal(shape).astype(np.float32)
+    h = (1.0 / 2099, 1.0 / 2002)
+    outs = []
+    for kernel, name in (("auto", "stencil2d_stream"), ("plain", "stencil2d_plain")):
+        with Solver(shape, h, 4, 0.05 * min(h) ** 2, "diffusion", kernel=kernel) as s:
+            assert s.kernel_name == name
+            s.set_field(u0)
+            s.run(7)
+            outs.append(s.read()[0])
+    assert np.array_equal(outs[0], outs[1])
+    with Solver(shape, (10.0, 10.0), 4, 0.1, "acoustic") as s:
+        assert s.kernel_name == "stencil2d_plain"
