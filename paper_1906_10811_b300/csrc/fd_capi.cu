@@ -694,13 +694,6 @@ void select_kernel(fd_ctx *c) {
     const bool want = c->opt.kernel == FD_KERNEL_TMA ||
                       (c->opt.kernel == FD_KERNEL_AUTO && !ac && pts >= kStream2dPoints);
     if (want) {
-      // segments of at least max(32, 4R) rows; about 64 warp streams per SM in all
-      const int strips = (c->g.n2 + kS2W - 1) / kS2W;
-      const int target = 64 * sms;
-      const int most = std::max(1, c->g.n1 / std::max(32, 4 * R));
-      int nseg = std::max(1, std::min((target + strips - 1) / strips, most));
-      c->s2_seglen = (c->g.n1 + nseg - 1) / nseg;
-      c->s2_nseg = (c->g.n1 + c->s2_seglen - 1) / c->s2_seglen;
 #define PICK2(RR)                                                                      \
   case RR:                                                                             \
     c->stream2d_fn = ac ? k_stencil2d_stream<RR, kAcoustic> : k_stencil2d_stream<RR, kDiffusion>; \
@@ -713,6 +706,22 @@ void select_kernel(fd_ctx *c) {
         PICK2(1) PICK2(2) PICK2(3) PICK2(4) PICK2(5) PICK2(6) PICK2(7) PICK2(8)
       }
 #undef PICK2
+      // one wave: as many warp streams as the SMs hold at once (strip by segment),
+      // segments of at least max(32, 4R) rows
+      int per_sm = 1;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c->stream2d_fn,
+                                                        s2_warps(R) * 32, s2_smem(R)) !=
+              cudaSuccess ||
+          per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+      }
+      const int strips = (c->g.n2 + kS2W - 1) / kS2W;
+      const int slots = sms * per_sm * s2_warps(R);
+      const int most = std::max(1, c->g.n1 / std::max(32, 4 * R));
+      const int nseg = std::max(1, std::min(slots / strips, most));
+      c->s2_seglen = (c->g.n1 + nseg - 1) / nseg;
+      c->s2_nseg = (c->g.n1 + c->s2_seglen - 1) / c->s2_seglen;
       c->kernel_name = "stencil2d_stream";
     }
   }
@@ -1706,12 +1715,16 @@ namespace {
 // epilogue (into fwi_buf[0]) and a step with the imaging epilogue (reading
 // fwi_buf[0], accumulating into fwi_buf[1]): the kernels of one backward step of
 // the FWI sweep.
+// The launches of a repetition follow each other without an event between them, as
+// in the replayed step graphs (an event before every launch leaves a gap that favours
+// configurations with fewer, longer CTAs); the median over kTuneBatches batches of
+// reps repetitions, per repetition.
+constexpr int kTuneBatches = 3;
 fd_status time_plan(fd_ctx *c, const TmaPlan &p, float *out, int reps, cudaEvent_t *ev,
                     double *us, float *const *fwi_buf = nullptr,
                     const unsigned char *unit_c = nullptr) {
   const int cur = c->cur;
-  for (int i = 0; i < 2 + reps; ++i) {
-    if (i >= 2) CU(cudaEventRecord(ev[i - 2], c->stream));
+  auto one = [&]() -> fd_status {
     cudaError_t e =
         launch_tma_step(p, cur, out, c->coef, c->d_err, SparseArgs{}, c->stream, unit_c);
     if (e == cudaSuccess && fwi_buf)
@@ -1722,17 +1735,25 @@ fd_status time_plan(fd_ctx *c, const TmaPlan &p, float *out, int reps, cudaEvent
                               fwi_buf[0], 1.f, c->stream, unit_c);
     if (e != cudaSuccess) return fail(c, FD_ECUDA, "autotune launch: %s", cudaGetErrorString(e));
     c->launches += fwi_buf ? 3 : 1;
+    return FD_OK;
+  };
+  fd_status st = FD_OK;
+  for (int i = 0; i < 2 && !st; ++i) st = one();  // warm-up
+  for (int b = 0; b < kTuneBatches && !st; ++b) {
+    CU(cudaEventRecord(ev[b], c->stream));
+    for (int i = 0; i < reps && !st; ++i) st = one();
   }
-  CU(cudaEventRecord(ev[reps], c->stream));
-  CU(cudaEventSynchronize(ev[reps]));
-  std::vector<double> t(reps);
-  for (int i = 0; i < reps; ++i) {
+  if (st) return st;
+  CU(cudaEventRecord(ev[kTuneBatches], c->stream));
+  CU(cudaEventSynchronize(ev[kTuneBatches]));
+  std::vector<double> t(kTuneBatches);
+  for (int b = 0; b < kTuneBatches; ++b) {
     float ms = 0.f;
-    CU(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
-    t[i] = 1e3 * ms;
+    CU(cudaEventElapsedTime(&ms, ev[b], ev[b + 1]));
+    t[b] = 1e3 * ms / reps;
   }
   std::sort(t.begin(), t.end());
-  *us = t[reps / 2];
+  *us = t[kTuneBatches / 2];
   return FD_OK;
 }
 
@@ -1766,7 +1787,7 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
     dfree(c, fbuf[1]);
     return st;
   }
-  std::vector<cudaEvent_t> ev(reps + 1, nullptr);
+  std::vector<cudaEvent_t> ev(kTuneBatches + 1, nullptr);
   for (auto &e : ev)
     if (!st && cudaEventCreate(&e) != cudaSuccess) st = fail(c, FD_ECUDA, "event creation");
   const int eq = c->eq == FD_ACOUSTIC ? kAcoustic : kDiffusion;
