@@ -327,8 +327,9 @@ fd_status fd_field_to_dense(fd_ctx *ctx, const float *padded, float *dense);
  *   {16, 32} × ctas_per_sm in 1..fit × (aligned 0 with zblock in {share/2,
  *   share, 2·share} | aligned 1 with m or 2m z-blocks, m = CTAs / tiles)
  *   × skip_c {0, 1} where it applies (once a model is set),
- *   three batches of reps ≥ 1 back-to-back launches after two warm-up
- *   launches, the median batch time per launch),
+ *   reps ≥ 1 launches captured in a CUDA graph and replayed three times
+ *   after two warm-up launches (eager batches where the stream cannot capture),
+ *   the median replay per launch),
  *   then use the fastest.  The candidate launches read the current fields
  *   and write a scratch field allocated for the call, so the solution is not
  *   disturbed; sources are not injected during the trials.  Synchronises the
