@@ -330,13 +330,13 @@ fd_status fd_field_to_dense(fd_ctx *ctx, const float *padded, float *dense);
  *   reps ≥ 1 launches captured in a CUDA graph and replayed three times
  *   after two warm-up launches (eager batches where the stream cannot capture),
  *   the median replay per launch),
- *   then use the fastest.  The candidate launches read the current fields
- *   and write a scratch field allocated for the call, so the solution is not
- *   disturbed; sources are not injected during the trials.  Synchronises the
+ *   then use the fastest.  The candidate launches step on two scratch
+ *   levels copied from the current ones, rotating them as fd_run does, so
+ *   the solution is not disturbed; sources are not injected during the trials.  Synchronises the
  *   context stream.  tried (may be NULL) receives up to max_tried measured
  *   configurations, *ntried (may be NULL) how many were measured (which may
  *   exceed max_tried); best (may be NULL)
- *   the chosen one.  FD_ENOMEM when the scratch field does not fit.
+ *   the chosen one.  FD_ENOMEM when the scratch levels do not fit.
  */
 typedef struct {
   int tile_x;

@@ -1713,19 +1713,27 @@ namespace {
 // repetition.  Launching with an event before every launch ranked the x-pair tile
 // ahead of the 32-wide one at 256³ so 8, which replays 2-4 % faster in the step graphs.
 constexpr int kTuneBatches = 3;
-fd_status time_plan(fd_ctx *c, const TmaPlan &p, float *out, int reps, cudaEvent_t *ev,
-                    double *us, float *const *fwi_buf = nullptr,
-                    const unsigned char *unit_c = nullptr) {
-  const int cur = c->cur;
+// The plan steps on two scratch levels (copies of the context's), rotating them like
+// fd_run: each launch reads the level the previous one wrote, so the timing sees the
+// L2 reuse of real steps (part of u^{n+1} is still in L2 when it is read as u^n).
+fd_status time_plan(fd_ctx *c, const TmaPlan &p, int reps, cudaEvent_t *ev, double *us,
+                    float *const *fwi_buf = nullptr, const unsigned char *unit_c = nullptr) {
+  int cur = 0;
+  reps += reps & 1;  // an even count: a replay ends on the parity it starts from
+  auto step = [&](float *d2, float *img, const float *img_d2, float scale) -> cudaError_t {
+    float *out = p.level[cur ^ 1];
+    const cudaError_t e =
+        (d2 || img) ? launch_tma_step_fwi(p, cur, out, c->coef, c->d_err, SparseArgs{}, d2, img,
+                                          img_d2, scale, c->stream, unit_c)
+                    : launch_tma_step(p, cur, out, c->coef, c->d_err, SparseArgs{}, c->stream,
+                                      unit_c);
+    cur ^= 1;
+    return e;
+  };
   auto one = [&]() -> fd_status {
-    cudaError_t e =
-        launch_tma_step(p, cur, out, c->coef, c->d_err, SparseArgs{}, c->stream, unit_c);
-    if (e == cudaSuccess && fwi_buf)
-      e = launch_tma_step_fwi(p, cur, out, c->coef, c->d_err, SparseArgs{}, fwi_buf[0], nullptr,
-                              nullptr, 0.f, c->stream, unit_c);
-    if (e == cudaSuccess && fwi_buf)
-      e = launch_tma_step_fwi(p, cur, out, c->coef, c->d_err, SparseArgs{}, nullptr, fwi_buf[1],
-                              fwi_buf[0], 1.f, c->stream, unit_c);
+    cudaError_t e = step(nullptr, nullptr, nullptr, 0.f);
+    if (e == cudaSuccess && fwi_buf) e = step(fwi_buf[0], nullptr, nullptr, 0.f);
+    if (e == cudaSuccess && fwi_buf) e = step(nullptr, fwi_buf[1], fwi_buf[0], 1.f);
     if (e != cudaSuccess) return fail(c, FD_ECUDA, "autotune launch: %s", cudaGetErrorString(e));
     c->launches += fwi_buf ? 3 : 1;
     return FD_OK;
@@ -1797,14 +1805,24 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
       return FD_OK;
     }
   }
-  float *scratch = nullptr, *fbuf[2] = {nullptr, nullptr};
-  fd_status st = dalloc(c, &scratch, (size_t)c->g.total);
+  // two scratch levels (the plans step on copies of the current ones), and for the
+  // FWI sweep the second-difference and imaging fields
+  float *lev[2] = {nullptr, nullptr}, *fbuf[2] = {nullptr, nullptr};
+  fd_status st = dalloc(c, &lev[0], (size_t)c->g.total);
+  if (!st) st = dalloc(c, &lev[1], (size_t)c->g.total);
+  if (!st)
+    CU(cudaMemcpyAsync(lev[0], c->u[c->cur], c->g.total * sizeof(float),
+                       cudaMemcpyDeviceToDevice, c->stream));
+  if (!st)
+    CU(cudaMemcpyAsync(lev[1], c->u[c->cur ^ 1], c->g.total * sizeof(float),
+                       cudaMemcpyDeviceToDevice, c->stream));
   if (!st && fwi) st = dalloc(c, &fbuf[0], (size_t)c->g.total);
   if (!st && fwi) st = dalloc(c, &fbuf[1], (size_t)c->g.total);
   if (!st && fwi) CU(cudaMemsetAsync(fbuf[0], 0, c->g.total * sizeof(float), c->stream));
   if (!st && fwi) CU(cudaMemsetAsync(fbuf[1], 0, c->g.total * sizeof(float), c->stream));
   if (st) {
-    dfree(c, scratch);
+    dfree(c, lev[0]);
+    dfree(c, lev[1]);
     dfree(c, fbuf[0]);
     dfree(c, fbuf[1]);
     return st;
@@ -1861,7 +1879,10 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
   // only with a model set: before it C is 0 everywhere and nothing would be skipped)
   const bool try_skip = c->eq == FD_ACOUSTIC && R <= 4 && c->model_set;
   unsigned char *flags = nullptr;
-  if (!st && try_skip) st = dalloc(c, &flags, (size_t)c->tma.args.ntiles * c->g.n0 * 2 + 64);
+  // flags for the most tile-planes any candidate has (the smallest tile, kTmaTX × 16)
+  const size_t max_flags = (size_t)((c->g.n2 + kTmaTX - 1) / kTmaTX) *
+                           (size_t)((c->g.n1 + tma_ty(2) - 1) / tma_ty(2)) * c->g.n0;
+  if (!st && try_skip) st = dalloc(c, &flags, max_flags);
   fd_tile_config win{};
   double win_us = 1e300;
   int n = 0;
@@ -1869,7 +1890,7 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
     if (st) break;
     TmaPlan r{};
     const char *why = nullptr;
-    if (plan_tma(r, c->g, eq, c->iso, c->u, c->A, c->C, cd.ny, cd.cps, cd.zb, cd.aligned, &why,
+    if (plan_tma(r, c->g, eq, c->iso, lev, c->A, c->C, cd.ny, cd.cps, cd.zb, cd.aligned, &why,
                  cd.tx, ctx_origin(c)) != cudaSuccess) {
       cudaGetLastError();
       continue;
@@ -1878,6 +1899,10 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
     for (int sk = 0; sk <= (try_skip ? 1 : 0) && !st; ++sk) {
       if (sk) {
         const int64_t nf = (int64_t)r.args.ntiles * c->g.n0;
+        if ((size_t)nf > max_flags) {  // cannot happen: the smallest tile bounds the count
+          st = fail(c, FD_ECUDA, "autotune: flag buffer too small");
+          break;
+        }
         k_unit_c<<<(unsigned)nf, 128, 0, c->stream>>>(c->C, c->g, r.args.tiles_x, cd.tx,
                                                        tma_ty(cd.ny), flags);
         if (cudaGetLastError() != cudaSuccess) {
@@ -1886,7 +1911,7 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
         }
       }
       double us = 0.0;
-      st = time_plan(c, r, scratch, reps, ev.data(), &us, fwi ? fbuf : nullptr,
+      st = time_plan(c, r, reps, ev.data(), &us, fwi ? fbuf : nullptr,
                      sk ? flags : nullptr);
       if (st) break;
       fd_tile_config cfg{cd.tx, tma_ty(cd.ny), r.args.zblock, r.per_sm, cd.aligned, sk, us};
@@ -1901,7 +1926,8 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
   dfree(c, flags);
   for (auto &e : ev)
     if (e) cudaEventDestroy(e);
-  dfree(c, scratch);
+  dfree(c, lev[0]);
+  dfree(c, lev[1]);
   dfree(c, fbuf[0]);
   dfree(c, fbuf[1]);
   if (st) return st;
