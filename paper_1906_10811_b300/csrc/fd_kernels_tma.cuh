@@ -53,19 +53,33 @@ constexpr long long kWaitBudget = 1ll << 31;  // clock cycles (~1 s at 2 GHz)
 __host__ __device__ constexpr int tma_ny(int R) { return R <= 4 ? 4 : 2; }   // default rows/thread
 __host__ __device__ constexpr int tma_ty(int NY) { return kTmaNW * NY; }      // tile height
 __host__ __device__ constexpr int tma_hxb(int R) { return (R + 3) / 4 * 4; }   // x halo, 16-B multiple
-__host__ __device__ constexpr int tma_du(int R) { return R + 4; }              // ring U slots
 __host__ __device__ constexpr int tma_bw(int R) { return kTmaTX + 2 * tma_hxb(R); }  // box width
 __host__ __device__ constexpr int tma_bh(int R, int NY) { return tma_ty(NY) + 2 * R; }  // box height
 __host__ __device__ constexpr int tma_ubytes(int R, int NY) { return tma_bw(R) * tma_bh(R, NY) * 4; }
 __host__ __device__ constexpr int tma_xbytes(int NY) { return kTmaTX * tma_ty(NY) * 4; }
 __host__ __device__ constexpr int tma_align128(int b) { return (b + 127) / 128 * 128; }
+// Ring U slots: the window needs R + 1 planes (the centre plane for the x/y
+// neighbours up to the newest plane entering the queue); the rest is prefetch.
+// The acoustic step keeps 3 planes of prefetch (its ring X of (u^{n-1}, A, C)
+// tiles holds most bytes in flight); diffusion reads only u^n, so its ring
+// grows to about diff_ring(R) bytes (up to 11 planes of prefetch) to keep
+// enough bytes in flight per SM for HBM: 100 KB (two CTAs an SM) from radius 3,
+// 56 KB below (up to four CTAs an SM, their register count allowing).
+__host__ __device__ constexpr int diff_ring(int R) { return (R <= 2 ? 56 : 100) * 1024; }
+__host__ __device__ constexpr int du_fill(int R, int slot_bytes) {
+  return R + 12 < diff_ring(R) / tma_align128(slot_bytes) ? R + 12
+                                                          : diff_ring(R) / tma_align128(slot_bytes);
+}
+__host__ __device__ constexpr int tma_du(int R, bool acoustic = true, int slot_bytes = 0) {
+  return acoustic || du_fill(R, slot_bytes) < R + 4 ? R + 4 : du_fill(R, slot_bytes);
+}
 // ring X: kTmaDX slots of (u^{n-1}, A, C); with the FWI epilogue 2 slots of
 // (u^{n-1}, A, C, d2, g) so two CTAs still fit on an SM
 __host__ __device__ constexpr int tma_dx(bool fwi) { return fwi ? 2 : kTmaDX; }
 __host__ __device__ constexpr int tma_xn(bool fwi) { return fwi ? 5 : 3; }
 // shared memory: barriers (1 KB) | ring U | ring X
 __host__ __device__ constexpr int tma_smem_bytes(int R, int NY, bool acoustic, bool fwi = false) {
-  return 1024 + tma_du(R) * tma_align128(tma_ubytes(R, NY)) +
+  return 1024 + tma_du(R, acoustic, tma_ubytes(R, NY)) * tma_align128(tma_ubytes(R, NY)) +
          (acoustic ? tma_dx(fwi) * tma_xn(fwi) * tma_xbytes(NY) : 0);
 }
 // Consumer loop unrolling: up to radius 4 by the whole window (2R+1 phases,
@@ -347,7 +361,7 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
                 const __grid_constant__ CUtensorMap map_g,   // FWI: img, tile box
                 const TmaArgs args, const BatchArgs bat) {
   constexpr int TY = tma_ty(NY);
-  constexpr int HXB = tma_hxb(R), BW = tma_bw(R), DU = tma_du(R);
+  constexpr int HXB = tma_hxb(R), BW = tma_bw(R), DU = tma_du(R, EQ == kAcoustic, tma_ubytes(R, NY));
   constexpr int USLOT = tma_align128(tma_ubytes(R, NY)) / 4;  // floats per ring-U slot
   constexpr int XT = kTmaTX * TY;                          // floats per tile
   constexpr int Q = 2 * R + 1;                             // window of planes
@@ -806,7 +820,7 @@ __host__ __device__ constexpr int xp_bw(int R) { return kXpTX + 2 * tma_hxb(R); 
 __host__ __device__ constexpr int xp_ubytes(int R, int NY) { return xp_bw(R) * tma_bh(R, NY) * 4; }
 __host__ __device__ constexpr int xp_xbytes(int NY) { return kXpTX * tma_ty(NY) * 4; }
 __host__ __device__ constexpr int xp_smem_bytes(int R, int NY, bool acoustic) {
-  return 1024 + tma_du(R) * tma_align128(xp_ubytes(R, NY)) +
+  return 1024 + tma_du(R, acoustic, xp_ubytes(R, NY)) * tma_align128(xp_ubytes(R, NY)) +
          (acoustic ? kTmaDX * 3 * xp_xbytes(NY) : 0);
 }
 // the queue holds 2·NY·(2R+1) floats a thread
@@ -877,7 +891,7 @@ k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXp
                const TmaArgs args, const BatchArgs) {
   constexpr bool AC = EQ == kAcoustic;
   constexpr int TY = tma_ty(NY);
-  constexpr int HXB = tma_hxb(R), BW = xp_bw(R), DU = tma_du(R), DX = kTmaDX;
+  constexpr int HXB = tma_hxb(R), BW = xp_bw(R), DU = tma_du(R, AC, xp_ubytes(R, NY)), DX = kTmaDX;
   constexpr int USLOT = tma_align128(xp_ubytes(R, NY)) / 4;  // floats per ring-U slot
   constexpr int XT = kXpTX * TY;                              // floats per ring-X tile
   constexpr int Q = 2 * R + 1;
