@@ -305,8 +305,14 @@ fd_status fd_field_to_dense(fd_ctx *ctx, const float *padded, float *dense);
  *                z-block-major order (a run may start or end inside a
  *                segment); 1 = CTAs get whole (z-block, tile) segments, at
  *                most one CTA per segment, so that the CTAs holding
- *                neighbouring tiles start their segments together.  A new
- *                context starts with 1 for FD_ACOUSTIC, 0 for FD_DIFFUSION
+ *                neighbouring tiles start their segments together; 2 (tile_x
+ *                64 only) = a work queue: z-layers (thick while much work remains, thin at
+ *                the end; zblock > 0 caps their height) cut into one item per
+ *                tile, taken layer by layer, tile by tile, by whichever CTA is
+ *                free, so the items in flight are neighbours at about the same
+ *                depth and the CTAs finish together (device memory: 16 bytes
+ *                per item, held by the plan).  A new context starts with 1 for
+ *                FD_ACOUSTIC, 0 for FD_DIFFUSION
  *   skip_c       FD_ACOUSTIC up to space order 8: 1 = tile-planes where C =
  *                (m−σ)/(m+σ) is 1 at every point (no damping) take C = 1 instead
  *                of loading it (4 of the 20 bytes per point; flags recomputed
@@ -318,14 +324,16 @@ fd_status fd_field_to_dense(fd_ctx *ctx, const float *padded, float *dense);
  *   context runs the plain kernel.
  * fd_set_tile_config: use cfg (tile_x 32 or 0, or 64, tile_y 16 or 32 or 0 for the
  *   default, zblock ≥ 0 with 0 meaning one CTA's share (aligned = 0) or the
- *   height that makes about as many segments as CTAs (aligned = 1),
- *   ctas_per_sm ≥ 0 with 0 meaning as many as fit, aligned and skip_c 0 or 1);
+ *   height that makes about as many segments as CTAs (aligned = 1) or no cap
+ *   on the layer height (aligned = 2), ctas_per_sm ≥ 0 with 0 meaning as many
+ *   as fit, aligned 0, 1 or 2, skip_c 0 or 1);
  *   FD_EINVAL for anything else, leaving the current configuration in
  *   place.  Captured graphs are dropped.
  * fd_autotune: time every configuration of the search space (tile_x in {32, 64}
  *   (32 only for fd_autotune_fwi) × tile_y in
  *   {16, 32} × ctas_per_sm in 1..fit × (aligned 0 with zblock in {share/2,
- *   share, 2·share} | aligned 1 with m or 2m z-blocks, m = CTAs / tiles)
+ *   share, 2·share} | aligned 1 with m or 2m z-blocks, m = CTAs / tiles |
+ *   aligned 2 with uncapped layers for tile_x 64)
  *   × skip_c {0, 1} where it applies (once a model is set),
  *   reps ≥ 1 launches captured in a CUDA graph and replayed three times
  *   after two warm-up launches (eager batches where the stream cannot capture),

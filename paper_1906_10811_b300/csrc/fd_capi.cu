@@ -1416,7 +1416,7 @@ fd_status fd_set_tile_config(fd_ctx *c, const fd_tile_config *cfg) {
   const int tx = cfg->tile_x ? cfg->tile_x : kTmaTX;
   if (!tma_tx_supported(tx, c->eq == FD_ACOUSTIC ? kAcoustic : kDiffusion) || cfg->tile_y % kTmaNW ||
       (cfg->tile_y != 0 && !tma_ny_supported(cfg->tile_y / kTmaNW)) || cfg->zblock < 0 ||
-      cfg->ctas_per_sm < 0 || (cfg->aligned != 0 && cfg->aligned != 1) ||
+      cfg->ctas_per_sm < 0 || cfg->aligned < 0 || cfg->aligned > 2 ||
       (cfg->skip_c != 0 && cfg->skip_c != 1))
     return fail(c, FD_EINVAL,
                 "tile configuration %dx%d, zblock %d, %d CTAs/SM, aligned %d, skip_c %d is not offered",
@@ -1873,6 +1873,9 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
           dup |= d.ny == ny && d.cps == cps && d.zb == zb && d.aligned && d.tx == tx;
         if (!dup) cands.push_back({ny, cps, zb, 1, tx});
       }
+      // work queue (x-pair tiles): z-layers thick first, thin last, taken by
+      // whichever CTA is free
+      if (tx == kXpTX) cands.push_back({ny, cps, 0, 2, tx});
     }
   }
   // each candidate once more skipping the C tiles where C = 1 (acoustic, R <= 4;

@@ -34,7 +34,12 @@
 
 #include <algorithm>
 #include <climits>
+#include <cmath>
 #include <cudaTypedefs.h>
+#include <functional>
+#include <memory>
+#include <queue>
+#include <vector>
 
 #include "fd_common.cuh"
 
@@ -235,6 +240,11 @@ struct TmaArgs {
   float *img;          // if set: img += img_scale * u^{n+1} * img_d2 (imaging condition)
   const float *img_d2;
   float img_scale;
+  // work queue (aligned = 2, x-pair instances with QUEUE = true): {0, tile, za, zb}
+  // items, z-layer by z-layer, tile by tile; wq[0] = next ticket, wq[1] = CTAs done
+  const int4 *items;
+  int nitems;
+  unsigned *wq;
 };
 
 // The segment at work position q of a CTA's range [q, q1), advancing q.
@@ -250,6 +260,22 @@ __device__ __forceinline__ void next_segment(const TmaArgs &a, int64_t &q, int64
   } else {
     segment_at(q, q1, a.ntiles, a.zblock, a.g.n0, tile, za, zb);
     q += zb - za;
+  }
+}
+
+// Work queue: the producer lane takes the next item with a ticket; past the last
+// item it gets the end mark {-1, ...}.
+__device__ __forceinline__ int4 take_item(unsigned *ticket, const int4 *items, int nitems) {
+  const unsigned it = atomicAdd(ticket, 1u);
+  return it < (unsigned)nitems ? items[it] : make_int4(-1, 0, 0, 0);
+}
+// Called once per CTA after its producer took its last ticket: the last CTA of the
+// launch resets the queue for the next launch (launches of a plan are stream-ordered).
+__device__ __forceinline__ void queue_done(unsigned *wq) {
+  __threadfence();  // this CTA's tickets before its count
+  if (atomicAdd(&wq[1], 1u) == gridDim.x - 1) {
+    atomicExch(&wq[0], 0u);
+    atomicExch(&wq[1], 0u);
   }
 }
 
@@ -814,8 +840,22 @@ timeout:
 // pair.  The per-point operation sequence is that of k_stencil3d_tma (the same
 // sums in the same order, round to nearest; sources added in entry order), so
 // results are bitwise the same.  No batched or FWI instances.
+//
+// QUEUE: instead of a static share of the segments, the CTAs take {0, tile, za,
+// zb} items from a work queue (TmaArgs items/wq): z-layers thick first and thin
+// last, layer by layer, tile by tile, so the items in flight are neighbouring
+// tiles at about the same depth (their halo rows are read from DRAM once) and the
+// CTAs finish together.  The producer publishes each item to the consumers in a
+// shared-memory ring before the item's first plane; the last CTA out resets the
+// queue.  A separate instance, so that the static splits keep their own code.
 // ---------------------------------------------------------------------------
 constexpr int kXpTX = 64;
+// Work-queue items published ahead of use (shared memory at byte 512).  The
+// producer writes entry k + kItemRing after issuing every fill of items k ..
+// k + kItemRing - 1 (at least 1 + 2R each), which needs the ring-U slot of a
+// fill more than a ring depth later to be released: the consumers have read
+// entry k by then (static_assert in the kernel).
+constexpr int kItemRing = 16;
 __host__ __device__ constexpr int xp_bw(int R) { return kXpTX + 2 * tma_hxb(R); }
 __host__ __device__ constexpr int xp_ubytes(int R, int NY) { return xp_bw(R) * tma_bh(R, NY) * 4; }
 __host__ __device__ constexpr int xp_xbytes(int NY) { return kXpTX * tma_ty(NY) * 4; }
@@ -881,7 +921,7 @@ __device__ __noinline__ SourceHitsXp source_hits_xp_call(const int4 *entries,
                         nstep, vx, vy);
 }
 
-template <int R, int NY, int EQ, bool ISO>
+template <int R, int NY, int EQ, bool ISO, bool QUEUE = false>
 __global__ void __launch_bounds__(kTmaThreads, xp_minb(R, NY))
 k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXpTX + 2·HXB wide)
                const __grid_constant__ CUtensorMap map_p,  // u^{n-1}, tile box (kXpTX wide)
@@ -901,12 +941,16 @@ k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXp
   constexpr bool kUnitC = AC && R <= 4;
   constexpr int PH = (R + 1) / 2;  // x pairs each side of the lane's own
   static_assert(NY <= 4, "source rows are carried in a float4");
+  static_assert(!QUEUE || ((2 * DU + 2 * DX) * 8 + 4 <= 512 &&
+                           kItemRing * (1 + 2 * R) >= DU + 1 && 512 + kItemRing * 16 <= 1024),
+                "item ring: overlaps the barriers, or too shallow for ring U");
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t *full_u = reinterpret_cast<uint64_t *>(smem);
   uint64_t *empty_u = full_u + DU;
   uint64_t *full_x = empty_u + DU;
   uint64_t *empty_x = full_x + DX;
   volatile int *abort_flag = reinterpret_cast<volatile int *>(empty_x + DX);
+  volatile int4 *item_ring = reinterpret_cast<volatile int4 *>(smem + 512);  // QUEUE only
   float *ring_u = reinterpret_cast<float *>(smem + 1024);
   float *ring_x = ring_u + DU * USLOT;
 
@@ -928,11 +972,13 @@ k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXp
   __syncthreads();
 
   int64_t q0 = 0, q1 = 0;
-  if (args.aligned)
-    cta_range((int64_t)args.ntiles * ((args.g.n0 + args.zblock - 1) / args.zblock), blockIdx.x,
-              gridDim.x, q0, q1);
-  else
-    cta_range(args.W, blockIdx.x, gridDim.x, q0, q1);
+  if constexpr (!QUEUE) {
+    if (args.aligned)
+      cta_range((int64_t)args.ntiles * ((args.g.n0 + args.zblock - 1) / args.zblock), blockIdx.x,
+                gridDim.x, q0, q1);
+    else
+      cta_range(args.W, blockIdx.x, gridDim.x, q0, q1);
+  }
   const unsigned char *ucf = kUnitC ? args.unit_c : nullptr;
 
   if (warp == kTmaNW) {
@@ -948,9 +994,34 @@ k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXp
       const uint64_t keep = l2_policy_evict_last(), once = l2_policy_evict_first();
       bool ok = true;
       int64_t q = q0;
-      while (ok && q < q1) {
+      unsigned nitem = 0;  // QUEUE: items taken by this block
+      while (ok && (QUEUE || q < q1)) {
         int tile, za, zb;
-        next_segment(args, q, q1, tile, za, zb);
+        if constexpr (QUEUE) {
+          const int4 item = take_item(args.wq, args.items, args.nitems);
+          item_ring[nitem % kItemRing].x = item.x;
+          item_ring[nitem % kItemRing].y = item.y;
+          item_ring[nitem % kItemRing].z = item.z;
+          item_ring[nitem % kItemRing].w = item.w;
+          ++nitem;
+          if (item.x < 0) {
+            // no work left: complete the next ring-U phase without data so the
+            // consumers read the end mark published above
+            const uint32_t slot = su % DU;
+            if (su >= (uint32_t)DU && !mbar_wait(&empty_u[slot], ((su / DU) - 1) & 1)) {
+              ok = false;
+              break;
+            }
+            mbar_arrive(&full_u[slot]);
+            ++su;
+            break;
+          }
+          tile = item.y;
+          za = item.z;
+          zb = item.w;
+        } else {
+          next_segment(args, q, q1, tile, za, zb);
+        }
         const int x0 = (tile % args.tiles_x) * kXpTX, y0 = (tile / args.tiles_x) * TY;
         for (int p = za - R; p < zb + R; ++p) {
           if (*abort_flag) { ok = false; break; }
@@ -994,6 +1065,7 @@ k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXp
         drained &= mbar_wait(&full_x[last % DX], (last / DX) & 1);
       }
       if (!drained && atomicCAS(err, 0, 3) == 0) err[1] = blockIdx.x;
+      if constexpr (QUEUE) queue_done(args.wq);
     }
     return;
   }
@@ -1008,9 +1080,22 @@ k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXp
   const int64_t nstep = (AC && sp.step) ? *sp.step + sp.j : 0;
   float *const out = args.out;
   int64_t q = q0;
-  while (q < q1) {
+  unsigned nitem = 0;
+  while (QUEUE || q < q1) {
     int tile, za, zb;
-    next_segment(args, q, q1, tile, za, zb);
+    if constexpr (QUEUE) {
+      // the next item is published with the first fill of its planes
+      if (!mbar_wait(&full_u[su % DU], (su / DU) & 1)) goto timeout;
+      const int4 item = make_int4(item_ring[nitem % kItemRing].x, item_ring[nitem % kItemRing].y,
+                                  item_ring[nitem % kItemRing].z, item_ring[nitem % kItemRing].w);
+      ++nitem;
+      if (item.x < 0) break;
+      tile = item.y;
+      za = item.z;
+      zb = item.w;
+    } else {
+      next_segment(args, q, q1, tile, za, zb);
+    }
     const int n0 = g.n0;
     const int x = (tile % args.tiles_x) * kXpTX + 2 * lane;
     const int ybase = (tile / args.tiles_x) * TY + row0;
@@ -1226,8 +1311,63 @@ struct TmaPlan {
   int per_sm_fwi = 0;  // occupancy limit of fn_fwi
   int smem_fwi = 0;
   int sms = 0;
-  int tx = kTmaTX;     // tile width: kTmaTX, or kXpTX (diffusion, two x points a lane)
+  int tx = kTmaTX;     // tile width: kTmaTX, or kXpTX (two x points a lane)
+  // work queue (aligned = 2): device memory {ticket, done, 0, 0} followed by the
+  // items; shared by the copies of this plan, freed with the last
+  std::shared_ptr<int4> wq_mem;
+  std::vector<int> layers;  // the queue's z-layer heights, thick first
 };
+
+// Z-layer heights of a work queue of ntiles tiles over n0 planes for G CTAs.
+// Items are taken in order (layer by layer, tile by tile) by whichever CTA is
+// free, so the layers are thick while much work remains and thinner towards the
+// end: each layer about the remaining work per CTA over f, none thinner than
+// hmin (hcap > 0: none thicker than hcap).  Among f in {1, 1.5, 2, 3} and hmin in
+// {8, max(8, 2R)} the one with the shortest predicted makespan wins (list
+// scheduling of the items in order; an item of h planes costs h plus 0.3 per halo
+// plane it streams, 2R of them).
+inline std::vector<int> queue_layers(int n0, int ntiles, int G, int R, int hcap) {
+  auto build = [&](double f, int hmin) {
+    std::vector<int> hs;
+    hmin = std::min(hmin, n0);
+    for (int z = 0; z < n0;) {
+      const int rem = n0 - z;
+      int64_t h = (int64_t)std::ceil((double)rem * ntiles / (f * G));
+      h = std::max<int64_t>(h, hmin);
+      if (hcap > 0) h = std::min<int64_t>(h, std::max(hcap, hmin));
+      h = std::min<int64_t>(h, rem);
+      if (rem - h < hmin) h = rem;
+      hs.push_back((int)h);
+      z += (int)h;
+    }
+    return hs;
+  };
+  auto makespan = [&](const std::vector<int> &hs) {
+    std::priority_queue<double, std::vector<double>, std::greater<double>> free_at;
+    for (int i = 0; i < G; ++i) free_at.push(0.0);
+    double end = 0.0;
+    for (int h : hs)
+      for (int t = 0; t < ntiles; ++t) {
+        const double t1 = free_at.top() + h + 0.3 * 2 * R;
+        free_at.pop();
+        end = std::max(end, t1);
+        free_at.push(t1);
+      }
+    return end;
+  };
+  std::vector<int> best;
+  double best_t = 1e300;
+  for (double f : {1.0, 1.5, 2.0, 3.0})
+    for (int hmin : {8, std::max(8, 2 * R)}) {
+      std::vector<int> hs = build(f, hmin);
+      const double t = makespan(hs);
+      if (t < best_t - 1e-9) {
+        best_t = t;
+        best = hs;
+      }
+    }
+  return best;
+}
 
 using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
 
@@ -1303,8 +1443,10 @@ inline cudaError_t tma_configure(TmaPlan &pl, int ny) {
 
 // The x-pair kernel for rows-per-thread ny.
 template <int R, int EQ, bool ISO>
-inline cudaError_t xp_configure(TmaPlan &pl, int ny) {
-  TmaKernelFn fn = ny == 2 ? k_stencil3d_xp<R, 2, EQ, ISO> : k_stencil3d_xp<R, 4, EQ, ISO>;
+inline cudaError_t xp_configure(TmaPlan &pl, int ny, bool queue) {
+  TmaKernelFn fn = queue ? (ny == 2 ? k_stencil3d_xp<R, 2, EQ, ISO, true>
+                                    : k_stencil3d_xp<R, 4, EQ, ISO, true>)
+                         : (ny == 2 ? k_stencil3d_xp<R, 2, EQ, ISO> : k_stencil3d_xp<R, 4, EQ, ISO>);
   const int smem = xp_smem_bytes(R, ny, EQ == kAcoustic);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
@@ -1351,7 +1493,7 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float 
   const int R = g.R;
   if (ny == 0) ny = tma_ny(R);
   if (!tma_ny_supported(ny) || !tma_tx_supported(tx, eq) || per_sm < 0 || zblock < 0 ||
-      (aligned != 0 && aligned != 1)) {
+      aligned < 0 || aligned > 2 || (aligned == 2 && tx != kXpTX)) {
     *why = "unsupported tile configuration";
     return cudaErrorInvalidValue;
   }
@@ -1400,10 +1542,10 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float 
     break;
 #define XP_CASE(RR)                                                                    \
   case RR:                                                                             \
-    e = ac ? (iso ? xp_configure<RR, kAcoustic, true>(pl, ny)                          \
-                  : xp_configure<RR, kAcoustic, false>(pl, ny))                        \
-           : (iso ? xp_configure<RR, kDiffusion, true>(pl, ny)                         \
-                  : xp_configure<RR, kDiffusion, false>(pl, ny));                      \
+    e = ac ? (iso ? xp_configure<RR, kAcoustic, true>(pl, ny, aligned == 2)            \
+                  : xp_configure<RR, kAcoustic, false>(pl, ny, aligned == 2))          \
+           : (iso ? xp_configure<RR, kDiffusion, true>(pl, ny, aligned == 2)           \
+                  : xp_configure<RR, kDiffusion, false>(pl, ny, aligned == 2));        \
     break;
   if (xp) {
     switch (R) { XP_CASE(1) XP_CASE(2) XP_CASE(3) XP_CASE(4) XP_CASE(5) XP_CASE(6) XP_CASE(7) XP_CASE(8) }
@@ -1432,7 +1574,37 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float 
   pl.args.ntiles = pl.args.tiles_x * tiles_y;
   pl.args.W = (int64_t)pl.args.ntiles * g.n0;
   pl.args.aligned = aligned;
-  if (aligned) {
+  pl.args.items = nullptr;
+  pl.args.nitems = 0;
+  pl.args.wq = nullptr;
+  pl.wq_mem.reset();
+  pl.layers.clear();
+  if (aligned == 2) {
+    // work queue: z-layers (zblock > 0 caps their height), items layer by layer
+    pl.layers = queue_layers(g.n0, pl.args.ntiles, pl.grid, R, zblock);
+    std::vector<int4> h(1, make_int4(0, 0, 0, 0));  // the counters
+    int za = 0;
+    for (int hk : pl.layers) {
+      for (int t = 0; t < pl.args.ntiles; ++t) h.push_back(make_int4(0, t, za, za + hk));
+      za += hk;
+    }
+    int4 *d = nullptr;
+    cudaError_t e2 = cudaMalloc(&d, h.size() * sizeof(int4));
+    if (e2 == cudaSuccess) {
+      pl.wq_mem.reset(d, [](int4 *ptr) { cudaFree(ptr); });
+      e2 = cudaMemcpy(d, h.data(), h.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    }
+    if (e2 != cudaSuccess) {
+      pl.wq_mem.reset();
+      *why = "work queue allocation failed";
+      return e2;
+    }
+    pl.args.wq = reinterpret_cast<unsigned *>(d);
+    pl.args.items = d + 1;
+    pl.args.nitems = (int)(h.size() - 1);
+    pl.args.zblock = zblock;  // the cap as given (0: none); the kernel reads the items
+    if (pl.grid > pl.args.nitems) pl.grid = pl.args.nitems;
+  } else if (aligned) {
     // whole segments: z-blocks of zblock planes (0: as many blocks as make the
     // segments about fill the grid), at most one CTA per segment
     int zb = zblock;

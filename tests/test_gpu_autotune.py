@@ -53,7 +53,7 @@ def _configs(shape, so):
         for ty in (16, 32):
             for cps in (1, 2, 3):
                 for zb in (0, 3, 11, shape[0]):
-                    for al in (0, 1):
+                    for al in (0, 1, 2):
                         for sk in ((0, 1) if so <= 8 else (0,)):
                             try:
                                 s.set_tile_config(tile_y=ty, ctas_per_sm=cps, zblock=zb,
@@ -79,14 +79,35 @@ def test_every_tile_configuration_is_bitwise_the_default(so, shape):
         assert used["tile_y"] == cfg["tile_y"] and used["ctas_per_sm"] == cfg["ctas_per_sm"]
         assert used["tile_x"] == cfg["tile_x"]
         assert used["aligned"] == cfg["aligned"] and used["skip_c"] == cfg["skip_c"]
-        if cfg["zblock"]:
+        if cfg["zblock"] and cfg["aligned"] != 2:
             assert used["zblock"] == min(cfg["zblock"], shape[0])
+        if cfg["aligned"] == 2:  # the queue keeps its cap as given
+            assert used["zblock"] == cfg["zblock"]
         assert np.array_equal(u, ref[0]), cfg
         assert np.array_equal(up, ref[1]), cfg
         assert np.array_equal(rec, ref[2]), cfg
     o = oracle_acoustic(p, 60)
     assert rel_l2(ref[0], o["u"]) <= TOL_WAVE
     assert rel_l2(ref[2], o["rec"]) <= TOL_WAVE
+
+
+@pytest.mark.parametrize("tx,so", [(64, 4), (64, 8), (64, 16)])
+def test_work_queue_with_more_items_than_ctas(tx, so):
+    """aligned = 2 on a grid whose queue holds more items than the grid has CTAs
+    (one CTA per SM), so CTAs take several items in a row; bitwise the default tile
+    and within the tolerance of the oracle; every launch of the run reuses the queue
+    the previous one reset."""
+    shape = (96, 100, 130)
+    p = small_problem(shape, so, nt=40, nrec=21)
+    ref = _acoustic(p, 40)
+    cfg = dict(tile_x=tx, tile_y=16, ctas_per_sm=1, aligned=2)
+    u, up, rec, used = _acoustic(p, 40, cfg)
+    assert used["aligned"] == 2 and used["tile_x"] == tx
+    assert np.array_equal(u, ref[0]) and np.array_equal(up, ref[1])
+    assert np.array_equal(rec, ref[2])
+    o = oracle_acoustic(p, 40)
+    assert rel_l2(u, o["u"]) <= TOL_WAVE
+    assert rel_l2(rec, o["rec"]) <= TOL_WAVE
 
 
 def test_diffusion_tile_configurations_agree():
@@ -96,7 +117,9 @@ def test_diffusion_tile_configurations_agree():
     u0 = rng.standard_normal(shape).astype(np.float32)
     outs = []
     for cfg in (None, dict(tile_y=16), dict(tile_y=32, zblock=5), dict(tile_y=16, ctas_per_sm=1),
-                dict(aligned=1), dict(tile_y=16, zblock=9, aligned=1)):
+                dict(aligned=1), dict(tile_y=16, zblock=9, aligned=1), dict(tile_x=64, aligned=2),
+                dict(tile_x=64, tile_y=16, zblock=9, aligned=2, ctas_per_sm=1),
+                dict(tile_x=64, tile_y=16, aligned=2, ctas_per_sm=1)):
         s = Solver(shape, (1.0 / 40,) * 3, 6, 0.1 * (1.0 / 40) ** 2, "diffusion", kernel="tma")
         if cfg:
             s.set_tile_config(**cfg)
@@ -121,7 +144,8 @@ def test_autotune_picks_a_timed_configuration_and_keeps_the_solution():
     best, tried = s.autotune(reps=3)
     assert len(tried) >= 4
     assert {t["tile_y"] for t in tried} == {16, 32}
-    assert {t["aligned"] for t in tried} == {0, 1}
+    assert {t["aligned"] for t in tried} == {0, 1, 2}
+    assert all(t["tile_x"] == 64 for t in tried if t["aligned"] == 2)
     assert all(t["us_per_step"] > 0 for t in tried)
     key = lambda t: (t["tile_y"], t["zblock"], t["ctas_per_sm"], t["aligned"], t["skip_c"])
     assert {t["skip_c"] for t in tried} == {0, 1}
@@ -150,8 +174,8 @@ def test_bad_tile_configurations_are_rejected_and_keep_the_current_one():
     s = Solver((20, 24, 28), (10.0,) * 3, 8, 0.1, "acoustic", kernel="tma")
     before = s.tile_config
     for bad in (dict(tile_y=24), dict(tile_y=64), dict(zblock=-1), dict(ctas_per_sm=-2),
-                dict(ctas_per_sm=64), dict(aligned=2), dict(skip_c=3), dict(tile_x=48),
-                dict(tile_x=16)):
+                dict(ctas_per_sm=64), dict(aligned=3), dict(skip_c=3), dict(tile_x=48),
+                dict(tile_x=16), dict(aligned=2, tile_x=32)):
         with pytest.raises(FdError) as e:
             s.set_tile_config(**bad)
         assert e.value.status == FD_EINVAL
