@@ -295,8 +295,10 @@ fd_status fd_field_to_dense(fd_ctx *ctx, const float *padded, float *dense);
  *                same arithmetic per point).  fd_step_fwi and batches run 32:
  *                fd_step_fwi refuses a 64-wide configuration (FD_EUNSUPPORTED)
  *                and fd_batch_add puts the member back to the default
- *   tile_y       points per tile along y: 8 consumer warps × rows per thread,
- *                16 or 32
+ *   tile_y       points per tile along y: consumer warps × rows per thread,
+ *                16 (8 × 2) or 32 (8 × 4); with tile_x 64 from space order 8
+ *                also 24 (12 warps × 2 rows: more warps per SM where a
+ *                thread's registers allow only one CTA)
  *   zblock       z-streaming depth: consecutive planes a CTA streams on one
  *                tile before it moves to the next (the work is cut into
  *                z-blocks of this height; each cut costs 2R re-read planes)
@@ -322,7 +324,8 @@ fd_status fd_field_to_dense(fd_ctx *ctx, const float *padded, float *dense);
  *
  * fd_get_tile_config: the configuration fd_run uses; FD_EUNSUPPORTED when the
  *   context runs the plain kernel.
- * fd_set_tile_config: use cfg (tile_x 32 or 0, or 64, tile_y 16 or 32 or 0 for the
+ * fd_set_tile_config: use cfg (tile_x 32 or 0, or 64, tile_y 16, 24 (tile_x 64, space
+ *   order ≥ 8) or 32, or 0 for the
  *   default, zblock ≥ 0 with 0 meaning one CTA's share (aligned = 0) or the
  *   height that makes about as many segments as CTAs (aligned = 1) or no cap
  *   on the layer height (aligned = 2), ctas_per_sm ≥ 0 with 0 meaning as many
@@ -331,7 +334,7 @@ fd_status fd_field_to_dense(fd_ctx *ctx, const float *padded, float *dense);
  *   place.  Captured graphs are dropped.
  * fd_autotune: time every configuration of the search space (tile_x in {32, 64}
  *   (32 only for fd_autotune_fwi) × tile_y in
- *   {16, 32} × ctas_per_sm in 1..fit × (aligned 0 with zblock in {share/2,
+ *   {16, 24, 32} × ctas_per_sm in 1..fit × (aligned 0 with zblock in {share/2,
  *   share, 2·share} | aligned 1 with m or 2m z-blocks, m = CTAs / tiles |
  *   aligned 2 with uncapped layers for tile_x 64)
  *   × skip_c {0, 1} where it applies (once a model is set),

@@ -1844,7 +1844,8 @@ fd_status autotune_impl(fd_ctx *c, int reps, fd_tile_config *best, fd_tile_confi
   const std::vector<int> widths =
       fwi ? std::vector<int>{kTmaTX} : std::vector<int>{kTmaTX, kXpTX};
   for (int tx : widths)
-  for (int ny : {2, 4}) {
+  for (int ny : {2, 3, 4}) {
+    if (ny == 3 && (tx != kXpTX || !xp_hc_supported(R, 3))) continue;  // 24 rows: x-pair only
     TmaPlan p{};
     const char *why = nullptr;
     if (st || plan_tma(p, c->g, eq, c->iso, c->u, c->A, c->C, ny, 0, 0, 0, &why, tx,

@@ -865,6 +865,15 @@ __host__ __device__ constexpr int xp_smem_bytes(int R, int NY, bool acoustic) {
 }
 // the queue holds 2·NY·(2R+1) floats a thread
 __host__ __device__ constexpr int xp_minb(int R, int NY) { return tma_minb(R, 2 * NY); }
+// Tile heights of the x-pair kernel, by height code hc = tile_y / 8 (the host's
+// "ny"): 16 rows = 8 consumer warps × 2 rows, 32 = 8 × 4, and 24 = 12 warps × 2
+// rows (radius 4 and up: more warps to hide latency where a thread's registers
+// allow only one CTA per SM).  The size helpers above take hc.
+__host__ __device__ constexpr int xp_nw(int hc) { return hc == 3 ? 12 : kTmaNW; }
+__host__ __device__ constexpr int xp_rows(int hc) { return hc == 3 ? 2 : hc; }
+__host__ __device__ constexpr bool xp_hc_supported(int R, int hc) {
+  return hc == 2 || hc == 4 || (hc == 3 && R >= 4);
+}
 
 // Source corners at plane zc of this tile for the lane's x pair: vx holds rows
 // 0..3 at x, vy rows 0..3 at x + 1 (see source_hits).
@@ -921,8 +930,8 @@ __device__ __noinline__ SourceHitsXp source_hits_xp_call(const int4 *entries,
                         nstep, vx, vy);
 }
 
-template <int R, int NY, int EQ, bool ISO, bool QUEUE = false>
-__global__ void __launch_bounds__(kTmaThreads, xp_minb(R, NY))
+template <int R, int NY, int EQ, bool ISO, bool QUEUE = false, int NW = kTmaNW>
+__global__ void __launch_bounds__((NW + 1) * 32, xp_minb(R, NY))
 k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXpTX + 2·HXB wide)
                const __grid_constant__ CUtensorMap map_p,  // u^{n-1}, tile box (kXpTX wide)
                const __grid_constant__ CUtensorMap map_a,  // A, tile box
@@ -930,9 +939,11 @@ k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXp
                const __grid_constant__ CUtensorMap, const __grid_constant__ CUtensorMap,
                const TmaArgs args, const BatchArgs) {
   constexpr bool AC = EQ == kAcoustic;
-  constexpr int TY = tma_ty(NY);
-  constexpr int HXB = tma_hxb(R), BW = xp_bw(R), DU = tma_du(R, AC, xp_ubytes(R, NY)), DX = kTmaDX;
-  constexpr int USLOT = tma_align128(xp_ubytes(R, NY)) / 4;  // floats per ring-U slot
+  constexpr int HC = NW * NY / kTmaNW;                       // height code (tile_y / 8)
+  static_assert(NW * NY % kTmaNW == 0 && xp_nw(HC) == NW && xp_rows(HC) == NY, "tile shape");
+  constexpr int TY = tma_ty(HC);                               // NW·NY rows
+  constexpr int HXB = tma_hxb(R), BW = xp_bw(R), DU = tma_du(R, AC, xp_ubytes(R, HC)), DX = kTmaDX;
+  constexpr int USLOT = tma_align128(xp_ubytes(R, HC)) / 4;  // floats per ring-U slot
   constexpr int XT = kXpTX * TY;                              // floats per ring-X tile
   constexpr int Q = 2 * R + 1;
   constexpr int U = tma_unroll(R);
@@ -959,11 +970,11 @@ k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXp
   if (threadIdx.x == 0) {
     for (int i = 0; i < DU; ++i) {
       mbar_init(&full_u[i], 1);
-      mbar_init(&empty_u[i], kTmaNW);
+      mbar_init(&empty_u[i], NW);
     }
     for (int i = 0; i < DX; ++i) {
       mbar_init(&full_x[i], 1);
-      mbar_init(&empty_x[i], kTmaNW);
+      mbar_init(&empty_x[i], NW);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -981,7 +992,7 @@ k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXp
   }
   const unsigned char *ucf = kUnitC ? args.unit_c : nullptr;
 
-  if (warp == kTmaNW) {
+  if (warp == NW) {
     // ------------------------------- producer -------------------------------
     if (lane == 0) {
       tma_prefetch_desc(&map_u);
@@ -1047,7 +1058,7 @@ k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXp
             ok = false;
             break;
           }
-          mbar_expect_tx(&full_u[slot], xp_ubytes(R, NY));
+          mbar_expect_tx(&full_u[slot], xp_ubytes(R, HC));
           tma_load_3d_hint(ring_u + slot * USLOT, &map_u, x0 - HXB + args.org.ox,
                            y0 - R + args.org.oy, p + args.org.oz, &full_u[slot], keep);
           ++su;
@@ -1304,6 +1315,7 @@ struct TmaPlan {
   TmaKernelFn fn_multi = nullptr;  // batches (default tile height only)
   TmaKernelFn fn_fwi = nullptr;    // one shot with the FWI epilogue (acoustic)
   int grid = 0, smem = 0;
+  int threads = kTmaThreads;  // of fn: (consumer warps + 1) × 32
   int grid_multi = 0, smem_multi = 0;
   int ny = 0;          // rows per consumer thread
   int per_sm = 0;      // resident CTAs per SM the persistent grid is sized for
@@ -1418,6 +1430,7 @@ inline cudaError_t tma_instance(TmaKernelFn &fn, int &smem, int &per_sm) {
 template <int R, int EQ, bool ISO>
 inline cudaError_t tma_configure(TmaPlan &pl, int ny) {
   constexpr int NYD = tma_ny(R);
+  pl.threads = kTmaThreads;
   cudaError_t e = ny == 2 ? tma_instance<R, 2, EQ, ISO, false>(pl.fn, pl.smem, pl.per_sm_max)
                           : tma_instance<R, 4, EQ, ISO, false>(pl.fn, pl.smem, pl.per_sm_max);
   if (e != cudaSuccess) return e;
@@ -1444,17 +1457,27 @@ inline cudaError_t tma_configure(TmaPlan &pl, int ny) {
 // The x-pair kernel for rows-per-thread ny.
 template <int R, int EQ, bool ISO>
 inline cudaError_t xp_configure(TmaPlan &pl, int ny, bool queue) {
-  TmaKernelFn fn = queue ? (ny == 2 ? k_stencil3d_xp<R, 2, EQ, ISO, true>
-                                    : k_stencil3d_xp<R, 4, EQ, ISO, true>)
-                         : (ny == 2 ? k_stencil3d_xp<R, 2, EQ, ISO> : k_stencil3d_xp<R, 4, EQ, ISO>);
+  // ny is the height code: 2 → 8 warps × 2 rows, 3 → 12 × 2 (radius 4 and up), 4 → 8 × 4
+  TmaKernelFn fn = nullptr;
+  if (ny == 2)
+    fn = queue ? k_stencil3d_xp<R, 2, EQ, ISO, true> : k_stencil3d_xp<R, 2, EQ, ISO>;
+  else if (ny == 4)
+    fn = queue ? k_stencil3d_xp<R, 4, EQ, ISO, true> : k_stencil3d_xp<R, 4, EQ, ISO>;
+  else if constexpr (xp_hc_supported(R, 3)) {
+    if (ny == 3)
+      fn = queue ? k_stencil3d_xp<R, 2, EQ, ISO, true, 12> : k_stencil3d_xp<R, 2, EQ, ISO, false, 12>;
+  }
+  if (!fn) return cudaErrorInvalidValue;
+  const int threads = (xp_nw(ny) + 1) * 32;
   const int smem = xp_smem_bytes(R, ny, EQ == kAcoustic);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl.per_sm_max, fn, kTmaThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl.per_sm_max, fn, threads, smem);
   if (e == cudaSuccess && pl.per_sm_max < 1) e = cudaErrorInvalidConfiguration;
   if (e != cudaSuccess) return e;
   pl.fn = fn;
   pl.smem = smem;
+  pl.threads = threads;
   pl.fn_multi = nullptr;
   pl.fn_fwi = nullptr;
   pl.smem_multi = 0;
@@ -1467,7 +1490,7 @@ inline cudaError_t xp_configure(TmaPlan &pl, int ny, bool queue) {
 }
 
 // Tile configurations the pipelined kernel offers (the autotuner's space).
-inline bool tma_ny_supported(int ny) { return ny == 2 || ny == 4; }
+inline bool tma_ny_supported(int ny) { return ny == 2 || ny == 3 || ny == 4; }
 inline bool tma_tx_supported(int tx, int) { return tx == kTmaTX || tx == kXpTX; }
 
 // Build the plan: tensor maps for both levels and the coefficient fields, for
@@ -1493,7 +1516,8 @@ inline cudaError_t plan_tma(TmaPlan &pl, const Geom &g, int eq, bool iso, float 
   const int R = g.R;
   if (ny == 0) ny = tma_ny(R);
   if (!tma_ny_supported(ny) || !tma_tx_supported(tx, eq) || per_sm < 0 || zblock < 0 ||
-      aligned < 0 || aligned > 2 || (aligned == 2 && tx != kXpTX)) {
+      aligned < 0 || aligned > 2 || (aligned == 2 && tx != kXpTX) ||
+      (ny == 3 && (tx != kXpTX || !xp_hc_supported(R, 3)))) {
     *why = "unsupported tile configuration";
     return cudaErrorInvalidValue;
   }
@@ -1638,7 +1662,7 @@ inline cudaError_t launch_tma_step(const TmaPlan &pl, int cur, float *out, const
   a.err = err;
   a.sp = sp;
   a.unit_c = unit_c;
-  pl.fn<<<pl.grid, kTmaThreads, pl.smem, s>>>(pl.map_u[cur], pl.map_t[cur ^ 1], pl.map_a,
+  pl.fn<<<pl.grid, pl.threads, pl.smem, s>>>(pl.map_u[cur], pl.map_t[cur ^ 1], pl.map_a,
                                               pl.map_c, pl.map_c, pl.map_c, a, BatchArgs{});
   return cudaGetLastError();
 }

@@ -50,7 +50,7 @@ def _configs(shape, so):
     out = []
     s = Solver(shape, (10.0,) * 3, so, 0.1, "acoustic", kernel="tma")
     for tx in (32, 64):
-        for ty in (16, 32):
+        for ty in (16, 24, 32):
             for cps in (1, 2, 3):
                 for zb in (0, 3, 11, shape[0]):
                     for al in (0, 1, 2):
@@ -72,7 +72,9 @@ def test_every_tile_configuration_is_bitwise_the_default(so, shape):
     ref = _acoustic(p, 60)
     cfgs = _configs(shape, so)
     heights = {c["tile_y"] for c in cfgs}
-    assert heights == {16, 32}, cfgs
+    # 24 rows: 12 consumer warps of the x-pair kernel, from space order 8
+    assert heights == ({16, 24, 32} if so >= 8 else {16, 32}), cfgs
+    assert all(c["tile_x"] == 64 for c in cfgs if c["tile_y"] == 24)
     assert {c["tile_x"] for c in cfgs} == {32, 64}, cfgs
     for cfg in cfgs:
         u, up, rec, used = _acoustic(p, 60, cfg)
@@ -91,8 +93,8 @@ def test_every_tile_configuration_is_bitwise_the_default(so, shape):
     assert rel_l2(ref[2], o["rec"]) <= TOL_WAVE
 
 
-@pytest.mark.parametrize("tx,so", [(64, 4), (64, 8), (64, 16)])
-def test_work_queue_with_more_items_than_ctas(tx, so):
+@pytest.mark.parametrize("tx,ty,so", [(64, 16, 4), (64, 16, 8), (64, 16, 16), (64, 24, 16)])
+def test_work_queue_with_more_items_than_ctas(tx, ty, so):
     """aligned = 2 on a grid whose queue holds more items than the grid has CTAs
     (one CTA per SM), so CTAs take several items in a row; bitwise the default tile
     and within the tolerance of the oracle; every launch of the run reuses the queue
@@ -100,14 +102,37 @@ def test_work_queue_with_more_items_than_ctas(tx, so):
     shape = (96, 100, 130)
     p = small_problem(shape, so, nt=40, nrec=21)
     ref = _acoustic(p, 40)
-    cfg = dict(tile_x=tx, tile_y=16, ctas_per_sm=1, aligned=2)
+    cfg = dict(tile_x=tx, tile_y=ty, ctas_per_sm=1, aligned=2)
     u, up, rec, used = _acoustic(p, 40, cfg)
-    assert used["aligned"] == 2 and used["tile_x"] == tx
+    assert used["aligned"] == 2 and used["tile_x"] == tx and used["tile_y"] == ty
     assert np.array_equal(u, ref[0]) and np.array_equal(up, ref[1])
     assert np.array_equal(rec, ref[2])
     o = oracle_acoustic(p, 40)
     assert rel_l2(u, o["u"]) <= TOL_WAVE
     assert rel_l2(rec, o["rec"]) <= TOL_WAVE
+
+
+@pytest.mark.parametrize("so", (8, 16))
+def test_diffusion_24_row_tiles_agree(so):
+    """12 consumer warps (24-row x-pair tiles), static split and work queue, bitwise
+    the default tile on a ragged diffusion grid."""
+    from paper_1906_10811_b300 import Solver
+    rng = np.random.default_rng(so)
+    shape = (40, 61, 150)
+    u0 = rng.standard_normal(shape).astype(np.float32)
+    outs = []
+    for cfg in (None, dict(tile_x=64, tile_y=24), dict(tile_x=64, tile_y=24, aligned=1),
+                dict(tile_x=64, tile_y=24, aligned=2, ctas_per_sm=1)):
+        s = Solver(shape, (1.0 / 60,) * 3, so, 0.05 * (1.0 / 60) ** 2, "diffusion", kernel="tma")
+        if cfg:
+            s.set_tile_config(**cfg)
+            assert s.tile_config["tile_y"] == 24
+        s.set_field(u0)
+        s.run(15)
+        outs.append(s.read()[0])
+        s.close()
+    for u in outs[1:]:
+        assert np.array_equal(u, outs[0])
 
 
 def test_diffusion_tile_configurations_agree():
@@ -143,7 +168,7 @@ def test_autotune_picks_a_timed_configuration_and_keeps_the_solution():
     s.set_model(p["m"], p["damp"])
     best, tried = s.autotune(reps=3)
     assert len(tried) >= 4
-    assert {t["tile_y"] for t in tried} == {16, 32}
+    assert {t["tile_y"] for t in tried} == {16, 24, 32}
     assert {t["aligned"] for t in tried} == {0, 1, 2}
     assert all(t["tile_x"] == 64 for t in tried if t["aligned"] == 2)
     assert all(t["us_per_step"] > 0 for t in tried)
