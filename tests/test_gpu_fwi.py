@@ -244,8 +244,12 @@ def test_run_fwi_sequence_is_bitwise_the_single_steps(reverse):
     p = _shot(shape=(26, 30, 41), nt=160)        # wavelet long enough for 10 + 2 × 70 steps
     nt = 70
     out = []
+    # one stream for the library calls and the torch ops that fill their buffers (the
+    # binding calls below do not order a private solver stream with torch's)
+    work = torch.cuda.Stream()
     for seq in (False, True):
-        with Solver(p["shape"], p["spacing"], 8, p["dt"], "acoustic", device=True) as s:
+        with torch.cuda.stream(work), \
+                Solver(p["shape"], p["spacing"], 8, p["dt"], "acoustic", device=True) as s:
             dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
             s.set_model(dev(p["m"]), dev(p["damp"]))
             s.set_sources(dev(p["src_coords"]), dev(p["wavelet"]))
@@ -280,7 +284,9 @@ def test_residual_misfit_and_adjoint_wavelet():
     from paper_1906_10811_b300 import binding as B
     p = _shot(shape=(24, 28, 30), nt=77, nrec=37)
     rng = np.random.default_rng(8)
-    with Solver(p["shape"], p["spacing"], 8, p["dt"], "acoustic", device=True) as s:
+    work = torch.cuda.Stream()  # the library and the torch ops on one stream (as above)
+    with torch.cuda.stream(work), \
+            Solver(p["shape"], p["spacing"], 8, p["dt"], "acoustic", device=True) as s:
         dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
         s.set_model(dev(p["m"]), dev(p["damp"]))
         s.set_sources(dev(p["src_coords"]), dev(p["wavelet"]))
@@ -294,8 +300,9 @@ def test_residual_misfit_and_adjoint_wavelet():
         wav = torch.full((77, 37), float("nan"), device="cuda")
         J = B.fd_residual(s.ctx, d_obs, wav)
         J2 = B.fd_residual(s.ctx, d_obs)                  # no wavelet: J only, same value
-    r = (rec - d_obs).cpu().numpy()                       # float32 subtraction, as recorded
-    assert np.array_equal(wav.cpu().numpy(), r[1:][::-1])
+        r = (rec - d_obs).cpu().numpy()                   # float32 subtraction, as recorded
+        wav_h = wav.cpu().numpy()
+    assert np.array_equal(wav_h, r[1:][::-1])
     Jref = 0.5 * float(np.sum(r.astype(np.float64) ** 2))
     assert J == J2
     assert abs(J - Jref) <= 1e-12 * Jref
