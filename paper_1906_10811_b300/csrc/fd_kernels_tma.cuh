@@ -931,7 +931,7 @@ __device__ __noinline__ SourceHitsXp source_hits_xp_call(const int4 *entries,
 }
 
 template <int R, int NY, int EQ, bool ISO, bool QUEUE = false, int NW = kTmaNW>
-__global__ void __launch_bounds__((NW + 1) * 32, xp_minb(R, NY))
+__global__ void __launch_bounds__((NW + 1) * 32, NW == kTmaNW ? xp_minb(R, NY) : 1)
 k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXpTX + 2·HXB wide)
                const __grid_constant__ CUtensorMap map_p,  // u^{n-1}, tile box (kXpTX wide)
                const __grid_constant__ CUtensorMap map_a,  // A, tile box
