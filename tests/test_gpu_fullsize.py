@@ -9,8 +9,11 @@
   box the test runs on.
 * 512³ at so 4/8/12/16: one step from random fields, checked on sampled points
   (random, grid corners, tile and z-block seams) against the oracle evaluated
-  point by point on (2R+1)³ windows; and 20 steps at so 8 and 16 against the
-  oracle on the whole grid.
+  point by point on (2R+1)³ windows, with the default tile and with the tile the
+  autotuner picks (the bench's sweep configuration: on the B300 the x-pair work
+  queue, 24-row tiles at so 12/16); 20 steps at so 8 and 16 against the oracle on
+  the whole grid, the tuned tile bitwise the default one; the 512³ diffusion step
+  (so 4/8/16, tuned tile) on sampled points.
 """
 
 import numpy as np
@@ -148,14 +151,85 @@ def test_one_step_512_sampled(so):
 
 @pytest.mark.parametrize("so", (8, 16))
 def test_twenty_steps_512_whole_grid(so):
+    """The default tile and the autotuned one (the bench's sweep configuration):
+    bitwise the same, and within the tolerance of the oracle on the whole grid."""
     from paper_1906_10811_b300 import Solver
     m, damp, dt, u, up = _model_512(so)
-    with Solver((512,) * 3, (10.0,) * 3, so, dt, "acoustic") as s:
-        s.set_model(m, damp)
-        s.set_field(u, up)
-        s.run(20)
-        g, _ = s.read()
-        gp = s.read_prev()
+    runs = []
+    for tune in (False, True):
+        with Solver((512,) * 3, (10.0,) * 3, so, dt, "acoustic") as s:
+            s.set_model(m, damp)
+            if tune:
+                s.autotune(reps=2)
+            s.set_field(u, up)
+            s.run(20)
+            g, _ = s.read()
+            runs.append((g, s.read_prev(), s.tile_config))
+    (g, gp, _), (gt, gpt, used) = runs
+    assert np.array_equal(g, gt) and np.array_equal(gp, gpt), used
     ou, oup, _ = oracle.acoustic(m, dt, (10.0,) * 3, so, 20, damp=damp, u_cur=u, u_prev=up)
     assert rel_l2(g, ou) <= TOL_WAVE
     assert rel_l2(gp, oup) <= TOL_WAVE
+
+
+# ---------------------------------------------------------------------------
+# 512³ in the configurations the bench's sweep runs: the autotuner picks the tile
+# (on the B300: the x-pair kernel's work queue, 24-row tiles of 12 consumer warps
+# at so 12 and 16), then one step is checked on sampled points.
+
+@pytest.mark.parametrize("so", (4, 8, 12, 16))
+def test_one_step_512_sampled_tuned_tile(so):
+    from paper_1906_10811_b300 import Solver
+    R = so // 2
+    m, damp, dt, u, up = _model_512(so)
+    with Solver((512,) * 3, (10.0,) * 3, so, dt, "acoustic") as s:
+        s.set_model(m, damp)
+        s.autotune(reps=2)
+        used = s.tile_config
+        s.set_field(u, up)
+        s.run(1)
+        g, _ = s.read()
+    rng = np.random.default_rng(200 + so)
+    got, ref = [], []
+    for p in _sample_points(512, R, rng):
+        mw = np.ones((2 * R + 1,) * 3)
+        dw = np.zeros((2 * R + 1,) * 3)
+        mw[R, R, R] = m[p]
+        dw[R, R, R] = damp[p]
+        o, _, _ = oracle.acoustic(mw, dt, (10.0,) * 3, so, 1, damp=dw,
+                                  u_cur=_window(u, p, R, 0.0), u_prev=_window(up, p, R, 0.0))
+        got.append(g[p])
+        ref.append(o[R, R, R])
+    got, ref = np.array(got, np.float64), np.array(ref)
+    assert rel_l2(got, ref) <= 1e-5, used
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max(), used
+
+
+@pytest.mark.parametrize("so", (4, 8, 16))
+def test_diffusion_one_step_512_sampled_tuned_tile(so):
+    """The 512³ diffusion sweep's step (ν dt/h² = 0.05) from a random field, tile
+    autotuned: sampled interior points against the oracle on (2R+1)³ windows, boundary
+    nodes unchanged."""
+    from paper_1906_10811_b300 import Solver
+    R, n = so // 2, 512
+    h = 1.0 / (n - 1)
+    nu, dt = 0.5, 0.05 * h * h / 0.5
+    u = fdsynth.random_field((n,) * 3, seed=300 + so)
+    with Solver((n,) * 3, (h,) * 3, so, dt, "diffusion", nu=nu) as s:
+        s.autotune(reps=2)
+        used = s.tile_config
+        s.set_field(u)
+        s.run(1)
+        g, _ = s.read()
+    rng = np.random.default_rng(400 + so)
+    got, ref = [], []
+    for p in _sample_points(n, R, rng):
+        if min(p) == 0 or max(p) == n - 1:   # boundary node: held
+            assert g[p] == u[p], (p, used)
+            continue
+        o = oracle.diffusion(_window(u, p, R, 0.0), (h,) * 3, so, nu, dt, 1)
+        got.append(g[p])
+        ref.append(o[R, R, R])
+    got, ref = np.array(got, np.float64), np.array(ref)
+    assert rel_l2(got, ref) <= 1e-5, used
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max(), used
