@@ -1083,7 +1083,15 @@ k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXp
 
   // --------------------------------- consumers --------------------------------
   float2 qp[NY][QL];  // queue: row j, the lane's x pair
-  uint32_t su = 0, sx = 0;
+  // ring-U position of the next fill to consume: slot and phase parity, kept
+  // incrementally (DU is not a power of two; no division per plane)
+  uint32_t uslot = 0, upar = 0, sx = 0;
+  auto next_u = [&]() {
+    if (++uslot == (uint32_t)DU) {
+      uslot = 0;
+      upar ^= 1u;
+    }
+  };
   const int row0 = warp * NY;
   const float2 *wp0 = args.c.wp[0], *wp1 = args.c.wp[1], *wp2 = args.c.wp[2];
   const Geom g = args.g;
@@ -1096,7 +1104,7 @@ k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXp
     int tile, za, zb;
     if constexpr (QUEUE) {
       // the next item is published with the first fill of its planes
-      if (!mbar_wait(&full_u[su % DU], (su / DU) & 1)) goto timeout;
+      if (!mbar_wait(&full_u[uslot], upar)) goto timeout;
       const int4 item = make_int4(item_ring[nitem % kItemRing].x, item_ring[nitem % kItemRing].y,
                                   item_ring[nitem % kItemRing].z, item_ring[nitem % kItemRing].w);
       ++nitem;
@@ -1132,8 +1140,8 @@ k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXp
 #pragma unroll
     for (int m = 0; m < 2 * R; ++m) {
       const int p = za - R + m;
-      const uint32_t slot = su % DU;
-      if (!mbar_wait(&full_u[slot], (su / DU) & 1)) goto timeout;
+      const uint32_t slot = uslot;
+      if (!mbar_wait(&full_u[slot], upar)) goto timeout;
       const float *pl = ring_u + slot * USLOT + (R + row0) * BW + HXB + 2 * lane;
 #pragma unroll
       for (int j = 0; j < NY; ++j) qp[j][m] = *reinterpret_cast<const float2 *>(pl + j * BW);
@@ -1141,7 +1149,7 @@ k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXp
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty_u[slot]);
       }
-      ++su;
+      next_u();
     }
     {
       const int nseg = zb - za;
@@ -1152,13 +1160,14 @@ k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXp
           if (i >= nseg) goto segment_done;
           {
             const int zc = za + i;
-            const uint32_t slot = su % DU;
-            if (!mbar_wait(&full_u[slot], (su / DU) & 1)) goto timeout;
+            const uint32_t slot = uslot;
+            if (!mbar_wait(&full_u[slot], upar)) goto timeout;
             const float *pl = ring_u + slot * USLOT + (R + row0) * BW + HXB + 2 * lane;
 #pragma unroll
             for (int j = 0; j < NY; ++j)
               qp[j][tma_qslot<U, Q>(ph, 2 * R)] = *reinterpret_cast<const float2 *>(pl + j * BW);
-            const uint32_t cs = (su - R) % DU;  // ring-U slot holding plane zc
+            // ring-U slot holding plane zc, R fills back (at least 2R fills consumed)
+            const uint32_t cs = slot >= (uint32_t)R ? slot - R : slot + DU - R;
             const float *cp = ring_u + cs * USLOT + row0 * BW + HXB + 2 * lane;
             const float *xs = nullptr;
             uint32_t xslot = 0;
@@ -1276,7 +1285,7 @@ k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXp
               if (zc + R >= zb) mbar_arrive(&empty_u[slot]);  // trailing plane: queue only
             }
             if (AC) ++sx;
-            ++su;
+            next_u();
             ++i;
           }
         }
