@@ -1178,8 +1178,12 @@ k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXp
             }
             const bool cone = kUnitC && ucf && ucf[(int64_t)tile * n0 + zc];
             float2 ycol[NY + 2 * R];  // the lane's pair, rows row0-R .. row0+NY-1+R
+            // the thread's own rows of plane zc are in its z-queue already (loaded
+            // from the same shared-memory words): only the 2R halo rows are read
 #pragma unroll
-            for (int r = 0; r < NY + 2 * R; ++r) ycol[r] = *reinterpret_cast<const float2 *>(cp + r * BW);
+            for (int r = 0; r < NY + 2 * R; ++r)
+              ycol[r] = (r >= R && r < R + NY) ? qp[r - R][tma_qslot<U, Q>(ph, R)]
+                                               : *reinterpret_cast<const float2 *>(cp + r * BW);
             float2 val[NY];
 #pragma unroll
             for (int j = 0; j < NY; ++j) {
