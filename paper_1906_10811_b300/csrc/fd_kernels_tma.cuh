@@ -678,8 +678,17 @@ k_stencil3d_tma(const __grid_constant__ CUtensorMap map_u,   // u^n, halo box
             }
             const bool cone = kUnitC && ucf && ucf[(int64_t)tile * n0 + zc];
             float ycol[NY + 2 * R];  // this thread's column, rows row0-R .. row0+NY-1+R
+            // the thread's own rows of plane zc are in its z-queue already (loaded
+            // from the same shared-memory words): only the 2R halo rows are read
 #pragma unroll
-            for (int r = 0; r < NY + 2 * R; ++r) ycol[r] = cp[r * BW];
+            for (int r = 0; r < NY + 2 * R; ++r) {
+              if (r >= R && r < R + NY) {
+                const float2 q2 = qp[(r - R) >> 1][tma_qslot<U, Q>(ph, R)];
+                ycol[r] = ((r - R) & 1) ? q2.y : q2.x;
+              } else {
+                ycol[r] = cp[r * BW];
+              }
+            }
             float val[NY];
             // y-neighbours at ±k of the row pair (j, j+1).  Where R + j + k is even
             // the operands are the column's aligned register pairs and one packed
