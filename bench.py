@@ -64,13 +64,12 @@ WORKLOADS = {
 # are summarised in profiles/.  Absent (null) when not captured for the kernel
 # and tile configuration as they are now.
 NCU_TRAFFIC = {
-    # profiles/stencil3d_xp_acoustic256_so8.md ("interior tensor maps"): the x-pair kernel
-    # (64 x 32 tiles, 1 CTA/SM), L2 not flushed between launches (the bench's conditions):
-    # mean of 3 launches, read 261.36 MB + write 68.56 MB
-    ("stencil3d_xp_acoustic", "acoustic256", 8, 64, 32, 64, 1, 1, 0): 329.92e6,
-    # profiles/stencil3d_tma_acoustic256_so8.md ("interior tensor maps"): the 32-wide kernel
-    # (32 x 32 tiles, 2 CTAs/SM), same conditions: read 259.39 MB + write 66.86 MB
-    ("stencil3d_tma_acoustic", "acoustic256", 8, 32, 32, 64, 2, 1, 0): 326.25e6,
+    # profiles/stencil3d_tma_acoustic256_so8.md ("Warm-L2 DRAM traffic"): the 32-wide kernel
+    # (32 x 32 tiles, 2 CTAs/SM, 64-plane segments), L2 not flushed between launches (the
+    # bench's conditions): mean of 3 launches, read 260.47 MB + write 68.50 MB
+    ("stencil3d_tma_acoustic", "acoustic256", 8, 32, 32, 64, 2, 1, 0): 328.97e6,
+    # same section, the x-pair kernel (64 x 32 tiles, 1 CTA/SM): read 260.04 MB + write 66.80 MB
+    ("stencil3d_xp_acoustic", "acoustic256", 8, 64, 32, 64, 1, 1, 0): 326.84e6,
 }
 
 
