@@ -92,9 +92,12 @@ __host__ __device__ constexpr int s2_hx(int R) { return (R + 3) / 4 * 4; }  // x
 __host__ __device__ constexpr int s2_rw(int R) { return kS2W + 2 * s2_hx(R); }  // staged row (floats)
 // ring rows per warp: a multiple of the queue length 2R+1 (an unrolled group of that
 // many rows then addresses ring and queue slots statically) holding the R rows back
-// to the one being updated, the row in use and about 8 rows in flight
+// to the one being updated, the row in use and about 8 rows in flight.  Above radius
+// 4 one queue length: the loop is unrolled over the ring, and two queue lengths of a
+// radius-8 body overflowed the instruction cache ("no instruction" the top stall);
+// there the step is compute-bound and 4-7 rows in flight are enough
 __host__ __device__ constexpr int s2_nr(int R) {
-  return (2 * R + 1) * ((R + 2 + 8 + 2 * R) / (2 * R + 1));
+  return R > 4 ? 2 * R + 1 : (2 * R + 1) * ((R + 2 + 8 + 2 * R) / (2 * R + 1));
 }
 __host__ __device__ constexpr int s2_d(int R) {  // rows in flight
   return s2_nr(R) - R - 2 < 10 ? s2_nr(R) - R - 2 : 10;
