@@ -105,9 +105,13 @@ def test_slabs_on_separate_streams_chunked_and_with_x_pair_tiles():
     ref_u, ref_rec = _whole(p, nt)
     u, rec, _ = _slabs(p, nt, 3, streams="separate", chunks=[1, 17, 42])
     assert np.array_equal(u, ref_u) and np.array_equal(rec, ref_rec)
-    tile = dict(tile_x=64, tile_y=16, aligned=1)
-    u, rec, _ = _slabs(p, nt, 3, tile=tile)
-    assert np.array_equal(u, ref_u) and np.array_equal(rec, ref_rec)
+    # x-pair tiles with a static split, with the work queue, and 24-row tiles (12
+    # consumer warps) with the queue: each slab plans its own queue over its planes
+    for tile in (dict(tile_x=64, tile_y=16, aligned=1),
+                 dict(tile_x=64, tile_y=16, aligned=2, ctas_per_sm=1),
+                 dict(tile_x=64, tile_y=24, aligned=2)):
+        u, rec, _ = _slabs(p, nt, 3, tile=tile)
+        assert np.array_equal(u, ref_u) and np.array_equal(rec, ref_rec), tile
 
 
 def test_halo_export_import_is_the_copy_between_slabs():
