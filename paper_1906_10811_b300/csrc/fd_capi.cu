@@ -667,12 +667,15 @@ void select_kernel(fd_ctx *c) {
   const int R = c->so / 2;
   const bool three = c->ndim == 3;
   const bool ac = c->eq == FD_ACOUSTIC;
+  const bool iso2 = !three && c->coef.iso2;
 #define PICK(RR)                                                                       \
   case RR:                                                                             \
     c->plain_fn = three ? (ac ? k_stencil_plain<RR, kAcoustic, true>                   \
                               : k_stencil_plain<RR, kDiffusion, true>)                 \
-                        : (ac ? k_stencil_plain<RR, kAcoustic, false>                  \
-                              : k_stencil_plain<RR, kDiffusion, false>);               \
+                  : iso2 ? (ac ? k_stencil_plain<RR, kAcoustic, false, true>           \
+                               : k_stencil_plain<RR, kDiffusion, false, true>)         \
+                         : (ac ? k_stencil_plain<RR, kAcoustic, false>                 \
+                               : k_stencil_plain<RR, kDiffusion, false>);              \
     break;
   switch (R) {
     PICK(1) PICK(2) PICK(3) PICK(4) PICK(5) PICK(6) PICK(7) PICK(8)
@@ -696,10 +699,11 @@ void select_kernel(fd_ctx *c) {
     if (want) {
 #define PICK2(RR)                                                                      \
   case RR:                                                                             \
-    c->stream2d_fn = ac ? k_stencil2d_stream<RR, kAcoustic> : k_stencil2d_stream<RR, kDiffusion>; \
-    cudaFuncSetAttribute(k_stencil2d_stream<RR, kAcoustic>,                            \
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, s2_smem(RR));    \
-    cudaFuncSetAttribute(k_stencil2d_stream<RR, kDiffusion>,                           \
+    c->stream2d_fn = iso2 ? (ac ? k_stencil2d_stream<RR, kAcoustic, true>              \
+                                : k_stencil2d_stream<RR, kDiffusion, true>)            \
+                          : (ac ? k_stencil2d_stream<RR, kAcoustic>                    \
+                                : k_stencil2d_stream<RR, kDiffusion>);                 \
+    cudaFuncSetAttribute((const void *)c->stream2d_fn,                                 \
                          cudaFuncAttributeMaxDynamicSharedMemorySize, s2_smem(RR));    \
     break;
       switch (R) {
@@ -926,6 +930,8 @@ fd_status fd_create(fd_ctx **out, int ndim, const int64_t *shape, const double *
       c->coef.wp[ax][k] = make_float2(c->coef.w[ax][k], c->coef.w[ax][k]);
     }
   }
+  // 2-D with equal spacing: the 2-D kernels take one weight per offset (plain_lap)
+  c->coef.iso2 = ndim == 2 && spacing[0] == spacing[1] ? 1 : 0;
   select_kernel(c);
 
   auto bail = [&](fd_status st) {
@@ -2522,10 +2528,12 @@ __global__ void k_noalloc_init_stats(unsigned *stats) {
   stats[1] = 0u;           // no invalid value seen
 }
 
-StencilFn plain_acoustic_fn(int R, bool three) {
-#define NA_PICK(RR) \
-  case RR:          \
-    return three ? k_stencil_plain<RR, kAcoustic, true> : k_stencil_plain<RR, kAcoustic, false>;
+StencilFn plain_acoustic_fn(int R, bool three, bool iso2) {
+#define NA_PICK(RR)                                                                    \
+  case RR:                                                                             \
+    return three ? k_stencil_plain<RR, kAcoustic, true>                                \
+                 : (iso2 ? k_stencil_plain<RR, kAcoustic, false, true>                 \
+                         : k_stencil_plain<RR, kAcoustic, false>);
   switch (R) {
     NA_PICK(1) NA_PICK(2) NA_PICK(3) NA_PICK(4) NA_PICK(5) NA_PICK(6) NA_PICK(7) NA_PICK(8)
   }
@@ -2661,7 +2669,8 @@ extern "C" fd_status fd_acoustic_run_noalloc(int ndim, const int64_t *shape, con
       coef.wp[ax][k] = make_float2(coef.w[ax][k], coef.w[ax][k]);
     }
   }
-  StencilFn fn = plain_acoustic_fn(R, ndim == 3);
+  coef.iso2 = ndim == 2 && spacing[0] == spacing[1] ? 1 : 0;  // as fd_create sets it
+  StencilFn fn = plain_acoustic_fn(R, ndim == 3, coef.iso2 != 0);
   float *cur = lev0, *prev = lev1;
   dim3 block(32, 8);
   dim3 grid((g.n2 + 31) / 32, (g.n1 + 7) / 8, g.n0);

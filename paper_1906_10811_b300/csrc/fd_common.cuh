@@ -46,6 +46,7 @@ __host__ __device__ inline int64_t gidx(const Geom &g, int z, int y, int x) {
 struct Coef {
   float w[3][kMaxR + 1];  // w[axis][k] for k = 1..R; axis 0 unused in 2-D
   float2 wp[3][kMaxR + 1];  // the same weights as pairs (w, w) for packed FP32x2 arithmetic
+  int iso2;               // 2-D with equal spacing: w[1] = w[2], one weight per offset
 };
 
 }  // namespace fdk

@@ -23,8 +23,20 @@ namespace fdk {
 // operator annihilates constants (no drift from rounded weights).  One FMA chain
 // runs over the y offsets, then continues over x (then z): a kernel that streams
 // rows takes the y part from a register queue and the x part from the staged row.
-template <int R, bool THREE_D, typename NB>
+// ISO2 (2-D, equal spacing): one weight per offset multiplies the sum of the four
+// neighbours minus 4u, ((u_{y+k} + u_{y-k}) + (u_{x+k} + u_{x-k})) - 4u: five
+// operations an offset instead of six, still exact on constants (2c + 2c = 4c and
+// 4u are exact), as the 3-D pipelined kernels do for equal spacing.
+template <int R, bool THREE_D, typename NB, bool ISO2 = false>
 __device__ __forceinline__ float plain_lap(float uc, const Coef &c, NB nb) {
+  if constexpr (ISO2 && !THREE_D) {
+    const float nuc4 = -4.f * uc;
+    float lap = 0.f;
+#pragma unroll
+    for (int k = 1; k <= R; ++k)
+      lap = fmaf(c.w[2][k], ((nb(1, k) + nb(1, -k)) + (nb(2, k) + nb(2, -k))) + nuc4, lap);
+    return lap;
+  }
   const float uc2 = uc + uc;
   float lap = 0.f;
 #pragma unroll
@@ -43,16 +55,17 @@ __device__ __forceinline__ float leapfrog(float a, float cc, float uc, float pre
   return fmaf(a, lap, fmaf(1.f + cc, uc, -cc * prev));
 }
 
-template <int R, int EQ, bool THREE_D>
+template <int R, int EQ, bool THREE_D, bool ISO2 = false>
 __device__ __forceinline__ void plain_point(const float *__restrict__ u, float *un,
                                             const float *__restrict__ A,
                                             const float *__restrict__ C, const Geom &g,
                                             const Coef &c, int z, int y, int x) {
   const int64_t p = gidx(g, z, y, x);
   const float uc = u[p];
-  const float lap = plain_lap<R, THREE_D>(uc, c, [&](int ax, int k) {
+  auto nb = [&](int ax, int k) {
     return u[p + (ax == 2 ? (int64_t)k : ax == 1 ? (int64_t)k * g.px : (int64_t)k * g.plane)];
-  });
+  };
+  const float lap = plain_lap<R, THREE_D, decltype(nb), ISO2>(uc, c, nb);
   if (EQ == kAcoustic) {
     un[p] = leapfrog(A[p], C[p], uc, un[p], lap);
   } else {
@@ -62,7 +75,7 @@ __device__ __forceinline__ void plain_point(const float *__restrict__ u, float *
   }
 }
 
-template <int R, int EQ, bool THREE_D>
+template <int R, int EQ, bool THREE_D, bool ISO2 = false>
 __global__ void __launch_bounds__(256)
 k_stencil_plain(const float *__restrict__ u, float *un, const float *__restrict__ A,
                 const float *__restrict__ C, Geom g, Coef c) {
@@ -70,7 +83,7 @@ k_stencil_plain(const float *__restrict__ u, float *un, const float *__restrict_
   const int y = blockIdx.y * 8 + threadIdx.y;
   const int z = blockIdx.z;
   if (x >= g.n2 || y >= g.n1) return;
-  plain_point<R, EQ, THREE_D>(u, un, A, C, g, c, z, y, x);
+  plain_point<R, EQ, THREE_D, ISO2>(u, un, A, C, g, c, z, y, x);
 }
 
 // ---------------------------------------------------------------------------
@@ -121,7 +134,7 @@ __device__ __forceinline__ void s2_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-template <int R, int EQ>
+template <int R, int EQ, bool ISO2 = false>
 __global__ void __launch_bounds__(s2_warps(R) * 32)
 k_stencil2d_stream(const float *__restrict__ u, float *un, const float *__restrict__ A,
                    const float *__restrict__ C, Geom g, Coef c, int nseg, int seglen) {
@@ -175,26 +188,32 @@ k_stencil2d_stream(const float *__restrict__ u, float *un, const float *__restri
       if (t >= 2 * R) {  // row y = ya + t - 2R: its y neighbours are all in the queue
         const int y = ya + t - 2 * R;
         const float2 ucy = q[(ph + Q - R) % Q];
-        const float2 nuc2 = make_float2(-(ucy.x + ucy.x), -(ucy.y + ucy.y));
         float2 lap = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int k = 1; k <= R; ++k)
-          lap = __ffma2_rn(c.wp[1][k],
-                           __fadd2_rn(__fadd2_rn(q[(ph + Q - R + k) % Q], q[(ph + 2 * Q - R - k) % Q]),
-                                      nuc2),
-                           lap);
         const float *rr = rg + ((ph + NR - R) % NR) * RW + HX + 2 * lane;  // row y, staged
         float2 xp[2 * PH + 1];  // the row's pairs around the lane's own
 #pragma unroll
         for (int d = -PH; d <= PH; ++d) xp[d + PH] = *reinterpret_cast<const float2 *>(rr + 2 * d);
+        // u(x+k) + u(x-k) at the pair: aligned pairs for even k, halves of the
+        // neighbouring pairs for odd k
+        auto xsum = [&](int k) -> float2 {
+          if ((k & 1) == 0) return __fadd2_rn(xp[PH + k / 2], xp[PH - k / 2]);
+          return make_float2(__fadd_rn(xp[PH + (k - 1) / 2].y, xp[PH - (k + 1) / 2].y),
+                             __fadd_rn(xp[PH + (k + 1) / 2].x, xp[PH - (k - 1) / 2].x));
+        };
+        auto ysum = [&](int k) -> float2 {  // u(y+k) + u(y-k) from the queue
+          return __fadd2_rn(q[(ph + Q - R + k) % Q], q[(ph + 2 * Q - R - k) % Q]);
+        };
+        if constexpr (ISO2) {  // plain_lap's equal-spacing form
+          const float2 nuc4 = make_float2(-4.f * ucy.x, -4.f * ucy.y);
 #pragma unroll
-        for (int k = 1; k <= R; ++k) {
-          const float2 sx =
-              (k & 1) == 0
-                  ? __fadd2_rn(xp[PH + k / 2], xp[PH - k / 2])
-                  : make_float2(__fadd_rn(xp[PH + (k - 1) / 2].y, xp[PH - (k + 1) / 2].y),
-                                __fadd_rn(xp[PH + (k + 1) / 2].x, xp[PH - (k - 1) / 2].x));
-          lap = __ffma2_rn(c.wp[2][k], __fadd2_rn(sx, nuc2), lap);
+          for (int k = 1; k <= R; ++k)
+            lap = __ffma2_rn(c.wp[2][k], __fadd2_rn(__fadd2_rn(ysum(k), xsum(k)), nuc4), lap);
+        } else {
+          const float2 nuc2 = make_float2(-(ucy.x + ucy.x), -(ucy.y + ucy.y));
+#pragma unroll
+          for (int k = 1; k <= R; ++k) lap = __ffma2_rn(c.wp[1][k], __fadd2_rn(ysum(k), nuc2), lap);
+#pragma unroll
+          for (int k = 1; k <= R; ++k) lap = __ffma2_rn(c.wp[2][k], __fadd2_rn(xsum(k), nuc2), lap);
         }
         const bool yin = hold ? (y > 0 && y < g.n1 - 1) : true;
         const int64_t p = gidx(g, 0, y, x);
@@ -439,7 +458,11 @@ k_stencil2d_batch(const MemberDesc *__restrict__ d, int n, const int64_t *tick, 
   const int y = (int)(b / m.blocks_x) * 8 + threadIdx.y;
   if (x >= m.g.n2 || y >= m.g.n1) return;
   const int par = m.cur0 ^ (int)((*tick + j) & 1);
-  plain_point<R, kAcoustic, false>(m.level[par], m.level[par ^ 1], m.A, m.C, m.g, m.c, 0, y, x);
+  if (m.c.iso2)  // per member (a block holds one member's points)
+    plain_point<R, kAcoustic, false, true>(m.level[par], m.level[par ^ 1], m.A, m.C, m.g, m.c, 0,
+                                           y, x);
+  else
+    plain_point<R, kAcoustic, false>(m.level[par], m.level[par ^ 1], m.A, m.C, m.g, m.c, 0, y, x);
 }
 
 // Source corners of the 2-D members: entry = (member, corner).
