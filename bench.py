@@ -101,9 +101,10 @@ def parse():
     ap.add_argument("--tile", default="auto",
                     help="auto: the autotuner picks the pipelined kernel's tile configuration "
                          "before the timed region; default: the built-in one; "
-                         "TY,ZB,CPS[,AL[,SK[,TX]]]: tile height, z-block height, CTAs per SM, "
-                         "whole-segment split, C-tile skipping and tile width (64: the "
-                         "diffusion x-pair kernel) given explicitly")
+                         "TY,ZB,CPS[,AL[,SK[,TX]]]: tile height (16, 32; 24 with TX 64 from "
+                         "so 8), z-block height, CTAs per SM, split (0 equal ranges, 1 whole "
+                         "segments, 2 work queue with TX 64), C-tile skipping and tile width "
+                         "(64: the x-pair kernel) given explicitly")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--extras", default="sweep512,serving,fwi320,c1,diffusion2d,oracle",
