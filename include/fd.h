@@ -376,7 +376,11 @@ fd_status fd_autotune_fwi(fd_ctx *ctx, int reps, fd_tile_config *best, fd_tile_c
 
 /* (Library service.)  Name of the stencil kernel variant fd_run launches (static string):
  * "stencil3d_tma_<equation>" (32-wide tiles), "stencil3d_xp_<equation>"
- * (64-wide tiles, two x points a lane), "stencil3d_plain" or "stencil2d_plain". */
+ * (64-wide tiles, two x points a lane), "stencil3d_plain", "stencil2d_plain",
+ * "stencil2d_stream" (2-D rows staged and streamed) or "stencil2d_stream2" (2-D
+ * diffusion at space order 2 or 4 with the zero halo: two steps a launch, u^{n+2}
+ * from u^n, bitwise two single steps; a chunk of odd length ends with one single step;
+ * the second level then holds an older state, so only fd_read's level is u^n). */
 const char *fd_kernel_name(const fd_ctx *ctx);
 
 /*

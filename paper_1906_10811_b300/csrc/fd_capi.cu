@@ -98,6 +98,7 @@ struct GraphEntry {
 using StencilFn = void (*)(const float *, float *, const float *, const float *, Geom, Coef);
 using StencilFnStream = void (*)(const float *, float *, const float *, const float *, Geom, Coef,
                                  int, int);
+using StencilFnStream2 = void (*)(const float *, float *, Geom, Coef, int, int);
 using StencilFn2D = void (*)(const MemberDesc *, int, const int64_t *, int);
 
 }  // namespace
@@ -127,7 +128,10 @@ struct fd_ctx {
   // kernel selection
   StencilFn plain_fn = nullptr;
   StencilFnStream stream2d_fn = nullptr;  // 2-D grids: rows staged and streamed along y
+  // 2-D diffusion, radius 1-2, zero halo: two steps a launch (u^{n+2} from u^n)
+  StencilFnStream2 stream2d2_fn = nullptr;
   int s2_nseg = 0, s2_seglen = 0;         // its row segments per strip and their length
+  int s2t_nseg = 0, s2t_seglen = 0;       // the same for the two-step stream (60-column strips)
   TmaPlan tma{};
   bool use_tma = false;
   bool iso = false;          // equal spacing on all axes (pipelined kernel variant)
@@ -414,6 +418,20 @@ fd_status launch_stencil(fd_ctx *c, const float *ucur, float *unext, int j) {
   return FD_OK;
 }
 
+// Two steps in one launch (the 2-D diffusion stream): u^{n+2} from ucur into unext.
+fd_status launch_stencil2(fd_ctx *c, const float *ucur, float *unext) {
+  const int64_t items = (int64_t)((c->g.n2 + kS2W2 - 1) / kS2W2) * c->s2t_nseg;
+  const int nw = s2_warps(c->g.R);
+  c->stream2d2_fn<<<(unsigned)((items + nw - 1) / nw), nw * 32, s2t_smem(c->g.R), c->stream>>>(
+      ucur, unext, c->g, c->coef, c->s2t_nseg, c->s2t_seglen);
+  CHECK_LAUNCH();
+  ++c->launches;
+  return FD_OK;
+}
+
+// Level flips of a chunk of len steps: one per launch (two-step launches cover pairs).
+int chunk_flips(const fd_ctx *c, int len) { return c->stream2d2_fn ? len / 2 + (len & 1) : len; }
+
 // Source injection of step j into unext (kernels without the fused epilogue).
 fd_status launch_inject(fd_ctx *c, float *unext, int j) {
   const int n = c->nsrc * c->nc;
@@ -479,9 +497,18 @@ fd_status profile_mark(fd_ctx *c, bool end, int launches) {
 
 fd_status enqueue_chunk(fd_ctx *c, int parity, int len, bool timed) {
   const bool overlap = c->fused && c->nrec > 0;
-  for (int j = 0; j < len; ++j) {
-    const int b = parity ^ (j & 1);
+  int b = parity;  // level holding u^n of step j
+  for (int j = 0; j < len; ++j, b ^= 1) {
     float *ucur = c->u[b], *unext = c->u[b ^ 1];
+    if (c->stream2d2_fn && j + 1 < len) {
+      // steps j and j+1 in one launch (2-D diffusion: no odd halo, sources or receivers)
+      fd_status st = timed ? profile_mark(c, false, 0) : FD_OK;
+      if (!st) st = launch_stencil2(c, ucur, unext);
+      if (!st && timed) st = profile_mark(c, true, 2);
+      if (st) return st;
+      ++j;
+      continue;
+    }
     if (overlap && j >= 2) CU(cudaStreamWaitEvent(c->stream, c->ev_rec[j & 1], 0));
     if (c->opt.boundary == FD_BOUNDARY_ODD) {
       // halo of u^n = odd mirror of the interior about the boundary nodes
@@ -683,6 +710,7 @@ void select_kernel(fd_ctx *c) {
 #undef PICK
   c->kernel_name = three ? "stencil3d_plain" : "stencil2d_plain";
   c->stream2d_fn = nullptr;
+  c->stream2d2_fn = nullptr;
   if (!three) {
     // rows staged and streamed along y: on request (FD_KERNEL_TMA), and by default for
     // diffusion on grids too large for L2, where one thread per point keeps too few
@@ -719,6 +747,33 @@ void select_kernel(fd_ctx *c) {
       c->s2_seglen = (c->g.n1 + nseg - 1) / nseg;
       c->s2_nseg = (c->g.n1 + c->s2_seglen - 1) / c->s2_seglen;
       c->kernel_name = "stencil2d_stream";
+      // diffusion at radius 1-2 with the zero halo: pairs of steps in one pass (the
+      // step moves 8 bytes a point and has compute to spare; two steps move 8 in all)
+      if (!ac && R <= 2 && c->opt.boundary != FD_BOUNDARY_ODD) {
+        if (R == 1)
+          c->stream2d2_fn = iso2 ? k_stencil2d_stream2<1, true> : k_stencil2d_stream2<1, false>;
+        else
+          c->stream2d2_fn = iso2 ? k_stencil2d_stream2<2, true> : k_stencil2d_stream2<2, false>;
+        cudaFuncSetAttribute((const void *)c->stream2d2_fn,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, s2t_smem(R));
+        // segments for one wave of its own occupancy (it holds more registers and
+        // shared memory a warp than the one-step stream), at least 32 rows
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)c->stream2d2_fn,
+                                                          s2_warps(R) * 32, s2t_smem(R)) !=
+                cudaSuccess ||
+            per_sm < 1) {
+          cudaGetLastError();
+          per_sm = 1;
+        }
+        const int strips2 = (c->g.n2 + kS2W2 - 1) / kS2W2;
+        const int64_t streams = (int64_t)per_sm * s2_warps(R) * sms;
+        const int most2 = std::max(1, c->g.n1 / 32);
+        const int nseg2 = (int)std::max<int64_t>(1, std::min<int64_t>(streams / strips2, most2));
+        c->s2t_seglen = (c->g.n1 + nseg2 - 1) / nseg2;
+        c->s2t_nseg = (c->g.n1 + c->s2t_seglen - 1) / c->s2t_seglen;
+        c->kernel_name = "stencil2d_stream2";
+      }
     }
   }
 }
@@ -1232,7 +1287,7 @@ fd_status run_steps(fd_ctx *c, int nt, bool graphs) {
       st = enqueue_chunk(c, c->cur, len, c->opt.profile != 0);
       if (st) return st;
     }
-    c->cur ^= (len & 1);
+    c->cur ^= (chunk_flips(c, len) & 1);
     done += len;
   }
   c->step += nt;

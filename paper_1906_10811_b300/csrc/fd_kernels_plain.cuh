@@ -248,6 +248,172 @@ k_stencil2d_stream(const float *__restrict__ u, float *un, const float *__restri
 }
 
 // ---------------------------------------------------------------------------
+// Two diffusion steps in one pass of the row stream (radius 1 and 2, zero halo):
+// u^{n+2} from u^n, reading u^n once and writing u^{n+2} once, 4 instead of 8
+// bytes a point-step.  A warp streams the rows ya-2R .. yb+2R-1 of u^n into its
+// ring A as k_stencil2d_stream does; for each arriving row t it computes the
+// intermediate row i = t-R of u^{n+1} on 64 columns, its 60-column strip widened by
+// 2 each side (every lane a pair, lanes 0 and 31 the widening: no divergent edge
+// work), into ring B (2R+1 rows, shared memory) and
+// into a register queue of the lane's pair, and from those the row o = i-R of
+// u^{n+2}.  Both stages run plain_lap's operation sequence and plain_point's
+// update, and the intermediate values follow the single step's rules (zero
+// outside the grid, boundary nodes held when g.hold), so the result is bitwise
+// two launches of the one-step kernels.  Rows of u^n further than R outside the
+// grid (needed only by intermediate rows outside it, which are zero) are not
+// read.  The caller writes into the other level: u^{n+1} is never stored.
+// ---------------------------------------------------------------------------
+constexpr int kS2W2 = 60;  // output columns a warp of the two-step stream (a multiple of 4)
+__host__ __device__ constexpr int s2t_nr(int R) {  // ring A rows: a multiple of 2R+1
+  return (2 * R + 1) * ((2 * R + 2 + 8 + 2 * R) / (2 * R + 1));
+}
+__host__ __device__ constexpr int s2t_d(int R) { return s2t_nr(R) - 2 * R - 2; }  // in flight
+__host__ __device__ constexpr int s2t_smem(int R) {
+  return s2_warps(R) * (s2t_nr(R) + 2 * R + 1) * s2_rw(R) * 4;
+}
+
+template <int R, bool ISO2 = false>
+__global__ void __launch_bounds__(s2_warps(R) * 32)
+k_stencil2d_stream2(const float *__restrict__ u, float *un, Geom g, Coef c, int nseg, int seglen) {
+  constexpr int HX = s2_hx(R), RW = s2_rw(R), Q = 2 * R + 1, NR = s2t_nr(R), D = s2t_d(R);
+  constexpr int NWP = s2_warps(R);
+  constexpr int PH = (R + 1) / 2;  // x pairs each side of the lane's own
+  static_assert(R <= 2 && NR % Q == 0 && D >= 1 && HX == 4 && kS2W2 + 4 == kS2W,
+                "radius 1-2; 64 intermediate columns x0-2 .. x0+61 and their x neighbours "
+                "x0-4 .. x0+63 lie in the staged row x0-4 .. x0+67");
+  extern __shared__ __align__(16) float s2_ring[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int strips = (g.n2 + kS2W2 - 1) / kS2W2;
+  const int item = blockIdx.x * NWP + warp;
+  if (item >= strips * nseg) return;
+  const int strip = item % strips, seg = item / strips;
+  const int x0 = strip * kS2W2;  // the staged rows start at x0 - HX as in k_stencil2d_stream
+  const int ya = seg * seglen, yb = min(g.n1, ya + seglen);
+  if (ya >= yb) return;
+  float *ra = s2_ring + (size_t)warp * (NR + Q) * RW;  // u^n rows
+  float *rb = ra + NR * RW;                            // u^{n+1} rows, slot i mod Q
+  const int T = (yb - ya) + 4 * R;  // rows streamed: ya-2R .. yb+2R-1
+  const int col0 = x0 + kHaloX - HX;
+  auto issue = [&](int t) {  // row ya - 2R + t into ring slot t % NR
+    if (t < T) {
+      const int r = ya - 2 * R + t;
+      const bool row_in = r >= -R && r < g.n1 + R;  // rows of the padded layout
+      float *dst = ra + (t % NR) * RW;
+      const float *src = row_in ? u + gidx(g, 0, r, x0) - HX : u;
+#pragma unroll
+      for (int ch = lane; ch < RW / 4; ch += 32) {
+        const bool in = row_in && col0 + 4 * ch + 4 <= g.px;
+        s2_copy16(dst + 4 * ch, in ? src + 4 * ch : u, in ? 16 : 0);
+      }
+    }
+    s2_commit();
+  };
+  const bool hold = g.hold != 0;
+  // one step at a pair from its centre value, a y-sum accessor and the row's pairs
+  // around it: plain_lap's sequence (ISO2: one weight per offset), then uc + lap
+  auto lap_pair = [&](float2 uc, auto ysum, const float2 *xp) -> float2 {
+    auto xsum = [&](int k) -> float2 {
+      if ((k & 1) == 0) return __fadd2_rn(xp[PH + k / 2], xp[PH - k / 2]);
+      return make_float2(__fadd_rn(xp[PH + (k - 1) / 2].y, xp[PH - (k + 1) / 2].y),
+                         __fadd_rn(xp[PH + (k + 1) / 2].x, xp[PH - (k - 1) / 2].x));
+    };
+    float2 lap = make_float2(0.f, 0.f);
+    if constexpr (ISO2) {
+      const float2 nuc4 = make_float2(-4.f * uc.x, -4.f * uc.y);
+#pragma unroll
+      for (int k = 1; k <= R; ++k)
+        lap = __ffma2_rn(c.wp[2][k], __fadd2_rn(__fadd2_rn(ysum(k), xsum(k)), nuc4), lap);
+    } else {
+      const float2 nuc2 = make_float2(-(uc.x + uc.x), -(uc.y + uc.y));
+#pragma unroll
+      for (int k = 1; k <= R; ++k) lap = __ffma2_rn(c.wp[1][k], __fadd2_rn(ysum(k), nuc2), lap);
+#pragma unroll
+      for (int k = 1; k <= R; ++k) lap = __ffma2_rn(c.wp[2][k], __fadd2_rn(xsum(k), nuc2), lap);
+    }
+    return make_float2(uc.x + lap.x, uc.y + lap.y);
+  };
+  const int x = x0 - 2 + 2 * lane;  // the lane's pair; lanes 1..30 own output columns
+  const bool own = lane >= 1 && lane <= 30;
+  const bool xin0 = own && (hold ? (x > 0 && x < g.n2 - 1) : x < g.n2);
+  const bool xin1 = own && (hold ? (x + 1 > 0 && x + 1 < g.n2 - 1) : x + 1 < g.n2);
+  const int xo = 2 * lane - 2;  // the pair's offset from x0 in the staged rows
+  // the intermediate level at row y of the lane's pair (the single step's rules: zero
+  // outside the grid, boundary nodes held); the column part is the lane's own
+  const bool cin0 = x >= 0 && x < g.n2, cin1 = x + 1 >= 0 && x + 1 < g.n2;
+  const bool cbd0 = hold && (x == 0 || x == g.n2 - 1);
+  const bool cbd1 = hold && (x + 1 == 0 || x + 1 == g.n2 - 1);
+  const bool cfree = cin0 && cin1 && !cbd0 && !cbd1;  // both points updated on inner rows
+  const int ylo = hold ? 1 : 0;                        // inner rows ylo .. ylo+yspan-1
+  const unsigned yspan = (unsigned)(hold ? g.n1 - 2 : g.n1);
+  auto settle = [&](int y, float2 uc, float2 v) -> float2 {
+    if (cfree && (unsigned)(y - ylo) < yspan) return v;
+    float2 out = make_float2(0.f, 0.f);
+    if (y >= 0 && y < g.n1) {
+      const bool ybd = hold && (y == 0 || y == g.n1 - 1);
+      if (cin0) out.x = (ybd || cbd0) ? uc.x : v.x;
+      if (cin1) out.y = (ybd || cbd1) ? uc.y : v.y;
+    }
+    return out;
+  };
+  float2 qa[Q];  // u^n at the pair, row t in slot t % Q
+  float2 qb[Q];  // u^{n+1} at the pair, intermediate row of stream position t in slot t % Q
+#pragma unroll
+  for (int t = 0; t < D; ++t) issue(t);
+  for (int tb = 0; tb < T; tb += NR) {
+#pragma unroll
+    for (int ph = 0; ph < NR; ++ph) {
+      const int t = tb + ph;
+      if (t >= T) break;
+      issue(t + D);
+      s2_wait<D>();  // row t's copies have landed
+      __syncwarp();
+      qa[ph % Q] = *reinterpret_cast<const float2 *>(ra + ph * RW + HX + xo);
+      if (t >= 2 * R) {
+        // stage 1: row i = t-R of u^{n+1} (stream row ya-3R+t) on the widened strip
+        const int i = ya - 3 * R + t;
+        const float *ri = ra + ((ph + NR - R) % NR) * RW + HX;  // row i of u^n, staged
+        float *wb = rb + (ph % Q) * RW + HX;
+        float2 xp[2 * PH + 1];
+#pragma unroll
+        for (int d = -PH; d <= PH; ++d)
+          xp[d + PH] = *reinterpret_cast<const float2 *>(ri + xo + 2 * d);
+        const float2 uc = qa[(ph + Q - R) % Q];
+        auto ysum = [&](int k) -> float2 {
+          return __fadd2_rn(qa[(ph + Q - R + k) % Q], qa[(ph + 2 * Q - R - k) % Q]);
+        };
+        const float2 v = settle(i, uc, lap_pair(uc, ysum, xp));
+        qb[ph % Q] = v;
+        *reinterpret_cast<float2 *>(wb + xo) = v;
+      }
+      __syncwarp();  // ring B row i visible to the warp
+      if (t >= 4 * R) {
+        // stage 2: row o = i-R of u^{n+2} (stream row ya-4R+t) on the strip
+        const int o = ya - 4 * R + t;
+        const float *ro = rb + ((ph + Q - R) % Q) * RW + HX + xo;  // row o of u^{n+1}
+        float2 xp[2 * PH + 1];
+#pragma unroll
+        for (int d = -PH; d <= PH; ++d) xp[d + PH] = *reinterpret_cast<const float2 *>(ro + 2 * d);
+        const float2 vc = qb[(ph + Q - R) % Q];
+        auto ysum = [&](int k) -> float2 {
+          return __fadd2_rn(qb[(ph + Q - R + k) % Q], qb[(ph + 2 * Q - R - k) % Q]);
+        };
+        const float2 val = lap_pair(vc, ysum, xp);
+        const bool yin = hold ? (o > 0 && o < g.n1 - 1) : true;
+        if (yin) {
+          const int64_t p = gidx(g, 0, o, x);
+          if (xin0 && xin1)
+            *reinterpret_cast<float2 *>(un + p) = val;
+          else {
+            if (xin0) un[p] = val.x;
+            if (xin1) un[p + 1] = val.y;
+          }
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Layout moves between dense interior arrays and the padded layout.
 // ---------------------------------------------------------------------------
 __global__ void k_scatter(const float *__restrict__ dense, float *__restrict__ padded, Geom g) {

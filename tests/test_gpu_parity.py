@@ -405,6 +405,36 @@ def test_diffusion_every_node_updated(kernel, shape, tile, so):
     assert rel_l2(held, ref) > 1e-4                # the two sweeps differ measurably
 
 
+@pytest.mark.parametrize("so", (2, 4))
+@pytest.mark.parametrize("shape", [(61, 53), (17, 130), (530, 601), (1500, 90)])
+def test_2d_diffusion_two_steps_a_launch_are_bitwise_single_steps(so, shape):
+    """2-D diffusion at radius 1-2 streams pairs of steps (u^{n+2} from u^n in one
+    pass, the intermediate level on a strip widened by R columns each side): bitwise
+    the plain kernel's single steps, for equal and unequal spacing, the held boundary
+    and every node updated, over chunks of odd lengths (a single step closes each),
+    with graph replay and with eager launches."""
+    from paper_1906_10811_b300 import Solver
+    rng = np.random.default_rng(so * 7 + shape[0])
+    u0 = rng.standard_normal(shape).astype(np.float32)
+    for h in ((1.0 / 50, 1.0 / 50), (1.0 / 40, 1.0 / 30)):
+        for hold in (True, False):
+            outs = []
+            for kernel, graphs in (("plain", True), ("tma", True), ("tma", False)):
+                with Solver(shape, h, so, 0.05 * min(h) ** 2, "diffusion", kernel=kernel,
+                            graphs=graphs, dirichlet_interior=hold) as s:
+                    if kernel == "tma":
+                        assert s.kernel_name == "stencil2d_stream2"
+                    s.set_field(u0)
+                    for n in (1, 3, 40, 2):
+                        s.run(n)
+                    assert s.steps == 46
+                    outs.append(s.read()[0])
+            assert np.array_equal(outs[1], outs[0]), (h, hold)
+            assert np.array_equal(outs[2], outs[0]), (h, hold)
+            ref = oracle.diffusion(u0, h, so, 0.5, 0.05 * min(h) ** 2, 46, interior=hold)
+            assert rel_l2(outs[0], ref) <= 1e-5
+
+
 def test_large_2d_diffusion_streams_rows_by_default():
     """From 4 M points a 2-D diffusion context runs the row-streaming kernel unless
     asked for plain; the acoustic step keeps the plain kernel; both kernels agree."""
@@ -414,7 +444,7 @@ def test_large_2d_diffusion_streams_rows_by_default():
     u0 = rng.standard_normal(shape).astype(np.float32)
     h = (1.0 / 2099, 1.0 / 2002)
     outs = []
-    for kernel, name in (("auto", "stencil2d_stream"), ("plain", "stencil2d_plain")):
+    for kernel, name in (("auto", "stencil2d_stream2"), ("plain", "stencil2d_plain")):
         with Solver(shape, h, 4, 0.05 * min(h) ** 2, "diffusion", kernel=kernel) as s:
             assert s.kernel_name == name
             s.set_field(u0)
