@@ -572,6 +572,12 @@ def run_diffusion(args):
                 "stencil_share_of_step": round(st_ms / ms, 4),
                 "peak_source": f"{peak_kind} HBM copy bandwidth (of {peak_kind})",
                 "gpts_per_s_kernel": round(npts / avg_s / 1e9, 2)}
+    if kernel_name == "stencil2d_stream2":
+        # two steps a launch: the profile counts steps, so the figures above are per
+        # step at the algorithmic 8 B per point-step; the launch moves 4 per point-step
+        roofline["bytes_moved_per_point_step"] = BYTES_PER_POINT["diffusion"] / 2
+        roofline["note"] = ("two steps a launch: per-step time at the algorithmic 8 B per "
+                            "point-step; each launch reads u^n and writes u^{n+2} once")
     e2e = None
     if not args.no_e2e:
         u0_h = torch.from_numpy(q["u0"]).pin_memory().numpy()
@@ -733,8 +739,10 @@ def sweep512_result(reps=2, orders=SWEEP_ORDERS):
 def diffusion2d_result(n=10000, orders=(2, 4, 8, 16), nt=100, reps=2):
     """The paper's benchmark problem (§5.1.2: 2-D diffusion, sine-mode data, ν = 0.5,
     interior update) at n² = 10000², a size the paper measured: per space order the
-    kernel, µs per launch, fraction of the measured copy bandwidth at 8 B/pt and
-    GPts/s of whole sweeps (field reset + nt steps)."""
+    kernel, µs per step (the profile counts steps; the two-step stream at so 2/4 runs
+    two a launch), fraction of the measured copy bandwidth at the algorithmic 8 B per
+    point-step, the bytes per point-step the kernel actually moves (4 for two steps a
+    launch) and GPts/s of whole sweeps (field reset + nt steps)."""
     import torch
     from paper_1906_10811_b300 import Solver
     peak, peak_kind = load_peak()
@@ -766,7 +774,9 @@ def diffusion2d_result(n=10000, orders=(2, 4, 8, 16), nt=100, reps=2):
         n_st, st_ms = s.profile()
         avg = st_ms / max(n_st, 1) / 1e3
         ach = BYTES_PER_POINT["diffusion"] * npts / avg / 1e9
+        moved = BYTES_PER_POINT["diffusion"] / (2 if s.kernel_name == "stencil2d_stream2" else 1)
         out[f"so{so}"] = {"kernel": s.kernel_name, "us_per_launch": round(avg * 1e6, 2),
+                          "us_per_step": round(avg * 1e6, 2), "bytes_moved_per_point_step": moved,
                           "achieved_gbs": round(ach, 1), "frac": round(ach / peak, 4),
                           "gpts_per_s_kernel": round(npts / avg / 1e9, 2),
                           "gpts_per_s_sweep": round(npts * nt * reps / (ms / 1e3) / 1e9, 2)}
