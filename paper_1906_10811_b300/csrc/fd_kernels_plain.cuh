@@ -357,6 +357,10 @@ k_stencil2d_stream2(const float *__restrict__ u, float *un, Geom g, Coef c, int 
   };
   float2 qa[Q];  // u^n at the pair, row t in slot t % Q
   float2 qb[Q];  // u^{n+1} at the pair, intermediate row of stream position t in slot t % Q
+  // ring B's columns outside those stage 1 writes are read (and discarded) by the edge
+  // lanes' stage 2: zero them once so that every shared-memory read is of written data
+  for (int k = lane; k < Q * RW; k += 32) rb[k] = 0.f;
+  __syncwarp();
 #pragma unroll
   for (int t = 0; t < D; ++t) issue(t);
   for (int tb = 0; tb < T; tb += NR) {
@@ -387,7 +391,8 @@ k_stencil2d_stream2(const float *__restrict__ u, float *un, Geom g, Coef c, int 
       }
       __syncwarp();  // ring B row i visible to the warp
       if (t >= 4 * R) {
-        // stage 2: row o = i-R of u^{n+2} (stream row ya-4R+t) on the strip
+        // stage 2: row o = i-R of u^{n+2} (stream row ya-4R+t) on the strip; lanes 0
+        // and 31 compute with ring B's zeroed edge columns and store nothing
         const int o = ya - 4 * R + t;
         const float *ro = rb + ((ph + Q - R) % Q) * RW + HX + xo;  // row o of u^{n+1}
         float2 xp[2 * PH + 1];
