@@ -955,7 +955,12 @@ k_stencil3d_xp(const __grid_constant__ CUtensorMap map_u,  // u^n, halo box (kXp
   constexpr int USLOT = tma_align128(xp_ubytes(R, HC)) / 4;  // floats per ring-U slot
   constexpr int XT = kXpTX * TY;                              // floats per ring-X tile
   constexpr int Q = 2 * R + 1;
-  constexpr int U = tma_unroll(R);
+  // 12 consumer warps run at the 128-register cap of 416 threads: the acoustic step
+  // unrolls by 2 there (two fewer queue planes a row, no spills; so 16 at 512³ 542 ->
+  // 533 µs) where the window is not unrolled whole; diffusion lost 3-4 % that way
+  constexpr int U = (EQ == kAcoustic && NW != kTmaNW && tma_unroll(R) < 2 * R + 1)
+                        ? 2
+                        : tma_unroll(R);
   constexpr int QL = U == Q ? Q : Q + U - 1;
   constexpr bool kSplit = R > 4;
   constexpr bool kUnitC = AC && R <= 4;
