@@ -158,6 +158,11 @@ class Solver:
         return B.fd_get_tile_config(self.ctx)
 
     def set_tile_config(self, tile_y=0, zblock=0, ctas_per_sm=0, aligned=0, skip_c=0, tile_x=0):
+        """Tile configuration of the pipelined 3-D kernel (fd_set_tile_config): tile_x 32
+        or 64 (two x points a lane), tile_y 16 or 32 (24 with tile_x 64 from space order
+        8: 12 consumer warps), split aligned 0 (equal ranges), 1 (whole segments) or 2
+        (work queue, tile_x 64), skip_c 1 to skip C where it is 1; 0 means the default.
+        Every configuration computes the same bits."""
         self._in()
         B.fd_set_tile_config(self.ctx, tile_y=tile_y, zblock=zblock, ctas_per_sm=ctas_per_sm,
                              aligned=aligned, skip_c=skip_c, tile_x=tile_x)
