@@ -131,7 +131,8 @@ struct fd_ctx {
   // 2-D diffusion, radius 1-2, zero halo: two steps a launch (u^{n+2} from u^n)
   StencilFnStream2 stream2d2_fn = nullptr;
   int s2_nseg = 0, s2_seglen = 0;         // its row segments per strip and their length
-  int s2t_nseg = 0, s2t_seglen = 0;       // the same for the two-step stream (60-column strips)
+  int s2t_nseg = 0, s2t_seglen = 0;       // the same for the two-step stream (strips s2t_w(P) wide)
+  int s2t_p = 1;                          // its pairs a lane
   TmaPlan tma{};
   bool use_tma = false;
   bool iso = false;          // equal spacing on all axes (pipelined kernel variant)
@@ -420,9 +421,11 @@ fd_status launch_stencil(fd_ctx *c, const float *ucur, float *unext, int j) {
 
 // Two steps in one launch (the 2-D diffusion stream): u^{n+2} from ucur into unext.
 fd_status launch_stencil2(fd_ctx *c, const float *ucur, float *unext) {
-  const int64_t items = (int64_t)((c->g.n2 + kS2W2 - 1) / kS2W2) * c->s2t_nseg;
+  const int w = s2t_w(c->s2t_p);
+  const int64_t items = (int64_t)((c->g.n2 + w - 1) / w) * c->s2t_nseg;
   const int nw = s2_warps(c->g.R);
-  c->stream2d2_fn<<<(unsigned)((items + nw - 1) / nw), nw * 32, s2t_smem(c->g.R), c->stream>>>(
+  c->stream2d2_fn<<<(unsigned)((items + nw - 1) / nw), nw * 32, s2t_smem(c->g.R, c->s2t_p),
+                    c->stream>>>(
       ucur, unext, c->g, c->coef, c->s2t_nseg, c->s2t_seglen);
   CHECK_LAUNCH();
   ++c->launches;
@@ -750,25 +753,39 @@ void select_kernel(fd_ctx *c) {
       // diffusion at radius 1-2 with the zero halo: pairs of steps in one pass (the
       // step moves 8 bytes a point and has compute to spare; two steps move 8 in all)
       if (!ac && R <= 2 && c->opt.boundary != FD_BOUNDARY_ODD) {
-        if (R == 1)
-          c->stream2d2_fn = iso2 ? k_stencil2d_stream2<1, true> : k_stencil2d_stream2<1, false>;
-        else
-          c->stream2d2_fn = iso2 ? k_stencil2d_stream2<2, true> : k_stencil2d_stream2<2, false>;
-        cudaFuncSetAttribute((const void *)c->stream2d2_fn,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, s2t_smem(R));
-        // segments for one wave of its own occupancy (it holds more registers and
-        // shared memory a warp than the one-step stream), at least 32 rows
-        int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)c->stream2d2_fn,
-                                                          s2_warps(R) * 32, s2t_smem(R)) !=
-                cudaSuccess ||
-            per_sm < 1) {
-          cudaGetLastError();
-          per_sm = 1;
-        }
-        const int strips2 = (c->g.n2 + kS2W2 - 1) / kS2W2;
-        const int64_t streams = (int64_t)per_sm * s2_warps(R) * sms;
+        // two pairs a lane (124-column strips, half the per-row work a point) where the
+        // grid has the strips and segments to fill a wave with them; one pair otherwise
+        auto pick = [&](int P) -> StencilFnStream2 {
+          if (R == 1)
+            return P == 2 ? (iso2 ? k_stencil2d_stream2<1, true, 2> : k_stencil2d_stream2<1, false, 2>)
+                          : (iso2 ? k_stencil2d_stream2<1, true, 1> : k_stencil2d_stream2<1, false, 1>);
+          return P == 2 ? (iso2 ? k_stencil2d_stream2<2, true, 2> : k_stencil2d_stream2<2, false, 2>)
+                        : (iso2 ? k_stencil2d_stream2<2, true, 1> : k_stencil2d_stream2<2, false, 1>);
+        };
+        // streams a wave holds (segments of at least 32 rows) for P pairs a lane
+        auto wave = [&](int P, StencilFnStream2 fn, int *streams) {
+          int per_sm = 0;
+          cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               s2t_smem(R, P));
+          if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn,
+                                                            s2_warps(R) * 32, s2t_smem(R, P)) !=
+                  cudaSuccess ||
+              per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+          }
+          *streams = per_sm * s2_warps(R) * sms;
+        };
         const int most2 = std::max(1, c->g.n1 / 32);
+        int streams2 = 0;
+        wave(2, pick(2), &streams2);
+        const int64_t items2 = (int64_t)((c->g.n2 + s2t_w(2) - 1) / s2t_w(2)) * most2;
+        c->s2t_p = items2 >= streams2 ? 2 : 1;
+        c->stream2d2_fn = pick(c->s2t_p);
+        int streams = streams2;
+        if (c->s2t_p == 1) wave(1, c->stream2d2_fn, &streams);
+        // segments for one wave of the kernel's own occupancy, at least 32 rows
+        const int strips2 = (c->g.n2 + s2t_w(c->s2t_p) - 1) / s2t_w(c->s2t_p);
         const int nseg2 = (int)std::max<int64_t>(1, std::min<int64_t>(streams / strips2, most2));
         c->s2t_seglen = (c->g.n1 + nseg2 - 1) / nseg2;
         c->s2t_nseg = (c->g.n1 + c->s2t_seglen - 1) / c->s2t_seglen;

@@ -263,24 +263,29 @@ k_stencil2d_stream(const float *__restrict__ u, float *un, const float *__restri
 // grid (needed only by intermediate rows outside it, which are zero) are not
 // read.  The caller writes into the other level: u^{n+1} is never stored.
 // ---------------------------------------------------------------------------
-constexpr int kS2W2 = 60;  // output columns a warp of the two-step stream (a multiple of 4)
+// P pairs a lane (halves of 64 columns of the widened strip): a warp outputs 64P-4
+// columns (a multiple of 4) from staged rows 64P + 2·HX wide
+__host__ __device__ constexpr int s2t_w(int P) { return 64 * P - 4; }
+__host__ __device__ constexpr int s2t_rw(int R, int P) { return 64 * P + 2 * s2_hx(R); }
 __host__ __device__ constexpr int s2t_nr(int R) {  // ring A rows: a multiple of 2R+1
   return (2 * R + 1) * ((2 * R + 2 + 8 + 2 * R) / (2 * R + 1));
 }
 __host__ __device__ constexpr int s2t_d(int R) { return s2t_nr(R) - 2 * R - 2; }  // in flight
-__host__ __device__ constexpr int s2t_smem(int R) {
-  return s2_warps(R) * (s2t_nr(R) + 2 * R + 1) * s2_rw(R) * 4;
+__host__ __device__ constexpr int s2t_smem(int R, int P) {
+  return s2_warps(R) * (s2t_nr(R) + 2 * R + 1) * s2t_rw(R, P) * 4;
 }
 
-template <int R, bool ISO2 = false>
+template <int R, bool ISO2 = false, int NP = 1>
 __global__ void __launch_bounds__(s2_warps(R) * 32)
 k_stencil2d_stream2(const float *__restrict__ u, float *un, Geom g, Coef c, int nseg, int seglen) {
-  constexpr int HX = s2_hx(R), RW = s2_rw(R), Q = 2 * R + 1, NR = s2t_nr(R), D = s2t_d(R);
+  constexpr int HX = s2_hx(R), RW = s2t_rw(R, NP), Q = 2 * R + 1, NR = s2t_nr(R), D = s2t_d(R);
+  constexpr int kS2P = NP;            // pairs a lane
+  constexpr int kS2W2 = s2t_w(kS2P);  // output columns a warp
   constexpr int NWP = s2_warps(R);
   constexpr int PH = (R + 1) / 2;  // x pairs each side of the lane's own
-  static_assert(R <= 2 && NR % Q == 0 && D >= 1 && HX == 4 && kS2W2 + 4 == kS2W,
-                "radius 1-2; 64 intermediate columns x0-2 .. x0+61 and their x neighbours "
-                "x0-4 .. x0+63 lie in the staged row x0-4 .. x0+67");
+  static_assert(R <= 2 && NR % Q == 0 && D >= 1 && HX == 4 && (kS2P == 1 || kS2P == 2),
+                "radius 1-2; the 64·P intermediate columns x0-2 .. x0+64P-3 and their x "
+                "neighbours x0-4 .. x0+64P-1 lie in the staged row x0-4 .. x0+64P+3");
   extern __shared__ __align__(16) float s2_ring[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int strips = (g.n2 + kS2W2 - 1) / kS2W2;
@@ -332,33 +337,41 @@ k_stencil2d_stream2(const float *__restrict__ u, float *un, Geom g, Coef c, int 
     }
     return make_float2(uc.x + lap.x, uc.y + lap.y);
   };
-  const int x = x0 - 2 + 2 * lane;  // the lane's pair; lanes 1..30 own output columns
-  const bool own = lane >= 1 && lane <= 30;
-  const bool xin0 = own && (hold ? (x > 0 && x < g.n2 - 1) : x < g.n2);
-  const bool xin1 = own && (hold ? (x + 1 > 0 && x + 1 < g.n2 - 1) : x + 1 < g.n2);
-  const int xo = 2 * lane - 2;  // the pair's offset from x0 in the staged rows
-  // the intermediate level at row y of the lane's pair (the single step's rules: zero
-  // outside the grid, boundary nodes held); the column part is the lane's own
-  const bool cin0 = x >= 0 && x < g.n2, cin1 = x + 1 >= 0 && x + 1 < g.n2;
-  const bool cbd0 = hold && (x == 0 || x == g.n2 - 1);
-  const bool cbd1 = hold && (x + 1 == 0 || x + 1 == g.n2 - 1);
-  const bool cfree = cin0 && cin1 && !cbd0 && !cbd1;  // both points updated on inner rows
-  const int ylo = hold ? 1 : 0;                        // inner rows ylo .. ylo+yspan-1
+  // the lane's pairs, one in each 64-column half of the widened strip: pair p at x[p] =
+  // x0 - 2 + 64p + 2·lane; every pair but the strip's first and last owns output columns
+  int x[kS2P], xo[kS2P];
+  bool xin0[kS2P], xin1[kS2P], cin0[kS2P], cin1[kS2P], cbd0[kS2P], cbd1[kS2P], cfree[kS2P];
+#pragma unroll
+  for (int p = 0; p < kS2P; ++p) {
+    x[p] = x0 - 2 + 64 * p + 2 * lane;
+    xo[p] = 64 * p + 2 * lane - 2;  // the pair's offset from x0 in the staged rows
+    const bool own = !(p == 0 && lane == 0) && !(p == kS2P - 1 && lane == 31);
+    xin0[p] = own && (hold ? (x[p] > 0 && x[p] < g.n2 - 1) : x[p] < g.n2);
+    xin1[p] = own && (hold ? (x[p] + 1 > 0 && x[p] + 1 < g.n2 - 1) : x[p] + 1 < g.n2);
+    // the intermediate level's column rules (zero outside the grid, held boundary)
+    cin0[p] = x[p] >= 0 && x[p] < g.n2;
+    cin1[p] = x[p] + 1 >= 0 && x[p] + 1 < g.n2;
+    cbd0[p] = hold && (x[p] == 0 || x[p] == g.n2 - 1);
+    cbd1[p] = hold && (x[p] + 1 == 0 || x[p] + 1 == g.n2 - 1);
+    cfree[p] = cin0[p] && cin1[p] && !cbd0[p] && !cbd1[p];  // updated on inner rows
+  }
+  const int ylo = hold ? 1 : 0;  // inner rows ylo .. ylo+yspan-1
   const unsigned yspan = (unsigned)(hold ? g.n1 - 2 : g.n1);
-  auto settle = [&](int y, float2 uc, float2 v) -> float2 {
-    if (cfree && (unsigned)(y - ylo) < yspan) return v;
+  // the intermediate level at row y of pair p (the single step's rules)
+  auto settle = [&](int p, int y, float2 uc, float2 v) -> float2 {
+    if (cfree[p] && (unsigned)(y - ylo) < yspan) return v;
     float2 out = make_float2(0.f, 0.f);
     if (y >= 0 && y < g.n1) {
       const bool ybd = hold && (y == 0 || y == g.n1 - 1);
-      if (cin0) out.x = (ybd || cbd0) ? uc.x : v.x;
-      if (cin1) out.y = (ybd || cbd1) ? uc.y : v.y;
+      if (cin0[p]) out.x = (ybd || cbd0[p]) ? uc.x : v.x;
+      if (cin1[p]) out.y = (ybd || cbd1[p]) ? uc.y : v.y;
     }
     return out;
   };
-  float2 qa[Q];  // u^n at the pair, row t in slot t % Q
-  float2 qb[Q];  // u^{n+1} at the pair, intermediate row of stream position t in slot t % Q
+  float2 qa[kS2P][Q];  // u^n at pair p, row t in slot t % Q
+  float2 qb[kS2P][Q];  // u^{n+1} at pair p, intermediate row of stream position t in slot t % Q
   // ring B's columns outside those stage 1 writes are read (and discarded) by the edge
-  // lanes' stage 2: zero them once so that every shared-memory read is of written data
+  // pairs' stage 2: zero them once so that every shared-memory read is of written data
   for (int k = lane; k < Q * RW; k += 32) rb[k] = 0.f;
   __syncwarp();
 #pragma unroll
@@ -371,46 +384,55 @@ k_stencil2d_stream2(const float *__restrict__ u, float *un, Geom g, Coef c, int 
       issue(t + D);
       s2_wait<D>();  // row t's copies have landed
       __syncwarp();
-      qa[ph % Q] = *reinterpret_cast<const float2 *>(ra + ph * RW + HX + xo);
+#pragma unroll
+      for (int p = 0; p < kS2P; ++p)
+        qa[p][ph % Q] = *reinterpret_cast<const float2 *>(ra + ph * RW + HX + xo[p]);
       if (t >= 2 * R) {
         // stage 1: row i = t-R of u^{n+1} (stream row ya-3R+t) on the widened strip
         const int i = ya - 3 * R + t;
         const float *ri = ra + ((ph + NR - R) % NR) * RW + HX;  // row i of u^n, staged
         float *wb = rb + (ph % Q) * RW + HX;
-        float2 xp[2 * PH + 1];
 #pragma unroll
-        for (int d = -PH; d <= PH; ++d)
-          xp[d + PH] = *reinterpret_cast<const float2 *>(ri + xo + 2 * d);
-        const float2 uc = qa[(ph + Q - R) % Q];
-        auto ysum = [&](int k) -> float2 {
-          return __fadd2_rn(qa[(ph + Q - R + k) % Q], qa[(ph + 2 * Q - R - k) % Q]);
-        };
-        const float2 v = settle(i, uc, lap_pair(uc, ysum, xp));
-        qb[ph % Q] = v;
-        *reinterpret_cast<float2 *>(wb + xo) = v;
+        for (int p = 0; p < kS2P; ++p) {
+          float2 xp[2 * PH + 1];
+#pragma unroll
+          for (int d = -PH; d <= PH; ++d)
+            xp[d + PH] = *reinterpret_cast<const float2 *>(ri + xo[p] + 2 * d);
+          const float2 uc = qa[p][(ph + Q - R) % Q];
+          auto ysum = [&](int k) -> float2 {
+            return __fadd2_rn(qa[p][(ph + Q - R + k) % Q], qa[p][(ph + 2 * Q - R - k) % Q]);
+          };
+          const float2 v = settle(p, i, uc, lap_pair(uc, ysum, xp));
+          qb[p][ph % Q] = v;
+          *reinterpret_cast<float2 *>(wb + xo[p]) = v;
+        }
       }
       __syncwarp();  // ring B row i visible to the warp
       if (t >= 4 * R) {
-        // stage 2: row o = i-R of u^{n+2} (stream row ya-4R+t) on the strip; lanes 0
-        // and 31 compute with ring B's zeroed edge columns and store nothing
+        // stage 2: row o = i-R of u^{n+2} (stream row ya-4R+t) on the strip; the edge
+        // pairs compute with ring B's zeroed edge columns and store nothing
         const int o = ya - 4 * R + t;
-        const float *ro = rb + ((ph + Q - R) % Q) * RW + HX + xo;  // row o of u^{n+1}
-        float2 xp[2 * PH + 1];
-#pragma unroll
-        for (int d = -PH; d <= PH; ++d) xp[d + PH] = *reinterpret_cast<const float2 *>(ro + 2 * d);
-        const float2 vc = qb[(ph + Q - R) % Q];
-        auto ysum = [&](int k) -> float2 {
-          return __fadd2_rn(qb[(ph + Q - R + k) % Q], qb[(ph + 2 * Q - R - k) % Q]);
-        };
-        const float2 val = lap_pair(vc, ysum, xp);
+        const float *ro = rb + ((ph + Q - R) % Q) * RW + HX;  // row o of u^{n+1}
         const bool yin = hold ? (o > 0 && o < g.n1 - 1) : true;
-        if (yin) {
-          const int64_t p = gidx(g, 0, o, x);
-          if (xin0 && xin1)
-            *reinterpret_cast<float2 *>(un + p) = val;
-          else {
-            if (xin0) un[p] = val.x;
-            if (xin1) un[p + 1] = val.y;
+#pragma unroll
+        for (int p = 0; p < kS2P; ++p) {
+          float2 xp[2 * PH + 1];
+#pragma unroll
+          for (int d = -PH; d <= PH; ++d)
+            xp[d + PH] = *reinterpret_cast<const float2 *>(ro + xo[p] + 2 * d);
+          const float2 vc = qb[p][(ph + Q - R) % Q];
+          auto ysum = [&](int k) -> float2 {
+            return __fadd2_rn(qb[p][(ph + Q - R + k) % Q], qb[p][(ph + 2 * Q - R - k) % Q]);
+          };
+          const float2 val = lap_pair(vc, ysum, xp);
+          if (yin) {
+            const int64_t q = gidx(g, 0, o, x[p]);
+            if (xin0[p] && xin1[p])
+              *reinterpret_cast<float2 *>(un + q) = val;
+            else {
+              if (xin0[p]) un[q] = val.x;
+              if (xin1[p]) un[q + 1] = val.y;
+            }
           }
         }
       }

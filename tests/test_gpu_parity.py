@@ -435,6 +435,30 @@ def test_2d_diffusion_two_steps_a_launch_are_bitwise_single_steps(so, shape):
             assert rel_l2(outs[0], ref) <= 1e-5
 
 
+@pytest.mark.parametrize("so", (2, 4))
+def test_2d_two_step_stream_with_two_pairs_a_lane(so):
+    """On a grid with enough 124-column strips to fill the GPU, the two-step stream
+    gives each lane two pairs (a 128-column intermediate strip): bitwise the plain
+    kernel's single steps, equal and unequal spacing, held and free boundary, a ragged
+    last strip (12000 = 96 strips of 124 + 96 columns), odd step count."""
+    from paper_1906_10811_b300 import Solver
+    shape = (4000, 12000)
+    rng = np.random.default_rng(11 + so)
+    u0 = rng.standard_normal(shape).astype(np.float32)
+    for h in ((1.0 / 50, 1.0 / 50), (1.0 / 40, 1.0 / 30)):
+        for hold in (True, False):
+            outs = []
+            for kernel in ("plain", "tma"):
+                with Solver(shape, h, so, 0.05 * min(h) ** 2, "diffusion", kernel=kernel,
+                            dirichlet_interior=hold) as s:
+                    if kernel == "tma":
+                        assert s.kernel_name == "stencil2d_stream2"
+                    s.set_field(u0)
+                    s.run(5)
+                    outs.append(s.read()[0])
+            assert np.array_equal(outs[1], outs[0]), (h, hold)
+
+
 def test_large_2d_diffusion_streams_rows_by_default():
     """From 4 M points a 2-D diffusion context runs the row-streaming kernel unless
     asked for plain; the acoustic step keeps the plain kernel; both kernels agree."""
