@@ -774,8 +774,10 @@ def diffusion2d_result(n=10000, orders=(2, 4, 8, 16), nt=100, reps=2):
         n_st, st_ms = s.profile()
         avg = st_ms / max(n_st, 1) / 1e3
         ach = BYTES_PER_POINT["diffusion"] * npts / avg / 1e9
-        moved = BYTES_PER_POINT["diffusion"] / (2 if s.kernel_name == "stencil2d_stream2" else 1)
-        out[f"so{so}"] = {"kernel": s.kernel_name, "us_per_launch": round(avg * 1e6, 2),
+        per_launch = 2 if s.kernel_name == "stencil2d_stream2" else 1
+        moved = BYTES_PER_POINT["diffusion"] / per_launch
+        out[f"so{so}"] = {"kernel": s.kernel_name, "steps_per_launch": per_launch,
+                          "us_per_launch": round(avg * per_launch * 1e6, 2),
                           "us_per_step": round(avg * 1e6, 2), "bytes_moved_per_point_step": moved,
                           "achieved_gbs": round(ach, 1), "frac": round(ach / peak, 4),
                           "gpts_per_s_kernel": round(npts / avg / 1e9, 2),
