@@ -131,6 +131,7 @@ struct fd_ctx {
   // 2-D diffusion, radius 1-2, zero halo: two steps a launch (u^{n+2} from u^n)
   StencilFnStream2 stream2d2_fn = nullptr;
   int s2_nseg = 0, s2_seglen = 0;         // its row segments per strip and their length
+  int s2_p = 1;                           // its pairs a lane (strips 64·s2_p wide)
   int s2t_nseg = 0, s2t_seglen = 0;       // the same for the two-step stream (strips s2t_w(P) wide)
   int s2t_p = 1;                          // its pairs a lane
   TmaPlan tma{};
@@ -406,9 +407,11 @@ fd_status launch_stencil(fd_ctx *c, const float *ucur, float *unext, int j) {
   }
   dim3 block(32, 8);
   if (c->stream2d_fn) {
-    const int64_t items = (int64_t)((c->g.n2 + kS2W - 1) / kS2W) * c->s2_nseg;
+    const int w = kS2W * c->s2_p;
+    const int64_t items = (int64_t)((c->g.n2 + w - 1) / w) * c->s2_nseg;
     const int nw = s2_warps(c->g.R);
-    c->stream2d_fn<<<(unsigned)((items + nw - 1) / nw), nw * 32, s2_smem(c->g.R), c->stream>>>(
+    c->stream2d_fn<<<(unsigned)((items + nw - 1) / nw), nw * 32, s2_smem(c->g.R, c->s2_p),
+                     c->stream>>>(
         ucur, unext, c->A, c->C, c->g, c->coef, c->s2_nseg, c->s2_seglen);
     CHECK_LAUNCH();
     return FD_OK;
@@ -744,8 +747,34 @@ void select_kernel(fd_ctx *c) {
       // about 64 warp streams per SM in all (measured ahead of sizing the grid to one
       // wave of the occupancy: 0.88 against 0.81 of the copy bandwidth at 10000² so 2),
       // segments of at least max(32, 4R) rows
-      const int strips = (c->g.n2 + kS2W - 1) / kS2W;
       const int most = std::max(1, c->g.n1 / std::max(32, 4 * R));
+      // diffusion at radius 2-6: two pairs a lane (128-column strips, the per-row work
+      // shared by twice the points) where the grid has the strips and segments for those
+      // streams (10000²: so 8 172.7 -> 153.1 µs, so 12 202.1 -> 178.1; at radius 1, 7
+      // and 8 one pair a lane was as fast or faster: the doubled loop body of radius
+      // 7-8 gives back the gain)
+      c->s2_p = 1;
+      if (!ac && R >= 2 && R <= 6 &&
+          (int64_t)((c->g.n2 + 2 * kS2W - 1) / (2 * kS2W)) * most >= 64 * sms) {
+        StencilFnStream f2 = nullptr;
+#define PICK2P(RR)                                                                     \
+  case RR:                                                                             \
+    f2 = iso2 ? k_stencil2d_stream<RR, kDiffusion, true, 2>                            \
+              : k_stencil2d_stream<RR, kDiffusion, false, 2>;                          \
+    break;
+        switch (R) {
+          PICK2P(2) PICK2P(3) PICK2P(4) PICK2P(5) PICK2P(6)
+        }
+#undef PICK2P
+        if (f2 && cudaFuncSetAttribute((const void *)f2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       s2_smem(R, 2)) == cudaSuccess) {
+          c->stream2d_fn = f2;
+          c->s2_p = 2;
+        } else {
+          cudaGetLastError();
+        }
+      }
+      const int strips = (c->g.n2 + kS2W * c->s2_p - 1) / (kS2W * c->s2_p);
       const int nseg = std::max(1, std::min((64 * sms + strips - 1) / strips, most));
       c->s2_seglen = (c->g.n1 + nseg - 1) / nseg;
       c->s2_nseg = (c->g.n1 + c->s2_seglen - 1) / c->s2_seglen;

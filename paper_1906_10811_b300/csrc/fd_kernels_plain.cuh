@@ -87,12 +87,13 @@ k_stencil_plain(const float *__restrict__ u, float *un, const float *__restrict_
 }
 
 // ---------------------------------------------------------------------------
-// 2-D step streamed along y.  A warp owns a strip of kS2W = 64 columns (a lane per
-// pair of adjacent x points) and a segment of rows [ya, yb).  Rows ya-R .. yb+R-1
+// 2-D step streamed along y.  A warp owns a strip of 64·NP columns (a lane per NP
+// pairs of adjacent x points, one in each 64-column part) and a segment of rows
+// [ya, yb).  Rows ya-R .. yb+R-1
 // of u^n (with the x halo) are copied into the warp's ring in shared memory with
 // cp.async, s2_d(R) rows ahead of the row in use, so many bytes stay in flight (one
 // thread per point keeps too few to fill HBM on large grids).  Each arriving row's
-// values at the lane's pair enter a register queue of 2R+1 rows; R rows later the
+// values at the lane's pairs enter a register queue of 2R+1 rows; R rows later the
 // warp updates the middle row: the y part of the Laplacian from the queue, the x
 // part from that row's staged copy, still in the ring.  The per-point operation
 // sequence is plain_lap's and plain_point's (packed FP32x2 over the pair: each
@@ -100,9 +101,11 @@ k_stencil_plain(const float *__restrict__ u, float *un, const float *__restrict_
 // kernel's.  Warps are independent streams; neighbouring strips of a segment run
 // together, so the halo columns they share come from L2.
 // ---------------------------------------------------------------------------
-constexpr int kS2W = 64;  // strip width (columns)
+constexpr int kS2W = 64;  // strip width (columns) a pair a lane
 __host__ __device__ constexpr int s2_hx(int R) { return (R + 3) / 4 * 4; }  // x halo, 16-B multiple
-__host__ __device__ constexpr int s2_rw(int R) { return kS2W + 2 * s2_hx(R); }  // staged row (floats)
+__host__ __device__ constexpr int s2_rw(int R, int P = 1) {  // staged row (floats), P pairs a lane
+  return kS2W * P + 2 * s2_hx(R);
+}
 // ring rows per warp: a multiple of the queue length 2R+1 (an unrolled group of that
 // many rows then addresses ring and queue slots statically) holding the R rows back
 // to the one being updated, the row in use and about 8 rows in flight.  Above radius
@@ -117,7 +120,12 @@ __host__ __device__ constexpr int s2_d(int R) {  // rows in flight
 }
 // warps (streams) per block: 8, or 4 above radius 4 (registers and the ring)
 __host__ __device__ constexpr int s2_warps(int R) { return R <= 4 ? 8 : 4; }
-__host__ __device__ constexpr int s2_smem(int R) { return s2_warps(R) * s2_nr(R) * s2_rw(R) * 4; }
+__host__ __device__ constexpr int s2_smem(int R, int P = 1) {
+  return s2_warps(R) * s2_nr(R) * s2_rw(R, P) * 4;
+}
+// blocks an SM the registers are sized for: two pairs a lane up to radius 4 keep two
+// blocks of 8 warps (128 registers a thread)
+__host__ __device__ constexpr int s2_minb(int R, int P) { return P == 2 && R <= 4 ? 2 : 1; }
 
 __device__ __forceinline__ uint32_t s2_saddr(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -134,22 +142,24 @@ __device__ __forceinline__ void s2_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-template <int R, int EQ, bool ISO2 = false>
-__global__ void __launch_bounds__(s2_warps(R) * 32)
+template <int R, int EQ, bool ISO2 = false, int NP = 1>
+__global__ void __launch_bounds__(s2_warps(R) * 32, s2_minb(R, NP))
 k_stencil2d_stream(const float *__restrict__ u, float *un, const float *__restrict__ A,
                    const float *__restrict__ C, Geom g, Coef c, int nseg, int seglen) {
-  constexpr int HX = s2_hx(R), RW = s2_rw(R), NR = s2_nr(R), Q = 2 * R + 1, D = s2_d(R);
+  constexpr int HX = s2_hx(R), RW = s2_rw(R, NP), NR = s2_nr(R), Q = 2 * R + 1, D = s2_d(R);
+  constexpr int W = kS2W * NP;  // strip width
   constexpr int NWP = s2_warps(R);
   constexpr int PH = (R + 1) / 2;  // x pairs each side of the lane's own
   constexpr bool AC = EQ == kAcoustic;
   static_assert(NR % Q == 0 && NR >= D + R + 2, "ring holds the rows in flight and in use");
+  static_assert(NP == 1 || NP == 2, "one or two pairs a lane");
   extern __shared__ __align__(16) float s2_ring[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int strips = (g.n2 + kS2W - 1) / kS2W;
+  const int strips = (g.n2 + W - 1) / W;
   const int item = blockIdx.x * NWP + warp;
   if (item >= strips * nseg) return;
   const int strip = item % strips, seg = item / strips;  // neighbouring strips together
-  const int x0 = strip * kS2W;
+  const int x0 = strip * W;
   const int ya = seg * seglen, yb = min(g.n1, ya + seglen);
   if (ya >= yb) return;
   float *rg = s2_ring + (size_t)warp * NR * RW;
@@ -169,11 +179,15 @@ k_stencil2d_stream(const float *__restrict__ u, float *un, const float *__restri
     }
     s2_commit();  // an empty group past the end keeps the wait count fixed
   };
-  const int x = x0 + 2 * lane;
   const bool hold = !AC && g.hold;
-  const bool xin0 = hold ? (x > 0 && x < g.n2 - 1) : x < g.n2;
-  const bool xin1 = hold ? (x + 1 > 0 && x + 1 < g.n2 - 1) : x + 1 < g.n2;
-  float2 q[Q];  // u^n at the pair, row t in slot t % Q
+  bool xin0[NP], xin1[NP];  // the points of pair p (x = x0 + 64p + 2·lane) to update
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const int x = x0 + kS2W * p + 2 * lane;
+    xin0[p] = hold ? (x > 0 && x < g.n2 - 1) : x < g.n2;
+    xin1[p] = hold ? (x + 1 > 0 && x + 1 < g.n2 - 1) : x + 1 < g.n2;
+  }
+  float2 q[NP][Q];  // u^n at pair p, row t in slot t % Q
 #pragma unroll
   for (int t = 0; t < D; ++t) issue(t);
   for (int tb = 0; tb < T; tb += NR) {
@@ -184,62 +198,68 @@ k_stencil2d_stream(const float *__restrict__ u, float *un, const float *__restri
       issue(t + D);
       s2_wait<D>();  // row t's copies (all but the newest D groups) have landed
       __syncwarp();
-      q[ph % Q] = *reinterpret_cast<const float2 *>(rg + ph * RW + HX + 2 * lane);
+#pragma unroll
+      for (int p = 0; p < NP; ++p)
+        q[p][ph % Q] = *reinterpret_cast<const float2 *>(rg + ph * RW + HX + kS2W * p + 2 * lane);
       if (t >= 2 * R) {  // row y = ya + t - 2R: its y neighbours are all in the queue
         const int y = ya + t - 2 * R;
-        const float2 ucy = q[(ph + Q - R) % Q];
-        float2 lap = make_float2(0.f, 0.f);
-        const float *rr = rg + ((ph + NR - R) % NR) * RW + HX + 2 * lane;  // row y, staged
-        float2 xp[2 * PH + 1];  // the row's pairs around the lane's own
-#pragma unroll
-        for (int d = -PH; d <= PH; ++d) xp[d + PH] = *reinterpret_cast<const float2 *>(rr + 2 * d);
-        // u(x+k) + u(x-k) at the pair: aligned pairs for even k, halves of the
-        // neighbouring pairs for odd k
-        auto xsum = [&](int k) -> float2 {
-          if ((k & 1) == 0) return __fadd2_rn(xp[PH + k / 2], xp[PH - k / 2]);
-          return make_float2(__fadd_rn(xp[PH + (k - 1) / 2].y, xp[PH - (k + 1) / 2].y),
-                             __fadd_rn(xp[PH + (k + 1) / 2].x, xp[PH - (k - 1) / 2].x));
-        };
-        auto ysum = [&](int k) -> float2 {  // u(y+k) + u(y-k) from the queue
-          return __fadd2_rn(q[(ph + Q - R + k) % Q], q[(ph + 2 * Q - R - k) % Q]);
-        };
-        if constexpr (ISO2) {  // plain_lap's equal-spacing form
-          const float2 nuc4 = make_float2(-4.f * ucy.x, -4.f * ucy.y);
-#pragma unroll
-          for (int k = 1; k <= R; ++k)
-            lap = __ffma2_rn(c.wp[2][k], __fadd2_rn(__fadd2_rn(ysum(k), xsum(k)), nuc4), lap);
-        } else {
-          const float2 nuc2 = make_float2(-(ucy.x + ucy.x), -(ucy.y + ucy.y));
-#pragma unroll
-          for (int k = 1; k <= R; ++k) lap = __ffma2_rn(c.wp[1][k], __fadd2_rn(ysum(k), nuc2), lap);
-#pragma unroll
-          for (int k = 1; k <= R; ++k) lap = __ffma2_rn(c.wp[2][k], __fadd2_rn(xsum(k), nuc2), lap);
-        }
         const bool yin = hold ? (y > 0 && y < g.n1 - 1) : true;
-        const int64_t p = gidx(g, 0, y, x);
-        float2 val;
-        if (AC) {
-          float2 prev, a, cc;
-          if (xin0 && xin1) {
-            prev = *reinterpret_cast<const float2 *>(un + p);
-            a = *reinterpret_cast<const float2 *>(A + p);
-            cc = *reinterpret_cast<const float2 *>(C + p);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+          const int x = x0 + kS2W * p + 2 * lane;
+          const float2 ucy = q[p][(ph + Q - R) % Q];
+          float2 lap = make_float2(0.f, 0.f);
+          const float *rr = rg + ((ph + NR - R) % NR) * RW + HX + kS2W * p + 2 * lane;  // row y
+          float2 xp[2 * PH + 1];  // the row's pairs around the lane's own
+#pragma unroll
+          for (int d = -PH; d <= PH; ++d) xp[d + PH] = *reinterpret_cast<const float2 *>(rr + 2 * d);
+          // u(x+k) + u(x-k) at the pair: aligned pairs for even k, halves of the
+          // neighbouring pairs for odd k
+          auto xsum = [&](int k) -> float2 {
+            if ((k & 1) == 0) return __fadd2_rn(xp[PH + k / 2], xp[PH - k / 2]);
+            return make_float2(__fadd_rn(xp[PH + (k - 1) / 2].y, xp[PH - (k + 1) / 2].y),
+                               __fadd_rn(xp[PH + (k + 1) / 2].x, xp[PH - (k - 1) / 2].x));
+          };
+          auto ysum = [&](int k) -> float2 {  // u(y+k) + u(y-k) from the queue
+            return __fadd2_rn(q[p][(ph + Q - R + k) % Q], q[p][(ph + 2 * Q - R - k) % Q]);
+          };
+          if constexpr (ISO2) {  // plain_lap's equal-spacing form
+            const float2 nuc4 = make_float2(-4.f * ucy.x, -4.f * ucy.y);
+#pragma unroll
+            for (int k = 1; k <= R; ++k)
+              lap = __ffma2_rn(c.wp[2][k], __fadd2_rn(__fadd2_rn(ysum(k), xsum(k)), nuc4), lap);
           } else {
-            prev = make_float2(xin0 ? un[p] : 0.f, xin1 ? un[p + 1] : 0.f);
-            a = make_float2(xin0 ? A[p] : 0.f, xin1 ? A[p + 1] : 0.f);
-            cc = make_float2(xin0 ? C[p] : 0.f, xin1 ? C[p + 1] : 0.f);
+            const float2 nuc2 = make_float2(-(ucy.x + ucy.x), -(ucy.y + ucy.y));
+#pragma unroll
+            for (int k = 1; k <= R; ++k) lap = __ffma2_rn(c.wp[1][k], __fadd2_rn(ysum(k), nuc2), lap);
+#pragma unroll
+            for (int k = 1; k <= R; ++k) lap = __ffma2_rn(c.wp[2][k], __fadd2_rn(xsum(k), nuc2), lap);
           }
-          val = make_float2(leapfrog(a.x, cc.x, ucy.x, prev.x, lap.x),
-                            leapfrog(a.y, cc.y, ucy.y, prev.y, lap.y));
-        } else {
-          val = make_float2(ucy.x + lap.x, ucy.y + lap.y);
-        }
-        if (yin) {
-          if (xin0 && xin1)
-            *reinterpret_cast<float2 *>(un + p) = val;
-          else {
-            if (xin0) un[p] = val.x;
-            if (xin1) un[p + 1] = val.y;
+          const int64_t pi = gidx(g, 0, y, x);
+          float2 val;
+          if (AC) {
+            float2 prev, a, cc;
+            if (xin0[p] && xin1[p]) {
+              prev = *reinterpret_cast<const float2 *>(un + pi);
+              a = *reinterpret_cast<const float2 *>(A + pi);
+              cc = *reinterpret_cast<const float2 *>(C + pi);
+            } else {
+              prev = make_float2(xin0[p] ? un[pi] : 0.f, xin1[p] ? un[pi + 1] : 0.f);
+              a = make_float2(xin0[p] ? A[pi] : 0.f, xin1[p] ? A[pi + 1] : 0.f);
+              cc = make_float2(xin0[p] ? C[pi] : 0.f, xin1[p] ? C[pi + 1] : 0.f);
+            }
+            val = make_float2(leapfrog(a.x, cc.x, ucy.x, prev.x, lap.x),
+                              leapfrog(a.y, cc.y, ucy.y, prev.y, lap.y));
+          } else {
+            val = make_float2(ucy.x + lap.x, ucy.y + lap.y);
+          }
+          if (yin) {
+            if (xin0[p] && xin1[p])
+              *reinterpret_cast<float2 *>(un + pi) = val;
+            else {
+              if (xin0[p]) un[pi] = val.x;
+              if (xin1[p]) un[pi + 1] = val.y;
+            }
           }
         }
       }

@@ -459,6 +459,38 @@ def test_2d_two_step_stream_with_two_pairs_a_lane(so):
             assert np.array_equal(outs[1], outs[0]), (h, hold)
 
 
+@pytest.mark.parametrize("so,boundary", ((6, "zero"), (8, "zero"), (10, "zero"), (12, "zero"),
+                                         (4, "odd")))
+def test_2d_stream_with_two_pairs_a_lane(so, boundary):
+    """At radius 2-6, where the grid has enough 128-column strips and segments of
+    max(32, 2·so) rows for 64 warp streams an SM, the one-step 2-D diffusion stream
+    gives each lane two pairs: bitwise the plain kernel, equal and unequal spacing,
+    held and free boundary (zero halo; so 4 runs one step a launch with the odd
+    reflection), a ragged last strip (12000 = 93 strips of 128 + 96 columns)."""
+    import torch
+    from paper_1906_10811_b300 import Solver
+    shape = (4000, 12000)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert -(-shape[1] // 128) * (shape[0] // max(32, 2 * so)) >= 64 * sms
+    rng = np.random.default_rng(23 + so)
+    u0 = rng.standard_normal(shape).astype(np.float32)
+    if boundary == "odd":
+        u0[0, :] = u0[-1, :] = u0[:, 0] = u0[:, -1] = 0.0
+    holds = (True, False) if boundary == "zero" else (True,)
+    for h in ((1.0 / 50, 1.0 / 50), (1.0 / 40, 1.0 / 30)):
+        for hold in holds:
+            outs = []
+            for kernel in ("plain", "tma"):
+                with Solver(shape, h, so, 0.02 * min(h) ** 2, "diffusion", kernel=kernel,
+                            dirichlet_interior=hold, boundary=boundary) as s:
+                    if kernel == "tma":
+                        assert s.kernel_name == "stencil2d_stream"
+                    s.set_field(u0)
+                    s.run(3)
+                    outs.append(s.read()[0])
+            assert np.array_equal(outs[1], outs[0]), (h, hold)
+
+
 def test_large_2d_diffusion_streams_rows_by_default():
     """From 4 M points a 2-D diffusion context runs the row-streaming kernel unless
     asked for plain; the acoustic step keeps the plain kernel; both kernels agree."""
