@@ -131,7 +131,7 @@ struct fd_ctx {
   // 2-D diffusion, radius 1-2, zero halo: two steps a launch (u^{n+2} from u^n)
   StencilFnStream2 stream2d2_fn = nullptr;
   int s2_nseg = 0, s2_seglen = 0;         // its row segments per strip and their length
-  int s2_p = 1;                           // its pairs a lane (strips 64·s2_p wide)
+  int s2_p = 1;                           // its pairs a lane, adjacent (strips 64·s2_p wide)
   int s2t_nseg = 0, s2t_seglen = 0;       // the same for the two-step stream (strips s2t_w(P) wide)
   int s2t_p = 1;                          // its pairs a lane
   TmaPlan tma{};
@@ -748,13 +748,13 @@ void select_kernel(fd_ctx *c) {
       // wave of the occupancy: 0.88 against 0.81 of the copy bandwidth at 10000² so 2),
       // segments of at least max(32, 4R) rows
       const int most = std::max(1, c->g.n1 / std::max(32, 4 * R));
-      // diffusion at radius 2-6: two pairs a lane (128-column strips, the per-row work
-      // shared by twice the points) where the grid has the strips and segments for those
-      // streams (10000²: so 8 172.7 -> 153.1 µs, so 12 202.1 -> 178.1; at radius 1, 7
-      // and 8 one pair a lane was as fast or faster: the doubled loop body of radius
-      // 7-8 gives back the gain)
+      // diffusion at radius 2-7: four adjacent points a lane (128-column strips, 16-byte
+      // shared-memory reads and stores, the per-row work shared by twice the points)
+      // where the grid has the strips and segments for those streams (10000²: so 8
+      // 172.7 -> 148.6 µs, so 12 202.1 -> 163.1, so 14 212.3 -> 203.3; at radius 1 and 8
+      // one pair a lane was as fast or faster)
       c->s2_p = 1;
-      if (!ac && R >= 2 && R <= 6 &&
+      if (!ac && R >= 2 && R <= 7 &&
           (int64_t)((c->g.n2 + 2 * kS2W - 1) / (2 * kS2W)) * most >= 64 * sms) {
         StencilFnStream f2 = nullptr;
 #define PICK2P(RR)                                                                     \
@@ -763,7 +763,7 @@ void select_kernel(fd_ctx *c) {
               : k_stencil2d_stream<RR, kDiffusion, false, 2>;                          \
     break;
         switch (R) {
-          PICK2P(2) PICK2P(3) PICK2P(4) PICK2P(5) PICK2P(6)
+          PICK2P(2) PICK2P(3) PICK2P(4) PICK2P(5) PICK2P(6) PICK2P(7)
         }
 #undef PICK2P
         if (f2 && cudaFuncSetAttribute((const void *)f2, cudaFuncAttributeMaxDynamicSharedMemorySize,

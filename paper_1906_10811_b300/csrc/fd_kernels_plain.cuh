@@ -87,9 +87,9 @@ k_stencil_plain(const float *__restrict__ u, float *un, const float *__restrict_
 }
 
 // ---------------------------------------------------------------------------
-// 2-D step streamed along y.  A warp owns a strip of 64·NP columns (a lane per NP
-// pairs of adjacent x points, one in each 64-column part) and a segment of rows
-// [ya, yb).  Rows ya-R .. yb+R-1
+// 2-D step streamed along y.  A warp owns a strip of 64·NP columns (a lane per pair
+// of adjacent x points, or with NP = 2 per four adjacent points, read from shared
+// memory 16 bytes at a time) and a segment of rows [ya, yb).  Rows ya-R .. yb+R-1
 // of u^n (with the x halo) are copied into the warp's ring in shared memory with
 // cp.async, s2_d(R) rows ahead of the row in use, so many bytes stay in flight (one
 // thread per point keeps too few to fill HBM on large grids).  Each arriving row's
@@ -123,8 +123,8 @@ __host__ __device__ constexpr int s2_warps(int R) { return R <= 4 ? 8 : 4; }
 __host__ __device__ constexpr int s2_smem(int R, int P = 1) {
   return s2_warps(R) * s2_nr(R) * s2_rw(R, P) * 4;
 }
-// blocks an SM the registers are sized for: two pairs a lane up to radius 4 keep two
-// blocks of 8 warps (128 registers a thread)
+// blocks an SM the registers are sized for: four points a lane up to radius 4 keep
+// two blocks of 8 warps (128 registers a thread)
 __host__ __device__ constexpr int s2_minb(int R, int P) { return P == 2 && R <= 4 ? 2 : 1; }
 
 __device__ __forceinline__ uint32_t s2_saddr(const void *p) {
@@ -152,7 +152,7 @@ k_stencil2d_stream(const float *__restrict__ u, float *un, const float *__restri
   constexpr int PH = (R + 1) / 2;  // x pairs each side of the lane's own
   constexpr bool AC = EQ == kAcoustic;
   static_assert(NR % Q == 0 && NR >= D + R + 2, "ring holds the rows in flight and in use");
-  static_assert(NP == 1 || NP == 2, "one or two pairs a lane");
+  static_assert(NP == 1 || NP == 2, "one pair or four adjacent points a lane");
   extern __shared__ __align__(16) float s2_ring[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int strips = (g.n2 + W - 1) / W;
@@ -180,10 +180,12 @@ k_stencil2d_stream(const float *__restrict__ u, float *un, const float *__restri
     s2_commit();  // an empty group past the end keeps the wait count fixed
   };
   const bool hold = !AC && g.hold;
-  bool xin0[NP], xin1[NP];  // the points of pair p (x = x0 + 64p + 2·lane) to update
+  constexpr int LW = 2 * NP;  // points a lane: its pairs p at x0 + LW·lane + 2p
+  constexpr int CH = HX / 4;  // 16-byte chunks of the staged row each side of a lane's four
+  bool xin0[NP], xin1[NP];    // the points of pair p to update
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
-    const int x = x0 + kS2W * p + 2 * lane;
+    const int x = x0 + LW * lane + 2 * p;
     xin0[p] = hold ? (x > 0 && x < g.n2 - 1) : x < g.n2;
     xin1[p] = hold ? (x + 1 > 0 && x + 1 < g.n2 - 1) : x + 1 < g.n2;
   }
@@ -198,27 +200,52 @@ k_stencil2d_stream(const float *__restrict__ u, float *un, const float *__restri
       issue(t + D);
       s2_wait<D>();  // row t's copies (all but the newest D groups) have landed
       __syncwarp();
-#pragma unroll
-      for (int p = 0; p < NP; ++p)
-        q[p][ph % Q] = *reinterpret_cast<const float2 *>(rg + ph * RW + HX + kS2W * p + 2 * lane);
+      if constexpr (NP == 1) {
+        q[0][ph % Q] = *reinterpret_cast<const float2 *>(rg + ph * RW + HX + 2 * lane);
+      } else {
+        const float4 v = *reinterpret_cast<const float4 *>(rg + ph * RW + HX + 4 * lane);
+        q[0][ph % Q] = make_float2(v.x, v.y);
+        q[1][ph % Q] = make_float2(v.z, v.w);
+      }
       if (t >= 2 * R) {  // row y = ya + t - 2R: its y neighbours are all in the queue
         const int y = ya + t - 2 * R;
         const bool yin = hold ? (y > 0 && y < g.n1 - 1) : true;
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
-          const int x = x0 + kS2W * p + 2 * lane;
-          const float2 ucy = q[p][(ph + Q - R) % Q];
-          float2 lap = make_float2(0.f, 0.f);
-          const float *rr = rg + ((ph + NR - R) % NR) * RW + HX + kS2W * p + 2 * lane;  // row y
-          float2 xp[2 * PH + 1];  // the row's pairs around the lane's own
+        const float *rr = rg + ((ph + NR - R) % NR) * RW + HX + LW * lane;  // row y, staged
+        float2 xp[NP == 1 ? 2 * PH + 1 : 1];  // one pair: the row's pairs around its own
+        float4 xc[NP == 1 ? 1 : 2 * CH + 1];  // four points: the 16-byte chunks around them
+        if constexpr (NP == 1) {
 #pragma unroll
           for (int d = -PH; d <= PH; ++d) xp[d + PH] = *reinterpret_cast<const float2 *>(rr + 2 * d);
+        } else {
+#pragma unroll
+          for (int d = -CH; d <= CH; ++d) xc[d + CH] = *reinterpret_cast<const float4 *>(rr + 4 * d);
+        }
+        auto xv = [&](int i) -> float {  // four points: u at the lane's first x + i
+          const int j = i + 4 * CH;
+          const float4 &c4 = xc[j >> 2];
+          return (j & 3) == 0 ? c4.x : (j & 3) == 1 ? c4.y : (j & 3) == 2 ? c4.z : c4.w;
+        };
+        float2 val[NP];  // u^{n+1} at the lane's pairs
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+          const int x = x0 + LW * lane + 2 * p;
+          const float2 ucy = q[p][(ph + Q - R) % Q];
+          float2 lap = make_float2(0.f, 0.f);
           // u(x+k) + u(x-k) at the pair: aligned pairs for even k, halves of the
           // neighbouring pairs for odd k
           auto xsum = [&](int k) -> float2 {
-            if ((k & 1) == 0) return __fadd2_rn(xp[PH + k / 2], xp[PH - k / 2]);
-            return make_float2(__fadd_rn(xp[PH + (k - 1) / 2].y, xp[PH - (k + 1) / 2].y),
-                               __fadd_rn(xp[PH + (k + 1) / 2].x, xp[PH - (k - 1) / 2].x));
+            if constexpr (NP == 1) {
+              if ((k & 1) == 0) return __fadd2_rn(xp[PH + k / 2], xp[PH - k / 2]);
+              return make_float2(__fadd_rn(xp[PH + (k - 1) / 2].y, xp[PH - (k + 1) / 2].y),
+                                 __fadd_rn(xp[PH + (k + 1) / 2].x, xp[PH - (k - 1) / 2].x));
+            } else {
+              const int o = 2 * p;
+              if ((k & 1) == 0)
+                return __fadd2_rn(make_float2(xv(o + k), xv(o + k + 1)),
+                                  make_float2(xv(o - k), xv(o - k + 1)));
+              return make_float2(__fadd_rn(xv(o + k), xv(o - k)),
+                                 __fadd_rn(xv(o + 1 + k), xv(o + 1 - k)));
+            }
           };
           auto ysum = [&](int k) -> float2 {  // u(y+k) + u(y-k) from the queue
             return __fadd2_rn(q[p][(ph + Q - R + k) % Q], q[p][(ph + 2 * Q - R - k) % Q]);
@@ -236,7 +263,6 @@ k_stencil2d_stream(const float *__restrict__ u, float *un, const float *__restri
             for (int k = 1; k <= R; ++k) lap = __ffma2_rn(c.wp[2][k], __fadd2_rn(xsum(k), nuc2), lap);
           }
           const int64_t pi = gidx(g, 0, y, x);
-          float2 val;
           if (AC) {
             float2 prev, a, cc;
             if (xin0[p] && xin1[p]) {
@@ -248,17 +274,28 @@ k_stencil2d_stream(const float *__restrict__ u, float *un, const float *__restri
               a = make_float2(xin0[p] ? A[pi] : 0.f, xin1[p] ? A[pi + 1] : 0.f);
               cc = make_float2(xin0[p] ? C[pi] : 0.f, xin1[p] ? C[pi + 1] : 0.f);
             }
-            val = make_float2(leapfrog(a.x, cc.x, ucy.x, prev.x, lap.x),
-                              leapfrog(a.y, cc.y, ucy.y, prev.y, lap.y));
+            val[p] = make_float2(leapfrog(a.x, cc.x, ucy.x, prev.x, lap.x),
+                                 leapfrog(a.y, cc.y, ucy.y, prev.y, lap.y));
           } else {
-            val = make_float2(ucy.x + lap.x, ucy.y + lap.y);
+            val[p] = make_float2(ucy.x + lap.x, ucy.y + lap.y);
           }
-          if (yin) {
-            if (xin0[p] && xin1[p])
-              *reinterpret_cast<float2 *>(un + pi) = val;
-            else {
-              if (xin0[p]) un[pi] = val.x;
-              if (xin1[p]) un[pi + 1] = val.y;
+        }
+        // the four points in one 16-byte store where all are updated (x a multiple of 4,
+        // row pitch and x halo multiples of 32 floats: aligned), else point by point
+        if (yin) {
+          const int64_t pi = gidx(g, 0, y, x0 + LW * lane);
+          if (NP == 2 && xin0[0] && xin1[0] && xin0[NP - 1] && xin1[NP - 1]) {
+            *reinterpret_cast<float4 *>(un + pi) =
+                make_float4(val[0].x, val[0].y, val[NP - 1].x, val[NP - 1].y);
+          } else {
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+              if (xin0[p] && xin1[p])
+                *reinterpret_cast<float2 *>(un + pi + 2 * p) = val[p];
+              else {
+                if (xin0[p]) un[pi + 2 * p] = val[p].x;
+                if (xin1[p]) un[pi + 2 * p + 1] = val[p].y;
+              }
             }
           }
         }

@@ -460,11 +460,12 @@ def test_2d_two_step_stream_with_two_pairs_a_lane(so):
 
 
 @pytest.mark.parametrize("so,boundary", ((6, "zero"), (8, "zero"), (10, "zero"), (12, "zero"),
-                                         (4, "odd")))
-def test_2d_stream_with_two_pairs_a_lane(so, boundary):
-    """At radius 2-6, where the grid has enough 128-column strips and segments of
+                                         (14, "zero"), (4, "odd")))
+def test_2d_stream_with_four_points_a_lane(so, boundary):
+    """At radius 2-7, where the grid has enough 128-column strips and segments of
     max(32, 2·so) rows for 64 warp streams an SM, the one-step 2-D diffusion stream
-    gives each lane two pairs: bitwise the plain kernel, equal and unequal spacing,
+    gives each lane four adjacent points (16-byte shared-memory reads, one 16-byte
+    store where all four are updated): bitwise the plain kernel, equal and unequal spacing,
     held and free boundary (zero halo; so 4 runs one step a launch with the odd
     reflection), a ragged last strip (12000 = 93 strips of 128 + 96 columns)."""
     import torch
