@@ -93,6 +93,8 @@ def parse():
                     help="serving: most grid points one batch tick updates (0: no cap); "
                          "65 M (about four 256^3 shots) keeps the GPU saturated while a "
                          "long shot is not stretched by everything admitted beside it")
+    ap.add_argument("--ticks-per-round", type=int, default=32,
+                    help="serving: most batch steps between admission points")
     ap.add_argument("--so", type=int, default=None)
     ap.add_argument("--n", type=int, default=None,
                     help="acoustic workloads: grid points per axis instead of the workload's")
@@ -1071,7 +1073,7 @@ def serving_result(args, rank=0, world=1):
     clocks = ClockSampler(gpu_id)
     be = DeviceBackend(8)
     srv = Server(be, hbm_budget=int(args.hbm_budget_gb * 2 ** 30), max_members=64,
-                 ticks_per_round=32, work_cap=args.work_cap)
+                 ticks_per_round=args.ticks_per_round, work_cap=args.work_cap)
     batched = summarize(srv.serve(reqs))
     be.close()
     seq = summarize(serve_sequential(reqs))
@@ -1086,7 +1088,8 @@ def serving_result(args, rank=0, world=1):
                        "receivers": "128-512", "mean_gap_s": args.mean_gap,
                        "hbm_budget_gb": args.hbm_budget_gb, "grid_point_updates": pts,
                        "admission": "first come first served, tick work cap %d points" %
-                                    args.work_cap},
+                                    args.work_cap,
+                       "ticks_per_round": args.ticks_per_round},
             "serving": {k: round(v, 4) for k, v in batched.items()},
             "sequential": {k: round(v, 4) for k, v in seq.items()},
             "speedup_vs_sequential": round(batched["shots_per_s"] / seq["shots_per_s"], 3),
